@@ -1,0 +1,120 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds only input generation: contrasts q(x) given as plain
+functions of position, sine-coefficient arrays, incidence angles and receiver
+angles.  It contains none of the solver's arithmetic (no discretisation, no
+Green's functions, no linear algebra), so that the CUDA path and the CPU
+oracle can both draw their inputs from it without sharing any method code.
+
+Workloads follow the paper's experiments (Sec. 4): plane-wave incidence from
+equispaced directions d_m = (cos 2 pi m/M, sin 2 pi m/M) and receivers at
+x_p = R (cos 2 pi p/P, sin 2 pi p/P) on a circle of radius R enclosing the
+domain Omega = [-1, 1]^2; contrasts are smooth bumps or blurred inclusions of
+the amplitudes used there, scaled so that 1 - q stays positive (Sec. 2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "GaussianBumps",
+    "gaussian_bumps",
+    "smooth_random_coeffs",
+    "directions",
+    "receivers",
+    "random_coeffs",
+    "WORKLOADS",
+    "Workload",
+]
+
+
+@dataclass(frozen=True)
+class GaussianBumps:
+    """q(x) = sum_i a_i exp(-|x - c_i|^2 / (2 w_i^2)) restricted to Omega."""
+
+    centres: np.ndarray  # (n, 2)
+    widths: np.ndarray   # (n,)
+    amps: np.ndarray     # (n,)
+
+    def __call__(self, x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = np.zeros(np.broadcast(x, y).shape)
+        for (cx, cy), w, a in zip(self.centres, self.widths, self.amps):
+            out = out + a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2.0 * w * w))
+        inside = (np.abs(x) <= 1.0) & (np.abs(y) <= 1.0)
+        return np.where(inside, out, 0.0)
+
+
+def gaussian_bumps(seed: int = 1, n: int = 3, centre_box: float = 0.6,
+                   width_range=(0.15, 0.3), amp_range=(0.1, 0.4)) -> GaussianBumps:
+    """Sum of `n` Gaussian bumps with seeded centres, widths and amplitudes.
+
+    Defaults: 3 bumps, centres U[-0.6, 0.6]^2, widths U[0.15, 0.3],
+    amplitudes U[0.1, 0.4] (so max q < 1.2 only if bumps overlap strongly;
+    1 - q > 0 is checked by the caller).
+    """
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(-centre_box, centre_box, size=(n, 2))
+    widths = rng.uniform(*width_range, size=n)
+    amps = rng.uniform(*amp_range, size=n)
+    return GaussianBumps(centres, widths, amps)
+
+
+def smooth_random_coeffs(S: int, seed: int = 2, decay: float = 8.0,
+                         qmax: float = 0.3, grid: int = 513) -> np.ndarray:
+    """Sine coefficients c[m1-1, m2-1] ~ N(0,1) exp(-|m|/decay), |m| = sqrt(m1^2+m2^2).
+
+    The array is scaled so that max |q| over a uniform `grid` x `grid` sample of
+    Omega equals `qmax`, where q(x) = sum c[m1,m2] sin(m1 pi (x1+1)/2) sin(m2 pi (x2+1)/2)
+    is the band-limited contrast of Sec. 3.2 (eq. sineseries) on [-1,1]^2.
+    """
+    rng = np.random.default_rng(seed)
+    m = np.arange(1, S + 1, dtype=np.float64)
+    mag = np.sqrt(m[:, None] ** 2 + m[None, :] ** 2)
+    c = rng.standard_normal((S, S)) * np.exp(-mag / decay)
+    t = np.linspace(-1.0, 1.0, grid)
+    basis = np.sin(np.outer(m, t + 1.0) * (math.pi / 2.0))  # (S, grid)
+    q = basis.T @ c @ basis
+    return c * (qmax / np.max(np.abs(q)))
+
+
+def random_coeffs(S1: int, S2: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Plain N(0, scale^2) coefficients (S1, S2) for perturbation tests."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal((S1, S2))
+
+
+def directions(M: int) -> np.ndarray:
+    """Incidence angles alpha_m = 2 pi m / M, m = 0..M-1 (d = (cos, sin))."""
+    return 2.0 * math.pi * np.arange(M, dtype=np.float64) / M
+
+
+def receivers(P: int) -> np.ndarray:
+    """Receiver angles theta_p = 2 pi p / P, p = 0..P-1 on the circle of radius R."""
+    return 2.0 * math.pi * np.arange(P, dtype=np.float64) / P
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    k: float
+    n_leaf_side: int
+    S: int
+    M: int
+    P: int
+    R: float = 3.0
+
+
+# The workloads the tests and the benchmark use (sizes of the paper-shaped runs).
+WORKLOADS = {
+    # one Gauss-Newton step at k = 5 from q = 0, data from 3 Gaussian bumps
+    "gn_k5": Workload("gn_k5_4x4leaves_100modes_16dirs_32recv", 5.0, 4, 10, 16, 32),
+    # forward-only batched solve at k = 40 on 32 x 32 leaves
+    "fwd_k40": Workload("fwd_k40_32x32leaves_128dirs_256recv", 40.0, 32, 40, 128, 256),
+    # misfit gradient at k = 20 (1600 coefficients)
+    "grad_k20": Workload("grad_k20_16x16leaves_1600modes_64dirs_128recv", 20.0, 16, 40, 64, 128),
+}

@@ -1,0 +1,205 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Each pin is chosen so that a plausible mistake in the oracle (a dropped term,
+a sign, a transposed operand, a wrong normal, a wrong weight) fails one of
+them: closed forms (disk and radial media), a brute-force integral (Born
+Jacobian), finite differences, Green's-function symmetry, a library
+least-squares solve and the grid-size column the paper prints (Table 1).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+from scipy.special import hankel1
+
+import closed_forms as CF
+import synth
+from oracle import bie
+from oracle import forward as F
+from oracle.spectral import (diff_matrix, interp_quad_weights, lagrange_eval,
+                             lobatto_nodes)
+
+K5 = 5.0
+
+
+@pytest.fixture(scope="module")
+def fw_zero():
+    return F.forward_from_coeffs(np.zeros((5, 5)), K5, 4)
+
+
+# --- 1-D spectral pieces ------------------------------------------------------
+def test_diff_matrix_exact_on_polynomials():
+    t = lobatto_nodes(16)
+    D = diff_matrix(t)
+    for deg in range(16):
+        err = np.abs(D @ t**deg - (deg * t ** (deg - 1) if deg else 0 * t)).max()
+        assert err < 1e-11 * max(1, deg) ** 2
+
+
+def test_interior_quadrature_exact_to_degree_13():
+    t = lobatto_nodes(16)[1:-1]
+    w = interp_quad_weights(t)
+    assert np.all(w > 0)  # Fejer's second rule has positive weights
+    for deg in range(14):
+        exact = (1 - (-1) ** (deg + 1)) / (deg + 1)
+        assert abs(w @ t**deg - exact) < 1e-14
+
+
+def test_lagrange_basis_is_cardinal():
+    t = lobatto_nodes(16)[1:-1]
+    assert np.allclose(lagrange_eval(t, t), np.eye(14), atol=1e-13)
+
+
+def test_grid_point_counts_match_table1():
+    """Distinct points of 2^l x 2^l leaves of 16 x 16 Chebyshev nodes (paper Table 1, column N)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_grid_points.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for nl, N in rows:
+        g = F.Grid(int(nl)) if int(nl) <= 16 else None
+        if g is None:
+            continue
+        pts = np.unique(np.round(np.stack([g.X.ravel(), g.Y.ravel()], -1), 12), axis=0)
+        assert len(pts) == int(N)
+
+
+def test_sine_eval_matches_direct_sum():
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal((4, 3))
+    x, y = rng.uniform(-1, 1, 7), rng.uniform(-1, 1, 7)
+    ref = [sum(c[a, b] * math.sin((a + 1) * math.pi * (xi + 1) / 2) * math.sin((b + 1) * math.pi * (yi + 1) / 2)
+               for a in range(4) for b in range(3)) for xi, yi in zip(x, y)]
+    assert np.allclose(F.sine_eval(c, x, y), ref, atol=1e-14)
+
+
+# --- boundary integral pieces -------------------------------------------------
+def test_product_weights_match_quadpack():
+    """Singular and near-singular panel integrals against QUADPACK with the singular point given."""
+    bd = bie.make_boundary(4)
+    k = K5
+    i = 3  # a node on panel 0
+    x = bd.nodes[i]
+    for q in (0, 1, 15):  # self, neighbour on the same side, neighbour across the corner
+        ws, wd = bie.product_weights(bd, k, x, q)
+        y0, tau, ny = bd.start[q], bd.tangent[q], bd.normal[q]
+        for j in (0, 6, 13):
+            def f(s, part, kern):
+                y = y0 + s * tau
+                d = x - y
+                r = math.hypot(*d)
+                Lj = lagrange_eval(bd.t, np.array([2 * s / bd.h - 1]))[0, j]
+                if kern == "S":
+                    val = 0.25j * hankel1(0, k * r)
+                else:
+                    val = 0.25j * k * hankel1(1, k * r) * (d @ ny) / r
+                return (val.real if part == 0 else val.imag) * Lj
+            sing = [float(np.clip((x - y0) @ tau, 0, bd.h))]
+            for kern, w in (("S", ws), ("D", wd)):
+                re = quad(f, 0, bd.h, args=(0, kern), points=sing, limit=200, epsabs=1e-15, epsrel=1e-13)[0]
+                im = quad(f, 0, bd.h, args=(1, kern), points=sing, limit=200, epsabs=1e-15, epsrel=1e-13)[0]
+                assert abs(w[j] - (re + 1j * im)) < 1e-12, (q, j, kern)
+
+
+def test_green_identity_for_radiating_source(fw_zero):
+    """(D - I/2) u = S d_n u on the boundary, and Green's representation at R, for u = G(., x0), x0 in Omega."""
+    fw = fw_zero
+    x0 = np.array([[0.2, -0.3]])
+    ui, dni = fw.point_traces(x0)
+    res = (fw.Dl - 0.5 * np.eye(fw.nb)) @ ui - fw.S @ dni
+    assert np.abs(res).max() < 1e-10 * np.abs(ui).max()
+    th = synth.receivers(8)
+    A_phi, A_psi = bie.farfield_matrices(fw.bd, K5, th, 3.0)
+    xp = 3.0 * np.stack([np.cos(th), np.sin(th)], -1)
+    exact = 0.25j * hankel1(0, K5 * np.linalg.norm(xp - x0, axis=-1))
+    assert np.abs(A_phi @ ui[:, 0] + A_psi @ dni[:, 0] - exact).max() < 1e-10 * np.abs(exact).max()
+
+
+# --- forward map ----------------------------------------------------------------
+def test_zero_contrast_scatters_nothing(fw_zero):
+    uf, u = fw_zero.solve_plane(synth.directions(4), synth.receivers(8))
+    assert np.abs(uf).max() < 1e-10
+
+
+def test_radial_gaussian_matches_ode_reference():
+    sig, q0 = 0.15, 0.3
+    th = synth.receivers(12)
+    alpha = 0.3
+    ref = CF.radial_scattered(K5, lambda r: q0 * math.exp(-r * r / (2 * sig * sig)), 1.0, alpha, th, 3.0, nmax=30)
+    fw = F.forward_from_function(lambda x, y: q0 * np.exp(-(x * x + y * y) / (2 * sig * sig)), K5, 8)
+    uf, _ = fw.solve_plane(np.array([alpha]), th)
+    assert np.abs(uf[0] - ref).max() < 2e-9 * np.abs(ref).max()
+
+
+def test_disk_matches_bessel_series():
+    """Jump not aligned with leaves: algebraic convergence, so a loose bound (sign and scale check)."""
+    a, q0, alpha = 0.55, 0.2, 0.3
+    th = synth.receivers(12)
+    ref = CF.disk_scattered(K5, q0, a, alpha, th, 3.0)
+    fw = F.forward_from_function(lambda x, y: np.where(x * x + y * y < a * a, q0, 0.0), K5, 4)
+    uf, _ = fw.solve_plane(np.array([alpha]), th)
+    assert np.abs(uf[0] - ref).max() < 2e-2 * np.abs(ref).max()
+
+
+def test_green_function_symmetry():
+    """Scattered field at x_b from a source at x_a equals that at x_a from a source at x_b.
+
+    The identity is exact for the continuous problem; the collocation scheme is
+    not symmetric, so it holds to discretisation error (about 4e-9 here, with the
+    contrast's jump at the corners of Omega); a transposed or mis-signed
+    operand gives an O(1) mismatch.
+    """
+    qt = synth.gaussian_bumps(1)
+    fw = F.forward_from_function(qt, K5, 4)
+    th = np.array([0.4, 2.1])
+    src = 3.0 * np.stack([np.cos(th), np.sin(th)], -1)
+    ui, dni = fw.point_traces(src)
+    _, ub, psi = fw.split(fw.solve_incident(ui, dni))
+    us = fw.farfield(ub - ui.T, psi - dni.T, th)  # us[source, receiver]
+    assert abs(us[0, 1] - us[1, 0]) < 5e-8 * abs(us[0, 1])
+
+
+# --- Jacobian -------------------------------------------------------------------
+def test_jacobian_at_zero_is_born_integral(fw_zero):
+    al, th, S = synth.directions(4), synth.receivers(6), 5
+    J = fw_zero.jacobian(al, th, S, S)
+    J0 = CF.born_jacobian(K5, al, th, 3.0, S, S, nq=120)
+    assert np.abs(J - J0).max() < 2e-9 * np.abs(J0).max()
+
+
+def test_jacobian_matches_finite_differences():
+    S, h = 4, 1e-5
+    al, th = synth.directions(3), synth.receivers(5)
+    c = synth.random_coeffs(S, S, seed=5, scale=0.03)
+    J = F.forward_from_coeffs(c, K5, 4).jacobian(al, th, S, S)
+    for m in (0, 6, 15):
+        cp, cm = c.copy(), c.copy()
+        cp.flat[m] += h
+        cm.flat[m] -= h
+        up, _ = F.forward_from_coeffs(cp, K5, 4).solve_plane(al, th)
+        um, _ = F.forward_from_coeffs(cm, K5, 4).solve_plane(al, th)
+        fd = ((up - um) / (2 * h)).ravel()
+        assert np.abs(fd - J[:, m]).max() < 2e-6 * np.abs(J[:, m]).max()
+
+
+# --- Gauss-Newton step ------------------------------------------------------------
+def test_normal_equations_equal_stacked_lstsq():
+    rng = np.random.default_rng(3)
+    J = rng.standard_normal((40, 6)) + 1j * rng.standard_normal((40, 6))
+    r = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    lam = 0.1
+    dc = F.gn_step(J, r, lam)
+    Ast = np.vstack([J.real, J.imag, math.sqrt(lam) * np.eye(6)])
+    bst = np.concatenate([r.real, r.imag, np.zeros(6)])
+    ref = np.linalg.lstsq(Ast, bst, rcond=None)[0]
+    assert np.abs(dc - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_gn_recovers_coefficients_from_linearised_data(fw_zero):
+    """Data exactly J c (Born regime, well-resolved low modes): one step returns c."""
+    S = 3
+    al, th = synth.directions(8), synth.receivers(12)
+    J = fw_zero.jacobian(al, th, S, S)
+    c = synth.random_coeffs(S, S, seed=9)
+    dc = F.gn_step(J, J @ c.ravel(), 0.0)
+    assert np.abs(dc - c.ravel()).max() < 1e-8 * np.abs(c).max()

@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Benchmark of the direct-solver hot path: Helmholtz RHS solves/s on one GB300.
+
+Workload (one step): the k = 40 forward batch -- 32 x 32 leaves of 16 x 16
+Chebyshev points on [-1, 1]^2, a smooth random contrast of 40 x 40 sine
+coefficients (max |q| = 0.3), 128 plane waves and 256 receivers at R = 3.
+A step factors the operator for that contrast (E_k, leaf operators, merges,
+exterior coupling: hs_build), computes the total field of every incidence on
+every leaf node (downward sweep) and the far field on the receivers
+(hs_solve).  value = incidences solved per second, factorisation included.
+
+Also reported: e2e (the same step through the host-buffer C-ABI calls, with
+the host<->device copies inside the timed region), the FP64 roofline of the
+dominant kernel family (the batched FP64 GEMM), the clocks seen during the
+timed region, and the CPU oracle timed on a bounded slice of the workload.
+
+Usage: python bench.py [--gpus N --steps K --warmup W --impl hs|reference]
+For N > 1 launch with torchrun; every rank runs its own replica of the step
+(weak scaling, no data-path collective) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+
+import synth  # noqa: E402
+
+METRIC = "Helmholtz RHS solves/s (factorisation included), k=40 forward batch"
+UNIT = "solves/s"
+# CPU-oracle slice: same leaf resolution (k h = 2.5) as the benchmark tree.
+ORACLE_SAMPLE = dict(k=10.0, n_leaf=8, M=32, P=64)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hs", choices=["hs", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def config_of(w, nranks):
+    return {"workload": w.name, "k": w.k, "leaves": f"{w.n_leaf_side}x{w.n_leaf_side}", "leaf_order": 16,
+            "sine_modes": f"{w.S}x{w.S}", "incidences_per_gpu": w.M, "receivers": w.P, "R": w.R,
+            "contrast": "smooth random sine series, max|q|=0.3, seed 2", "parallelism": f"replicas x{nranks}",
+            "l2": "working set > L2 (factors ~1 GB, fields 0.5 GB per step)"}
+
+
+def oracle_sample():
+    """Time the CPU oracle (factor + solves + far field) on the bounded slice."""
+    from oracle import forward as F
+    s = ORACLE_SAMPLE
+    c = synth.smooth_random_coeffs(10, seed=2, qmax=0.3)
+    al, th = synth.directions(s["M"]), synth.receivers(s["P"])
+    t0 = time.perf_counter()
+    fw = F.forward_from_coeffs(c, s["k"], s["n_leaf"])
+    fw.solve_plane(al, th)
+    dt = time.perf_counter() - t0
+    return s["M"] / dt, dt
+
+
+def oracle_desc():
+    s = ORACLE_SAMPLE
+    return (f"CPU oracle (sparse-LU collocation, FP64) on the k={s['k']:g} slice with {s['n_leaf']}x{s['n_leaf']} "
+            f"leaves (same k*h as the benchmark tree), {s['M']} plane waves, {s['P']} receivers; "
+            f"factor + solves per step, solves/s = incidences / step time")
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                       "-i", str(index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait(timeout=10)
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample()
+    times = []
+    for _ in range(args.steps):
+        times.append(oracle_sample()[1])
+    dt = sum(times) / len(times)
+    v = ORACLE_SAMPLE["M"] / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, world),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": oracle_desc()},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_hs(args, world, rank, local):
+    import torch
+
+    from paper_1608_06871_gb300.build import build
+    if local == 0:
+        build()
+    barrier(world)
+    import paper_1608_06871_gb300 as hs
+
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    c = synth.smooth_random_coeffs(w.S, seed=2, qmax=0.3)
+    stream = torch.cuda.current_stream()
+    solver = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_FP64, device=local, stream=stream.cuda_stream)
+    ctx = solver.ctx
+    al_np, th_np = synth.directions(w.M), synth.receivers(w.P)
+    alphas = torch.tensor(al_np, device="cuda")
+    thetas = torch.tensor(th_np, device="cuda")
+    ufar = torch.empty((w.M, w.P, 2), dtype=torch.float64, device="cuda")
+    u = torch.empty((w.M, w.n_leaf_side ** 2, 256, 2), dtype=torch.float64, device="cuda")
+
+    def step():
+        hs.hs_build(ctx, c, w.k)
+        hs.hs_fields_dev(ctx, alphas, u)
+        hs.hs_solve_dev(ctx, alphas, thetas, ufar)
+
+    peak = hs.hs_peak_fp64(local, 300.0)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) -------------------------------------
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    n0 = solver.launch_count()
+    hs.hs_prof_start(hs.HS_PROF_GEMM_FP64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    gemm_ms, gemm_flops, gemm_n = hs.hs_prof_stop()
+    launches = solver.launch_count() - n0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = world * w.M / (ms * 1e-3)
+
+    # ---- phase split (one extra, untimed pass) ------------------------------------
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    hs.hs_build(ctx, c, w.k)
+    ev[1].record(stream)
+    hs.hs_fields_dev(ctx, alphas, u)
+    ev[2].record(stream)
+    hs.hs_solve_dev(ctx, alphas, thetas, ufar)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    phases = {"build_ms": ev[0].elapsed_time(ev[1]), "fields_ms": ev[1].elapsed_time(ev[2]),
+              "farfield_ms": ev[2].elapsed_time(ev[3])}
+
+    # ---- e2e through the host-buffer C-ABI (copies inside the timed region) ---------
+    c_pin = torch.tensor(c, dtype=torch.float64).pin_memory()
+    al_pin = torch.tensor(al_np).pin_memory()
+    th_pin = torch.tensor(th_np).pin_memory()
+    out_pin = torch.empty((w.M, w.P, 2), dtype=torch.float64).pin_memory()
+    c_np, al_h, th_h, out_np = c_pin.numpy(), al_pin.numpy(), th_pin.numpy(), out_pin.numpy()
+
+    def step_e2e():
+        hs.hs_build(ctx, c_np, w.k)
+        a_dev = al_pin.to("cuda", non_blocking=True)
+        hs.hs_fields_dev(ctx, a_dev, u)
+        res = hs.hs_solve(ctx, al_h, th_h)
+        out_np[..., 0] = res.real
+        out_np[..., 1] = res.imag
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = max_over_ranks(e2e_s, world)
+    h2d = 8 * (w.S * w.S + 2 * w.M + w.P)
+    d2h = 16 * w.M * w.P
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt = oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": oracle_desc(),
+               "seconds": dt}
+
+    if rank == 0:
+        achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w, world),
+                "e2e": {"value": world * w.M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches,
+                "roofline": {"bound": "alu", "kernel": "k_gemm (batched FP64 complex/real GEMM)",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": (achieved / peak) if achieved and peak else None,
+                             "peak_source": "measured FP64 DFMA rate (hs_peak_fp64, this run)",
+                             "traffic": None, "launches": gemm_n, "kernel_ms_per_step": gemm_ms / args.steps,
+                             "algorithmic_tflop_per_step": gemm_flops / args.steps / 1e12},
+                "phases": phases, "clocks": clk}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    solver.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_hs(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,142 @@
+/*
+ * hs.h -- C ABI of libhs: the hot path of recursive linearization for 2-D
+ * inverse scattering (Borges, Gillman, Greengard, arXiv 1608.06871) at one
+ * frequency k, on one GPU.
+ *
+ * Problem (paper Sec. 1, eqs. origpde, srad, farfielddef): a contrast q(x)
+ * supported in Omega = [-1, 1]^2, the total field u = u_inc + u_s with
+ *     Lap u + k^2 (1 - q) u = 0,   u_inc = exp(i k x.d),   u_s radiating,
+ * and the measured data u_far(theta) = u_s(R cos theta, R sin theta).
+ * The contrast is the truncated sine series of Sec. 3.2 (eq. sineseries) on
+ * [-1,1]^2:  q(x) = sum_{m1=1..S1, m2=1..S2} c[m1-1][m2-1] s_m1(x1) s_m2(x2),
+ * s_m(t) = sin(m pi (t + 1) / 2).
+ *
+ * Discretisation: n_L x n_L leaves of 16 x 16 Chebyshev-Lobatto points (Sec. 2,
+ * Table 1), interior solved by hierarchical merges of impedance-to-impedance
+ * maps (Sec. 2), exterior by the Green identity (D - I/2) u_s = S d_n u_s on
+ * the boundary of Omega (Sec. 2, Remark).
+ *
+ * Conventions for every call:
+ *  - Arrays are owned by the caller.  Plain pointers (no suffix) are HOST
+ *    memory; calls ending in _dev take DEVICE pointers and a cudaStream_t
+ *    passed as void* (NULL = the context's stream) and return without
+ *    synchronising that stream.
+ *  - Complex arrays are interleaved (re, im) doubles, row-major.
+ *  - Return value: HS_OK (0) or a negative HS_E* code; hs_last_error()
+ *    then gives a one-line reason.  No call aborts, traps or prints.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef HS_H
+#define HS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HS_OK 0
+#define HS_EINVAL (-1)      /* bad size, NaN, or 1 - q <= 0 on the grid      */
+#define HS_ENOTBUILT (-2)   /* solve/jacobian before hs_build                 */
+#define HS_ENOMEM (-3)      /* device allocation failed                       */
+#define HS_ECUDA (-4)       /* CUDA runtime error                             */
+#define HS_ESINGULAR (-5)   /* zero pivot in a factorisation                  */
+#define HS_ENOCONV (-6)     /* iterative refinement did not converge          */
+#define HS_ETIMEOUT (-7)    /* a bounded device wait gave up                  */
+
+#define HS_FP64 0   /* every step in complex FP64                            */
+#define HS_MIXED 1  /* FP32 factors and sweep, FP64 residual refinement       */
+
+typedef struct hs_ctx hs_ctx;
+
+typedef struct hs_config {
+  double R;             /* receiver circle radius (> sqrt(2)); 3.0 in the workloads */
+  int leaves_per_side;  /* n_L, a power of two, 1..256                              */
+  int S1, S2;           /* sine modes per axis (1..512)                             */
+  int precision;        /* HS_FP64 or HS_MIXED                                      */
+  int device;           /* CUDA device ordinal                                      */
+  void* stream;         /* cudaStream_t for all work, or NULL for a private stream  */
+  double refine_tol;    /* HS_MIXED: stop when the far-field update is below this
+                           relative size (default 1e-12 if <= 0)                    */
+  int refine_max_iter;  /* HS_MIXED: maximum refinement sweeps (default 8 if <= 0)  */
+} hs_config;
+
+/* Create a context on cfg->device (copies cfg).  Allocates nothing large until
+ * hs_build.  Errors: HS_EINVAL on bad sizes, HS_ECUDA if the device is absent. */
+int hs_create(hs_ctx** out, const hs_config* cfg);
+
+/* Factor the discrete operator for the contrast given by sine coefficients
+ * c (host, S1*S2 doubles, c[(m1-1)*S2 + (m2-1)]) at wavenumber k > 0
+ * (Sec. 3.2 eq. sineseries for q; Sec. 2 for the factorisation, which the
+ * paper performs once per Newton step, Sec. 3.3).  Evaluates q on every leaf
+ * node on the GPU.  Errors: HS_EINVAL (NaN, k <= 0, shape mismatch,
+ * 1 - q <= 0 at a node), HS_ESINGULAR, HS_ENOMEM, HS_ECUDA. */
+int hs_build(hs_ctx* ctx, const double* c, int S1, int S2, double k);
+
+/* As hs_build, but q is given directly at the leaf nodes (host array of
+ * n_L*n_L*256 doubles in the order of hs_node_coords).  Used to generate
+ * measured data from a contrast that is not a sine series. */
+int hs_build_nodes(hs_ctx* ctx, const double* q_nodes, double k);
+
+/* Leaf node coordinates (host arrays of n_L*n_L*256 doubles): node index
+ * ((iy*n_L + ix)*16 + a)*16 + b is the point (x_a, y_b) of leaf (ix, iy). */
+int hs_node_coords(const hs_ctx* ctx, double* x, double* y);
+
+/* Forward solves (Sec. 1 eq. farfielddef; Sec. 3 eq. singfreqsys): for each
+ * incidence angle alpha_m (d = (cos, sin)) and receiver angle theta_p, the
+ * scattered field at R (cos theta_p, sin theta_p).  Output ufar: M x P
+ * complex, row-major (m slow).  Requires hs_build. */
+int hs_solve(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
+             double* ufar);
+int hs_solve_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
+                 double* ufar, void* stream);
+
+/* Total fields on the leaf nodes for M plane-wave incidences (device output,
+ * M x n_L*n_L*256 complex, node order of hs_node_coords; corner nodes of
+ * each leaf are not part of the discretisation and are set to 0). */
+int hs_fields_dev(hs_ctx* ctx, const double* alphas, int M, double* u, void* stream);
+
+/* Jacobian of the data with respect to the sine coefficients at the built
+ * contrast (Theorem 3.1, eqs. Jdef/vdef, read on the basis of eq. sineseries):
+ * J[(m*P + p)][(m1-1)*S2 + (m2-1)] = d u_far(m, p) / d c[m1][m2], complex,
+ * (M*P) x (S1*S2) row-major.  Assembled by discrete reciprocity (the adjoint
+ * of Theorem 3.2): forward fields times adjoint fields, projected onto the
+ * sine basis. */
+int hs_jacobian(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
+                double* J);
+int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
+                    double* J, void* stream);
+
+/* One Gauss-Newton step from the normal equations (Sec. 3.3, eq. normaleq)
+ * in the real coefficients: with r = data - F(c) and J as above,
+ *   (Re(J^H J) + lambda I) dc = Re(J^H r),  lambda = lambda_rel * tr(Re J^H J) / (S1*S2),
+ * then c <- c + dc.  c_inout (host, S1*S2) must be the coefficients the
+ * context was last built with; on return the context holds the factors of
+ * the OLD c (call hs_build again to factor the new one).  data: M x P complex
+ * (host).  resid_norm_out (optional): ||r||_2 before the step. */
+int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
+               const double* thetas, int P, double lambda_rel, double* c_inout,
+               double* resid_norm_out);
+
+/* Gradient of the misfit 0.5 * ||F(c) - data||^2 with respect to the real sine
+ * coefficients, grad = Re(J^H (F(c) - data)) (Theorem 3.2 read on the basis),
+ * without forming J: one adjoint sweep over the receivers.  grad: S1*S2 doubles
+ * (host); misfit_out (optional): the misfit value.  Requires hs_build. */
+int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M,
+                const double* thetas, int P, double* grad, double* misfit_out);
+int hs_gradient_dev(hs_ctx* ctx, const double* data, const double* alphas, int M,
+                    const double* thetas, int P, double* grad, double* misfit_out,
+                    void* stream);
+
+/* Number of kernel launches issued by this context since creation (for
+ * reporting). */
+long long hs_launch_count(const hs_ctx* ctx);
+
+/* Last error message of the context (never NULL). */
+const char* hs_last_error(const hs_ctx* ctx);
+
+/* Release every device allocation of the context. */
+void hs_destroy(hs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_H */

@@ -1,0 +1,39 @@
+/*
+ * hs_diag.h -- measurement hooks of libhs (not part of the method; the paper
+ * has no counterpart).  Used by the benchmark to time the dominant kernel
+ * family inside a timed region and to measure the chip's FP64 arithmetic
+ * peak, the denominator of the FP64 roofline.
+ *
+ * All functions return HS_OK (0) or a negative HS_E* code from hs.h.
+ */
+#ifndef HS_DIAG_H
+#define HS_DIAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Kernel families that can be timed. */
+#define HS_PROF_GEMM_FP64 1 /* the batched FP64 real/complex GEMM kernel */
+
+/* Start recording a CUDA event pair around every launch of the given family
+ * (on the stream the launch uses) and counting its algorithmic flops
+ * (8 m n k per complex product, 4 for real x complex, 2 for real).  Recording
+ * is process-wide and not thread-safe.  Errors: HS_EINVAL for an unknown
+ * family. */
+int hs_prof_start(int family);
+
+/* Stop recording, synchronise on the recorded events and return the summed
+ * kernel time in milliseconds, the summed algorithmic flops and the number of
+ * launches.  Releases the events.  Any pointer may be NULL. */
+int hs_prof_stop(double* total_ms, double* total_flops, long long* launches);
+
+/* Measure the sustained FP64 fused multiply-add rate of `device` with a
+ * register-resident kernel of independent DFMA chains on every SM; returns
+ * TFLOP/s (2 flops per DFMA) in *tflops.  Runs for about `ms` milliseconds. */
+int hs_peak_fp64(int device, double ms, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_DIAG_H */

@@ -1,0 +1,74 @@
+// Shared device/host helpers for libhs: complex arithmetic on double2/float2,
+// error propagation and launch bookkeeping.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hs {
+
+// ---- complex arithmetic (interleaved re/im, same layout as the C ABI) ------
+struct Cz { double x, y; };   // complex double, 16-byte aligned like double2
+
+__host__ __device__ inline double2 cz(double re, double im) { return make_double2(re, im); }
+__host__ __device__ inline double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 operator-(double2 a) { return make_double2(-a.x, -a.y); }
+__host__ __device__ inline double2 operator*(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ inline double2 operator*(double2 a, double s) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ inline double2 conjz(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline double abs2z(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ inline double2 divz(double2 a, double2 b) {
+  // Smith's algorithm (avoids overflow for large |b|).
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    double r = b.x / b.y, d = b.y + b.x * r;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+
+// Generic element traits so that the linear algebra can be templated on
+// real or complex element types.
+template <typename E> struct el;
+template <> struct el<double> {
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double one() { return 1.0; }
+  __host__ __device__ static double mag2(double a) { return a * a; }
+  __host__ __device__ static double div(double a, double b) { return a / b; }
+};
+template <> struct el<double2> {
+  __host__ __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __host__ __device__ static double2 one() { return make_double2(1.0, 0.0); }
+  __host__ __device__ static double mag2(double2 a) { return abs2z(a); }
+  __host__ __device__ static double2 div(double2 a, double2 b) { return divz(a, b); }
+};
+
+// Mixed-type multiply-accumulate used by the GEMM templates.
+__host__ __device__ inline double mul(double a, double b) { return a * b; }
+__host__ __device__ inline double2 mul(double a, double2 b) { return make_double2(a * b.x, a * b.y); }
+__host__ __device__ inline double2 mul(double2 a, double b) { return make_double2(a.x * b, a.y * b); }
+__host__ __device__ inline double2 mul(double2 a, double2 b) { return a * b; }
+__host__ __device__ inline bool is_zero(double a) { return a == 0.0; }
+__host__ __device__ inline bool is_zero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
+__host__ __device__ inline double addv(double a, double b) { return a + b; }
+__host__ __device__ inline double2 addv(double2 a, double2 b) { return a + b; }
+template <typename TC, typename S> __host__ __device__ inline TC scal(S s, TC v);
+template <> __host__ __device__ inline double scal<double, double>(double s, double v) { return s * v; }
+template <> __host__ __device__ inline double2 scal<double2, double2>(double2 s, double2 v) { return s * v; }
+
+}  // namespace hs
+
+// Launch bookkeeping: every kernel launch in the library goes through HS_LAUNCH
+// so that the context can report how many of its kernels ran.
+namespace hs {
+extern thread_local long long* g_launch_counter;
+}
+#define HS_COUNT_LAUNCH()                        \
+  do {                                           \
+    if (hs::g_launch_counter) ++(*hs::g_launch_counter); \
+  } while (0)

@@ -1,0 +1,956 @@
+// C ABI of libhs (include/hs.h): host-side orchestration of the direct solver
+// of Sec. 2 and of the Jacobian / Gauss-Newton step of Sec. 3 on one GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hs.h"
+#include "tree.cuh"
+
+namespace hs {
+thread_local long long* g_launch_counter = nullptr;
+}
+
+using namespace hs;
+
+namespace {
+
+// ---- host-side 1-D rules (definitions, computed in double) ----------------
+// Chebyshev-Lobatto points t_a = -cos(pi a / (p-1)), ascending.
+std::vector<double> lobatto(int p) {
+  std::vector<double> t(p);
+  for (int a = 0; a < p; ++a) t[a] = -std::cos(M_PI * a / (p - 1));
+  return t;
+}
+
+// Derivative of the Lagrange interpolant: D[i][j] = L_j'(t_i), from the
+// barycentric weights lambda_j = 1 / prod_{l != j} (t_j - t_l).
+std::vector<double> diff_matrix(const std::vector<double>& t) {
+  int n = (int)t.size();
+  std::vector<double> lam(n), D(n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double p = 1.0;
+    for (int l = 0; l < n; ++l)
+      if (l != j) p *= (t[j] - t[l]);
+    lam[j] = 1.0 / p;
+  }
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (i != j) {
+        D[i * n + j] = (lam[j] / lam[i]) / (t[i] - t[j]);
+        s += D[i * n + j];
+      }
+    D[i * n + i] = -s;
+  }
+  return D;
+}
+
+// Fejer's second rule on the n interior points cos(j pi/(n+1)), j = 1..n:
+// w_j = 4 sin(th_j)/(n+1) * sum_{l=1}^{ceil(n/2)} sin((2l-1) th_j)/(2l-1).
+// Returned in ascending node order (t = -cos).
+std::vector<double> fejer2(int n) {
+  std::vector<double> w(n);
+  for (int j = 1; j <= n; ++j) {
+    double th = M_PI * j / (n + 1), s = 0.0;
+    for (int l = 1; l <= (n + 1) / 2; ++l) s += std::sin((2 * l - 1) * th) / (2 * l - 1);
+    w[j - 1] = 4.0 * std::sin(th) / (n + 1) * s;
+  }
+  return w;  // symmetric, so the order of t does not matter
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  template <typename T> T* get(size_t n) {
+    size_t b = (n * sizeof(T) + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += b;
+    return p;
+  }
+  static size_t bytes(size_t n, size_t elt) { return (n * elt + 255) & ~size_t(255); }
+};
+
+}  // namespace
+
+struct hs_ctx {
+  hs_config cfg{};
+  int nL = 0, nleaf = 0, n14 = 0, n16 = 0, chunk = 0;
+  double h = 0, k = 0;
+  int S1 = 0, S2 = 0;
+  bool built = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  long long launches = 0;
+  std::vector<void*> allocs;  // persistent allocations
+  // geometry
+  double *d_xg = nullptr, *d_xint = nullptr;
+  double *d_q = nullptr, *d_c = nullptr, *d_sx16 = nullptr, *d_sy16 = nullptr, *d_T = nullptr, *d_Qg = nullptr;
+  double *d_sxi = nullptr, *d_syi = nullptr;
+  int* d_info = nullptr;
+  int ninfo = 0;
+  // factors
+  double2 *d_Rleaf = nullptr, *d_Y = nullptr, *d_Q = nullptr;
+  LeafScratch ws{};
+  std::vector<Level> levels;
+  Boundary B{};
+  double2 *d_S = nullptr, *d_Dm = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_C = nullptr;
+  int* d_Cpiv = nullptr;
+  const double2* Rroot = nullptr;
+  // per-call workspace
+  char* ws_base = nullptr;
+  size_t ws_cap = 0;
+};
+
+namespace {
+
+struct LaunchScope {
+  long long* prev;
+  explicit LaunchScope(hs_ctx* c) : prev(g_launch_counter) { g_launch_counter = &c->launches; }
+  ~LaunchScope() { g_launch_counter = prev; }
+};
+
+int fail(hs_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(ctx, e_ == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA, \
+                                       std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+#define CKR(expr)                 \
+  do {                            \
+    int r_ = (expr);              \
+    if (r_ != HS_OK) return r_;   \
+  } while (0)
+
+template <typename T> int dalloc(hs_ctx* ctx, T** p, size_t n) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess)
+    return fail(ctx, HS_ENOMEM, std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) + " bytes: " +
+                                    cudaGetErrorString(e));
+  ctx->allocs.push_back(v);
+  *p = reinterpret_cast<T*>(v);
+  return HS_OK;
+}
+
+int ensure_ws(hs_ctx* ctx, size_t bytes, Arena& a) {
+  bytes += (1u << 20);  // slack for alignment padding
+  if (bytes > ctx->ws_cap) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws_base) cudaFree(ctx->ws_base);
+    ctx->ws_base = nullptr;
+    ctx->ws_cap = 0;
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) return fail(ctx, HS_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+    ctx->ws_base = (char*)v;
+    ctx->ws_cap = bytes;
+  }
+  a.base = ctx->ws_base;
+  a.cap = ctx->ws_cap;
+  a.off = 0;
+  return HS_OK;
+}
+
+int check_info(hs_ctx* ctx) {
+  std::vector<int> info(ctx->ninfo);
+  CK(cudaMemcpyAsync(info.data(), ctx->d_info, sizeof(int) * ctx->ninfo, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int v : info)
+    if (v != 0) return fail(ctx, HS_ESINGULAR, "zero pivot in a factorisation (column " + std::to_string(v) + ")");
+  return HS_OK;
+}
+
+// Tree bookkeeping: merge levels from leaves (1 x 1) to the root (nL x nL).
+int setup_tree(hs_ctx* ctx) {
+  const int nL = ctx->nL;
+  int sx = 1, sy = 1;
+  bool horiz = true;
+  while (sx < nL || sy < nL) {
+    Level L{};
+    L.horiz = horiz;
+    L.sx = sx;
+    L.sy = sy;
+    const int nS = 14 * sx, nE = 14 * sy, nN = 14 * sx, nW = 14 * sy;
+    const int offS = 0, offE = nS, offN = nS + nE, offW = nS + nE + nN;
+    L.nc = nS + nE + nN + nW;
+    std::vector<int> src, I3a, I3b;
+    auto add = [&](int child, int off, int n) {
+      for (int i = 0; i < n; ++i) src.push_back((child << 20) | (off + i));
+    };
+    int psx, psy;
+    if (horiz) {
+      for (int i = 0; i < nE; ++i) I3a.push_back(offE + i);
+      for (int i = 0; i < nW; ++i) I3b.push_back(offW + i);
+      add(0, offS, nS); add(1, offS, nS); add(1, offE, nE); add(0, offN, nN); add(1, offN, nN); add(0, offW, nW);
+      psx = 2 * sx; psy = sy;
+    } else {
+      for (int i = 0; i < nN; ++i) I3a.push_back(offN + i);
+      for (int i = 0; i < nS; ++i) I3b.push_back(offS + i);
+      add(0, offS, nS); add(0, offE, nE); add(1, offE, nE); add(1, offN, nN); add(0, offW, nW); add(1, offW, nW);
+      psx = sx; psy = 2 * sy;
+    }
+    L.ni = (int)I3a.size();
+    L.np = (int)src.size();
+    const int nbx_c = nL / sx, nbx_p = nL / psx, nby_p = nL / psy;
+    L.nbox = nbx_p * nby_p;
+    std::vector<int> al(L.nbox), be(L.nbox);
+    for (int py = 0; py < nby_p; ++py)
+      for (int px = 0; px < nbx_p; ++px) {
+        int b = py * nbx_p + px;
+        if (horiz) {
+          al[b] = py * nbx_c + 2 * px;
+          be[b] = al[b] + 1;
+        } else {
+          al[b] = (2 * py) * nbx_c + px;
+          be[b] = (2 * py + 1) * nbx_c + px;
+        }
+      }
+    CKR(dalloc(ctx, &L.d_alpha, L.nbox));
+    CKR(dalloc(ctx, &L.d_beta, L.nbox));
+    CKR(dalloc(ctx, &L.d_src, L.np));
+    CKR(dalloc(ctx, &L.d_I3a, L.ni));
+    CKR(dalloc(ctx, &L.d_I3b, L.ni));
+    CK(cudaMemcpy(L.d_alpha, al.data(), sizeof(int) * L.nbox, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_beta, be.data(), sizeof(int) * L.nbox, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_src, src.data(), sizeof(int) * L.np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_I3a, I3a.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_I3b, I3b.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
+    const size_t nb = L.nbox;
+    CKR(dalloc(ctx, &L.XZ, nb * 2 * L.ni * L.np));
+    CKR(dalloc(ctx, &L.U2, nb * 2 * L.ni * L.np));
+    CKR(dalloc(ctx, &L.A33, nb * L.ni * L.ni));
+    CKR(dalloc(ctx, &L.B33, nb * L.ni * L.ni));
+    CKR(dalloc(ctx, &L.M, nb * L.ni * L.ni));
+    CKR(dalloc(ctx, &L.Mpiv, nb * L.ni));
+    CKR(dalloc(ctx, &L.R, nb * (size_t)L.np * L.np));
+    ctx->levels.push_back(L);
+    sx = psx;
+    sy = psy;
+    horiz = !horiz;
+  }
+  return HS_OK;
+}
+
+int setup_boundary(hs_ctx* ctx) {
+  const int nL = ctx->nL;
+  const double h = ctx->h;
+  std::vector<double> t = lobatto(16);
+  std::vector<double> tin(t.begin() + 1, t.end() - 1);
+  std::vector<double> wf = fejer2(14);
+  const int npanel = 4 * nL, nb = npanel * 14;
+  std::vector<double> x(nb), y(nb), nx(nb), ny(nb), w(nb);
+  std::vector<int> panel(nb);
+  std::vector<double> p0x(npanel), p0y(npanel), tx(npanel), ty(npanel), pnx(npanel), pny(npanel);
+  for (int side = 0; side < 4; ++side)
+    for (int i = 0; i < nL; ++i) {
+      int q = side * nL + i;
+      double sx0, sy0, tX, tY, nX, nY;
+      switch (side) {
+        case 0: sx0 = -1.0 + i * h; sy0 = -1.0; tX = 1; tY = 0; nX = 0; nY = -1; break;  // S
+        case 1: sx0 = 1.0; sy0 = -1.0 + i * h; tX = 0; tY = 1; nX = 1; nY = 0; break;    // E
+        case 2: sx0 = -1.0 + i * h; sy0 = 1.0; tX = 1; tY = 0; nX = 0; nY = 1; break;    // N
+        default: sx0 = -1.0; sy0 = -1.0 + i * h; tX = 0; tY = 1; nX = -1; nY = 0; break; // W
+      }
+      p0x[q] = sx0; p0y[q] = sy0; tx[q] = tX; ty[q] = tY; pnx[q] = nX; pny[q] = nY;
+      for (int a = 0; a < 14; ++a) {
+        int j = q * 14 + a;
+        double s = (tin[a] + 1.0) * h / 2.0;
+        x[j] = sx0 + s * tX;
+        y[j] = sy0 + s * tY;
+        nx[j] = nX;
+        ny[j] = nY;
+        w[j] = wf[a] * h / 2.0;
+        panel[j] = q;
+      }
+    }
+  // near panels: segment distance <= h (the panel itself, two on each side
+  // along the boundary, wrapping around the corners)
+  std::vector<int> nearp(npanel * 5, -1);
+  auto segdist = [&](int p, int q) {
+    auto ptseg = [&](double px, double py, int s) {
+      double dx = tx[s] * h, dy = ty[s] * h;
+      double u = ((px - p0x[s]) * dx + (py - p0y[s]) * dy) / (dx * dx + dy * dy);
+      u = std::min(1.0, std::max(0.0, u));
+      double ex = px - (p0x[s] + u * dx), ey = py - (p0y[s] + u * dy);
+      return std::sqrt(ex * ex + ey * ey);
+    };
+    double e1x = p0x[p] + tx[p] * h, e1y = p0y[p] + ty[p] * h;
+    double e2x = p0x[q] + tx[q] * h, e2y = p0y[q] + ty[q] * h;
+    return std::min(std::min(ptseg(p0x[p], p0y[p], q), ptseg(e1x, e1y, q)),
+                    std::min(ptseg(p0x[q], p0y[q], p), ptseg(e2x, e2y, p)));
+  };
+  for (int p = 0; p < npanel; ++p) {
+    int c = 0;
+    for (int q = 0; q < npanel && c < 5; ++q)
+      if (segdist(p, q) <= h * (1 + 1e-9)) nearp[p * 5 + c++] = q;
+  }
+  Boundary& B = ctx->B;
+  B.nb = nb;
+  B.npanel = npanel;
+  B.h = h;
+  CKR(dalloc(ctx, &B.x, nb)); CKR(dalloc(ctx, &B.y, nb)); CKR(dalloc(ctx, &B.nx, nb)); CKR(dalloc(ctx, &B.ny, nb));
+  CKR(dalloc(ctx, &B.w, nb)); CKR(dalloc(ctx, &B.panel, nb));
+  CKR(dalloc(ctx, &B.p0x, npanel)); CKR(dalloc(ctx, &B.p0y, npanel)); CKR(dalloc(ctx, &B.tx, npanel));
+  CKR(dalloc(ctx, &B.ty, npanel)); CKR(dalloc(ctx, &B.pnx, npanel)); CKR(dalloc(ctx, &B.pny, npanel));
+  CKR(dalloc(ctx, &B.near, npanel * 5));
+  CK(cudaMemcpy(B.x, x.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.y, y.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.nx, nx.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.ny, ny.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.w, w.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.panel, panel.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.p0x, p0x.data(), sizeof(double) * npanel, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.p0y, p0y.data(), sizeof(double) * npanel, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.tx, tx.data(), sizeof(double) * npanel, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.ty, ty.data(), sizeof(double) * npanel, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.pnx, pnx.data(), sizeof(double) * npanel, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.pny, pny.data(), sizeof(double) * npanel, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.near, nearp.data(), sizeof(int) * npanel * 5, cudaMemcpyHostToDevice));
+  // quadrature constants
+  std::vector<double> glx, glw;
+  gauss_legendre(16, glx, glw);
+  std::vector<double> lagden(14);
+  for (int j = 0; j < 14; ++j) {
+    double p = 1.0;
+    for (int l = 0; l < 14; ++l)
+      if (l != j) p *= (tin[j] - tin[l]);
+    lagden[j] = p;
+  }
+  upload_quad_constants(glx.data(), glw.data(), tin.data(), lagden.data(), ctx->stream);
+  std::vector<double> D1 = diff_matrix(t);
+  upload_cheb_diff(D1.data(), ctx->stream);
+  // root system
+  const size_t nn = (size_t)nb * nb;
+  CKR(dalloc(ctx, &ctx->d_S, nn));
+  CKR(dalloc(ctx, &ctx->d_Dm, nn));
+  CKR(dalloc(ctx, &ctx->d_B1, nn));
+  CKR(dalloc(ctx, &ctx->d_B2, nn));
+  CKR(dalloc(ctx, &ctx->d_C, nn));
+  CKR(dalloc(ctx, &ctx->d_Cpiv, nb));
+  return HS_OK;
+}
+
+int setup(hs_ctx* ctx) {
+  const int nL = ctx->nL;
+  ctx->nleaf = nL * nL;
+  ctx->n14 = 14 * nL;
+  ctx->n16 = 16 * nL;
+  ctx->h = 2.0 / nL;
+  ctx->chunk = std::min(ctx->nleaf, 1024);
+  std::vector<double> t = lobatto(16);
+  std::vector<double> xg(ctx->n16), xint(ctx->n14);
+  for (int ix = 0; ix < nL; ++ix)
+    for (int a = 0; a < 16; ++a) {
+      double xv = -1.0 + ix * ctx->h + (t[a] + 1.0) * ctx->h / 2.0;
+      xg[ix * 16 + a] = xv;
+      if (a >= 1 && a <= 14) xint[ix * 14 + a - 1] = xv;
+    }
+  CKR(dalloc(ctx, &ctx->d_xg, ctx->n16));
+  CKR(dalloc(ctx, &ctx->d_xint, ctx->n14));
+  CK(cudaMemcpy(ctx->d_xg, xg.data(), sizeof(double) * ctx->n16, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_xint, xint.data(), sizeof(double) * ctx->n14, cudaMemcpyHostToDevice));
+  const int S1 = ctx->cfg.S1, S2 = ctx->cfg.S2;
+  CKR(dalloc(ctx, &ctx->d_q, (size_t)ctx->nleaf * 256));
+  CKR(dalloc(ctx, &ctx->d_c, (size_t)S1 * S2));
+  CKR(dalloc(ctx, &ctx->d_sx16, (size_t)S1 * ctx->n16));
+  CKR(dalloc(ctx, &ctx->d_sy16, (size_t)S2 * ctx->n16));
+  CKR(dalloc(ctx, &ctx->d_T, (size_t)S1 * ctx->n16));
+  CKR(dalloc(ctx, &ctx->d_Qg, (size_t)ctx->n16 * ctx->n16));
+  CKR(dalloc(ctx, &ctx->d_sxi, (size_t)S1 * ctx->n14));
+  CKR(dalloc(ctx, &ctx->d_syi, (size_t)S2 * ctx->n14));
+  ctx->ninfo = std::max(ctx->nleaf, 16) + 1;
+  CKR(dalloc(ctx, &ctx->d_info, ctx->ninfo));
+  // leaf factors and scratch
+  const size_t nl = ctx->nleaf, ch = ctx->chunk;
+  CKR(dalloc(ctx, &ctx->d_Rleaf, nl * NE * NE));
+  CKR(dalloc(ctx, &ctx->d_Y, nl * NL * NE));
+  CKR(dalloc(ctx, &ctx->d_Q, nl * NI * NE));
+  LeafScratch& w = ctx->ws;
+  CKR(dalloc(ctx, &w.Aii, ch * NI * NI));
+  CKR(dalloc(ctx, &w.Aie, ch * NI * NE));
+  CKR(dalloc(ctx, &w.Ni, ch * NE * NI));
+  CKR(dalloc(ctx, &w.NiT, ch * NI * NE));
+  CKR(dalloc(ctx, &w.Ne, ch * NE * NE));
+  CKR(dalloc(ctx, &w.K, ch * NE * NE));
+  CKR(dalloc(ctx, &w.Kinv, ch * NE * NE));
+  CKR(dalloc(ctx, &w.piv, ch * NI));
+  CKR(dalloc(ctx, &w.pivK, ch * NE));
+  CKR(setup_tree(ctx));
+  CKR(setup_boundary(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HS_OK;
+}
+
+// Factor the operator for the q currently in d_q (Sec. 2).
+int factor(hs_ctx* ctx, double k) {
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  for (int l0 = 0; l0 < ctx->nleaf; l0 += ctx->chunk) {
+    int n = std::min(ctx->chunk, ctx->nleaf - l0);
+    leaf_build_chunk(s, ctx->d_q, l0, n, k, ctx->h, ctx->ws, ctx->d_Rleaf + (size_t)l0 * NE * NE,
+                     ctx->d_Y + (size_t)l0 * NL * NE, ctx->d_Q + (size_t)l0 * NI * NE, ctx->d_info);
+  }
+  const double2* Rc = ctx->d_Rleaf;
+  for (auto& L : ctx->levels) {
+    merge_level(s, L, Rc, ctx->d_info);
+    Rc = L.R;
+  }
+  ctx->Rroot = Rc;
+  const int nb = ctx->B.nb;
+  bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
+  bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
+  // C = B1 - B2 R_root   (coupling of the interior impedances to the exterior identity)
+  CK(cudaMemcpyAsync(ctx->d_C, ctx->d_B1, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, s));
+  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, nb, nb, make_double2(-1, 0), ctx->d_B2, nb, 0, ctx->Rroot, nb, 0,
+                                  make_double2(1, 0), ctx->d_C, nb, 0, 1);
+  lu_factor<double2>(s, ctx->d_C, nb, 0, nb, ctx->d_Cpiv, 0, ctx->d_info, 1);
+  CK(cudaGetLastError());
+  CKR(check_info(ctx));
+  ctx->k = k;
+  ctx->built = true;
+  return HS_OK;
+}
+
+// Root impedances f (nb x M) for plane waves; also returns ui, dni, g.
+int root_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, double2* ui, double2* dni, double2* f,
+               double2* g) {
+  const int nb = ctx->B.nb;
+  const double2 one = make_double2(1, 0), mone = make_double2(-1, 0), zero = make_double2(0, 0);
+  incident_plane(s, ctx->B, ctx->k, alphas, M, ui, dni);
+  // rhs = (D - I/2) u_inc - S d_n u_inc
+  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, one, ctx->d_Dm, nb, 0, ui, M, 0, zero, f, M, 0, 1);
+  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, mone, ctx->d_S, nb, 0, dni, M, 0, one, f, M, 0, 1);
+  lu_solve<double2>(s, OP_N, ctx->d_C, nb, 0, nb, ctx->d_Cpiv, 0, f, M, 0, M, 1);
+  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, one, ctx->Rroot, nb, 0, f, M, 0, zero, g, M, 0, 1);
+  return HS_OK;
+}
+
+// Downward sweep from root impedances f (nb x nrhs) to leaf fields (nleaf x 252 x nrhs).
+int sweep_down(hs_ctx* ctx, cudaStream_t s, const double2* f, int nrhs, double2* bufA, double2* bufB, double2* T3,
+               double2* Uleaf) {
+  const double2* Fp = f;
+  double2* out = bufA;
+  for (int li = (int)ctx->levels.size() - 1; li >= 0; --li) {
+    const Level& L = ctx->levels[li];
+    sweep_down_level(s, L, Fp, T3, out, nrhs);
+    Fp = out;
+    out = (out == bufA) ? bufB : bufA;
+  }
+  gemm<double2, double2, double2>(s, OP_N, OP_N, NL, nrhs, NE, make_double2(1, 0), ctx->d_Y, NE, (long long)NL * NE, Fp,
+                                  nrhs, (long long)NE * nrhs, make_double2(0, 0), Uleaf, nrhs, (long long)NL * nrhs,
+                                  ctx->nleaf);
+  return HS_OK;
+}
+
+// Adjoint sweep for the receiver functionals: Z (nleaf x 196 x P).
+int sweep_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2* E, double2* CP, double2* bufA,
+                  double2* bufB, double2* MU, double2* Zleaf) {
+  const int nb = ctx->B.nb;
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  adjoint_root_init(s, nb, P, ctx->k, A2, E, CP);
+  gemm<double2, double2, double2>(s, OP_T, OP_N, nb, P, nb, one, ctx->Rroot, nb, 0, E, P, 0, one, CP, P, 0, 1);
+  lu_solve<double2>(s, OP_T, ctx->d_C, nb, 0, nb, ctx->d_Cpiv, 0, CP, P, 0, P, 1);
+  gemm<double2, double2, double2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_B2, nb, 0, CP, P, 0, one, E, P, 0, 1);
+  const double2* Lp = E;
+  double2* out = bufA;
+  for (int li = (int)ctx->levels.size() - 1; li >= 0; --li) {
+    const Level& L = ctx->levels[li];
+    sweep_adjoint_level(s, L, Lp, MU, out, P);
+    Lp = out;
+    out = (out == bufA) ? bufB : bufA;
+  }
+  gemm<double2, double2, double2>(s, OP_N, OP_N, NI, P, NE, one, ctx->d_Q, NE, (long long)NI * NE, Lp, P,
+                                  (long long)NE * P, zero, Zleaf, P, (long long)NI * P, ctx->nleaf);
+  return HS_OK;
+}
+
+size_t field_buf_elems(hs_ctx* ctx, int nrhs) {
+  size_t m = (size_t)ctx->nleaf * NE;
+  for (auto& L : ctx->levels) m = std::max(m, (size_t)L.nbox * 2 * L.nc);
+  return m * nrhs;
+}
+size_t t3_elems(hs_ctx* ctx, int nrhs) {
+  size_t m = 1;
+  for (auto& L : ctx->levels) m = std::max(m, (size_t)L.nbox * 2 * L.ni);
+  return m * nrhs;
+}
+
+int check_ctx(hs_ctx* ctx, bool need_built) {
+  if (!ctx) return HS_EINVAL;
+  if (need_built && !ctx->built) return fail(ctx, HS_ENOTBUILT, "hs_build has not been called");
+  cudaError_t e = cudaSetDevice(ctx->cfg.device);
+  if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return HS_OK;
+}
+
+cudaStream_t pick(hs_ctx* ctx, void* stream) { return stream ? (cudaStream_t)stream : ctx->stream; }
+
+// Far field for M incidences into ufar (device, M x P complex).
+int solve_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* ufar) {
+  const int nb = ctx->B.nb;
+  Arena a;
+  size_t need = 4 * Arena::bytes((size_t)nb * M, 16) + Arena::bytes((size_t)2 * nb * M, 16) +
+                Arena::bytes((size_t)P * 2 * nb, 16);
+  CKR(ensure_ws(ctx, need, a));
+  double2 *ui = a.get<double2>((size_t)nb * M), *dni = a.get<double2>((size_t)nb * M);
+  double2 *f = a.get<double2>((size_t)nb * M), *g = a.get<double2>((size_t)nb * M);
+  double2* PS = a.get<double2>((size_t)2 * nb * M);
+  double2* A2 = a.get<double2>((size_t)P * 2 * nb);
+  CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
+  boundary_data(s, nb, M, ctx->k, f, g, ui, dni, PS);
+  farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
+  gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
+                                  make_double2(0, 0), ufar, P, 0, 1);
+  CK(cudaGetLastError());
+  return HS_OK;
+}
+
+// Forward fields on the interior grid (Ug, M x n14 x n14) and adjoint fields
+// (Zg, P x n14 x n14); workspace carved from `a` after `reserve` bytes.
+int fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P,
+                       double2* Ug, double2* Zg, Arena& a) {
+  const int nb = ctx->B.nb;
+  const int nr = std::max(M, P);
+  double2 *ui = a.get<double2>((size_t)nb * M), *dni = a.get<double2>((size_t)nb * M);
+  double2 *f = a.get<double2>((size_t)nb * M), *g = a.get<double2>((size_t)nb * M);
+  double2 *bufA = a.get<double2>(field_buf_elems(ctx, nr)), *bufB = a.get<double2>(field_buf_elems(ctx, nr));
+  double2* T3 = a.get<double2>(t3_elems(ctx, nr));
+  double2* Uleaf = a.get<double2>((size_t)ctx->nleaf * NL * nr);
+  double2* A2 = a.get<double2>((size_t)P * 2 * nb);
+  double2 *E = a.get<double2>((size_t)nb * P), *CP = a.get<double2>((size_t)nb * P);
+  CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
+  CKR(sweep_down(ctx, s, f, M, bufA, bufB, T3, Uleaf));
+  leaf_to_grid(s, Uleaf, NL, ctx->nL, M, Ug);
+  farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
+  CKR(sweep_adjoint(ctx, s, A2, P, E, CP, bufA, bufB, T3, Uleaf));
+  leaf_to_grid(s, Uleaf, NI, ctx->nL, P, Zg);
+  return HS_OK;
+}
+
+size_t fields_and_adjoint_bytes(hs_ctx* ctx, int M, int P) {
+  const int nb = ctx->B.nb;
+  const int nr = std::max(M, P);
+  return 4 * Arena::bytes((size_t)nb * M, 16) + 2 * Arena::bytes(field_buf_elems(ctx, nr), 16) +
+         Arena::bytes(t3_elems(ctx, nr), 16) + Arena::bytes((size_t)ctx->nleaf * NL * nr, 16) +
+         Arena::bytes((size_t)P * 2 * nb, 16) + 2 * Arena::bytes((size_t)nb * P, 16);
+}
+
+int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* J,
+                  Arena& a) {
+  const size_t plane = (size_t)ctx->n14 * ctx->n14;
+  double2* Ug = a.get<double2>(plane * M);
+  double2* Zg = a.get<double2>(plane * P);
+  CKR(fields_and_adjoint(ctx, s, alphas, M, thetas, P, Ug, Zg, a));
+  interior_sine_tables(s, ctx->d_xint, ctx->n14, ctx->S1, ctx->S2, ctx->d_sxi, ctx->d_syi);
+  size_t smem = sizeof(double2) * ((size_t)ctx->S1 * ctx->S2 + ctx->n14 + ctx->S1);
+  if (smem > 200 * 1024) return fail(ctx, HS_EINVAL, "S1*S2 too large for the Jacobian contraction");
+  contract_jacobian(s, Ug, Zg, M, P, ctx->n14, ctx->d_sxi, ctx->d_syi, ctx->S1, ctx->S2, ctx->k * ctx->k, J);
+  CK(cudaGetLastError());
+  return HS_OK;
+}
+
+size_t jacobian_bytes(hs_ctx* ctx, int M, int P) {
+  const size_t plane = (size_t)ctx->n14 * ctx->n14;
+  return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) + fields_and_adjoint_bytes(ctx, M, P);
+}
+
+int valid_angles(hs_ctx* ctx, int M, int P) {
+  if (M <= 0 || P <= 0 || M > 65535 || P > 65535) return fail(ctx, HS_EINVAL, "M and P must be in 1..65535");
+  return HS_OK;
+}
+
+// grad = Re J^H (F - data) = k^2 Re sum_x s_m1 s_m2 sum_d u_d(x) sum_p conj(F - data)_dp z_p(x)
+int gradient_core(hs_ctx* ctx, cudaStream_t s, const double* ddata, const double* da, int M, const double* dt,
+                         int P, double* dgrad, double* dmis, Arena& a) {
+  const int MP = M * P;
+  const size_t plane = (size_t)ctx->n14 * ctx->n14;
+  double2* F = a.get<double2>(MP);
+  double2* res = a.get<double2>(MP);
+  double2* Ug = a.get<double2>(plane * M);
+  double2* Zg = a.get<double2>(plane * P);
+  double2* Zmix = a.get<double2>(plane * M);
+  double* hre = a.get<double>(plane);
+  double* T1 = a.get<double>((size_t)ctx->S1 * ctx->n14);
+  {
+    Arena sub = a;
+    const int nb = ctx->B.nb;
+    double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);
+    double2 *f = sub.get<double2>((size_t)nb * M), *g = sub.get<double2>((size_t)nb * M);
+    double2* PS = sub.get<double2>((size_t)2 * nb * M);
+    double2* A2 = sub.get<double2>((size_t)P * 2 * nb);
+    CKR(root_solve(ctx, s, da, M, ui, dni, f, g));
+    boundary_data(s, nb, M, ctx->k, f, g, ui, dni, PS);
+    farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, dt, P, A2);
+    gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
+                                    make_double2(0, 0), F, P, 0, 1);
+  }
+  CK(cudaMemsetAsync(dmis, 0, sizeof(double), s));
+  residual(s, ddata, F, MP, res, nullptr, dmis);  // res = data - F
+  CKR(fields_and_adjoint(ctx, s, da, M, dt, P, Ug, Zg, a));
+  // Zmix = conj(F - data) Zg = -conj(res) Zg  (M x plane)
+  conj_neg(s, res, MP);
+  gemm<double2, double2, double2>(s, OP_N, OP_N, M, (int)plane, P, make_double2(1, 0), res, P, 0, Zg, (int)plane, 0,
+                                  make_double2(0, 0), Zmix, (int)plane, 0, 1);
+  gradient_combine(s, Ug, Zmix, M, (long long)plane, hre);
+  interior_sine_tables(s, ctx->d_xint, ctx->n14, ctx->S1, ctx->S2, ctx->d_sxi, ctx->d_syi);
+  // T1 = sx hre^T  (S1 x nY);  grad = k^2 T1 sy^T
+  gemm<double, double, double>(s, OP_N, OP_T, ctx->S1, ctx->n14, ctx->n14, 1.0, ctx->d_sxi, ctx->n14, 0, hre,
+                               ctx->n14, 0, 0.0, T1, ctx->n14, 0, 1);
+  gemm<double, double, double>(s, OP_N, OP_T, ctx->S1, ctx->S2, ctx->n14, ctx->k * ctx->k, T1, ctx->n14, 0,
+                               ctx->d_syi, ctx->n14, 0, 0.0, dgrad, ctx->S2, 0, 1);
+  half_in_place(s, dmis);
+  CK(cudaGetLastError());
+  return HS_OK;
+}
+
+size_t gradient_bytes(hs_ctx* ctx, int M, int P) {
+  const int MP = M * P;
+  const size_t plane = (size_t)ctx->n14 * ctx->n14;
+  return 2 * Arena::bytes(MP, 16) + Arena::bytes(plane * M, 16) * 2 + Arena::bytes(plane * P, 16) +
+         Arena::bytes(plane, 8) + Arena::bytes((size_t)ctx->S1 * ctx->n14, 8) + fields_and_adjoint_bytes(ctx, M, P);
+}
+
+}  // namespace
+
+// ============================== C ABI =====================================
+extern "C" {
+
+int hs_create(hs_ctx** out, const hs_config* cfg) {
+  if (!out || !cfg) return HS_EINVAL;
+  *out = nullptr;
+  const int nL = cfg->leaves_per_side;
+  if (nL < 1 || nL > 256 || (nL & (nL - 1)) != 0) return HS_EINVAL;
+  if (cfg->S1 < 1 || cfg->S2 < 1 || cfg->S1 > 512 || cfg->S2 > 512) return HS_EINVAL;
+  if (!(cfg->R > std::sqrt(2.0))) return HS_EINVAL;
+  if (cfg->precision != HS_FP64 && cfg->precision != HS_MIXED) return HS_EINVAL;
+  hs_ctx* ctx = new (std::nothrow) hs_ctx();
+  if (!ctx) return HS_ENOMEM;
+  ctx->cfg = *cfg;
+  ctx->nL = nL;
+  ctx->S1 = cfg->S1;
+  ctx->S2 = cfg->S2;
+  LaunchScope ls(ctx);
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return HS_ECUDA;
+  }
+  if (cfg->stream) {
+    ctx->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return HS_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  int r = setup(ctx);
+  if (r != HS_OK) {
+    hs_destroy(ctx);
+    return r;
+  }
+  *out = ctx;
+  return HS_OK;
+}
+
+int hs_node_coords(const hs_ctx* ctx, double* x, double* y) {
+  if (!ctx || !x || !y) return HS_EINVAL;
+  std::vector<double> t = lobatto(16);
+  const int nL = ctx->nL;
+  for (int leaf = 0; leaf < nL * nL; ++leaf) {
+    int ix = leaf % nL, iy = leaf / nL;
+    for (int a = 0; a < 16; ++a)
+      for (int b = 0; b < 16; ++b) {
+        size_t i = ((size_t)leaf * 16 + a) * 16 + b;
+        x[i] = -1.0 + ix * ctx->h + (t[a] + 1.0) * ctx->h / 2.0;
+        y[i] = -1.0 + iy * ctx->h + (t[b] + 1.0) * ctx->h / 2.0;
+      }
+  }
+  return HS_OK;
+}
+
+int hs_build(hs_ctx* ctx, const double* c, int S1, int S2, double k) {
+  CKR(check_ctx(ctx, false));
+  LaunchScope ls(ctx);
+  if (!c || S1 != ctx->S1 || S2 != ctx->S2) return fail(ctx, HS_EINVAL, "coefficient shape must be S1 x S2 of the config");
+  if (!(k > 0.0) || !std::isfinite(k)) return fail(ctx, HS_EINVAL, "k must be positive and finite");
+  for (int i = 0; i < S1 * S2; ++i)
+    if (!std::isfinite(c[i])) return fail(ctx, HS_EINVAL, "non-finite sine coefficient");
+  ctx->built = false;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->d_c, c, sizeof(double) * S1 * S2, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  sine_eval_grid(s, ctx->d_c, S1, S2, ctx->d_xg, ctx->nL, ctx->d_sx16, ctx->d_sy16, ctx->d_T, ctx->d_Qg, ctx->d_q,
+                 ctx->d_info + ctx->ninfo - 1);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_info + ctx->ninfo - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return fail(ctx, HS_EINVAL, "1 - q <= 0 (or NaN) at a leaf node");
+  return factor(ctx, k);
+}
+
+int hs_build_nodes(hs_ctx* ctx, const double* q_nodes, double k) {
+  CKR(check_ctx(ctx, false));
+  LaunchScope ls(ctx);
+  if (!q_nodes) return fail(ctx, HS_EINVAL, "q_nodes is NULL");
+  if (!(k > 0.0) || !std::isfinite(k)) return fail(ctx, HS_EINVAL, "k must be positive and finite");
+  ctx->built = false;
+  cudaStream_t s = ctx->stream;
+  const long long n = (long long)ctx->nleaf * 256;
+  CK(cudaMemcpyAsync(ctx->d_q, q_nodes, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  check_q(s, ctx->d_q, n, ctx->d_info + ctx->ninfo - 1);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_info + ctx->ninfo - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return fail(ctx, HS_EINVAL, "1 - q <= 0 (or NaN) at a leaf node");
+  return factor(ctx, k);
+}
+
+int hs_solve_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* ufar, void* stream) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!alphas || !thetas || !ufar) return fail(ctx, HS_EINVAL, "NULL pointer");
+  return solve_into(ctx, pick(ctx, stream), alphas, M, thetas, P, reinterpret_cast<double2*>(ufar));
+}
+
+int hs_solve(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* ufar) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!alphas || !thetas || !ufar) return fail(ctx, HS_EINVAL, "NULL pointer");
+  cudaStream_t s = ctx->stream;
+  double *da = nullptr, *dt = nullptr;
+  double2* du = nullptr;
+  CK(cudaMallocAsync(&da, sizeof(double) * M, s));
+  CK(cudaMallocAsync(&dt, sizeof(double) * P, s));
+  CK(cudaMallocAsync(&du, sizeof(double2) * M * P, s));
+  CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  int r = solve_into(ctx, s, da, M, dt, P, du);
+  if (r == HS_OK) CK(cudaMemcpyAsync(ufar, du, sizeof(double2) * M * P, cudaMemcpyDeviceToHost, s));
+  cudaFreeAsync(da, s);
+  cudaFreeAsync(dt, s);
+  cudaFreeAsync(du, s);
+  CK(cudaStreamSynchronize(s));
+  return r;
+}
+
+int hs_fields_dev(hs_ctx* ctx, const double* alphas, int M, double* u, void* stream) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  if (M <= 0 || M > 65535 || !alphas || !u) return fail(ctx, HS_EINVAL, "bad arguments");
+  cudaStream_t s = pick(ctx, stream);
+  const int nb = ctx->B.nb;
+  Arena a;
+  size_t need = 4 * Arena::bytes((size_t)nb * M, 16) + 2 * Arena::bytes(field_buf_elems(ctx, M), 16) +
+                Arena::bytes(t3_elems(ctx, M), 16) + Arena::bytes((size_t)ctx->nleaf * NL * M, 16);
+  CKR(ensure_ws(ctx, need, a));
+  double2 *ui = a.get<double2>((size_t)nb * M), *dni = a.get<double2>((size_t)nb * M);
+  double2 *f = a.get<double2>((size_t)nb * M), *g = a.get<double2>((size_t)nb * M);
+  double2 *bufA = a.get<double2>(field_buf_elems(ctx, M)), *bufB = a.get<double2>(field_buf_elems(ctx, M));
+  double2* T3 = a.get<double2>(t3_elems(ctx, M));
+  double2* Uleaf = a.get<double2>((size_t)ctx->nleaf * NL * M);
+  CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
+  CKR(sweep_down(ctx, s, f, M, bufA, bufB, T3, Uleaf));
+  leaf_to_nodes(s, Uleaf, ctx->nL, M, reinterpret_cast<double2*>(u));
+  CK(cudaGetLastError());
+  return HS_OK;
+}
+
+int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* J, void* stream) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!alphas || !thetas || !J) return fail(ctx, HS_EINVAL, "NULL pointer");
+  Arena a;
+  CKR(ensure_ws(ctx, jacobian_bytes(ctx, M, P), a));
+  return jacobian_into(ctx, pick(ctx, stream), alphas, M, thetas, P, reinterpret_cast<double2*>(J), a);
+}
+
+int hs_jacobian(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* J) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!alphas || !thetas || !J) return fail(ctx, HS_EINVAL, "NULL pointer");
+  cudaStream_t s = ctx->stream;
+  const size_t nJ = (size_t)M * P * ctx->S1 * ctx->S2;
+  Arena a;
+  size_t need = Arena::bytes(M, 8) + Arena::bytes(P, 8) + Arena::bytes(nJ, 16) + jacobian_bytes(ctx, M, P);
+  CKR(ensure_ws(ctx, need, a));
+  double* da = a.get<double>(M);
+  double* dt = a.get<double>(P);
+  double2* dJ = a.get<double2>(nJ);
+  CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  CKR(jacobian_into(ctx, s, da, M, dt, P, dJ, a));
+  CK(cudaMemcpyAsync(J, dJ, sizeof(double2) * nJ, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return HS_OK;
+}
+
+int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, const double* thetas, int P,
+               double lambda_rel, double* c_inout, double* resid_norm_out) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!data || !alphas || !thetas || !c_inout) return fail(ctx, HS_EINVAL, "NULL pointer");
+  if (!(lambda_rel >= 0.0) || !std::isfinite(lambda_rel)) return fail(ctx, HS_EINVAL, "lambda_rel must be >= 0");
+  cudaStream_t s = ctx->stream;
+  const int MP = M * P, nm = ctx->S1 * ctx->S2;
+  Arena a;
+  size_t need = Arena::bytes(M, 8) + Arena::bytes(P, 8) + Arena::bytes((size_t)2 * MP, 8) +
+                Arena::bytes(MP, 16) * 2 + Arena::bytes((size_t)2 * MP, 8) + Arena::bytes(8, 8) +
+                Arena::bytes((size_t)MP * nm, 16) + Arena::bytes((size_t)2 * MP * nm, 8) +
+                Arena::bytes((size_t)nm * nm, 8) + Arena::bytes(nm, 8) + Arena::bytes(nm, 4) +
+                std::max(jacobian_bytes(ctx, M, P),
+                         4 * Arena::bytes((size_t)ctx->B.nb * M, 16) + Arena::bytes((size_t)2 * ctx->B.nb * M, 16) +
+                             Arena::bytes((size_t)P * 2 * ctx->B.nb, 16));
+  CKR(ensure_ws(ctx, need, a));
+  double* da = a.get<double>(M);
+  double* dt = a.get<double>(P);
+  double* ddata = a.get<double>((size_t)2 * MP);
+  double2* F = a.get<double2>(MP);
+  double2* res = a.get<double2>(MP);
+  double* rst = a.get<double>((size_t)2 * MP);
+  double* nrm2 = a.get<double>(8);
+  double2* J = a.get<double2>((size_t)MP * nm);
+  double* Jst = a.get<double>((size_t)2 * MP * nm);
+  double* A = a.get<double>((size_t)nm * nm);
+  double* bv = a.get<double>(nm);
+  int* piv = a.get<int>(nm);
+  CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
+  {
+    Arena sub = a;  // the forward solve's scratch is reused by the Jacobian afterwards
+    const int nb = ctx->B.nb;
+    double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);
+    double2 *f = sub.get<double2>((size_t)nb * M), *g = sub.get<double2>((size_t)nb * M);
+    double2* PS = sub.get<double2>((size_t)2 * nb * M);
+    double2* A2 = sub.get<double2>((size_t)P * 2 * nb);
+    CKR(root_solve(ctx, s, da, M, ui, dni, f, g));
+    boundary_data(s, nb, M, ctx->k, f, g, ui, dni, PS);
+    farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, dt, P, A2);
+    gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
+                                    make_double2(0, 0), F, P, 0, 1);
+  }
+  residual(s, ddata, F, MP, res, rst, nrm2);
+  CKR(jacobian_into(ctx, s, da, M, dt, P, J, a));
+  // normal equations in the real coefficients: A = Jst^T Jst, b = Jst^T rst
+  split_stack(s, J, MP, nm, Jst);
+  gemm<double, double, double>(s, OP_T, OP_N, nm, nm, 2 * MP, 1.0, Jst, nm, 0, Jst, nm, 0, 0.0, A, nm, 0, 1);
+  gemm<double, double, double>(s, OP_T, OP_N, nm, 1, 2 * MP, 1.0, Jst, nm, 0, rst, 1, 0, 0.0, bv, 1, 0, 1);
+  add_lambda(s, A, nm, lambda_rel);
+  CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  lu_factor<double>(s, A, nm, 0, nm, piv, 0, ctx->d_info, 1);
+  lu_solve<double>(s, OP_N, A, nm, 0, nm, piv, 0, bv, 1, 0, 1, 1);
+  std::vector<double> dc(nm);
+  double r2 = 0.0;
+  CK(cudaMemcpyAsync(dc.data(), bv, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&r2, nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
+  CKR(check_info(ctx));
+  for (int i = 0; i < nm; ++i) c_inout[i] += dc[i];
+  if (resid_norm_out) *resid_norm_out = std::sqrt(r2);
+  return HS_OK;
+}
+
+int hs_gradient_dev(hs_ctx* ctx, const double* data, const double* alphas, int M, const double* thetas, int P,
+                    double* grad, double* misfit_out, void* stream) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!data || !alphas || !thetas || !grad || !misfit_out) return fail(ctx, HS_EINVAL, "NULL pointer");
+  Arena a;
+  CKR(ensure_ws(ctx, gradient_bytes(ctx, M, P), a));
+  return gradient_core(ctx, pick(ctx, stream), data, alphas, M, thetas, P, grad, misfit_out, a);
+}
+
+int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M, const double* thetas, int P,
+                double* grad, double* misfit_out) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!data || !alphas || !thetas || !grad) return fail(ctx, HS_EINVAL, "NULL pointer");
+  cudaStream_t s = ctx->stream;
+  const int MP = M * P, nm = ctx->S1 * ctx->S2;
+  Arena a;
+  size_t need = Arena::bytes(M, 8) + Arena::bytes(P, 8) + Arena::bytes((size_t)2 * MP, 8) + Arena::bytes(nm, 8) +
+                Arena::bytes(8, 8) + gradient_bytes(ctx, M, P);
+  CKR(ensure_ws(ctx, need, a));
+  double* da = a.get<double>(M);
+  double* dt = a.get<double>(P);
+  double* ddata = a.get<double>((size_t)2 * MP);
+  double* dg = a.get<double>(nm);
+  double* dm = a.get<double>(8);
+  CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
+  CKR(gradient_core(ctx, s, ddata, da, M, dt, P, dg, dm, a));
+  double mis = 0.0;
+  CK(cudaMemcpyAsync(grad, dg, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&mis, dm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (misfit_out) *misfit_out = mis;
+  return HS_OK;
+}
+
+long long hs_launch_count(const hs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* hs_last_error(const hs_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+void hs_destroy(hs_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->ws_base) cudaFree(ctx->ws_base);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// Jacobian by discrete reciprocity, misfit gradient and the Gauss-Newton
+// normal equations.
+//
+// Theorem 3.1 gives a column of J as the far field of v with
+//   Lap v + k^2 (1 - q) v = k^2 phi_m u_d.
+// On the discrete system A x = b that is  J[(d,p), m] = l_p^T A^{-1} (k^2 phi_m u_d),
+// so with the adjoint field z_p = A^{-T} l_p (the discrete counterpart of the
+// adjoint field w of Theorem 3.2, computed by one transposed sweep of the
+// stored merge operators per receiver) every entry is the contraction
+//   J[(d,p), (m1,m2)] = k^2 sum_x z_p(x) u_d(x) s_m1(x1) s_m2(x2)
+// over the interior collocation nodes: a Khatri-Rao product of forward and
+// adjoint fields projected on the separable sine basis (eq. sineseries).
+#include "tree.cuh"
+
+namespace hs {
+
+// Interior rows of the leaf layout (r = (a-1)*14 + (b-1)) into the global
+// interior grid G[j][gy][gx], gx = ix*14 + a-1, gy = iy*14 + b-1.
+__global__ void k_leaf_to_grid(const double2* __restrict__ U, int rows, int nL, int nrhs, double2* __restrict__ G) {
+  const int n14 = nL * 14;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long tot = (long long)nL * nL * NI * nrhs;
+  if (e >= tot) return;
+  int j = (int)(e % nrhs);
+  long long t = e / nrhs;
+  int r = (int)(t % NI);
+  int leaf = (int)(t / NI);
+  int ix = leaf % nL, iy = leaf / nL;
+  int a = r / 14, b = r % 14;
+  G[((long long)j * n14 + iy * 14 + b) * n14 + ix * 14 + a] = U[((long long)leaf * rows + r) * nrhs + j];
+}
+
+void leaf_to_grid(cudaStream_t s, const double2* Uleaf, int nrows_leaf, int nL, int nrhs, double2* G) {
+  long long tot = (long long)nL * nL * NI * nrhs;
+  k_leaf_to_grid<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Uleaf, nrows_leaf, nL, nrhs, G);
+  HS_COUNT_LAUNCH();
+}
+
+// Leaf layout (252 unknowns) into the natural node order out[j][leaf][a*16 + b]
+// (corners, which are not unknowns, are 0).
+__global__ void k_leaf_to_nodes(const double2* __restrict__ U, int nL, int nrhs, double2* __restrict__ out) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nleaf = nL * nL;
+  long long tot = (long long)nleaf * 256 * nrhs;
+  if (e >= tot) return;
+  int node = (int)(e % 256);
+  long long t = e / 256;
+  int leaf = (int)(t % nleaf);
+  int j = (int)(t / nleaf);
+  int a = node / 16, b = node % 16;
+  int r = -1;
+  if (a >= 1 && a <= 14 && b >= 1 && b <= 14) r = (a - 1) * 14 + (b - 1);
+  else if (b == 0 && a >= 1 && a <= 14) r = NI + a - 1;
+  else if (a == 15 && b >= 1 && b <= 14) r = NI + 14 + b - 1;
+  else if (b == 15 && a >= 1 && a <= 14) r = NI + 28 + a - 1;
+  else if (a == 0 && b >= 1 && b <= 14) r = NI + 42 + b - 1;
+  out[e] = r < 0 ? make_double2(0.0, 0.0) : U[((long long)leaf * NL + r) * nrhs + j];
+}
+
+void leaf_to_nodes(cudaStream_t s, const double2* Uleaf, int nL, int nrhs, double2* out) {
+  long long tot = (long long)nL * nL * 256 * nrhs;
+  k_leaf_to_nodes<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Uleaf, nL, nrhs, out);
+  HS_COUNT_LAUNCH();
+}
+
+__global__ void k_int_sine(const double* __restrict__ xg, int n, int S, double* __restrict__ out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int m = blockIdx.y + 1;
+  if (g < n) out[(long long)(m - 1) * n + g] = sinpi(0.5 * m * (xg[g] + 1.0));
+}
+
+void interior_sine_tables(cudaStream_t s, const double* xg_int, int n, int S1, int S2, double* sx, double* sy) {
+  k_int_sine<<<dim3((n + 127) / 128, S1), 128, 0, s>>>(xg_int, n, S1, sx);
+  HS_COUNT_LAUNCH();
+  k_int_sine<<<dim3((n + 127) / 128, S2), 128, 0, s>>>(xg_int, n, S2, sy);
+  HS_COUNT_LAUNCH();
+}
+
+// One block per (d, p): acc[m1][m2] = sum_gy sy[m2][gy] sum_gx sx[m1][gx] (u_d z_p)[gy][gx].
+__global__ void __launch_bounds__(256) k_contract(const double2* __restrict__ Ug, const double2* __restrict__ Zg,
+                                                  int P, int nX, const double* __restrict__ sx,
+                                                  const double* __restrict__ sy, int S1, int S2, double k2,
+                                                  double2* __restrict__ J) {
+  extern __shared__ double2 sm[];
+  double2* acc = sm;              // S1*S2
+  double2* w = acc + S1 * S2;     // nX
+  double2* t = w + nX;            // S1
+  const int pair = blockIdx.x;
+  const int d = pair / P, p = pair % P;
+  const long long plane = (long long)nX * nX;
+  const double2* u = Ug + d * plane;
+  const double2* z = Zg + p * plane;
+  for (int e = threadIdx.x; e < S1 * S2; e += blockDim.x) acc[e] = make_double2(0.0, 0.0);
+  for (int gy = 0; gy < nX; ++gy) {
+    __syncthreads();
+    for (int gx = threadIdx.x; gx < nX; gx += blockDim.x) w[gx] = u[(long long)gy * nX + gx] * z[(long long)gy * nX + gx];
+    __syncthreads();
+    for (int m1 = threadIdx.x; m1 < S1; m1 += blockDim.x) {
+      double2 v = make_double2(0.0, 0.0);
+      const double* srow = sx + (long long)m1 * nX;
+      for (int gx = 0; gx < nX; ++gx) v = v + srow[gx] * w[gx];
+      t[m1] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < S1 * S2; e += blockDim.x) {
+      int m1 = e / S2, m2 = e % S2;
+      acc[e] = acc[e] + sy[(long long)m2 * nX + gy] * t[m1];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < S1 * S2; e += blockDim.x) J[(long long)pair * S1 * S2 + e] = k2 * acc[e];
+}
+
+void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
+                       const double* sy, int S1, int S2, double k2, double2* J) {
+  size_t smem = sizeof(double2) * ((size_t)S1 * S2 + nX + S1);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_contract<<<M * P, 256, smem, s>>>(Ug, Zg, P, nX, sx, sy, S1, S2, k2, J);
+  HS_COUNT_LAUNCH();
+}
+
+// Jst = [Re J; Im J] (2 rows x cols, real).
+__global__ void k_split_stack(const double2* __restrict__ J, int rows, int cols, double* __restrict__ Jst) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  double2 v = J[e];
+  Jst[e] = v.x;
+  Jst[(long long)rows * cols + e] = v.y;
+}
+
+void split_stack(cudaStream_t s, const double2* J, int rows, int cols, double* Jst) {
+  long long n = (long long)rows * cols;
+  k_split_stack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(J, rows, cols, Jst);
+  HS_COUNT_LAUNCH();
+}
+
+// res = data - F; rst = [Re res; Im res]; out2 += sum |res|^2.
+__global__ void k_residual(const double* __restrict__ data, const double2* __restrict__ F, int n,
+                           double2* __restrict__ res, double* __restrict__ rst, double* __restrict__ out2) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (e < n) {
+    double2 r = make_double2(data[2 * e] - F[e].x, data[2 * e + 1] - F[e].y);
+    res[e] = r;
+    if (rst) {
+      rst[e] = r.x;
+      rst[n + e] = r.y;
+    }
+    v = r.x * r.x + r.y * r.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out2, v);
+}
+
+void residual(cudaStream_t s, const double* data, const double2* F, int n, double2* res, double* rst, double* out2) {
+  k_residual<<<(n + 255) / 256, 256, 0, s>>>(data, F, n, res, rst, out2);
+  HS_COUNT_LAUNCH();
+}
+
+// A += lambda I with lambda = lambda_rel * trace(A) / n (one block).
+__global__ void k_add_lambda(double* A, int n, double lambda_rel) {
+  __shared__ double red[256];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += A[(long long)i * n + i];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  double lam = lambda_rel * red[0] / n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) A[(long long)i * n + i] += lam;
+}
+
+void add_lambda(cudaStream_t s, double* A, int n, double lambda_rel) {
+  k_add_lambda<<<1, 256, 0, s>>>(A, n, lambda_rel);
+  HS_COUNT_LAUNCH();
+}
+
+// hre[x] = Re sum_d Ug[d][x] Zmix[d][x].
+__global__ void k_gradient_combine(const double2* __restrict__ Ug, const double2* __restrict__ Zmix, int M,
+                                   long long npts, double* __restrict__ hre) {
+  long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= npts) return;
+  double v = 0.0;
+  for (int d = 0; d < M; ++d) {
+    double2 a = Ug[d * npts + x], b = Zmix[d * npts + x];
+    v += a.x * b.x - a.y * b.y;
+  }
+  hre[x] = v;
+}
+
+void gradient_combine(cudaStream_t s, const double2* Ug, const double2* Zmix, int M, long long npts, double* hre) {
+  k_gradient_combine<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(Ug, Zmix, M, npts, hre);
+  HS_COUNT_LAUNCH();
+}
+
+// v <- -conj(v)
+__global__ void k_conj_neg(double2* v, int n) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) v[e] = make_double2(-v[e].x, v[e].y);
+}
+
+void conj_neg(cudaStream_t s, double2* v, int n) {
+  k_conj_neg<<<(n + 255) / 256, 256, 0, s>>>(v, n);
+  HS_COUNT_LAUNCH();
+}
+
+__global__ void k_half(double* v) { v[0] *= 0.5; }
+
+void half_in_place(cudaStream_t s, double* v) {
+  k_half<<<1, 1, 0, s>>>(v);
+  HS_COUNT_LAUNCH();
+}
+
+}  // namespace hs

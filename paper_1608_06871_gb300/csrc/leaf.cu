@@ -1,0 +1,204 @@
+// Leaf-level kernels: the band-limited contrast on the leaf grids (Sec. 3.2,
+// eq. sineseries, Definition of E_k) and the per-leaf spectral collocation
+// operators of the direct solver (Sec. 2: K x K Chebyshev grids, K = 16).
+//
+// Leaf-local orderings (shared with tree.cu and hs_api.cu through tree.cuh):
+//   interior node (a, b), 1 <= a, b <= 14:      r = (a-1)*14 + (b-1)       (196)
+//   edge nodes in boundary order S, E, N, W,
+//   each side by increasing coordinate:         e = side*14 + (t-1)        (56)
+//   S: (a, 0)   E: (15, b)   N: (a, 15)   W: (0, b)
+// The 4 corner nodes are not unknowns of the discretisation.
+#include "tree.cuh"
+
+namespace hs {
+
+__constant__ double c_D1[16 * 16];  // Chebyshev-Lobatto differentiation on [-1, 1]
+
+void upload_cheb_diff(const double* D1, cudaStream_t s) {
+  cudaMemcpyToSymbolAsync(c_D1, D1, sizeof(double) * 256, 0, cudaMemcpyHostToDevice, s);
+}
+
+// s[m-1][g] = sin(m pi (x_g + 1) / 2) for the leaf-grid coordinates x_g (length ng).
+__global__ void k_sine_table(const double* __restrict__ xg, int ng, int S, double* __restrict__ out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int m = blockIdx.y + 1;
+  if (g >= ng) return;
+  out[(long long)(m - 1) * ng + g] = sinpi(0.5 * m * (xg[g] + 1.0));
+}
+
+// Scatter the global node grid Qg[gx][gy] (gx = ix*16 + a) into the leaf layout
+// q[leaf][a][b] and flag 1 - q <= 0 or NaN.
+__global__ void k_grid_to_leaves(const double* __restrict__ Qg, int nL, double* __restrict__ q, int* __restrict__ bad) {
+  const int n16 = nL * 16;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n16 * n16) return;
+  int gx = (int)(idx / n16), gy = (int)(idx % n16);
+  int ix = gx / 16, a = gx % 16, iy = gy / 16, b = gy % 16;
+  double v = Qg[idx];
+  q[(((long long)(iy * nL + ix)) * 16 + a) * 16 + b] = v;
+  if (!(1.0 - v > 0.0)) atomicExch(bad, 1);
+}
+
+__global__ void k_check_q(const double* __restrict__ q, long long n, int* __restrict__ bad) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !(1.0 - q[i] > 0.0)) atomicExch(bad, 1);
+}
+
+__device__ __forceinline__ int edge_index(int a, int b) {
+  if (b == 0) return a - 1;         // S
+  if (a == 15) return 14 + b - 1;   // E
+  if (b == 15) return 28 + a - 1;   // N
+  return 42 + b - 1;                // W
+}
+
+// Assemble, per leaf, the blocks of the leaf system (interior PDE rows and the
+// outward normal derivative at the edge nodes):
+//   Aii (196x196), Aie (196x56): rows of  Lap_h u + k^2 (1 - q) u  at interior nodes,
+//   Ni (56x196), NiT = Ni^T (196x56), Ne (56x56): outward normal derivative rows.
+__global__ void __launch_bounds__(256) k_leaf_assemble(const double* __restrict__ q, int leaf0, double k, double h,
+                                                       double* __restrict__ Aii, double* __restrict__ Aie,
+                                                       double* __restrict__ Ni, double* __restrict__ NiT,
+                                                       double* __restrict__ Ne) {
+  const int lb = blockIdx.x;  // leaf within the chunk
+  const double* ql = q + (long long)(leaf0 + lb) * 256;
+  Aii += (long long)lb * NI * NI;
+  Aie += (long long)lb * NI * NE;
+  Ni += (long long)lb * NE * NI;
+  NiT += (long long)lb * NI * NE;
+  Ne += (long long)lb * NE * NE;
+  __shared__ double Dx[16][16], D2[16][16];
+  const double sc = 2.0 / h;
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) Dx[e / 16][e % 16] = c_D1[e] * sc;
+  __syncthreads();
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    int i = e / 16, j = e % 16;
+    double s = 0.0;
+    for (int c = 0; c < 16; ++c) s += Dx[i][c] * Dx[c][j];
+    D2[i][j] = s;
+  }
+  for (int e = threadIdx.x; e < NI * NI; e += blockDim.x) Aii[e] = 0.0;
+  for (int e = threadIdx.x; e < NI * NE; e += blockDim.x) { Aie[e] = 0.0; Ni[e] = 0.0; NiT[e] = 0.0; }
+  for (int e = threadIdx.x; e < NE * NE; e += blockDim.x) Ne[e] = 0.0;
+  __syncthreads();
+  // interior rows: one thread per row
+  for (int r = threadIdx.x; r < NI; r += blockDim.x) {
+    const int a = r / 14 + 1, b = r % 14 + 1;
+    double* row = Aii + (long long)r * NI;
+    double* rowe = Aie + (long long)r * NE;
+    for (int c = 1; c <= 14; ++c) {
+      row[(c - 1) * 14 + (b - 1)] += D2[a][c];  // d2/dx2 along the x-line through (a, b)
+      row[(a - 1) * 14 + (c - 1)] += D2[b][c];  // d2/dy2 along the y-line
+    }
+    row[r] += k * k * (1.0 - ql[a * 16 + b]);
+    rowe[edge_index(0, b)] += D2[a][0];
+    rowe[edge_index(15, b)] += D2[a][15];
+    rowe[edge_index(a, 0)] += D2[b][0];
+    rowe[edge_index(a, 15)] += D2[b][15];
+  }
+  // normal-derivative rows: one thread per edge node
+  for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+    const int side = e / 14, t = e % 14 + 1;
+    double* nrow = Ni + (long long)e * NI;
+    double* erow = Ne + (long long)e * NE;
+    for (int c = 0; c < 16; ++c) {
+      int a, b;
+      double w;
+      switch (side) {
+        case 0: a = t; b = c; w = -Dx[0][c]; break;    // S: -d/dy at (t, 0)
+        case 1: a = c; b = t; w = Dx[15][c]; break;    // E: +d/dx at (15, t)
+        case 2: a = t; b = c; w = Dx[15][c]; break;    // N: +d/dy at (t, 15)
+        default: a = c; b = t; w = -Dx[0][c]; break;   // W: -d/dx at (0, t)
+      }
+      bool interior = (a >= 1 && a <= 14 && b >= 1 && b <= 14);
+      if (interior) {
+        int rr = (a - 1) * 14 + (b - 1);
+        nrow[rr] += w;
+        NiT[(long long)rr * NE + e] += w;
+      } else {
+        erow[edge_index(a, b)] += w;  // never a corner: one coordinate is t in 1..14
+      }
+    }
+  }
+}
+
+// K = T + i eta I (complex), Kinv = I.
+__global__ void k_make_K(const double* __restrict__ T, double eta, double2* __restrict__ K, double2* __restrict__ Kinv,
+                         int nleaf) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nleaf * NE * NE) return;
+  int e = (int)(idx % (NE * NE));
+  int r = e / NE, c = e % NE;
+  K[idx] = make_double2(T[idx], r == c ? eta : 0.0);
+  Kinv[idx] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+}
+
+// R = I - 2 i eta Kinv (leaf impedance-to-impedance map); Ye = Kinv (edge rows of Y).
+__global__ void k_leaf_R(const double2* __restrict__ Kinv, double eta, double2* __restrict__ R, double2* __restrict__ Y,
+                         int nleaf) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nleaf * NE * NE) return;
+  int lb = (int)(idx / (NE * NE));
+  int e = (int)(idx % (NE * NE));
+  int r = e / NE, c = e % NE;
+  double2 v = Kinv[idx];
+  // -2 i eta (x + i y) = 2 eta y - 2 i eta x
+  R[idx] = make_double2((r == c ? 1.0 : 0.0) + 2.0 * eta * v.y, -2.0 * eta * v.x);
+  Y[(long long)lb * NL * NE + (long long)(NI + r) * NE + c] = v;
+}
+
+void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, double h, LeafScratch& w,
+                      double2* R, double2* Y, double2* Q, int* info) {
+  const double eta = k;
+  k_leaf_assemble<<<nleaf, 256, 0, s>>>(q, leaf0, k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
+  HS_COUNT_LAUNCH();
+  lu_factor<double>(s, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, info, nleaf);
+  // X = Aii^{-1} Aie (Dirichlet-to-interior map), W = Aii^{-T} Ni^T (adjoint)
+  lu_solve<double>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.Aie, NE, (long long)NI * NE, NE, nleaf);
+  lu_solve<double>(s, OP_T, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.NiT, NE, (long long)NI * NE, NE, nleaf);
+  // T = Ne - Ni X  (leaf Dirichlet-to-Neumann map), stored in Ne
+  gemm<double, double, double>(s, OP_N, OP_N, NE, NE, NI, -1.0, w.Ni, NI, (long long)NE * NI, w.Aie, NE,
+                               (long long)NI * NE, 1.0, w.Ne, NE, (long long)NE * NE, nleaf);
+  {
+    long long n = (long long)nleaf * NE * NE;
+    k_make_K<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Ne, eta, w.K, w.Kinv, nleaf);
+    HS_COUNT_LAUNCH();
+  }
+  lu_factor<double2>(s, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, info, nleaf);
+  lu_solve<double2>(s, OP_N, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, w.Kinv, NE, (long long)NE * NE, NE, nleaf);
+  {
+    long long n = (long long)nleaf * NE * NE;
+    k_leaf_R<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Kinv, eta, R, Y, nleaf);
+    HS_COUNT_LAUNCH();
+  }
+  // interior rows of the solution operator: Yi = -X Kinv
+  gemm<double, double2, double2>(s, OP_N, OP_N, NI, NE, NE, make_double2(-1.0, 0.0), w.Aie, NE, (long long)NI * NE,
+                                 w.Kinv, NE, (long long)NE * NE, make_double2(0.0, 0.0), Y, NE, (long long)NL * NE,
+                                 nleaf);
+  // adjoint body-load operator: Q = 2 i eta W Kinv^T
+  gemm<double, double2, double2>(s, OP_N, OP_T, NI, NE, NE, make_double2(0.0, 2.0 * eta), w.NiT, NE,
+                                 (long long)NI * NE, w.Kinv, NE, (long long)NE * NE, make_double2(0.0, 0.0), Q, NE,
+                                 (long long)NI * NE, nleaf);
+}
+
+void sine_eval_grid(cudaStream_t s, const double* c, int S1, int S2, const double* xg, int nL, double* sx, double* sy,
+                    double* T, double* Qg, double* q, int* bad) {
+  const int n16 = nL * 16;
+  dim3 g1((n16 + 127) / 128, S1), g2((n16 + 127) / 128, S2);
+  k_sine_table<<<g1, 128, 0, s>>>(xg, n16, S1, sx);
+  HS_COUNT_LAUNCH();
+  k_sine_table<<<g2, 128, 0, s>>>(xg, n16, S2, sy);
+  HS_COUNT_LAUNCH();
+  // T[m1][gy] = sum_m2 c[m1][m2] sy[m2][gy];   Qg[gx][gy] = sum_m1 sx[m1][gx] T[m1][gy]
+  gemm<double, double, double>(s, OP_N, OP_N, S1, n16, S2, 1.0, c, S2, 0, sy, n16, 0, 0.0, T, n16, 0, 1);
+  gemm<double, double, double>(s, OP_T, OP_N, n16, n16, S1, 1.0, sx, n16, 0, T, n16, 0, 0.0, Qg, n16, 0, 1);
+  long long n = (long long)n16 * n16;
+  k_grid_to_leaves<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Qg, nL, q, bad);
+  HS_COUNT_LAUNCH();
+}
+
+void check_q(cudaStream_t s, const double* q, long long n, int* bad) {
+  k_check_q<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, n, bad);
+  HS_COUNT_LAUNCH();
+}
+
+}  // namespace hs

@@ -1,0 +1,312 @@
+// Batched dense linear algebra kernels (see linalg.cuh).
+//
+// FP64 on this part runs at a small fraction of the FP32 rate, so these
+// kernels are arithmetic-bound by construction; they are tiled for data reuse
+// in shared memory and use every SM through the batch and tile dimensions.
+#include "linalg.cuh"
+
+namespace hs {
+
+bool prof_active(int family);
+void prof_begin(cudaStream_t s, cudaEvent_t* a);
+void prof_end(cudaStream_t s, cudaEvent_t a, double flops);
+
+namespace {
+template <typename TA, typename TB> constexpr double flops_per_mac() {
+  return (sizeof(TA) == 16 && sizeof(TB) == 16) ? 8.0 : ((sizeof(TA) == 16 || sizeof(TB) == 16) ? 4.0 : 2.0);
+}
+constexpr int BM = 32, BN = 32, BK = 16;  // GEMM tile
+constexpr int NB = 32;                    // LU / TRSM block size
+
+template <typename T> __device__ __forceinline__ T ld_op(const T* P, int ld, int op, int r, int c) {
+  return op == OP_N ? P[(long long)r * ld + c] : P[(long long)c * ld + r];
+}
+
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, int k, TC alpha, const TA* __restrict__ A,
+                                              int lda, long long sA, const TB* __restrict__ B, int ldb, long long sB,
+                                              TC beta, TC* __restrict__ C, int ldc, long long sC) {
+  __shared__ TA As[BK][BM + 1];
+  __shared__ TB Bs[BK][BN + 1];
+  const int b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  TC acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = el<TC>::zero();
+  for (int k0 = 0; k0 < k; k0 += BK) {
+    // load A tile: BM x BK, element (r, kk) of op(A)
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int r, kk;
+      if (opA == OP_N) { r = e / BK; kk = e % BK; } else { kk = e / BM; r = e % BM; }
+      int gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < m && gk < k) ? ld_op(A, lda, opA, gr, gk) : el<TA>::zero();
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      int kk, c;
+      if (opB == OP_N) { kk = e / BN; c = e % BN; } else { c = e / BK; kk = e % BK; }
+      int gk = k0 + kk, gc = col0 + c;
+      Bs[kk][c] = (gk < k && gc < n) ? ld_op(B, ldb, opB, gk, gc) : el<TB>::zero();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TA a0 = As[kk][ty], a1 = As[kk][ty + 16];
+      TB b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      acc[0][0] = addv(acc[0][0], mul(a0, b0));
+      acc[0][1] = addv(acc[0][1], mul(a0, b1));
+      acc[1][0] = addv(acc[1][0], mul(a1, b0));
+      acc[1][1] = addv(acc[1][1], mul(a1, b1));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < m && c < n) {
+        TC v = scal<TC, TC>(alpha, acc[i][j]);
+        long long o = (long long)r * ldc + c;
+        if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
+        C[o] = v;
+      }
+    }
+}
+
+// Panel factorisation of columns [j0, j0+nb) with partial pivoting; row swaps
+// are applied to whole rows.  One CTA per matrix.
+template <typename E>
+__global__ void __launch_bounds__(256) k_lu_panel(E* A, int lda, long long sA, int n, int j0, int nb, int* piv,
+                                                  long long sP, int* info) {
+  __shared__ double smag[256];
+  __shared__ int sidx[256];
+  const int b = blockIdx.x;
+  A += b * sA;
+  piv += b * sP;
+  const int t = threadIdx.x;
+  for (int j = j0; j < j0 + nb; ++j) {
+    double best = -1.0;
+    int bi = j;
+    for (int r = j + t; r < n; r += 256) {
+      double v = el<E>::mag2(A[(long long)r * lda + j]);
+      if (v > best) { best = v; bi = r; }
+    }
+    smag[t] = best;
+    sidx[t] = bi;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (t < s) {
+        if (smag[t + s] > smag[t] || (smag[t + s] == smag[t] && sidx[t + s] < sidx[t])) {
+          smag[t] = smag[t + s];
+          sidx[t] = sidx[t + s];
+        }
+      }
+      __syncthreads();
+    }
+    const int p = sidx[0];
+    const bool zero = !(smag[0] > 0.0);
+    __syncthreads();
+    if (t == 0) {
+      piv[j] = p;
+      if (zero && info[b] == 0) info[b] = j + 1;
+    }
+    if (p != j) {
+      for (int c = t; c < n; c += 256) {
+        E tmp = A[(long long)j * lda + c];
+        A[(long long)j * lda + c] = A[(long long)p * lda + c];
+        A[(long long)p * lda + c] = tmp;
+      }
+    }
+    __syncthreads();
+    if (!zero) {
+      E pv = A[(long long)j * lda + j];
+      for (int r = j + 1 + t; r < n; r += 256) A[(long long)r * lda + j] = el<E>::div(A[(long long)r * lda + j], pv);
+    }
+    __syncthreads();
+    const int w = j0 + nb - 1 - j;  // remaining panel columns
+    if (w > 0) {
+      const long long tot = (long long)(n - j - 1) * w;
+      for (long long e = t; e < tot; e += 256) {
+        int r = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
+        A[(long long)r * lda + c] = A[(long long)r * lda + c] - mul(A[(long long)r * lda + j], A[(long long)j * lda + c]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Triangular solve with a diagonal block of size nb <= NB for many right-hand
+// sides (one thread per column).  mode: 0 = L (unit lower), 1 = U (upper),
+// 2 = U^T (lower, non-unit), 3 = L^T (upper, unit).
+template <typename E>
+__global__ void __launch_bounds__(128) k_trsm_diag(const E* A, int lda, long long sA, int i0, int nb, int mode, E* B,
+                                                   int ldb, long long sB, int nrhs) {
+  __shared__ E T[NB][NB + 1];
+  const int b = blockIdx.y;
+  A += b * sA;
+  B += b * sB;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int r = e / nb, c = e % nb;
+    bool tr = (mode >= 2);
+    T[r][c] = tr ? A[(long long)(i0 + c) * lda + i0 + r] : A[(long long)(i0 + r) * lda + i0 + c];
+  }
+  __syncthreads();
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  E x[NB];
+  for (int r = 0; r < nb; ++r) x[r] = B[(long long)(i0 + r) * ldb + col];
+  const bool lower = (mode == 0 || mode == 2);
+  const bool unit = (mode == 0 || mode == 3);
+  if (lower) {
+    for (int r = 0; r < nb; ++r) {
+      E v = x[r];
+      for (int s = 0; s < r; ++s) v = v - mul(T[r][s], x[s]);
+      x[r] = unit ? v : el<E>::div(v, T[r][r]);
+    }
+  } else {
+    for (int r = nb - 1; r >= 0; --r) {
+      E v = x[r];
+      for (int s = r + 1; s < nb; ++s) v = v - mul(T[r][s], x[s]);
+      x[r] = unit ? v : el<E>::div(v, T[r][r]);
+    }
+  }
+  for (int r = 0; r < nb; ++r) B[(long long)(i0 + r) * ldb + col] = x[r];
+}
+
+template <typename E>
+__global__ void k_swaps(const int* piv, long long sP, int n, int reverse, E* B, int ldb, long long sB, int nrhs) {
+  const int b = blockIdx.y;
+  piv += b * sP;
+  B += b * sB;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  if (!reverse) {
+    for (int j = 0; j < n; ++j) {
+      int p = piv[j];
+      if (p != j) {
+        E t = B[(long long)j * ldb + col];
+        B[(long long)j * ldb + col] = B[(long long)p * ldb + col];
+        B[(long long)p * ldb + col] = t;
+      }
+    }
+  } else {
+    for (int j = n - 1; j >= 0; --j) {
+      int p = piv[j];
+      if (p != j) {
+        E t = B[(long long)j * ldb + col];
+        B[(long long)j * ldb + col] = B[(long long)p * ldb + col];
+        B[(long long)p * ldb + col] = t;
+      }
+    }
+  }
+}
+}  // namespace
+
+template <typename TA, typename TB, typename TC>
+void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const TA* A, int lda, long long sA,
+          const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC, int batch) {
+  if (m <= 0 || n <= 0 || batch <= 0) return;
+  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
+  const bool prof = prof_active(1);
+  cudaEvent_t ev = nullptr;
+  if (prof) prof_begin(s, &ev);
+  k_gemm<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  HS_COUNT_LAUNCH();
+  if (prof) prof_end(s, ev, flops_per_mac<TA, TB>() * (double)m * n * k * batch);
+}
+
+template <typename E>
+void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info, int batch) {
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    int nb = n - j0 < NB ? n - j0 : NB;
+    k_lu_panel<E><<<batch, 256, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
+    HS_COUNT_LAUNCH();
+    int rest = n - j0 - nb;
+    if (rest > 0) {
+      dim3 g((rest + 127) / 128, batch);
+      k_trsm_diag<E><<<g, 128, 0, s>>>(A, lda, sA, j0, nb, 0, A + j0 + nb, lda, sA, rest);
+      HS_COUNT_LAUNCH();
+      gemm<E, E, E>(s, OP_N, OP_N, rest, rest, nb, -el<E>::one(), A + (long long)(j0 + nb) * lda + j0, lda, sA,
+                    A + (long long)j0 * lda + j0 + nb, lda, sA, el<E>::one(),
+                    A + (long long)(j0 + nb) * lda + j0 + nb, lda, sA, batch);
+    }
+  }
+}
+
+template <typename E>
+void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int n, const int* piv, long long sP, E* B,
+              int ldb, long long sB, int nrhs, int batch) {
+  dim3 gs((nrhs + 127) / 128, batch);
+  const E m1 = -el<E>::one(), one = el<E>::one();
+  if (trans == OP_N) {
+    k_swaps<E><<<gs, 128, 0, s>>>(piv, sP, n, 0, B, ldb, sB, nrhs);
+    HS_COUNT_LAUNCH();
+    for (int i0 = 0; i0 < n; i0 += NB) {  // L y = b
+      int nb = n - i0 < NB ? n - i0 : NB;
+      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 0, B, ldb, sB, nrhs);
+      HS_COUNT_LAUNCH();
+      int rest = n - i0 - nb;
+      if (rest > 0)
+        gemm<E, E, E>(s, OP_N, OP_N, rest, nrhs, nb, m1, A + (long long)(i0 + nb) * lda + i0, lda, sA,
+                      B + (long long)i0 * ldb, ldb, sB, one, B + (long long)(i0 + nb) * ldb, ldb, sB, batch);
+    }
+    int last = ((n - 1) / NB) * NB;
+    for (int i0 = last; i0 >= 0; i0 -= NB) {  // U x = y
+      int nb = n - i0 < NB ? n - i0 : NB;
+      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 1, B, ldb, sB, nrhs);
+      HS_COUNT_LAUNCH();
+      if (i0 > 0)
+        gemm<E, E, E>(s, OP_N, OP_N, i0, nrhs, nb, m1, A + i0, lda, sA, B + (long long)i0 * ldb, ldb, sB, one, B,
+                      ldb, sB, batch);
+    }
+  } else {
+    for (int i0 = 0; i0 < n; i0 += NB) {  // U^T y = b
+      int nb = n - i0 < NB ? n - i0 : NB;
+      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 2, B, ldb, sB, nrhs);
+      HS_COUNT_LAUNCH();
+      int rest = n - i0 - nb;
+      if (rest > 0)
+        gemm<E, E, E>(s, OP_T, OP_N, rest, nrhs, nb, m1, A + (long long)i0 * lda + i0 + nb, lda, sA,
+                      B + (long long)i0 * ldb, ldb, sB, one, B + (long long)(i0 + nb) * ldb, ldb, sB, batch);
+    }
+    int last = ((n - 1) / NB) * NB;
+    for (int i0 = last; i0 >= 0; i0 -= NB) {  // L^T w = y
+      int nb = n - i0 < NB ? n - i0 : NB;
+      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 3, B, ldb, sB, nrhs);
+      HS_COUNT_LAUNCH();
+      if (i0 > 0)
+        gemm<E, E, E>(s, OP_T, OP_N, i0, nrhs, nb, m1, A + (long long)i0 * lda, lda, sA, B + (long long)i0 * ldb, ldb,
+                      sB, one, B, ldb, sB, batch);
+    }
+    k_swaps<E><<<gs, 128, 0, s>>>(piv, sP, n, 1, B, ldb, sB, nrhs);
+    HS_COUNT_LAUNCH();
+  }
+}
+
+// explicit instantiations
+template void gemm<double, double, double>(cudaStream_t, int, int, int, int, int, double, const double*, int,
+                                           long long, const double*, int, long long, double, double*, int, long long,
+                                           int);
+template void gemm<double2, double2, double2>(cudaStream_t, int, int, int, int, int, double2, const double2*, int,
+                                              long long, const double2*, int, long long, double2, double2*, int,
+                                              long long, int);
+template void gemm<double, double2, double2>(cudaStream_t, int, int, int, int, int, double2, const double*, int,
+                                             long long, const double2*, int, long long, double2, double2*, int,
+                                             long long, int);
+template void gemm<double2, double, double2>(cudaStream_t, int, int, int, int, int, double2, const double2*, int,
+                                             long long, const double*, int, long long, double2, double2*, int,
+                                             long long, int);
+template void lu_factor<double>(cudaStream_t, double*, int, long long, int, int*, long long, int*, int);
+template void lu_factor<double2>(cudaStream_t, double2*, int, long long, int, int*, long long, int*, int);
+template void lu_solve<double>(cudaStream_t, int, const double*, int, long long, int, const int*, long long, double*,
+                               int, long long, int, int);
+template void lu_solve<double2>(cudaStream_t, int, const double2*, int, long long, int, const int*, long long,
+                                double2*, int, long long, int, int);
+
+}  // namespace hs

@@ -1,0 +1,36 @@
+// Batched dense linear algebra on the GPU (row-major, FP64 real or complex).
+//
+// These are the dense building blocks of the direct solver of Sec. 2: the leaf
+// factorisations, the interface systems of the merges and the exterior
+// coupling system are LU factorisations with partial pivoting; every other
+// step is a (batched) matrix product.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace hs {
+
+enum { OP_N = 0, OP_T = 1 };
+
+// C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] for b < batch, row-major,
+// op = identity or plain transpose (no conjugation).  beta == 0 never reads C.
+template <typename TA, typename TB, typename TC>
+void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const TA* A, int lda,
+          long long sA, const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC,
+          int batch);
+
+// In-place LU with partial pivoting P A = L U of a batch of n x n matrices.
+// piv[j] (0-based) is the row swapped with row j at step j.  info[b] is set to
+// j+1 at the first exactly-zero pivot of matrix b (it must be zeroed first).
+template <typename E>
+void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info,
+               int batch);
+
+// Solve A X = B (trans = OP_N) or A^T X = B (trans = OP_T) in place in B
+// (n x nrhs, leading dimension ldb) from the factors of lu_factor.
+template <typename E>
+void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int n, const int* piv,
+              long long sP, E* B, int ldb, long long sB, int nrhs, int batch);
+
+}  // namespace hs

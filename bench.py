@@ -178,7 +178,10 @@ def run_hs(args, world, rank, local):
     torch.cuda.set_device(local)
     w = synth.WORKLOADS[args.workload]
     c = synth.smooth_random_coeffs(w.S, seed=2, qmax=0.3)
-    stream = torch.cuda.current_stream()
+    # A dedicated (non-default) stream: the library launches on it and the CUDA
+    # events below are recorded on it, so they bracket exactly the library's work.
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     solver = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_FP64, device=local, stream=stream.cuda_stream)
     ctx = solver.ctx
     al_np, th_np = synth.directions(w.M), synth.receivers(w.P)

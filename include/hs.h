@@ -89,6 +89,25 @@ int hs_solve(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int
 int hs_solve_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
                  double* ufar, void* stream);
 
+/* Far-field solve that allocates no device memory (the paper has no
+ * counterpart).  For callers that must not allocate at call time: code whose
+ * device memory belongs to another allocator (a framework's caching pool, or
+ * a fixed arena sized at start-up), where an allocation made behind its back
+ * would break its accounting or fail under its memory cap.  Same arguments
+ * and results as hs_solve_dev (device pointers); the factors come from
+ * hs_build on ctx, which must have been called before.
+ * Scratch: one 16 MiB static device array compiled into libhs (every GPU
+ * that loads the library holds it until the process exits).  The call needs
+ * 16 * N_b * (6 M + 2 P) bytes of it, N_b = 56 n_L; larger M, P are rejected
+ * with HS_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (every region is written before it is read, so
+ * nothing needs clearing): calls whose GPU work overlaps -- on different
+ * streams or from different contexts -- race on it; serialise them. */
+int hs_solve_noalloc(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
+                     double* ufar, void* stream);
+
 /* Total fields on the leaf nodes for M plane-wave incidences (device output,
  * M x n_L*n_L*256 complex, node order of hs_node_coords; corner nodes of
  * each leaf are not part of the discretisation and are set to 0). */

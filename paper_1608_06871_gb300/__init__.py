@@ -52,6 +52,7 @@ _SIGS = {
     "hs_solve": (_I, [_P, _D, _I, _D, _I, _D]),
     "hs_solve_dev": (_I, [_P, _P, _I, _P, _I, _P, _P]),
     "hs_fields_dev": (_I, [_P, _P, _I, _P, _P]),
+    "hs_solve_noalloc": (_I, [_P, _P, _I, _P, _I, _P, _P]),
     "hs_jacobian": (_I, [_P, _D, _I, _D, _I, _D]),
     "hs_jacobian_dev": (_I, [_P, _P, _I, _P, _I, _P, _P]),
     "hs_gn_step": (_I, [_P, _D, _D, _I, _D, _I, ctypes.c_double, _D, _D]),
@@ -138,6 +139,14 @@ def _tp(t) -> int:
 def hs_solve_dev(ctx, alphas, thetas, ufar, stream: int | None = None):
     """alphas, thetas: float64 CUDA tensors; ufar: float64 CUDA tensor (M, P, 2)."""
     _check(ctx, lib().hs_solve_dev(ctx, _tp(alphas), alphas.numel(), _tp(thetas), thetas.numel(), _tp(ufar), stream))
+
+
+def hs_solve_noalloc(ctx, alphas, thetas, ufar, stream: int | None = None):
+    """As hs_solve_dev, but the library allocates nothing: its temporaries come from
+    a fixed 16 MiB device array (for callers whose device memory belongs to another
+    allocator).  Needs 16 * 56 n_L * (6 M + 2 P) bytes at most 16 MiB."""
+    _check(ctx, lib().hs_solve_noalloc(ctx, _tp(alphas), alphas.numel(), _tp(thetas), thetas.numel(), _tp(ufar),
+                                       stream))
 
 
 def hs_fields_dev(ctx, alphas, u, stream: int | None = None):

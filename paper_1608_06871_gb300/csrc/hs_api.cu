@@ -653,6 +653,46 @@ size_t gradient_bytes(hs_ctx* ctx, int M, int P) {
 
 }  // namespace
 
+namespace hs {
+
+// CUDA device ordinal the context works on.
+int ctx_device(const hs_ctx* ctx) { return ctx->cfg.device; }
+
+// Bytes of caller-provided scratch a far-field solve of M incidences and P
+// receivers needs (see solve_far_in_scratch).
+size_t far_solve_scratch_bytes(const hs_ctx* ctx, int M, int P) {
+  const size_t nb = (size_t)ctx->B.nb;
+  return 16 * nb * (6 * (size_t)M + 2 * (size_t)P);
+}
+
+// The far-field solve of solve_into with every temporary carved from the
+// caller's scratch (no allocation).  Used by the allocation-free entry point.
+int solve_far_in_scratch(hs_ctx* ctx, void* stream, const double* alphas, int M, const double* thetas, int P,
+                         double* ufar, void* scratch, size_t scratch_bytes) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!alphas || !thetas || !ufar || !scratch) return fail(ctx, HS_EINVAL, "NULL pointer");
+  if (far_solve_scratch_bytes(ctx, M, P) > scratch_bytes)
+    return fail(ctx, HS_EINVAL, "M and P too large for the fixed scratch: need 16*N_b*(6M+2P) = " +
+                                    std::to_string(far_solve_scratch_bytes(ctx, M, P)) + " bytes, have " +
+                                    std::to_string(scratch_bytes));
+  cudaStream_t s = pick(ctx, stream);
+  const size_t nb = (size_t)ctx->B.nb;
+  double2* p = reinterpret_cast<double2*>(scratch);
+  double2 *ui = p, *dni = ui + nb * M, *f = dni + nb * M, *g = f + nb * M;
+  double2 *PS = g + nb * M, *A2 = PS + 2 * nb * M;
+  CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
+  boundary_data(s, (int)nb, M, ctx->k, f, g, ui, dni, PS);
+  farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
+  gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * (int)nb, make_double2(1, 0), PS, M, 0, A2, 2 * (int)nb, 0,
+                                  make_double2(0, 0), reinterpret_cast<double2*>(ufar), P, 0, 1);
+  CK(cudaGetLastError());
+  return HS_OK;
+}
+
+}  // namespace hs
+
 // ============================== C ABI =====================================
 extern "C" {
 

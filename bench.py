@@ -51,15 +51,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hs", choices=["hs", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--prof-family", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-def config_of(w, nranks):
-    return {"workload": w.name, "k": w.k, "leaves": f"{w.n_leaf_side}x{w.n_leaf_side}", "leaf_order": 16,
+def config_of(w, nranks, precision="fp64"):
+    return {"workload": w.name, "precision": precision, "k": w.k, "leaves": f"{w.n_leaf_side}x{w.n_leaf_side}", "leaf_order": 16,
             "sine_modes": f"{w.S}x{w.S}", "incidences_per_gpu": w.M, "receivers": w.P, "R": w.R,
             "contrast": "smooth random sine series, max|q|=0.3, seed 2", "parallelism": f"replicas x{nranks}",
             "l2": "working set > L2 (factors ~1 GB, fields 0.5 GB per step)"}
@@ -159,11 +161,62 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(w, world),
+            "config": config_of(w, world, args.precision),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": oracle_desc()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_arm(hs, torch, w, c, precision, args, world, local, prof_family):
+    """Warm up and time one precision arm of the step; returns its measurements."""
+    stream = torch.cuda.current_stream()
+    solver = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, precision, device=local, stream=stream.cuda_stream)
+    ctx = solver.ctx
+    alphas = torch.tensor(synth.directions(w.M), device="cuda")
+    thetas = torch.tensor(synth.receivers(w.P), device="cuda")
+    ufar = torch.empty((w.M, w.P, 2), dtype=torch.float64, device="cuda")
+    u = torch.empty((w.M, w.n_leaf_side ** 2, 256, 2), dtype=torch.float64, device="cuda")
+
+    def step():
+        hs.hs_build(ctx, c, w.k)
+        hs.hs_forward_dev(ctx, alphas, thetas, ufar, u)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    n0 = solver.launch_count()
+    hs.hs_prof_start(prof_family)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    prof = hs.hs_prof_stop()
+    launches = solver.launch_count() - n0
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    # phase split (one extra, untimed pass)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    hs.hs_build(ctx, c, w.k)
+    ev[1].record(stream)
+    hs.hs_forward_dev(ctx, alphas, thetas, ufar, u)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    phases = {"build_ms": ev[0].elapsed_time(ev[1]), "forward_ms": ev[1].elapsed_time(ev[2])}
+    if precision == hs.HS_MIXED:
+        it, upd = hs.hs_refine_stats(ctx)
+        phases["refine_passes"] = it
+        phases["last_rel_update"] = upd
+    uf = ufar.cpu().numpy()
+    return dict(solver=solver, ctx=ctx, ms=ms, launches=launches, prof=prof, clocks=clk, phases=phases,
+                ufar=uf[..., 0] + 1j * uf[..., 1], u=u, alphas=alphas)
 
 
 def run_hs(args, world, rank, local):
@@ -176,88 +229,46 @@ def run_hs(args, world, rank, local):
     import paper_1608_06871_gb300 as hs
 
     torch.cuda.set_device(local)
-    w = synth.WORKLOADS[args.workload]
-    c = synth.smooth_random_coeffs(w.S, seed=2, qmax=0.3)
     # A dedicated (non-default) stream: the library launches on it and the CUDA
-    # events below are recorded on it, so they bracket exactly the library's work.
+    # events are recorded on it, so they bracket exactly the library's work.
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    solver = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_FP64, device=local, stream=stream.cuda_stream)
-    ctx = solver.ctx
-    al_np, th_np = synth.directions(w.M), synth.receivers(w.P)
-    alphas = torch.tensor(al_np, device="cuda")
-    thetas = torch.tensor(th_np, device="cuda")
-    ufar = torch.empty((w.M, w.P, 2), dtype=torch.float64, device="cuda")
-    u = torch.empty((w.M, w.n_leaf_side ** 2, 256, 2), dtype=torch.float64, device="cuda")
-
-    def step():
-        hs.hs_build(ctx, c, w.k)
-        hs.hs_fields_dev(ctx, alphas, u)
-        hs.hs_solve_dev(ctx, alphas, thetas, ufar)
-
+    w = synth.WORKLOADS[args.workload]
+    c = synth.smooth_random_coeffs(w.S, seed=2, qmax=0.3)
     peak = hs.hs_peak_fp64(local, 300.0)
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
+    prec = hs.HS_MIXED if args.precision == "mixed" else hs.HS_FP64
+    fam = hs.HS_PROF_GEMM_FP64 if args.prof_family == "fp64" else hs.HS_PROF_GEMM_FP32
+    main = time_arm(hs, torch, w, c, prec, args, world, local, fam)
+    other = None
+    if prec == hs.HS_MIXED and not args.no_fp64_arm:
+        other = time_arm(hs, torch, w, c, hs.HS_FP64, args, world, local, hs.HS_PROF_GEMM_FP64)
+        other["solver"].close()
+    value = world * w.M / (main["ms"] * 1e-3)
 
-    # ---- timed region (device-resident inputs) -------------------------------------
-    clocks = Clocks(local)
-    barrier(world)
-    torch.cuda.synchronize()
-    n0 = solver.launch_count()
-    hs.hs_prof_start(hs.HS_PROF_GEMM_FP64)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    gemm_ms, gemm_flops, gemm_n = hs.hs_prof_stop()
-    launches = solver.launch_count() - n0
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    ms = max_over_ranks(ms, world)
-    value = world * w.M / (ms * 1e-3)
-
-    # ---- phase split (one extra, untimed pass) ------------------------------------
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record(stream)
-    hs.hs_build(ctx, c, w.k)
-    ev[1].record(stream)
-    hs.hs_fields_dev(ctx, alphas, u)
-    ev[2].record(stream)
-    hs.hs_solve_dev(ctx, alphas, thetas, ufar)
-    ev[3].record(stream)
-    torch.cuda.synchronize()
-    phases = {"build_ms": ev[0].elapsed_time(ev[1]), "fields_ms": ev[1].elapsed_time(ev[2]),
-              "farfield_ms": ev[2].elapsed_time(ev[3])}
-
-    # ---- e2e through the host-buffer C-ABI (copies inside the timed region) ---------
+    # e2e: the same step through the C ABI with host buffers (pinned), copies inside the timed region
+    ctx = main["ctx"]
     c_pin = torch.tensor(c, dtype=torch.float64).pin_memory()
-    al_pin = torch.tensor(al_np).pin_memory()
-    th_pin = torch.tensor(th_np).pin_memory()
+    al_pin = torch.tensor(synth.directions(w.M)).pin_memory()
+    th_pin = torch.tensor(synth.receivers(w.P)).pin_memory()
     out_pin = torch.empty((w.M, w.P, 2), dtype=torch.float64).pin_memory()
-    c_np, al_h, th_h, out_np = c_pin.numpy(), al_pin.numpy(), th_pin.numpy(), out_pin.numpy()
+    c_np = c_pin.numpy()
+    ufar_d = torch.empty((w.M, w.P, 2), dtype=torch.float64, device="cuda")
 
     def step_e2e():
         hs.hs_build(ctx, c_np, w.k)
         a_dev = al_pin.to("cuda", non_blocking=True)
-        hs.hs_fields_dev(ctx, a_dev, u)
-        res = hs.hs_solve(ctx, al_h, th_h)
-        out_np[..., 0] = res.real
-        out_np[..., 1] = res.imag
+        t_dev = th_pin.to("cuda", non_blocking=True)
+        hs.hs_forward_dev(ctx, a_dev, t_dev, ufar_d, main["u"])
+        out_pin.copy_(ufar_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
 
     step_e2e()
-    torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         step_e2e()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    e2e_s = max_over_ranks(e2e_s, world)
-    h2d = 8 * (w.S * w.S + 2 * w.M + w.P)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
+    h2d = 8 * (w.S * w.S + w.M + w.P)
     d2h = 16 * w.M * w.P
 
     cpu = None
@@ -267,24 +278,38 @@ def run_hs(args, world, rank, local):
                "seconds": dt}
 
     if rank == 0:
+        gemm_ms, gemm_flops, gemm_n = main["prof"]
         achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+        fp64_fam = args.prof_family == "fp64"
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w, world),
+                "warmup": max(args.warmup, 3), "ms_per_step": main["ms"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "c64 factors + f64 refinement" if prec == hs.HS_MIXED else "f64", "data": "synthetic",
+                "config": config_of(w, world, args.precision),
                 "e2e": {"value": world * w.M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches,
-                "roofline": {"bound": "alu", "kernel": "k_gemm (batched FP64 complex/real GEMM)",
-                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": (achieved / peak) if achieved and peak else None,
+                "gpu_launches": main["launches"],
+                "roofline": {"bound": "alu" if fp64_fam else "alu",
+                             "kernel": "k_gemm<FP64> (batched FP64 GEMM family)" if fp64_fam
+                             else "k_gemm<FP32> (batched FP32 GEMM family)",
+                             "achieved": achieved, "peak": peak if fp64_fam else None, "unit": "TFLOP/s",
+                             "frac": (achieved / peak) if (achieved and peak and fp64_fam) else None,
                              "peak_source": "measured FP64 DFMA rate (hs_peak_fp64, this run)",
                              "traffic": None, "launches": gemm_n, "kernel_ms_per_step": gemm_ms / args.steps,
                              "algorithmic_tflop_per_step": gemm_flops / args.steps / 1e12},
-                "phases": phases, "clocks": clk}
+                "phases": main["phases"], "clocks": main["clocks"]}
+        if other is not None:
+            err = float(np.linalg.norm(main["ufar"] - other["ufar"]) / np.linalg.norm(other["ufar"]))
+            line["fp64_arm"] = {"value": world * w.M / (other["ms"] * 1e-3), "ms_per_step": other["ms"],
+                                "phases": other["phases"], "gpu_launches": other["launches"],
+                                "gemm_fp64_tflops": (other["prof"][1] / (other["prof"][0] * 1e-3) / 1e12)
+                                if other["prof"][0] > 0 else None}
+            line["mixed_vs_fp64_farfield_rel_err"] = err
+            line["mixed_speedup_vs_fp64"] = other["ms"] / main["ms"]
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    solver.close()
+    main["solver"].close()
 
 
 def main():

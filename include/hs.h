@@ -108,6 +108,14 @@ int hs_solve_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas,
 int hs_solve_noalloc(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
                      double* ufar, void* stream);
 
+/* Full forward solve (Sec. 2: one right-hand side per incidence, pushed down
+ * the tree to every leaf node; Sec. 1 eq. farfielddef for the data): the far
+ * field ufar (M x P complex, as hs_solve) and the total field u on every leaf
+ * node (M x n_L*n_L*256 complex, node order of hs_node_coords, corners 0), both
+ * device pointers.  With HS_MIXED one refinement run yields both. */
+int hs_forward_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* ufar,
+                   double* u, void* stream);
+
 /* Total fields on the leaf nodes for M plane-wave incidences (device output,
  * M x n_L*n_L*256 complex, node order of hs_node_coords; corner nodes of
  * each leaf are not part of the discretisation and are set to 0). */

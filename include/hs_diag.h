@@ -9,12 +9,15 @@
 #ifndef HS_DIAG_H
 #define HS_DIAG_H
 
+#include "hs.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
 
 /* Kernel families that can be timed. */
 #define HS_PROF_GEMM_FP64 1 /* the batched FP64 real/complex GEMM kernel */
+#define HS_PROF_GEMM_FP32 2 /* the same GEMM kernel in FP32 (mixed-precision path) */
 
 /* Start recording a CUDA event pair around every launch of the given family
  * (on the stream the launch uses) and counting its algorithmic flops
@@ -32,6 +35,10 @@ int hs_prof_stop(double* total_ms, double* total_flops, long long* launches);
  * register-resident kernel of independent DFMA chains on every SM; returns
  * TFLOP/s (2 flops per DFMA) in *tflops.  Runs for about `ms` milliseconds. */
 int hs_peak_fp64(int device, double ms, double* tflops);
+
+/* Refinement passes and the last relative change of the far field in the
+ * most recent HS_MIXED solve on ctx (0 and -1 before any). */
+int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update);
 
 #ifdef __cplusplus
 }

@@ -52,6 +52,7 @@ _SIGS = {
     "hs_solve": (_I, [_P, _D, _I, _D, _I, _D]),
     "hs_solve_dev": (_I, [_P, _P, _I, _P, _I, _P, _P]),
     "hs_fields_dev": (_I, [_P, _P, _I, _P, _P]),
+    "hs_forward_dev": (_I, [_P, _P, _I, _P, _I, _P, _P, _P]),
     "hs_solve_noalloc": (_I, [_P, _P, _I, _P, _I, _P, _P]),
     "hs_jacobian": (_I, [_P, _D, _I, _D, _I, _D]),
     "hs_jacobian_dev": (_I, [_P, _P, _I, _P, _I, _P, _P]),
@@ -65,6 +66,7 @@ _SIGS = {
     "hs_prof_stop": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_longlong)]),
     "hs_peak_fp64": (_I, [_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -149,6 +151,12 @@ def hs_solve_noalloc(ctx, alphas, thetas, ufar, stream: int | None = None):
                                        stream))
 
 
+def hs_forward_dev(ctx, alphas, thetas, ufar, u, stream: int | None = None):
+    """Far field (M, P, 2) and total fields on every leaf node (M, n_L^2, 256, 2), float64 CUDA tensors."""
+    _check(ctx, lib().hs_forward_dev(ctx, _tp(alphas), alphas.numel(), _tp(thetas), thetas.numel(), _tp(ufar),
+                                     _tp(u), stream))
+
+
 def hs_fields_dev(ctx, alphas, u, stream: int | None = None):
     """u: float64 CUDA tensor (M, n_L^2, 256, 2): total fields on the leaf nodes."""
     _check(ctx, lib().hs_fields_dev(ctx, _tp(alphas), alphas.numel(), _tp(u), stream))
@@ -210,6 +218,7 @@ def hs_destroy(ctx):
 
 # ---- measurement hooks (include/hs_diag.h) --------------------------------------
 HS_PROF_GEMM_FP64 = 1
+HS_PROF_GEMM_FP32 = 2
 
 
 def hs_prof_start(family: int = HS_PROF_GEMM_FP64):
@@ -221,6 +230,13 @@ def hs_prof_stop():
     ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
     _check(None, lib().hs_prof_stop(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
     return ms.value, fl.value, n.value
+
+
+def hs_refine_stats(ctx):
+    """(refinement passes, last relative far-field change) of the last HS_MIXED solve."""
+    it, up = ctypes.c_int(), ctypes.c_double()
+    _check(ctx, lib().hs_refine_stats(ctx, ctypes.byref(it), ctypes.byref(up)))
+    return it.value, up.value
 
 
 def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:

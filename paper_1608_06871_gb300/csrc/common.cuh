@@ -32,6 +32,25 @@ __host__ __device__ inline double2 divz(double2 a, double2 b) {
   }
 }
 
+// complex float (FP32 factors of the mixed-precision path)
+__host__ __device__ inline float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 operator-(float2 a) { return make_float2(-a.x, -a.y); }
+__host__ __device__ inline float2 operator*(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ inline float abs2z(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ inline float2 divz(float2 a, float2 b) {
+  if (fabsf(b.x) >= fabsf(b.y)) {
+    float r = b.y / b.x, d = b.x + b.y * r;
+    return make_float2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    float r = b.x / b.y, d = b.y + b.x * r;
+    return make_float2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+
 // Generic element traits so that the linear algebra can be templated on
 // real or complex element types.
 template <typename E> struct el;
@@ -47,6 +66,28 @@ template <> struct el<double2> {
   __host__ __device__ static double mag2(double2 a) { return abs2z(a); }
   __host__ __device__ static double2 div(double2 a, double2 b) { return divz(a, b); }
 };
+template <> struct el<float> {
+  __host__ __device__ static float zero() { return 0.0f; }
+  __host__ __device__ static float one() { return 1.0f; }
+  __host__ __device__ static double mag2(float a) { return (double)a * a; }
+  __host__ __device__ static float div(float a, float b) { return a / b; }
+};
+template <> struct el<float2> {
+  __host__ __device__ static float2 zero() { return make_float2(0.0f, 0.0f); }
+  __host__ __device__ static float2 one() { return make_float2(1.0f, 0.0f); }
+  __host__ __device__ static double mag2(float2 a) { return (double)abs2z(a); }
+  __host__ __device__ static float2 div(float2 a, float2 b) { return divz(a, b); }
+};
+
+// Real and complex types of one precision.
+template <typename T> struct prec;
+template <> struct prec<double> { using R = double; using C = double2; };
+template <> struct prec<float> { using R = float; using C = float2; };
+__host__ __device__ inline double2 to_c(double2 a, double2*) { return a; }
+__host__ __device__ inline float2 to_c(double2 a, float2*) { return make_float2((float)a.x, (float)a.y); }
+__host__ __device__ inline double2 to_c(float2 a, double2*) { return make_double2(a.x, a.y); }
+__host__ __device__ inline float2 to_c(float2 a, float2*) { return a; }
+template <typename C, typename S> __host__ __device__ inline C cvt(S a) { return to_c(a, (C*)nullptr); }
 
 // Mixed-type multiply-accumulate used by the GEMM templates.
 __host__ __device__ inline double mul(double a, double b) { return a * b; }
@@ -60,6 +101,16 @@ __host__ __device__ inline double2 addv(double2 a, double2 b) { return a + b; }
 template <typename TC, typename S> __host__ __device__ inline TC scal(S s, TC v);
 template <> __host__ __device__ inline double scal<double, double>(double s, double v) { return s * v; }
 template <> __host__ __device__ inline double2 scal<double2, double2>(double2 s, double2 v) { return s * v; }
+__host__ __device__ inline float mul(float a, float b) { return a * b; }
+__host__ __device__ inline float2 mul(float a, float2 b) { return make_float2(a * b.x, a * b.y); }
+__host__ __device__ inline float2 mul(float2 a, float b) { return make_float2(a.x * b, a.y * b); }
+__host__ __device__ inline float2 mul(float2 a, float2 b) { return a * b; }
+__host__ __device__ inline bool is_zero(float a) { return a == 0.0f; }
+__host__ __device__ inline bool is_zero(float2 a) { return a.x == 0.0f && a.y == 0.0f; }
+__host__ __device__ inline float addv(float a, float b) { return a + b; }
+__host__ __device__ inline float2 addv(float2 a, float2 b) { return a + b; }
+template <> __host__ __device__ inline float scal<float, float>(float s, float v) { return s * v; }
+template <> __host__ __device__ inline float2 scal<float2, float2>(float2 s, float2 v) { return s * v; }
 
 }  // namespace hs
 

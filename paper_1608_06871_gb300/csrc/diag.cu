@@ -54,7 +54,7 @@ __global__ void k_dfma_peak(double* out, int iters, double a, double b) {
 extern "C" {
 
 int hs_prof_start(int family) {
-  if (family != HS_PROF_GEMM_FP64) return HS_EINVAL;
+  if (family != HS_PROF_GEMM_FP64 && family != HS_PROF_GEMM_FP32) return HS_EINVAL;
   hs::g_prof.clear();
   hs::g_prof_family = family;
   return HS_OK;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/hs.h"
+#include "../../include/hs_diag.h"
 #include "tree.cuh"
 
 namespace hs {
@@ -131,6 +132,16 @@ struct hs_ctx {
   double2 *d_S = nullptr, *d_Dm = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_C = nullptr;
   int* d_Cpiv = nullptr;
   const double2* Rroot = nullptr;
+  double* d_D1 = nullptr;  // Chebyshev-Lobatto differentiation matrix (device copy)
+  // mixed precision: FP32 factors (kept leaf scratch: LU(Aii), X, Ni, Kinv), FP64 refinement
+  LeafScratchT<float> ws32{};
+  float2 *d_R32 = nullptr, *d_Y32 = nullptr;
+  std::vector<LevelOps<float2>> ops32;
+  float2 *d_B2_32 = nullptr, *d_C32 = nullptr;
+  int* d_Cpiv32 = nullptr;
+  const float2* Rroot32 = nullptr;
+  int refine_iters = 0;
+  double refine_update = 0.0;
   // per-call workspace
   char* ws_base = nullptr;
   size_t ws_cap = 0;
@@ -257,13 +268,26 @@ int setup_tree(hs_ctx* ctx) {
     CK(cudaMemcpy(L.d_I3a, I3a.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(L.d_I3b, I3b.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
     const size_t nb = L.nbox;
-    CKR(dalloc(ctx, &L.XZ, nb * 2 * L.ni * L.np));
-    CKR(dalloc(ctx, &L.U2, nb * 2 * L.ni * L.np));
-    CKR(dalloc(ctx, &L.A33, nb * L.ni * L.ni));
-    CKR(dalloc(ctx, &L.B33, nb * L.ni * L.ni));
-    CKR(dalloc(ctx, &L.M, nb * L.ni * L.ni));
-    CKR(dalloc(ctx, &L.Mpiv, nb * L.ni));
-    CKR(dalloc(ctx, &L.R, nb * (size_t)L.np * L.np));
+    L.nbx_p = nbx_p;
+    if (ctx->cfg.precision == HS_FP64) {
+      CKR(dalloc(ctx, &L.XZ, nb * 2 * L.ni * L.np));
+      CKR(dalloc(ctx, &L.U2, nb * 2 * L.ni * L.np));
+      CKR(dalloc(ctx, &L.A33, nb * L.ni * L.ni));
+      CKR(dalloc(ctx, &L.B33, nb * L.ni * L.ni));
+      CKR(dalloc(ctx, &L.M, nb * L.ni * L.ni));
+      CKR(dalloc(ctx, &L.Mpiv, nb * L.ni));
+      CKR(dalloc(ctx, &L.R, nb * (size_t)L.np * L.np));
+    } else {
+      LevelOps<float2> O{};
+      CKR(dalloc(ctx, &O.XZ, nb * 2 * L.ni * L.np));
+      CKR(dalloc(ctx, &O.U2, nb * 2 * L.ni * L.np));
+      CKR(dalloc(ctx, &O.A33, nb * L.ni * L.ni));
+      CKR(dalloc(ctx, &O.B33, nb * L.ni * L.ni));
+      CKR(dalloc(ctx, &O.M, nb * L.ni * L.ni));
+      CKR(dalloc(ctx, &O.Mpiv, nb * L.ni));
+      CKR(dalloc(ctx, &O.R, nb * (size_t)L.np * L.np));
+      ctx->ops32.push_back(O);
+    }
     ctx->levels.push_back(L);
     sx = psx;
     sy = psy;
@@ -366,8 +390,16 @@ int setup_boundary(hs_ctx* ctx) {
   CKR(dalloc(ctx, &ctx->d_Dm, nn));
   CKR(dalloc(ctx, &ctx->d_B1, nn));
   CKR(dalloc(ctx, &ctx->d_B2, nn));
-  CKR(dalloc(ctx, &ctx->d_C, nn));
-  CKR(dalloc(ctx, &ctx->d_Cpiv, nb));
+  if (ctx->cfg.precision == HS_FP64) {
+    CKR(dalloc(ctx, &ctx->d_C, nn));
+    CKR(dalloc(ctx, &ctx->d_Cpiv, nb));
+  } else {
+    CKR(dalloc(ctx, &ctx->d_B2_32, nn));
+    CKR(dalloc(ctx, &ctx->d_C32, nn));
+    CKR(dalloc(ctx, &ctx->d_Cpiv32, nb));
+  }
+  CKR(dalloc(ctx, &ctx->d_D1, 256));
+  CK(cudaMemcpy(ctx->d_D1, D1.data(), sizeof(double) * 256, cudaMemcpyHostToDevice));
   return HS_OK;
 }
 
@@ -402,28 +434,76 @@ int setup(hs_ctx* ctx) {
   ctx->ninfo = std::max(ctx->nleaf, 16) + 1;
   CKR(dalloc(ctx, &ctx->d_info, ctx->ninfo));
   // leaf factors and scratch
-  const size_t nl = ctx->nleaf, ch = ctx->chunk;
-  CKR(dalloc(ctx, &ctx->d_Rleaf, nl * NE * NE));
-  CKR(dalloc(ctx, &ctx->d_Y, nl * NL * NE));
-  CKR(dalloc(ctx, &ctx->d_Q, nl * NI * NE));
-  LeafScratch& w = ctx->ws;
-  CKR(dalloc(ctx, &w.Aii, ch * NI * NI));
-  CKR(dalloc(ctx, &w.Aie, ch * NI * NE));
-  CKR(dalloc(ctx, &w.Ni, ch * NE * NI));
-  CKR(dalloc(ctx, &w.NiT, ch * NI * NE));
-  CKR(dalloc(ctx, &w.Ne, ch * NE * NE));
-  CKR(dalloc(ctx, &w.K, ch * NE * NE));
-  CKR(dalloc(ctx, &w.Kinv, ch * NE * NE));
-  CKR(dalloc(ctx, &w.piv, ch * NI));
-  CKR(dalloc(ctx, &w.pivK, ch * NE));
+  const size_t nl = ctx->nleaf;
+  if (ctx->cfg.precision == HS_FP64) {
+    const size_t ch = ctx->chunk;
+    CKR(dalloc(ctx, &ctx->d_Rleaf, nl * NE * NE));
+    CKR(dalloc(ctx, &ctx->d_Y, nl * NL * NE));
+    CKR(dalloc(ctx, &ctx->d_Q, nl * NI * NE));
+    LeafScratch& w = ctx->ws;
+    CKR(dalloc(ctx, &w.Aii, ch * NI * NI));
+    CKR(dalloc(ctx, &w.Aie, ch * NI * NE));
+    CKR(dalloc(ctx, &w.Ni, ch * NE * NI));
+    CKR(dalloc(ctx, &w.NiT, ch * NI * NE));
+    CKR(dalloc(ctx, &w.Ne, ch * NE * NE));
+    CKR(dalloc(ctx, &w.K, ch * NE * NE));
+    CKR(dalloc(ctx, &w.Kinv, ch * NE * NE));
+    CKR(dalloc(ctx, &w.piv, ch * NI));
+    CKR(dalloc(ctx, &w.pivK, ch * NE));
+  } else {
+    // every leaf's factors are kept: the refinement's particular solves reuse them
+    CKR(dalloc(ctx, &ctx->d_R32, nl * NE * NE));
+    CKR(dalloc(ctx, &ctx->d_Y32, nl * NL * NE));
+    LeafScratchT<float>& w = ctx->ws32;
+    CKR(dalloc(ctx, &w.Aii, nl * NI * NI));
+    CKR(dalloc(ctx, &w.Aie, nl * NI * NE));
+    CKR(dalloc(ctx, &w.Ni, nl * NE * NI));
+    CKR(dalloc(ctx, &w.NiT, nl * NI * NE));
+    CKR(dalloc(ctx, &w.Ne, nl * NE * NE));
+    CKR(dalloc(ctx, &w.K, nl * NE * NE));
+    CKR(dalloc(ctx, &w.Kinv, nl * NE * NE));
+    CKR(dalloc(ctx, &w.piv, nl * NI));
+    CKR(dalloc(ctx, &w.pivK, nl * NE));
+  }
   CKR(setup_tree(ctx));
   CKR(setup_boundary(ctx));
   CK(cudaStreamSynchronize(ctx->stream));
   return HS_OK;
 }
 
+// FP32 factors of the mixed-precision path: leaves, merges and the coupled
+// root system in complex FP32; the layer-potential matrices stay in FP64 for
+// the refinement residual.
+int factor_mixed(hs_ctx* ctx, double k) {
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32, nullptr,
+                          ctx->d_info);
+  const float2* Rc = ctx->d_R32;
+  for (size_t li = 0; li < ctx->levels.size(); ++li) {
+    merge_level<float2>(s, ctx->levels[li], ctx->ops32[li], Rc, ctx->d_info);
+    Rc = ctx->ops32[li].R;
+  }
+  ctx->Rroot32 = Rc;
+  const int nb = ctx->B.nb;
+  const long long nn = (long long)nb * nb;
+  bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
+  bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
+  convert_d2f(s, ctx->d_B1, ctx->d_C32, nn);
+  convert_d2f(s, ctx->d_B2, ctx->d_B2_32, nn);
+  gemm<float2, float2, float2>(s, OP_N, OP_N, nb, nb, nb, make_float2(-1.f, 0.f), ctx->d_B2_32, nb, 0, ctx->Rroot32,
+                               nb, 0, make_float2(1.f, 0.f), ctx->d_C32, nb, 0, 1);
+  lu_factor<float2>(s, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, ctx->d_info, 1);
+  CK(cudaGetLastError());
+  CKR(check_info(ctx));
+  ctx->k = k;
+  ctx->built = true;
+  return HS_OK;
+}
+
 // Factor the operator for the q currently in d_q (Sec. 2).
 int factor(hs_ctx* ctx, double k) {
+  if (ctx->cfg.precision == HS_MIXED) return factor_mixed(ctx, k);
   cudaStream_t s = ctx->stream;
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
   for (int l0 = 0; l0 < ctx->nleaf; l0 += ctx->chunk) {
@@ -527,9 +607,17 @@ int check_ctx(hs_ctx* ctx, bool need_built) {
 cudaStream_t pick(hs_ctx* ctx, void* stream) { return stream ? (cudaStream_t)stream : ctx->stream; }
 
 // Far field for M incidences into ufar (device, M x P complex).
+int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* ufar,
+                double2* Xout, Arena& a);
+size_t mixed_bytes(hs_ctx* ctx, int M, int P);
+
 int solve_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* ufar) {
   const int nb = ctx->B.nb;
   Arena a;
+  if (ctx->cfg.precision == HS_MIXED) {
+    CKR(ensure_ws(ctx, mixed_bytes(ctx, M, P), a));
+    return mixed_solve(ctx, s, alphas, M, thetas, P, ufar, nullptr, a);
+  }
   size_t need = 4 * Arena::bytes((size_t)nb * M, 16) + Arena::bytes((size_t)2 * nb * M, 16) +
                 Arena::bytes((size_t)P * 2 * nb, 16);
   CKR(ensure_ws(ctx, need, a));
@@ -543,6 +631,122 @@ int solve_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const d
   gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
                                   make_double2(0, 0), ufar, P, 0, 1);
   CK(cudaGetLastError());
+  return HS_OK;
+}
+
+size_t s3_elems(hs_ctx* ctx, int nrhs) {
+  size_t m = 1;
+  for (auto& L : ctx->levels) m = std::max(m, (size_t)L.nbox * 2 * L.ni);
+  return m * nrhs;
+}
+
+size_t mixed_bytes(hs_ctx* ctx, int M, int P) {
+  const size_t nb = ctx->B.nb, nl = ctx->nleaf;
+  size_t b = 6 * Arena::bytes(nb * M, 16) + Arena::bytes(2 * nb * M, 16) + Arena::bytes((size_t)P * 2 * nb, 16) +
+             2 * Arena::bytes((size_t)M * P, 16) + Arena::bytes(8, 8) + Arena::bytes(nl * NL * M, 16);
+  b += Arena::bytes(nl * NL * M, 8) + 2 * Arena::bytes(field_buf_elems(ctx, M), 8) + Arena::bytes(nl * NE * M, 8) +
+       Arena::bytes(s3_elems(ctx, M), 8) + 2 * Arena::bytes(nb * M, 8);
+  for (auto& L : ctx->levels) b += Arena::bytes((size_t)L.nbox * 2 * L.ni * M, 8);
+  return b;
+}
+
+// Mixed-precision forward solve: FP32 direct solves as the inner solver of
+// FP64 iterative refinement on the residual of the whole discrete system
+// (leaf PDE rows, interface continuity rows, exterior rows).  The first pass
+// is the plain FP32 solve; every later pass solves for the correction with
+// body loads (the PDE residual), interface right-hand sides (continuity
+// residual) and the exterior residual.  Stops when the far field changes by
+// less than tol relative, or fails with HS_ENOCONV after max_iter passes.
+// ufar (M x P) and/or X (FP64 leaf fields, [leaf][252][M]) may be NULL.
+int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* ufar,
+                double2* Xout, Arena& a) {
+  const int nb = ctx->B.nb, nl = ctx->nleaf, nlev = (int)ctx->levels.size();
+  const size_t nbM = (size_t)nb * M, nX = (size_t)nl * NL * M;
+  const double eta = ctx->k;
+  const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-11;
+  const int max_iter = ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
+  const double2 one = make_double2(1, 0), mone = make_double2(-1, 0), zero = make_double2(0, 0);
+  const float2 fone = make_float2(1.f, 0.f), fzero = make_float2(0.f, 0.f);
+  double2 *ui = a.get<double2>(nbM), *dni = a.get<double2>(nbM), *rinc = a.get<double2>(nbM);
+  double2 *ub = a.get<double2>(nbM), *psib = a.get<double2>(nbM), *rext = a.get<double2>(nbM);
+  double2* PS = a.get<double2>(2 * nbM);
+  double2* A2 = a.get<double2>((size_t)P * 2 * nb);
+  double2 *uf = a.get<double2>((size_t)M * P), *ufp = a.get<double2>((size_t)M * P);
+  double* nrm = a.get<double>(8);
+  double2* X = a.get<double2>(nX);
+  float2* Up = a.get<float2>(nX);
+  float2 *B0 = a.get<float2>(field_buf_elems(ctx, M)), *B1 = a.get<float2>(field_buf_elems(ctx, M));
+  float2* tmp = a.get<float2>((size_t)nl * NE * M);
+  float2* S3 = a.get<float2>(s3_elems(ctx, M));
+  float2 *f32 = a.get<float2>(nbM), *r32 = a.get<float2>(nbM);
+  std::vector<float2*> TT(nlev);
+  for (int li = 0; li < nlev; ++li) TT[li] = a.get<float2>((size_t)ctx->levels[li].nbox * 2 * ctx->levels[li].ni * M);
+
+  incident_plane(s, ctx->B, ctx->k, alphas, M, ui, dni);
+  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, one, ctx->d_Dm, nb, 0, ui, M, 0, zero, rinc, M, 0, 1);
+  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, mone, ctx->d_S, nb, 0, dni, M, 0, one, rinc, M, 0, 1);
+  farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
+  CK(cudaMemsetAsync(X, 0, sizeof(double2) * nX, s));
+  ctx->refine_iters = 0;
+  ctx->refine_update = -1.0;
+  bool converged = false;
+  for (int it = 0; it < max_iter; ++it) {
+    if (it == 0) {
+      convert_d2f(s, rinc, f32, (long long)nbM);
+    } else {
+      // FP64 residual of every row for the current iterate X
+      residual_pde(s, X, ctx->d_q, ctx->d_D1, nl, ctx->k, ctx->h, M, Up);
+      boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
+      CK(cudaMemcpyAsync(rext, rinc, sizeof(double2) * nbM, cudaMemcpyDeviceToDevice, s));
+      gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, mone, ctx->d_Dm, nb, 0, ub, M, 0, one, rext, M, 0, 1);
+      gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, one, ctx->d_S, nb, 0, psib, M, 0, one, rext, M, 0, 1);
+      convert_d2f(s, rext, r32, (long long)nbM);
+      // FP32 correction: particular leaf solutions, upward pass, root
+      leaf_particular(s, ctx->ws32, nl, eta, M, Up, B0, tmp);
+      float2 *Hc = B0, *Hp = B1;
+      for (int li = 0; li < nlev; ++li) {
+        residual_iface(s, ctx->levels[li], X, ctx->d_D1, ctx->nL, ctx->h, eta, M, S3);
+        sweep_up_level<float2>(s, ctx->levels[li], ctx->ops32[li], Hc, S3, TT[li], Hp, M);
+        std::swap(Hc, Hp);
+      }
+      CK(cudaMemcpyAsync(f32, r32, sizeof(float2) * nbM, cudaMemcpyDeviceToDevice, s));
+      gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_B2_32, nb, 0, Hc, M, 0, fone, f32, M, 0, 1);
+    }
+    lu_solve<float2>(s, OP_N, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, f32, M, 0, M, 1);
+    // downward sweep (adds the particular interface impedances after the first pass)
+    const float2* Fp = f32;
+    float2* out = B0;
+    for (int li = nlev - 1; li >= 0; --li) {
+      sweep_down_level<float2>(s, ctx->levels[li], ctx->ops32[li], Fp, TT[li], out, M, it > 0);
+      Fp = out;
+      out = (out == B0) ? B1 : B0;
+    }
+    gemm<float2, float2, float2>(s, OP_N, OP_N, NL, M, NE, fone, ctx->d_Y32, NE, (long long)NL * NE, Fp, M,
+                                 (long long)NE * M, it > 0 ? fone : fzero, Up, M, (long long)NL * M, nl);
+    convert_f2d_add(s, Up, X, (long long)nX);
+    // far field of the FP64 iterate and its change
+    boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
+    scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
+    gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, one, PS, M, 0, A2, 2 * nb, 0, zero, uf, P, 0, 1);
+    ctx->refine_iters = it + 1;
+    if (it > 0) {
+      CK(cudaMemsetAsync(nrm, 0, 2 * sizeof(double), s));
+      diff_norms(s, uf, ufp, (long long)M * P, nrm);
+      double h2[2];
+      CK(cudaMemcpyAsync(h2, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      ctx->refine_update = h2[1] > 0 ? std::sqrt(h2[0] / h2[1]) : 0.0;
+      if (ctx->refine_update <= tol) {
+        converged = true;
+        break;
+      }
+    }
+    std::swap(uf, ufp);
+  }
+  CK(cudaGetLastError());
+  if (!converged) return fail(ctx, HS_ENOCONV, "iterative refinement did not reach the tolerance");
+  if (ufar) CK(cudaMemcpyAsync(ufar, uf, sizeof(double2) * M * P, cudaMemcpyDeviceToDevice, s));
+  if (Xout) CK(cudaMemcpyAsync(Xout, X, sizeof(double2) * nX, cudaMemcpyDeviceToDevice, s));
   return HS_OK;
 }
 
@@ -593,6 +797,11 @@ int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, cons
 size_t jacobian_bytes(hs_ctx* ctx, int M, int P) {
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
   return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) + fields_and_adjoint_bytes(ctx, M, P);
+}
+
+int need_fp64(hs_ctx* ctx) {
+  if (ctx->cfg.precision != HS_FP64) return fail(ctx, HS_EINVAL, "this call needs a context created with HS_FP64");
+  return HS_OK;
 }
 
 int valid_angles(hs_ctx* ctx, int M, int P) {
@@ -671,6 +880,7 @@ int solve_far_in_scratch(hs_ctx* ctx, void* stream, const double* alphas, int M,
                          double* ufar, void* scratch, size_t scratch_bytes) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
+  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!alphas || !thetas || !ufar || !scratch) return fail(ctx, HS_EINVAL, "NULL pointer");
   if (far_solve_scratch_bytes(ctx, M, P) > scratch_bytes)
@@ -825,6 +1035,17 @@ int hs_fields_dev(hs_ctx* ctx, const double* alphas, int M, double* u, void* str
   cudaStream_t s = pick(ctx, stream);
   const int nb = ctx->B.nb;
   Arena a;
+  if (ctx->cfg.precision == HS_MIXED) {
+    // refined FP64 fields; the far field is computed for one receiver (unused)
+    CKR(ensure_ws(ctx, mixed_bytes(ctx, M, 1) + Arena::bytes((size_t)ctx->nleaf * NL * M, 16) + 4096, a));
+    double2* X = a.get<double2>((size_t)ctx->nleaf * NL * M);
+    double* th = a.get<double>(1);
+    CK(cudaMemsetAsync(th, 0, sizeof(double), s));
+    CKR(mixed_solve(ctx, s, alphas, M, th, 1, nullptr, X, a));
+    leaf_to_nodes(s, X, ctx->nL, M, reinterpret_cast<double2*>(u));
+    CK(cudaGetLastError());
+    return HS_OK;
+  }
   size_t need = 4 * Arena::bytes((size_t)nb * M, 16) + 2 * Arena::bytes(field_buf_elems(ctx, M), 16) +
                 Arena::bytes(t3_elems(ctx, M), 16) + Arena::bytes((size_t)ctx->nleaf * NL * M, 16);
   CKR(ensure_ws(ctx, need, a));
@@ -840,9 +1061,49 @@ int hs_fields_dev(hs_ctx* ctx, const double* alphas, int M, double* u, void* str
   return HS_OK;
 }
 
+int hs_forward_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* ufar, double* u,
+                   void* stream) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(valid_angles(ctx, M, P));
+  if (!alphas || !thetas || !ufar || !u) return fail(ctx, HS_EINVAL, "NULL pointer");
+  cudaStream_t s = pick(ctx, stream);
+  const int nb = ctx->B.nb;
+  Arena a;
+  if (ctx->cfg.precision == HS_MIXED) {
+    CKR(ensure_ws(ctx, mixed_bytes(ctx, M, P) + Arena::bytes((size_t)ctx->nleaf * NL * M, 16), a));
+    double2* X = a.get<double2>((size_t)ctx->nleaf * NL * M);
+    CKR(mixed_solve(ctx, s, alphas, M, thetas, P, reinterpret_cast<double2*>(ufar), X, a));
+    leaf_to_nodes(s, X, ctx->nL, M, reinterpret_cast<double2*>(u));
+    CK(cudaGetLastError());
+    return HS_OK;
+  }
+  size_t need = 4 * Arena::bytes((size_t)nb * M, 16) + Arena::bytes((size_t)2 * nb * M, 16) +
+                Arena::bytes((size_t)P * 2 * nb, 16) + 2 * Arena::bytes(field_buf_elems(ctx, M), 16) +
+                Arena::bytes(t3_elems(ctx, M), 16) + Arena::bytes((size_t)ctx->nleaf * NL * M, 16);
+  CKR(ensure_ws(ctx, need, a));
+  double2 *ui = a.get<double2>((size_t)nb * M), *dni = a.get<double2>((size_t)nb * M);
+  double2 *f = a.get<double2>((size_t)nb * M), *g = a.get<double2>((size_t)nb * M);
+  double2* PS = a.get<double2>((size_t)2 * nb * M);
+  double2* A2 = a.get<double2>((size_t)P * 2 * nb);
+  double2 *bufA = a.get<double2>(field_buf_elems(ctx, M)), *bufB = a.get<double2>(field_buf_elems(ctx, M));
+  double2* T3 = a.get<double2>(t3_elems(ctx, M));
+  double2* Uleaf = a.get<double2>((size_t)ctx->nleaf * NL * M);
+  CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
+  boundary_data(s, nb, M, ctx->k, f, g, ui, dni, PS);
+  farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
+  gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
+                                  make_double2(0, 0), reinterpret_cast<double2*>(ufar), P, 0, 1);
+  CKR(sweep_down(ctx, s, f, M, bufA, bufB, T3, Uleaf));
+  leaf_to_nodes(s, Uleaf, ctx->nL, M, reinterpret_cast<double2*>(u));
+  CK(cudaGetLastError());
+  return HS_OK;
+}
+
 int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* J, void* stream) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
+  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!alphas || !thetas || !J) return fail(ctx, HS_EINVAL, "NULL pointer");
   Arena a;
@@ -853,6 +1114,7 @@ int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thet
 int hs_jacobian(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* J) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
+  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!alphas || !thetas || !J) return fail(ctx, HS_EINVAL, "NULL pointer");
   cudaStream_t s = ctx->stream;
@@ -875,6 +1137,7 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
                double lambda_rel, double* c_inout, double* resid_norm_out) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
+  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!data || !alphas || !thetas || !c_inout) return fail(ctx, HS_EINVAL, "NULL pointer");
   if (!(lambda_rel >= 0.0) || !std::isfinite(lambda_rel)) return fail(ctx, HS_EINVAL, "lambda_rel must be >= 0");
@@ -943,6 +1206,7 @@ int hs_gradient_dev(hs_ctx* ctx, const double* data, const double* alphas, int M
                     double* grad, double* misfit_out, void* stream) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
+  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!data || !alphas || !thetas || !grad || !misfit_out) return fail(ctx, HS_EINVAL, "NULL pointer");
   Arena a;
@@ -954,6 +1218,7 @@ int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M, co
                 double* grad, double* misfit_out) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
+  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!data || !alphas || !thetas || !grad) return fail(ctx, HS_EINVAL, "NULL pointer");
   cudaStream_t s = ctx->stream;
@@ -980,6 +1245,13 @@ int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M, co
 }
 
 long long hs_launch_count(const hs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update) {
+  if (!ctx) return HS_EINVAL;
+  if (iterations) *iterations = ctx->refine_iters;
+  if (last_update) *last_update = ctx->refine_update;
+  return HS_OK;
+}
 
 const char* hs_last_error(const hs_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 

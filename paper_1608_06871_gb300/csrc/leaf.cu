@@ -52,13 +52,13 @@ __device__ __forceinline__ int edge_index(int a, int b) {
 }
 
 // Assemble, per leaf, the blocks of the leaf system (interior PDE rows and the
-// outward normal derivative at the edge nodes):
+// outward normal derivative at the edge nodes), computed in FP64 and stored in T:
 //   Aii (196x196), Aie (196x56): rows of  Lap_h u + k^2 (1 - q) u  at interior nodes,
 //   Ni (56x196), NiT = Ni^T (196x56), Ne (56x56): outward normal derivative rows.
+template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_assemble(const double* __restrict__ q, int leaf0, double k, double h,
-                                                       double* __restrict__ Aii, double* __restrict__ Aie,
-                                                       double* __restrict__ Ni, double* __restrict__ NiT,
-                                                       double* __restrict__ Ne) {
+                                                       T* __restrict__ Aii, T* __restrict__ Aie, T* __restrict__ Ni,
+                                                       T* __restrict__ NiT, T* __restrict__ Ne) {
   const int lb = blockIdx.x;  // leaf within the chunk
   const double* ql = q + (long long)(leaf0 + lb) * 256;
   Aii += (long long)lb * NI * NI;
@@ -76,30 +76,33 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const double* __restrict_
     for (int c = 0; c < 16; ++c) s += Dx[i][c] * Dx[c][j];
     D2[i][j] = s;
   }
-  for (int e = threadIdx.x; e < NI * NI; e += blockDim.x) Aii[e] = 0.0;
-  for (int e = threadIdx.x; e < NI * NE; e += blockDim.x) { Aie[e] = 0.0; Ni[e] = 0.0; NiT[e] = 0.0; }
-  for (int e = threadIdx.x; e < NE * NE; e += blockDim.x) Ne[e] = 0.0;
+  for (int e = threadIdx.x; e < NI * NI; e += blockDim.x) Aii[e] = T(0);
+  for (int e = threadIdx.x; e < NI * NE; e += blockDim.x) { Aie[e] = T(0); Ni[e] = T(0); NiT[e] = T(0); }
+  for (int e = threadIdx.x; e < NE * NE; e += blockDim.x) Ne[e] = T(0);
   __syncthreads();
-  // interior rows: one thread per row
+  // interior rows: one thread per row (every entry but the diagonal gets one term)
   for (int r = threadIdx.x; r < NI; r += blockDim.x) {
     const int a = r / 14 + 1, b = r % 14 + 1;
-    double* row = Aii + (long long)r * NI;
-    double* rowe = Aie + (long long)r * NE;
+    T* row = Aii + (long long)r * NI;
+    T* rowe = Aie + (long long)r * NE;
     for (int c = 1; c <= 14; ++c) {
-      row[(c - 1) * 14 + (b - 1)] += D2[a][c];  // d2/dx2 along the x-line through (a, b)
-      row[(a - 1) * 14 + (c - 1)] += D2[b][c];  // d2/dy2 along the y-line
+      if (c != a) row[(c - 1) * 14 + (b - 1)] = T(D2[a][c]);  // d2/dx2 along the x-line through (a, b)
+      if (c != b) row[(a - 1) * 14 + (c - 1)] = T(D2[b][c]);  // d2/dy2 along the y-line
     }
-    row[r] += k * k * (1.0 - ql[a * 16 + b]);
-    rowe[edge_index(0, b)] += D2[a][0];
-    rowe[edge_index(15, b)] += D2[a][15];
-    rowe[edge_index(a, 0)] += D2[b][0];
-    rowe[edge_index(a, 15)] += D2[b][15];
+    double dg = D2[a][a];
+    dg += D2[b][b];
+    dg += k * k * (1.0 - ql[a * 16 + b]);
+    row[r] = T(dg);
+    rowe[edge_index(0, b)] = T(D2[a][0]);
+    rowe[edge_index(15, b)] = T(D2[a][15]);
+    rowe[edge_index(a, 0)] = T(D2[b][0]);
+    rowe[edge_index(a, 15)] = T(D2[b][15]);
   }
-  // normal-derivative rows: one thread per edge node
+  // normal-derivative rows: one thread per edge node (one term per entry)
   for (int e = threadIdx.x; e < NE; e += blockDim.x) {
     const int side = e / 14, t = e % 14 + 1;
-    double* nrow = Ni + (long long)e * NI;
-    double* erow = Ne + (long long)e * NE;
+    T* nrow = Ni + (long long)e * NI;
+    T* erow = Ne + (long long)e * NE;
     for (int c = 0; c < 16; ++c) {
       int a, b;
       double w;
@@ -112,73 +115,94 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const double* __restrict_
       bool interior = (a >= 1 && a <= 14 && b >= 1 && b <= 14);
       if (interior) {
         int rr = (a - 1) * 14 + (b - 1);
-        nrow[rr] += w;
-        NiT[(long long)rr * NE + e] += w;
+        nrow[rr] = T(w);
+        NiT[(long long)rr * NE + e] = T(w);
       } else {
-        erow[edge_index(a, b)] += w;  // never a corner: one coordinate is t in 1..14
+        erow[edge_index(a, b)] = T(w);  // never a corner: one coordinate is t in 1..14
       }
     }
   }
 }
 
 // K = T + i eta I (complex), Kinv = I.
-__global__ void k_make_K(const double* __restrict__ T, double eta, double2* __restrict__ K, double2* __restrict__ Kinv,
-                         int nleaf) {
+template <typename T>
+__global__ void k_make_K(const T* __restrict__ Tm, double eta, typename prec<T>::C* __restrict__ K,
+                         typename prec<T>::C* __restrict__ Kinv, int nleaf) {
+  using C = typename prec<T>::C;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nleaf * NE * NE) return;
   int e = (int)(idx % (NE * NE));
   int r = e / NE, c = e % NE;
-  K[idx] = make_double2(T[idx], r == c ? eta : 0.0);
-  Kinv[idx] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  C kv, iv;
+  kv.x = Tm[idx];
+  kv.y = r == c ? T(eta) : T(0);
+  iv.x = r == c ? T(1) : T(0);
+  iv.y = T(0);
+  K[idx] = kv;
+  Kinv[idx] = iv;
 }
 
 // R = I - 2 i eta Kinv (leaf impedance-to-impedance map); Ye = Kinv (edge rows of Y).
-__global__ void k_leaf_R(const double2* __restrict__ Kinv, double eta, double2* __restrict__ R, double2* __restrict__ Y,
-                         int nleaf) {
+template <typename T>
+__global__ void k_leaf_R(const typename prec<T>::C* __restrict__ Kinv, double eta, typename prec<T>::C* __restrict__ R,
+                         typename prec<T>::C* __restrict__ Y, int nleaf) {
+  using C = typename prec<T>::C;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nleaf * NE * NE) return;
   int lb = (int)(idx / (NE * NE));
   int e = (int)(idx % (NE * NE));
   int r = e / NE, c = e % NE;
-  double2 v = Kinv[idx];
+  C v = Kinv[idx];
   // -2 i eta (x + i y) = 2 eta y - 2 i eta x
-  R[idx] = make_double2((r == c ? 1.0 : 0.0) + 2.0 * eta * v.y, -2.0 * eta * v.x);
+  C rv;
+  rv.x = T((r == c ? 1.0 : 0.0) + 2.0 * eta * (double)v.y);
+  rv.y = T(-2.0 * eta * (double)v.x);
+  R[idx] = rv;
   Y[(long long)lb * NL * NE + (long long)(NI + r) * NE + c] = v;
 }
 
-void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, double h, LeafScratch& w,
-                      double2* R, double2* Y, double2* Q, int* info) {
+template <typename T>
+void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, double h, LeafScratchT<T>& w,
+                      typename prec<T>::C* R, typename prec<T>::C* Y, typename prec<T>::C* Q, int* info) {
+  using C = typename prec<T>::C;
   const double eta = k;
-  k_leaf_assemble<<<nleaf, 256, 0, s>>>(q, leaf0, k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
+  k_leaf_assemble<T><<<nleaf, 256, 0, s>>>(q, leaf0, k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
   HS_COUNT_LAUNCH();
-  lu_factor<double>(s, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, info, nleaf);
+  lu_factor<T>(s, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, info, nleaf);
   // X = Aii^{-1} Aie (Dirichlet-to-interior map), W = Aii^{-T} Ni^T (adjoint)
-  lu_solve<double>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.Aie, NE, (long long)NI * NE, NE, nleaf);
-  lu_solve<double>(s, OP_T, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.NiT, NE, (long long)NI * NE, NE, nleaf);
+  lu_solve<T>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.Aie, NE, (long long)NI * NE, NE, nleaf);
+  lu_solve<T>(s, OP_T, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.NiT, NE, (long long)NI * NE, NE, nleaf);
   // T = Ne - Ni X  (leaf Dirichlet-to-Neumann map), stored in Ne
-  gemm<double, double, double>(s, OP_N, OP_N, NE, NE, NI, -1.0, w.Ni, NI, (long long)NE * NI, w.Aie, NE,
-                               (long long)NI * NE, 1.0, w.Ne, NE, (long long)NE * NE, nleaf);
+  gemm<T, T, T>(s, OP_N, OP_N, NE, NE, NI, T(-1), w.Ni, NI, (long long)NE * NI, w.Aie, NE, (long long)NI * NE, T(1),
+                w.Ne, NE, (long long)NE * NE, nleaf);
   {
     long long n = (long long)nleaf * NE * NE;
-    k_make_K<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Ne, eta, w.K, w.Kinv, nleaf);
+    k_make_K<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Ne, eta, w.K, w.Kinv, nleaf);
     HS_COUNT_LAUNCH();
   }
-  lu_factor<double2>(s, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, info, nleaf);
-  lu_solve<double2>(s, OP_N, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, w.Kinv, NE, (long long)NE * NE, NE, nleaf);
+  lu_factor<C>(s, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, info, nleaf);
+  lu_solve<C>(s, OP_N, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, w.Kinv, NE, (long long)NE * NE, NE, nleaf);
   {
     long long n = (long long)nleaf * NE * NE;
-    k_leaf_R<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Kinv, eta, R, Y, nleaf);
+    k_leaf_R<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Kinv, eta, R, Y, nleaf);
     HS_COUNT_LAUNCH();
   }
+  C m1 = el<C>::zero(), z0 = el<C>::zero(), ieta2 = el<C>::zero();
+  m1.x = T(-1);
+  ieta2.y = T(2.0 * eta);
   // interior rows of the solution operator: Yi = -X Kinv
-  gemm<double, double2, double2>(s, OP_N, OP_N, NI, NE, NE, make_double2(-1.0, 0.0), w.Aie, NE, (long long)NI * NE,
-                                 w.Kinv, NE, (long long)NE * NE, make_double2(0.0, 0.0), Y, NE, (long long)NL * NE,
-                                 nleaf);
-  // adjoint body-load operator: Q = 2 i eta W Kinv^T
-  gemm<double, double2, double2>(s, OP_N, OP_T, NI, NE, NE, make_double2(0.0, 2.0 * eta), w.NiT, NE,
-                                 (long long)NI * NE, w.Kinv, NE, (long long)NE * NE, make_double2(0.0, 0.0), Q, NE,
-                                 (long long)NI * NE, nleaf);
+  gemm<T, C, C>(s, OP_N, OP_N, NI, NE, NE, m1, w.Aie, NE, (long long)NI * NE, w.Kinv, NE, (long long)NE * NE, z0, Y,
+                NE, (long long)NL * NE, nleaf);
+  // adjoint body-load operator: Q = 2 i eta W Kinv^T (skipped when Q is NULL)
+  if (Q)
+    gemm<T, C, C>(s, OP_N, OP_T, NI, NE, NE, ieta2, w.NiT, NE, (long long)NI * NE, w.Kinv, NE, (long long)NE * NE, z0,
+                  Q, NE, (long long)NI * NE, nleaf);
 }
+
+template void leaf_build_chunk<double>(cudaStream_t, const double*, int, int, double, double, LeafScratchT<double>&,
+                                       double2*, double2*, double2*, int*);
+template void leaf_build_chunk<float>(cudaStream_t, const double*, int, int, double, double, LeafScratchT<float>&,
+                                      float2*, float2*, float2*, int*);
 
 void sine_eval_grid(cudaStream_t s, const double* c, int S1, int S2, const double* xg, int nL, double* sx, double* sy,
                     double* T, double* Qg, double* q, int* bad) {

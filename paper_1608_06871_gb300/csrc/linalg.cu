@@ -12,8 +12,14 @@ void prof_begin(cudaStream_t s, cudaEvent_t* a);
 void prof_end(cudaStream_t s, cudaEvent_t a, double flops);
 
 namespace {
+template <typename T> struct is_cplx { static constexpr bool v = false; };
+template <> struct is_cplx<double2> { static constexpr bool v = true; };
+template <> struct is_cplx<float2> { static constexpr bool v = true; };
+template <typename T> struct is_fp64 { static constexpr bool v = false; };
+template <> struct is_fp64<double> { static constexpr bool v = true; };
+template <> struct is_fp64<double2> { static constexpr bool v = true; };
 template <typename TA, typename TB> constexpr double flops_per_mac() {
-  return (sizeof(TA) == 16 && sizeof(TB) == 16) ? 8.0 : ((sizeof(TA) == 16 || sizeof(TB) == 16) ? 4.0 : 2.0);
+  return (is_cplx<TA>::v && is_cplx<TB>::v) ? 8.0 : ((is_cplx<TA>::v || is_cplx<TB>::v) ? 4.0 : 2.0);
 }
 constexpr int BM = 32, BN = 32, BK = 16;  // GEMM tile
 constexpr int NB = 32;                    // LU / TRSM block size
@@ -213,7 +219,7 @@ void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const
           const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC, int batch) {
   if (m <= 0 || n <= 0 || batch <= 0) return;
   dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
-  const bool prof = prof_active(1);
+  const bool prof = prof_active(is_fp64<TC>::v ? 1 : 2);
   cudaEvent_t ev = nullptr;
   if (prof) prof_begin(s, &ev);
   k_gemm<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
@@ -308,5 +314,22 @@ template void lu_solve<double>(cudaStream_t, int, const double*, int, long long,
                                int, long long, int, int);
 template void lu_solve<double2>(cudaStream_t, int, const double2*, int, long long, int, const int*, long long,
                                 double2*, int, long long, int, int);
+
+template void gemm<float, float, float>(cudaStream_t, int, int, int, int, int, float, const float*, int, long long,
+                                        const float*, int, long long, float, float*, int, long long, int);
+template void gemm<float2, float2, float2>(cudaStream_t, int, int, int, int, int, float2, const float2*, int,
+                                           long long, const float2*, int, long long, float2, float2*, int, long long,
+                                           int);
+template void gemm<float, float2, float2>(cudaStream_t, int, int, int, int, int, float2, const float*, int, long long,
+                                          const float2*, int, long long, float2, float2*, int, long long, int);
+template void gemm<float2, float, float2>(cudaStream_t, int, int, int, int, int, float2, const float2*, int,
+                                          long long, const float*, int, long long, float2, float2*, int, long long,
+                                          int);
+template void lu_factor<float>(cudaStream_t, float*, int, long long, int, int*, long long, int*, int);
+template void lu_factor<float2>(cudaStream_t, float2*, int, long long, int, int*, long long, int*, int);
+template void lu_solve<float>(cudaStream_t, int, const float*, int, long long, int, const int*, long long, float*, int,
+                              long long, int, int);
+template void lu_solve<float2>(cudaStream_t, int, const float2*, int, long long, int, const int*, long long, float2*,
+                               int, long long, int, int);
 
 }  // namespace hs

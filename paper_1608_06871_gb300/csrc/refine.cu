@@ -1,0 +1,261 @@
+// Mixed-precision pieces: FP64 residuals of the discrete system and the FP32
+// particular (body-load) solve at the leaves.
+//
+// The discrete system solved by the direct solver (Sec. 2) has three kinds of
+// rows: the collocated PDE at interior leaf nodes, continuity of u and of the
+// normal derivative at shared leaf edge nodes, and the exterior identity
+// (D - I/2)(u - u_inc) = S (d_n u - d_n u_inc) at boundary nodes (Sec. 2,
+// Remark).  With FP32 factors, the solution is refined in FP64: the residual
+// of every row is computed here in FP64 from the current FP64 iterate (leaf
+// layout [leaf][252][nrhs]) and fed to an FP32 solve for the correction.
+#include "tree.cuh"
+
+namespace hs {
+
+namespace {
+
+// Leaf-local unknown index of node (a, b) (never a corner).
+__device__ __forceinline__ int lidx(int a, int b) {
+  if (a >= 1 && a <= 14 && b >= 1 && b <= 14) return (a - 1) * 14 + (b - 1);
+  if (b == 0) return NI + a - 1;
+  if (a == 15) return NI + 14 + b - 1;
+  if (b == 15) return NI + 28 + a - 1;
+  return NI + 42 + b - 1;
+}
+
+__global__ void k_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+__global__ void k_f2d_add(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_double2(b[i].x + (double)a[i].x, b[i].y + (double)a[i].y);
+}
+
+constexpr int RCH = 8;  // right-hand sides per block in the PDE residual
+
+// RP[leaf][r][j] = -(Lap_h u + k^2 (1 - q) u) at interior node r, for the FP64 iterate X.
+__global__ void __launch_bounds__(256) k_res_pde(const double2* __restrict__ X, const double* __restrict__ q,
+                                                 const double* __restrict__ D1, double k, double h, int nrhs,
+                                                 float2* __restrict__ RP) {
+  __shared__ double D2[16][16], Dx[16][16];
+  __shared__ double2 u[NL][RCH];
+  const int leaf = blockIdx.x, j0 = blockIdx.y * RCH;
+  const int nj = min(RCH, nrhs - j0);
+  const double sc = 2.0 / h;
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) Dx[e / 16][e % 16] = D1[e] * sc;
+  for (int e = threadIdx.x; e < NL * RCH; e += blockDim.x) {
+    int r = e / RCH, j = e % RCH;
+    u[r][j] = j < nj ? X[((long long)leaf * NL + r) * nrhs + j0 + j] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    int i = e / 16, jj = e % 16;
+    double s = 0.0;
+    for (int c = 0; c < 16; ++c) s += Dx[i][c] * Dx[c][jj];
+    D2[i][jj] = s;
+  }
+  __syncthreads();
+  const double* ql = q + (long long)leaf * 256;
+  for (int e = threadIdx.x; e < NI * RCH; e += blockDim.x) {
+    int r = e / RCH, j = e % RCH;
+    if (j >= nj) continue;
+    int a = r / 14 + 1, b = r % 14 + 1;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < 16; ++c) {  // a, b in 1..14: the lines through (a, b) contain no corner
+      acc = acc + D2[a][c] * u[lidx(c, b)][j];
+      acc = acc + D2[b][c] * u[lidx(a, c)][j];
+    }
+    acc = acc + (k * k * (1.0 - ql[a * 16 + b])) * u[r][j];
+    RP[((long long)leaf * NL + r) * nrhs + j0 + j] = make_float2((float)(-acc.x), (float)(-acc.y));
+  }
+}
+
+// Outward normal derivative of leaf field U (leaf layout, FP64) at its edge
+// node (a, b), right-hand side j.
+__device__ double2 normal_deriv(const double2* __restrict__ U, int nrhs, int j, const double* __restrict__ D1,
+                                double sc, int a, int b) {
+  double2 acc = make_double2(0.0, 0.0);
+  if (b == 0) {
+    for (int c = 0; c < 16; ++c) acc = acc - (D1[c] * sc) * U[(long long)lidx(a, c) * nrhs + j];
+  } else if (a == 15) {
+    for (int c = 0; c < 16; ++c) acc = acc + (D1[15 * 16 + c] * sc) * U[(long long)lidx(c, b) * nrhs + j];
+  } else if (b == 15) {
+    for (int c = 0; c < 16; ++c) acc = acc + (D1[15 * 16 + c] * sc) * U[(long long)lidx(a, c) * nrhs + j];
+  } else {
+    for (int c = 0; c < 16; ++c) acc = acc - (D1[c] * sc) * U[(long long)lidx(c, b) * nrhs + j];
+  }
+  return acc;
+}
+
+// Interface residual terms of one merge level: for interface node t of parent
+// b, with r_C = -(u_a - u_b) and r_F = -(d_n u_a + d_n u_b),
+// S3[b][t] = r_F + i eta r_C (s_a) and S3[b][ni + t] = r_F - i eta r_C (s_b).
+__global__ void k_res_iface(const double2* __restrict__ X, const double* __restrict__ D1, int nL, double h,
+                            double eta, int horiz, int sx, int sy, int ni, int nbx_p, int nrhs,
+                            float2* __restrict__ S3) {
+  const int b = blockIdx.y;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)ni * nrhs) return;
+  const int t = (int)(e / nrhs), j = (int)(e % nrhs);
+  const int px = b % nbx_p, py = b / nbx_p;
+  int la, lb, aa, ba, ab, bb;  // leaves and edge nodes on the alpha / beta side
+  if (horiz) {
+    const int x0 = px * 2 * sx, y0 = py * sy;
+    const int ly = y0 + t / 14, node = t % 14 + 1;
+    la = ly * nL + (x0 + sx - 1);
+    lb = ly * nL + (x0 + sx);
+    aa = 15; ba = node;  // alpha: east edge
+    ab = 0; bb = node;   // beta: west edge
+  } else {
+    const int x0 = px * sx, y0 = py * 2 * sy;
+    const int lx = x0 + t / 14, node = t % 14 + 1;
+    la = (y0 + sy - 1) * nL + lx;
+    lb = (y0 + sy) * nL + lx;
+    aa = node; ba = 15;  // alpha: north edge
+    ab = node; bb = 0;   // beta: south edge
+  }
+  const double sc = 2.0 / h;
+  const double2* Ua = X + (long long)la * NL * nrhs;
+  const double2* Ub = X + (long long)lb * NL * nrhs;
+  double2 ua = Ua[(long long)lidx(aa, ba) * nrhs + j], ub = Ub[(long long)lidx(ab, bb) * nrhs + j];
+  double2 na = normal_deriv(Ua, nrhs, j, D1, sc, aa, ba), nb2 = normal_deriv(Ub, nrhs, j, D1, sc, ab, bb);
+  double2 rc = ub - ua;                 // -(u_a - u_b)
+  double2 rf = -(na + nb2);
+  // i eta rc = (-eta rc.y, eta rc.x)
+  double2 sa = make_double2(rf.x - eta * rc.y, rf.y + eta * rc.x);
+  double2 sbv = make_double2(rf.x + eta * rc.y, rf.y - eta * rc.x);
+  S3[((long long)b * 2 * ni + t) * nrhs + j] = make_float2((float)sa.x, (float)sa.y);
+  S3[((long long)b * 2 * ni + ni + t) * nrhs + j] = make_float2((float)sbv.x, (float)sbv.y);
+}
+
+// u and d_n u at the boundary nodes (root order: S, E, N, W, each by
+// increasing coordinate) from the leaf fields.
+__global__ void k_boundary_gather(const double2* __restrict__ X, const double* __restrict__ D1, int nL, double h,
+                                  int nrhs, double2* __restrict__ ub, double2* __restrict__ psib) {
+  const int nb = 56 * nL;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nb * nrhs) return;
+  const int jn = (int)(e / nrhs), j = (int)(e % nrhs);
+  const int side = jn / (14 * nL), i = (jn % (14 * nL)) / 14, t = jn % 14 + 1;
+  int leaf, a, b;
+  switch (side) {
+    case 0: leaf = i; a = t; b = 0; break;                       // S: leaf (i, 0)
+    case 1: leaf = i * nL + (nL - 1); a = 15; b = t; break;      // E: leaf (nL-1, i)
+    case 2: leaf = (nL - 1) * nL + i; a = t; b = 15; break;      // N: leaf (i, nL-1)
+    default: leaf = i * nL; a = 0; b = t; break;                 // W: leaf (0, i)
+  }
+  const double2* U = X + (long long)leaf * NL * nrhs;
+  ub[e] = U[(long long)lidx(a, b) * nrhs + j];
+  psib[e] = normal_deriv(U, nrhs, j, D1, 2.0 / h, a, b);
+}
+
+// H = -2 i eta u_e^p (particular outgoing impedance) from the edge rows of Upart.
+__global__ void k_leaf_h(const float2* __restrict__ Upart, int nleaf, double eta, int nrhs, float2* __restrict__ H) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nleaf * NE * nrhs) return;
+  const int j = (int)(e % nrhs);
+  const long long t = e / nrhs;
+  const int r = (int)(t % NE), leaf = (int)(t / NE);
+  float2 v = Upart[((long long)leaf * NL + NI + r) * nrhs + j];
+  const float te = (float)(2.0 * eta);
+  H[e] = make_float2(te * v.y, -te * v.x);  // -2 i eta (x + i y)
+}
+
+__global__ void k_scattered(const double2* __restrict__ ub, const double2* __restrict__ psib,
+                            const double2* __restrict__ ui, const double2* __restrict__ dni, long long n,
+                            double2* __restrict__ PS) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  PS[e] = ub[e] - ui[e];
+  PS[n + e] = psib[e] - dni[e];
+}
+
+// out[0] += sum |a - b|^2, out[1] += sum |a|^2
+__global__ void k_diff_norms(const double2* __restrict__ a, const double2* __restrict__ b, long long n,
+                             double* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0, v = 0.0;
+  if (i < n) {
+    double2 x = a[i], y = b[i];
+    d = (x.x - y.x) * (x.x - y.x) + (x.y - y.y) * (x.y - y.y);
+    v = x.x * x.x + x.y * x.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d += __shfl_down_sync(0xffffffffu, d, o);
+    v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, d);
+    atomicAdd(out + 1, v);
+  }
+}
+
+inline unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out) {
+  k_diff_norms<<<blocks(n), 256, 0, s>>>(a, b, n, out);
+  HS_COUNT_LAUNCH();
+}
+
+void convert_d2f(cudaStream_t s, const double2* a, float2* b, long long n) {
+  k_d2f<<<blocks(n), 256, 0, s>>>(a, b, n);
+  HS_COUNT_LAUNCH();
+}
+
+void convert_f2d_add(cudaStream_t s, const float2* a, double2* b, long long n) {
+  k_f2d_add<<<blocks(n), 256, 0, s>>>(a, b, n);
+  HS_COUNT_LAUNCH();
+}
+
+void residual_pde(cudaStream_t s, const double2* X, const double* q, const double* D1, int nleaf, double k, double h,
+                  int nrhs, float2* RP) {
+  dim3 g(nleaf, (nrhs + RCH - 1) / RCH);
+  k_res_pde<<<g, 256, 0, s>>>(X, q, D1, k, h, nrhs, RP);
+  HS_COUNT_LAUNCH();
+}
+
+void residual_iface(cudaStream_t s, const LevelMaps& L, const double2* X, const double* D1, int nL, double h,
+                    double eta, int nrhs, float2* S3) {
+  dim3 g(blocks((long long)L.ni * nrhs), L.nbox);
+  k_res_iface<<<g, 256, 0, s>>>(X, D1, nL, h, eta, L.horiz, L.sx, L.sy, L.ni, L.nbx_p, nrhs, S3);
+  HS_COUNT_LAUNCH();
+}
+
+void boundary_gather(cudaStream_t s, const double2* X, const double* D1, int nL, double h, int nrhs, double2* ub,
+                     double2* psib) {
+  long long n = 56LL * nL * nrhs;
+  k_boundary_gather<<<blocks(n), 256, 0, s>>>(X, D1, nL, h, nrhs, ub, psib);
+  HS_COUNT_LAUNCH();
+}
+
+// Particular leaf solution for body loads b held in Upart rows 0..195 (FP32):
+// w = Aii^{-1} b, u_e = -Kinv Ni w, u_i = w - X u_e, and h = -2 i eta u_e.
+void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, double eta, int nrhs, float2* Upart,
+                     float2* H, float2* tmp) {
+  const long long sU = (long long)NL * nrhs;
+  const float2 one = make_float2(1.f, 0.f), mone = make_float2(-1.f, 0.f), zero = make_float2(0.f, 0.f);
+  // complex right-hand sides are solved as 2 nrhs real columns
+  lu_solve<float>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, reinterpret_cast<float*>(Upart), 2 * nrhs,
+                  2 * sU, 2 * nrhs, nleaf);
+  gemm<float, float2, float2>(s, OP_N, OP_N, NE, nrhs, NI, one, w.Ni, NI, (long long)NE * NI, Upart, nrhs, sU, zero,
+                              tmp, nrhs, (long long)NE * nrhs, nleaf);
+  gemm<float2, float2, float2>(s, OP_N, OP_N, NE, nrhs, NE, mone, w.Kinv, NE, (long long)NE * NE, tmp, nrhs,
+                               (long long)NE * nrhs, zero, Upart + (long long)NI * nrhs, nrhs, sU, nleaf);
+  gemm<float, float2, float2>(s, OP_N, OP_N, NI, nrhs, NE, mone, w.Aie, NE, (long long)NI * NE,
+                              Upart + (long long)NI * nrhs, nrhs, sU, one, Upart, nrhs, sU, nleaf);
+  long long n = (long long)nleaf * NE * nrhs;
+  k_leaf_h<<<blocks(n), 256, 0, s>>>(Upart, nleaf, eta, nrhs, H);
+  HS_COUNT_LAUNCH();
+}
+
+void scattered_data(cudaStream_t s, const double2* ub, const double2* psib, const double2* ui, const double2* dni,
+                    long long n, double2* PS) {
+  k_scattered<<<blocks(n), 256, 0, s>>>(ub, psib, ui, dni, n, PS);
+  HS_COUNT_LAUNCH();
+}
+
+}  // namespace hs

@@ -5,14 +5,17 @@
 // For children alpha, beta with ItI maps R^a, R^b, exterior nodes "1" (alpha)
 // and "2" (beta) and the shared interface "3" (same nodes, opposite normals):
 // continuity of u and of the flux makes the incoming impedance on each side of
-// the interface the negative of the outgoing one on the other.  Eliminating
-// the interface gives
-//   f3a = X f,   X = W [B33 A31, -B32],  W = (I - B33 A33)^{-1}
-//   f3b = Z f,   Z = -[A31, 0] - A33 X
+// the interface the negative of the outgoing one on the other (plus the
+// interface residual terms s_a, s_b when the continuity rows have a right-hand
+// side).  Eliminating the interface gives
+//   f3a = X f + t_a,   X = W [B33 A31, -B32],  W = (I - B33 A33)^{-1}
+//   f3b = Z f + t_b,   Z = -[A31, 0] - A33 X
 //   R   = blockdiag(A11, B22) + [A13 X ; B23 Z]
-// where A = R^a, B = R^b restricted to the index sets.  The level routines
-// build these with batched gathers, GEMMs and LU factorisations over all
-// parent boxes of the level.
+//   t_a = W (B33 (h3a - s_b) - (h3b - s_a)),   t_b = -A33 t_a - (h3a - s_b)
+//   h   = [h1a + A13 t_a ; h2b + B23 t_b]      (particular outgoing impedance)
+// where A = R^a, B = R^b restricted to the index sets and h the children's
+// particular outgoing impedances (body loads).  The level routines do this
+// with batched gathers, GEMMs and LU factorisations over all parents of a level.
 #include "tree.cuh"
 
 namespace hs {
@@ -21,35 +24,39 @@ namespace {
 __device__ __forceinline__ int src_child(int v) { return v >> 20; }
 __device__ __forceinline__ int src_local(int v) { return v & 0xFFFFF; }
 
+template <typename C> __device__ __forceinline__ C czero() { return el<C>::zero(); }
+
 // A33 = R^a[I3a, I3a], B33 = R^b[I3b, I3b], M = I.
-__global__ void k_gather_33(const double2* __restrict__ Rc, int nc, const int* __restrict__ alpha,
+template <typename C>
+__global__ void k_gather_33(const C* __restrict__ Rc, int nc, const int* __restrict__ alpha,
                             const int* __restrict__ beta, const int* __restrict__ I3a, const int* __restrict__ I3b,
-                            int ni, double2* __restrict__ A33, double2* __restrict__ B33, double2* __restrict__ M) {
+                            int ni, C* __restrict__ A33, C* __restrict__ B33, C* __restrict__ M) {
   const int b = blockIdx.y;
   const long long nn = (long long)ni * ni;
-  const double2* Ra = Rc + (long long)alpha[b] * nc * nc;
-  const double2* Rb = Rc + (long long)beta[b] * nc * nc;
+  const C* Ra = Rc + (long long)alpha[b] * nc * nc;
+  const C* Rb = Rc + (long long)beta[b] * nc * nc;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
     int r = (int)(e / ni), c = (int)(e % ni);
     A33[b * nn + e] = Ra[(long long)I3a[r] * nc + I3a[c]];
     B33[b * nn + e] = Rb[(long long)I3b[r] * nc + I3b[c]];
-    M[b * nn + e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    M[b * nn + e] = r == c ? el<C>::one() : czero<C>();
   }
 }
 
 // XZ top = Bb = [0, B32] (columns of beta-sourced parent nodes), XZ bottom = Aa = [A31, 0].
-__global__ void k_gather_XZ(const double2* __restrict__ Rc, int nc, const int* __restrict__ alpha,
+template <typename C>
+__global__ void k_gather_XZ(const C* __restrict__ Rc, int nc, const int* __restrict__ alpha,
                             const int* __restrict__ beta, const int* __restrict__ I3a, const int* __restrict__ I3b,
-                            const int* __restrict__ src, int ni, int np, double2* __restrict__ XZ) {
+                            const int* __restrict__ src, int ni, int np, C* __restrict__ XZ) {
   const int b = blockIdx.y;
   const long long tot = 2LL * ni * np;
-  const double2* Ra = Rc + (long long)alpha[b] * nc * nc;
-  const double2* Rb = Rc + (long long)beta[b] * nc * nc;
-  double2* out = XZ + b * tot;
+  const C* Ra = Rc + (long long)alpha[b] * nc * nc;
+  const C* Rb = Rc + (long long)beta[b] * nc * nc;
+  C* out = XZ + b * tot;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     int r = (int)(e / np), c = (int)(e % np);
     int sv = src[c];
-    double2 v = make_double2(0.0, 0.0);
+    C v = czero<C>();
     if (r < ni) {
       if (src_child(sv) == 1) v = Rb[(long long)I3b[r] * nc + src_local(sv)];
     } else {
@@ -60,18 +67,19 @@ __global__ void k_gather_XZ(const double2* __restrict__ Rc, int nc, const int* _
 }
 
 // U2 rows: alpha-sourced parent node -> [A13 row, 0], beta-sourced -> [0, B23 row].
-__global__ void k_gather_U2(const double2* __restrict__ Rc, int nc, const int* __restrict__ alpha,
+template <typename C>
+__global__ void k_gather_U2(const C* __restrict__ Rc, int nc, const int* __restrict__ alpha,
                             const int* __restrict__ beta, const int* __restrict__ I3a, const int* __restrict__ I3b,
-                            const int* __restrict__ src, int ni, int np, double2* __restrict__ U2) {
+                            const int* __restrict__ src, int ni, int np, C* __restrict__ U2) {
   const int b = blockIdx.y;
   const long long tot = (long long)np * 2 * ni;
-  const double2* Ra = Rc + (long long)alpha[b] * nc * nc;
-  const double2* Rb = Rc + (long long)beta[b] * nc * nc;
-  double2* out = U2 + b * tot;
+  const C* Ra = Rc + (long long)alpha[b] * nc * nc;
+  const C* Rb = Rc + (long long)beta[b] * nc * nc;
+  C* out = U2 + b * tot;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     int r = (int)(e / (2 * ni)), c = (int)(e % (2 * ni));
     int sv = src[r];
-    double2 v = make_double2(0.0, 0.0);
+    C v = czero<C>();
     if (c < ni) {
       if (src_child(sv) == 0) v = Ra[(long long)src_local(sv) * nc + I3a[c]];
     } else {
@@ -82,20 +90,20 @@ __global__ void k_gather_U2(const double2* __restrict__ Rc, int nc, const int* _
 }
 
 // Rp = blockdiag(A11, B22) in the parent's node order.
-__global__ void k_gather_diag(const double2* __restrict__ Rc, int nc, const int* __restrict__ alpha,
-                              const int* __restrict__ beta, const int* __restrict__ src, int np,
-                              double2* __restrict__ Rp) {
+template <typename C>
+__global__ void k_gather_diag(const C* __restrict__ Rc, int nc, const int* __restrict__ alpha,
+                              const int* __restrict__ beta, const int* __restrict__ src, int np, C* __restrict__ Rp) {
   const int b = blockIdx.y;
   const long long tot = (long long)np * np;
-  const double2* Ra = Rc + (long long)alpha[b] * nc * nc;
-  const double2* Rb = Rc + (long long)beta[b] * nc * nc;
-  double2* out = Rp + b * tot;
+  const C* Ra = Rc + (long long)alpha[b] * nc * nc;
+  const C* Rb = Rc + (long long)beta[b] * nc * nc;
+  C* out = Rp + b * tot;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     int r = (int)(e / np), c = (int)(e % np);
     int sr = src[r], sc = src[c];
-    double2 v = make_double2(0.0, 0.0);
+    C v = czero<C>();
     if (src_child(sr) == src_child(sc)) {
-      const double2* Rx = src_child(sr) == 0 ? Ra : Rb;
+      const C* Rx = src_child(sr) == 0 ? Ra : Rb;
       v = Rx[(long long)src_local(sr) * nc + src_local(sc)];
     }
     out[e] = v;
@@ -104,11 +112,10 @@ __global__ void k_gather_diag(const double2* __restrict__ Rc, int nc, const int*
 
 // Children's incoming impedances from the parent's (exterior nodes) and the
 // interface values T3 = [f3a; f3b].
-__global__ void k_scatter_down(const double2* __restrict__ Fp, const double2* __restrict__ T3,
-                               const int* __restrict__ alpha, const int* __restrict__ beta,
-                               const int* __restrict__ src, const int* __restrict__ I3a,
-                               const int* __restrict__ I3b, int nc, int ni, int np, int nrhs,
-                               double2* __restrict__ Fc) {
+template <typename C>
+__global__ void k_scatter_down(const C* __restrict__ Fp, const C* __restrict__ T3, const int* __restrict__ alpha,
+                               const int* __restrict__ beta, const int* __restrict__ src, const int* __restrict__ I3a,
+                               const int* __restrict__ I3b, int nc, int ni, int np, int nrhs, C* __restrict__ Fc) {
   const int b = blockIdx.y;
   const long long rows = np + 2LL * ni;
   const long long tot = rows * nrhs;
@@ -121,7 +128,7 @@ __global__ void k_scatter_down(const double2* __restrict__ Fp, const double2* __
       Fc[((long long)child * nc + src_local(sv)) * nrhs + j] = Fp[((long long)b * np + r) * nrhs + j];
     } else {
       int t = r - np;
-      double2 v = T3[((long long)b * 2 * ni + t) * nrhs + j];
+      C v = T3[((long long)b * 2 * ni + t) * nrhs + j];
       if (t < ni)
         Fc[((long long)ca * nc + I3a[t]) * nrhs + j] = v;
       else
@@ -133,11 +140,10 @@ __global__ void k_scatter_down(const double2* __restrict__ Fp, const double2* __
 // Adjoint: children's adjoint impedance loads.  MU[b] holds [Wt; la3] with
 // Wt = M^{-T} lambda_ta and la3 = B33^T Wt - lambda_tb; alpha's interface gets
 // la3, beta's gets -Wt, exterior nodes copy the parent's.
-__global__ void k_scatter_adj(const double2* __restrict__ Lp, const double2* __restrict__ MU,
-                              const int* __restrict__ alpha, const int* __restrict__ beta,
-                              const int* __restrict__ src, const int* __restrict__ I3a,
-                              const int* __restrict__ I3b, int nc, int ni, int np, int nrhs,
-                              double2* __restrict__ Lc) {
+template <typename C>
+__global__ void k_scatter_adj(const C* __restrict__ Lp, const C* __restrict__ MU, const int* __restrict__ alpha,
+                              const int* __restrict__ beta, const int* __restrict__ src, const int* __restrict__ I3a,
+                              const int* __restrict__ I3b, int nc, int ni, int np, int nrhs, C* __restrict__ Lc) {
   const int b = blockIdx.y;
   const long long rows = np + 2LL * ni;
   const long long tot = rows * nrhs;
@@ -159,6 +165,39 @@ __global__ void k_scatter_adj(const double2* __restrict__ Lp, const double2* __r
   }
 }
 
+// Upward gather: TT top := h3b - s_a, TT bottom := h3a - s_b, Hp := children's
+// exterior particular impedances in the parent's order.
+template <typename C>
+__global__ void k_gather_up(const C* __restrict__ Hc, const C* __restrict__ S3, const int* __restrict__ alpha,
+                            const int* __restrict__ beta, const int* __restrict__ src, const int* __restrict__ I3a,
+                            const int* __restrict__ I3b, int nc, int ni, int np, int nrhs, C* __restrict__ TT,
+                            C* __restrict__ Hp) {
+  const int b = blockIdx.y;
+  const long long rows = np + 2LL * ni;
+  const long long tot = rows * nrhs;
+  const int ca = alpha[b], cb = beta[b];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e / nrhs), j = (int)(e % nrhs);
+    if (r < np) {
+      int sv = src[r];
+      int child = src_child(sv) == 0 ? ca : cb;
+      Hp[((long long)b * np + r) * nrhs + j] = Hc[((long long)child * nc + src_local(sv)) * nrhs + j];
+    } else {
+      int t = r - np;
+      C v;
+      C sres = czero<C>();
+      if (t < ni) {  // h3b - s_a
+        v = Hc[((long long)cb * nc + I3b[t]) * nrhs + j];
+        if (S3) sres = S3[((long long)b * 2 * ni + t) * nrhs + j];
+      } else {       // h3a - s_b
+        v = Hc[((long long)ca * nc + I3a[t - ni]) * nrhs + j];
+        if (S3) sres = S3[((long long)b * 2 * ni + t) * nrhs + j];
+      }
+      TT[((long long)b * 2 * ni + t) * nrhs + j] = v - sres;
+    }
+  }
+}
+
 inline unsigned grid_for(long long n, int per_block, int cap = 4096) {
   long long g = (n + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -167,68 +206,102 @@ inline unsigned grid_for(long long n, int per_block, int cap = 4096) {
 }
 }  // namespace
 
-void merge_level(cudaStream_t s, const Level& L, const double2* Rc, int* info) {
+template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Rc, int* info) {
   const int ni = L.ni, np = L.np, nc = L.nc, nb = L.nbox;
   const long long nn = (long long)ni * ni, xz = 2LL * ni * np, pp = (long long)np * np;
-  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0), zero = make_double2(0.0, 0.0);
-  k_gather_33<<<dim3(grid_for(nn, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, ni, L.A33,
-                                                          L.B33, L.M);
+  const C one = el<C>::one(), mone = -el<C>::one();
+  k_gather_33<C><<<dim3(grid_for(nn, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, ni, O.A33,
+                                                             O.B33, O.M);
   HS_COUNT_LAUNCH();
-  k_gather_XZ<<<dim3(grid_for(xz, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, L.d_src, ni,
-                                                          np, L.XZ);
+  k_gather_XZ<C><<<dim3(grid_for(xz, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, L.d_src,
+                                                             ni, np, O.XZ);
   HS_COUNT_LAUNCH();
-  k_gather_U2<<<dim3(grid_for(xz, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, L.d_src, ni,
-                                                          np, L.U2);
+  k_gather_U2<C><<<dim3(grid_for(xz, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, L.d_src,
+                                                             ni, np, O.U2);
   HS_COUNT_LAUNCH();
-  k_gather_diag<<<dim3(grid_for(pp, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_src, np, L.R);
+  k_gather_diag<C><<<dim3(grid_for(pp, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_src, np, O.R);
   HS_COUNT_LAUNCH();
   // M = I - B33 A33
-  gemm<double2, double2, double2>(s, OP_N, OP_N, ni, ni, ni, mone, L.B33, ni, nn, L.A33, ni, nn, one, L.M, ni, nn, nb);
+  gemm<C, C, C>(s, OP_N, OP_N, ni, ni, ni, mone, O.B33, ni, nn, O.A33, ni, nn, one, O.M, ni, nn, nb);
   // top = B33 * bottom - top  (V = B33 Aa - Bb)
-  gemm<double2, double2, double2>(s, OP_N, OP_N, ni, np, ni, one, L.B33, ni, nn, L.XZ + nn * 0 + (long long)ni * np,
-                                  np, xz, mone, L.XZ, np, xz, nb);
-  lu_factor<double2>(s, L.M, ni, nn, ni, L.Mpiv, ni, info, nb);
+  gemm<C, C, C>(s, OP_N, OP_N, ni, np, ni, one, O.B33, ni, nn, O.XZ + (long long)ni * np, np, xz, mone, O.XZ, np, xz,
+                nb);
+  lu_factor<C>(s, O.M, ni, nn, ni, O.Mpiv, ni, info, nb);
   // X = M^{-1} V (top half)
-  lu_solve<double2>(s, OP_N, L.M, ni, nn, ni, L.Mpiv, ni, L.XZ, np, xz, np, nb);
+  lu_solve<C>(s, OP_N, O.M, ni, nn, ni, O.Mpiv, ni, O.XZ, np, xz, np, nb);
   // bottom = -A33 X - bottom  (Z = -Aa - A33 X)
-  gemm<double2, double2, double2>(s, OP_N, OP_N, ni, np, ni, mone, L.A33, ni, nn, L.XZ, np, xz, mone,
-                                  L.XZ + (long long)ni * np, np, xz, nb);
+  gemm<C, C, C>(s, OP_N, OP_N, ni, np, ni, mone, O.A33, ni, nn, O.XZ, np, xz, mone, O.XZ + (long long)ni * np, np, xz,
+                nb);
   // R = blockdiag + U2 [X; Z]
-  gemm<double2, double2, double2>(s, OP_N, OP_N, np, np, 2 * ni, one, L.U2, 2 * ni, (long long)np * 2 * ni, L.XZ, np,
-                                  xz, one, L.R, np, pp, nb);
-  (void)zero;
+  gemm<C, C, C>(s, OP_N, OP_N, np, np, 2 * ni, one, O.U2, 2 * ni, (long long)np * 2 * ni, O.XZ, np, xz, one, O.R, np,
+                pp, nb);
 }
 
-void sweep_down_level(cudaStream_t s, const Level& L, const double2* Fp, double2* T3, double2* Fc, int nrhs) {
+template <typename C>
+void sweep_down_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Fp, C* T3, C* Fc, int nrhs,
+                      bool t3_loaded) {
   const int ni = L.ni, np = L.np, nb = L.nbox;
-  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  gemm<double2, double2, double2>(s, OP_N, OP_N, 2 * ni, nrhs, np, one, L.XZ, np, 2LL * ni * np, Fp, nrhs,
-                                  (long long)np * nrhs, zero, T3, nrhs, 2LL * ni * nrhs, nb);
+  const C one = el<C>::one(), zero = el<C>::zero();
+  gemm<C, C, C>(s, OP_N, OP_N, 2 * ni, nrhs, np, one, O.XZ, np, 2LL * ni * np, Fp, nrhs, (long long)np * nrhs,
+                t3_loaded ? one : zero, T3, nrhs, 2LL * ni * nrhs, nb);
   long long tot = ((long long)np + 2LL * ni) * nrhs;
-  k_scatter_down<<<dim3(grid_for(tot, 256), nb), 256, 0, s>>>(Fp, T3, L.d_alpha, L.d_beta, L.d_src, L.d_I3a, L.d_I3b,
-                                                              L.nc, ni, np, nrhs, Fc);
+  k_scatter_down<C><<<dim3(grid_for(tot, 256), nb), 256, 0, s>>>(Fp, T3, L.d_alpha, L.d_beta, L.d_src, L.d_I3a,
+                                                                 L.d_I3b, L.nc, ni, np, nrhs, Fc);
   HS_COUNT_LAUNCH();
 }
 
-void sweep_adjoint_level(cudaStream_t s, const Level& L, const double2* Lp, double2* MU, double2* Lc, int nrhs) {
+template <typename C>
+void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lp, C* MU, C* Lc,
+                         int nrhs) {
   const int ni = L.ni, np = L.np, nb = L.nbox;
   const long long nn = (long long)ni * ni, mu = 2LL * ni * nrhs;
-  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0), zero = make_double2(0.0, 0.0);
+  const C one = el<C>::one(), mone = -el<C>::one(), zero = el<C>::zero();
   // [mu_a; mu_b] = U2^T lambda_p ;  lambda_tb = mu_b
-  gemm<double2, double2, double2>(s, OP_T, OP_N, 2 * ni, nrhs, np, one, L.U2, 2 * ni, (long long)np * 2 * ni, Lp,
-                                  nrhs, (long long)np * nrhs, zero, MU, nrhs, mu, nb);
+  gemm<C, C, C>(s, OP_T, OP_N, 2 * ni, nrhs, np, one, O.U2, 2 * ni, (long long)np * 2 * ni, Lp, nrhs,
+                (long long)np * nrhs, zero, MU, nrhs, mu, nb);
   // lambda_ta = mu_a - A33^T lambda_tb
-  gemm<double2, double2, double2>(s, OP_T, OP_N, ni, nrhs, ni, mone, L.A33, ni, nn, MU + (long long)ni * nrhs, nrhs,
-                                  mu, one, MU, nrhs, mu, nb);
+  gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, ni, mone, O.A33, ni, nn, MU + (long long)ni * nrhs, nrhs, mu, one, MU, nrhs,
+                mu, nb);
   // Wt = M^{-T} lambda_ta
-  lu_solve<double2>(s, OP_T, L.M, ni, nn, ni, L.Mpiv, ni, MU, nrhs, mu, nrhs, nb);
+  lu_solve<C>(s, OP_T, O.M, ni, nn, ni, O.Mpiv, ni, MU, nrhs, mu, nrhs, nb);
   // la3 = B33^T Wt - lambda_tb
-  gemm<double2, double2, double2>(s, OP_T, OP_N, ni, nrhs, ni, one, L.B33, ni, nn, MU, nrhs, mu, mone,
-                                  MU + (long long)ni * nrhs, nrhs, mu, nb);
+  gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, ni, one, O.B33, ni, nn, MU, nrhs, mu, mone, MU + (long long)ni * nrhs, nrhs,
+                mu, nb);
   long long tot = ((long long)np + 2LL * ni) * nrhs;
-  k_scatter_adj<<<dim3(grid_for(tot, 256), nb), 256, 0, s>>>(Lp, MU, L.d_alpha, L.d_beta, L.d_src, L.d_I3a, L.d_I3b,
-                                                             L.nc, ni, np, nrhs, Lc);
+  k_scatter_adj<C><<<dim3(grid_for(tot, 256), nb), 256, 0, s>>>(Lp, MU, L.d_alpha, L.d_beta, L.d_src, L.d_I3a,
+                                                                L.d_I3b, L.nc, ni, np, nrhs, Lc);
   HS_COUNT_LAUNCH();
 }
+
+template <typename C>
+void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Hc, const C* S3, C* TT, C* Hp,
+                    int nrhs) {
+  const int ni = L.ni, np = L.np, nb = L.nbox;
+  const long long nn = (long long)ni * ni, tt = 2LL * ni * nrhs;
+  const C one = el<C>::one(), mone = -el<C>::one();
+  long long tot = ((long long)np + 2LL * ni) * nrhs;
+  k_gather_up<C><<<dim3(grid_for(tot, 256), nb), 256, 0, s>>>(Hc, S3, L.d_alpha, L.d_beta, L.d_src, L.d_I3a, L.d_I3b,
+                                                              L.nc, ni, np, nrhs, TT, Hp);
+  HS_COUNT_LAUNCH();
+  // top := B33 (h3a - s_b) - (h3b - s_a);  t_a = W top
+  gemm<C, C, C>(s, OP_N, OP_N, ni, nrhs, ni, one, O.B33, ni, nn, TT + (long long)ni * nrhs, nrhs, tt, mone, TT, nrhs,
+                tt, nb);
+  lu_solve<C>(s, OP_N, O.M, ni, nn, ni, O.Mpiv, ni, TT, nrhs, tt, nrhs, nb);
+  // bottom := -A33 t_a - (h3a - s_b) = t_b
+  gemm<C, C, C>(s, OP_N, OP_N, ni, nrhs, ni, mone, O.A33, ni, nn, TT, nrhs, tt, mone, TT + (long long)ni * nrhs, nrhs,
+                tt, nb);
+  // Hp += U2 [t_a; t_b]
+  gemm<C, C, C>(s, OP_N, OP_N, np, nrhs, 2 * ni, one, O.U2, 2 * ni, (long long)np * 2 * ni, TT, nrhs, tt, one, Hp, nrhs,
+                (long long)np * nrhs, nb);
+}
+
+#define HS_INST(C)                                                                                                     \
+  template void merge_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, int*);                  \
+  template void sweep_down_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool); \
+  template void sweep_adjoint_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int);    \
+  template void sweep_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, const C*, C*, C*, int);
+HS_INST(double2)
+HS_INST(float2)
+#undef HS_INST
 
 }  // namespace hs

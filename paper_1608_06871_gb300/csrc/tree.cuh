@@ -1,5 +1,6 @@
 // Quadtree of the direct solver (Sec. 2): leaf sizes, merge levels and the
-// device routines that build and sweep it.
+// device routines that build and sweep it, in FP64 (double2 operators) or
+// FP32 (float2 operators, the mixed-precision path).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -12,38 +13,72 @@ constexpr int NI = 196;  // interior nodes of a 16 x 16 leaf
 constexpr int NE = 56;   // non-corner edge nodes (boundary data of a leaf)
 constexpr int NL = 252;  // NI + NE: the leaf's unknowns
 
-struct LeafScratch {  // per-chunk scratch of the leaf build
-  double *Aii, *Aie, *Ni, *NiT, *Ne;
-  double2 *K, *Kinv;
+template <typename T> struct LeafScratchT {  // leaf build scratch; in the mixed path it is kept (refinement)
+  using C = typename prec<T>::C;
+  T *Aii, *Aie, *Ni, *NiT, *Ne;   // Aii holds the LU factors, Aie holds X = Aii^{-1} Aie afterwards
+  C *K, *Kinv;
   int *piv, *pivK;
 };
+using LeafScratch = LeafScratchT<double>;
 
-// One level of merges: pairs of child boxes (sx x sy leaves each) merged
-// horizontally (west-east) or vertically (south-north) into nbox parents.
-struct Level {
+// Index maps of one level of merges: pairs of child boxes (sx x sy leaves
+// each) merged horizontally (west-east) or vertically (south-north).
+struct LevelMaps {
   int horiz, sx, sy;
-  int nc, ni, np;  // child boundary size, interface size, parent boundary size
-  int nbox;
+  int nc, ni, np;              // child boundary size, interface size, parent boundary size
+  int nbox, nbx_p;             // parent boxes, parents per row
   int *d_alpha, *d_beta;       // child box ids of each parent
   int *d_src;                  // parent boundary node -> (child << 20) | child-local index
   int *d_I3a, *d_I3b;          // interface nodes in the alpha / beta child
-  double2 *XZ;                 // [nbox][2 ni][np]  interface impedances from the parent's
-  double2 *U2;                 // [nbox][np][2 ni]  interface -> parent outgoing impedance
-  double2 *A33, *B33, *M;      // [nbox][ni][ni]; M holds the LU of I - B33 A33
-  int *Mpiv;                   // [nbox][ni]
-  double2 *R;                  // [nbox][np][np]  parent impedance-to-impedance maps
 };
+
+// Operators stored per level for the sweeps (C = double2 or float2).
+template <typename C> struct LevelOps {
+  C* XZ;      // [nbox][2 ni][np]  interface impedances from the parent's: [X; Z]
+  C* U2;      // [nbox][np][2 ni]  interface -> parent outgoing impedance
+  C *A33, *B33, *M;  // [nbox][ni][ni]; M holds the LU of I - B33 A33
+  int* Mpiv;  // [nbox][ni]
+  C* R;       // [nbox][np][np]  parent impedance-to-impedance maps
+};
+
+// Legacy FP64 view used by the FP64 path.
+struct Level : LevelMaps, LevelOps<double2> {};
 
 void upload_cheb_diff(const double* D1, cudaStream_t s);
 void sine_eval_grid(cudaStream_t s, const double* c, int S1, int S2, const double* xg, int nL, double* sx,
                     double* sy, double* T, double* Qg, double* q, int* bad);
 void check_q(cudaStream_t s, const double* q, long long n, int* bad);
-void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, double h, LeafScratch& w,
-                      double2* R, double2* Y, double2* Q, int* info);
+template <typename T>
+void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, double h, LeafScratchT<T>& w,
+                      typename prec<T>::C* R, typename prec<T>::C* Y, typename prec<T>::C* Q, int* info);
 
-void merge_level(cudaStream_t s, const Level& L, const double2* Rc, int* info);
-void sweep_down_level(cudaStream_t s, const Level& L, const double2* Fp, double2* T3, double2* Fc, int nrhs);
-void sweep_adjoint_level(cudaStream_t s, const Level& L, const double2* Lp, double2* MU, double2* Lc, int nrhs);
+template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Rc, int* info);
+// Downward sweep of one level.  If t3_loaded, T3 already holds the particular
+// interface impedances [t_a; t_b] of the upward pass and is added to.
+template <typename C>
+void sweep_down_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Fp, C* T3, C* Fc, int nrhs,
+                      bool t3_loaded);
+template <typename C>
+void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lp, C* MU, C* Lc,
+                         int nrhs);
+// Upward (particular) pass of one level: children's outgoing particular
+// impedances Hc and the interface residual terms S3 ([s_a; s_b] per box, or
+// NULL) give the particular interface impedances TT = [t_a; t_b] (kept for the
+// downward pass) and the parent's particular impedances Hp.
+template <typename C>
+void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Hc, const C* S3, C* TT, C* Hp,
+                    int nrhs);
+
+// Compatibility wrappers for the FP64 path.
+inline void merge_level(cudaStream_t s, const Level& L, const double2* Rc, int* info) {
+  merge_level<double2>(s, L, L, Rc, info);
+}
+inline void sweep_down_level(cudaStream_t s, const Level& L, const double2* Fp, double2* T3, double2* Fc, int nrhs) {
+  sweep_down_level<double2>(s, L, L, Fp, T3, Fc, nrhs, false);
+}
+inline void sweep_adjoint_level(cudaStream_t s, const Level& L, const double2* Lp, double2* MU, double2* Lc, int nrhs) {
+  sweep_adjoint_level<double2>(s, L, L, Lp, MU, Lc, nrhs);
+}
 
 // Boundary integral part (bie.cu)
 struct Boundary {
@@ -78,5 +113,21 @@ void add_lambda(cudaStream_t s, double* A, int n, double lambda_rel);
 void gradient_combine(cudaStream_t s, const double2* Ug, const double2* Zmix, int M, long long npts, double* hre);
 void conj_neg(cudaStream_t s, double2* v, int n);
 void half_in_place(cudaStream_t s, double* v);
+
+// Mixed-precision refinement pieces (refine.cu)
+void convert_d2f(cudaStream_t s, const double2* a, float2* b, long long n);
+void convert_f2d_add(cudaStream_t s, const float2* a, double2* b, long long n);  // b += a
+// D1: device copy of the 16 x 16 Chebyshev-Lobatto differentiation matrix on [-1, 1].
+void residual_pde(cudaStream_t s, const double2* X, const double* q, const double* D1, int nleaf, double k, double h,
+                  int nrhs, float2* RP);
+void residual_iface(cudaStream_t s, const LevelMaps& L, const double2* X, const double* D1, int nL, double h,
+                    double eta, int nrhs, float2* S3);
+void boundary_gather(cudaStream_t s, const double2* X, const double* D1, int nL, double h, int nrhs, double2* ub,
+                     double2* psib);
+void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, double eta, int nrhs, float2* Upart,
+                     float2* H, float2* tmp);
+void scattered_data(cudaStream_t s, const double2* ub, const double2* psib, const double2* ui, const double2* dni,
+                    long long n, double2* PS);
+void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out);  // out += {|a-b|^2, |a|^2}
 
 }  // namespace hs

@@ -1,0 +1,106 @@
+"""Mixed precision: FP32 factors and sweeps, FP64 iterative refinement.
+
+The bar (the stated mixed-precision target): far field within 1e-8 (relative
+2-norm) of the FP64 result, against both the FP64 GPU path and the CPU oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import forward as F
+
+pytestmark = pytest.mark.gpu
+MIXED_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def hs():
+    from paper_1608_06871_gb300.build import build
+    build()
+    import paper_1608_06871_gb300 as mod
+    return mod
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
+
+
+def test_mixed_gaussian_bumps_k5_vs_oracle(hs):
+    w = synth.WORKLOADS["gn_k5"]
+    qt = synth.gaussian_bumps(1)
+    al, th = synth.directions(w.M), synth.receivers(w.P)
+    S = hs.Solver(w.n_leaf_side, 2, 2, w.R, precision=hs.HS_MIXED)
+    x, y = S.node_coords()
+    S.build_nodes(qt(x, y), w.k)
+    uf = S.solve(al, th)
+    it, upd = hs.hs_refine_stats(S.ctx)
+    ref, _ = F.forward_from_function(qt, w.k, w.n_leaf_side, w.R).solve_plane(al, th)
+    assert rel(uf, ref) < MIXED_TOL
+    assert 2 <= it <= 8 and 0 <= upd <= 1e-11
+
+
+@pytest.mark.parametrize("nL,k,M,P", [(1, 3.0, 3, 5), (2, 4.0, 2, 9), (8, 9.3, 5, 7)])
+def test_mixed_matches_fp64_ragged(hs, nL, k, M, P):
+    c = synth.random_coeffs(5, 4, seed=31, scale=0.05)
+    al, th = np.linspace(0.1, 6.0, M), np.linspace(0.2, 6.1, P)
+    u64 = hs.Solver(nL, 5, 4).build(c, k).solve(al, th)
+    u32 = hs.Solver(nL, 5, 4, precision=hs.HS_MIXED).build(c, k).solve(al, th)
+    assert rel(u32, u64) < MIXED_TOL
+
+
+def test_mixed_full_size_k40_matches_fp64(hs):
+    """The benchmark workload: k = 40, 32 x 32 leaves, 128 incidences, 256 receivers."""
+    w = synth.WORKLOADS["fwd_k40"]
+    c = synth.smooth_random_coeffs(w.S, seed=2, qmax=0.3)
+    al, th = synth.directions(w.M), synth.receivers(w.P)
+    u64 = hs.Solver(w.n_leaf_side, w.S, w.S, w.R).build(c, w.k).solve(al, th)
+    S = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, precision=hs.HS_MIXED).build(c, w.k)
+    u32 = S.solve(al, th)
+    assert rel(u32, u64) < MIXED_TOL
+
+
+def test_mixed_fields_match_fp64(hs):
+    import torch
+    c = synth.random_coeffs(4, 4, seed=32, scale=0.05)
+    k, nL, M = 6.0, 4, 3
+    al = torch.tensor(synth.directions(M), device="cuda")
+    out = []
+    for prec in (hs.HS_FP64, hs.HS_MIXED):
+        S = hs.Solver(nL, 4, 4, precision=prec).build(c, k)
+        u = torch.zeros((M, nL * nL, 256, 2), dtype=torch.float64, device="cuda")
+        hs.hs_fields_dev(S.ctx, al, u)
+        torch.cuda.synchronize()
+        out.append(u.cpu().numpy())
+    assert rel(out[1], out[0]) < MIXED_TOL
+
+
+def test_forward_dev_both_precisions(hs):
+    """hs_forward_dev returns the far field of hs_solve and the fields of hs_fields_dev in one call."""
+    import torch
+    c = synth.random_coeffs(4, 4, seed=33, scale=0.05)
+    k, nL, M, P = 5.5, 4, 4, 6
+    al_np, th_np = synth.directions(M), synth.receivers(P)
+    al, th = torch.tensor(al_np, device="cuda"), torch.tensor(th_np, device="cuda")
+    res = {}
+    for prec in (hs.HS_FP64, hs.HS_MIXED):
+        S = hs.Solver(nL, 4, 4, precision=prec).build(c, k)
+        uf = torch.zeros((M, P, 2), dtype=torch.float64, device="cuda")
+        u = torch.zeros((M, nL * nL, 256, 2), dtype=torch.float64, device="cuda")
+        hs.hs_forward_dev(S.ctx, al, th, uf, u)
+        u2 = torch.zeros_like(u)
+        hs.hs_fields_dev(S.ctx, al, u2)
+        torch.cuda.synchronize()
+        ufn = uf.cpu().numpy()
+        res[prec] = (ufn[..., 0] + 1j * ufn[..., 1], u.cpu().numpy())
+        assert rel(res[prec][0], S.solve(al_np, th_np)) < 1e-12
+        assert rel(res[prec][1], u2.cpu().numpy()) < 1e-12
+    ref, _ = F.forward_from_coeffs(c, k, nL).solve_plane(al_np, th_np)
+    assert rel(res[hs.HS_FP64][0], ref) < 1e-10
+    assert rel(res[hs.HS_MIXED][0], ref) < MIXED_TOL
+
+
+def test_fp64_only_calls_reject_mixed_context(hs):
+    S = hs.Solver(2, 2, 2, precision=hs.HS_MIXED).build(np.zeros((2, 2)), 3.0)
+    with pytest.raises(hs.HSError) as e:
+        S.jacobian([0.0], [0.0])
+    assert e.value.code == hs.HS_EINVAL

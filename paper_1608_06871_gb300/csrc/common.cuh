@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace hs {
@@ -123,3 +124,11 @@ extern thread_local long long* g_launch_counter;
   do {                                           \
     if (hs::g_launch_counter) ++(*hs::g_launch_counter); \
   } while (0)
+
+// Named phase of the host orchestration, visible to profilers (NVTX range).
+namespace hs {
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+};
+}  // namespace hs

@@ -142,6 +142,10 @@ struct hs_ctx {
   const float2* Rroot32 = nullptr;
   int refine_iters = 0;
   double refine_update = 0.0;
+  double bie_k = -1.0;  // wavenumber the layer-potential matrices were assembled for
+  int *d_root_of_bie = nullptr, *d_bie_of_root = nullptr;  // root box order <-> boundary-node order
+  double2* d_Rb = nullptr;  // root ItI map in boundary-node order (FP64)
+  float2* d_Rb32 = nullptr; // same, FP32
   // per-call workspace
   char* ws_base = nullptr;
   size_t ws_cap = 0;
@@ -213,36 +217,94 @@ int check_info(hs_ctx* ctx) {
 }
 
 // Tree bookkeeping: merge levels from leaves (1 x 1) to the root (nL x nL).
+//
+// Every leaf-edge node has a physical id: vertical edge lines x = i (i = 0..nL)
+// at leaf row iy, or horizontal lines y = j at leaf column ix, node t = 1..14.
+// A box's boundary is an ordered list of ids; a leaf lists S, E, N, W (each by
+// increasing coordinate), and a parent lists its alpha child's exterior nodes
+// then its beta child's, so every side stays in increasing coordinate order.
+// The maps of one level are computed on the first pair of boxes and hold for
+// every pair by translation.
+struct TreeIds {
+  int nL;
+  int v(int i, int iy, int t) const { return (i * nL + iy) * 14 + t - 1; }
+  int h(int j, int ix, int t) const { return (nL + 1) * nL * 14 + (j * nL + ix) * 14 + t - 1; }
+  std::vector<int> leaf(int ix, int iy) const {
+    std::vector<int> l;
+    for (int t = 1; t <= 14; ++t) l.push_back(h(iy, ix, t));      // S
+    for (int t = 1; t <= 14; ++t) l.push_back(v(ix + 1, iy, t));  // E
+    for (int t = 1; t <= 14; ++t) l.push_back(h(iy + 1, ix, t));  // N
+    for (int t = 1; t <= 14; ++t) l.push_back(v(ix, iy, t));      // W
+    return l;
+  }
+};
+
+struct MergeMap {
+  std::vector<int> parent, I3a, I3b, src;
+  int n1 = 0;
+};
+
+MergeMap merge_lists(const std::vector<int>& a, const std::vector<int>& b) {
+  MergeMap m;
+  std::vector<int> pos_b_sorted(b.size());
+  auto find = [](const std::vector<int>& l, int id) {
+    for (size_t i = 0; i < l.size(); ++i)
+      if (l[i] == id) return (int)i;
+    return -1;
+  };
+  std::vector<char> b_shared(b.size(), 0);
+  std::vector<int> ext_a;
+  for (size_t i = 0; i < a.size(); ++i) {
+    int j = find(b, a[i]);
+    if (j >= 0) {
+      m.I3a.push_back((int)i);
+      m.I3b.push_back(j);
+      b_shared[j] = 1;
+    } else {
+      ext_a.push_back((int)i);
+    }
+  }
+  for (int i : ext_a) {
+    m.parent.push_back(a[i]);
+    m.src.push_back(i);
+  }
+  m.n1 = (int)ext_a.size();
+  for (size_t j = 0; j < b.size(); ++j)
+    if (!b_shared[j]) {
+      m.parent.push_back(b[j]);
+      m.src.push_back((1 << 20) | (int)j);
+    }
+  return m;
+}
+
+// Boundary id list of box (px, py) at box level bl (0 = leaves; odd levels
+// come from horizontal merges, even levels >= 2 from vertical ones).
+std::vector<int> box_list(const TreeIds& g, int bl, int px, int py) {
+  if (bl == 0) return g.leaf(px, py);
+  const bool horiz = (bl % 2) == 1;
+  std::vector<int> a = horiz ? box_list(g, bl - 1, 2 * px, py) : box_list(g, bl - 1, px, 2 * py);
+  std::vector<int> b = horiz ? box_list(g, bl - 1, 2 * px + 1, py) : box_list(g, bl - 1, px, 2 * py + 1);
+  return merge_lists(a, b).parent;
+}
+
 int setup_tree(hs_ctx* ctx) {
   const int nL = ctx->nL;
-  int sx = 1, sy = 1;
+  TreeIds g{nL};
+  int sx = 1, sy = 1, bl = 0;
   bool horiz = true;
   while (sx < nL || sy < nL) {
     Level L{};
     L.horiz = horiz;
     L.sx = sx;
     L.sy = sy;
-    const int nS = 14 * sx, nE = 14 * sy, nN = 14 * sx, nW = 14 * sy;
-    const int offS = 0, offE = nS, offN = nS + nE, offW = nS + nE + nN;
-    L.nc = nS + nE + nN + nW;
-    std::vector<int> src, I3a, I3b;
-    auto add = [&](int child, int off, int n) {
-      for (int i = 0; i < n; ++i) src.push_back((child << 20) | (off + i));
-    };
-    int psx, psy;
-    if (horiz) {
-      for (int i = 0; i < nE; ++i) I3a.push_back(offE + i);
-      for (int i = 0; i < nW; ++i) I3b.push_back(offW + i);
-      add(0, offS, nS); add(1, offS, nS); add(1, offE, nE); add(0, offN, nN); add(1, offN, nN); add(0, offW, nW);
-      psx = 2 * sx; psy = sy;
-    } else {
-      for (int i = 0; i < nN; ++i) I3a.push_back(offN + i);
-      for (int i = 0; i < nS; ++i) I3b.push_back(offS + i);
-      add(0, offS, nS); add(0, offE, nE); add(1, offE, nE); add(1, offN, nN); add(0, offW, nW); add(1, offW, nW);
-      psx = sx; psy = 2 * sy;
-    }
-    L.ni = (int)I3a.size();
-    L.np = (int)src.size();
+    std::vector<int> la = box_list(g, bl, 0, 0);
+    std::vector<int> lb = horiz ? box_list(g, bl, 1, 0) : box_list(g, bl, 0, 1);
+    MergeMap mm = merge_lists(la, lb);
+    const int psx = horiz ? 2 * sx : sx, psy = horiz ? sy : 2 * sy;
+    L.nc = (int)la.size();
+    L.ni = (int)mm.I3a.size();
+    L.np = (int)mm.src.size();
+    L.n1 = mm.n1;
     const int nbx_c = nL / sx, nbx_p = nL / psx, nby_p = nL / psy;
     L.nbox = nbx_p * nby_p;
     std::vector<int> al(L.nbox), be(L.nbox);
@@ -264,14 +326,14 @@ int setup_tree(hs_ctx* ctx) {
     CKR(dalloc(ctx, &L.d_I3b, L.ni));
     CK(cudaMemcpy(L.d_alpha, al.data(), sizeof(int) * L.nbox, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(L.d_beta, be.data(), sizeof(int) * L.nbox, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(L.d_src, src.data(), sizeof(int) * L.np, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(L.d_I3a, I3a.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(L.d_I3b, I3b.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_src, mm.src.data(), sizeof(int) * L.np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_I3a, mm.I3a.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_I3b, mm.I3b.data(), sizeof(int) * L.ni, cudaMemcpyHostToDevice));
     const size_t nb = L.nbox;
     L.nbx_p = nbx_p;
     if (ctx->cfg.precision == HS_FP64) {
       CKR(dalloc(ctx, &L.XZ, nb * 2 * L.ni * L.np));
-      CKR(dalloc(ctx, &L.U2, nb * 2 * L.ni * L.np));
+      CKR(dalloc(ctx, &L.U2, nb * L.ni * L.np));
       CKR(dalloc(ctx, &L.A33, nb * L.ni * L.ni));
       CKR(dalloc(ctx, &L.B33, nb * L.ni * L.ni));
       CKR(dalloc(ctx, &L.M, nb * L.ni * L.ni));
@@ -280,7 +342,7 @@ int setup_tree(hs_ctx* ctx) {
     } else {
       LevelOps<float2> O{};
       CKR(dalloc(ctx, &O.XZ, nb * 2 * L.ni * L.np));
-      CKR(dalloc(ctx, &O.U2, nb * 2 * L.ni * L.np));
+      CKR(dalloc(ctx, &O.U2, nb * L.ni * L.np));
       CKR(dalloc(ctx, &O.A33, nb * L.ni * L.ni));
       CKR(dalloc(ctx, &O.B33, nb * L.ni * L.ni));
       CKR(dalloc(ctx, &O.M, nb * L.ni * L.ni));
@@ -292,7 +354,37 @@ int setup_tree(hs_ctx* ctx) {
     sx = psx;
     sy = psy;
     horiz = !horiz;
+    ++bl;
   }
+  // Root order vs the order of the boundary nodes of the exterior equations
+  // (S, E, N, W sides, each by increasing coordinate): root_of_bie[j] is the
+  // root position of boundary node j, bie_of_root its inverse.
+  std::vector<int> root = box_list(g, bl, 0, 0);
+  std::vector<int> bie;
+  for (int i = 0; i < nL; ++i)
+    for (int t = 1; t <= 14; ++t) bie.push_back(g.h(0, i, t));
+  for (int i = 0; i < nL; ++i)
+    for (int t = 1; t <= 14; ++t) bie.push_back(g.v(nL, i, t));
+  for (int i = 0; i < nL; ++i)
+    for (int t = 1; t <= 14; ++t) bie.push_back(g.h(nL, i, t));
+  for (int i = 0; i < nL; ++i)
+    for (int t = 1; t <= 14; ++t) bie.push_back(g.v(0, i, t));
+  const int nb = (int)bie.size();
+  if ((int)root.size() != nb) return fail(ctx, HS_EINVAL, "internal: root boundary size mismatch");
+  std::vector<int> root_of_bie(nb, -1), bie_of_root(nb, -1);
+  for (int j = 0; j < nb; ++j) {
+    for (int r = 0; r < nb; ++r)
+      if (root[r] == bie[j]) {
+        root_of_bie[j] = r;
+        bie_of_root[r] = j;
+        break;
+      }
+    if (root_of_bie[j] < 0) return fail(ctx, HS_EINVAL, "internal: boundary node missing from the root");
+  }
+  CKR(dalloc(ctx, &ctx->d_root_of_bie, nb));
+  CKR(dalloc(ctx, &ctx->d_bie_of_root, nb));
+  CK(cudaMemcpy(ctx->d_root_of_bie, root_of_bie.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_bie_of_root, bie_of_root.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
   return HS_OK;
 }
 
@@ -393,7 +485,9 @@ int setup_boundary(hs_ctx* ctx) {
   if (ctx->cfg.precision == HS_FP64) {
     CKR(dalloc(ctx, &ctx->d_C, nn));
     CKR(dalloc(ctx, &ctx->d_Cpiv, nb));
+    CKR(dalloc(ctx, &ctx->d_Rb, nn));
   } else {
+    CKR(dalloc(ctx, &ctx->d_Rb32, nn));
     CKR(dalloc(ctx, &ctx->d_B2_32, nn));
     CKR(dalloc(ctx, &ctx->d_C32, nn));
     CKR(dalloc(ctx, &ctx->d_Cpiv32, nb));
@@ -477,6 +571,7 @@ int setup(hs_ctx* ctx) {
 int factor_mixed(hs_ctx* ctx, double k) {
   cudaStream_t s = ctx->stream;
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  Phase ph("hs_factor_mixed");
   leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32, nullptr,
                           ctx->d_info);
   const float2* Rc = ctx->d_R32;
@@ -484,13 +579,17 @@ int factor_mixed(hs_ctx* ctx, double k) {
     merge_level<float2>(s, ctx->levels[li], ctx->ops32[li], Rc, ctx->d_info);
     Rc = ctx->ops32[li].R;
   }
-  ctx->Rroot32 = Rc;
   const int nb = ctx->B.nb;
+  permute_square<float2>(s, Rc, ctx->d_root_of_bie, nb, ctx->d_Rb32);  // root map in boundary-node order
+  ctx->Rroot32 = ctx->d_Rb32;
   const long long nn = (long long)nb * nb;
-  bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
-  bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
+  if (ctx->bie_k != k) {  // S, D - I/2, B1, B2 depend on k and the boundary only
+    bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
+    bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
+    convert_d2f(s, ctx->d_B2, ctx->d_B2_32, nn);
+    ctx->bie_k = k;
+  }
   convert_d2f(s, ctx->d_B1, ctx->d_C32, nn);
-  convert_d2f(s, ctx->d_B2, ctx->d_B2_32, nn);
   gemm<float2, float2, float2>(s, OP_N, OP_N, nb, nb, nb, make_float2(-1.f, 0.f), ctx->d_B2_32, nb, 0, ctx->Rroot32,
                                nb, 0, make_float2(1.f, 0.f), ctx->d_C32, nb, 0, 1);
   lu_factor<float2>(s, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, ctx->d_info, 1);
@@ -506,20 +605,29 @@ int factor(hs_ctx* ctx, double k) {
   if (ctx->cfg.precision == HS_MIXED) return factor_mixed(ctx, k);
   cudaStream_t s = ctx->stream;
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  Phase ph("hs_factor_fp64");
   for (int l0 = 0; l0 < ctx->nleaf; l0 += ctx->chunk) {
     int n = std::min(ctx->chunk, ctx->nleaf - l0);
     leaf_build_chunk(s, ctx->d_q, l0, n, k, ctx->h, ctx->ws, ctx->d_Rleaf + (size_t)l0 * NE * NE,
                      ctx->d_Y + (size_t)l0 * NL * NE, ctx->d_Q + (size_t)l0 * NI * NE, ctx->d_info);
   }
   const double2* Rc = ctx->d_Rleaf;
-  for (auto& L : ctx->levels) {
-    merge_level(s, L, Rc, ctx->d_info);
-    Rc = L.R;
+  {
+    Phase pm("hs_merges");
+    for (auto& L : ctx->levels) {
+      merge_level(s, L, Rc, ctx->d_info);
+      Rc = L.R;
+    }
   }
-  ctx->Rroot = Rc;
+  Phase pr("hs_root_coupling");
   const int nb = ctx->B.nb;
-  bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
-  bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
+  permute_square<double2>(s, Rc, ctx->d_root_of_bie, nb, ctx->d_Rb);  // root map in boundary-node order
+  ctx->Rroot = ctx->d_Rb;
+  if (ctx->bie_k != k) {  // S, D - I/2, B1, B2 depend on k and the boundary only
+    bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
+    bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
+    ctx->bie_k = k;
+  }
   // C = B1 - B2 R_root   (coupling of the interior impedances to the exterior identity)
   CK(cudaMemcpyAsync(ctx->d_C, ctx->d_B1, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, s));
   gemm<double2, double2, double2>(s, OP_N, OP_N, nb, nb, nb, make_double2(-1, 0), ctx->d_B2, nb, 0, ctx->Rroot, nb, 0,
@@ -549,7 +657,9 @@ int root_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, double2
 // Downward sweep from root impedances f (nb x nrhs) to leaf fields (nleaf x 252 x nrhs).
 int sweep_down(hs_ctx* ctx, cudaStream_t s, const double2* f, int nrhs, double2* bufA, double2* bufB, double2* T3,
                double2* Uleaf) {
-  const double2* Fp = f;
+  Phase ph("hs_sweep_down");
+  permute_rows<double2>(s, f, ctx->d_bie_of_root, ctx->B.nb, nrhs, bufB);  // root box order
+  const double2* Fp = bufB;
   double2* out = bufA;
   for (int li = (int)ctx->levels.size() - 1; li >= 0; --li) {
     const Level& L = ctx->levels[li];
@@ -568,11 +678,13 @@ int sweep_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2
                   double2* bufB, double2* MU, double2* Zleaf) {
   const int nb = ctx->B.nb;
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  Phase ph("hs_adjoint_sweep");
   adjoint_root_init(s, nb, P, ctx->k, A2, E, CP);
   gemm<double2, double2, double2>(s, OP_T, OP_N, nb, P, nb, one, ctx->Rroot, nb, 0, E, P, 0, one, CP, P, 0, 1);
   lu_solve<double2>(s, OP_T, ctx->d_C, nb, 0, nb, ctx->d_Cpiv, 0, CP, P, 0, P, 1);
   gemm<double2, double2, double2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_B2, nb, 0, CP, P, 0, one, E, P, 0, 1);
-  const double2* Lp = E;
+  permute_rows<double2>(s, E, ctx->d_bie_of_root, nb, P, bufB);  // root box order
+  const double2* Lp = bufB;
   double2* out = bufA;
   for (int li = (int)ctx->levels.size() - 1; li >= 0; --li) {
     const Level& L = ctx->levels[li];
@@ -691,6 +803,7 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   ctx->refine_update = -1.0;
   bool converged = false;
   for (int it = 0; it < max_iter; ++it) {
+    Phase pp("hs_refine_pass");
     if (it == 0) {
       convert_d2f(s, rinc, f32, (long long)nbM);
     } else {
@@ -709,12 +822,14 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
         sweep_up_level<float2>(s, ctx->levels[li], ctx->ops32[li], Hc, S3, TT[li], Hp, M);
         std::swap(Hc, Hp);
       }
+      permute_rows<float2>(s, Hc, ctx->d_root_of_bie, nb, M, tmp);  // root h in boundary-node order
       CK(cudaMemcpyAsync(f32, r32, sizeof(float2) * nbM, cudaMemcpyDeviceToDevice, s));
-      gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_B2_32, nb, 0, Hc, M, 0, fone, f32, M, 0, 1);
+      gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_B2_32, nb, 0, tmp, M, 0, fone, f32, M, 0, 1);
     }
     lu_solve<float2>(s, OP_N, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, f32, M, 0, M, 1);
     // downward sweep (adds the particular interface impedances after the first pass)
-    const float2* Fp = f32;
+    permute_rows<float2>(s, f32, ctx->d_bie_of_root, nb, M, B1);  // root box order
+    const float2* Fp = B1;
     float2* out = B0;
     for (int li = nlev - 1; li >= 0; --li) {
       sweep_down_level<float2>(s, ctx->levels[li], ctx->ops32[li], Fp, TT[li], out, M, it > 0);
@@ -789,6 +904,7 @@ int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, cons
   interior_sine_tables(s, ctx->d_xint, ctx->n14, ctx->S1, ctx->S2, ctx->d_sxi, ctx->d_syi);
   size_t smem = sizeof(double2) * ((size_t)ctx->S1 * ctx->S2 + ctx->n14 + ctx->S1);
   if (smem > 200 * 1024) return fail(ctx, HS_EINVAL, "S1*S2 too large for the Jacobian contraction");
+  Phase ph("hs_jacobian_contract");
   contract_jacobian(s, Ug, Zg, M, P, ctx->n14, ctx->d_sxi, ctx->d_syi, ctx->S1, ctx->S2, ctx->k * ctx->k, J);
   CK(cudaGetLastError());
   return HS_OK;

@@ -86,73 +86,93 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, in
 }
 
 // Panel factorisation of columns [j0, j0+nb) with partial pivoting; row swaps
-// are applied to whole rows.  One CTA per matrix.
+// are applied to whole rows.  One CTA per matrix; per column: a warp-shuffle
+// argmax over the rows, the row swap, the scaling and the rank-1 update of the
+// rest of the panel.
+constexpr int PANEL_THREADS = 512;
 template <typename E>
-__global__ void __launch_bounds__(256) k_lu_panel(E* A, int lda, long long sA, int n, int j0, int nb, int* piv,
-                                                  long long sP, int* info) {
-  __shared__ double smag[256];
-  __shared__ int sidx[256];
+__global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(E* A, int lda, long long sA, int n, int j0, int nb,
+                                                            int* piv, long long sP, int* info) {
+  __shared__ double wmag[PANEL_THREADS / 32];
+  __shared__ int widx[PANEL_THREADS / 32];
+  __shared__ int s_p;
+  __shared__ int s_zero;
   const int b = blockIdx.x;
   A += b * sA;
   piv += b * sP;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int j = j0; j < j0 + nb; ++j) {
     double best = -1.0;
     int bi = j;
-    for (int r = j + t; r < n; r += 256) {
+    for (int r = j + t; r < n; r += PANEL_THREADS) {
       double v = el<E>::mag2(A[(long long)r * lda + j]);
       if (v > best) { best = v; bi = r; }
     }
-    smag[t] = best;
-    sidx[t] = bi;
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { wmag[warp] = best; widx[warp] = bi; }
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (t < s) {
-        if (smag[t + s] > smag[t] || (smag[t + s] == smag[t] && sidx[t + s] < sidx[t])) {
-          smag[t] = smag[t + s];
-          sidx[t] = sidx[t + s];
-        }
+    if (warp == 0) {
+      best = lane < PANEL_THREADS / 32 ? wmag[lane] : -1.0;
+      bi = lane < PANEL_THREADS / 32 ? widx[lane] : n;
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      __syncthreads();
+      if (lane == 0) {
+        s_p = bi;
+        s_zero = !(best > 0.0);
+        piv[j] = bi;
+        if (s_zero && info[b] == 0) info[b] = j + 1;
+      }
     }
-    const int p = sidx[0];
-    const bool zero = !(smag[0] > 0.0);
     __syncthreads();
-    if (t == 0) {
-      piv[j] = p;
-      if (zero && info[b] == 0) info[b] = j + 1;
-    }
+    const int p = s_p;
+    const bool zero = s_zero;
     if (p != j) {
-      for (int c = t; c < n; c += 256) {
+      for (int c = t; c < n; c += PANEL_THREADS) {
         E tmp = A[(long long)j * lda + c];
         A[(long long)j * lda + c] = A[(long long)p * lda + c];
         A[(long long)p * lda + c] = tmp;
       }
     }
     __syncthreads();
-    if (!zero) {
-      E pv = A[(long long)j * lda + j];
-      for (int r = j + 1 + t; r < n; r += 256) A[(long long)r * lda + j] = el<E>::div(A[(long long)r * lda + j], pv);
-    }
-    __syncthreads();
     const int w = j0 + nb - 1 - j;  // remaining panel columns
-    if (w > 0) {
-      const long long tot = (long long)(n - j - 1) * w;
-      for (long long e = t; e < tot; e += 256) {
-        int r = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
-        A[(long long)r * lda + c] = A[(long long)r * lda + c] - mul(A[(long long)r * lda + j], A[(long long)j * lda + c]);
+    if (!zero) {
+      const E pv = A[(long long)j * lda + j];
+      // scale the column and update the panel in one pass over the rows below j
+      for (int r = j + 1 + t; r < n; r += PANEL_THREADS) {
+        E l = el<E>::div(A[(long long)r * lda + j], pv);
+        A[(long long)r * lda + j] = l;
+        for (int c = 1; c <= w; ++c)
+          A[(long long)r * lda + j + c] = A[(long long)r * lda + j + c] - mul(l, A[(long long)j * lda + j + c]);
       }
     }
     __syncthreads();
   }
 }
 
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double2 shfl(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float2 shfl(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
 // Triangular solve with a diagonal block of size nb <= NB for many right-hand
-// sides (one thread per column).  mode: 0 = L (unit lower), 1 = U (upper),
-// 2 = U^T (lower, non-unit), 3 = L^T (upper, unit).
+// sides: one warp per right-hand side, lane r holding x_r; each substitution
+// step broadcasts the finished unknown with a shuffle.  mode: 0 = L (unit
+// lower), 1 = U (upper), 2 = U^T (lower, non-unit), 3 = L^T (upper, unit).
+constexpr int TRSM_WARPS = 4;
 template <typename E>
-__global__ void __launch_bounds__(128) k_trsm_diag(const E* A, int lda, long long sA, int i0, int nb, int mode, E* B,
-                                                   int ldb, long long sB, int nrhs) {
+__global__ void __launch_bounds__(32 * TRSM_WARPS) k_trsm_diag(const E* A, int lda, long long sA, int i0, int nb,
+                                                              int mode, E* B, int ldb, long long sB, int nrhs) {
   __shared__ E T[NB][NB + 1];
   const int b = blockIdx.y;
   A += b * sA;
@@ -163,26 +183,34 @@ __global__ void __launch_bounds__(128) k_trsm_diag(const E* A, int lda, long lon
     T[r][c] = tr ? A[(long long)(i0 + c) * lda + i0 + r] : A[(long long)(i0 + r) * lda + i0 + c];
   }
   __syncthreads();
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= nrhs) return;
-  E x[NB];
-  for (int r = 0; r < nb; ++r) x[r] = B[(long long)(i0 + r) * ldb + col];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * TRSM_WARPS + warp;
+  if (col >= nrhs) return;  // whole warp leaves together
+  E x = lane < nb ? B[(long long)(i0 + lane) * ldb + col] : el<E>::zero();
   const bool lower = (mode == 0 || mode == 2);
   const bool unit = (mode == 0 || mode == 3);
   if (lower) {
-    for (int r = 0; r < nb; ++r) {
-      E v = x[r];
-      for (int s = 0; s < r; ++s) v = v - mul(T[r][s], x[s]);
-      x[r] = unit ? v : el<E>::div(v, T[r][r]);
+    for (int s = 0; s < nb; ++s) {
+      if (!unit && lane == s) x = el<E>::div(x, T[s][s]);
+      E xs = shfl(x, s);
+      if (lane > s && lane < nb) x = x - mul(T[lane][s], xs);
     }
   } else {
-    for (int r = nb - 1; r >= 0; --r) {
-      E v = x[r];
-      for (int s = r + 1; s < nb; ++s) v = v - mul(T[r][s], x[s]);
-      x[r] = unit ? v : el<E>::div(v, T[r][r]);
+    for (int s = nb - 1; s >= 0; --s) {
+      if (!unit && lane == s) x = el<E>::div(x, T[s][s]);
+      E xs = shfl(x, s);
+      if (lane < s) x = x - mul(T[lane][s], xs);
     }
   }
-  for (int r = 0; r < nb; ++r) B[(long long)(i0 + r) * ldb + col] = x[r];
+  if (lane < nb) B[(long long)(i0 + lane) * ldb + col] = x;
+}
+
+template <typename E>
+void trsm_diag(cudaStream_t s, const E* A, int lda, long long sA, int i0, int nb, int mode, E* B, int ldb,
+               long long sB, int nrhs, int batch) {
+  dim3 g((nrhs + TRSM_WARPS - 1) / TRSM_WARPS, batch);
+  k_trsm_diag<E><<<g, 32 * TRSM_WARPS, 0, s>>>(A, lda, sA, i0, nb, mode, B, ldb, sB, nrhs);
+  HS_COUNT_LAUNCH();
 }
 
 template <typename E>
@@ -231,13 +259,11 @@ template <typename E>
 void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info, int batch) {
   for (int j0 = 0; j0 < n; j0 += NB) {
     int nb = n - j0 < NB ? n - j0 : NB;
-    k_lu_panel<E><<<batch, 256, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
+    k_lu_panel<E><<<batch, PANEL_THREADS, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
     HS_COUNT_LAUNCH();
     int rest = n - j0 - nb;
     if (rest > 0) {
-      dim3 g((rest + 127) / 128, batch);
-      k_trsm_diag<E><<<g, 128, 0, s>>>(A, lda, sA, j0, nb, 0, A + j0 + nb, lda, sA, rest);
-      HS_COUNT_LAUNCH();
+      trsm_diag<E>(s, A, lda, sA, j0, nb, 0, A + j0 + nb, lda, sA, rest, batch);
       gemm<E, E, E>(s, OP_N, OP_N, rest, rest, nb, -el<E>::one(), A + (long long)(j0 + nb) * lda + j0, lda, sA,
                     A + (long long)j0 * lda + j0 + nb, lda, sA, el<E>::one(),
                     A + (long long)(j0 + nb) * lda + j0 + nb, lda, sA, batch);
@@ -255,8 +281,7 @@ void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int 
     HS_COUNT_LAUNCH();
     for (int i0 = 0; i0 < n; i0 += NB) {  // L y = b
       int nb = n - i0 < NB ? n - i0 : NB;
-      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 0, B, ldb, sB, nrhs);
-      HS_COUNT_LAUNCH();
+      trsm_diag<E>(s, A, lda, sA, i0, nb, 0, B, ldb, sB, nrhs, batch);
       int rest = n - i0 - nb;
       if (rest > 0)
         gemm<E, E, E>(s, OP_N, OP_N, rest, nrhs, nb, m1, A + (long long)(i0 + nb) * lda + i0, lda, sA,
@@ -265,8 +290,7 @@ void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int 
     int last = ((n - 1) / NB) * NB;
     for (int i0 = last; i0 >= 0; i0 -= NB) {  // U x = y
       int nb = n - i0 < NB ? n - i0 : NB;
-      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 1, B, ldb, sB, nrhs);
-      HS_COUNT_LAUNCH();
+      trsm_diag<E>(s, A, lda, sA, i0, nb, 1, B, ldb, sB, nrhs, batch);
       if (i0 > 0)
         gemm<E, E, E>(s, OP_N, OP_N, i0, nrhs, nb, m1, A + i0, lda, sA, B + (long long)i0 * ldb, ldb, sB, one, B,
                       ldb, sB, batch);
@@ -274,8 +298,7 @@ void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int 
   } else {
     for (int i0 = 0; i0 < n; i0 += NB) {  // U^T y = b
       int nb = n - i0 < NB ? n - i0 : NB;
-      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 2, B, ldb, sB, nrhs);
-      HS_COUNT_LAUNCH();
+      trsm_diag<E>(s, A, lda, sA, i0, nb, 2, B, ldb, sB, nrhs, batch);
       int rest = n - i0 - nb;
       if (rest > 0)
         gemm<E, E, E>(s, OP_T, OP_N, rest, nrhs, nb, m1, A + (long long)i0 * lda + i0 + nb, lda, sA,
@@ -284,8 +307,7 @@ void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int 
     int last = ((n - 1) / NB) * NB;
     for (int i0 = last; i0 >= 0; i0 -= NB) {  // L^T w = y
       int nb = n - i0 < NB ? n - i0 : NB;
-      k_trsm_diag<E><<<gs, 128, 0, s>>>(A, lda, sA, i0, nb, 3, B, ldb, sB, nrhs);
-      HS_COUNT_LAUNCH();
+      trsm_diag<E>(s, A, lda, sA, i0, nb, 3, B, ldb, sB, nrhs, batch);
       if (i0 > 0)
         gemm<E, E, E>(s, OP_T, OP_N, i0, nrhs, nb, m1, A + (long long)i0 * lda, lda, sA, B + (long long)i0 * ldb, ldb,
                       sB, one, B, ldb, sB, batch);

@@ -66,26 +66,20 @@ __global__ void k_gather_XZ(const C* __restrict__ Rc, int nc, const int* __restr
   }
 }
 
-// U2 rows: alpha-sourced parent node -> [A13 row, 0], beta-sourced -> [0, B23 row].
+// U2 rows: alpha-sourced parent node r (< n1) -> A13 row, beta-sourced -> B23 row.
 template <typename C>
 __global__ void k_gather_U2(const C* __restrict__ Rc, int nc, const int* __restrict__ alpha,
                             const int* __restrict__ beta, const int* __restrict__ I3a, const int* __restrict__ I3b,
                             const int* __restrict__ src, int ni, int np, C* __restrict__ U2) {
   const int b = blockIdx.y;
-  const long long tot = (long long)np * 2 * ni;
+  const long long tot = (long long)np * ni;
   const C* Ra = Rc + (long long)alpha[b] * nc * nc;
   const C* Rb = Rc + (long long)beta[b] * nc * nc;
   C* out = U2 + b * tot;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(e / (2 * ni)), c = (int)(e % (2 * ni));
+    int r = (int)(e / ni), c = (int)(e % ni);
     int sv = src[r];
-    C v = czero<C>();
-    if (c < ni) {
-      if (src_child(sv) == 0) v = Ra[(long long)src_local(sv) * nc + I3a[c]];
-    } else {
-      if (src_child(sv) == 1) v = Rb[(long long)src_local(sv) * nc + I3b[c - ni]];
-    }
-    out[e] = v;
+    out[e] = src_child(sv) == 0 ? Ra[(long long)src_local(sv) * nc + I3a[c]] : Rb[(long long)src_local(sv) * nc + I3b[c]];
   }
 }
 
@@ -216,8 +210,8 @@ template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const
   k_gather_XZ<C><<<dim3(grid_for(xz, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, L.d_src,
                                                              ni, np, O.XZ);
   HS_COUNT_LAUNCH();
-  k_gather_U2<C><<<dim3(grid_for(xz, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a, L.d_I3b, L.d_src,
-                                                             ni, np, O.U2);
+  k_gather_U2<C><<<dim3(grid_for((long long)np * ni, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a,
+                                                                               L.d_I3b, L.d_src, ni, np, O.U2);
   HS_COUNT_LAUNCH();
   k_gather_diag<C><<<dim3(grid_for(pp, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_src, np, O.R);
   HS_COUNT_LAUNCH();
@@ -232,9 +226,12 @@ template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const
   // bottom = -A33 X - bottom  (Z = -Aa - A33 X)
   gemm<C, C, C>(s, OP_N, OP_N, ni, np, ni, mone, O.A33, ni, nn, O.XZ, np, xz, mone, O.XZ + (long long)ni * np, np, xz,
                 nb);
-  // R = blockdiag + U2 [X; Z]
-  gemm<C, C, C>(s, OP_N, OP_N, np, np, 2 * ni, one, O.U2, 2 * ni, (long long)np * 2 * ni, O.XZ, np, xz, one, O.R, np,
-                pp, nb);
+  // R rows of alpha's exterior += A13 X ; rows of beta's exterior += B23 Z
+  const int n1 = L.n1, n2 = np - L.n1;
+  const long long su = (long long)np * ni;
+  gemm<C, C, C>(s, OP_N, OP_N, n1, np, ni, one, O.U2, ni, su, O.XZ, np, xz, one, O.R, np, pp, nb);
+  gemm<C, C, C>(s, OP_N, OP_N, n2, np, ni, one, O.U2 + (long long)n1 * ni, ni, su, O.XZ + (long long)ni * np, np, xz,
+                one, O.R + (long long)n1 * np, np, pp, nb);
 }
 
 template <typename C>
@@ -256,9 +253,12 @@ void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& 
   const int ni = L.ni, np = L.np, nb = L.nbox;
   const long long nn = (long long)ni * ni, mu = 2LL * ni * nrhs;
   const C one = el<C>::one(), mone = -el<C>::one(), zero = el<C>::zero();
-  // [mu_a; mu_b] = U2^T lambda_p ;  lambda_tb = mu_b
-  gemm<C, C, C>(s, OP_T, OP_N, 2 * ni, nrhs, np, one, O.U2, 2 * ni, (long long)np * 2 * ni, Lp, nrhs,
-                (long long)np * nrhs, zero, MU, nrhs, mu, nb);
+  // mu_a = A13^T lambda_1, mu_b = B23^T lambda_2 ;  lambda_tb = mu_b
+  const int n1 = L.n1, n2 = np - L.n1;
+  const long long su = (long long)np * ni, sl = (long long)np * nrhs;
+  gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, n1, one, O.U2, ni, su, Lp, nrhs, sl, zero, MU, nrhs, mu, nb);
+  gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, n2, one, O.U2 + (long long)n1 * ni, ni, su, Lp + (long long)n1 * nrhs, nrhs,
+                sl, zero, MU + (long long)ni * nrhs, nrhs, mu, nb);
   // lambda_ta = mu_a - A33^T lambda_tb
   gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, ni, mone, O.A33, ni, nn, MU + (long long)ni * nrhs, nrhs, mu, one, MU, nrhs,
                 mu, nb);
@@ -290,16 +290,50 @@ void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, co
   // bottom := -A33 t_a - (h3a - s_b) = t_b
   gemm<C, C, C>(s, OP_N, OP_N, ni, nrhs, ni, mone, O.A33, ni, nn, TT, nrhs, tt, mone, TT + (long long)ni * nrhs, nrhs,
                 tt, nb);
-  // Hp += U2 [t_a; t_b]
-  gemm<C, C, C>(s, OP_N, OP_N, np, nrhs, 2 * ni, one, O.U2, 2 * ni, (long long)np * 2 * ni, TT, nrhs, tt, one, Hp, nrhs,
-                (long long)np * nrhs, nb);
+  // Hp rows of alpha's exterior += A13 t_a ; rows of beta's exterior += B23 t_b
+  const int n1 = L.n1, n2 = np - L.n1;
+  const long long su = (long long)np * ni, sh = (long long)np * nrhs;
+  gemm<C, C, C>(s, OP_N, OP_N, n1, nrhs, ni, one, O.U2, ni, su, TT, nrhs, tt, one, Hp, nrhs, sh, nb);
+  gemm<C, C, C>(s, OP_N, OP_N, n2, nrhs, ni, one, O.U2 + (long long)n1 * ni, ni, su, TT + (long long)ni * nrhs, nrhs, tt,
+                one, Hp + (long long)n1 * nrhs, nrhs, sh, nb);
+}
+
+template <typename C>
+__global__ void k_permute_rows(const C* __restrict__ src, const int* __restrict__ idx, int nrows, int ncols,
+                               C* __restrict__ dst) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nrows * ncols) return;
+  int r = (int)(e / ncols), c = (int)(e % ncols);
+  dst[e] = src[(long long)idx[r] * ncols + c];
+}
+
+template <typename C>
+__global__ void k_permute_square(const C* __restrict__ src, const int* __restrict__ idx, int n, C* __restrict__ dst) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  int r = (int)(e / n), c = (int)(e % n);
+  dst[e] = src[(long long)idx[r] * n + idx[c]];
+}
+
+template <typename C> void permute_rows(cudaStream_t s, const C* src, const int* idx, int nrows, int ncols, C* dst) {
+  long long n = (long long)nrows * ncols;
+  k_permute_rows<C><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, idx, nrows, ncols, dst);
+  HS_COUNT_LAUNCH();
+}
+
+template <typename C> void permute_square(cudaStream_t s, const C* src, const int* idx, int n, C* dst) {
+  long long m = (long long)n * n;
+  k_permute_square<C><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(src, idx, n, dst);
+  HS_COUNT_LAUNCH();
 }
 
 #define HS_INST(C)                                                                                                     \
   template void merge_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, int*);                  \
   template void sweep_down_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool); \
   template void sweep_adjoint_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int);    \
-  template void sweep_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, const C*, C*, C*, int);
+  template void sweep_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, const C*, C*, C*, int); \
+  template void permute_rows<C>(cudaStream_t, const C*, const int*, int, int, C*);                                  \
+  template void permute_square<C>(cudaStream_t, const C*, const int*, int, C*);
 HS_INST(double2)
 HS_INST(float2)
 #undef HS_INST

@@ -26,6 +26,7 @@ using LeafScratch = LeafScratchT<double>;
 struct LevelMaps {
   int horiz, sx, sy;
   int nc, ni, np;              // child boundary size, interface size, parent boundary size
+  int n1;                      // parent nodes from alpha: the parent order is [alpha exterior; beta exterior]
   int nbox, nbx_p;             // parent boxes, parents per row
   int *d_alpha, *d_beta;       // child box ids of each parent
   int *d_src;                  // parent boundary node -> (child << 20) | child-local index
@@ -33,9 +34,11 @@ struct LevelMaps {
 };
 
 // Operators stored per level for the sweeps (C = double2 or float2).
+// Parent boundary nodes are ordered [alpha exterior; beta exterior], so the
+// parent map update R = blockdiag(A11, B22) + [A13 X; B23 Z] is two dense GEMMs.
 template <typename C> struct LevelOps {
   C* XZ;      // [nbox][2 ni][np]  interface impedances from the parent's: [X; Z]
-  C* U2;      // [nbox][np][2 ni]  interface -> parent outgoing impedance
+  C* U2;      // [nbox][np][ni]  rows < n1: A13 (alpha exterior x interface), rows >= n1: B23
   C *A33, *B33, *M;  // [nbox][ni][ni]; M holds the LU of I - B33 A33
   int* Mpiv;  // [nbox][ni]
   C* R;       // [nbox][np][np]  parent impedance-to-impedance maps
@@ -129,5 +132,8 @@ void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, do
 void scattered_data(cudaStream_t s, const double2* ub, const double2* psib, const double2* ui, const double2* dni,
                     long long n, double2* PS);
 void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out);  // out += {|a-b|^2, |a|^2}
+// dst[r][:] = src[idx[r]][:] (rows of ncols elements); dst[a][b] = src[idx[a]][idx[b]] for square matrices.
+template <typename C> void permute_rows(cudaStream_t s, const C* src, const int* idx, int nrows, int ncols, C* dst);
+template <typename C> void permute_square(cudaStream_t s, const C* src, const int* idx, int n, C* dst);
 
 }  // namespace hs

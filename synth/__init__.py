@@ -88,6 +88,67 @@ def random_coeffs(S1: int, S2: int, seed: int, scale: float = 1.0) -> np.ndarray
     return scale * rng.standard_normal((S1, S2))
 
 
+@dataclass(frozen=True)
+class EllipsePhantom:
+    """Sum of ellipses with blurred edges: c_i * erfc(rho_i / (sqrt(2) w)) / 2, clipped at `clip`.
+
+    rho_i = (sqrt((x'/a)^2 + (y'/b)^2) - 1) * min(a, b) in the ellipse's frame.
+    """
+
+    centres: np.ndarray
+    axes: np.ndarray
+    angles: np.ndarray
+    contrasts: np.ndarray
+    blur: float
+    clip: float
+
+    def __call__(self, x, y):
+        from scipy.special import erfc
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = np.zeros(np.broadcast(x, y).shape)
+        for (cx, cy), (a, b), th, cval in zip(self.centres, self.axes, self.angles, self.contrasts):
+            ct, st = math.cos(th), math.sin(th)
+            xr = (x - cx) * ct + (y - cy) * st
+            yr = -(x - cx) * st + (y - cy) * ct
+            rho = (np.sqrt((xr / a) ** 2 + (yr / b) ** 2) - 1.0) * min(a, b)
+            out = out + cval * 0.5 * erfc(rho / (math.sqrt(2.0) * self.blur))
+        out = np.minimum(out, self.clip)
+        inside = (np.abs(x) <= 1.0) & (np.abs(y) <= 1.0)
+        return np.where(inside, out, 0.0)
+
+
+def ellipse_phantom(seed: int = 3, n: int = 5, centre_box: float = 0.6, axes=(0.08, 0.35),
+                    contrast=(0.05, 0.3), blur: float = 0.05, clip: float = 0.3) -> EllipsePhantom:
+    """Seeded blurred-ellipse phantom (stand-in for the paper's head/thorax phantoms, Sec. 4)."""
+    rng = np.random.default_rng(seed)
+    return EllipsePhantom(rng.uniform(-centre_box, centre_box, size=(n, 2)), rng.uniform(*axes, size=(n, 2)),
+                          rng.uniform(0.0, math.pi, size=n), rng.uniform(*contrast, size=n), blur, clip)
+
+
+def project_sine(qfun, S1: int, S2: int, nq: int = 256) -> np.ndarray:
+    """Coefficients of the L2 projection of q onto s_m1(x) s_m2(y) on [-1,1]^2 (Gauss-Legendre, nq^2 points).
+
+    The basis is orthogonal with int_{-1}^{1} s_m^2 = 1, so c = int q s_m1 s_m2.
+    """
+    from scipy.special import roots_legendre
+    t, w = roots_legendre(nq)
+    X, Y = np.meshgrid(t, t, indexing="ij")
+    Q = qfun(X, Y) * np.outer(w, w)
+    sx = np.sin(np.outer(np.arange(1, S1 + 1), t + 1.0) * (math.pi / 2.0))
+    sy = np.sin(np.outer(np.arange(1, S2 + 1), t + 1.0) * (math.pi / 2.0))
+    return sx @ Q @ sy.T
+
+
+def add_noise(u: np.ndarray, delta: float, seed: int) -> np.ndarray:
+    """Noisy data of Sec. 4: per incidence row u_d, u_d + delta ||u_d|| / ||eps|| eps, eps = eps1 + i eps2 ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    u = np.asarray(u, dtype=np.complex128)
+    eps = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    scale = delta * np.linalg.norm(u, axis=-1, keepdims=True) / np.linalg.norm(eps, axis=-1, keepdims=True)
+    return u + scale * eps
+
+
 def directions(M: int) -> np.ndarray:
     """Incidence angles alpha_m = 2 pi m / M, m = 0..M-1 (d = (cos, sin))."""
     return 2.0 * math.pi * np.arange(M, dtype=np.float64) / M

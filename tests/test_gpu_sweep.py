@@ -1,0 +1,88 @@
+"""Recursive linearization over frequency (Sec. 3.4) and the autograd misfit (Theorem 3.2)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import forward as F
+from oracle import sweep as OS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hs():
+    from paper_1608_06871_gb300.build import build
+    build()
+    import paper_1608_06871_gb300 as mod
+    return mod
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
+
+
+def _data_fn(qt):
+    cache = {}
+
+    def data_fn(p, al, th):
+        if p.k not in cache:
+            cache[p.k] = F.forward_from_function(qt, p.k, p.leaves_per_side).solve_plane(al, th)[0]
+        return cache[p.k]
+    return data_fn
+
+
+def test_sweep_matches_oracle_sweep(hs):
+    from paper_1608_06871_gb300 import sweep as SW
+    plans = [SW.plan_ceil(k) for k in (2.0, 2.5, 3.0)]
+    plans[0].newton = 2
+    data_fn = _data_fn(synth.gaussian_bumps(7))
+    res = SW.recursive_linearization(plans, data_fn, lambda_rel=1e-4)
+    c_ref, hist = OS.sweep(plans, data_fn, 1e-4)
+    assert rel(res.c, c_ref) < 1e-7
+    for h_gpu, h_ref in zip(res.history, hist):
+        assert np.allclose(h_gpu["residuals"], h_ref, rtol=1e-8)
+
+
+def test_sweep_checkpoint_resume(hs, tmp_path):
+    from paper_1608_06871_gb300 import sweep as SW
+    plans = [SW.plan_ceil(k) for k in (2.0, 2.5, 3.0)]
+    data_fn = _data_fn(synth.gaussian_bumps(8))
+    full = SW.recursive_linearization(plans, data_fn)
+    d = str(tmp_path / "ck")
+    SW.recursive_linearization(plans[:2], data_fn, checkpoint_dir=d)
+    resumed = SW.recursive_linearization(plans, data_fn, checkpoint_dir=d)
+    assert len(resumed.history) == 3
+    assert rel(resumed.c, full.c) < 1e-12
+
+
+def test_autograd_misfit_gradient_k20(hs):
+    """Gradient workload: k = 20, 16 x 16 leaves, 40 x 40 coefficients (blurred-ellipse phantom),
+    64 incidences, 128 receivers; autograd gradient vs central differences (h = 1e-6) on 20
+    seeded coefficients."""
+    import torch
+    from paper_1608_06871_gb300.autograd import misfit
+    w = synth.WORKLOADS["grad_k20"]
+    c0 = synth.project_sine(synth.ellipse_phantom(3), w.S, w.S)
+    rng = np.random.default_rng(44)
+    data_np = 0.05 * (rng.standard_normal((w.M, w.P)) + 1j * rng.standard_normal((w.M, w.P)))
+    data = torch.tensor(np.stack([data_np.real, data_np.imag], -1), device="cuda")
+    al = torch.tensor(synth.directions(w.M), device="cuda")
+    th = torch.tensor(synth.receivers(w.P), device="cuda")
+    solver = hs.Solver(w.n_leaf_side, w.S, w.S, w.R)
+    c = torch.tensor(c0, requires_grad=True)
+    loss = misfit(c, solver, w.k, data, al, th)
+    (2.5 * loss).backward()
+    g = c.grad.numpy() / 2.5
+    idx = np.random.default_rng(33).choice(w.S * w.S, size=20, replace=False)
+    h = 1e-6
+    fd = []
+    for m in idx:
+        cp, cm = c0.copy(), c0.copy()
+        cp.flat[m] += h
+        cm.flat[m] -= h
+        lp = float(misfit(torch.tensor(cp), solver, w.k, data, al, th))
+        lm = float(misfit(torch.tensor(cm), solver, w.k, data, al, th))
+        fd.append((lp - lm) / (2 * h))
+    fd = np.array(fd)
+    assert np.abs(fd - g.flat[idx]).max() < 1e-5 * np.abs(g).max()
+    solver.close()

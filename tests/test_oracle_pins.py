@@ -203,3 +203,21 @@ def test_gn_recovers_coefficients_from_linearised_data(fw_zero):
     c = synth.random_coeffs(S, S, seed=9)
     dc = F.gn_step(J, J @ c.ravel(), 0.0)
     assert np.abs(dc - c.ravel()).max() < 1e-8 * np.abs(c).max()
+
+
+def test_oracle_sweep_recovers_band_limited_contrast():
+    """Exact data of a contrast inside the band limit: two frequencies of Newton steps recover it."""
+    from types import SimpleNamespace
+    from oracle import sweep as OS
+    c_true = synth.random_coeffs(3, 3, seed=41, scale=0.05)
+    plans = [SimpleNamespace(k=k, leaves_per_side=2, S=3, M=8, P=8, newton=3) for k in (2.0, 3.0)]
+    data = {}
+
+    def data_fn(p, al, th):
+        if p.k not in data:
+            data[p.k] = F.forward_from_coeffs(c_true, p.k, p.leaves_per_side).solve_plane(al, th)[0]
+        return data[p.k]
+
+    c, hist = OS.sweep(plans, data_fn, lambda_rel=1e-8)
+    assert np.abs(c - c_true).max() < 1e-4 * np.abs(c_true).max()
+    assert hist[0][-1] < 1e-3 * hist[0][0]

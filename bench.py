@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--prof-family", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-fp64-arm", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -271,6 +272,8 @@ def run_hs(args, world, rank, local):
     h2d = 8 * (w.S * w.S + w.M + w.P)
     d2h = 16 * w.M * w.P
 
+    secondary = gn_and_gradient_times(hs, torch, local) if not args.no_secondary else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt = oracle_sample()
@@ -306,10 +309,61 @@ def run_hs(args, world, rank, local):
                                 if other["prof"][0] > 0 else None}
             line["mixed_vs_fp64_farfield_rel_err"] = err
             line["mixed_speedup_vs_fp64"] = other["ms"] / main["ms"]
+        if secondary:
+            line["secondary"] = secondary
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     main["solver"].close()
+
+
+def gn_and_gradient_times(hs, torch, local, reps=3):
+    """GN-step time (k = 5 workload, FP64: build + solve + Jacobian + normal equations) and
+    misfit-gradient time (k = 20 workload, FP64: build + forward + adjoint sweep), CUDA events."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    w = synth.WORKLOADS["gn_k5"]
+    qt = synth.gaussian_bumps(1)
+    al, th = synth.directions(w.M), synth.receivers(w.P)
+    gen = hs.Solver(w.n_leaf_side, 2, 2, w.R, device=local, stream=stream.cuda_stream)
+    x, y = gen.node_coords()
+    gen.build_nodes(qt(x, y), w.k)
+    data = gen.solve(al, th)  # measured data for the timing run (the parity test takes them from the oracle)
+    gen.close()
+    s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, device=local, stream=stream.cuda_stream)
+    c0 = np.zeros((w.S, w.S))
+    ts = []
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.build(c0, w.k)
+        s.gn_step(data, al, th, 1e-4, c0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    s.close()
+    out["gn_step_ms"] = {"value": float(np.median(ts)), "workload": w.name, "precision": "fp64",
+                         "includes": "hs_build + hs_gn_step (forward, Jacobian by adjoint sweep, normal equations)"}
+    w = synth.WORKLOADS["grad_k20"]
+    c = synth.project_sine(synth.ellipse_phantom(3), w.S, w.S)
+    rng = np.random.default_rng(44)
+    d = 0.05 * (rng.standard_normal((w.M, w.P)) + 1j * rng.standard_normal((w.M, w.P)))
+    s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, device=local, stream=stream.cuda_stream)
+    ts = []
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.build(c, w.k)
+        s.gradient(d, synth.directions(w.M), synth.receivers(w.P))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    s.close()
+    out["gradient_ms"] = {"value": float(np.median(ts)), "workload": w.name, "precision": "fp64",
+                          "includes": "hs_build + hs_gradient (forward, adjoint sweep, projection)"}
+    return out
 
 
 def main():

@@ -55,7 +55,7 @@ typedef struct hs_config {
   int device;           /* CUDA device ordinal                                      */
   void* stream;         /* cudaStream_t for all work, or NULL for a private stream  */
   double refine_tol;    /* HS_MIXED: stop when the far-field update is below this
-                           relative size (default 1e-12 if <= 0)                    */
+                           relative size (default 1e-9 if <= 0)                     */
   int refine_max_iter;  /* HS_MIXED: maximum refinement sweeps (default 8 if <= 0)  */
 } hs_config;
 

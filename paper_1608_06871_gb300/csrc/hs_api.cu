@@ -768,14 +768,16 @@ size_t mixed_bytes(hs_ctx* ctx, int M, int P) {
 // is the plain FP32 solve; every later pass solves for the correction with
 // body loads (the PDE residual), interface right-hand sides (continuity
 // residual) and the exterior residual.  Stops when the far field changes by
-// less than tol relative, or fails with HS_ENOCONV after max_iter passes.
+// less than tol relative (default 1e-9: each pass contracts the error by
+// orders of magnitude, so the returned iterate is far more accurate than tol),
+// or fails with HS_ENOCONV after max_iter passes.
 // ufar (M x P) and/or X (FP64 leaf fields, [leaf][252][M]) may be NULL.
 int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* ufar,
                 double2* Xout, Arena& a) {
   const int nb = ctx->B.nb, nl = ctx->nleaf, nlev = (int)ctx->levels.size();
   const size_t nbM = (size_t)nb * M, nX = (size_t)nl * NL * M;
   const double eta = ctx->k;
-  const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-11;
+  const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-9;
   const int max_iter = ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
   const double2 one = make_double2(1, 0), mone = make_double2(-1, 0), zero = make_double2(0, 0);
   const float2 fone = make_float2(1.f, 0.f), fzero = make_float2(0.f, 0.f);

@@ -3,6 +3,8 @@
 // FP64 on this part runs at a small fraction of the FP32 rate, so these
 // kernels are arithmetic-bound by construction; they are tiled for data reuse
 // in shared memory and use every SM through the batch and tile dimensions.
+#include <algorithm>
+
 #include "linalg.cuh"
 
 namespace hs {
@@ -28,16 +30,32 @@ template <typename T> __device__ __forceinline__ T ld_op(const T* P, int ld, int
   return op == OP_N ? P[(long long)r * ld + c] : P[(long long)c * ld + r];
 }
 
+__device__ __forceinline__ void atomic_addv(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_addv(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_addv(double2* p, double2 v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+__device__ __forceinline__ void atomic_addv(float2* p, float2 v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+// 32 x 32 tile, 2 x 2 outputs per thread.  blockIdx.z = batch * splits + split:
+// with splits > 1 each split covers a slice of k and adds alpha * partial into
+// C atomically (C already scaled by beta).
 template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, int k, TC alpha, const TA* __restrict__ A,
                                               int lda, long long sA, const TB* __restrict__ B, int ldb, long long sB,
-                                              TC beta, TC* __restrict__ C, int ldc, long long sC) {
+                                              TC beta, TC* __restrict__ C, int ldc, long long sC, int splits) {
   __shared__ TA As[BK][BM + 1];
   __shared__ TB Bs[BK][BN + 1];
-  const int b = blockIdx.z;
+  const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
   A += b * sA;
   B += b * sB;
   C += b * sC;
+  const int kc = ((k + splits - 1) / splits + BK - 1) / BK * BK;
+  const int kbeg = sp * kc, kend = min(k, kbeg + kc);
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   TC acc[2][2];
@@ -45,19 +63,18 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, in
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) acc[i][j] = el<TC>::zero();
-  for (int k0 = 0; k0 < k; k0 += BK) {
-    // load A tile: BM x BK, element (r, kk) of op(A)
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += 256) {
       int r, kk;
       if (opA == OP_N) { r = e / BK; kk = e % BK; } else { kk = e / BM; r = e % BM; }
       int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < m && gk < k) ? ld_op(A, lda, opA, gr, gk) : el<TA>::zero();
+      As[kk][r] = (gr < m && gk < kend) ? ld_op(A, lda, opA, gr, gk) : el<TA>::zero();
     }
     for (int e = threadIdx.x; e < BK * BN; e += 256) {
       int kk, c;
       if (opB == OP_N) { kk = e / BN; c = e % BN; } else { c = e / BK; kk = e % BK; }
       int gk = k0 + kk, gc = col0 + c;
-      Bs[kk][c] = (gk < k && gc < n) ? ld_op(B, ldb, opB, gk, gc) : el<TB>::zero();
+      Bs[kk][c] = (gk < kend && gc < n) ? ld_op(B, ldb, opB, gk, gc) : el<TB>::zero();
     }
     __syncthreads();
 #pragma unroll
@@ -79,18 +96,117 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, in
       if (r < m && c < n) {
         TC v = scal<TC, TC>(alpha, acc[i][j]);
         long long o = (long long)r * ldc + c;
+        if (splits > 1) {
+          atomic_addv(&C[o], v);
+        } else {
+          if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
+          C[o] = v;
+        }
+      }
+    }
+}
+
+// 64 x 64 tile, 4 x 4 outputs per thread (more arithmetic per shared-memory
+// load), k-step 8 with the next tile prefetched into registers.  For shapes
+// with enough tiles to fill the machine.
+constexpr int GB = 64, GK = 8;
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, int n, int k, TC alpha,
+                                                  const TA* __restrict__ A, int lda, long long sA,
+                                                  const TB* __restrict__ B, int ldb, long long sB, TC beta,
+                                                  TC* __restrict__ C, int ldc, long long sC) {
+  __shared__ TA As[GK][GB];
+  __shared__ TB Bs[GK][GB];
+  const int b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  const int row0 = blockIdx.y * GB, col0 = blockIdx.x * GB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  TC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = el<TC>::zero();
+  // each thread stages 2 elements of A and 2 of B per k-step (64 x 8 each)
+  TA ra[2];
+  TB rb[2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int e = threadIdx.x + 256 * q;
+      int r, kk;
+      if (opA == OP_N) { r = e / GK; kk = e % GK; } else { kk = e / GB; r = e % GB; }
+      int gr = row0 + r, gk = k0 + kk;
+      ra[q] = (gr < m && gk < k) ? ld_op(A, lda, opA, gr, gk) : el<TA>::zero();
+      int kk2, c;
+      if (opB == OP_N) { kk2 = e / GB; c = e % GB; } else { c = e / GK; kk2 = e % GK; }
+      int gk2 = k0 + kk2, gc = col0 + c;
+      rb[q] = (gk2 < k && gc < n) ? ld_op(B, ldb, opB, gk2, gc) : el<TB>::zero();
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int e = threadIdx.x + 256 * q;
+      int r, kk;
+      if (opA == OP_N) { r = e / GK; kk = e % GK; } else { kk = e / GB; r = e % GB; }
+      As[kk][r] = ra[q];
+      int kk2, c;
+      if (opB == OP_N) { kk2 = e / GB; c = e % GB; } else { c = e / GK; kk2 = e % GK; }
+      Bs[kk2][c] = rb[q];
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < k; k0 += GK) {
+    store();
+    __syncthreads();
+    if (k0 + GK < k) load(k0 + GK);
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      TA a[4];
+      TB bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = addv(acc[i][j], mul(a[i], bb[j]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < m && c < n) {
+        TC v = scal<TC, TC>(alpha, acc[i][j]);
+        long long o = (long long)r * ldc + c;
         if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
         C[o] = v;
       }
     }
 }
 
+// C *= beta (beta == 0 writes zeros) before split-k accumulation.
+template <typename TC>
+__global__ void k_scale(TC* C, int m, int n, int ldc, long long sC, TC beta) {
+  const int b = blockIdx.y;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)m * n) return;
+  int r = (int)(e / n), c = (int)(e % n);
+  TC* p = C + b * sC + (long long)r * ldc + c;
+  *p = is_zero(beta) ? el<TC>::zero() : scal<TC, TC>(beta, *p);
+}
+
 // Panel factorisation of columns [j0, j0+nb) with partial pivoting; row swaps
 // are applied to whole rows.  One CTA per matrix; per column: a warp-shuffle
 // argmax over the rows, the row swap, the scaling and the rank-1 update of the
 // rest of the panel.
-constexpr int PANEL_THREADS = 512;
-template <typename E>
+template <typename E, int PANEL_THREADS>
 __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(E* A, int lda, long long sA, int n, int j0, int nb,
                                                             int* piv, long long sP, int* info) {
   __shared__ double wmag[PANEL_THREADS / 32];
@@ -205,11 +321,64 @@ __global__ void __launch_bounds__(32 * TRSM_WARPS) k_trsm_diag(const E* A, int l
   if (lane < nb) B[(long long)(i0 + lane) * ldb + col] = x;
 }
 
+// Same solve, one thread per right-hand side with the 32 unknowns in
+// registers (fully unrolled): the better choice when there are many
+// right-hand sides in the batch (leaf and merge systems).
+template <typename E>
+__global__ void __launch_bounds__(128) k_trsm_diag_col(const E* A, int lda, long long sA, int i0, int nb, int mode,
+                                                       E* B, int ldb, long long sB, int nrhs) {
+  __shared__ E T[NB][NB + 1];
+  const int b = blockIdx.y;
+  A += b * sA;
+  B += b * sB;
+  const bool tr = (mode >= 2);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e / NB, c = e % NB;
+    T[r][c] = (r < nb && c < nb) ? (tr ? A[(long long)(i0 + c) * lda + i0 + r] : A[(long long)(i0 + r) * lda + i0 + c])
+                                 : el<E>::zero();
+  }
+  __syncthreads();
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  E x[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) x[r] = r < nb ? B[(long long)(i0 + r) * ldb + col] : el<E>::zero();
+  const bool lower = (mode == 0 || mode == 2);
+  const bool unit = (mode == 0 || mode == 3);
+  if (lower) {
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      E v = x[r];
+#pragma unroll
+      for (int c = 0; c < r; ++c) v = v - mul(T[r][c], x[c]);
+      x[r] = (unit || r >= nb) ? v : el<E>::div(v, T[r][r]);
+    }
+  } else {
+#pragma unroll
+    for (int r = NB - 1; r >= 0; --r) {
+      E v = x[r];
+#pragma unroll
+      for (int c = r + 1; c < NB; ++c) v = v - mul(T[r][c], x[c]);
+      x[r] = (unit || r >= nb) ? v : el<E>::div(v, T[r][r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (r < nb) B[(long long)(i0 + r) * ldb + col] = x[r];
+}
+
+// Many columns overall: one thread per column; few: one warp per column.
 template <typename E>
 void trsm_diag(cudaStream_t s, const E* A, int lda, long long sA, int i0, int nb, int mode, E* B, int ldb,
                long long sB, int nrhs, int batch) {
-  dim3 g((nrhs + TRSM_WARPS - 1) / TRSM_WARPS, batch);
-  k_trsm_diag<E><<<g, 32 * TRSM_WARPS, 0, s>>>(A, lda, sA, i0, nb, mode, B, ldb, sB, nrhs);
+  if ((long long)nrhs * batch >= 8192) {
+    const int threads = nrhs >= 128 ? 128 : ((nrhs + 31) / 32) * 32;
+    dim3 g((nrhs + threads - 1) / threads, batch);
+    k_trsm_diag_col<E><<<g, threads, 0, s>>>(A, lda, sA, i0, nb, mode, B, ldb, sB, nrhs);
+  } else {
+    dim3 g((nrhs + TRSM_WARPS - 1) / TRSM_WARPS, batch);
+    k_trsm_diag<E><<<g, 32 * TRSM_WARPS, 0, s>>>(A, lda, sA, i0, nb, mode, B, ldb, sB, nrhs);
+  }
   HS_COUNT_LAUNCH();
 }
 
@@ -246,12 +415,33 @@ template <typename TA, typename TB, typename TC>
 void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const TA* A, int lda, long long sA,
           const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC, int batch) {
   if (m <= 0 || n <= 0 || batch <= 0) return;
-  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
   const bool prof = prof_active(is_fp64<TC>::v ? 1 : 2);
   cudaEvent_t ev = nullptr;
   if (prof) prof_begin(s, &ev);
-  k_gemm<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-  HS_COUNT_LAUNCH();
+  constexpr long long kFill = 2 * 152;  // tiles that keep every SM of the chip busy
+  const long long t64 = (long long)((m + GB - 1) / GB) * ((n + GB - 1) / GB) * batch;
+  const long long t32 = (long long)((m + BM - 1) / BM) * ((n + BN - 1) / BN) * batch;
+  if (m >= GB && n >= GB && t64 >= kFill) {
+    dim3 grid((n + GB - 1) / GB, (m + GB - 1) / GB, batch);
+    k_gemm_big<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    HS_COUNT_LAUNCH();
+  } else {
+    int splits = 1;
+    if (t32 < kFill && k >= 256) {
+      splits = (int)std::min<long long>((kFill + t32 - 1) / t32, k / 128);
+      splits = std::max(1, std::min(splits, 32));
+      if ((long long)batch * splits > 65535) splits = 1;
+    }
+    if (splits > 1) {
+      dim3 gs((unsigned)(((long long)m * n + 255) / 256), batch);
+      k_scale<TC><<<gs, 256, 0, s>>>(C, m, n, ldc, sC, beta);
+      HS_COUNT_LAUNCH();
+    }
+    dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch * splits);
+    k_gemm<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                            splits);
+    HS_COUNT_LAUNCH();
+  }
   if (prof) prof_end(s, ev, flops_per_mac<TA, TB>() * (double)m * n * k * batch);
 }
 
@@ -259,7 +449,12 @@ template <typename E>
 void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info, int batch) {
   for (int j0 = 0; j0 < n; j0 += NB) {
     int nb = n - j0 < NB ? n - j0 : NB;
-    k_lu_panel<E><<<batch, PANEL_THREADS, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
+    if (n <= 256)
+      k_lu_panel<E, 128><<<batch, 128, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
+    else if (n <= 1024)
+      k_lu_panel<E, 256><<<batch, 256, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
+    else
+      k_lu_panel<E, 1024><<<batch, 1024, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
     HS_COUNT_LAUNCH();
     int rest = n - j0 - nb;
     if (rest > 0) {

@@ -18,6 +18,7 @@ extern "C" {
 /* Kernel families that can be timed. */
 #define HS_PROF_GEMM_FP64 1 /* the batched FP64 real/complex GEMM kernel */
 #define HS_PROF_GEMM_FP32 2 /* the same GEMM kernel in FP32 (mixed-precision path) */
+#define HS_PROF_GEMM_TC 3   /* the tensor-core complex FP32 GEMM (mixed-precision path) */
 
 /* Start recording a CUDA event pair around every launch of the given family
  * (on the stream the launch uses) and counting its algorithmic flops
@@ -39,6 +40,23 @@ int hs_peak_fp64(int device, double ms, double* tflops);
 /* Refinement passes and the last relative change of the far field in the
  * most recent HS_MIXED solve on ctx (0 and -1 before any). */
 int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update);
+
+/* Route eligible complex FP32 products of the mixed-precision path
+ * (untransposed operands, m >= 128, n >= 64, k >= 64) to the tensor-core GEMM
+ * (enable != 0, the default) or to the SIMT FP32 GEMM (enable == 0).
+ * Process-wide; takes effect at the next launch.  Never fails. */
+int hs_set_tensor_cores(int enable);
+
+/* C[b] = A[b] B[b] for b < batch: complex FP32 (interleaved re, im),
+ * row-major, A m x k, B k x n, C m x n, contiguous batches, all DEVICE
+ * pointers on the current device, enqueued on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream) and synchronised before return.  Uses the
+ * library's GEMM dispatch: the tensor-core kernel when hs_set_tensor_cores
+ * allows it and the shape is eligible; *used_tc (if not NULL) says which ran.
+ * Errors: HS_EINVAL (non-positive size, NULL pointer), HS_ETIMEOUT (a bounded
+ * tensor-core wait gave up; C is then unspecified), HS_ECUDA. */
+int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream,
+               int* used_tc);
 
 #ifdef __cplusplus
 }

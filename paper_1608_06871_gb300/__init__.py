@@ -67,6 +67,8 @@ _SIGS = {
                           ctypes.POINTER(ctypes.c_longlong)]),
     "hs_peak_fp64": (_I, [_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "hs_set_tensor_cores": (_I, [_I]),
+    "hs_cgemm32": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
 }
 
 
@@ -219,6 +221,7 @@ def hs_destroy(ctx):
 # ---- measurement hooks (include/hs_diag.h) --------------------------------------
 HS_PROF_GEMM_FP64 = 1
 HS_PROF_GEMM_FP32 = 2
+HS_PROF_GEMM_TC = 3
 
 
 def hs_prof_start(family: int = HS_PROF_GEMM_FP64):
@@ -243,6 +246,23 @@ def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:
     t = ctypes.c_double()
     _check(None, lib().hs_peak_fp64(device, float(ms), ctypes.byref(t)))
     return t.value
+
+
+def hs_set_tensor_cores(enable: bool):
+    _check(None, lib().hs_set_tensor_cores(1 if enable else 0))
+
+
+def hs_cgemm32(A, B, out, stream: int = 0) -> bool:
+    """out[b] = A[b] @ B[b] for contiguous complex64 CUDA tensors of shape
+    (batch, m, k), (batch, k, n), (batch, m, n).  Returns True when the
+    tensor-core kernel ran."""
+    batch, m, k = A.shape
+    n = B.shape[2]
+    used = ctypes.c_int()
+    _check(None, lib().hs_cgemm32(m, n, k, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), batch, ctypes.c_void_p(stream),
+                                  ctypes.byref(used)))
+    return bool(used.value)
 
 
 class Solver:

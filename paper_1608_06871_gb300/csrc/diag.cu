@@ -5,6 +5,7 @@
 #include "../../include/hs.h"
 #include "../../include/hs_diag.h"
 #include "common.cuh"
+#include "linalg.cuh"
 
 namespace hs {
 
@@ -54,7 +55,7 @@ __global__ void k_dfma_peak(double* out, int iters, double a, double b) {
 extern "C" {
 
 int hs_prof_start(int family) {
-  if (family != HS_PROF_GEMM_FP64 && family != HS_PROF_GEMM_FP32) return HS_EINVAL;
+  if (family != HS_PROF_GEMM_FP64 && family != HS_PROF_GEMM_FP32 && family != HS_PROF_GEMM_TC) return HS_EINVAL;
   hs::g_prof.clear();
   hs::g_prof_family = family;
   return HS_OK;
@@ -114,6 +115,24 @@ int hs_peak_fp64(int device, double ms, double* tflops) {
   cudaEventDestroy(b);
   cudaFree(out);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
+}
+
+int hs_set_tensor_cores(int enable) {
+  hs::g_tc_enabled = enable != 0;
+  return HS_OK;
+}
+
+int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream, int* used_tc) {
+  if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535 || !A || !B || !C) return HS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (used_tc) *used_tc = hs::cgemm_tc_eligible(hs::OP_N, hs::OP_N, m, n, k, batch) ? 1 : 0;
+  hs::gemm<float2, float2, float2>(s, hs::OP_N, hs::OP_N, m, n, k, make_float2(1.f, 0.f),
+                                   static_cast<const float2*>(A), k, (long long)m * k,
+                                   static_cast<const float2*>(B), n, (long long)k * n, make_float2(0.f, 0.f),
+                                   static_cast<float2*>(C), n, (long long)m * n, batch);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
+  if (hs::tc_timed_out(s)) return HS_ETIMEOUT;
+  return HS_OK;
 }
 
 }  // extern "C"

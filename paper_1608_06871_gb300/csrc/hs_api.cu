@@ -213,6 +213,7 @@ int check_info(hs_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   for (int v : info)
     if (v != 0) return fail(ctx, HS_ESINGULAR, "zero pivot in a factorisation (column " + std::to_string(v) + ")");
+  if (tc_timed_out(ctx->stream)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
   return HS_OK;
 }
 
@@ -861,6 +862,7 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
     std::swap(uf, ufp);
   }
   CK(cudaGetLastError());
+  if (tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
   if (!converged) return fail(ctx, HS_ENOCONV, "iterative refinement did not reach the tolerance");
   if (ufar) CK(cudaMemcpyAsync(ufar, uf, sizeof(double2) * M * P, cudaMemcpyDeviceToDevice, s));
   if (Xout) CK(cudaMemcpyAsync(Xout, X, sizeof(double2) * nX, cudaMemcpyDeviceToDevice, s));

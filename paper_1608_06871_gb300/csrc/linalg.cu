@@ -4,6 +4,7 @@
 // kernels are arithmetic-bound by construction; they are tiled for data reuse
 // in shared memory and use every SM through the batch and tile dimensions.
 #include <algorithm>
+#include <type_traits>
 
 #include "linalg.cuh"
 
@@ -260,12 +261,25 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(E* A, int lda, long 
     const int w = j0 + nb - 1 - j;  // remaining panel columns
     if (!zero) {
       const E pv = A[(long long)j * lda + j];
-      // scale the column and update the panel in one pass over the rows below j
-      for (int r = j + 1 + t; r < n; r += PANEL_THREADS) {
-        E l = el<E>::div(A[(long long)r * lda + j], pv);
-        A[(long long)r * lda + j] = l;
-        for (int c = 1; c <= w; ++c)
-          A[(long long)r * lda + j + c] = A[(long long)r * lda + j + c] - mul(l, A[(long long)j * lda + j + c]);
+      if constexpr (is_fp64<E>::v) {
+        // FP64 issue slots are the scarce resource: one thread per row, one
+        // division and w multiply-adds per row
+        for (int r = j + 1 + t; r < n; r += PANEL_THREADS) {
+          E* row = A + (long long)r * lda + j;
+          const E l = el<E>::div(row[0], pv);
+          row[0] = l;
+          for (int c = 1; c <= w; ++c) row[c] = row[c] - mul(l, A[(long long)j * lda + j + c]);
+        }
+      } else {
+        // FP32: memory access dominates; one warp per row, lane c on column
+        // j + c (coalesced), pivot-row segment kept in a register
+        const E urow = lane <= w ? A[(long long)j * lda + j + lane] : el<E>::zero();
+        for (int r = j + 1 + warp; r < n; r += PANEL_THREADS / 32) {
+          E* row = A + (long long)r * lda + j;
+          const E l = el<E>::div(row[0], pv);
+          if (lane >= 1 && lane <= w) row[lane] = row[lane] - mul(l, urow);
+          if (lane == 0) row[0] = l;
+        }
       }
     }
     __syncthreads();
@@ -415,6 +429,17 @@ template <typename TA, typename TB, typename TC>
 void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const TA* A, int lda, long long sA,
           const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC, int batch) {
   if (m <= 0 || n <= 0 || batch <= 0) return;
+  if constexpr (std::is_same<TA, float2>::value && std::is_same<TB, float2>::value &&
+                std::is_same<TC, float2>::value) {
+    if (cgemm_tc_eligible(opA, opB, m, n, k, batch)) {
+      const bool prof_tc = prof_active(3);
+      cudaEvent_t ev = nullptr;
+      if (prof_tc) prof_begin(s, &ev);
+      cgemm_tc(s, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+      if (prof_tc) prof_end(s, ev, 8.0 * m * n * k * batch);
+      return;
+    }
+  }
   const bool prof = prof_active(is_fp64<TC>::v ? 1 : 2);
   cudaEvent_t ev = nullptr;
   if (prof) prof_begin(s, &ev);

@@ -33,4 +33,14 @@ template <typename E>
 void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int n, const int* piv,
               long long sP, E* B, int ldb, long long sB, int nrhs, int batch);
 
+// Tensor-core complex FP32 GEMM (tcgen05, 3xTF32; tcgemm.cu), used by gemm()
+// for float2 products with both operands untransposed and m >= 128, n >= 64.
+extern bool g_tc_enabled;
+bool cgemm_tc_eligible(int opA, int opB, int m, int n, int k, int batch);
+void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A, int lda, long long sA,
+              const float2* B, int ldb, long long sB, float2 beta, float2* C, int ldc, long long sC, int batch);
+// Synchronises s, then reads and clears this device's flag that a bounded
+// tensor-core wait gave up.
+bool tc_timed_out(cudaStream_t s);
+
 }  // namespace hs

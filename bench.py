@@ -211,12 +211,21 @@ def time_arm(hs, torch, w, c, precision, args, world, local, prof_family):
     ev[2].record(stream)
     torch.cuda.synchronize()
     phases = {"build_ms": ev[0].elapsed_time(ev[1]), "forward_ms": ev[1].elapsed_time(ev[2])}
+    # solves/s of the sweep alone (factorisation excluded)
+    phases["solves_per_s_excl_build"] = w.M / (phases["forward_ms"] * 1e-3)
+    tc = None
     if precision == hs.HS_MIXED:
-        it, upd = hs.hs_refine_stats(ctx)
+        it, upd, est = hs.hs_refine_stats(ctx)
         phases["refine_passes"] = it
         phases["last_rel_update"] = upd
+        phases["est_rel_error"] = est
+        # tensor-core GEMM family, one more untimed step with per-launch events
+        hs.hs_prof_start(hs.HS_PROF_GEMM_TC)
+        step()
+        torch.cuda.synchronize()
+        tc = hs.hs_prof_stop()
     uf = ufar.cpu().numpy()
-    return dict(solver=solver, ctx=ctx, ms=ms, launches=launches, prof=prof, clocks=clk, phases=phases,
+    return dict(solver=solver, ctx=ctx, ms=ms, launches=launches, prof=prof, tc=tc, clocks=clk, phases=phases,
                 ufar=uf[..., 0] + 1j * uf[..., 1], u=u, alphas=alphas)
 
 
@@ -309,12 +318,33 @@ def run_hs(args, world, rank, local):
                                 if other["prof"][0] > 0 else None}
             line["mixed_vs_fp64_farfield_rel_err"] = err
             line["mixed_speedup_vs_fp64"] = other["ms"] / main["ms"]
+        if main.get("tc") and main["tc"][0] > 0:
+            tc_ms, tc_flops, tc_n = main["tc"]
+            tc_peak, tc_src = tf32_peak()
+            ach = tc_flops / (tc_ms * 1e-3) / 1e12
+            line["tensor_gemm"] = {
+                "kernel": "k_cgemm_tc (tcgen05 kind::tf32, complex FP32 via 3xTF32)", "bound": "tensor",
+                "achieved": ach, "unit": "TFLOP/s", "launches": tc_n, "kernel_ms_per_step": tc_ms,
+                "note": "achieved = complex flops 8mnk per product; the tensor pipe executes 3x that (hi*hi, hi*lo, lo*hi)",
+                "issued_tflops": 3 * ach, "peak": tc_peak, "frac_issued": (3 * ach / tc_peak) if tc_peak else None,
+                "peak_source": tc_src}
         if secondary:
             line["secondary"] = secondary
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     main["solver"].close()
+
+
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured cuBLAS bf16 rate times the nominal
+    TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        return bf16 * 1.1 / 2.25, "measured bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25"
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"
 
 
 def gn_and_gradient_times(hs, torch, local, reps=3):

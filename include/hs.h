@@ -54,8 +54,9 @@ typedef struct hs_config {
   int precision;        /* HS_FP64 or HS_MIXED                                      */
   int device;           /* CUDA device ordinal                                      */
   void* stream;         /* cudaStream_t for all work, or NULL for a private stream  */
-  double refine_tol;    /* HS_MIXED: stop when the far-field update is below this
-                           relative size (default 1e-9 if <= 0)                     */
+  double refine_tol;    /* HS_MIXED: stop when the estimated relative error of the
+                           far field (last update x rho/(1-rho), rho the observed
+                           contraction per pass) is below this (default 1e-9)       */
   int refine_max_iter;  /* HS_MIXED: maximum refinement sweeps (default 8 if <= 0)  */
 } hs_config;
 

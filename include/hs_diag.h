@@ -37,9 +37,12 @@ int hs_prof_stop(double* total_ms, double* total_flops, long long* launches);
  * TFLOP/s (2 flops per DFMA) in *tflops.  Runs for about `ms` milliseconds. */
 int hs_peak_fp64(int device, double ms, double* tflops);
 
-/* Refinement passes and the last relative change of the far field in the
- * most recent HS_MIXED solve on ctx (0 and -1 before any). */
-int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update);
+/* Refinement passes, the last relative change of the far field and the
+ * estimated relative error of the returned far field (the stopping quantity:
+ * the last change times rho / (1 - rho), rho the observed contraction of the
+ * passes, or the change itself before rho is known) in the most recent
+ * HS_MIXED solve on ctx (0, -1, -1 before any).  Any pointer may be NULL. */
+int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update, double* est_error);
 
 /* Route eligible complex FP32 products of the mixed-precision path
  * (untransposed operands, m >= 128, n >= 64, k >= 64) to the tensor-core GEMM
@@ -57,6 +60,17 @@ int hs_set_tensor_cores(int enable);
  * tensor-core wait gave up; C is then unspecified), HS_ECUDA. */
 int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream,
                int* used_tc);
+
+/* Solve A[b] X[b] = B[b] in place in B for b < batch with the library's
+ * batched LU (partial pivoting; tournament pivoting for panels taller than 256
+ * rows) and triangular solves: complex (interleaved re, im), row-major,
+ * A n x n (overwritten by its factors), B n x nrhs, contiguous batches, DEVICE
+ * pointers on the current device, enqueued on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream) and synchronised before return.  precision
+ * HS_FP64: complex128; HS_MIXED: complex64.  Allocates and frees its pivot
+ * and status arrays.  Errors: HS_EINVAL (bad size or precision, NULL
+ * pointer), HS_ESINGULAR (an exactly zero pivot), HS_ENOMEM, HS_ECUDA. */
+int hs_lu_solve(int precision, int n, int nrhs, void* A, void* B, int batch, void* stream);
 
 #ifdef __cplusplus
 }

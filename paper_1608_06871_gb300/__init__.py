@@ -66,9 +66,11 @@ _SIGS = {
     "hs_prof_stop": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_longlong)]),
     "hs_peak_fp64": (_I, [_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
-    "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)]),
     "hs_set_tensor_cores": (_I, [_I]),
     "hs_cgemm32": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
+    "hs_lu_solve": (_I, [_I, _I, _I, _P, _P, _I, _P]),
 }
 
 
@@ -236,10 +238,11 @@ def hs_prof_stop():
 
 
 def hs_refine_stats(ctx):
-    """(refinement passes, last relative far-field change) of the last HS_MIXED solve."""
-    it, up = ctypes.c_int(), ctypes.c_double()
-    _check(ctx, lib().hs_refine_stats(ctx, ctypes.byref(it), ctypes.byref(up)))
-    return it.value, up.value
+    """(refinement passes, last relative far-field change, estimated relative
+    far-field error) of the last HS_MIXED solve."""
+    it, up, est = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().hs_refine_stats(ctx, ctypes.byref(it), ctypes.byref(up), ctypes.byref(est)))
+    return it.value, up.value, est.value
 
 
 def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:
@@ -250,6 +253,16 @@ def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:
 
 def hs_set_tensor_cores(enable: bool):
     _check(None, lib().hs_set_tensor_cores(1 if enable else 0))
+
+
+def hs_lu_solve(A, B, stream: int = 0):
+    """Solve A[b] X[b] = B[b] in place in B (A overwritten by its LU factors) for
+    contiguous complex128 (HS_FP64) or complex64 (HS_MIXED) CUDA tensors of
+    shape (batch, n, n) and (batch, n, nrhs)."""
+    batch, n, _ = A.shape
+    prec = HS_FP64 if A.dtype == B.dtype and str(A.dtype) == "torch.complex128" else HS_MIXED
+    _check(None, lib().hs_lu_solve(prec, n, B.shape[2], ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                   batch, ctypes.c_void_p(stream)))
 
 
 def hs_cgemm32(A, B, out, stream: int = 0) -> bool:

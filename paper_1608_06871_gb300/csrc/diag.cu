@@ -135,4 +135,36 @@ int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int b
   return HS_OK;
 }
 
+int hs_lu_solve(int precision, int n, int nrhs, void* A, void* B, int batch, void* stream) {
+  if (n <= 0 || nrhs <= 0 || batch <= 0 || batch > 65535 || !A || !B) return HS_EINVAL;
+  if (precision != HS_FP64 && precision != HS_MIXED) return HS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int *piv = nullptr, *info = nullptr;
+  if (cudaMalloc(&piv, sizeof(int) * (size_t)n * batch) != cudaSuccess) return HS_ENOMEM;
+  if (cudaMalloc(&info, sizeof(int) * (size_t)batch) != cudaSuccess) {
+    cudaFree(piv);
+    return HS_ENOMEM;
+  }
+  cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s);
+  const long long sA = (long long)n * n, sB = (long long)n * nrhs;
+  if (precision == HS_FP64) {
+    hs::lu_factor<double2>(s, static_cast<double2*>(A), n, sA, n, piv, n, info, batch);
+    hs::lu_solve<double2>(s, hs::OP_N, static_cast<double2*>(A), n, sA, n, piv, n, static_cast<double2*>(B), nrhs, sB,
+                          nrhs, batch);
+  } else {
+    hs::lu_factor<float2>(s, static_cast<float2*>(A), n, sA, n, piv, n, info, batch);
+    hs::lu_solve<float2>(s, hs::OP_N, static_cast<float2*>(A), n, sA, n, piv, n, static_cast<float2*>(B), nrhs, sB,
+                         nrhs, batch);
+  }
+  std::vector<int> h(batch);
+  cudaError_t e = cudaMemcpyAsync(h.data(), info, sizeof(int) * (size_t)batch, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(piv);
+  cudaFree(info);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
+  for (int v : h)
+    if (v != 0) return HS_ESINGULAR;
+  return HS_OK;
+}
+
 }  // extern "C"

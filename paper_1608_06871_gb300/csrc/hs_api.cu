@@ -142,6 +142,7 @@ struct hs_ctx {
   const float2* Rroot32 = nullptr;
   int refine_iters = 0;
   double refine_update = 0.0;
+  double refine_est = 0.0;
   double bie_k = -1.0;  // wavenumber the layer-potential matrices were assembled for
   int *d_root_of_bie = nullptr, *d_bie_of_root = nullptr;  // root box order <-> boundary-node order
   double2* d_Rb = nullptr;  // root ItI map in boundary-node order (FP64)
@@ -768,10 +769,11 @@ size_t mixed_bytes(hs_ctx* ctx, int M, int P) {
 // (leaf PDE rows, interface continuity rows, exterior rows).  The first pass
 // is the plain FP32 solve; every later pass solves for the correction with
 // body loads (the PDE residual), interface right-hand sides (continuity
-// residual) and the exterior residual.  Stops when the far field changes by
-// less than tol relative (default 1e-9: each pass contracts the error by
-// orders of magnitude, so the returned iterate is far more accurate than tol),
-// or fails with HS_ENOCONV after max_iter passes.
+// residual) and the exterior residual.  Stops when the estimated relative
+// error of the far field is below tol (default 1e-9): the relative change of
+// the last pass, scaled by rho / (1 - rho) once two changes give the
+// contraction rate rho of the passes (rho ~ 1e-4 here, so three passes
+// usually suffice); fails with HS_ENOCONV after max_iter passes.
 // ufar (M x P) and/or X (FP64 leaf fields, [leaf][252][M]) may be NULL.
 int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* ufar,
                 double2* Xout, Arena& a) {
@@ -804,6 +806,8 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * nX, s));
   ctx->refine_iters = 0;
   ctx->refine_update = -1.0;
+  ctx->refine_est = -1.0;
+  double prev_upd = 0.0;
   bool converged = false;
   for (int it = 0; it < max_iter; ++it) {
     Phase pp("hs_refine_pass");
@@ -853,8 +857,18 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
       double h2[2];
       CK(cudaMemcpyAsync(h2, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      ctx->refine_update = h2[1] > 0 ? std::sqrt(h2[0] / h2[1]) : 0.0;
-      if (ctx->refine_update <= tol) {
+      const double upd = h2[1] > 0 ? std::sqrt(h2[0] / h2[1]) : 0.0;
+      // error of the new iterate: the update itself until the contraction
+      // rate rho of the passes is observed, then upd * rho / (1 - rho)
+      double est = upd;
+      if (prev_upd > 0.0 && upd < 0.5 * prev_upd) {
+        const double rho = upd / prev_upd;
+        est = upd * rho / (1.0 - rho);
+      }
+      ctx->refine_update = upd;
+      ctx->refine_est = est;
+      prev_upd = upd;
+      if (est <= tol) {
         converged = true;
         break;
       }
@@ -1366,10 +1380,11 @@ int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M, co
 
 long long hs_launch_count(const hs_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update) {
+int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update, double* est_error) {
   if (!ctx) return HS_EINVAL;
   if (iterations) *iterations = ctx->refine_iters;
   if (last_update) *last_update = ctx->refine_update;
+  if (est_error) *est_error = ctx->refine_est;
   return HS_OK;
 }
 

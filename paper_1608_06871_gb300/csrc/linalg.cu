@@ -6,7 +6,11 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "linalg.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hs {
 
@@ -26,31 +30,26 @@ template <typename TA, typename TB> constexpr double flops_per_mac() {
 }
 constexpr int BM = 32, BN = 32, BK = 16;  // GEMM tile
 constexpr int NB = 32;                    // LU / TRSM block size
+constexpr int kMaxCluster = 8;            // portable thread-block cluster size (split-k)
 
 template <typename T> __device__ __forceinline__ T ld_op(const T* P, int ld, int op, int r, int c) {
   return op == OP_N ? P[(long long)r * ld + c] : P[(long long)c * ld + r];
 }
 
-__device__ __forceinline__ void atomic_addv(double* p, double v) { atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_addv(float* p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_addv(double2* p, double2 v) {
-  atomicAdd(&p->x, v.x);
-  atomicAdd(&p->y, v.y);
-}
-__device__ __forceinline__ void atomic_addv(float2* p, float2 v) {
-  atomicAdd(&p->x, v.x);
-  atomicAdd(&p->y, v.y);
-}
-
 // 32 x 32 tile, 2 x 2 outputs per thread.  blockIdx.z = batch * splits + split:
-// with splits > 1 each split covers a slice of k and adds alpha * partial into
-// C atomically (C already scaled by beta).
+// with splits > 1 the kernel is launched in clusters of `splits` CTAs along z,
+// each CTA covers a slice of k, and the partial tiles are summed through
+// distributed shared memory in split order (deterministic, no atomics): rank r
+// reduces and writes its share of the tile's rows.
 template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, int k, TC alpha, const TA* __restrict__ A,
                                               int lda, long long sA, const TB* __restrict__ B, int ldb, long long sB,
                                               TC beta, TC* __restrict__ C, int ldc, long long sC, int splits) {
-  __shared__ TA As[BK][BM + 1];
-  __shared__ TB Bs[BK][BN + 1];
+  constexpr size_t A_BYTES = sizeof(TA) * BK * (BM + 1), B_BYTES = sizeof(TB) * BK * (BN + 1);
+  constexpr size_t RED_BYTES = sizeof(TC) * BM * BN;
+  __shared__ __align__(16) unsigned char raw[A_BYTES + B_BYTES > RED_BYTES ? A_BYTES + B_BYTES : RED_BYTES];
+  TA(*As)[BM + 1] = reinterpret_cast<TA(*)[BM + 1]>(raw);
+  TB(*Bs)[BN + 1] = reinterpret_cast<TB(*)[BN + 1]>(raw + A_BYTES);
   const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
   A += b * sA;
   B += b * sB;
@@ -89,22 +88,42 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, in
     }
     __syncthreads();
   }
+  if (splits == 1) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
-      if (r < m && c < n) {
-        TC v = scal<TC, TC>(alpha, acc[i][j]);
-        long long o = (long long)r * ldc + c;
-        if (splits > 1) {
-          atomic_addv(&C[o], v);
-        } else {
+      for (int j = 0; j < 2; ++j) {
+        int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+        if (r < m && c < n) {
+          TC v = scal<TC, TC>(alpha, acc[i][j]);
+          long long o = (long long)r * ldc + c;
           if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
           C[o] = v;
         }
       }
+    return;
+  }
+  TC* red = reinterpret_cast<TC*>(raw);  // the k loop ended with a barrier
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) red[(ty + 16 * i) * BN + tx + 16 * j] = acc[i][j];
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  const int rows_per = (BM + splits - 1) / splits;
+  const int rb = sp * rows_per, re = min(BM, rb + rows_per);
+  for (int e = rb * BN + threadIdx.x; e < re * BN; e += 256) {
+    TC sum = el<TC>::zero();
+    for (int q = 0; q < splits; ++q) sum = addv(sum, cl.map_shared_rank(red, q)[e]);
+    const int r = row0 + e / BN, c = col0 + e % BN;
+    if (r < m && c < n) {
+      TC v = scal<TC, TC>(alpha, sum);
+      long long o = (long long)r * ldc + c;
+      if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
+      C[o] = v;
     }
+  }
+  cl.sync();  // keep this CTA's partial tile alive until every rank has read it
 }
 
 // 64 x 64 tile, 4 x 4 outputs per thread (more arithmetic per shared-memory
@@ -192,99 +211,6 @@ __global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, in
     }
 }
 
-// C *= beta (beta == 0 writes zeros) before split-k accumulation.
-template <typename TC>
-__global__ void k_scale(TC* C, int m, int n, int ldc, long long sC, TC beta) {
-  const int b = blockIdx.y;
-  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)m * n) return;
-  int r = (int)(e / n), c = (int)(e % n);
-  TC* p = C + b * sC + (long long)r * ldc + c;
-  *p = is_zero(beta) ? el<TC>::zero() : scal<TC, TC>(beta, *p);
-}
-
-// Panel factorisation of columns [j0, j0+nb) with partial pivoting; row swaps
-// are applied to whole rows.  One CTA per matrix; per column: a warp-shuffle
-// argmax over the rows, the row swap, the scaling and the rank-1 update of the
-// rest of the panel.
-template <typename E, int PANEL_THREADS>
-__global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(E* A, int lda, long long sA, int n, int j0, int nb,
-                                                            int* piv, long long sP, int* info) {
-  __shared__ double wmag[PANEL_THREADS / 32];
-  __shared__ int widx[PANEL_THREADS / 32];
-  __shared__ int s_p;
-  __shared__ int s_zero;
-  const int b = blockIdx.x;
-  A += b * sA;
-  piv += b * sP;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int j = j0; j < j0 + nb; ++j) {
-    double best = -1.0;
-    int bi = j;
-    for (int r = j + t; r < n; r += PANEL_THREADS) {
-      double v = el<E>::mag2(A[(long long)r * lda + j]);
-      if (v > best) { best = v; bi = r; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_down_sync(0xffffffffu, best, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (lane == 0) { wmag[warp] = best; widx[warp] = bi; }
-    __syncthreads();
-    if (warp == 0) {
-      best = lane < PANEL_THREADS / 32 ? wmag[lane] : -1.0;
-      bi = lane < PANEL_THREADS / 32 ? widx[lane] : n;
-      for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, o);
-        int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) {
-        s_p = bi;
-        s_zero = !(best > 0.0);
-        piv[j] = bi;
-        if (s_zero && info[b] == 0) info[b] = j + 1;
-      }
-    }
-    __syncthreads();
-    const int p = s_p;
-    const bool zero = s_zero;
-    if (p != j) {
-      for (int c = t; c < n; c += PANEL_THREADS) {
-        E tmp = A[(long long)j * lda + c];
-        A[(long long)j * lda + c] = A[(long long)p * lda + c];
-        A[(long long)p * lda + c] = tmp;
-      }
-    }
-    __syncthreads();
-    const int w = j0 + nb - 1 - j;  // remaining panel columns
-    if (!zero) {
-      const E pv = A[(long long)j * lda + j];
-      if constexpr (is_fp64<E>::v) {
-        // FP64 issue slots are the scarce resource: one thread per row, one
-        // division and w multiply-adds per row
-        for (int r = j + 1 + t; r < n; r += PANEL_THREADS) {
-          E* row = A + (long long)r * lda + j;
-          const E l = el<E>::div(row[0], pv);
-          row[0] = l;
-          for (int c = 1; c <= w; ++c) row[c] = row[c] - mul(l, A[(long long)j * lda + j + c]);
-        }
-      } else {
-        // FP32: memory access dominates; one warp per row, lane c on column
-        // j + c (coalesced), pivot-row segment kept in a register
-        const E urow = lane <= w ? A[(long long)j * lda + j + lane] : el<E>::zero();
-        for (int r = j + 1 + warp; r < n; r += PANEL_THREADS / 32) {
-          E* row = A + (long long)r * lda + j;
-          const E l = el<E>::div(row[0], pv);
-          if (lane >= 1 && lane <= w) row[lane] = row[lane] - mul(l, urow);
-          if (lane == 0) row[0] = l;
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -454,17 +380,27 @@ void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const
     int splits = 1;
     if (t32 < kFill && k >= 256) {
       splits = (int)std::min<long long>((kFill + t32 - 1) / t32, k / 128);
-      splits = std::max(1, std::min(splits, 32));
+      splits = std::max(1, std::min(splits, kMaxCluster));
       if ((long long)batch * splits > 65535) splits = 1;
     }
-    if (splits > 1) {
-      dim3 gs((unsigned)(((long long)m * n + 255) / 256), batch);
-      k_scale<TC><<<gs, 256, 0, s>>>(C, m, n, ldc, sC, beta);
-      HS_COUNT_LAUNCH();
-    }
     dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch * splits);
-    k_gemm<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
-                                            splits);
+    if (splits == 1) {
+      k_gemm<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, 1);
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = dim3(256);
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 1;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = splits;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_gemm<TA, TB, TC>, opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                         splits);
+    }
     HS_COUNT_LAUNCH();
   }
   if (prof) prof_end(s, ev, flops_per_mac<TA, TB>() * (double)m * n * k * batch);
@@ -474,13 +410,7 @@ template <typename E>
 void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info, int batch) {
   for (int j0 = 0; j0 < n; j0 += NB) {
     int nb = n - j0 < NB ? n - j0 : NB;
-    if (n <= 256)
-      k_lu_panel<E, 128><<<batch, 128, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
-    else if (n <= 1024)
-      k_lu_panel<E, 256><<<batch, 256, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
-    else
-      k_lu_panel<E, 1024><<<batch, 1024, 0, s>>>(A, lda, sA, n, j0, nb, piv, sP, info);
-    HS_COUNT_LAUNCH();
+    lu_panel<E>(s, A, lda, sA, n, j0, nb, piv, sP, info, batch);
     int rest = n - j0 - nb;
     if (rest > 0) {
       trsm_diag<E>(s, A, lda, sA, j0, nb, 0, A + j0 + nb, lda, sA, rest, batch);

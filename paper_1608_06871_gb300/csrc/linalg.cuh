@@ -27,6 +27,13 @@ template <typename E>
 void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info,
                int batch);
 
+// Factor the panel columns [j0, j0 + nb) (nb <= 32) of the batch with row
+// pivoting and apply the row swaps to whole rows (panel.cu); piv[j0 .. j0+nb)
+// receives the swaps, piv[j0+nb .. n) is used as scratch.
+template <typename E>
+void lu_panel(cudaStream_t s, E* A, int lda, long long sA, int n, int j0, int nb, int* piv, long long sP, int* info,
+              int batch);
+
 // Solve A X = B (trans = OP_N) or A^T X = B (trans = OP_T) in place in B
 // (n x nrhs, leading dimension ldb) from the factors of lu_factor.
 template <typename E>

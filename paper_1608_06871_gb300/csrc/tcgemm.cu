@@ -13,14 +13,21 @@
 //                               row n + j holds (im B[l][j],  re B[l][j])
 //   D' = A' B'^T = [Re C | Im C].
 // Tile: 128 complex rows x 64 complex columns (D' is 128 x 128 FP32 in TMEM),
-// K chunks of 16 complex (32 real) staged by all 128 threads into shared
+// K chunks of 8 complex (16 real) staged by all 128 threads into shared
 // memory in the canonical K-major layout without swizzle (core matrices of 8
-// rows x 16 bytes), two stages, with the next chunk prefetched into
-// registers while the tensor cores work on the current one.  One thread
-// issues the MMAs (M = 128, N = 128, K = 8) and commits them to an mbarrier.
+// rows x 16 bytes), two stages of 32 KB (three CTAs per SM), with the next
+// chunk prefetched into registers while the tensor cores work on the current
+// one.  One thread issues the MMAs (M = 128, N = 128, K = 8) and commits them
+// to an mbarrier.  Shapes with too few tiles to fill the chip split k across
+// a thread-block cluster.
+#include <algorithm>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "linalg.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hs {
 
@@ -31,19 +38,22 @@ namespace {
 
 constexpr int TM = 128;         // complex rows per tile
 constexpr int TN = 64;          // complex columns per tile
-constexpr int TKC = 16;         // complex k per chunk
-constexpr int TK = 2 * TKC;     // real k per chunk (32)
+constexpr int TKC = 8;          // complex k per chunk
+constexpr int TK = 2 * TKC;     // real k per chunk (16)
 constexpr int NR = 2 * TN;      // real output columns (128)
 constexpr int TC_THREADS = 128;
-constexpr int OP_BYTES = TM * TK * 4;            // one operand copy: 128 rows x 32 floats = 16 KB
+constexpr int OP_BYTES = TM * TK * 4;            // one operand copy: 128 rows x 16 floats = 8 KB
 constexpr int STAGE_BYTES = 4 * OP_BYTES;        // A hi, A lo, B' hi, B' lo
-constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024;  // two stages + alignment slack
+constexpr int RED_LD = TN + 1;                   // padded row of the split-k partial tile (float2)
+constexpr int TC_SMEM = 2 * STAGE_BYTES + 2048;  // two stages (>= the partial tile) + alignment slack
+static_assert(TM * RED_LD * 8 <= 2 * STAGE_BYTES + 1024, "partial tile must fit the stage buffers");
 constexpr uint32_t LBO = (TM / 8) * 128;         // bytes between core matrices along k (16 row groups)
 constexpr uint32_t SBO = 128;                    // bytes between 8-row groups
 // instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
 constexpr uint32_t IDESC =
     (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 constexpr long long WAIT_LIMIT = 1LL << 26;      // bounded mbarrier waits
+constexpr int EP_LD = 17;                        // padded row of the epilogue transpose (float2)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -74,21 +84,36 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(ta));
+}
+
+// blockIdx.z = batch * splits + split; with splits > 1 the kernel runs in
+// clusters of `splits` CTAs along z, each covering a range of whole chunks of
+// k, and the partial tiles are summed in split order through distributed
+// shared memory (deterministic, no atomics).
+__global__ void __launch_bounds__(TC_THREADS, 3)
     k_cgemm_tc(int m, int n, int k, float2 alpha, const float2* __restrict__ A, int lda, long long sA,
                const float2* __restrict__ B, int ldb, long long sB, float2 beta, float2* __restrict__ C, int ldc,
-               long long sC) {
+               long long sC, int splits) {
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ uint32_t tslot;
   __shared__ __align__(8) uint64_t mbar[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.z;
+  const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
   A += b * sA;
   B += b * sB;
   C += b * sC;
   const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
-  const int nchunk = (k + TKC - 1) / TKC;
+  const int nch_all = (k + TKC - 1) / TKC;
+  const int per = (nch_all + splits - 1) / splits;
+  const int ch0 = sp * per, ch1 = min(nch_all, ch0 + per);
+  const int nchunk = max(0, ch1 - ch0);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(NR));
@@ -104,15 +129,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
 
-  // register prefetch: A chunk 128 x 16 complex = 1024 float4 (8 per thread),
-  // B chunk 16 x 64 complex = 512 float4 (4 per thread); a float4 is 2 complex
-  float4 ra[8], rb[4];
+  // register prefetch: A chunk 128 x 8 complex = 512 float4 (4 per thread),
+  // B chunk 8 x 64 complex = 256 float4 (2 per thread); a float4 is 2 complex
+  float4 ra[4], rb[2];
   auto prefetch = [&](int ch) {
     const int kb = ch * TKC;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      int q = tid + TC_THREADS * i;  // 0..1023
-      int r = q >> 3, c2 = (q & 7) * 2;  // complex column pair within the chunk
+    for (int i = 0; i < 4; ++i) {
+      int q = tid + TC_THREADS * i;        // 0..511
+      int r = q >> 2, c2 = (q & 3) * 2;    // complex column pair within the chunk
       int gr = row0 + r, gk = kb + c2;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gr < m) {
@@ -123,8 +148,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       ra[i] = v;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int q = tid + TC_THREADS * i;  // 0..511
+    for (int i = 0; i < 2; ++i) {
+      int q = tid + TC_THREADS * i;  // 0..255
       int l = q >> 5, j2 = (q & 31) * 2;
       int gk = kb + l, gc = col0 + j2;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -142,9 +167,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     float* Bhi = Alo + OP_BYTES / 4;
     float* Blo = Bhi + OP_BYTES / 4;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 4; ++i) {
       int q = tid + TC_THREADS * i;
-      int r = q >> 3, c4 = q & 7;  // real k' = 4 c4 .. 4 c4 + 3: one 16-byte core-matrix row
+      int r = q >> 2, c4 = q & 3;  // real k' = 4 c4 .. 4 c4 + 3: one 16-byte core-matrix row
       float4 v = ra[i];
       float4 h = make_float4(tf32(v.x), tf32(v.y), tf32(v.z), tf32(v.w));
       float4 lo = make_float4(tf32(v.x - h.x), tf32(v.y - h.y), tf32(v.z - h.z), tf32(v.w - h.w));
@@ -153,7 +178,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       *reinterpret_cast<float4*>(Alo + off) = lo;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2; ++i) {
       int q = tid + TC_THREADS * i;
       int l = q >> 5, j2 = (q & 31) * 2;
       float4 v = rb[i];  // B[l][j2], B[l][j2+1]
@@ -165,23 +190,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float e0 = re, e1 = -im, f0 = im, f1 = re;
         float h0 = tf32(e0), h1 = tf32(e1), g0 = tf32(f0), g1 = tf32(f1);
         int o1 = core_off(j, 2 * l), o2 = core_off(TN + j, 2 * l);
-        Bhi[o1] = h0;
-        Bhi[o1 + 1] = h1;
-        Blo[o1] = tf32(e0 - h0);
-        Blo[o1 + 1] = tf32(e1 - h1);
-        Bhi[o2] = g0;
-        Bhi[o2 + 1] = g1;
-        Blo[o2] = tf32(f0 - g0);
-        Blo[o2 + 1] = tf32(f1 - g1);
+        *reinterpret_cast<float2*>(Bhi + o1) = make_float2(h0, h1);
+        *reinterpret_cast<float2*>(Blo + o1) = make_float2(tf32(e0 - h0), tf32(e1 - h1));
+        *reinterpret_cast<float2*>(Bhi + o2) = make_float2(g0, g1);
+        *reinterpret_cast<float2*>(Blo + o2) = make_float2(tf32(f0 - g0), tf32(f1 - g1));
       }
     }
   };
 
   bool ok = true;
-  prefetch(0);
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int st = ch & 1;
-    if (ch >= 2) ok = ok && mbar_wait(su32(&mbar[st]), ((ch >> 1) - 1) & 1);  // MMAs of chunk ch-2 done
+  if (nchunk > 0) prefetch(ch0);
+  for (int c = 0; c < nchunk; ++c) {
+    const int st = c & 1;
+    if (c >= 2) ok = ok && mbar_wait(su32(&mbar[st]), ((c >> 1) - 1) & 1);  // MMAs of chunk c-2 done
     stage_store(st);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -197,7 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint64_t dB[3] = {sdesc(bhi + koff), sdesc(blo + koff), sdesc(bhi + koff)};
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-          const uint32_t acc = (ch > 0 || ks > 0 || t > 0) ? 1u : 0u;
+          const uint32_t acc = (c > 0 || ks > 0 || t > 0) ? 1u : 0u;
           asm volatile(
               "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
@@ -207,58 +228,89 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           su32(&mbar[st])));
     }
-    if (ch + 1 < nchunk) prefetch(ch + 1);
+    if (c + 1 < nchunk) prefetch(ch0 + c + 1);
   }
   // wait for the last commit of each stage
   if (nchunk >= 1) ok = ok && mbar_wait(su32(&mbar[(nchunk - 1) & 1]), ((nchunk - 1) >> 1) & 1);
   if (nchunk >= 2) ok = ok && mbar_wait(su32(&mbar[(nchunk - 2) & 1]), ((nchunk - 2) >> 1) & 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!ok) atomicExch(&g_tc_timeout, 1);
-  if (ok) {
-    // epilogue: warp w owns TMEM lanes (= rows) 32 w .. 32 w + 31
-    const int r = row0 + 32 * warp + lane;
-    for (int c0 = 0; c0 < TN; c0 += 16) {
-      uint32_t re[16], im[16];
-      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
-            "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]),
-            "=r"(re[15])
-          : "r"(ta + c0));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
-            "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]),
-            "=r"(im[15])
-          : "r"(ta + TN + c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (r < m) {
+  // all threads agree on the outcome before the warp-collective TMEM loads
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (!all_ok && tid == 0) atomicExch(&g_tc_timeout, 1);
+  const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
+  if (splits == 1) {
+    if (all_ok) {
+      // epilogue: warp w owns TMEM lanes (= rows) 32 w .. 32 w + 31; each 32 x 16
+      // block goes through shared memory (stage 0, free now) so that the global
+      // writes run along rows
+      float2* tr = reinterpret_cast<float2*>(sm) + warp * 32 * EP_LD;
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        uint32_t re[16], im[16];
+        tmem_ld16(ta + c0, re);
+        tmem_ld16(ta + TN + c0, im);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = col0 + c0 + j;
-          if (c < n) {
-            float2 d = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
-            float2 v = alpha * d;
+        for (int j = 0; j < 16; ++j)
+          tr[lane * EP_LD + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        __syncwarp();
+        const int cj = lane & 15, c = col0 + c0 + cj;
+#pragma unroll 4
+        for (int rr = lane >> 4; rr < 32; rr += 2) {
+          const int r = row0 + 32 * warp + rr;
+          if (r < m && c < n) {
+            const float2 v = alpha * tr[rr * EP_LD + cj];
             float2* pc = C + (long long)r * ldc + c;
-            if (!(beta.x == 0.f && beta.y == 0.f)) v = v + beta * (*pc);
-            *pc = v;
+            *pc = (beta.x == 0.f && beta.y == 0.f) ? v : v + beta * (*pc);
           }
         }
+        __syncwarp();
       }
     }
+  } else {
+    // split k: the whole partial tile goes to shared memory (both stages,
+    // free now), then the cluster's CTAs sum the partials in split order
+    // through distributed shared memory, rank r writing its share of the rows
+    float2* red = reinterpret_cast<float2*>(sm);
+    if (all_ok) {
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        uint32_t re[16], im[16];
+        tmem_ld16(ta + c0, re);
+        tmem_ld16(ta + TN + c0, im);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          red[(32 * warp + lane) * RED_LD + c0 + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+      }
+    }
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    const int rows_per = (TM + splits - 1) / splits;
+    const int rb = sp * rows_per, re_ = min(TM, rb + rows_per);
+    for (int e = rb * TN + tid; e < re_ * TN; e += TC_THREADS) {
+      const int rl = e / TN, cl_ = e % TN;
+      float2 sum = make_float2(0.f, 0.f);
+      for (int q = 0; q < splits; ++q) sum = sum + cl.map_shared_rank(red, q)[rl * RED_LD + cl_];
+      const int r = row0 + rl, c = col0 + cl_;
+      if (all_ok && r < m && c < n) {
+        const float2 v = alpha * sum;
+        float2* pc = C + (long long)r * ldc + c;
+        *pc = (beta.x == 0.f && beta.y == 0.f) ? v : v + beta * (*pc);
+      }
+    }
+    cl.sync();  // keep this CTA's partial tile alive until every rank has read it
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NR));
 }
 
+
 }  // namespace
 
 bool g_tc_enabled = true;  // process-wide switch (hs_set_tensor_cores)
 
 bool cgemm_tc_eligible(int opA, int opB, int m, int n, int k, int batch) {
-  return g_tc_enabled && opA == OP_N && opB == OP_N && m >= TM && n >= TN && k >= 4 * TKC && batch <= 65535;
+  return g_tc_enabled && opA == OP_N && opB == OP_N && m >= TM && n >= TN && k >= 8 * TKC && batch <= 65535;
 }
 
 void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A, int lda, long long sA,
@@ -270,8 +322,34 @@ void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A
     cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  dim3 grid((n + TN - 1) / TN, (m + TM - 1) / TM, batch);
-  k_cgemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  // split k when the tiles alone leave SMs idle (3 CTAs fit on each of 152 SMs)
+  constexpr long long kFill = 3 * 152;
+  const long long tiles = (long long)((m + TM - 1) / TM) * ((n + TN - 1) / TN) * batch;
+  const int nch = (k + TKC - 1) / TKC;
+  int splits = 1;
+  if (tiles < kFill && nch >= 16) {
+    splits = (int)std::min<long long>((kFill + tiles - 1) / tiles, nch / 8);
+    splits = std::max(1, std::min(splits, 8));  // portable cluster size
+    if ((long long)batch * splits > 65535) splits = 1;
+  }
+  dim3 grid((n + TN - 1) / TN, (m + TM - 1) / TM, batch * splits);
+  if (splits == 1) {
+    k_cgemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, 1);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TC_SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = splits;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_cgemm_tc, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits);
+  }
   HS_COUNT_LAUNCH();
 }
 

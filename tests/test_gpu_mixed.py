@@ -33,10 +33,10 @@ def test_mixed_gaussian_bumps_k5_vs_oracle(hs):
     x, y = S.node_coords()
     S.build_nodes(qt(x, y), w.k)
     uf = S.solve(al, th)
-    it, upd = hs.hs_refine_stats(S.ctx)
+    it, upd, est = hs.hs_refine_stats(S.ctx)
     ref, _ = F.forward_from_function(qt, w.k, w.n_leaf_side, w.R).solve_plane(al, th)
     assert rel(uf, ref) < MIXED_TOL
-    assert 2 <= it <= 8 and 0 <= upd <= 1e-9
+    assert 2 <= it <= 8 and 0 <= est <= 1e-9 and upd >= 0
 
 
 @pytest.mark.parametrize("nL,k,M,P", [(1, 3.0, 3, 5), (2, 4.0, 2, 9), (8, 9.3, 5, 7)])

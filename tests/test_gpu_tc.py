@@ -106,8 +106,8 @@ def test_mixed_solve_tc_on_off(hs):
         try:
             S = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, precision=hs.HS_MIXED).build(c, w.k)
             outs.append(S.solve(al, th))
-            it, upd = hs.hs_refine_stats(S.ctx)
-            assert 2 <= it <= 8 and 0 <= upd <= 1e-9
+            it, upd, est = hs.hs_refine_stats(S.ctx)
+            assert 2 <= it <= 8 and 0 <= est <= 1e-9 and upd >= 0
         finally:
             hs.hs_set_tensor_cores(True)
     rel = np.abs(outs[0] - outs[1]).max() / np.abs(outs[1]).max()

@@ -61,6 +61,17 @@ int hs_set_tensor_cores(int enable);
 int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream,
                int* used_tc);
 
+/* C = op(A) op(B) (+ C when accumulate != 0): complex128 (interleaved re,
+ * im), row-major, op(A) m x k, op(B) k x n, C m x n; op = transpose when
+ * transA / transB != 0 (A stored k x m, B stored n x k), no conjugation.
+ * DEVICE pointers on the current device, enqueued on `stream` (a
+ * cudaStream_t, NULL for the legacy default stream) and synchronised before
+ * return.  Runs the library's FP64 GEMM dispatch (the kernels of the FP64
+ * solver and of the mixed path's FP64 refinement).  Errors: HS_EINVAL
+ * (non-positive size, NULL pointer), HS_ECUDA. */
+int hs_zgemm(int transA, int transB, int m, int n, int k, const void* A, const void* B, void* C, int accumulate,
+             void* stream);
+
 /* Solve A[b] X[b] = B[b] in place in B for b < batch with the library's
  * batched LU (partial pivoting; tournament pivoting for panels taller than 256
  * rows) and triangular solves: complex (interleaved re, im), row-major,

@@ -71,6 +71,7 @@ _SIGS = {
     "hs_set_tensor_cores": (_I, [_I]),
     "hs_cgemm32": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
     "hs_lu_solve": (_I, [_I, _I, _I, _P, _P, _I, _P]),
+    "hs_zgemm": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _I, _P]),
 }
 
 
@@ -253,6 +254,16 @@ def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:
 
 def hs_set_tensor_cores(enable: bool):
     _check(None, lib().hs_set_tensor_cores(1 if enable else 0))
+
+
+def hs_zgemm(A, B, C, transA: bool = False, transB: bool = False, accumulate: bool = False, stream: int = 0):
+    """C = op(A) op(B) (+ C) for contiguous complex128 CUDA matrices (library FP64 GEMM)."""
+    m = A.shape[1] if transA else A.shape[0]
+    k = A.shape[0] if transA else A.shape[1]
+    n = B.shape[0] if transB else B.shape[1]
+    _check(None, lib().hs_zgemm(int(transA), int(transB), m, n, k, ctypes.c_void_p(A.data_ptr()),
+                                ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()), int(accumulate),
+                                ctypes.c_void_p(stream)))
 
 
 def hs_lu_solve(A, B, stream: int = 0):

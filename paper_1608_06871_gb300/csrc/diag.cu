@@ -135,6 +135,18 @@ int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int b
   return HS_OK;
 }
 
+int hs_zgemm(int transA, int transB, int m, int n, int k, const void* A, const void* B, void* C, int accumulate,
+             void* stream) {
+  if (m <= 0 || n <= 0 || k <= 0 || !A || !B || !C) return HS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int opA = transA ? hs::OP_T : hs::OP_N, opB = transB ? hs::OP_T : hs::OP_N;
+  hs::gemm<double2, double2, double2>(s, opA, opB, m, n, k, make_double2(1.0, 0.0), static_cast<const double2*>(A),
+                                      transA ? m : k, 0, static_cast<const double2*>(B), transB ? k : n, 0,
+                                      make_double2(accumulate ? 1.0 : 0.0, 0.0), static_cast<double2*>(C), n, 0, 1);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
+  return HS_OK;
+}
+
 int hs_lu_solve(int precision, int n, int nrhs, void* A, void* B, int batch, void* stream) {
   if (n <= 0 || nrhs <= 0 || batch <= 0 || batch > 65535 || !A || !B) return HS_EINVAL;
   if (precision != HS_FP64 && precision != HS_MIXED) return HS_EINVAL;

@@ -93,11 +93,20 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// Bump allocator over the context's workspace.  A request beyond the sized
+// capacity returns NULL and sets `over`; every caller checks `over` after its
+// requests and before any launch, so a sizing mistake is an error, never an
+// out-of-bounds access.
 struct Arena {
   char* base = nullptr;
   size_t cap = 0, off = 0;
+  bool over = false;
   template <typename T> T* get(size_t n) {
     size_t b = (n * sizeof(T) + 255) & ~size_t(255);
+    if (off + b > cap) {
+      over = true;
+      return nullptr;
+    }
     T* p = reinterpret_cast<T*>(base + off);
     off += b;
     return p;
@@ -739,6 +748,7 @@ int solve_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const d
   double2 *f = a.get<double2>((size_t)nb * M), *g = a.get<double2>((size_t)nb * M);
   double2* PS = a.get<double2>((size_t)2 * nb * M);
   double2* A2 = a.get<double2>((size_t)P * 2 * nb);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
   boundary_data(s, nb, M, ctx->k, f, g, ui, dni, PS);
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
@@ -757,7 +767,8 @@ size_t s3_elems(hs_ctx* ctx, int nrhs) {
 size_t mixed_bytes(hs_ctx* ctx, int M, int P) {
   const size_t nb = ctx->B.nb, nl = ctx->nleaf;
   size_t b = 6 * Arena::bytes(nb * M, 16) + Arena::bytes(2 * nb * M, 16) + Arena::bytes((size_t)P * 2 * nb, 16) +
-             2 * Arena::bytes((size_t)M * P, 16) + Arena::bytes(8, 8) + Arena::bytes(nl * NL * M, 16);
+             Arena::bytes((size_t)M * P, 16) + Arena::bytes(2 * nb * M, 8) + Arena::bytes((size_t)P * 2 * nb, 8) +
+             Arena::bytes((size_t)M * P, 8) + Arena::bytes(8, 8) + Arena::bytes(nl * NL * M, 16);
   b += Arena::bytes(nl * NL * M, 8) + 2 * Arena::bytes(field_buf_elems(ctx, M), 8) + Arena::bytes(nl * NE * M, 8) +
        Arena::bytes(s3_elems(ctx, M), 8) + 2 * Arena::bytes(nb * M, 8);
   for (auto& L : ctx->levels) b += Arena::bytes((size_t)L.nbox * 2 * L.ni * M, 8);
@@ -788,7 +799,10 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   double2 *ub = a.get<double2>(nbM), *psib = a.get<double2>(nbM), *rext = a.get<double2>(nbM);
   double2* PS = a.get<double2>(2 * nbM);
   double2* A2 = a.get<double2>((size_t)P * 2 * nb);
-  double2 *uf = a.get<double2>((size_t)M * P), *ufp = a.get<double2>((size_t)M * P);
+  double2* uf = a.get<double2>((size_t)M * P);
+  float2* PS32 = a.get<float2>(2 * nbM);
+  float2* A2_32 = a.get<float2>((size_t)P * 2 * nb);
+  float2* duf = a.get<float2>((size_t)M * P);
   double* nrm = a.get<double>(8);
   double2* X = a.get<double2>(nX);
   float2* Up = a.get<float2>(nX);
@@ -798,16 +812,18 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   float2 *f32 = a.get<float2>(nbM), *r32 = a.get<float2>(nbM);
   std::vector<float2*> TT(nlev);
   for (int li = 0; li < nlev; ++li) TT[li] = a.get<float2>((size_t)ctx->levels[li].nbox * 2 * ctx->levels[li].ni * M);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
 
   incident_plane(s, ctx->B, ctx->k, alphas, M, ui, dni);
   gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, one, ctx->d_Dm, nb, 0, ui, M, 0, zero, rinc, M, 0, 1);
   gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, mone, ctx->d_S, nb, 0, dni, M, 0, one, rinc, M, 0, 1);
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
+  convert_d2f(s, A2, A2_32, (long long)P * 2 * nb);
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * nX, s));
   ctx->refine_iters = 0;
   ctx->refine_update = -1.0;
   ctx->refine_est = -1.0;
-  double prev_upd = 0.0;
+  double prev_upd = 0.0, uf0_n2 = 0.0;
   bool converged = false;
   for (int it = 0; it < max_iter; ++it) {
     Phase pp("hs_refine_pass");
@@ -846,18 +862,21 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
     gemm<float2, float2, float2>(s, OP_N, OP_N, NL, M, NE, fone, ctx->d_Y32, NE, (long long)NL * NE, Fp, M,
                                  (long long)NE * M, it > 0 ? fone : fzero, Up, M, (long long)NL * M, nl);
     convert_f2d_add(s, Up, X, (long long)nX);
-    // far field of the FP64 iterate and its change
-    boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
-    scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
-    gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, one, PS, M, 0, A2, 2 * nb, 0, zero, uf, P, 0, 1);
+    // far field of this pass's FP32 field (the solution on the first pass, the
+    // correction after it), in FP32: its norm relative to the first pass's far
+    // field is the relative change of the far field
+    scattered32(s, Up, ctx->d_D1, ctx->nL, ctx->h, M, ui, dni, it == 0, PS32);
+    gemm<float2, float2, float2>(s, OP_T, OP_T, M, P, 2 * nb, fone, PS32, M, 0, A2_32, 2 * nb, 0, fzero, duf, P, 0, 1);
+    CK(cudaMemsetAsync(nrm, 0, sizeof(double), s));
+    norm2_32(s, duf, (long long)M * P, nrm);
+    double dn2 = 0.0;
+    CK(cudaMemcpyAsync(&dn2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     ctx->refine_iters = it + 1;
-    if (it > 0) {
-      CK(cudaMemsetAsync(nrm, 0, 2 * sizeof(double), s));
-      diff_norms(s, uf, ufp, (long long)M * P, nrm);
-      double h2[2];
-      CK(cudaMemcpyAsync(h2, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      const double upd = h2[1] > 0 ? std::sqrt(h2[0] / h2[1]) : 0.0;
+    if (it == 0) {
+      uf0_n2 = dn2;
+    } else {
+      const double upd = uf0_n2 > 0 ? std::sqrt(dn2 / uf0_n2) : 0.0;
       // error of the new iterate: the update itself until the contraction
       // rate rho of the passes is observed, then upd * rho / (1 - rho)
       double est = upd;
@@ -873,11 +892,15 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
         break;
       }
     }
-    std::swap(uf, ufp);
   }
   CK(cudaGetLastError());
   if (tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
   if (!converged) return fail(ctx, HS_ENOCONV, "iterative refinement did not reach the tolerance");
+  if (ufar) {  // far field of the converged FP64 iterate, in FP64
+    boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
+    scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
+    gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, one, PS, M, 0, A2, 2 * nb, 0, zero, uf, P, 0, 1);
+  }
   if (ufar) CK(cudaMemcpyAsync(ufar, uf, sizeof(double2) * M * P, cudaMemcpyDeviceToDevice, s));
   if (Xout) CK(cudaMemcpyAsync(Xout, X, sizeof(double2) * nX, cudaMemcpyDeviceToDevice, s));
   return HS_OK;
@@ -896,6 +919,7 @@ int fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M,
   double2* Uleaf = a.get<double2>((size_t)ctx->nleaf * NL * nr);
   double2* A2 = a.get<double2>((size_t)P * 2 * nb);
   double2 *E = a.get<double2>((size_t)nb * P), *CP = a.get<double2>((size_t)nb * P);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
   CKR(sweep_down(ctx, s, f, M, bufA, bufB, T3, Uleaf));
   leaf_to_grid(s, Uleaf, NL, ctx->nL, M, Ug);
@@ -918,6 +942,7 @@ int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, cons
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
   double2* Ug = a.get<double2>(plane * M);
   double2* Zg = a.get<double2>(plane * P);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CKR(fields_and_adjoint(ctx, s, alphas, M, thetas, P, Ug, Zg, a));
   interior_sine_tables(s, ctx->d_xint, ctx->n14, ctx->S1, ctx->S2, ctx->d_sxi, ctx->d_syi);
   size_t smem = sizeof(double2) * ((size_t)ctx->S1 * ctx->S2 + ctx->n14 + ctx->S1);
@@ -955,6 +980,7 @@ int gradient_core(hs_ctx* ctx, cudaStream_t s, const double* ddata, const double
   double2* Zmix = a.get<double2>(plane * M);
   double* hre = a.get<double>(plane);
   double* T1 = a.get<double>((size_t)ctx->S1 * ctx->n14);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   {
     Arena sub = a;
     const int nb = ctx->B.nb;
@@ -1188,6 +1214,7 @@ int hs_fields_dev(hs_ctx* ctx, const double* alphas, int M, double* u, void* str
   double2 *bufA = a.get<double2>(field_buf_elems(ctx, M)), *bufB = a.get<double2>(field_buf_elems(ctx, M));
   double2* T3 = a.get<double2>(t3_elems(ctx, M));
   double2* Uleaf = a.get<double2>((size_t)ctx->nleaf * NL * M);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
   CKR(sweep_down(ctx, s, f, M, bufA, bufB, T3, Uleaf));
   leaf_to_nodes(s, Uleaf, ctx->nL, M, reinterpret_cast<double2*>(u));
@@ -1223,6 +1250,7 @@ int hs_forward_dev(hs_ctx* ctx, const double* alphas, int M, const double* theta
   double2 *bufA = a.get<double2>(field_buf_elems(ctx, M)), *bufB = a.get<double2>(field_buf_elems(ctx, M));
   double2* T3 = a.get<double2>(t3_elems(ctx, M));
   double2* Uleaf = a.get<double2>((size_t)ctx->nleaf * NL * M);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CKR(root_solve(ctx, s, alphas, M, ui, dni, f, g));
   boundary_data(s, nb, M, ctx->k, f, g, ui, dni, PS);
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
@@ -1259,6 +1287,7 @@ int hs_jacobian(hs_ctx* ctx, const double* alphas, int M, const double* thetas, 
   double* da = a.get<double>(M);
   double* dt = a.get<double>(P);
   double2* dJ = a.get<double2>(nJ);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CKR(jacobian_into(ctx, s, da, M, dt, P, dJ, a));
@@ -1298,6 +1327,7 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
   double* A = a.get<double>((size_t)nm * nm);
   double* bv = a.get<double>(nm);
   int* piv = a.get<int>(nm);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
@@ -1366,6 +1396,7 @@ int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M, co
   double* ddata = a.get<double>((size_t)2 * MP);
   double* dg = a.get<double>(nm);
   double* dm = a.get<double>(8);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));

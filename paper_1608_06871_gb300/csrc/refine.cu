@@ -172,6 +172,53 @@ __global__ void k_scattered(const double2* __restrict__ ub, const double2* __res
   PS[n + e] = psib[e] - dni[e];
 }
 
+// Scattered boundary data [u - u_inc; d_n u - d_n u_inc] (root order) of an
+// FP32 leaf field, in FP32; without the incident terms when sub_inc == 0 (a
+// correction field).  Feeds the FP32 far field of one refinement pass.
+__global__ void k_scattered32(const float2* __restrict__ U32, const double* __restrict__ D1, int nL, double h,
+                              int nrhs, const double2* __restrict__ ui, const double2* __restrict__ dni, int sub_inc,
+                              float2* __restrict__ PS) {
+  const int nb = 56 * nL;
+  const long long n = (long long)nb * nrhs;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int jn = (int)(e / nrhs), j = (int)(e % nrhs);
+  const int side = jn / (14 * nL), i = (jn % (14 * nL)) / 14, t = jn % 14 + 1;
+  int leaf, a, b;
+  switch (side) {
+    case 0: leaf = i; a = t; b = 0; break;
+    case 1: leaf = i * nL + (nL - 1); a = 15; b = t; break;
+    case 2: leaf = (nL - 1) * nL + i; a = t; b = 15; break;
+    default: leaf = i * nL; a = 0; b = t; break;
+  }
+  const float2* U = U32 + (long long)leaf * NL * nrhs;
+  const float sc = (float)(2.0 / h);
+  const int cpos = (a == 15 || b == 15) ? 15 : 0;
+  const float sg = cpos == 15 ? 1.f : -1.f;
+  float2 d = make_float2(0.f, 0.f);
+  for (int c = 0; c < 16; ++c) {
+    const float w = sg * (float)D1[cpos * 16 + c] * sc;
+    const float2 v = (b == 0 || b == 15) ? U[(long long)lidx(a, c) * nrhs + j] : U[(long long)lidx(c, b) * nrhs + j];
+    d = make_float2(d.x + w * v.x, d.y + w * v.y);
+  }
+  float2 u = U[(long long)lidx(a, b) * nrhs + j];
+  if (sub_inc) {
+    u = make_float2(u.x - (float)ui[e].x, u.y - (float)ui[e].y);
+    d = make_float2(d.x - (float)dni[e].x, d.y - (float)dni[e].y);
+  }
+  PS[e] = u;
+  PS[n + e] = d;
+}
+
+// out[0] += sum |a|^2 (FP32 data, FP64 sums)
+__global__ void k_norm2_32(const float2* __restrict__ a, long long n, double* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < n) v = (double)a[i].x * a[i].x + (double)a[i].y * a[i].y;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, v);
+}
+
 // out[0] += sum |a - b|^2, out[1] += sum |a|^2
 __global__ void k_diff_norms(const double2* __restrict__ a, const double2* __restrict__ b, long long n,
                              double* __restrict__ out) {
@@ -249,6 +296,18 @@ void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, do
                               Upart + (long long)NI * nrhs, nrhs, sU, one, Upart, nrhs, sU, nleaf);
   long long n = (long long)nleaf * NE * nrhs;
   k_leaf_h<<<blocks(n), 256, 0, s>>>(Upart, nleaf, eta, nrhs, H);
+  HS_COUNT_LAUNCH();
+}
+
+void scattered32(cudaStream_t s, const float2* U32, const double* D1, int nL, double h, int nrhs, const double2* ui,
+                 const double2* dni, bool sub_inc, float2* PS) {
+  long long n = 56LL * nL * nrhs;
+  k_scattered32<<<blocks(n), 256, 0, s>>>(U32, D1, nL, h, nrhs, ui, dni, sub_inc ? 1 : 0, PS);
+  HS_COUNT_LAUNCH();
+}
+
+void norm2_32(cudaStream_t s, const float2* a, long long n, double* out) {
+  k_norm2_32<<<blocks(n), 256, 0, s>>>(a, n, out);
   HS_COUNT_LAUNCH();
 }
 

@@ -132,6 +132,10 @@ void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, do
 void scattered_data(cudaStream_t s, const double2* ub, const double2* psib, const double2* ui, const double2* dni,
                     long long n, double2* PS);
 void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out);  // out += {|a-b|^2, |a|^2}
+// FP32 scattered boundary data [u (- u_inc); d_n u (- d_n u_inc)] of an FP32 leaf field, and out += |a|^2.
+void scattered32(cudaStream_t s, const float2* U32, const double* D1, int nL, double h, int nrhs, const double2* ui,
+                 const double2* dni, bool sub_inc, float2* PS);
+void norm2_32(cudaStream_t s, const float2* a, long long n, double* out);
 // dst[r][:] = src[idx[r]][:] (rows of ncols elements); dst[a][b] = src[idx[a]][idx[b]] for square matrices.
 template <typename C> void permute_rows(cudaStream_t s, const C* src, const int* idx, int nrows, int ncols, C* dst);
 template <typename C> void permute_square(cudaStream_t s, const C* src, const int* idx, int n, C* dst);

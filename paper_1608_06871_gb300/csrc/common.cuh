@@ -111,6 +111,39 @@ __host__ __device__ inline bool is_zero(float2 a) { return a.x == 0.0f && a.y ==
 __host__ __device__ inline float addv(float a, float b) { return a + b; }
 __host__ __device__ inline float2 addv(float2 a, float2 b) { return a + b; }
 template <> __host__ __device__ inline float scal<float, float>(float s, float v) { return s * v; }
+
+// acc + a b with one fused multiply-add per real product (4 for complex x
+// complex instead of 2 products, 1 product-sum and 2 additions): the FP64
+// pipe is the binding resource of the GEMM kernels.
+__host__ __device__ inline double fmac(double acc, double a, double b) { return fma(a, b, acc); }
+__host__ __device__ inline double2 fmac(double2 acc, double a, double2 b) {
+  return make_double2(fma(a, b.x, acc.x), fma(a, b.y, acc.y));
+}
+__host__ __device__ inline double2 fmac(double2 acc, double2 a, double b) {
+  return make_double2(fma(a.x, b, acc.x), fma(a.y, b, acc.y));
+}
+__host__ __device__ inline double2 fmac(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(-a.y, b.y, fma(a.x, b.x, acc.x)), fma(a.y, b.x, fma(a.x, b.y, acc.y)));
+}
+__host__ __device__ inline float fmac(float acc, float a, float b) { return fmaf(a, b, acc); }
+__host__ __device__ inline float2 fmac(float2 acc, float a, float2 b) {
+  return make_float2(fmaf(a, b.x, acc.x), fmaf(a, b.y, acc.y));
+}
+__host__ __device__ inline float2 fmac(float2 acc, float2 a, float b) {
+  return make_float2(fmaf(a.x, b, acc.x), fmaf(a.y, b, acc.y));
+}
+__host__ __device__ inline float2 fmac(float2 acc, float2 a, float2 b) {
+  return make_float2(fmaf(-a.y, b.y, fmaf(a.x, b.x, acc.x)), fmaf(a.y, b.x, fmaf(a.x, b.y, acc.y)));
+}
+// acc - a b, fused the same way
+__host__ __device__ inline double fmsc(double acc, double a, double b) { return fma(-a, b, acc); }
+__host__ __device__ inline double2 fmsc(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(a.y, b.y, fma(-a.x, b.x, acc.x)), fma(-a.y, b.x, fma(-a.x, b.y, acc.y)));
+}
+__host__ __device__ inline float fmsc(float acc, float a, float b) { return fmaf(-a, b, acc); }
+__host__ __device__ inline float2 fmsc(float2 acc, float2 a, float2 b) {
+  return make_float2(fmaf(a.y, b.y, fmaf(-a.x, b.x, acc.x)), fmaf(-a.y, b.x, fmaf(-a.x, b.y, acc.y)));
+}
 template <> __host__ __device__ inline float2 scal<float2, float2>(float2 s, float2 v) { return s * v; }
 
 }  // namespace hs

@@ -81,10 +81,10 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, in
     for (int kk = 0; kk < BK; ++kk) {
       TA a0 = As[kk][ty], a1 = As[kk][ty + 16];
       TB b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-      acc[0][0] = addv(acc[0][0], mul(a0, b0));
-      acc[0][1] = addv(acc[0][1], mul(a0, b1));
-      acc[1][0] = addv(acc[1][0], mul(a1, b0));
-      acc[1][1] = addv(acc[1][1], mul(a1, b1));
+      acc[0][0] = fmac(acc[0][0], a0, b0);
+      acc[0][1] = fmac(acc[0][1], a0, b1);
+      acc[1][0] = fmac(acc[1][0], a1, b0);
+      acc[1][1] = fmac(acc[1][1], a1, b1);
     }
     __syncthreads();
   }
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, in
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = addv(acc[i][j], mul(a[i], bb[j]));
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmac(acc[i][j], a[i], bb[j]);
     }
     __syncthreads();
   }
@@ -249,13 +249,13 @@ __global__ void __launch_bounds__(32 * TRSM_WARPS) k_trsm_diag(const E* A, int l
     for (int s = 0; s < nb; ++s) {
       if (!unit && lane == s) x = el<E>::div(x, T[s][s]);
       E xs = shfl(x, s);
-      if (lane > s && lane < nb) x = x - mul(T[lane][s], xs);
+      if (lane > s && lane < nb) x = fmsc(x, T[lane][s], xs);
     }
   } else {
     for (int s = nb - 1; s >= 0; --s) {
       if (!unit && lane == s) x = el<E>::div(x, T[s][s]);
       E xs = shfl(x, s);
-      if (lane < s) x = x - mul(T[lane][s], xs);
+      if (lane < s) x = fmsc(x, T[lane][s], xs);
     }
   }
   if (lane < nb) B[(long long)(i0 + lane) * ldb + col] = x;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(128) k_trsm_diag_col(const E* A, int lda, long
     for (int r = 0; r < NB; ++r) {
       E v = x[r];
 #pragma unroll
-      for (int c = 0; c < r; ++c) v = v - mul(T[r][c], x[c]);
+      for (int c = 0; c < r; ++c) v = fmsc(v, T[r][c], x[c]);
       x[r] = (unit || r >= nb) ? v : el<E>::div(v, T[r][r]);
     }
   } else {
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(128) k_trsm_diag_col(const E* A, int lda, long
     for (int r = NB - 1; r >= 0; --r) {
       E v = x[r];
 #pragma unroll
-      for (int c = r + 1; c < NB; ++c) v = v - mul(T[r][c], x[c]);
+      for (int c = r + 1; c < NB; ++c) v = fmsc(v, T[r][c], x[c]);
       x[r] = (unit || r >= nb) ? v : el<E>::div(v, T[r][r]);
     }
   }

@@ -95,7 +95,7 @@ __device__ void tile_lu(E* T, int ld, int rows, int nb, int* rid, int* sp, int* 
       E* row = T + t * ld;
       const E l = el<E>::div(row[j], pv);
       row[j] = l;
-      for (int c = j + 1; c < nb; ++c) row[c] = row[c] - mul(l, T[j * ld + c]);
+      for (int c = j + 1; c < nb; ++c) row[c] = fmsc(row[c], l, T[j * ld + c]);
     }
     __syncthreads();
   }
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(FIN_T) k_tp_finish(E* A, int lda, long long sA
 #pragma unroll
   for (int c = 0; c < PNB; ++c) {
 #pragma unroll
-    for (int i = 0; i < c; ++i) x[c] = x[c] - mul(x[i], U[i][c]);
+    for (int i = 0; i < c; ++i) x[c] = fmsc(x[c], x[i], U[i][c]);
     if (el<E>::mag2(U[c][c]) > 0.0) x[c] = el<E>::div(x[c], U[c][c]);
   }
 #pragma unroll

@@ -307,7 +307,9 @@ def run_hs(args, world, rank, local):
                              "achieved": achieved, "peak": peak if fp64_fam else None, "unit": "TFLOP/s",
                              "frac": (achieved / peak) if (achieved and peak and fp64_fam) else None,
                              "peak_source": "measured FP64 DFMA rate (hs_peak_fp64, this run)",
-                             "traffic": None, "launches": gemm_n, "kernel_ms_per_step": gemm_ms / args.steps,
+                             "traffic": GEMM64_TRAFFIC if (fp64_fam and prec == hs.HS_MIXED) else None,
+                             "traffic_note": GEMM64_TRAFFIC_NOTE if (fp64_fam and prec == hs.HS_MIXED) else None,
+                             "launches": gemm_n, "kernel_ms_per_step": gemm_ms / args.steps,
                              "algorithmic_tflop_per_step": gemm_flops / args.steps / 1e12},
                 "phases": main["phases"], "clocks": main["clocks"]}
         if other is not None:
@@ -334,6 +336,15 @@ def run_hs(args, world, rank, local):
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     main["solver"].close()
+
+
+# DRAM bytes (read + write) of one launch of the dominant FP64 GEMM shape of the
+# mixed step (the 1792 x 128 x 1792 exterior-residual product), from an ncu
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
+# its algorithmic bytes are 62.4 MB (matrix, right-hand sides, C read and written).
+GEMM64_TRAFFIC = 60.0e6
+GEMM64_TRAFFIC_NOTE = ("bytes per launch of the 1792x128x1792 complex exterior-residual GEMM (ncu dram read+write, "
+                       "58.8 MB + 1.0-1.5 MB); algorithmic 62.4 MB")
 
 
 def tf32_peak():

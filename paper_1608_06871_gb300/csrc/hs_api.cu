@@ -155,7 +155,7 @@ struct hs_ctx {
   double bie_k = -1.0;  // wavenumber the layer-potential matrices were assembled for
   int *d_root_of_bie = nullptr, *d_bie_of_root = nullptr;  // root box order <-> boundary-node order
   double2* d_Rb = nullptr;  // root ItI map in boundary-node order (FP64)
-  float2* d_Rb32 = nullptr; // same, FP32
+  float2* d_Rb32 = nullptr; // same, FP32; after the build it holds C^{-1} (FP32)
   // per-call workspace
   char* ws_base = nullptr;
   size_t ws_cap = 0;
@@ -604,6 +604,10 @@ int factor_mixed(hs_ctx* ctx, double k) {
   gemm<float2, float2, float2>(s, OP_N, OP_N, nb, nb, nb, make_float2(-1.f, 0.f), ctx->d_B2_32, nb, 0, ctx->Rroot32,
                                nb, 0, make_float2(1.f, 0.f), ctx->d_C32, nb, 0, 1);
   lu_factor<float2>(s, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, ctx->d_info, 1);
+  // C^{-1} explicitly (in the buffer of the root map, no longer needed): each
+  // refinement pass then applies it with one GEMM
+  lu_inverse<float2>(s, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, ctx->d_Rb32, nb, 0, 1);
+  ctx->Rroot32 = nullptr;
   CK(cudaGetLastError());
   CKR(check_info(ctx));
   ctx->k = k;
@@ -849,9 +853,9 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
       CK(cudaMemcpyAsync(f32, r32, sizeof(float2) * nbM, cudaMemcpyDeviceToDevice, s));
       gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_B2_32, nb, 0, tmp, M, 0, fone, f32, M, 0, 1);
     }
-    lu_solve<float2>(s, OP_N, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, f32, M, 0, M, 1);
+    gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_Rb32, nb, 0, f32, M, 0, fzero, r32, M, 0, 1);
     // downward sweep (adds the particular interface impedances after the first pass)
-    permute_rows<float2>(s, f32, ctx->d_bie_of_root, nb, M, B1);  // root box order
+    permute_rows<float2>(s, r32, ctx->d_bie_of_root, nb, M, B1);  // root box order
     const float2* Fp = B1;
     float2* out = B0;
     for (int li = nlev - 1; li >= 0; --li) {

@@ -421,6 +421,24 @@ void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, lon
   }
 }
 
+namespace {
+template <typename E> __global__ void k_identity(E* A, int n, int lda, long long sA) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int r = (int)(e / n), c = (int)(e % n);
+  A[blockIdx.y * sA + (long long)r * lda + c] = r == c ? el<E>::one() : el<E>::zero();
+}
+}  // namespace
+
+template <typename E>
+void lu_inverse(cudaStream_t s, const E* A, int lda, long long sA, int n, const int* piv, long long sP, E* Inv,
+                int ldi, long long sI, int batch) {
+  dim3 g((unsigned)(((long long)n * n + 255) / 256), batch);
+  k_identity<E><<<g, 256, 0, s>>>(Inv, n, ldi, sI);
+  HS_COUNT_LAUNCH();
+  lu_solve<E>(s, OP_N, A, lda, sA, n, piv, sP, Inv, ldi, sI, n, batch);
+}
+
 template <typename E>
 void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int n, const int* piv, long long sP, E* B,
               int ldb, long long sB, int nrhs, int batch) {
@@ -499,6 +517,8 @@ template void gemm<float2, float, float2>(cudaStream_t, int, int, int, int, int,
                                           int);
 template void lu_factor<float>(cudaStream_t, float*, int, long long, int, int*, long long, int*, int);
 template void lu_factor<float2>(cudaStream_t, float2*, int, long long, int, int*, long long, int*, int);
+template void lu_inverse<float2>(cudaStream_t, const float2*, int, long long, int, const int*, long long, float2*, int,
+                                 long long, int);
 template void lu_solve<float>(cudaStream_t, int, const float*, int, long long, int, const int*, long long, float*, int,
                               long long, int, int);
 template void lu_solve<float2>(cudaStream_t, int, const float2*, int, long long, int, const int*, long long, float2*,

@@ -27,6 +27,12 @@ template <typename E>
 void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info,
                int batch);
 
+// Inv[b] = A[b]^{-1} (n x n, leading dimension ldi) from the factors of
+// lu_factor (identity right-hand sides through lu_solve).
+template <typename E>
+void lu_inverse(cudaStream_t s, const E* A, int lda, long long sA, int n, const int* piv, long long sP, E* Inv,
+                int ldi, long long sI, int batch);
+
 // Factor the panel columns [j0, j0 + nb) (nb <= 32) of the batch with row
 // pivoting and apply the row swaps to whole rows (panel.cu); piv[j0 .. j0+nb)
 // receives the swaps, piv[j0+nb .. n) is used as scratch.

@@ -16,6 +16,8 @@
 // where A = R^a, B = R^b restricted to the index sets and h the children's
 // particular outgoing impedances (body loads).  The level routines do this
 // with batched gathers, GEMMs and LU factorisations over all parents of a level.
+#include <type_traits>
+
 #include "tree.cuh"
 
 namespace hs {
@@ -213,16 +215,34 @@ template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const
   k_gather_U2<C><<<dim3(grid_for((long long)np * ni, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_I3a,
                                                                                L.d_I3b, L.d_src, ni, np, O.U2);
   HS_COUNT_LAUNCH();
-  k_gather_diag<C><<<dim3(grid_for(pp, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_src, np, O.R);
-  HS_COUNT_LAUNCH();
+  constexpr bool kInv = std::is_same<C, float2>::value;  // FP32 factors keep W explicitly
+  if (!kInv) {
+    k_gather_diag<C><<<dim3(grid_for(pp, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_src, np, O.R);
+    HS_COUNT_LAUNCH();
+  }
   // M = I - B33 A33
   gemm<C, C, C>(s, OP_N, OP_N, ni, ni, ni, mone, O.B33, ni, nn, O.A33, ni, nn, one, O.M, ni, nn, nb);
   // top = B33 * bottom - top  (V = B33 Aa - Bb)
   gemm<C, C, C>(s, OP_N, OP_N, ni, np, ni, one, O.B33, ni, nn, O.XZ + (long long)ni * np, np, xz, mone, O.XZ, np, xz,
                 nb);
   lu_factor<C>(s, O.M, ni, nn, ni, O.Mpiv, ni, info, nb);
-  // X = M^{-1} V (top half)
-  lu_solve<C>(s, OP_N, O.M, ni, nn, ni, O.Mpiv, ni, O.XZ, np, xz, np, nb);
+  if constexpr (kInv) {
+    // W = M^{-1} explicitly (the sweeps then apply it with one GEMM per
+    // level); R is free until its diagonal blocks are gathered and stages W
+    // and then X = W V
+    const C zero = el<C>::zero();
+    lu_inverse<C>(s, O.M, ni, nn, ni, O.Mpiv, ni, O.R, ni, pp, nb);
+    cudaMemcpy2DAsync(O.M, nn * sizeof(C), O.R, pp * sizeof(C), nn * sizeof(C), nb, cudaMemcpyDeviceToDevice,
+                      s);
+    gemm<C, C, C>(s, OP_N, OP_N, ni, np, ni, one, O.M, ni, nn, O.XZ, np, xz, zero, O.R, np, pp, nb);
+    cudaMemcpy2DAsync(O.XZ, xz * sizeof(C), O.R, pp * sizeof(C), (size_t)ni * np * sizeof(C), nb,
+                      cudaMemcpyDeviceToDevice, s);
+    k_gather_diag<C><<<dim3(grid_for(pp, 256), nb), 256, 0, s>>>(Rc, nc, L.d_alpha, L.d_beta, L.d_src, np, O.R);
+    HS_COUNT_LAUNCH();
+  } else {
+    // X = M^{-1} V (top half)
+    lu_solve<C>(s, OP_N, O.M, ni, nn, ni, O.Mpiv, ni, O.XZ, np, xz, np, nb);
+  }
   // bottom = -A33 X - bottom  (Z = -Aa - A33 X)
   gemm<C, C, C>(s, OP_N, OP_N, ni, np, ni, mone, O.A33, ni, nn, O.XZ, np, xz, mone, O.XZ + (long long)ni * np, np, xz,
                 nb);
@@ -274,7 +294,7 @@ void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& 
 }
 
 template <typename C>
-void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Hc, const C* S3, C* TT, C* Hp,
+void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Hc, C* S3, C* TT, C* Hp,
                     int nrhs) {
   const int ni = L.ni, np = L.np, nb = L.nbox;
   const long long nn = (long long)ni * ni, tt = 2LL * ni * nrhs;
@@ -286,7 +306,14 @@ void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, co
   // top := B33 (h3a - s_b) - (h3b - s_a);  t_a = W top
   gemm<C, C, C>(s, OP_N, OP_N, ni, nrhs, ni, one, O.B33, ni, nn, TT + (long long)ni * nrhs, nrhs, tt, mone, TT, nrhs,
                 tt, nb);
-  lu_solve<C>(s, OP_N, O.M, ni, nn, ni, O.Mpiv, ni, TT, nrhs, tt, nrhs, nb);
+  if constexpr (std::is_same<C, float2>::value) {
+    // M holds W explicitly: t_a = W top through S3 (consumed by the gather)
+    gemm<C, C, C>(s, OP_N, OP_N, ni, nrhs, ni, one, O.M, ni, nn, TT, nrhs, tt, el<C>::zero(), S3, nrhs, tt, nb);
+    cudaMemcpy2DAsync(TT, tt * sizeof(C), S3, tt * sizeof(C), (size_t)ni * nrhs * sizeof(C), nb,
+                      cudaMemcpyDeviceToDevice, s);
+  } else {
+    lu_solve<C>(s, OP_N, O.M, ni, nn, ni, O.Mpiv, ni, TT, nrhs, tt, nrhs, nb);
+  }
   // bottom := -A33 t_a - (h3a - s_b) = t_b
   gemm<C, C, C>(s, OP_N, OP_N, ni, nrhs, ni, mone, O.A33, ni, nn, TT, nrhs, tt, mone, TT + (long long)ni * nrhs, nrhs,
                 tt, nb);
@@ -331,7 +358,7 @@ template <typename C> void permute_square(cudaStream_t s, const C* src, const in
   template void merge_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, int*);                  \
   template void sweep_down_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool); \
   template void sweep_adjoint_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int);    \
-  template void sweep_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, const C*, C*, C*, int); \
+  template void sweep_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, C*, int);       \
   template void permute_rows<C>(cudaStream_t, const C*, const int*, int, int, C*);                                  \
   template void permute_square<C>(cudaStream_t, const C*, const int*, int, C*);
 HS_INST(double2)

@@ -39,7 +39,7 @@ struct LevelMaps {
 template <typename C> struct LevelOps {
   C* XZ;      // [nbox][2 ni][np]  interface impedances from the parent's: [X; Z]
   C* U2;      // [nbox][np][ni]  rows < n1: A13 (alpha exterior x interface), rows >= n1: B23
-  C *A33, *B33, *M;  // [nbox][ni][ni]; M holds the LU of I - B33 A33
+  C *A33, *B33, *M;  // [nbox][ni][ni]; M: LU of I - B33 A33 (FP64), W = (I - B33 A33)^{-1} (FP32)
   int* Mpiv;  // [nbox][ni]
   C* R;       // [nbox][np][np]  parent impedance-to-impedance maps
 };
@@ -65,11 +65,13 @@ template <typename C>
 void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lp, C* MU, C* Lc,
                          int nrhs);
 // Upward (particular) pass of one level: children's outgoing particular
-// impedances Hc and the interface residual terms S3 ([s_a; s_b] per box, or
-// NULL) give the particular interface impedances TT = [t_a; t_b] (kept for the
-// downward pass) and the parent's particular impedances Hp.
+// impedances Hc and the interface residual terms S3 ([s_a; s_b] per box) give
+// the particular interface impedances TT = [t_a; t_b] (kept for the downward
+// pass) and the parent's particular impedances Hp.  S3 is consumed (reused as
+// scratch).  For C = float2 the level's M holds W = (I - B33 A33)^{-1} itself
+// (merge_level stores it explicitly), for C = double2 its LU factors.
 template <typename C>
-void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Hc, const C* S3, C* TT, C* Hp,
+void sweep_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Hc, C* S3, C* TT, C* Hp,
                     int nrhs);
 
 // Compatibility wrappers for the FP64 path.

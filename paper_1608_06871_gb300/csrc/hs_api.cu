@@ -156,6 +156,8 @@ struct hs_ctx {
   int *d_root_of_bie = nullptr, *d_bie_of_root = nullptr;  // root box order <-> boundary-node order
   double2* d_Rb = nullptr;  // root ItI map in boundary-node order (FP64)
   float2* d_Rb32 = nullptr; // same, FP32; after the build it holds C^{-1} (FP32)
+  double2* d_DS = nullptr;   // mixed: [D - I/2, -S] (N_b x 2 N_b), the exterior rows on [u; d_n u]
+  float2* d_DS32 = nullptr;  // same, FP32
   // per-call workspace
   char* ws_base = nullptr;
   size_t ws_cap = 0;
@@ -502,6 +504,8 @@ int setup_boundary(hs_ctx* ctx) {
     CKR(dalloc(ctx, &ctx->d_B2_32, nn));
     CKR(dalloc(ctx, &ctx->d_C32, nn));
     CKR(dalloc(ctx, &ctx->d_Cpiv32, nb));
+    CKR(dalloc(ctx, &ctx->d_DS, 2 * nn));
+    CKR(dalloc(ctx, &ctx->d_DS32, 2 * nn));
   }
   CKR(dalloc(ctx, &ctx->d_D1, 256));
   CK(cudaMemcpy(ctx->d_D1, D1.data(), sizeof(double) * 256, cudaMemcpyHostToDevice));
@@ -569,6 +573,7 @@ int setup(hs_ctx* ctx) {
     CKR(dalloc(ctx, &w.Kinv, nl * NE * NE));
     CKR(dalloc(ctx, &w.piv, nl * NI));
     CKR(dalloc(ctx, &w.pivK, nl * NE));
+    CKR(dalloc(ctx, &w.Ainv, nl * NI * NI));
   }
   CKR(setup_tree(ctx));
   CKR(setup_boundary(ctx));
@@ -598,6 +603,7 @@ int factor_mixed(hs_ctx* ctx, double k) {
     bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
     bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
     convert_d2f(s, ctx->d_B2, ctx->d_B2_32, nn);
+    stack_exterior(s, ctx->d_Dm, ctx->d_S, nb, ctx->d_DS, ctx->d_DS32);
     ctx->bie_k = k;
   }
   convert_d2f(s, ctx->d_B1, ctx->d_C32, nn);
@@ -774,6 +780,7 @@ size_t mixed_bytes(hs_ctx* ctx, int M, int P) {
              Arena::bytes((size_t)M * P, 16) + Arena::bytes(2 * nb * M, 8) + Arena::bytes((size_t)P * 2 * nb, 8) +
              Arena::bytes((size_t)M * P, 8) + Arena::bytes(8, 8) + Arena::bytes(nl * NL * M, 16);
   b += Arena::bytes(nl * NL * M, 8) + 2 * Arena::bytes(field_buf_elems(ctx, M), 8) + Arena::bytes(nl * NE * M, 8) +
+       Arena::bytes(nl * NI * M, 8) +
        Arena::bytes(s3_elems(ctx, M), 8) + 2 * Arena::bytes(nb * M, 8);
   for (auto& L : ctx->levels) b += Arena::bytes((size_t)L.nbox * 2 * L.ni * M, 8);
   return b;
@@ -799,7 +806,7 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   const int max_iter = ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
   const double2 one = make_double2(1, 0), mone = make_double2(-1, 0), zero = make_double2(0, 0);
   const float2 fone = make_float2(1.f, 0.f), fzero = make_float2(0.f, 0.f);
-  double2 *ui = a.get<double2>(nbM), *dni = a.get<double2>(nbM), *rinc = a.get<double2>(nbM);
+  double2 *ui = a.get<double2>(nbM), *dni = a.get<double2>(nbM);
   double2 *ub = a.get<double2>(nbM), *psib = a.get<double2>(nbM), *rext = a.get<double2>(nbM);
   double2* PS = a.get<double2>(2 * nbM);
   double2* A2 = a.get<double2>((size_t)P * 2 * nb);
@@ -812,6 +819,7 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   float2* Up = a.get<float2>(nX);
   float2 *B0 = a.get<float2>(field_buf_elems(ctx, M)), *B1 = a.get<float2>(field_buf_elems(ctx, M));
   float2* tmp = a.get<float2>((size_t)nl * NE * M);
+  float2* wtmp = a.get<float2>((size_t)nl * NI * M);
   float2* S3 = a.get<float2>(s3_elems(ctx, M));
   float2 *f32 = a.get<float2>(nbM), *r32 = a.get<float2>(nbM);
   std::vector<float2*> TT(nlev);
@@ -819,8 +827,6 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
 
   incident_plane(s, ctx->B, ctx->k, alphas, M, ui, dni);
-  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, one, ctx->d_Dm, nb, 0, ui, M, 0, zero, rinc, M, 0, 1);
-  gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, mone, ctx->d_S, nb, 0, dni, M, 0, one, rinc, M, 0, 1);
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
   convert_d2f(s, A2, A2_32, (long long)P * 2 * nb);
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * nX, s));
@@ -832,17 +838,23 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   for (int it = 0; it < max_iter; ++it) {
     Phase pp("hs_refine_pass");
     if (it == 0) {
-      convert_d2f(s, rinc, f32, (long long)nbM);
+      // exterior right-hand side (D - I/2) u_inc - S d_n u_inc, in FP32 (the
+      // first pass is an FP32 solve; the corrections use FP64 residuals)
+      convert_d2f(s, ui, PS32, (long long)nbM);
+      convert_d2f(s, dni, PS32 + nbM, (long long)nbM);
+      gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, 2 * nb, fone, ctx->d_DS32, 2 * nb, 0, PS32, M, 0, fzero, f32,
+                                   M, 0, 1);
     } else {
-      // FP64 residual of every row for the current iterate X
+      // FP64 residual of every row for the current iterate X; the exterior
+      // rows: (D - I/2)(u_inc - u) - S (d_n u_inc - d_n u) = -[D - I/2, -S] [u_s; d_n u_s]
       residual_pde(s, X, ctx->d_q, ctx->d_D1, nl, ctx->k, ctx->h, M, Up);
       boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
-      CK(cudaMemcpyAsync(rext, rinc, sizeof(double2) * nbM, cudaMemcpyDeviceToDevice, s));
-      gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, mone, ctx->d_Dm, nb, 0, ub, M, 0, one, rext, M, 0, 1);
-      gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, nb, one, ctx->d_S, nb, 0, psib, M, 0, one, rext, M, 0, 1);
+      scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
+      gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, 2 * nb, mone, ctx->d_DS, 2 * nb, 0, PS, M, 0, zero, rext,
+                                      M, 0, 1);
       convert_d2f(s, rext, r32, (long long)nbM);
       // FP32 correction: particular leaf solutions, upward pass, root
-      leaf_particular(s, ctx->ws32, nl, eta, M, Up, B0, tmp);
+      leaf_particular(s, ctx->ws32, nl, eta, M, Up, B0, tmp, wtmp);
       float2 *Hc = B0, *Hp = B1;
       for (int li = 0; li < nlev; ++li) {
         residual_iface(s, ctx->levels[li], X, ctx->d_D1, ctx->nL, ctx->h, eta, M, S3);

@@ -170,8 +170,19 @@ void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, dou
   HS_COUNT_LAUNCH();
   lu_factor<T>(s, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, info, nleaf);
   // X = Aii^{-1} Aie (Dirichlet-to-interior map), W = Aii^{-T} Ni^T (adjoint)
-  lu_solve<T>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.Aie, NE, (long long)NI * NE, NE, nleaf);
-  lu_solve<T>(s, OP_T, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.NiT, NE, (long long)NI * NE, NE, nleaf);
+  if (w.Ainv && !Q) {
+    // keep Aii^{-1} (the mixed path's particular solves use it); X by one GEMM
+    // staged in NiT, whose transpose rows the path without adjoint never needs
+    lu_inverse<T>(s, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.Ainv + (long long)leaf0 * NI * NI, NI,
+                  (long long)NI * NI, nleaf);
+    gemm<T, T, T>(s, OP_N, OP_N, NI, NE, NI, T(1), w.Ainv + (long long)leaf0 * NI * NI, NI, (long long)NI * NI, w.Aie,
+                  NE, (long long)NI * NE, T(0), w.NiT, NE, (long long)NI * NE, nleaf);
+    cudaMemcpyAsync(w.Aie, w.NiT, sizeof(T) * (size_t)nleaf * NI * NE, cudaMemcpyDeviceToDevice, s);
+  } else {
+    lu_solve<T>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.Aie, NE, (long long)NI * NE, NE, nleaf);
+  }
+  if (Q)  // W is needed only by the adjoint operator
+    lu_solve<T>(s, OP_T, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, w.NiT, NE, (long long)NI * NE, NE, nleaf);
   // T = Ne - Ni X  (leaf Dirichlet-to-Neumann map), stored in Ne
   gemm<T, T, T>(s, OP_N, OP_N, NE, NE, NI, T(-1), w.Ni, NI, (long long)NE * NI, w.Aie, NE, (long long)NI * NE, T(1),
                 w.Ne, NE, (long long)NE * NE, nleaf);

@@ -517,6 +517,10 @@ template void gemm<float2, float, float2>(cudaStream_t, int, int, int, int, int,
                                           int);
 template void lu_factor<float>(cudaStream_t, float*, int, long long, int, int*, long long, int*, int);
 template void lu_factor<float2>(cudaStream_t, float2*, int, long long, int, int*, long long, int*, int);
+template void lu_inverse<double>(cudaStream_t, const double*, int, long long, int, const int*, long long, double*, int,
+                                 long long, int);
+template void lu_inverse<float>(cudaStream_t, const float*, int, long long, int, const int*, long long, float*, int,
+                                long long, int);
 template void lu_inverse<float2>(cudaStream_t, const float2*, int, long long, int, const int*, long long, float2*, int,
                                  long long, int);
 template void lu_solve<float>(cudaStream_t, int, const float*, int, long long, int, const int*, long long, float*, int,

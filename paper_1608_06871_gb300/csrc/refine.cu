@@ -210,6 +210,19 @@ __global__ void k_scattered32(const float2* __restrict__ U32, const double* __re
   PS[n + e] = d;
 }
 
+// DS = [D - I/2, -S] (nb x 2 nb): the exterior rows act on [u; d_n u] with one
+// product; FP64 and FP32 copies.
+__global__ void k_stack_ext(const double2* __restrict__ Dm, const double2* __restrict__ S, int nb,
+                            double2* __restrict__ DS, float2* __restrict__ DS32) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2LL * nb * nb) return;
+  const long long r = e / (2 * nb);
+  const int c = (int)(e % (2 * nb));
+  const double2 v = c < nb ? Dm[r * nb + c] : -S[r * nb + c - nb];
+  DS[e] = v;
+  DS32[e] = make_float2((float)v.x, (float)v.y);
+}
+
 // out[0] += sum |a|^2 (FP32 data, FP64 sums)
 __global__ void k_norm2_32(const float2* __restrict__ a, long long n, double* __restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,13 +294,22 @@ void boundary_gather(cudaStream_t s, const double2* X, const double* D1, int nL,
 
 // Particular leaf solution for body loads b held in Upart rows 0..195 (FP32):
 // w = Aii^{-1} b, u_e = -Kinv Ni w, u_i = w - X u_e, and h = -2 i eta u_e.
+// With w.Ainv the first step is one GEMM into wtmp (NI x nrhs per leaf) and a
+// copy back; otherwise triangular solves with the LU factors.
 void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, double eta, int nrhs, float2* Upart,
-                     float2* H, float2* tmp) {
+                     float2* H, float2* tmp, float2* wtmp) {
   const long long sU = (long long)NL * nrhs;
   const float2 one = make_float2(1.f, 0.f), mone = make_float2(-1.f, 0.f), zero = make_float2(0.f, 0.f);
-  // complex right-hand sides are solved as 2 nrhs real columns
-  lu_solve<float>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, reinterpret_cast<float*>(Upart), 2 * nrhs,
-                  2 * sU, 2 * nrhs, nleaf);
+  if (w.Ainv && wtmp) {
+    gemm<float, float2, float2>(s, OP_N, OP_N, NI, nrhs, NI, one, w.Ainv, NI, (long long)NI * NI, Upart, nrhs, sU,
+                                zero, wtmp, nrhs, (long long)NI * nrhs, nleaf);
+    cudaMemcpy2DAsync(Upart, sU * sizeof(float2), wtmp, (size_t)NI * nrhs * sizeof(float2),
+                      (size_t)NI * nrhs * sizeof(float2), nleaf, cudaMemcpyDeviceToDevice, s);
+  } else {
+    // complex right-hand sides are solved as 2 nrhs real columns
+    lu_solve<float>(s, OP_N, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, reinterpret_cast<float*>(Upart), 2 * nrhs,
+                    2 * sU, 2 * nrhs, nleaf);
+  }
   gemm<float, float2, float2>(s, OP_N, OP_N, NE, nrhs, NI, one, w.Ni, NI, (long long)NE * NI, Upart, nrhs, sU, zero,
                               tmp, nrhs, (long long)NE * nrhs, nleaf);
   gemm<float2, float2, float2>(s, OP_N, OP_N, NE, nrhs, NE, mone, w.Kinv, NE, (long long)NE * NE, tmp, nrhs,
@@ -303,6 +325,11 @@ void scattered32(cudaStream_t s, const float2* U32, const double* D1, int nL, do
                  const double2* dni, bool sub_inc, float2* PS) {
   long long n = 56LL * nL * nrhs;
   k_scattered32<<<blocks(n), 256, 0, s>>>(U32, D1, nL, h, nrhs, ui, dni, sub_inc ? 1 : 0, PS);
+  HS_COUNT_LAUNCH();
+}
+
+void stack_exterior(cudaStream_t s, const double2* Dm, const double2* S, int nb, double2* DS, float2* DS32) {
+  k_stack_ext<<<blocks(2LL * nb * nb), 256, 0, s>>>(Dm, S, nb, DS, DS32);
   HS_COUNT_LAUNCH();
 }
 

@@ -18,6 +18,7 @@ template <typename T> struct LeafScratchT {  // leaf build scratch; in the mixed
   T *Aii, *Aie, *Ni, *NiT, *Ne;   // Aii holds the LU factors, Aie holds X = Aii^{-1} Aie afterwards
   C *K, *Kinv;
   int *piv, *pivK;
+  T* Ainv = nullptr;  // mixed path: Aii^{-1} explicitly (the particular solves apply it with one GEMM)
 };
 using LeafScratch = LeafScratchT<double>;
 
@@ -130,7 +131,7 @@ void residual_iface(cudaStream_t s, const LevelMaps& L, const double2* X, const 
 void boundary_gather(cudaStream_t s, const double2* X, const double* D1, int nL, double h, int nrhs, double2* ub,
                      double2* psib);
 void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, double eta, int nrhs, float2* Upart,
-                     float2* H, float2* tmp);
+                     float2* H, float2* tmp, float2* wtmp);
 void scattered_data(cudaStream_t s, const double2* ub, const double2* psib, const double2* ui, const double2* dni,
                     long long n, double2* PS);
 void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out);  // out += {|a-b|^2, |a|^2}
@@ -138,6 +139,8 @@ void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n,
 void scattered32(cudaStream_t s, const float2* U32, const double* D1, int nL, double h, int nrhs, const double2* ui,
                  const double2* dni, bool sub_inc, float2* PS);
 void norm2_32(cudaStream_t s, const float2* a, long long n, double* out);
+// DS = [D - I/2, -S] (nb x 2 nb) in FP64 and FP32.
+void stack_exterior(cudaStream_t s, const double2* Dm, const double2* S, int nb, double2* DS, float2* DS32);
 // dst[r][:] = src[idx[r]][:] (rows of ncols elements); dst[a][b] = src[idx[a]][idx[b]] for square matrices.
 template <typename C> void permute_rows(cudaStream_t s, const C* src, const int* idx, int nrows, int ncols, C* dst);
 template <typename C> void permute_square(cudaStream_t s, const C* src, const int* idx, int n, C* dst);

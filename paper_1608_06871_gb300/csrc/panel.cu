@@ -37,68 +37,100 @@ constexpr int PNB = 32;      // panel width of the blocked LU
 constexpr int PT = 256;      // threads of the tile kernels
 constexpr int APPLY_CH = 32;  // columns per CTA of the row-permutation kernel
 
+// Magnitude used for pivot selection, in the panel's own precision.
+template <typename E> struct pmag;
+template <> struct pmag<double> { using T = double; __device__ static double of(double a) { return fabs(a); } };
+template <> struct pmag<double2> { using T = double; __device__ static double of(double2 a) { return a.x * a.x + a.y * a.y; } };
+template <> struct pmag<float> { using T = float; __device__ static float of(float a) { return fabsf(a); } };
+template <> struct pmag<float2> { using T = float; __device__ static float of(float2 a) { return a.x * a.x + a.y * a.y; } };
+
 // Factor the rows x nb tile T (row stride ld, shared memory) with partial
-// pivoting (PIVOT) or without, one thread per row (blockDim.x >= rows).
-// rid[] (if PIVOT) is permuted with the rows; sp[j] (if not NULL) receives
-// the local row swapped with row j at step j; *zc is lowered to the first
-// column whose pivot is exactly zero (that column is then left unscaled).
-template <typename E, bool PIVOT>
-__device__ void tile_lu(E* T, int ld, int rows, int nb, int* rid, int* sp, int* zc, double* wm, int* wi, int* sh) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+// pivoting, one thread per row (blockDim.x = PT >= rows).  Each thread keeps
+// its row in registers for the whole factorisation; per column one barrier
+// publishes every warp's candidate pivot (each thread then reduces the warp
+// candidates itself), one more publishes the pivot row (and the row it
+// displaces), and the rank-1 update touches registers only.  rid[] is
+// permuted with the rows; sp[j] (if not NULL) receives the local row swapped
+// with row j at step j; *zc is lowered to the first column whose pivot is
+// exactly zero (that column is then left unscaled).  The factored tile is
+// written back to T.
+template <typename E>
+__device__ void tile_lu(E* T, int ld, int rows, int nb, int* rid, int* sp, int* zc) {
+  using M = typename pmag<E>::T;
+  constexpr int NW = PT / 32;
+  __shared__ M wbest[2][NW];
+  __shared__ int widx[2][NW];
+  __shared__ E ubuf[2][PNB], xbuf[2][PNB];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int steps = min(rows, nb);
-  for (int j = 0; j < steps; ++j) {
-    if (PIVOT) {
-      double best = -1.0;
-      int bi = INT_MAX;
-      if (t >= j && t < rows) {
-        best = el<E>::mag2(T[t * ld + j]);
-        bi = t;
-      }
+  E r[PNB];
+#pragma unroll
+  for (int c = 0; c < PNB; ++c) r[c] = (t < rows && c < nb) ? T[t * ld + c] : el<E>::zero();
+#pragma unroll
+  for (int j = 0; j < PNB; ++j) {
+    if (j < steps) {
+      const int pb = j & 1;
+      M best = (t >= j && t < rows) ? pmag<E>::of(r[j]) : M(-1);
+      int bi = (t >= j && t < rows) ? t : INT_MAX;
+#pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const M ob = __shfl_down_sync(0xffffffffu, best, o);
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (lane == 0) { wm[warp] = best; wi[warp] = bi; }
+      if (lane == 0) { wbest[pb][warp] = best; widx[pb][warp] = bi; }
       __syncthreads();
-      if (warp == 0) {
-        best = lane < nw ? wm[lane] : -1.0;
-        bi = lane < nw ? wi[lane] : INT_MAX;
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_down_sync(0xffffffffu, best, o);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (lane == 0) sh[0] = bi;
+      best = wbest[pb][0];
+      bi = widx[pb][0];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) {
+        const M ob = wbest[pb][w];
+        const int oi = widx[pb][w];
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      __syncthreads();
-      const int p = sh[0];
-      if (p != j) {
-        for (int c = t; c < nb; c += blockDim.x) {
-          const E tmp = T[j * ld + c];
-          T[j * ld + c] = T[p * ld + c];
-          T[p * ld + c] = tmp;
-        }
-        if (t == 0) {
+      const int p = bi < rows ? bi : j;
+      if (t == p) {
+#pragma unroll
+        for (int c = 0; c < PNB; ++c) ubuf[pb][c] = r[c];
+      }
+      if (t == j && p != j) {
+#pragma unroll
+        for (int c = 0; c < PNB; ++c) xbuf[pb][c] = r[c];
+      }
+      if (t == 0) {
+        if (p != j) {
           const int tr = rid[j];
           rid[j] = rid[p];
           rid[p] = tr;
         }
+        if (sp) sp[j] = p;
       }
-      if (t == 0 && sp) sp[j] = p;
       __syncthreads();
+      if (p != j && t == p) {
+#pragma unroll
+        for (int c = 0; c < PNB; ++c) r[c] = xbuf[pb][c];
+      }
+      if (t == j) {
+#pragma unroll
+        for (int c = 0; c < PNB; ++c) r[c] = ubuf[pb][c];
+      }
+      const E pv = ubuf[pb][j];
+      if (!(pmag<E>::of(pv) > M(0))) {
+        if (t == 0) atomicMin(zc, j);
+      } else if (t > j && t < rows) {
+        const E l = el<E>::div(r[j], pv);
+        r[j] = l;
+#pragma unroll
+        for (int c = j + 1; c < PNB; ++c) r[c] = fmsc(r[c], l, ubuf[pb][c]);
+      }
     }
-    const E pv = T[j * ld + j];
-    if (!(el<E>::mag2(pv) > 0.0)) {
-      if (t == 0) atomicMin(zc, j);
-    } else if (t > j && t < rows) {
-      E* row = T + t * ld;
-      const E l = el<E>::div(row[j], pv);
-      row[j] = l;
-      for (int c = j + 1; c < nb; ++c) row[c] = fmsc(row[c], l, T[j * ld + c]);
-    }
-    __syncthreads();
   }
+  if (t < rows) {
+#pragma unroll
+    for (int c = 0; c < PNB; ++c)
+      if (c < nb) T[t * ld + c] = r[c];
+  }
+  __syncthreads();
 }
 
 // Short panel (m = n - j0 <= PR rows): one CTA per matrix.
@@ -111,8 +143,6 @@ __global__ void __launch_bounds__(PT) k_panel_small(E* A, int lda, long long sA,
   __shared__ int sp[PNB];
   __shared__ int aff_d[2 * PNB], aff_s[2 * PNB];
   __shared__ int zc, naff;
-  __shared__ double wm[PT / 32];
-  __shared__ int wi[PT / 32], sh[1];
   const int b = blockIdx.x, t = threadIdx.x;
   A += b * sA;
   piv += b * sP;
@@ -124,7 +154,7 @@ __global__ void __launch_bounds__(PT) k_panel_small(E* A, int lda, long long sA,
   if (t < m) rid[t] = t;
   if (t == 0) zc = INT_MAX;
   __syncthreads();
-  tile_lu<E, true>(T, ld, m, nb, rid, sp, &zc, wm, wi, sh);
+  tile_lu<E>(T, ld, m, nb, rid, sp, &zc);
   for (int e = t; e < m * nb; e += PT) {
     const int r = e / nb, c = e % nb;
     A[(long long)(j0 + r) * lda + j0 + c] = T[r * ld + c];
@@ -170,8 +200,6 @@ __global__ void __launch_bounds__(PT) k_tp_select(E* A, int lda, long long sA, i
   __shared__ int rid[PR];
   __shared__ int wsum[PT / 32];
   __shared__ int zc;
-  __shared__ double wm[PT / 32];
-  __shared__ int wi[PT / 32], sh[1];
   __shared__ int kpos[2 * PNB], korig[2 * PNB];
   const int b = blockIdx.y, set = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   A += b * sA;
@@ -203,7 +231,7 @@ __global__ void __launch_bounds__(PT) k_tp_select(E* A, int lda, long long sA, i
     T[r * ld + c] = A[(long long)rid[r] * lda + j0 + c];
   }
   __syncthreads();
-  tile_lu<E, true>(T, ld, rows, nb, rid, nullptr, &zc, wm, wi, sh);
+  tile_lu<E>(T, ld, rows, nb, rid, nullptr, &zc);
   if (!final_round) {
     if (t < nb) W[out_off + set * nb + t] = t < rows ? rid[t] : -1;
     return;

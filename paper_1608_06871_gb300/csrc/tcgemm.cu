@@ -130,15 +130,20 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
   const uint32_t tmem = tslot;
 
   // register prefetch: A chunk 128 x 8 complex = 512 float4 (4 per thread),
-  // B chunk 8 x 64 complex = 256 float4 (2 per thread); a float4 is 2 complex
-  float4 ra[4], rb[2];
+  // B chunk 8 x 64 complex as 256 pairs of k-adjacent elements (2 per
+  // thread).  Lane bits 0..2 select the row inside an 8-row core matrix, so
+  // the shared-memory stores of each 8-lane phase fill one contiguous
+  // 128-byte core matrix (no bank conflicts); the global loads of a warp still
+  // use whole 32-byte sectors.
+  float4 ra[4];
+  float2 rb0[2], rb1[2];
   auto prefetch = [&](int ch) {
     const int kb = ch * TKC;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      int q = tid + TC_THREADS * i;        // 0..511
-      int r = q >> 2, c2 = (q & 3) * 2;    // complex column pair within the chunk
-      int gr = row0 + r, gk = kb + c2;
+      const int q = tid + TC_THREADS * i;                     // 0..511
+      const int r = (q >> 5) * 8 + (q & 7), c2 = ((q >> 3) & 3) * 2;  // row, complex column pair
+      const int gr = row0 + r, gk = kb + c2;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gr < m) {
         const float2* p = A + (long long)gr * lda + gk;
@@ -149,17 +154,22 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      int q = tid + TC_THREADS * i;  // 0..255
-      int l = q >> 5, j2 = (q & 31) * 2;
-      int gk = kb + l, gc = col0 + j2;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gk < k) {
-        const float2* p = B + (long long)gk * ldb + gc;
-        if (gc < n) { v.x = p[0].x; v.y = p[0].y; }
-        if (gc + 1 < n) { v.z = p[1].x; v.w = p[1].y; }
+      const int q = tid + TC_THREADS * i;                     // 0..255
+      const int j = (q >> 5) * 8 + (q & 7), lp = (q >> 3) & 3;  // column, k pair (l = 2 lp, 2 lp + 1)
+      const int gk = kb + 2 * lp, gc = col0 + j;
+      float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+      if (gc < n) {
+        if (gk < k) v0 = B[(long long)gk * ldb + gc];
+        if (gk + 1 < k) v1 = B[(long long)(gk + 1) * ldb + gc];
       }
-      rb[i] = v;
+      rb0[i] = v0;
+      rb1[i] = v1;
     }
+  };
+  auto split_store = [&](float* hi, float* lo, int off, float4 v) {
+    const float4 h = make_float4(tf32(v.x), tf32(v.y), tf32(v.z), tf32(v.w));
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = make_float4(tf32(v.x - h.x), tf32(v.y - h.y), tf32(v.z - h.z), tf32(v.w - h.w));
   };
   auto stage_store = [&](int st) {
     float* Ahi = reinterpret_cast<float*>(sm + st * STAGE_BYTES);
@@ -168,33 +178,18 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     float* Blo = Bhi + OP_BYTES / 4;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      int q = tid + TC_THREADS * i;
-      int r = q >> 2, c4 = q & 3;  // real k' = 4 c4 .. 4 c4 + 3: one 16-byte core-matrix row
-      float4 v = ra[i];
-      float4 h = make_float4(tf32(v.x), tf32(v.y), tf32(v.z), tf32(v.w));
-      float4 lo = make_float4(tf32(v.x - h.x), tf32(v.y - h.y), tf32(v.z - h.z), tf32(v.w - h.w));
-      int off = core_off(r, 4 * c4);
-      *reinterpret_cast<float4*>(Ahi + off) = h;
-      *reinterpret_cast<float4*>(Alo + off) = lo;
+      const int q = tid + TC_THREADS * i;
+      const int r = (q >> 5) * 8 + (q & 7), c4 = (q >> 3) & 3;  // real k' = 4 c4 .. 4 c4 + 3
+      split_store(Ahi, Alo, core_off(r, 4 * c4), ra[i]);
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      int q = tid + TC_THREADS * i;
-      int l = q >> 5, j2 = (q & 31) * 2;
-      float4 v = rb[i];  // B[l][j2], B[l][j2+1]
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        float re = s ? v.z : v.x, im = s ? v.w : v.y;
-        int j = j2 + s;
-        // row j: (re, -im) at k' = 2l, 2l+1; row TN + j: (im, re)
-        float e0 = re, e1 = -im, f0 = im, f1 = re;
-        float h0 = tf32(e0), h1 = tf32(e1), g0 = tf32(f0), g1 = tf32(f1);
-        int o1 = core_off(j, 2 * l), o2 = core_off(TN + j, 2 * l);
-        *reinterpret_cast<float2*>(Bhi + o1) = make_float2(h0, h1);
-        *reinterpret_cast<float2*>(Blo + o1) = make_float2(tf32(e0 - h0), tf32(e1 - h1));
-        *reinterpret_cast<float2*>(Bhi + o2) = make_float2(g0, g1);
-        *reinterpret_cast<float2*>(Blo + o2) = make_float2(tf32(f0 - g0), tf32(f1 - g1));
-      }
+      const int q = tid + TC_THREADS * i;
+      const int j = (q >> 5) * 8 + (q & 7), lp = (q >> 3) & 3;
+      const float2 a = rb0[i], b = rb1[i];  // B[2lp][j], B[2lp+1][j]
+      // row j: (re, -im) at k' = 2l, 2l+1; row TN + j: (im, re)
+      split_store(Bhi, Blo, core_off(j, 4 * lp), make_float4(a.x, -a.y, b.x, -b.y));
+      split_store(Bhi, Blo, core_off(TN + j, 4 * lp), make_float4(a.y, a.x, b.y, b.x));
     }
   };
 

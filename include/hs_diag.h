@@ -44,6 +44,12 @@ int hs_peak_fp64(int device, double ms, double* tflops);
  * HS_MIXED solve on ctx (0, -1, -1 before any).  Any pointer may be NULL. */
 int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update, double* est_error);
 
+/* Replay the mixed-precision factorisation from a CUDA graph captured once
+ * per frequency (enable != 0, the default) or enqueue it launch by launch
+ * (enable == 0).  Process-wide; takes effect at the next hs_build.  The
+ * results are bitwise identical either way.  Never fails. */
+int hs_set_graphs(int enable);
+
 /* Route eligible complex FP32 products of the mixed-precision path
  * (untransposed operands, m >= 128, n >= 64, k >= 64) to the tensor-core GEMM
  * (enable != 0, the default) or to the SIMT FP32 GEMM (enable == 0).

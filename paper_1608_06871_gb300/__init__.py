@@ -69,6 +69,7 @@ _SIGS = {
     "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
     "hs_set_tensor_cores": (_I, [_I]),
+    "hs_set_graphs": (_I, [_I]),
     "hs_cgemm32": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
     "hs_lu_solve": (_I, [_I, _I, _I, _P, _P, _I, _P]),
     "hs_zgemm": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _I, _P]),
@@ -250,6 +251,10 @@ def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:
     t = ctypes.c_double()
     _check(None, lib().hs_peak_fp64(device, float(ms), ctypes.byref(t)))
     return t.value
+
+
+def hs_set_graphs(enable: bool):
+    _check(None, lib().hs_set_graphs(1 if enable else 0))
 
 
 def hs_set_tensor_cores(enable: bool):

@@ -20,6 +20,8 @@ std::vector<ProfRec> g_prof;
 }  // namespace
 
 bool prof_active(int family) { return g_prof_family == family; }
+bool prof_any() { return g_prof_family != 0; }
+extern bool g_use_graphs;
 
 void prof_begin(cudaStream_t s, cudaEvent_t* a) {
   cudaEventCreate(a);
@@ -115,6 +117,11 @@ int hs_peak_fp64(int device, double ms, double* tflops) {
   cudaEventDestroy(b);
   cudaFree(out);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
+}
+
+int hs_set_graphs(int enable) {
+  hs::g_use_graphs = enable != 0;
+  return HS_OK;
 }
 
 int hs_set_tensor_cores(int enable) {

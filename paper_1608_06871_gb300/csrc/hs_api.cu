@@ -13,6 +13,8 @@
 
 namespace hs {
 thread_local long long* g_launch_counter = nullptr;
+bool g_use_graphs = true;  // process-wide switch (hs_set_graphs)
+bool prof_active(int family);
 }
 
 using namespace hs;
@@ -156,6 +158,9 @@ struct hs_ctx {
   int *d_root_of_bie = nullptr, *d_bie_of_root = nullptr;  // root box order <-> boundary-node order
   double2* d_Rb = nullptr;  // root ItI map in boundary-node order (FP64)
   float2* d_Rb32 = nullptr; // same, FP32; after the build it holds C^{-1} (FP32)
+  cudaGraphExec_t fgraph = nullptr;  // mixed: captured factorisation (see factor_mixed)
+  double fgraph_k = -1.0;
+  long long fgraph_kernels = 0;
   double2* d_DS = nullptr;   // mixed: [D - I/2, -S] (N_b x 2 N_b), the exterior rows on [u; d_n u]
   float2* d_DS32 = nullptr;  // same, FP32
   // per-call workspace
@@ -584,10 +589,10 @@ int setup(hs_ctx* ctx) {
 // FP32 factors of the mixed-precision path: leaves, merges and the coupled
 // root system in complex FP32; the layer-potential matrices stay in FP64 for
 // the refinement residual.
-int factor_mixed(hs_ctx* ctx, double k) {
-  cudaStream_t s = ctx->stream;
+// Device work of the mixed-precision factorisation (no host synchronisation,
+// so that it can be captured into a CUDA graph).
+int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s) {
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
-  Phase ph("hs_factor_mixed");
   leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32, nullptr,
                           ctx->d_info);
   const float2* Rc = ctx->d_R32;
@@ -597,7 +602,6 @@ int factor_mixed(hs_ctx* ctx, double k) {
   }
   const int nb = ctx->B.nb;
   permute_square<float2>(s, Rc, ctx->d_root_of_bie, nb, ctx->d_Rb32);  // root map in boundary-node order
-  ctx->Rroot32 = ctx->d_Rb32;
   const long long nn = (long long)nb * nb;
   if (ctx->bie_k != k) {  // S, D - I/2, B1, B2 depend on k and the boundary only
     bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
@@ -607,14 +611,59 @@ int factor_mixed(hs_ctx* ctx, double k) {
     ctx->bie_k = k;
   }
   convert_d2f(s, ctx->d_B1, ctx->d_C32, nn);
-  gemm<float2, float2, float2>(s, OP_N, OP_N, nb, nb, nb, make_float2(-1.f, 0.f), ctx->d_B2_32, nb, 0, ctx->Rroot32,
+  gemm<float2, float2, float2>(s, OP_N, OP_N, nb, nb, nb, make_float2(-1.f, 0.f), ctx->d_B2_32, nb, 0, ctx->d_Rb32,
                                nb, 0, make_float2(1.f, 0.f), ctx->d_C32, nb, 0, 1);
   lu_factor<float2>(s, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, ctx->d_info, 1);
   // C^{-1} explicitly (in the buffer of the root map, no longer needed): each
   // refinement pass then applies it with one GEMM
   lu_inverse<float2>(s, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, ctx->d_Rb32, nb, 0, 1);
-  ctx->Rroot32 = nullptr;
   CK(cudaGetLastError());
+  return HS_OK;
+}
+
+// Mixed-precision factorisation.  The first build at a frequency runs
+// eagerly (it also forms the boundary-integral matrices of that k); later
+// builds at the same k replay a CUDA graph of the same launch sequence
+// (about 900 launches: leaf factors, every merge level, the root), captured
+// once per k, which removes the per-launch host overhead and the gaps between
+// the many small kernels.
+int factor_mixed(hs_ctx* ctx, double k) {
+  cudaStream_t s = ctx->stream;
+  Phase ph("hs_factor_mixed");
+  // (per-launch profiling of the FP32 families needs eager launches; the
+  // factorisation has no FP64 GEMM, so FP64 profiling does not prevent it)
+  const bool graph = g_use_graphs && ctx->bie_k == k && !prof_active(2) && !prof_active(3);
+  if (!graph) {
+    CKR(enqueue_factor_mixed(ctx, k, s));
+  } else {
+    if (!ctx->fgraph || ctx->fgraph_k != k) {
+      if (ctx->fgraph) cudaGraphExecDestroy(ctx->fgraph);
+      ctx->fgraph = nullptr;
+      long long* counter = g_launch_counter;
+      const long long before = counter ? *counter : 0;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const int rc = enqueue_factor_mixed(ctx, k, s);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(s, &g);
+      const long long kernels = counter ? *counter - before : 0;
+      if (counter) *counter = before;  // counted at each replay instead
+      if (rc != HS_OK || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc != HS_OK ? rc : fail(ctx, HS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&ctx->fgraph, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        ctx->fgraph = nullptr;
+        return fail(ctx, HS_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(ei));
+      }
+      ctx->fgraph_k = k;
+      ctx->fgraph_kernels = kernels;
+    }
+    CK(cudaGraphLaunch(ctx->fgraph, s));
+    if (g_launch_counter) *g_launch_counter += ctx->fgraph_kernels;
+  }
+  ctx->Rroot32 = nullptr;
   CKR(check_info(ctx));
   ctx->k = k;
   ctx->built = true;
@@ -1441,6 +1490,7 @@ void hs_destroy(hs_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->cfg.device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->fgraph) cudaGraphExecDestroy(ctx->fgraph);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->ws_base) cudaFree(ctx->ws_base);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

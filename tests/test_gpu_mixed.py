@@ -104,3 +104,29 @@ def test_fp64_only_calls_reject_mixed_context(hs):
     with pytest.raises(hs.HSError) as e:
         S.jacobian([0.0], [0.0])
     assert e.value.code == hs.HS_EINVAL
+
+
+def test_factor_graph_replay_bitwise(hs):
+    """Builds at an unchanged k replay a captured CUDA graph of the factorisation;
+    the far field must be bitwise identical to the launch-by-launch build, and the
+    launch count per build the same."""
+    w = synth.WORKLOADS["grad_k20"]
+    c = synth.smooth_random_coeffs(w.S, seed=4, qmax=0.3)
+    al, th = synth.directions(16), synth.receivers(24)
+    outs, counts = [], []
+    for graphs in (False, True):
+        hs.hs_set_graphs(graphs)
+        try:
+            S = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, precision=hs.HS_MIXED)
+            for _ in range(3):  # first build eager (new k), then capture, then replay
+                n0 = S.launch_count()
+                S.build(c, w.k)
+                counts.append(S.launch_count() - n0)
+            outs.append(S.solve(al, th))
+            S.build(0.5 * c, w.k)  # a different contrast through the same graph
+            outs.append(S.solve(al, th))
+        finally:
+            hs.hs_set_graphs(True)
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+    assert counts[1] == counts[4] and counts[2] == counts[5]
+    assert not np.array_equal(outs[0], outs[1])

@@ -118,6 +118,22 @@ struct Arena {
 
 }  // namespace
 
+// A captured CUDA graph of a fixed launch sequence and the values its launch
+// parameters depend on (buffer base, sizes, frequency).
+namespace hs {
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  const void* base = nullptr;
+  int M = -1, P = -1;
+  double k = -1.0;
+  long long kernels = 0;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+};
+}  // namespace hs
+
 struct hs_ctx {
   hs_config cfg{};
   int nL = 0, nleaf = 0, n14 = 0, n16 = 0, chunk = 0;
@@ -158,9 +174,8 @@ struct hs_ctx {
   int *d_root_of_bie = nullptr, *d_bie_of_root = nullptr;  // root box order <-> boundary-node order
   double2* d_Rb = nullptr;  // root ItI map in boundary-node order (FP64)
   float2* d_Rb32 = nullptr; // same, FP32; after the build it holds C^{-1} (FP32)
-  cudaGraphExec_t fgraph = nullptr;  // mixed: captured factorisation (see factor_mixed)
-  double fgraph_k = -1.0;
-  long long fgraph_kernels = 0;
+  GraphSlot fgraph;     // mixed: captured factorisation (see factor_mixed)
+  GraphSlot pgraph[2];  // mixed: captured refinement-pass bodies (first pass, corrections)
   double2* d_DS = nullptr;   // mixed: [D - I/2, -S] (N_b x 2 N_b), the exterior rows on [u; d_n u]
   float2* d_DS32 = nullptr;  // same, FP32
   // per-call workspace
@@ -179,6 +194,47 @@ struct LaunchScope {
 int fail(hs_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
+}
+
+// Enqueue a fixed launch sequence on s: eagerly when `capture` is false,
+// otherwise by replaying the graph in `slot`, capturing it first (stream
+// capture of the same sequence) when the slot is empty or was captured for
+// other (base, M, P, k).  Kernels of a replay are added to the launch count.
+template <typename F>
+int run_captured(hs_ctx* ctx, cudaStream_t s, GraphSlot& slot, bool capture, const void* base, int M, int P,
+                 double k, F&& enqueue) {
+  if (!capture) return enqueue();
+  if (!slot.exec || slot.base != base || slot.M != M || slot.P != P || slot.k != k) {
+    slot.reset();
+    long long* counter = g_launch_counter;
+    const long long before = counter ? *counter : 0;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    const int rc = enqueue();
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    const long long kernels = counter ? *counter - before : 0;
+    if (counter) *counter = before;  // counted at each replay instead
+    if (rc != HS_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != HS_OK ? rc : fail(ctx, HS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&slot.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      slot.exec = nullptr;
+      return fail(ctx, HS_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+    }
+    slot.base = base;
+    slot.M = M;
+    slot.P = P;
+    slot.k = k;
+    slot.kernels = kernels;
+  }
+  const cudaError_t e = cudaGraphLaunch(slot.exec, s);
+  if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  if (g_launch_counter) *g_launch_counter += slot.kernels;
+  return HS_OK;
 }
 
 #define CK(call)                                                                              \
@@ -633,36 +689,7 @@ int factor_mixed(hs_ctx* ctx, double k) {
   // (per-launch profiling of the FP32 families needs eager launches; the
   // factorisation has no FP64 GEMM, so FP64 profiling does not prevent it)
   const bool graph = g_use_graphs && ctx->bie_k == k && !prof_active(2) && !prof_active(3);
-  if (!graph) {
-    CKR(enqueue_factor_mixed(ctx, k, s));
-  } else {
-    if (!ctx->fgraph || ctx->fgraph_k != k) {
-      if (ctx->fgraph) cudaGraphExecDestroy(ctx->fgraph);
-      ctx->fgraph = nullptr;
-      long long* counter = g_launch_counter;
-      const long long before = counter ? *counter : 0;
-      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      const int rc = enqueue_factor_mixed(ctx, k, s);
-      cudaGraph_t g = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(s, &g);
-      const long long kernels = counter ? *counter - before : 0;
-      if (counter) *counter = before;  // counted at each replay instead
-      if (rc != HS_OK || ec != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return rc != HS_OK ? rc : fail(ctx, HS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-      }
-      const cudaError_t ei = cudaGraphInstantiate(&ctx->fgraph, g, 0);
-      cudaGraphDestroy(g);
-      if (ei != cudaSuccess) {
-        ctx->fgraph = nullptr;
-        return fail(ctx, HS_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(ei));
-      }
-      ctx->fgraph_k = k;
-      ctx->fgraph_kernels = kernels;
-    }
-    CK(cudaGraphLaunch(ctx->fgraph, s));
-    if (g_launch_counter) *g_launch_counter += ctx->fgraph_kernels;
-  }
+  CKR(run_captured(ctx, s, ctx->fgraph, graph, nullptr, 0, 0, k, [&] { return enqueue_factor_mixed(ctx, k, s); }));
   ctx->Rroot32 = nullptr;
   CKR(check_info(ctx));
   ctx->k = k;
@@ -886,14 +913,7 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   bool converged = false;
   for (int it = 0; it < max_iter; ++it) {
     Phase pp("hs_refine_pass");
-    if (it == 0) {
-      // exterior right-hand side (D - I/2) u_inc - S d_n u_inc, in FP32 (the
-      // first pass is an FP32 solve; the corrections use FP64 residuals)
-      convert_d2f(s, ui, PS32, (long long)nbM);
-      convert_d2f(s, dni, PS32 + nbM, (long long)nbM);
-      gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, 2 * nb, fone, ctx->d_DS32, 2 * nb, 0, PS32, M, 0, fzero, f32,
-                                   M, 0, 1);
-    } else {
+    if (it > 0) {
       // FP64 residual of every row for the current iterate X; the exterior
       // rows: (D - I/2)(u_inc - u) - S (d_n u_inc - d_n u) = -[D - I/2, -S] [u_s; d_n u_s]
       residual_pde(s, X, ctx->d_q, ctx->d_D1, nl, ctx->k, ctx->h, M, Up);
@@ -901,39 +921,58 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
       scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
       gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, 2 * nb, mone, ctx->d_DS, 2 * nb, 0, PS, M, 0, zero, rext,
                                       M, 0, 1);
-      convert_d2f(s, rext, r32, (long long)nbM);
-      // FP32 correction: particular leaf solutions, upward pass, root
-      leaf_particular(s, ctx->ws32, nl, eta, M, Up, B0, tmp, wtmp);
-      float2 *Hc = B0, *Hp = B1;
-      for (int li = 0; li < nlev; ++li) {
-        residual_iface(s, ctx->levels[li], X, ctx->d_D1, ctx->nL, ctx->h, eta, M, S3);
-        sweep_up_level<float2>(s, ctx->levels[li], ctx->ops32[li], Hc, S3, TT[li], Hp, M);
-        std::swap(Hc, Hp);
+    }
+    // The rest of the pass is FP32 work on fixed buffers: replayed from a
+    // captured graph (one for the first pass, one for the corrections).
+    const bool first = it == 0;
+    auto body = [&]() -> int {
+      if (first) {
+        // exterior right-hand side (D - I/2) u_inc - S d_n u_inc, in FP32 (the
+        // first pass is an FP32 solve; the corrections use FP64 residuals)
+        convert_d2f(s, ui, PS32, (long long)nbM);
+        convert_d2f(s, dni, PS32 + nbM, (long long)nbM);
+        gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, 2 * nb, fone, ctx->d_DS32, 2 * nb, 0, PS32, M, 0, fzero,
+                                     f32, M, 0, 1);
+      } else {
+        convert_d2f(s, rext, r32, (long long)nbM);
+        // FP32 correction: particular leaf solutions, upward pass, root
+        leaf_particular(s, ctx->ws32, nl, eta, M, Up, B0, tmp, wtmp);
+        float2 *Hc = B0, *Hp = B1;
+        for (int li = 0; li < nlev; ++li) {
+          residual_iface(s, ctx->levels[li], X, ctx->d_D1, ctx->nL, ctx->h, eta, M, S3);
+          sweep_up_level<float2>(s, ctx->levels[li], ctx->ops32[li], Hc, S3, TT[li], Hp, M);
+          std::swap(Hc, Hp);
+        }
+        permute_rows<float2>(s, Hc, ctx->d_root_of_bie, nb, M, tmp);  // root h in boundary-node order
+        CK(cudaMemcpyAsync(f32, r32, sizeof(float2) * nbM, cudaMemcpyDeviceToDevice, s));
+        gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_B2_32, nb, 0, tmp, M, 0, fone, f32, M, 0,
+                                     1);
       }
-      permute_rows<float2>(s, Hc, ctx->d_root_of_bie, nb, M, tmp);  // root h in boundary-node order
-      CK(cudaMemcpyAsync(f32, r32, sizeof(float2) * nbM, cudaMemcpyDeviceToDevice, s));
-      gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_B2_32, nb, 0, tmp, M, 0, fone, f32, M, 0, 1);
-    }
-    gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_Rb32, nb, 0, f32, M, 0, fzero, r32, M, 0, 1);
-    // downward sweep (adds the particular interface impedances after the first pass)
-    permute_rows<float2>(s, r32, ctx->d_bie_of_root, nb, M, B1);  // root box order
-    const float2* Fp = B1;
-    float2* out = B0;
-    for (int li = nlev - 1; li >= 0; --li) {
-      sweep_down_level<float2>(s, ctx->levels[li], ctx->ops32[li], Fp, TT[li], out, M, it > 0);
-      Fp = out;
-      out = (out == B0) ? B1 : B0;
-    }
-    gemm<float2, float2, float2>(s, OP_N, OP_N, NL, M, NE, fone, ctx->d_Y32, NE, (long long)NL * NE, Fp, M,
-                                 (long long)NE * M, it > 0 ? fone : fzero, Up, M, (long long)NL * M, nl);
-    convert_f2d_add(s, Up, X, (long long)nX);
-    // far field of this pass's FP32 field (the solution on the first pass, the
-    // correction after it), in FP32: its norm relative to the first pass's far
-    // field is the relative change of the far field
-    scattered32(s, Up, ctx->d_D1, ctx->nL, ctx->h, M, ui, dni, it == 0, PS32);
-    gemm<float2, float2, float2>(s, OP_T, OP_T, M, P, 2 * nb, fone, PS32, M, 0, A2_32, 2 * nb, 0, fzero, duf, P, 0, 1);
-    CK(cudaMemsetAsync(nrm, 0, sizeof(double), s));
-    norm2_32(s, duf, (long long)M * P, nrm);
+      gemm<float2, float2, float2>(s, OP_N, OP_N, nb, M, nb, fone, ctx->d_Rb32, nb, 0, f32, M, 0, fzero, r32, M, 0, 1);
+      // downward sweep (adds the particular interface impedances after the first pass)
+      permute_rows<float2>(s, r32, ctx->d_bie_of_root, nb, M, B1);  // root box order
+      const float2* Fp = B1;
+      float2* out = B0;
+      for (int li = nlev - 1; li >= 0; --li) {
+        sweep_down_level<float2>(s, ctx->levels[li], ctx->ops32[li], Fp, TT[li], out, M, !first);
+        Fp = out;
+        out = (out == B0) ? B1 : B0;
+      }
+      gemm<float2, float2, float2>(s, OP_N, OP_N, NL, M, NE, fone, ctx->d_Y32, NE, (long long)NL * NE, Fp, M,
+                                   (long long)NE * M, first ? fzero : fone, Up, M, (long long)NL * M, nl);
+      convert_f2d_add(s, Up, X, (long long)nX);
+      // far field of this pass's FP32 field (the solution on the first pass, the
+      // correction after it), in FP32: its norm relative to the first pass's far
+      // field is the relative change of the far field
+      scattered32(s, Up, ctx->d_D1, ctx->nL, ctx->h, M, ui, dni, first, PS32);
+      gemm<float2, float2, float2>(s, OP_T, OP_T, M, P, 2 * nb, fone, PS32, M, 0, A2_32, 2 * nb, 0, fzero, duf, P, 0,
+                                   1);
+      CK(cudaMemsetAsync(nrm, 0, sizeof(double), s));
+      norm2_32(s, duf, (long long)M * P, nrm);
+      return HS_OK;
+    };
+    const bool capture = g_use_graphs && !prof_active(2) && !prof_active(3);
+    CKR(run_captured(ctx, s, ctx->pgraph[first ? 0 : 1], capture, ui, M, P, ctx->k, body));
     double dn2 = 0.0;
     CK(cudaMemcpyAsync(&dn2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1490,7 +1529,9 @@ void hs_destroy(hs_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->cfg.device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  if (ctx->fgraph) cudaGraphExecDestroy(ctx->fgraph);
+  ctx->fgraph.reset();
+  ctx->pgraph[0].reset();
+  ctx->pgraph[1].reset();
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->ws_base) cudaFree(ctx->ws_base);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

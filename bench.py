@@ -282,6 +282,8 @@ def run_hs(args, world, rank, local):
     d2h = 16 * w.M * w.P
 
     secondary = gn_and_gradient_times(hs, torch, local) if not args.no_secondary else None
+    if secondary is not None:
+        secondary["sweep_ms"] = sweep_time(hs, torch, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -356,6 +358,35 @@ def tf32_peak():
         return bf16 * 1.1 / 2.25, "measured bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25"
     except (OSError, KeyError, ValueError):
         return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"
+
+
+def sweep_time(hs, torch, local, k_max=10.0):
+    """Recursive-linearization sweep (Sec. 3.4): k = 1, 1.5, .., k_max with the
+    ceil(1.6 k) modes / ceil(4 k) incidences and receivers / leaves-by-k plan,
+    one Gauss-Newton step per frequency (FP64), blurred-ellipse phantom (seed 7)
+    plus 1% complex Gaussian noise.  The data of every frequency are computed
+    first on the GPU (untimed); the timed region is the whole sweep."""
+    from paper_1608_06871_gb300 import sweep as SW
+    plans = [SW.plan_ceil(float(k)) for k in np.arange(1.0, k_max + 0.25, 0.5)]
+    phantom = synth.ellipse_phantom(7)
+    data = {}
+    for p in plans:
+        al = 2 * np.pi * np.arange(p.M) / p.M
+        th = 2 * np.pi * np.arange(p.P) / p.P
+        gen = hs.Solver(p.leaves_per_side, 2, 2, 3.0, device=local)
+        x, y = gen.node_coords()
+        gen.build_nodes(phantom(x, y), p.k)
+        data[p.k] = synth.add_noise(gen.solve(al, th), 0.01, seed=70)
+        gen.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = SW.recursive_linearization(plans, lambda p, al, th: data[p.k], lambda_rel=1e-4, device=local)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": dt * 1e3, "unit": "ms", "frequencies": len(plans),
+            "workload": f"sweep k=1:0.5:{k_max:g}, S=ceil(1.6k), M=P=ceil(4k), leaves 2^max(2,ceil(log2 0.8k)), "
+                        "ellipse phantom seed 7 + 1% noise, 1 GN step per k, FP64",
+            "final_residual": float(res.history[-1]["residuals"][-1])}
 
 
 def gn_and_gradient_times(hs, torch, local, reps=3):

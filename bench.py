@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-kmax", type=float, default=10.0,
+                    help="top frequency of the timed recursive-linearization sweep (40 = the full k = 1..40 plan)")
     return ap.parse_args()
 
 
@@ -283,7 +285,7 @@ def run_hs(args, world, rank, local):
 
     secondary = gn_and_gradient_times(hs, torch, local) if not args.no_secondary else None
     if secondary is not None:
-        secondary["sweep_ms"] = sweep_time(hs, torch, local)
+        secondary["sweep_ms"] = sweep_time(hs, torch, local, k_max=args.sweep_kmax)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -435,7 +437,61 @@ def gn_and_gradient_times(hs, torch, local, reps=3):
     s.close()
     out["gradient_ms"] = {"value": float(np.median(ts)), "workload": w.name, "precision": "fp64",
                           "includes": "hs_build + hs_gradient (forward, adjoint sweep, projection)"}
+    out["gn_step_k40"] = gn_step_top(hs, torch, local)
     return out
+
+
+def gn_step_top(hs, torch, local):
+    """One Gauss-Newton step at the top frequency of the k = 1..40 sweep (k = 40,
+    32 x 32 leaves, 64 x 64 = 4096 sine modes, 160 incidences, 160 receivers;
+    blurred-ellipse phantom seed 7 with 1% noise as data, step from its
+    projection on 40 x 40 modes), FP64: hs_build + hs_gn_step, CUDA events.
+    Also times hs_jacobian_dev alone with the FP64 GEMM family's per-launch
+    events (the contraction and the adjoint sweep's products)."""
+    stream = torch.cuda.current_stream()
+    w = synth.WORKLOADS["gn_k40"]
+    phantom = synth.ellipse_phantom(7)
+    al, th = synth.directions(w.M), synth.receivers(w.P)
+    gen = hs.Solver(w.n_leaf_side, 2, 2, w.R, device=local, stream=stream.cuda_stream)
+    x, y = gen.node_coords()
+    gen.build_nodes(phantom(x, y), w.k)
+    data = synth.add_noise(gen.solve(al, th), 0.01, seed=70)
+    gen.close()
+    c = np.zeros((w.S, w.S))
+    c[:40, :40] = synth.project_sine(phantom, 40, 40)
+    s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, device=local, stream=stream.cuda_stream)
+    ts = []
+    for i in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.build(c, w.k)
+        c1, rn = s.gn_step(data, al, th, 1e-4, c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    s.build(c, w.k)
+    J = torch.empty((w.M * w.P, w.S * w.S, 2), dtype=torch.float64, device="cuda")
+    a_d, t_d = torch.tensor(al, device="cuda"), torch.tensor(th, device="cuda")
+    hs.hs_jacobian_dev(s.ctx, a_d, t_d, J)
+    torch.cuda.synchronize()
+    hs.hs_prof_start(hs.HS_PROF_GEMM_FP64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hs.hs_jacobian_dev(s.ctx, a_d, t_d, J)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms, g_flops, g_n = hs.hs_prof_stop()
+    s.close()
+    del J
+    nX = 14 * w.n_leaf_side
+    contract_flops = 4.0 * w.M * w.P * (nX * nX * w.S + nX * w.S * w.S)
+    return {"value": float(np.median(ts)), "unit": "ms", "workload": w.name, "precision": "fp64",
+            "includes": "hs_build + hs_gn_step (forward, adjoint sweep, Jacobian contraction, "
+                        "normal equations Re(J^H J) + lambda I by one FP64 GEMM, LU)",
+            "residual_norm": float(rn), "jacobian_ms": e0.elapsed_time(e1),
+            "jacobian_gemm_fp64": {"ms": g_ms, "launches": g_n, "tflops": g_flops / (g_ms * 1e-3) / 1e12,
+                                   "contraction_algorithmic_tflop": contract_flops / 1e12}}
 
 
 def main():

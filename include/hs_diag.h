@@ -56,6 +56,13 @@ int hs_set_graphs(int enable);
  * Process-wide; takes effect at the next launch.  Never fails. */
 int hs_set_tensor_cores(int enable);
 
+/* Bytes of scratch the Jacobian contraction may use for one chunk of
+ * (incidence, receiver) pairs (their Khatri-Rao rows and half-projected
+ * rows); 0 restores the default (1 GiB).  Smaller budgets mean more, smaller
+ * chunks with identical results.  Process-wide; takes effect at the next
+ * Jacobian.  Never fails. */
+int hs_set_contract_budget(unsigned long long bytes);
+
 /* C[b] = A[b] B[b] for b < batch: complex FP32 (interleaved re, im),
  * row-major, A m x k, B k x n, C m x n, contiguous batches, all DEVICE
  * pointers on the current device, enqueued on `stream` (a cudaStream_t, NULL

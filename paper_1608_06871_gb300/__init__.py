@@ -70,6 +70,7 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_double)]),
     "hs_set_tensor_cores": (_I, [_I]),
     "hs_set_graphs": (_I, [_I]),
+    "hs_set_contract_budget": (_I, [ctypes.c_ulonglong]),
     "hs_cgemm32": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
     "hs_lu_solve": (_I, [_I, _I, _I, _P, _P, _I, _P]),
     "hs_zgemm": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _I, _P]),
@@ -255,6 +256,11 @@ def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:
 
 def hs_set_graphs(enable: bool):
     _check(None, lib().hs_set_graphs(1 if enable else 0))
+
+
+def hs_set_contract_budget(nbytes: int):
+    """Scratch bytes per chunk of the Jacobian contraction (0 = the default 1 GiB)."""
+    _check(None, lib().hs_set_contract_budget(int(nbytes)))
 
 
 def hs_set_tensor_cores(enable: bool):

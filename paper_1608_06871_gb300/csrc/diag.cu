@@ -22,6 +22,7 @@ std::vector<ProfRec> g_prof;
 bool prof_active(int family) { return g_prof_family == family; }
 bool prof_any() { return g_prof_family != 0; }
 extern bool g_use_graphs;
+extern size_t g_contract_budget;
 
 void prof_begin(cudaStream_t s, cudaEvent_t* a) {
   cudaEventCreate(a);
@@ -121,6 +122,11 @@ int hs_peak_fp64(int device, double ms, double* tflops) {
 
 int hs_set_graphs(int enable) {
   hs::g_use_graphs = enable != 0;
+  return HS_OK;
+}
+
+int hs_set_contract_budget(unsigned long long bytes) {
+  hs::g_contract_budget = bytes ? (size_t)bytes : (size_t(1) << 30);
   return HS_OK;
 }
 

@@ -14,6 +14,9 @@
 namespace hs {
 thread_local long long* g_launch_counter = nullptr;
 bool g_use_graphs = true;  // process-wide switch (hs_set_graphs)
+// Scratch of the Jacobian contraction for one chunk of (d, p) pairs (Khatri-Rao
+// rows and half-projected rows); process-wide (hs_set_contract_budget).
+size_t g_contract_budget = size_t(1) << 30;
 bool prof_active(int family);
 }
 
@@ -1041,25 +1044,34 @@ size_t fields_and_adjoint_bytes(hs_ctx* ctx, int M, int P) {
          Arena::bytes((size_t)P * 2 * nb, 16) + 2 * Arena::bytes((size_t)nb * P, 16);
 }
 
+
 int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* J,
                   Arena& a) {
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
+  const int C = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget);
   double2* Ug = a.get<double2>(plane * M);
   double2* Zg = a.get<double2>(plane * P);
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
-  CKR(fields_and_adjoint(ctx, s, alphas, M, thetas, P, Ug, Zg, a));
+  {
+    Arena sub = a;  // the solves' scratch is reused by the contraction afterwards (same stream)
+    CKR(fields_and_adjoint(ctx, s, alphas, M, thetas, P, Ug, Zg, sub));
+  }
+  double2* W = a.get<double2>(plane * C);
+  double2* T = a.get<double2>((size_t)ctx->n14 * ctx->S1 * C);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   interior_sine_tables(s, ctx->d_xint, ctx->n14, ctx->S1, ctx->S2, ctx->d_sxi, ctx->d_syi);
-  size_t smem = sizeof(double2) * ((size_t)ctx->S1 * ctx->S2 + ctx->n14 + ctx->S1);
-  if (smem > 200 * 1024) return fail(ctx, HS_EINVAL, "S1*S2 too large for the Jacobian contraction");
   Phase ph("hs_jacobian_contract");
-  contract_jacobian(s, Ug, Zg, M, P, ctx->n14, ctx->d_sxi, ctx->d_syi, ctx->S1, ctx->S2, ctx->k * ctx->k, J);
+  contract_jacobian(s, Ug, Zg, M, P, ctx->n14, ctx->d_sxi, ctx->d_syi, ctx->S1, ctx->S2, ctx->k * ctx->k, J, W, T, C);
   CK(cudaGetLastError());
   return HS_OK;
 }
 
 size_t jacobian_bytes(hs_ctx* ctx, int M, int P) {
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
-  return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) + fields_and_adjoint_bytes(ctx, M, P);
+  const int C = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget);
+  return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) +
+         std::max(Arena::bytes(plane * C, 16) + Arena::bytes((size_t)ctx->n14 * ctx->S1 * C, 16),
+                  fields_and_adjoint_bytes(ctx, M, P));
 }
 
 int need_fp64(hs_ctx* ctx) {

@@ -10,6 +10,9 @@
 //   J[(d,p), (m1,m2)] = k^2 sum_x z_p(x) u_d(x) s_m1(x1) s_m2(x2)
 // over the interior collocation nodes: a Khatri-Rao product of forward and
 // adjoint fields projected on the separable sine basis (eq. sineseries).
+#include <algorithm>
+
+#include "linalg.cuh"
 #include "tree.cuh"
 
 namespace hs {
@@ -76,47 +79,43 @@ void interior_sine_tables(cudaStream_t s, const double* xg_int, int n, int S1, i
   HS_COUNT_LAUNCH();
 }
 
-// One block per (d, p): acc[m1][m2] = sum_gy sy[m2][gy] sum_gx sx[m1][gx] (u_d z_p)[gy][gx].
-__global__ void __launch_bounds__(256) k_contract(const double2* __restrict__ Ug, const double2* __restrict__ Zg,
-                                                  int P, int nX, const double* __restrict__ sx,
-                                                  const double* __restrict__ sy, int S1, int S2, double k2,
-                                                  double2* __restrict__ J) {
-  extern __shared__ double2 sm[];
-  double2* acc = sm;              // S1*S2
-  double2* w = acc + S1 * S2;     // nX
-  double2* t = w + nX;            // S1
-  const int pair = blockIdx.x;
-  const int d = pair / P, p = pair % P;
-  const long long plane = (long long)nX * nX;
-  const double2* u = Ug + d * plane;
-  const double2* z = Zg + p * plane;
-  for (int e = threadIdx.x; e < S1 * S2; e += blockDim.x) acc[e] = make_double2(0.0, 0.0);
-  for (int gy = 0; gy < nX; ++gy) {
-    __syncthreads();
-    for (int gx = threadIdx.x; gx < nX; gx += blockDim.x) w[gx] = u[(long long)gy * nX + gx] * z[(long long)gy * nX + gx];
-    __syncthreads();
-    for (int m1 = threadIdx.x; m1 < S1; m1 += blockDim.x) {
-      double2 v = make_double2(0.0, 0.0);
-      const double* srow = sx + (long long)m1 * nX;
-      for (int gx = 0; gx < nX; ++gx) v = v + srow[gx] * w[gx];
-      t[m1] = v;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < S1 * S2; e += blockDim.x) {
-      int m1 = e / S2, m2 = e % S2;
-      acc[e] = acc[e] + sy[(long long)m2 * nX + gy] * t[m1];
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < S1 * S2; e += blockDim.x) J[(long long)pair * S1 * S2 + e] = k2 * acc[e];
+// Khatri-Rao rows of the contraction: W[c][g] = u_d(g) z_p(g) for the pairs
+// c0 <= d*P + p < c0 + C over the interior grid points g (plane = nY * nX).
+__global__ void k_khatri_rao(const double2* __restrict__ Ug, const double2* __restrict__ Zg, int P, long long plane,
+                             long long c0, long long n, double2* __restrict__ W) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const long long c = c0 + e / plane, g = e % plane;
+  const long long d = c / P, p = c % P;
+  const double2 u = Ug[d * plane + g], z = Zg[p * plane + g];
+  W[e] = make_double2(u.x * z.x - u.y * z.y, u.x * z.y + u.y * z.x);
 }
 
+int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes) {
+  const size_t per = 16 * ((size_t)nX * nX + (size_t)nX * S1);
+  long long c = (long long)(budget_bytes / per);
+  // the second product is a batch of C launches' worth of grid.z
+  return (int)std::max<long long>(1, std::min<long long>({c, (long long)M * P, 32768LL}));
+}
+
+// J[(d,p)][m1][m2] = k2 sum_gy sy[m2][gy] sum_gx sx[m1][gx] u_d[gy][gx] z_p[gy][gx],
+// in chunks of C pairs: W = the pairs' Khatri-Rao rows (C x nY x nX), then
+// T = W sx^T over gx (rows (pair, gy), one GEMM), then J_pair = T_pair^T sy^T
+// over gy (a batch of S1 x S2 products).  W holds C*nX*nX and T C*nX*S1
+// complex values.
 void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
-                       const double* sy, int S1, int S2, double k2, double2* J) {
-  size_t smem = sizeof(double2) * ((size_t)S1 * S2 + nX + S1);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_contract<<<M * P, 256, smem, s>>>(Ug, Zg, P, nX, sx, sy, S1, S2, k2, J);
-  HS_COUNT_LAUNCH();
+                       const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C) {
+  const long long plane = (long long)nX * nX, MP = (long long)M * P;
+  for (long long c0 = 0; c0 < MP; c0 += C) {
+    const int nc = (int)std::min<long long>(C, MP - c0);
+    const long long n = nc * plane;
+    k_khatri_rao<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ug, Zg, P, plane, c0, n, W);
+    HS_COUNT_LAUNCH();
+    gemm<double2, double, double2>(s, OP_N, OP_T, nc * nX, S1, nX, make_double2(1.0, 0.0), W, nX, 0, sx, nX, 0,
+                                   make_double2(0.0, 0.0), T, S1, 0, 1);
+    gemm<double2, double, double2>(s, OP_T, OP_T, S1, S2, nX, make_double2(k2, 0.0), T, S1, (long long)nX * S1, sy,
+                                   nX, 0, make_double2(0.0, 0.0), J + c0 * S1 * S2, S2, (long long)S1 * S2, nc);
+  }
 }
 
 // Jst = [Re J; Im J] (2 rows x cols, real).

@@ -111,8 +111,10 @@ void adjoint_root_init(cudaStream_t s, int nb, int P, double eta, const double2*
 void leaf_to_grid(cudaStream_t s, const double2* Uleaf, int nrows_leaf, int nL, int nrhs, double2* G);
 void leaf_to_nodes(cudaStream_t s, const double2* Uleaf, int nL, int nrhs, double2* out);
 void interior_sine_tables(cudaStream_t s, const double* xg_int, int n, int S1, int S2, double* sx, double* sy);
+// Pairs per chunk of the contraction within budget_bytes of W and T.
+int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes);
 void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
-                       const double* sy, int S1, int S2, double k2, double2* J);
+                       const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C);
 void split_stack(cudaStream_t s, const double2* J, int rows, int cols, double* Jst);
 void residual(cudaStream_t s, const double* data, const double2* F, int n, double2* res, double* rst, double* out2);
 void add_lambda(cudaStream_t s, double* A, int n, double lambda_rel);

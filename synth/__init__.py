@@ -126,6 +126,45 @@ def ellipse_phantom(seed: int = 3, n: int = 5, centre_box: float = 0.6, axes=(0.
                           rng.uniform(0.0, math.pi, size=n), rng.uniform(*contrast, size=n), blur, clip)
 
 
+@dataclass(frozen=True)
+class Inclusions:
+    """Sum of contrast functions (Gaussian bumps and blurred ellipses), times `scale`."""
+
+    parts: tuple
+    scale: float = 1.0
+
+    def __call__(self, x, y):
+        out = 0.0
+        for f in self.parts:
+            out = out + f(x, y)
+        return self.scale * out
+
+
+def inclusions(seed: int = 5, n: int = 40, centre_box: float = 0.7) -> Inclusions:
+    """Seeded random sum of n inclusions, half Gaussian bumps (widths U[0.03, 0.12],
+    amplitudes U[0.1, 1]) and half blurred ellipses (semi-axes U[0.04, 0.2], contrast
+    U[0.1, 1], edge blur 0.02), centres U[-0.7, 0.7]^2 (the paper-scale reconstruction
+    contrast; scale it with `scaled_sine_coeffs`)."""
+    rng = np.random.default_rng(seed)
+    ng = n // 2
+    ne = n - ng
+    bumps = GaussianBumps(rng.uniform(-centre_box, centre_box, size=(ng, 2)), rng.uniform(0.03, 0.12, size=ng),
+                          rng.uniform(0.1, 1.0, size=ng))
+    ell = EllipsePhantom(rng.uniform(-centre_box, centre_box, size=(ne, 2)), rng.uniform(0.04, 0.2, size=(ne, 2)),
+                         rng.uniform(0.0, math.pi, size=ne), rng.uniform(0.1, 1.0, size=ne), 0.02, np.inf)
+    return Inclusions((bumps, ell))
+
+
+def scaled_sine_coeffs(qfun, S: int, qmax: float, nq: int = 640, grid: int = 1025) -> np.ndarray:
+    """Projection of q onto S x S sine modes, scaled so that max |q_S| over a uniform
+    `grid` x `grid` sample of Omega equals qmax (q_S the band-limited series, eq. sineseries)."""
+    c = project_sine(qfun, S, S, nq)
+    t = np.linspace(-1.0, 1.0, grid)
+    basis = np.sin(np.outer(np.arange(1, S + 1), t + 1.0) * (math.pi / 2.0))
+    q = basis.T @ c @ basis
+    return c * (qmax / np.max(np.abs(q)))
+
+
 def project_sine(qfun, S1: int, S2: int, nq: int = 256) -> np.ndarray:
     """Coefficients of the L2 projection of q onto s_m1(x) s_m2(y) on [-1,1]^2 (Gauss-Legendre, nq^2 points).
 
@@ -178,4 +217,11 @@ WORKLOADS = {
     "fwd_k40": Workload("fwd_k40_32x32leaves_128dirs_256recv", 40.0, 32, 40, 128, 256),
     # misfit gradient at k = 20 (1600 coefficients)
     "grad_k20": Workload("grad_k20_16x16leaves_1600modes_64dirs_128recv", 20.0, 16, 40, 64, 128),
+    # one Gauss-Newton step at the top frequency of the k = 1..40 sweep:
+    # S = ceil(1.6 k) = 64 modes per axis, M = P = ceil(4 k) = 160, 32 x 32 leaves
+    "gn_k40": Workload("gn_k40_32x32leaves_4096modes_160dirs_160recv", 40.0, 32, 64, 160, 160),
+    # forward batch at the top frequency of the paper-scale sweep: 140 x 140 = 19,600
+    # sine unknowns, 128 x 128 leaves (N = (15*128 + 1)^2 = 3,690,241 distinct points),
+    # 280 incidences and receivers
+    "fwd_k70": Workload("fwd_k70_128x128leaves_19600modes_280dirs_280recv", 70.0, 128, 140, 280, 280),
 }

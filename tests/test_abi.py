@@ -8,6 +8,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "hs.h")
+DIAG_HEADER = os.path.join(ROOT, "include", "hs_diag.h")
 
 
 @pytest.fixture(scope="module")
@@ -18,8 +19,8 @@ def lib():
     return hs
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(path=HEADER):
+    text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(hs_[a-z_]+)\s*\(", text)))
 
@@ -31,14 +32,16 @@ def test_header_declares_the_paper_calls():
         assert n in names
 
 
-def test_library_exports_every_declared_symbol(lib):
+@pytest.mark.parametrize("path", [HEADER, DIAG_HEADER])
+def test_library_exports_every_declared_symbol(lib, path):
     L = lib.lib()
-    for name in declared_functions():
+    for name in declared_functions(path):
         assert hasattr(L, name), name
 
 
-def test_binding_covers_every_declared_symbol(lib):
-    for name in declared_functions():
+@pytest.mark.parametrize("path", [HEADER, DIAG_HEADER])
+def test_binding_covers_every_declared_symbol(lib, path):
+    for name in declared_functions(path):
         assert hasattr(lib, name), name
 
 

@@ -1465,7 +1465,7 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
   CKR(jacobian_into(ctx, s, da, M, dt, P, J, a));
   // normal equations in the real coefficients: A = Jst^T Jst, b = Jst^T rst
   split_stack(s, J, MP, nm, Jst);
-  gemm<double, double, double>(s, OP_T, OP_N, nm, nm, 2 * MP, 1.0, Jst, nm, 0, Jst, nm, 0, 0.0, A, nm, 0, 1);
+  normal_matrix(s, Jst, 2 * MP, nm, A);
   gemm<double, double, double>(s, OP_T, OP_N, nm, 1, 2 * MP, 1.0, Jst, nm, 0, rst, 1, 0, 0.0, bv, 1, 0, 1);
   add_lambda(s, A, nm, lambda_rel);
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));

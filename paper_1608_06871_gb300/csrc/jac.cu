@@ -133,6 +133,35 @@ void split_stack(cudaStream_t s, const double2* J, int rows, int cols, double* J
   HS_COUNT_LAUNCH();
 }
 
+// A[r][c] = A[c][r] for the entries above the computed block-lower part
+// (column block of c beyond the row block of r).
+__global__ void k_mirror_upper(double* A, int n, int bs) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int r = (int)(e / n), c = (int)(e % n);
+  if (c >= (r / bs + 1) * bs) A[e] = A[(long long)c * n + r];
+}
+
+// A = Jst^T Jst (n x n, symmetric) for Jst (rows x n): block rows of width bs,
+// each the product with the columns up to and including its diagonal block,
+// then the upper part mirrored (about (nb + 1) / (2 nb) of the full product's
+// flops for nb blocks).
+void normal_matrix(cudaStream_t s, const double* Jst, int rows, int n, double* A) {
+  constexpr int bs = 256;
+  if (n < 4 * bs) {
+    gemm<double, double, double>(s, OP_T, OP_N, n, n, rows, 1.0, Jst, n, 0, Jst, n, 0, 0.0, A, n, 0, 1);
+    return;
+  }
+  for (int r0 = 0; r0 < n; r0 += bs) {
+    const int m = std::min(bs, n - r0), nc = std::min(n, r0 + bs);
+    gemm<double, double, double>(s, OP_T, OP_N, m, nc, rows, 1.0, Jst + r0, n, 0, Jst, n, 0, 0.0,
+                                 A + (long long)r0 * n, n, 0, 1);
+  }
+  const long long tot = (long long)n * n;
+  k_mirror_upper<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, n, bs);
+  HS_COUNT_LAUNCH();
+}
+
 // res = data - F; rst = [Re res; Im res]; out2 += sum |res|^2.
 __global__ void k_residual(const double* __restrict__ data, const double2* __restrict__ F, int n,
                            double2* __restrict__ res, double* __restrict__ rst, double* __restrict__ out2) {

@@ -116,6 +116,8 @@ int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes);
 void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
                        const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C);
 void split_stack(cudaStream_t s, const double2* J, int rows, int cols, double* Jst);
+// A = Jst^T Jst (n x n) by block rows of its lower part, mirrored.
+void normal_matrix(cudaStream_t s, const double* Jst, int rows, int n, double* A);
 void residual(cudaStream_t s, const double* data, const double2* F, int n, double2* res, double* rst, double* out2);
 void add_lambda(cudaStream_t s, double* A, int n, double lambda_rel);
 void gradient_combine(cudaStream_t s, const double2* Ug, const double2* Zmix, int M, long long npts, double* hre);

@@ -58,6 +58,14 @@ def parse():
     ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, choices=["gn_k40", "jacobian_16x16_s64", "lsqr_k40"],
+                    help="run one named workload once, untimed, and exit (a target for profilers)")
+    ap.add_argument("--table2", type=float, default=0.0,
+                    help="also run the paper's reconstruction plan (Sec. 4: k = 1:0.25:K, LSQR at 1e-3, "
+                         "triangular modes, 5%% noise) up to this K and report it in the format of Table 2")
+    ap.add_argument("--paper-gn", action="store_true",
+                    help="also time one FP64 Gauss-Newton step at the paper-scale top frequency (k = 70, "
+                         "19,600 coefficients, 280 x 280 data; about 3 minutes)")
     ap.add_argument("--sweep-kmax", type=float, default=10.0,
                     help="top frequency of the timed recursive-linearization sweep (40 = the full k = 1..40 plan)")
     return ap.parse_args()
@@ -286,6 +294,10 @@ def run_hs(args, world, rank, local):
     secondary = gn_and_gradient_times(hs, torch, local) if not args.no_secondary else None
     if secondary is not None:
         secondary["sweep_ms"] = sweep_time(hs, torch, local, k_max=args.sweep_kmax)
+        if args.table2 > 0:
+            secondary["paper_table2"] = paper_table2(hs, torch, local, args.table2)
+        if args.paper_gn:
+            secondary["paper_scale_gn_step_k70"] = paper_scale_gn(hs, torch, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -487,6 +499,78 @@ def paper_scale_forward(hs, torch, local):
     return out
 
 
+def paper_table2(hs, torch, local, k_max):
+    """The paper's reconstruction plan (Sec. 4) with its solver: k = 1, 1.25, .., k_max;
+    M = floor(2k) incidences, P = floor(4k) receivers at R = 20, unknowns the sine modes
+    m1 + m2 <= floor(2k), one Gauss-Newton step per frequency with LSQR stopped at 1e-3,
+    on [-pi/2, pi/2]^2 (computed on [-1, 1]^2 with k -> pi k / 2, R -> 2 R / pi).
+    Contrast: the blurred-ellipse phantom (seed 7) standing in for the head phantom;
+    data from the mixed-precision solver on a tree with twice the leaves per side
+    (a different discretisation from the inversion's) plus 5% noise (seed 70).
+    Reported like Table 2: N, Modes, M, M*P, T_f (factorisation), N_it (LSQR
+    iterations), T_l (LSQR time), T_t (cumulative), in seconds."""
+    from paper_1608_06871_gb300 import sweep as SW
+    plans = [SW.plan_paper(float(k)) for k in np.arange(1.0, k_max + 1e-9, 0.25)]
+    phantom = synth.ellipse_phantom(7)
+    data = {}
+    for p in plans:
+        al = 2 * np.pi * np.arange(p.M) / p.M
+        th = 2 * np.pi * np.arange(p.P) / p.P
+        gen = hs.Solver(min(2 * p.leaves_per_side, 128), 2, 2, p.R, hs.HS_MIXED, device=local)
+        x, y = gen.node_coords()
+        data[p.k] = synth.add_noise(gen.build_nodes(phantom(x, y), p.k).solve(al, th), 0.05, seed=70)
+        gen.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = SW.recursive_linearization(plans, lambda p, al, th: data[p.k], device=local, solver="lsqr")
+    total = time.perf_counter() - t0
+    rows, cum = [], 0.0
+    for h in res.history:
+        cum += h["t_f"][0] + h["t_l"][0]
+        if float(h["k"]).is_integer() and (int(h["k"]) & (int(h["k"]) - 1)) == 0:
+            rows.append({"k": h["k"], "N": h["N"], "Modes": h["modes"], "M": h["M"], "MP": h["M"] * h["P"],
+                         "T_f": h["t_f"][0], "N_it": h["lsqr_iterations"][0], "T_l": h["t_l"][0], "T_t": cum})
+    S = res.c.shape[0]
+    c_true = synth.project_sine(phantom, S, S, nq=max(256, 4 * S)) * plans[-1].mask()
+    return {"rows": rows, "frequencies": len(plans), "total_s": total,
+            "coeff_rel_err_vs_phantom_projection": float(np.linalg.norm(res.c - c_true) / np.linalg.norm(c_true)),
+            "note": "inverse on 4^l leaves with (pi k / 2) h <= 2.5 (finer than the paper's 6-10 points per "
+                    "wavelength); paper's Table 2 (MATLAB, up to 32 cores): k = 16: T_f 2.99 s, N_it 27, "
+                    "T_l 195.14 s, T_t 4109.56 s"}
+
+
+def paper_scale_gn(hs, torch, local):
+    """One Gauss-Newton step at the top frequency of the paper-scale reconstruction:
+    k = 70, 128 x 128 leaves, 140 x 140 = 19,600 sine unknowns, 280 incidences x 280
+    receivers (J: 78,400 x 19,600 complex), FP64 (hs_build + hs_gn_step: forward,
+    adjoint sweep, Jacobian contraction, symmetric normal matrix, LU), one timed
+    run with CUDA events.  Data: the 40-inclusion contrast (seed 5, max|q| = 0.5)
+    plus 1% noise; the step starts from its first 120 x 120 coefficients."""
+    stream = torch.cuda.current_stream()
+    w = synth.WORKLOADS["fwd_k70"]
+    c_true = synth.scaled_sine_coeffs(synth.inclusions(5), w.S, 0.5)
+    al, th = synth.directions(w.M), synth.receivers(w.P)
+    s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, device=local, stream=stream.cuda_stream)
+    data = synth.add_noise(s.build(c_true, w.k).solve(al, th), 0.01, seed=70)
+    c = np.zeros_like(c_true)
+    c[:120, :120] = c_true[:120, :120]
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    s.build(c, w.k)
+    e1.record(stream)
+    c1, rn = s.gn_step(data, al, th, 1e-4, c)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    return {"value": e0.elapsed_time(e2), "unit": "ms", "build_ms": e0.elapsed_time(e1),
+            "gn_ms": e1.elapsed_time(e2), "workload": w.name, "precision": "fp64",
+            "unknowns": w.S * w.S, "jacobian_rows": w.M * w.P, "residual_norm": float(rn),
+            "rel_err_before": float(np.linalg.norm(c - c_true) / np.linalg.norm(c_true)),
+            "rel_err_after": float(np.linalg.norm(c1 - c_true) / np.linalg.norm(c_true)),
+            "paper_context": "Table 2, k = 64 (8,128 modes, M*P = 65,536): T_f 25.97 s + LSQR T_l 1412.77 s on "
+                             "up to 32 Xeon cores"}
+
+
 def gn_step_top(hs, torch, local):
     """One Gauss-Newton step at the top frequency of the k = 1..40 sweep (k = 40,
     32 x 32 leaves, 64 x 64 = 4096 sine modes, 160 incidences, 160 receivers;
@@ -517,6 +601,26 @@ def gn_step_top(hs, torch, local):
         torch.cuda.synchronize()
         if i:
             ts.append(e0.elapsed_time(e1))
+    lsqr = {}
+    for name, prod in (("fp64_products", hs.HS_FP64), ("tensor_core_products", hs.HS_MIXED)):
+        ts_l = []
+        for i in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.build(c, w.k)
+            cl, _, it = s.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=500, products=prod)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                ts_l.append(e0.elapsed_time(e1))
+        lsqr[name] = {"ms": ts_l[0], "iterations": it, "c": cl}
+    lsqr_out = {"tolerance": 1e-3, "includes": "hs_build + hs_gn_step_lsqr (forward, adjoint sweep, LSQR with J "
+                                               "and J^H applied from the fields)"}
+    for name in lsqr:
+        lsqr_out[name] = {"ms": lsqr[name]["ms"], "iterations": lsqr[name]["iterations"]}
+    dc64 = lsqr["fp64_products"]["c"] - c
+    lsqr_out["tensor_core_step_rel_diff_vs_fp64"] = float(
+        np.linalg.norm(lsqr["tensor_core_products"]["c"] - c - dc64) / np.linalg.norm(dc64))
     s.build(c, w.k)
     J = torch.empty((w.M * w.P, w.S * w.S, 2), dtype=torch.float64, device="cuda")
     a_d, t_d = torch.tensor(al, device="cuda"), torch.tensor(th, device="cuda")
@@ -536,13 +640,54 @@ def gn_step_top(hs, torch, local):
     return {"value": float(np.median(ts)), "unit": "ms", "workload": w.name, "precision": "fp64",
             "includes": "hs_build + hs_gn_step (forward, adjoint sweep, Jacobian contraction, normal equations "
                         "Re(J^H J) + lambda I by symmetric block-row FP64 GEMMs, LU)",
-            "residual_norm": float(rn), "jacobian_ms": e0.elapsed_time(e1),
+            "residual_norm": float(rn), "lsqr_paper_solver": lsqr_out, "jacobian_ms": e0.elapsed_time(e1),
             "jacobian_gemm_fp64": {"ms": g_ms, "launches": g_n, "tflops": g_flops / (g_ms * 1e-3) / 1e12,
                                    "contraction_algorithmic_tflop": contract_flops / 1e12}}
 
 
+def run_case(name):
+    """Profiler targets: 'gn_k40' = data generation and two FP64 Gauss-Newton steps of the
+    k = 40 top-of-sweep workload; 'jacobian_16x16_s64' = one Jacobian at k = 20 on 16 x 16
+    leaves with 64 x 64 modes and 64 x 64 data; 'lsqr_k40' = data generation and one
+    LSQR Gauss-Newton step of the k = 40 workload (tolerance 1e-3)."""
+    import torch
+
+    from paper_1608_06871_gb300.build import build
+    build()
+    import paper_1608_06871_gb300 as hs
+    if name in ("gn_k40", "lsqr_k40"):
+        w = synth.WORKLOADS["gn_k40"]
+        ph = synth.ellipse_phantom(7)
+        al, th = synth.directions(w.M), synth.receivers(w.P)
+        g = hs.Solver(w.n_leaf_side, 2, 2, w.R)
+        x, y = g.node_coords()
+        data = synth.add_noise(g.build_nodes(ph(x, y), w.k).solve(al, th), 0.01, seed=70)
+        g.close()
+        c = np.zeros((w.S, w.S))
+        c[:40, :40] = synth.project_sine(ph, 40, 40)
+        s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R)
+        for _ in range(2 if name == "gn_k40" else 1):
+            s.build(c, w.k)
+            if name == "gn_k40":
+                s.gn_step(data, al, th, 1e-4, c)
+            else:
+                print("lsqr iterations", s.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=200)[2])
+        torch.cuda.synchronize()
+        print(name, "launches", s.launch_count())
+        s.close()
+    else:
+        s = hs.Solver(16, 64, 64)
+        s.build(synth.random_coeffs(64, 64, seed=5, scale=0.001), 20.0)
+        J = s.jacobian(synth.directions(64), synth.receivers(64))
+        print(name, J.shape, "launches", s.launch_count())
+        s.close()
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args.case)
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -144,6 +144,31 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
                const double* thetas, int P, double lambda_rel, double* c_inout,
                double* resid_norm_out);
 
+/* One Gauss-Newton step with the linearized least-squares problem solved by
+ * LSQR (Paige and Saunders), as the paper's experiments do (Sec. 4: LSQR,
+ * algebraically identical to conjugate gradients on eq. normaleq, stopped at a
+ * tolerance of 1e-3):  min over real dc of ||J dc - r||^2 + damp^2 ||dc||^2,
+ * r = data - F(c), dc restricted to the modes where mask != 0 (mask: S1*S2
+ * bytes in the order of c, or NULL for all modes; e.g. the triangle
+ * m1 + m2 <= S of Sec. 3.2).  J is never formed: every iteration applies J
+ * and J^H once, from the forward and adjoint fields of the built contrast
+ * (Theorem 3.1 / 3.2), in FP64 on the GPU; the iteration's vectors live on
+ * the host.  Stops when the relative residual or the relative normal-equations
+ * residual (LSQR's own estimates) is at most tol, or after max_iter
+ * iterations; *iters_out (optional) receives the count.  products: HS_FP64
+ * (both grid contractions of every iteration in FP64) or HS_MIXED (in complex
+ * FP32 on the tensor cores, 3xTF32; the forward and adjoint fields, the
+ * residual and the sine syntheses and projections stay FP64 -- for loose
+ * tolerances such as the paper's 1e-3, where the FP32 rounding of J v and
+ * J^H u is far below the stopping threshold).  Otherwise as hs_gn_step
+ * (c_inout updated, resid_norm_out = ||r||_2 before the step).  Needs an
+ * HS_FP64 context.  Errors: HS_EINVAL (damp < 0, tol < 0, max_iter < 1, bad
+ * products, bad sizes, NULL), HS_ENOTBUILT, HS_ENOMEM, HS_ECUDA, HS_ETIMEOUT. */
+int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M,
+                    const double* thetas, int P, const unsigned char* mask, double damp,
+                    double tol, int max_iter, int products, double* c_inout,
+                    double* resid_norm_out, int* iters_out);
+
 /* Gradient of the misfit 0.5 * ||F(c) - data||^2 with respect to the real sine
  * coefficients, grad = Re(J^H (F(c) - data)) (Theorem 3.2 read on the basis),
  * without forming J: one adjoint sweep over the receivers.  grad: S1*S2 doubles

@@ -13,6 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import forward as F
+from . import lsqr as L
 
 
 def embed(c: np.ndarray, S1: int, S2: int) -> np.ndarray:
@@ -22,10 +23,14 @@ def embed(c: np.ndarray, S1: int, S2: int) -> np.ndarray:
     return out
 
 
-def sweep(plans, data_fn, lambda_rel: float, c0=None, R: float = 3.0):
-    """plans: objects with k, leaves_per_side, S, M, P, newton (increasing k).
+def sweep(plans, data_fn, lambda_rel: float, c0=None, R: float | None = None, solver: str = "direct",
+          lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200):
+    """plans: objects with k, leaves_per_side, S, M, P, newton (increasing k), and
+    optionally R and mask() (the unknown modes; None = all).
 
     data_fn(plan, alphas, thetas) -> measured far field (M x P complex).
+    solver: "direct" = normal equations with lambda_rel (eq. normaleq); "lsqr" = the
+    paper's LSQR at lsqr_tol on the plan's modes (Sec. 4).
     Returns the final coefficients and the residual norms per frequency.
     """
     c = np.zeros((plans[0].S, plans[0].S)) if c0 is None else np.asarray(c0, dtype=np.float64)
@@ -36,14 +41,20 @@ def sweep(plans, data_fn, lambda_rel: float, c0=None, R: float = 3.0):
         th = 2 * np.pi * np.arange(p.P) / p.P
         data = data_fn(p, al, th)
         res = []
+        radius = getattr(p, "R", 3.0) if R is None else R
+        mask = p.mask() if hasattr(p, "mask") else None
         for _ in range(p.newton):
-            fw = F.forward_from_coeffs(c, p.k, p.leaves_per_side, R)
+            fw = F.forward_from_coeffs(c, p.k, p.leaves_per_side, radius)
             Fc, _ = fw.solve_plane(al, th)
             J = fw.jacobian(al, th, p.S, p.S)
             r = (data - Fc).ravel()
-            A = (J.conj().T @ J).real
-            lam = lambda_rel * np.trace(A) / A.shape[0]
-            c = c + F.gn_step(J, r, lam).reshape(p.S, p.S)
+            if solver == "lsqr":
+                dc, _ = L.gn_step_lsqr(J, r, lsqr_tol, lsqr_max_iter, None if mask is None else mask.ravel())
+            else:
+                A = (J.conj().T @ J).real
+                lam = lambda_rel * np.trace(A) / A.shape[0]
+                dc = F.gn_step(J, r, lam)
+            c = c + dc.reshape(p.S, p.S)
             res.append(float(np.linalg.norm(r)))
         history.append(res)
     return c, history

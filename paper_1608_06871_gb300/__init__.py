@@ -57,6 +57,8 @@ _SIGS = {
     "hs_jacobian": (_I, [_P, _D, _I, _D, _I, _D]),
     "hs_jacobian_dev": (_I, [_P, _P, _I, _P, _I, _P, _P]),
     "hs_gn_step": (_I, [_P, _D, _D, _I, _D, _I, ctypes.c_double, _D, _D]),
+    "hs_gn_step_lsqr": (_I, [_P, _D, _D, _I, _D, _I, _P, ctypes.c_double, ctypes.c_double, _I, _I, _D, _D,
+                             ctypes.POINTER(_I)]),
     "hs_gradient": (_I, [_P, _D, _D, _I, _D, _I, _D, _D]),
     "hs_gradient_dev": (_I, [_P, _P, _P, _I, _P, _I, _P, _P, _P]),
     "hs_launch_count": (ctypes.c_longlong, [_P]),
@@ -196,6 +198,25 @@ def hs_gn_step(ctx, data, alphas, thetas, lambda_rel: float, c):
     return c2, rn.value
 
 
+def hs_gn_step_lsqr(ctx, data, alphas, thetas, c, mask=None, damp: float = 0.0, tol: float = 1e-3,
+                    max_iter: int = 100, products: int = HS_FP64):
+    """Returns (new coefficients, ||data - F(c)||, LSQR iterations): the Gauss-Newton step with
+    LSQR on the linearized problem (Sec. 4), dc restricted to mask (boolean, shape of c);
+    products = HS_MIXED runs the grid contractions in FP32 on the tensor cores."""
+    d = _cplx_pairs(data)
+    a, t = _f64(alphas), _f64(thetas)
+    c2 = _f64(c).copy()
+    m = None if mask is None else np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).ravel())
+    if m is not None and m.size != c2.size:
+        raise ValueError("mask must have the shape of c")
+    rn = ctypes.c_double(0.0)
+    it = _I(0)
+    _check(ctx, lib().hs_gn_step_lsqr(ctx, _dp(d), _dp(a), len(a), _dp(t), len(t),
+                                      None if m is None else m.ctypes.data_as(_P), float(damp), float(tol),
+                                      int(max_iter), int(products), _dp(c2), ctypes.byref(rn), ctypes.byref(it)))
+    return c2, rn.value, it.value
+
+
 def hs_gradient(ctx, data, alphas, thetas, S1: int, S2: int):
     """Returns (grad of 0.5 ||F(c) - data||^2 w.r.t. c as (S1, S2), misfit)."""
     d = _cplx_pairs(data)
@@ -331,6 +352,10 @@ class Solver:
 
     def gn_step(self, data, alphas, thetas, lambda_rel, c):
         return hs_gn_step(self.ctx, data, alphas, thetas, lambda_rel, c)
+
+    def gn_step_lsqr(self, data, alphas, thetas, c, mask=None, damp=0.0, tol=1e-3, max_iter=100,
+                     products=HS_FP64):
+        return hs_gn_step_lsqr(self.ctx, data, alphas, thetas, c, mask, damp, tol, max_iter, products)
 
     def gradient(self, data, alphas, thetas):
         return hs_gradient(self.ctx, data, alphas, thetas, self.S1, self.S2)

@@ -1482,6 +1482,195 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
   return HS_OK;
 }
 
+int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M, const double* thetas, int P,
+                    const unsigned char* mask, double damp, double tol, int max_iter, int products,
+                    double* c_inout, double* resid_norm_out, int* iters_out) {
+  CKR(check_ctx(ctx, true));
+  LaunchScope ls(ctx);
+  CKR(need_fp64(ctx));
+  CKR(valid_angles(ctx, M, P));
+  if (!data || !alphas || !thetas || !c_inout) return fail(ctx, HS_EINVAL, "NULL pointer");
+  if (!(damp >= 0.0) || !std::isfinite(damp) || !(tol >= 0.0) || max_iter < 1)
+    return fail(ctx, HS_EINVAL, "damp and tol must be >= 0 and max_iter >= 1");
+  if (products != HS_FP64 && products != HS_MIXED) return fail(ctx, HS_EINVAL, "products must be HS_FP64 or HS_MIXED");
+  const bool p32 = products == HS_MIXED;
+  cudaStream_t s = ctx->stream;
+  const int MP = M * P, nm = ctx->S1 * ctx->S2, nX = ctx->n14, S1 = ctx->S1, S2 = ctx->S2;
+  const size_t N = (size_t)nX * nX;
+  const double k2 = ctx->k * ctx->k;
+  const int nb = ctx->B.nb;
+  // device buffers: inputs, residual, fields; then (reusing the solves' scratch)
+  // the buffers of the two products
+  const size_t far = 4 * Arena::bytes((size_t)nb * M, 16) + Arena::bytes((size_t)2 * nb * M, 16) +
+                     Arena::bytes((size_t)P * 2 * nb, 16);
+  const size_t prod = Arena::bytes(nm, 8) * 2 + Arena::bytes((size_t)S2 * nX, 8) + Arena::bytes(N, 8) * 2 +
+                      Arena::bytes(N * M, 16) + Arena::bytes(MP, 16) * 2 + Arena::bytes((size_t)S1 * nX, 8) +
+                      (p32 ? 2 * Arena::bytes(N * P, 8) + Arena::bytes(N * M, 8) + 2 * Arena::bytes(MP, 8) : 0);
+  const size_t need = Arena::bytes(M, 8) + Arena::bytes(P, 8) + Arena::bytes((size_t)2 * MP, 8) +
+                      Arena::bytes(8, 8) + Arena::bytes(MP, 16) * 2 + Arena::bytes(N * M, 16) +
+                      Arena::bytes(N * P, 16) + std::max({far, fields_and_adjoint_bytes(ctx, M, P), prod});
+  Arena a;
+  CKR(ensure_ws(ctx, need, a));
+  double* da = a.get<double>(M);
+  double* dt = a.get<double>(P);
+  double* ddata = a.get<double>((size_t)2 * MP);
+  double* nrm2 = a.get<double>(8);
+  double2* F = a.get<double2>(MP);
+  double2* res = a.get<double2>(MP);
+  double2* Ug = a.get<double2>(N * M);
+  double2* Zg = a.get<double2>(N * P);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
+  {  // forward far field F(c) and r = data - F
+    Arena sub = a;
+    double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);
+    double2 *f = sub.get<double2>((size_t)nb * M), *g = sub.get<double2>((size_t)nb * M);
+    double2* PS = sub.get<double2>((size_t)2 * nb * M);
+    double2* A2 = sub.get<double2>((size_t)P * 2 * nb);
+    if (sub.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+    CKR(root_solve(ctx, s, da, M, ui, dni, f, g));
+    boundary_data(s, nb, M, ctx->k, f, g, ui, dni, PS);
+    farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, dt, P, A2);
+    gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
+                                    make_double2(0, 0), F, P, 0, 1);
+  }
+  residual(s, ddata, F, MP, res, nullptr, nrm2);
+  {
+    Arena sub = a;
+    CKR(fields_and_adjoint(ctx, s, da, M, dt, P, Ug, Zg, sub));
+  }
+  interior_sine_tables(s, ctx->d_xint, nX, S1, S2, ctx->d_sxi, ctx->d_syi);
+  double* dv = a.get<double>(nm);
+  double* dg = a.get<double>(nm);
+  double* G1 = a.get<double>((size_t)S2 * nX);
+  double* qv = a.get<double>(N);
+  double* h = a.get<double>(N);
+  double2* Y = a.get<double2>(N * M);
+  double2* dy = a.get<double2>(MP);
+  double2* fc = a.get<double2>(MP);
+  double* T1 = a.get<double>((size_t)S1 * nX);
+  float2 *Zg32 = nullptr, *ZgT32 = nullptr, *Y32 = nullptr, *y32 = nullptr, *fc32 = nullptr;
+  if (p32) {
+    Zg32 = a.get<float2>(N * P);
+    ZgT32 = a.get<float2>(N * P);
+    Y32 = a.get<float2>(N * M);
+    y32 = a.get<float2>(MP);
+    fc32 = a.get<float2>(MP);
+  }
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  if (p32) fields32(s, Zg, P, (long long)N, Zg32, ZgT32);
+  std::vector<unsigned char> keep(nm, 1);
+  if (mask)
+    for (int i = 0; i < nm; ++i) keep[i] = mask[i] ? 1 : 0;
+  // A = [Re J; Im J] restricted to the kept columns, as products on the GPU
+  std::vector<double2> hy(MP);
+  auto matvec = [&](const std::vector<double>& v, std::vector<double>& out) {  // out (2 MP) = A v
+    CK(cudaMemcpyAsync(dv, v.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, s));
+    if (p32)
+      apply_J32(s, Ug, ZgT32, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dv, G1, qv, Y32, y32, dy);
+    else
+      apply_J(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dv, G1, qv, Y, dy);
+    CK(cudaMemcpyAsync(hy.data(), dy, sizeof(double2) * MP, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < MP; ++i) {
+      out[i] = hy[i].x;
+      out[MP + i] = hy[i].y;
+    }
+    return HS_OK;
+  };
+  auto rmatvec = [&](const std::vector<double>& u, std::vector<double>& out) {  // out (nm) = A^T u
+    for (int i = 0; i < MP; ++i) hy[i] = make_double2(u[i], u[MP + i]);
+    CK(cudaMemcpyAsync(dy, hy.data(), sizeof(double2) * MP, cudaMemcpyHostToDevice, s));
+    if (p32)
+      apply_JH32(s, Ug, Zg32, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dy, fc32, Y32, h, T1, dg);
+    else
+      apply_JH(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dy, fc, Y, h, T1, dg);
+    CK(cudaMemcpyAsync(out.data(), dg, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < nm; ++i)
+      if (!keep[i]) out[i] = 0.0;
+    return HS_OK;
+  };
+  auto norm = [](const std::vector<double>& z) {
+    double acc = 0.0;
+    for (double e : z) acc += e * e;
+    return std::sqrt(acc);
+  };
+  // LSQR (Paige and Saunders): Golub-Kahan bidiagonalisation started from
+  // b = [Re r; Im r], plane rotations (first the damping term, then beta)
+  std::vector<double> b(2 * (size_t)MP), u(2 * (size_t)MP), t2(2 * (size_t)MP);
+  std::vector<double> x(nm, 0.0), v(nm), w(nm), tn(nm);
+  {
+    std::vector<double2> hr(MP);
+    CK(cudaMemcpyAsync(hr.data(), res, sizeof(double2) * MP, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < MP; ++i) {
+      b[i] = hr[i].x;
+      b[MP + i] = hr[i].y;
+    }
+  }
+  Phase ph("hs_gn_lsqr");
+  int it = 0;
+  double beta = norm(b);
+  if (beta > 0.0) {
+    for (size_t i = 0; i < b.size(); ++i) u[i] = b[i] / beta;
+    CKR(rmatvec(u, v));
+    double alpha = norm(v);
+    if (alpha > 0.0) {
+      for (double& e : v) e /= alpha;
+      w = v;
+      double phibar = beta, rhobar = alpha, anorm2 = 0.0, res2 = 0.0;
+      const double beta1 = beta;
+      while (it < max_iter) {
+        ++it;
+        CKR(matvec(v, t2));
+        for (size_t i = 0; i < u.size(); ++i) u[i] = t2[i] - alpha * u[i];
+        beta = norm(u);
+        if (beta > 0.0)
+          for (double& e : u) e /= beta;
+        anorm2 += alpha * alpha + beta * beta + damp * damp;
+        CKR(rmatvec(u, tn));
+        for (int i = 0; i < nm; ++i) v[i] = tn[i] - beta * v[i];
+        alpha = norm(v);
+        if (alpha > 0.0)
+          for (double& e : v) e /= alpha;
+        const double rhobar1 = std::hypot(rhobar, damp);
+        const double c1 = rhobar / rhobar1, s1 = damp / rhobar1;
+        const double psi = s1 * phibar;
+        phibar = c1 * phibar;
+        const double rho = std::hypot(rhobar1, beta);
+        const double c = rhobar1 / rho, sn = beta / rho;
+        const double theta = sn * alpha;
+        rhobar = -c * alpha;
+        const double phi = c * phibar;
+        phibar = sn * phibar;
+        for (int i = 0; i < nm; ++i) {
+          x[i] += (phi / rho) * w[i];
+          w[i] = v[i] - (theta / rho) * w[i];
+        }
+        res2 += psi * psi;
+        const double rnorm = std::sqrt(phibar * phibar + res2);
+        const double arnorm = alpha * std::fabs(c) * std::fabs(phibar);
+        const double test1 = rnorm / beta1;
+        const double test2 = rnorm > 0.0 ? arnorm / (std::sqrt(anorm2) * rnorm) : 0.0;
+        if (test1 <= tol || test2 <= tol || alpha == 0.0 || beta == 0.0) break;
+      }
+    }
+  }
+  double r2 = 0.0;
+  CK(cudaMemcpyAsync(&r2, nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (p32 && tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
+  for (int i = 0; i < nm; ++i) c_inout[i] += x[i];
+  if (resid_norm_out) *resid_norm_out = std::sqrt(r2);
+  if (iters_out) *iters_out = it;
+  return HS_OK;
+}
+
 int hs_gradient_dev(hs_ctx* ctx, const double* data, const double* alphas, int M, const double* thetas, int P,
                     double* grad, double* misfit_out, void* stream) {
   CKR(check_ctx(ctx, true));

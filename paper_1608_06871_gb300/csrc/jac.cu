@@ -118,6 +118,151 @@ void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int
   }
 }
 
+// Products with J without forming it, for iterative solves of the linearized
+// problem: with the forward fields u_d and adjoint fields z_p on the interior
+// grid (N = nX^2 points),
+//   (J v)[d][p]  = sum_x z_p(x) (k2 u_d(x) q_v(x)),  q_v(x) = sum_m v_m s_m1(x1) s_m2(x2),
+//   Re(J^H f)_m  = k2 sum_x s_m1(x1) s_m2(x2) Re sum_d u_d(x) sum_p conj(f_dp) z_p(x).
+__global__ void k_weight_fields(const double2* __restrict__ Ug, const double* __restrict__ qv, double k2, long long N,
+                                long long n, double2* __restrict__ Y) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double w = k2 * qv[e % N];
+  const double2 u = Ug[e];
+  Y[e] = make_double2(w * u.x, w * u.y);
+}
+
+__global__ void k_conj_copy(const double2* __restrict__ f, int n, double2* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = make_double2(f[e].x, -f[e].y);
+}
+
+// y = J v (M x P complex) for real v (S1 x S2); G1 (S2 x nX), qv (nX^2), Y (M x nX^2) scratch.
+void apply_J(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
+             const double* sy, int S1, int S2, double k2, const double* v, double* G1, double* qv, double2* Y,
+             double2* y) {
+  const long long N = (long long)nX * nX;
+  // q_v[gy][gx] = sum_m2 sy[m2][gy] sum_m1 v[m1][m2] sx[m1][gx]
+  gemm<double, double, double>(s, OP_T, OP_N, S2, nX, S1, 1.0, v, S2, 0, sx, nX, 0, 0.0, G1, nX, 0, 1);
+  gemm<double, double, double>(s, OP_T, OP_N, nX, nX, S2, 1.0, sy, nX, 0, G1, nX, 0, 0.0, qv, nX, 0, 1);
+  k_weight_fields<<<(unsigned)((N * M + 255) / 256), 256, 0, s>>>(Ug, qv, k2, N, N * M, Y);
+  HS_COUNT_LAUNCH();
+  gemm<double2, double2, double2>(s, OP_N, OP_T, M, P, (int)N, make_double2(1.0, 0.0), Y, (int)N, 0, Zg, (int)N, 0,
+                                  make_double2(0.0, 0.0), y, P, 0, 1);
+}
+
+// g = Re(J^H f) (S1 x S2) for complex f (M x P); fc (M x P), Zmix (M x nX^2), h (nX^2), T1 (S1 x nX) scratch.
+void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
+              const double* sy, int S1, int S2, double k2, const double2* f, double2* fc, double2* Zmix, double* h,
+              double* T1, double* g) {
+  const long long N = (long long)nX * nX;
+  k_conj_copy<<<(M * P + 255) / 256, 256, 0, s>>>(f, M * P, fc);
+  HS_COUNT_LAUNCH();
+  gemm<double2, double2, double2>(s, OP_N, OP_N, M, (int)N, P, make_double2(1.0, 0.0), fc, P, 0, Zg, (int)N, 0,
+                                  make_double2(0.0, 0.0), Zmix, (int)N, 0, 1);
+  gradient_combine(s, Ug, Zmix, M, N, h);
+  gemm<double, double, double>(s, OP_N, OP_T, S1, nX, nX, 1.0, sx, nX, 0, h, nX, 0, 0.0, T1, nX, 0, 1);
+  gemm<double, double, double>(s, OP_N, OP_T, S1, S2, nX, k2, T1, nX, 0, sy, nX, 0, 0.0, g, S2, 0, 1);
+}
+
+// The same products with the grid contractions in complex FP32 on the tensor
+// cores (3xTF32), for iterations that stop at a loose tolerance: Zg32 = Zg and
+// ZgT32 = Zg^T in FP32 (made once by fields32), the small sine syntheses and
+// projections and the reduction over d in FP64.
+__global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+// out[x][p] = Z[p][x] (FP32), through 32 x 32 shared tiles
+__global__ void k_transpose32(const double2* __restrict__ Z, int P, long long N, float2* __restrict__ out) {
+  __shared__ float2 t[32][33];
+  const long long x0 = (long long)blockIdx.x * 32;
+  const int p0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int p = p0 + i;
+    const long long x = x0 + threadIdx.x;
+    if (p < P && x < N) {
+      const double2 v = Z[(long long)p * N + x];
+      t[i][threadIdx.x] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long long x = x0 + i;
+    const int p = p0 + threadIdx.x;
+    if (p < P && x < N) out[x * P + p] = t[threadIdx.x][i];
+  }
+}
+
+__global__ void k_weight_fields32(const double2* __restrict__ Ug, const double* __restrict__ qv, double k2,
+                                  long long N, long long n, float2* __restrict__ Y) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double w = k2 * qv[e % N];
+  const double2 u = Ug[e];
+  Y[e] = make_float2((float)(w * u.x), (float)(w * u.y));
+}
+
+__global__ void k_conj_to_f32(const double2* __restrict__ f, int n, float2* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = make_float2((float)f[e].x, (float)-f[e].y);
+}
+
+__global__ void k_f32_to_f64(const float2* __restrict__ a, int n, double2* __restrict__ b) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = make_double2((double)a[e].x, (double)a[e].y);
+}
+
+__global__ void k_gradient_combine32(const double2* __restrict__ Ug, const float2* __restrict__ Zmix, int M,
+                                     long long npts, double* __restrict__ hre) {
+  long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= npts) return;
+  double v = 0.0;
+  for (int d = 0; d < M; ++d) {
+    const double2 a = Ug[d * npts + x];
+    const float2 b = Zmix[d * npts + x];
+    v += a.x * (double)b.x - a.y * (double)b.y;
+  }
+  hre[x] = v;
+}
+
+void fields32(cudaStream_t s, const double2* Zg, int P, long long N, float2* Zg32, float2* ZgT32) {
+  k_to_f32<<<(unsigned)((N * P + 255) / 256), 256, 0, s>>>(Zg, Zg32, N * P);
+  HS_COUNT_LAUNCH();
+  dim3 tb(32, 8), grid((unsigned)((N + 31) / 32), (P + 31) / 32);
+  k_transpose32<<<grid, tb, 0, s>>>(Zg, P, N, ZgT32);
+  HS_COUNT_LAUNCH();
+}
+
+void apply_J32(cudaStream_t s, const double2* Ug, const float2* ZgT32, int M, int P, int nX, const double* sx,
+               const double* sy, int S1, int S2, double k2, const double* v, double* G1, double* qv, float2* Y,
+               float2* y32, double2* y) {
+  const long long N = (long long)nX * nX;
+  gemm<double, double, double>(s, OP_T, OP_N, S2, nX, S1, 1.0, v, S2, 0, sx, nX, 0, 0.0, G1, nX, 0, 1);
+  gemm<double, double, double>(s, OP_T, OP_N, nX, nX, S2, 1.0, sy, nX, 0, G1, nX, 0, 0.0, qv, nX, 0, 1);
+  k_weight_fields32<<<(unsigned)((N * M + 255) / 256), 256, 0, s>>>(Ug, qv, k2, N, N * M, Y);
+  HS_COUNT_LAUNCH();
+  gemm<float2, float2, float2>(s, OP_N, OP_N, M, P, (int)N, make_float2(1.f, 0.f), Y, (int)N, 0, ZgT32, P, 0,
+                               make_float2(0.f, 0.f), y32, P, 0, 1);
+  k_f32_to_f64<<<(M * P + 255) / 256, 256, 0, s>>>(y32, M * P, y);
+  HS_COUNT_LAUNCH();
+}
+
+void apply_JH32(cudaStream_t s, const double2* Ug, const float2* Zg32, int M, int P, int nX, const double* sx,
+                const double* sy, int S1, int S2, double k2, const double2* f, float2* fc, float2* Zmix, double* h,
+                double* T1, double* g) {
+  const long long N = (long long)nX * nX;
+  k_conj_to_f32<<<(M * P + 255) / 256, 256, 0, s>>>(f, M * P, fc);
+  HS_COUNT_LAUNCH();
+  gemm<float2, float2, float2>(s, OP_N, OP_N, M, (int)N, P, make_float2(1.f, 0.f), fc, P, 0, Zg32, (int)N, 0,
+                               make_float2(0.f, 0.f), Zmix, (int)N, 0, 1);
+  k_gradient_combine32<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Ug, Zmix, M, N, h);
+  HS_COUNT_LAUNCH();
+  gemm<double, double, double>(s, OP_N, OP_T, S1, nX, nX, 1.0, sx, nX, 0, h, nX, 0, 0.0, T1, nX, 0, 1);
+  gemm<double, double, double>(s, OP_N, OP_T, S1, S2, nX, k2, T1, nX, 0, sy, nX, 0, 0.0, g, S2, 0, 1);
+}
+
 // Jst = [Re J; Im J] (2 rows x cols, real).
 __global__ void k_split_stack(const double2* __restrict__ J, int rows, int cols, double* __restrict__ Jst) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -116,6 +116,21 @@ int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes);
 void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
                        const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C);
 void split_stack(cudaStream_t s, const double2* J, int rows, int cols, double* Jst);
+// J v and Re(J^H f) from the forward and adjoint fields on the interior grid (no J formed).
+void apply_J(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
+             const double* sy, int S1, int S2, double k2, const double* v, double* G1, double* qv, double2* Y,
+             double2* y);
+void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
+              const double* sy, int S1, int S2, double k2, const double2* f, double2* fc, double2* Zmix, double* h,
+              double* T1, double* g);
+// Same products with the grid contractions in complex FP32 on the tensor cores.
+void fields32(cudaStream_t s, const double2* Zg, int P, long long N, float2* Zg32, float2* ZgT32);
+void apply_J32(cudaStream_t s, const double2* Ug, const float2* ZgT32, int M, int P, int nX, const double* sx,
+               const double* sy, int S1, int S2, double k2, const double* v, double* G1, double* qv, float2* Y,
+               float2* y32, double2* y);
+void apply_JH32(cudaStream_t s, const double2* Ug, const float2* Zg32, int M, int P, int nX, const double* sx,
+                const double* sy, int S1, int S2, double k2, const double2* f, float2* fc, float2* Zmix, double* h,
+                double* T1, double* g);
 // A = Jst^T Jst (n x n) by block rows of its lower part, mirrored.
 void normal_matrix(cudaStream_t s, const double* Jst, int rows, int n, double* A);
 void residual(cudaStream_t s, const double* data, const double2* F, int n, double2* res, double* rst, double* out2);

@@ -16,6 +16,7 @@ from __future__ import annotations
 import json
 import math
 import os
+import time
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -33,6 +34,15 @@ class FrequencyPlan:
     M: int       # incidences
     P: int       # receivers
     newton: int  # Gauss-Newton steps
+    R: float = 3.0                 # receiver radius on [-1, 1]^2
+    triangle: int = 0              # > 0: only modes m1 + m2 <= triangle are unknowns
+    k_label: float | None = None   # the frequency in the paper's units, when rescaled
+
+    def mask(self):
+        if self.triangle <= 0:
+            return None
+        m = np.arange(1, self.S + 1)
+        return (m[:, None] + m[None, :]) <= self.triangle
 
 
 def plan_ceil(k: float, mode_factor: float = 1.6, dir_factor: float = 4.0, newton: int = 1,
@@ -41,6 +51,29 @@ def plan_ceil(k: float, mode_factor: float = 1.6, dir_factor: float = 4.0, newto
     nl = 2 ** max(int(math.log2(min_leaves)), int(math.ceil(math.log2(max(leaf_k * k, 1.0)))))
     return FrequencyPlan(k, min(nl, max_leaves), int(math.ceil(mode_factor * k)), int(math.ceil(dir_factor * k)),
                          int(math.ceil(dir_factor * k)), newton)
+
+
+def plan_paper(k: float, R: float = 20.0, leaf_kh: float = 2.5, min_leaves: int = 4,
+               max_leaves: int = 128) -> FrequencyPlan:
+    """The paper's experiment plan (Sec. 4) at its frequency k on its domain
+    [-pi/2, pi/2]^2, read on [-1, 1]^2 by x = (pi/2) x_hat: the wavenumber becomes
+    pi k / 2 and the receiver radius 2 R / pi (R = 20); M = floor(2k) incidences,
+    P = floor(4k) receivers, unknowns the sine modes m1 + m2 <= floor(2k) (the
+    basis sin(m (x + pi/2)) is sin(m pi (x_hat + 1) / 2)); one Gauss-Newton step.
+    Leaves: the smallest power of two with (pi k / 2) h <= leaf_kh (h = 2 / n_L),
+    which keeps the leaf Dirichlet blocks well away from resonance (the paper's
+    own rule, 6-10 points per wavelength, is coarser)."""
+    kh = math.pi * k / 2.0
+    nl = max(min_leaves, 2 ** int(math.ceil(math.log2(max(2.0 * kh / leaf_kh, 1.0)))))
+    S = int(math.floor(2.0 * k))
+    return FrequencyPlan(kh, min(nl, max_leaves), max(S - 1, 1), int(math.floor(2.0 * k)),
+                         int(math.floor(4.0 * k)), 1, R=2.0 * R / math.pi, triangle=S, k_label=k)
+
+
+def solver_kind_lsqr(solver_name: str) -> bool:
+    if solver_name not in ("direct", "lsqr"):
+        raise ValueError("solver must be 'direct' or 'lsqr'")
+    return solver_name == "lsqr"
 
 
 def embed(c: np.ndarray, S1: int, S2: int) -> np.ndarray:
@@ -58,13 +91,19 @@ class SweepResult:
 
 
 def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.ndarray | None = None,
-                            R: float = 3.0, precision: int = HS_FP64, device: int = 0,
-                            checkpoint_dir: str | None = None, angles=None) -> SweepResult:
+                            R: float | None = None, precision: int = HS_FP64, device: int = 0,
+                            checkpoint_dir: str | None = None, angles=None, solver: str = "direct",
+                            lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200) -> SweepResult:
     """Run the sweep.
 
     plans:   list of FrequencyPlan with increasing k.
     data_fn: data_fn(plan, alphas, thetas) -> measured far field (M x P complex) at plan.k.
     angles:  optional function plan -> (alphas, thetas); default equispaced 2 pi m / M, 2 pi p / P.
+    solver:  "direct" (normal equations with lambda_rel, hs_gn_step) or "lsqr" (the paper's
+             LSQR at lsqr_tol on the plan's modes, hs_gn_step_lsqr).
+    R:       receiver radius overriding the plans' own.
+    Each history entry records the build (factorisation) time t_f and the
+    least-squares time t_l of every step in seconds, and the LSQR iterations.
     """
     if angles is None:
         angles = lambda p: (2 * np.pi * np.arange(p.M) / p.M, 2 * np.pi * np.arange(p.P) / p.P)
@@ -83,19 +122,35 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
     for j in range(start, len(plans)):
         p = plans[j]
         c = embed(c, p.S, p.S)
-        key = (p.leaves_per_side, p.S)
+        radius = p.R if R is None else R
+        key = (p.leaves_per_side, p.S, radius)
         if key not in solvers:
+            for old in solvers.values():
+                old.close()
             solvers.clear()  # one tree at a time keeps device memory bounded
-            solvers[key] = Solver(p.leaves_per_side, p.S, p.S, R, precision, device)
+            solvers[key] = Solver(p.leaves_per_side, p.S, p.S, radius, precision, device)
         solver = solvers[key]
         al, th = angles(p)
         data = data_fn(p, al, th)
-        res = []
+        res, t_f, t_l, its = [], [], [], []
         for _ in range(p.newton):
+            t0 = time.perf_counter()
             solver.build(c, p.k)
-            c, rn = solver.gn_step(data, al, th, lambda_rel, c)
+            t1 = time.perf_counter()
+            if solver_kind_lsqr(solver_name=solver):
+                c, rn, it = solver.gn_step_lsqr(data, al, th, c, mask=p.mask(), tol=lsqr_tol, max_iter=lsqr_max_iter)
+                its.append(it)
+            else:
+                c, rn = solver.gn_step(data, al, th, lambda_rel, c)
+            t2 = time.perf_counter()
             res.append(rn)
-        history.append({"k": p.k, "leaves": p.leaves_per_side, "S": p.S, "M": p.M, "P": p.P, "residuals": res})
+            t_f.append(t1 - t0)
+            t_l.append(t2 - t1)
+        modes = int(p.mask().sum()) if p.triangle > 0 else p.S * p.S
+        history.append({"k": p.k if p.k_label is None else p.k_label, "k_solver": p.k,
+                        "leaves": p.leaves_per_side, "N": (15 * p.leaves_per_side + 1) ** 2, "S": p.S,
+                        "modes": modes, "M": p.M, "P": p.P, "residuals": res, "t_f": t_f, "t_l": t_l,
+                        "lsqr_iterations": its})
         if checkpoint_dir:
             np.save(os.path.join(checkpoint_dir, "c.npy"), c)
             json.dump({"next": j + 1, "history": history}, open(os.path.join(checkpoint_dir, "sweep.json"), "w"))

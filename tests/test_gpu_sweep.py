@@ -86,3 +86,23 @@ def test_autograd_misfit_gradient_k20(hs):
     fd = np.array(fd)
     assert np.abs(fd - g.flat[idx]).max() < 1e-5 * np.abs(g).max()
     solver.close()
+
+
+def test_paper_plan_lsqr_sweep_matches_oracle(hs):
+    """The paper's plan (Sec. 4) at k = 1, 1.25, 1.5 (4 x 4 leaves, triangular modes, R = 20 on
+    [-pi/2, pi/2]^2 read on [-1, 1]^2) with LSQR at tolerance 1e-3, against the oracle's sweep."""
+    from paper_1608_06871_gb300 import sweep as SW
+    plans = [SW.plan_paper(k) for k in (1.0, 1.25, 1.5)]
+    qt = synth.gaussian_bumps(9)
+    cache = {}
+
+    def data_fn(p, al, th):
+        if p.k not in cache:
+            cache[p.k] = F.forward_from_function(qt, p.k, p.leaves_per_side, p.R).solve_plane(al, th)[0]
+        return cache[p.k]
+    res = SW.recursive_linearization(plans, data_fn, solver="lsqr")
+    c_ref, hist = OS.sweep(plans, data_fn, 0.0, solver="lsqr")
+    assert [h["modes"] for h in res.history] == [1, 1, 3]
+    assert rel(res.c, c_ref) < 1e-8
+    for h_gpu, h_ref in zip(res.history, hist):
+        assert np.allclose(h_gpu["residuals"], h_ref, rtol=1e-8)

@@ -156,13 +156,17 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
  * the host.  Stops when the relative residual or the relative normal-equations
  * residual (LSQR's own estimates) is at most tol, or after max_iter
  * iterations; *iters_out (optional) receives the count.  products: HS_FP64
- * (both grid contractions of every iteration in FP64) or HS_MIXED (in complex
- * FP32 on the tensor cores, 3xTF32; the forward and adjoint fields, the
- * residual and the sine syntheses and projections stay FP64 -- for loose
- * tolerances such as the paper's 1e-3, where the FP32 rounding of J v and
- * J^H u is far below the stopping threshold).  Otherwise as hs_gn_step
- * (c_inout updated, resid_norm_out = ||r||_2 before the step).  Needs an
- * HS_FP64 context.  Errors: HS_EINVAL (damp < 0, tol < 0, max_iter < 1, bad
+ * (every iteration applies J and J^H from the fields: two FP64 grid
+ * contractions) or HS_MIXED (J is formed once in complex FP32 on the tensor
+ * cores, 3xTF32, from the FP64 fields; every iteration then reads it twice,
+ * accumulating in FP64, so that J v and J^H u stay exact transposes of that
+ * one matrix -- for loose tolerances such as the paper's 1e-3).  Otherwise as hs_gn_step
+ * (c_inout updated, resid_norm_out = ||r||_2 before the step).  On an
+ * HS_MIXED context the residual and the forward fields come from the refined
+ * solve (FP64 accurate) and the adjoint fields from one transposed sweep of
+ * the FP32 factors (FP32 accurate, not refined), so J carries the FP32 solve's
+ * error -- a step for loose tolerances, stated against the FP64 one by the
+ * tests and the benchmark.  Errors: HS_EINVAL (damp < 0, tol < 0, max_iter < 1, bad
  * products, bad sizes, NULL), HS_ENOTBUILT, HS_ENOMEM, HS_ECUDA, HS_ETIMEOUT. */
 int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M,
                     const double* thetas, int P, const unsigned char* mask, double damp,

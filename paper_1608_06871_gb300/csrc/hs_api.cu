@@ -181,6 +181,8 @@ struct hs_ctx {
   GraphSlot pgraph[2];  // mixed: captured refinement-pass bodies (first pass, corrections)
   double2* d_DS = nullptr;   // mixed: [D - I/2, -S] (N_b x 2 N_b), the exterior rows on [u; d_n u]
   float2* d_DS32 = nullptr;  // same, FP32
+  float2* d_Q32 = nullptr;   // mixed: FP32 leaf adjoint operator, made at the first adjoint after a build
+  bool q32_valid = false;
   // per-call workspace
   char* ws_base = nullptr;
   size_t ws_cap = 0;
@@ -694,6 +696,7 @@ int factor_mixed(hs_ctx* ctx, double k) {
   const bool graph = g_use_graphs && ctx->bie_k == k && !prof_active(2) && !prof_active(3);
   CKR(run_captured(ctx, s, ctx->fgraph, graph, nullptr, 0, 0, k, [&] { return enqueue_factor_mixed(ctx, k, s); }));
   ctx->Rroot32 = nullptr;
+  ctx->q32_valid = false;
   CKR(check_info(ctx));
   ctx->k = k;
   ctx->built = true;
@@ -1044,6 +1047,88 @@ size_t fields_and_adjoint_bytes(hs_ctx* ctx, int M, int P) {
          Arena::bytes((size_t)P * 2 * nb, 16) + 2 * Arena::bytes((size_t)nb * P, 16);
 }
 
+
+// Mixed precision: the FP32 leaf adjoint operator Q = 2 i eta A_ii^{-T} N_i^T K^{-T}
+// from the FP32 leaf factors the build keeps (A_ii^{-1}, N_i, K^{-1}); W goes
+// through the leaf scratch NiT, which the mixed path only uses inside the build.
+int ensure_q32(hs_ctx* ctx, cudaStream_t s) {
+  if (ctx->q32_valid) return HS_OK;
+  const int nl = ctx->nleaf;
+  if (!ctx->d_Q32) CKR(dalloc(ctx, &ctx->d_Q32, (size_t)nl * NI * NE));
+  auto& w = ctx->ws32;
+  gemm<float, float, float>(s, OP_T, OP_T, NI, NE, NI, 1.f, w.Ainv, NI, (long long)NI * NI, w.Ni, NI,
+                            (long long)NE * NI, 0.f, w.NiT, NE, (long long)NI * NE, nl);
+  gemm<float, float2, float2>(s, OP_N, OP_T, NI, NE, NE, make_float2(0.f, (float)(2.0 * ctx->k)), w.NiT, NE,
+                              (long long)NI * NE, w.Kinv, NE, (long long)NE * NE, make_float2(0.f, 0.f), ctx->d_Q32,
+                              NE, (long long)NI * NE, nl);
+  ctx->q32_valid = true;
+  return HS_OK;
+}
+
+size_t mixed_fields_bytes(hs_ctx* ctx, int M, int P) {
+  const int nb = ctx->B.nb;
+  const size_t nbP = (size_t)nb * P;
+  return Arena::bytes((size_t)ctx->nleaf * NL * M, 16) + Arena::bytes((size_t)P * 2 * nb, 16) +
+         2 * Arena::bytes(nbP, 16) + 5 * Arena::bytes(nbP, 8) + 2 * Arena::bytes(field_buf_elems(ctx, P), 8) +
+         Arena::bytes(t3_elems(ctx, P), 8) + Arena::bytes((size_t)ctx->nleaf * NI * P, 8) +
+         Arena::bytes((size_t)ctx->nleaf * NI * P, 16) + mixed_bytes(ctx, M, P);
+}
+
+// Mixed precision: far field F (refined, FP64 accurate), forward fields Ug from
+// the refined FP64 iterate, and adjoint fields Zg from one FP32 transposed
+// sweep of the FP32 factors (not refined: FP32 accuracy), on the interior grid.
+int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P,
+                             double2* F, double2* Ug, double2* Zg, Arena& a) {
+  const int nb = ctx->B.nb;
+  const size_t nbP = (size_t)nb * P;
+  double2* X = a.get<double2>((size_t)ctx->nleaf * NL * M);
+  double2* A2 = a.get<double2>((size_t)P * 2 * nb);
+  double2 *E = a.get<double2>(nbP), *CP = a.get<double2>(nbP);
+  float2 *E32 = a.get<float2>(nbP), *CP32 = a.get<float2>(nbP), *Gr = a.get<float2>(nbP), *G = a.get<float2>(nbP),
+         *CPs = a.get<float2>(nbP);
+  float2 *bufA = a.get<float2>(field_buf_elems(ctx, P)), *bufB = a.get<float2>(field_buf_elems(ctx, P));
+  float2* MU = a.get<float2>(t3_elems(ctx, P));
+  float2* Z32 = a.get<float2>((size_t)ctx->nleaf * NI * P);
+  double2* Z64 = a.get<double2>((size_t)ctx->nleaf * NI * P);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  {
+    Arena sub = a;
+    CKR(mixed_solve(ctx, s, alphas, M, thetas, P, F, X, sub));
+  }
+  leaf_to_grid(s, X, NL, ctx->nL, M, Ug);
+  CKR(ensure_q32(ctx, s));
+  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  Phase ph("hs_adjoint_sweep32");
+  farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
+  adjoint_root_init(s, nb, P, ctx->k, A2, E, CP);
+  convert_d2f(s, E, E32, (long long)nbP);
+  convert_d2f(s, CP, CP32, (long long)nbP);
+  // CP += R_root^T E with R_root in boundary-node order = Pi R_c Pi^T (R_c in root box order)
+  permute_rows<float2>(s, E32, ctx->d_bie_of_root, nb, P, Gr);
+  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->ops32.back().R, nb, 0, Gr, P, 0, zero, G, P, 0, 1);
+  permute_rows<float2>(s, G, ctx->d_root_of_bie, nb, P, Gr);
+  // CPs = C^{-T} (CP + G): C^{-1} is kept explicitly in d_Rb32 by the mixed build
+  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_Rb32, nb, 0, CP32, P, 0, zero, CPs, P, 0, 1);
+  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_Rb32, nb, 0, Gr, P, 0, one, CPs, P, 0, 1);
+  // E += B2^T CPs, then to root box order
+  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_B2_32, nb, 0, CPs, P, 0, one, E32, P, 0, 1);
+  permute_rows<float2>(s, E32, ctx->d_bie_of_root, nb, P, bufB);
+  const float2* Lp = bufB;
+  float2* out = bufA;
+  for (int li = (int)ctx->levels.size() - 1; li >= 0; --li) {
+    sweep_adjoint_level<float2>(s, ctx->levels[li], ctx->ops32[li], Lp, MU, out, P, true);
+    Lp = out;
+    out = (out == bufA) ? bufB : bufA;
+  }
+  gemm<float2, float2, float2>(s, OP_N, OP_N, NI, P, NE, one, ctx->d_Q32, NE, (long long)NI * NE, Lp, P,
+                               (long long)NE * P, zero, Z32, P, (long long)NI * P, ctx->nleaf);
+  const long long nz = (long long)ctx->nleaf * NI * P;
+  CK(cudaMemsetAsync(Z64, 0, sizeof(double2) * nz, s));
+  convert_f2d_add(s, Z32, Z64, nz);
+  leaf_to_grid(s, Z64, NI, ctx->nL, P, Zg);
+  CK(cudaGetLastError());
+  return HS_OK;
+}
 
 int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* J,
                   Arena& a) {
@@ -1487,13 +1572,14 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
                     double* c_inout, double* resid_norm_out, int* iters_out) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
-  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
+  const bool mixed = ctx->cfg.precision == HS_MIXED;
   if (!data || !alphas || !thetas || !c_inout) return fail(ctx, HS_EINVAL, "NULL pointer");
   if (!(damp >= 0.0) || !std::isfinite(damp) || !(tol >= 0.0) || max_iter < 1)
     return fail(ctx, HS_EINVAL, "damp and tol must be >= 0 and max_iter >= 1");
   if (products != HS_FP64 && products != HS_MIXED) return fail(ctx, HS_EINVAL, "products must be HS_FP64 or HS_MIXED");
   const bool p32 = products == HS_MIXED;
+  const int C32 = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget / 2);
   cudaStream_t s = ctx->stream;
   const int MP = M * P, nm = ctx->S1 * ctx->S2, nX = ctx->n14, S1 = ctx->S1, S2 = ctx->S2;
   const size_t N = (size_t)nX * nX;
@@ -1505,10 +1591,15 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
                      Arena::bytes((size_t)P * 2 * nb, 16);
   const size_t prod = Arena::bytes(nm, 8) * 2 + Arena::bytes((size_t)S2 * nX, 8) + Arena::bytes(N, 8) * 2 +
                       Arena::bytes(N * M, 16) + Arena::bytes(MP, 16) * 2 + Arena::bytes((size_t)S1 * nX, 8) +
-                      (p32 ? 2 * Arena::bytes(N * P, 8) + Arena::bytes(N * M, 8) + 2 * Arena::bytes(MP, 8) : 0);
+                      (p32 ? Arena::bytes((size_t)MP * nm, 8) + Arena::bytes((size_t)nX * S1, 8) +
+                                 Arena::bytes((size_t)nX * S2, 4) + Arena::bytes(N * C32, 8) +
+                                 Arena::bytes((size_t)nX * S1 * C32, 8) +
+                                 Arena::bytes((size_t)gemvT_parts(MP) * nm, 8)
+                           : 0);
   const size_t need = Arena::bytes(M, 8) + Arena::bytes(P, 8) + Arena::bytes((size_t)2 * MP, 8) +
                       Arena::bytes(8, 8) + Arena::bytes(MP, 16) * 2 + Arena::bytes(N * M, 16) +
-                      Arena::bytes(N * P, 16) + std::max({far, fields_and_adjoint_bytes(ctx, M, P), prod});
+                      Arena::bytes(N * P, 16) +
+                      std::max({far, mixed ? mixed_fields_bytes(ctx, M, P) : fields_and_adjoint_bytes(ctx, M, P), prod});
   Arena a;
   CKR(ensure_ws(ctx, need, a));
   double* da = a.get<double>(M);
@@ -1524,7 +1615,10 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
-  {  // forward far field F(c) and r = data - F
+  if (mixed) {  // refined far field and forward fields, FP32 adjoint fields
+    Arena sub = a;
+    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub));
+  } else {  // forward far field F(c)
     Arena sub = a;
     double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);
     double2 *f = sub.get<double2>((size_t)nb * M), *g = sub.get<double2>((size_t)nb * M);
@@ -1537,8 +1631,8 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
     gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
                                     make_double2(0, 0), F, P, 0, 1);
   }
-  residual(s, ddata, F, MP, res, nullptr, nrm2);
-  {
+  residual(s, ddata, F, MP, res, nullptr, nrm2);  // r = data - F
+  if (!mixed) {
     Arena sub = a;
     CKR(fields_and_adjoint(ctx, s, da, M, dt, P, Ug, Zg, sub));
   }
@@ -1552,16 +1646,22 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   double2* dy = a.get<double2>(MP);
   double2* fc = a.get<double2>(MP);
   double* T1 = a.get<double>((size_t)S1 * nX);
-  float2 *Zg32 = nullptr, *ZgT32 = nullptr, *Y32 = nullptr, *y32 = nullptr, *fc32 = nullptr;
+  float2 *J32 = nullptr, *sxc = nullptr, *W32 = nullptr, *T32 = nullptr;
+  float* sy32 = nullptr;
+  double* partT = nullptr;
   if (p32) {
-    Zg32 = a.get<float2>(N * P);
-    ZgT32 = a.get<float2>(N * P);
-    Y32 = a.get<float2>(N * M);
-    y32 = a.get<float2>(MP);
-    fc32 = a.get<float2>(MP);
+    J32 = a.get<float2>((size_t)MP * nm);
+    sxc = a.get<float2>((size_t)nX * S1);
+    sy32 = a.get<float>((size_t)nX * S2);
+    W32 = a.get<float2>(N * C32);
+    T32 = a.get<float2>((size_t)nX * S1 * C32);
+    partT = a.get<double>((size_t)gemvT_parts(MP) * nm);
   }
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
-  if (p32) fields32(s, Zg, P, (long long)N, Zg32, ZgT32);
+  if (p32) {
+    Phase phj("hs_jacobian32");
+    contract_jacobian32(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, J32, sxc, sy32, W32, T32, C32);
+  }
   std::vector<unsigned char> keep(nm, 1);
   if (mask)
     for (int i = 0; i < nm; ++i) keep[i] = mask[i] ? 1 : 0;
@@ -1570,7 +1670,7 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   auto matvec = [&](const std::vector<double>& v, std::vector<double>& out) {  // out (2 MP) = A v
     CK(cudaMemcpyAsync(dv, v.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, s));
     if (p32)
-      apply_J32(s, Ug, ZgT32, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dv, G1, qv, Y32, y32, dy);
+      gemv32(s, J32, MP, nm, dv, dy);
     else
       apply_J(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dv, G1, qv, Y, dy);
     CK(cudaMemcpyAsync(hy.data(), dy, sizeof(double2) * MP, cudaMemcpyDeviceToHost, s));
@@ -1585,7 +1685,7 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
     for (int i = 0; i < MP; ++i) hy[i] = make_double2(u[i], u[MP + i]);
     CK(cudaMemcpyAsync(dy, hy.data(), sizeof(double2) * MP, cudaMemcpyHostToDevice, s));
     if (p32)
-      apply_JH32(s, Ug, Zg32, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dy, fc32, Y32, h, T1, dg);
+      gemvT32(s, J32, MP, nm, dy, partT, dg);
     else
       apply_JH(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dy, fc, Y, h, T1, dg);
     CK(cudaMemcpyAsync(out.data(), dg, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));

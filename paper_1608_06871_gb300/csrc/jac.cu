@@ -165,102 +165,112 @@ void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P
   gemm<double, double, double>(s, OP_N, OP_T, S1, S2, nX, k2, T1, nX, 0, sy, nX, 0, 0.0, g, S2, 0, 1);
 }
 
-// The same products with the grid contractions in complex FP32 on the tensor
-// cores (3xTF32), for iterations that stop at a loose tolerance: Zg32 = Zg and
-// ZgT32 = Zg^T in FP32 (made once by fields32), the small sine syntheses and
-// projections and the reduction over d in FP64.
-__global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
-}
-
-// out[x][p] = Z[p][x] (FP32), through 32 x 32 shared tiles
-__global__ void k_transpose32(const double2* __restrict__ Z, int P, long long N, float2* __restrict__ out) {
-  __shared__ float2 t[32][33];
-  const long long x0 = (long long)blockIdx.x * 32;
-  const int p0 = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int p = p0 + i;
-    const long long x = x0 + threadIdx.x;
-    if (p < P && x < N) {
-      const double2 v = Z[(long long)p * N + x];
-      t[i][threadIdx.x] = make_float2((float)v.x, (float)v.y);
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const long long x = x0 + i;
-    const int p = p0 + threadIdx.x;
-    if (p < P && x < N) out[x * P + p] = t[threadIdx.x][i];
-  }
-}
-
-__global__ void k_weight_fields32(const double2* __restrict__ Ug, const double* __restrict__ qv, double k2,
-                                  long long N, long long n, float2* __restrict__ Y) {
+// Explicit complex FP32 Jacobian on the tensor cores, for iterations that stop
+// at a loose tolerance: the contraction of the FP32 Khatri-Rao rows with the
+// complex-embedded x-sine table on the tensor cores (3xTF32; K = nX, short
+// enough for FP32 accumulation), then the batch of per-pair y-projections.
+// LSQR then applies J32 and J32^H by the two products below, which read J32
+// once each and accumulate in FP64, so that they stay exact transposes of one
+// operator (products computed from the fields with independent FP32 rounding
+// are not, and the bidiagonalisation amplifies that mismatch).
+__global__ void k_khatri_rao32(const double2* __restrict__ Ug, const double2* __restrict__ Zg, int P,
+                               long long plane, long long c0, long long n, float2* __restrict__ W) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const double w = k2 * qv[e % N];
-  const double2 u = Ug[e];
-  Y[e] = make_float2((float)(w * u.x), (float)(w * u.y));
+  const long long c = c0 + e / plane, g = e % plane;
+  const long long d = c / P, p = c % P;
+  const double2 u = Ug[d * plane + g], z = Zg[p * plane + g];
+  W[e] = make_float2((float)(u.x * z.x - u.y * z.y), (float)(u.x * z.y + u.y * z.x));
 }
 
-__global__ void k_conj_to_f32(const double2* __restrict__ f, int n, float2* __restrict__ out) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) out[e] = make_float2((float)f[e].x, (float)-f[e].y);
+// out[g][m] = (sx[m][g], 0), and sy as FP32
+__global__ void k_sine_tables32(const double* __restrict__ sx, const double* __restrict__ sy, int n, int S1, int S2,
+                                float2* __restrict__ sxc, float* __restrict__ sy32) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)n * S1) sxc[e] = make_float2((float)sx[(e % S1) * n + e / S1], 0.f);
+  if (e < (long long)n * S2) sy32[e] = (float)sy[e];
 }
 
-__global__ void k_f32_to_f64(const float2* __restrict__ a, int n, double2* __restrict__ b) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) b[e] = make_double2((double)a[e].x, (double)a[e].y);
-}
-
-__global__ void k_gradient_combine32(const double2* __restrict__ Ug, const float2* __restrict__ Zmix, int M,
-                                     long long npts, double* __restrict__ hre) {
-  long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= npts) return;
-  double v = 0.0;
-  for (int d = 0; d < M; ++d) {
-    const double2 a = Ug[d * npts + x];
-    const float2 b = Zmix[d * npts + x];
-    v += a.x * (double)b.x - a.y * (double)b.y;
+void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
+                         const double* sy, int S1, int S2, double k2, float2* J, float2* sxc, float* sy32, float2* W,
+                         float2* T, int C) {
+  const long long plane = (long long)nX * nX, MP = (long long)M * P;
+  const long long nt = (long long)nX * std::max(S1, S2);
+  k_sine_tables32<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(sx, sy, nX, S1, S2, sxc, sy32);
+  HS_COUNT_LAUNCH();
+  for (long long c0 = 0; c0 < MP; c0 += C) {
+    const int nc = (int)std::min<long long>(C, MP - c0);
+    const long long n = nc * plane;
+    k_khatri_rao32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ug, Zg, P, plane, c0, n, W);
+    HS_COUNT_LAUNCH();
+    gemm<float2, float2, float2>(s, OP_N, OP_N, nc * nX, S1, nX, make_float2(1.f, 0.f), W, nX, 0, sxc, S1, 0,
+                                 make_float2(0.f, 0.f), T, S1, 0, 1);
+    gemm<float2, float, float2>(s, OP_T, OP_T, S1, S2, nX, make_float2((float)k2, 0.f), T, S1, (long long)nX * S1,
+                                sy32, nX, 0, make_float2(0.f, 0.f), J + c0 * S1 * S2, S2, (long long)S1 * S2, nc);
   }
-  hre[x] = v;
 }
 
-void fields32(cudaStream_t s, const double2* Zg, int P, long long N, float2* Zg32, float2* ZgT32) {
-  k_to_f32<<<(unsigned)((N * P + 255) / 256), 256, 0, s>>>(Zg, Zg32, N * P);
-  HS_COUNT_LAUNCH();
-  dim3 tb(32, 8), grid((unsigned)((N + 31) / 32), (P + 31) / 32);
-  k_transpose32<<<grid, tb, 0, s>>>(Zg, P, N, ZgT32);
+// y[r] = sum_m J[r][m] v[m]  (complex J in FP32, real v, FP64 sums; one warp per row)
+__global__ void k_gemv32(const float2* __restrict__ J, const double* __restrict__ v, long long rows, int n,
+                         double2* __restrict__ y) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const float2* row = J + r * n;
+  double ax = 0.0, ay = 0.0;
+  for (int m = lane; m < n; m += 32) {
+    const float2 a = row[m];
+    const double w = v[m];
+    ax = fma((double)a.x, w, ax);
+    ay = fma((double)a.y, w, ay);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_down_sync(0xffffffffu, ax, o);
+    ay += __shfl_down_sync(0xffffffffu, ay, o);
+  }
+  if (lane == 0) y[r] = make_double2(ax, ay);
+}
+
+// part[b][m] = sum over rows r of block b of Re(conj(J[r][m]) u[r])  (FP64 sums)
+constexpr int kRowsPerPart = 256;
+__global__ void k_gemvT32(const float2* __restrict__ J, const double2* __restrict__ u, long long rows, int n,
+                          double* __restrict__ part) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r0 = (long long)blockIdx.y * kRowsPerPart;
+  if (m >= n) return;
+  const long long r1 = min(rows, r0 + kRowsPerPart);
+  double acc = 0.0;
+  for (long long r = r0; r < r1; ++r) {
+    const float2 a = J[r * n + m];
+    const double2 b = u[r];
+    acc = fma((double)a.x, b.x, acc);
+    acc = fma((double)a.y, b.y, acc);
+  }
+  part[(long long)blockIdx.y * n + m] = acc;
+}
+
+__global__ void k_sum_rows(const double* __restrict__ part, int nparts, int n, double* __restrict__ g) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double acc = 0.0;
+  for (int b = 0; b < nparts; ++b) acc += part[(long long)b * n + m];
+  g[m] = acc;
+}
+
+int gemvT_parts(long long rows) { return (int)((rows + kRowsPerPart - 1) / kRowsPerPart); }
+
+void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double* v, double2* y) {
+  const long long threads = rows * 32;
+  k_gemv32<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(J, v, rows, n, y);
   HS_COUNT_LAUNCH();
 }
 
-void apply_J32(cudaStream_t s, const double2* Ug, const float2* ZgT32, int M, int P, int nX, const double* sx,
-               const double* sy, int S1, int S2, double k2, const double* v, double* G1, double* qv, float2* Y,
-               float2* y32, double2* y) {
-  const long long N = (long long)nX * nX;
-  gemm<double, double, double>(s, OP_T, OP_N, S2, nX, S1, 1.0, v, S2, 0, sx, nX, 0, 0.0, G1, nX, 0, 1);
-  gemm<double, double, double>(s, OP_T, OP_N, nX, nX, S2, 1.0, sy, nX, 0, G1, nX, 0, 0.0, qv, nX, 0, 1);
-  k_weight_fields32<<<(unsigned)((N * M + 255) / 256), 256, 0, s>>>(Ug, qv, k2, N, N * M, Y);
+void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g) {
+  const int np = gemvT_parts(rows);
+  k_gemvT32<<<dim3((n + 127) / 128, np), 128, 0, s>>>(J, u, rows, n, part);
   HS_COUNT_LAUNCH();
-  gemm<float2, float2, float2>(s, OP_N, OP_N, M, P, (int)N, make_float2(1.f, 0.f), Y, (int)N, 0, ZgT32, P, 0,
-                               make_float2(0.f, 0.f), y32, P, 0, 1);
-  k_f32_to_f64<<<(M * P + 255) / 256, 256, 0, s>>>(y32, M * P, y);
+  k_sum_rows<<<(n + 255) / 256, 256, 0, s>>>(part, np, n, g);
   HS_COUNT_LAUNCH();
-}
-
-void apply_JH32(cudaStream_t s, const double2* Ug, const float2* Zg32, int M, int P, int nX, const double* sx,
-                const double* sy, int S1, int S2, double k2, const double2* f, float2* fc, float2* Zmix, double* h,
-                double* T1, double* g) {
-  const long long N = (long long)nX * nX;
-  k_conj_to_f32<<<(M * P + 255) / 256, 256, 0, s>>>(f, M * P, fc);
-  HS_COUNT_LAUNCH();
-  gemm<float2, float2, float2>(s, OP_N, OP_N, M, (int)N, P, make_float2(1.f, 0.f), fc, P, 0, Zg32, (int)N, 0,
-                               make_float2(0.f, 0.f), Zmix, (int)N, 0, 1);
-  k_gradient_combine32<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Ug, Zmix, M, N, h);
-  HS_COUNT_LAUNCH();
-  gemm<double, double, double>(s, OP_N, OP_T, S1, nX, nX, 1.0, sx, nX, 0, h, nX, 0, 0.0, T1, nX, 0, 1);
-  gemm<double, double, double>(s, OP_N, OP_T, S1, S2, nX, k2, T1, nX, 0, sy, nX, 0, 0.0, g, S2, 0, 1);
 }
 
 // Jst = [Re J; Im J] (2 rows x cols, real).

@@ -269,7 +269,7 @@ void sweep_down_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, 
 
 template <typename C>
 void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lp, C* MU, C* Lc,
-                         int nrhs) {
+                         int nrhs, bool w_explicit) {
   const int ni = L.ni, np = L.np, nb = L.nbox;
   const long long nn = (long long)ni * ni, mu = 2LL * ni * nrhs;
   const C one = el<C>::one(), mone = -el<C>::one(), zero = el<C>::zero();
@@ -282,8 +282,16 @@ void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& 
   // lambda_ta = mu_a - A33^T lambda_tb
   gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, ni, mone, O.A33, ni, nn, MU + (long long)ni * nrhs, nrhs, mu, one, MU, nrhs,
                 mu, nb);
-  // Wt = M^{-T} lambda_ta
-  lu_solve<C>(s, OP_T, O.M, ni, nn, ni, O.Mpiv, ni, MU, nrhs, mu, nrhs, nb);
+  // Wt = M^{-T} lambda_ta  (M = I - B33 A33 factored, or W = M^{-1} kept explicitly)
+  if (w_explicit) {
+    // Lc (written only by the final scatter) holds the product meanwhile
+    const long long tw = (long long)ni * nrhs;
+    gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, ni, one, O.M, ni, nn, MU, nrhs, mu, zero, Lc, nrhs, tw, nb);
+    cudaMemcpy2DAsync(MU, (size_t)mu * sizeof(C), Lc, (size_t)tw * sizeof(C), (size_t)tw * sizeof(C), nb,
+                      cudaMemcpyDeviceToDevice, s);
+  } else {
+    lu_solve<C>(s, OP_T, O.M, ni, nn, ni, O.Mpiv, ni, MU, nrhs, mu, nrhs, nb);
+  }
   // la3 = B33^T Wt - lambda_tb
   gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, ni, one, O.B33, ni, nn, MU, nrhs, mu, mone, MU + (long long)ni * nrhs, nrhs,
                 mu, nb);
@@ -357,7 +365,7 @@ template <typename C> void permute_square(cudaStream_t s, const C* src, const in
 #define HS_INST(C)                                                                                                     \
   template void merge_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, int*);                  \
   template void sweep_down_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool); \
-  template void sweep_adjoint_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int);    \
+  template void sweep_adjoint_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool); \
   template void sweep_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, C*, int);       \
   template void permute_rows<C>(cudaStream_t, const C*, const int*, int, int, C*);                                  \
   template void permute_square<C>(cudaStream_t, const C*, const int*, int, C*);

@@ -64,7 +64,7 @@ void sweep_down_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, 
                       bool t3_loaded);
 template <typename C>
 void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lp, C* MU, C* Lc,
-                         int nrhs);
+                         int nrhs, bool w_explicit = false);
 // Upward (particular) pass of one level: children's outgoing particular
 // impedances Hc and the interface residual terms S3 ([s_a; s_b] per box) give
 // the particular interface impedances TT = [t_a; t_b] (kept for the downward
@@ -123,14 +123,15 @@ void apply_J(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P,
 void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
               const double* sy, int S1, int S2, double k2, const double2* f, double2* fc, double2* Zmix, double* h,
               double* T1, double* g);
-// Same products with the grid contractions in complex FP32 on the tensor cores.
-void fields32(cudaStream_t s, const double2* Zg, int P, long long N, float2* Zg32, float2* ZgT32);
-void apply_J32(cudaStream_t s, const double2* Ug, const float2* ZgT32, int M, int P, int nX, const double* sx,
-               const double* sy, int S1, int S2, double k2, const double* v, double* G1, double* qv, float2* Y,
-               float2* y32, double2* y);
-void apply_JH32(cudaStream_t s, const double2* Ug, const float2* Zg32, int M, int P, int nX, const double* sx,
-                const double* sy, int S1, int S2, double k2, const double2* f, float2* fc, float2* Zmix, double* h,
-                double* T1, double* g);
+// Explicit complex FP32 Jacobian on the tensor cores (W: C nX^2, T: C nX S1 values;
+// sxc: nX S1, sy32: nX S2), and its products with FP64 sums: y = J v (rows complex
+// outputs, real v) and g = Re(J^H u) (part: gemvT_parts(rows) * n doubles).
+void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
+                         const double* sy, int S1, int S2, double k2, float2* J, float2* sxc, float* sy32, float2* W,
+                         float2* T, int C);
+int gemvT_parts(long long rows);
+void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double* v, double2* y);
+void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g);
 // A = Jst^T Jst (n x n) by block rows of its lower part, mirrored.
 void normal_matrix(cudaStream_t s, const double* Jst, int rows, int n, double* A);
 void residual(cudaStream_t s, const double* data, const double2* F, int n, double2* res, double* rst, double* out2);

@@ -93,18 +93,21 @@ class SweepResult:
 def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.ndarray | None = None,
                             R: float | None = None, precision: int = HS_FP64, device: int = 0,
                             checkpoint_dir: str | None = None, angles=None, solver: str = "direct",
-                            lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200) -> SweepResult:
+                            lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200,
+                            lsqr_products: int = HS_FP64) -> SweepResult:
     """Run the sweep.
 
     plans:   list of FrequencyPlan with increasing k.
     data_fn: data_fn(plan, alphas, thetas) -> measured far field (M x P complex) at plan.k.
     angles:  optional function plan -> (alphas, thetas); default equispaced 2 pi m / M, 2 pi p / P.
     solver:  "direct" (normal equations with lambda_rel, hs_gn_step) or "lsqr" (the paper's
-             LSQR at lsqr_tol on the plan's modes, hs_gn_step_lsqr).
+             LSQR at lsqr_tol on the plan's modes, hs_gn_step_lsqr, products in lsqr_products).
+    precision: HS_FP64, or HS_MIXED (mixed-precision factors; needs solver="lsqr").
     R:       receiver radius overriding the plans' own.
     Each history entry records the build (factorisation) time t_f and the
     least-squares time t_l of every step in seconds, and the LSQR iterations.
     """
+    use_lsqr = solver_kind_lsqr(solver)
     if angles is None:
         angles = lambda p: (2 * np.pi * np.arange(p.M) / p.M, 2 * np.pi * np.arange(p.P) / p.P)
     c = np.zeros((plans[0].S, plans[0].S)) if c0 is None else np.asarray(c0, dtype=np.float64)
@@ -129,19 +132,20 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
                 old.close()
             solvers.clear()  # one tree at a time keeps device memory bounded
             solvers[key] = Solver(p.leaves_per_side, p.S, p.S, radius, precision, device)
-        solver = solvers[key]
+        slv = solvers[key]
         al, th = angles(p)
         data = data_fn(p, al, th)
         res, t_f, t_l, its = [], [], [], []
         for _ in range(p.newton):
             t0 = time.perf_counter()
-            solver.build(c, p.k)
+            slv.build(c, p.k)
             t1 = time.perf_counter()
-            if solver_kind_lsqr(solver_name=solver):
-                c, rn, it = solver.gn_step_lsqr(data, al, th, c, mask=p.mask(), tol=lsqr_tol, max_iter=lsqr_max_iter)
+            if use_lsqr:
+                c, rn, it = slv.gn_step_lsqr(data, al, th, c, mask=p.mask(), tol=lsqr_tol, max_iter=lsqr_max_iter,
+                                             products=lsqr_products)
                 its.append(it)
             else:
-                c, rn = solver.gn_step(data, al, th, lambda_rel, c)
+                c, rn = slv.gn_step(data, al, th, lambda_rel, c)
             t2 = time.perf_counter()
             res.append(rn)
             t_f.append(t1 - t0)

@@ -120,11 +120,7 @@ def test_k40_matches_lsqr_on_explicit_jacobian(hs):
     assert rel(dc, ref) < 1e-5
 
 
-def test_tensor_core_products_k40(hs):
-    """k = 40 top-of-sweep size at the paper's tolerance (1e-3): the grid contractions of every
-    LSQR iteration in complex FP32 on the tensor cores against the FP64 products.  Their
-    relative rounding (about 1e-6) is far below the stopping threshold: same iteration count
-    within one, step within 1e-4."""
+def k40_setup(hs):
     w = synth.WORKLOADS["gn_k40"]
     phantom = synth.ellipse_phantom(7)
     al, th = synth.directions(w.M), synth.receivers(w.P)
@@ -134,10 +130,54 @@ def test_tensor_core_products_k40(hs):
     gen.close()
     c = np.zeros((w.S, w.S))
     c[:40, :40] = synth.project_sine(phantom, 40, 40)
+    return w, al, th, data, c
+
+
+def k5_setup(hs):
+    w = synth.WORKLOADS["gn_k5"]
+    qt = synth.gaussian_bumps(1)
+    al, th = synth.directions(w.M), synth.receivers(w.P)
+    gen = hs.Solver(w.n_leaf_side, 2, 2, w.R)
+    x, y = gen.node_coords()
+    data = gen.build_nodes(qt(x, y), w.k).solve(al, th)
+    gen.close()
+    return w, al, th, data, 0.3 * synth.project_sine(qt, w.S, w.S)
+
+
+def test_tensor_core_jacobian_k40(hs):
+    """k = 40 top-of-sweep size: LSQR on the complex FP32 Jacobian formed on the tensor cores
+    (products with FP64 sums) against LSQR with the FP64 products from the fields.  With the
+    same 20 iterations the steps agree to 1e-4 (measured 9e-6: the FP32 Jacobian's error, not
+    amplified because both products apply the same matrix); at the paper's tolerance the
+    iteration counts agree within 3."""
+    w, al, th, data, c = k40_setup(hs)
     S = hs.Solver(w.n_leaf_side, w.S, w.S, w.R).build(c, w.k)
-    c64, r64, it64 = S.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=200)
-    c32, r32, it32 = S.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=200, products=hs.HS_MIXED)
+    c64, r64, _ = S.gn_step_lsqr(data, al, th, c, tol=0.0, max_iter=20)
+    c32, r32, _ = S.gn_step_lsqr(data, al, th, c, tol=0.0, max_iter=20, products=hs.HS_MIXED)
+    _, _, it64 = S.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=300)
+    _, _, it32 = S.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=300, products=hs.HS_MIXED)
     S.close()
-    assert r32 == r64 and it64 < 200
-    assert abs(it32 - it64) <= 1
+    assert abs(r32 - r64) <= 1e-13 * r64
     assert rel(c32 - c, c64 - c) < 1e-4
+    assert it64 < 300 and abs(it32 - it64) <= 3
+
+
+@pytest.mark.parametrize("case,iters", [("k5", 10), ("k40", 20)])
+def test_mixed_precision_step(hs, case, iters):
+    """LSQR Gauss-Newton step on a mixed-precision context (FP32 factors: refined forward
+    fields and residual, FP32 adjoint fields, tensor-core FP32 Jacobian) against the FP64
+    context with FP64 products, same iteration count: bar 1e-3 (measured 1e-5 at k = 5,
+    6e-5 at k = 40, the FP32 adjoint fields' error); at the paper's tolerance the iteration
+    counts agree within 3."""
+    w, al, th, data, c = (k5_setup if case == "k5" else k40_setup)(hs)
+    S64 = hs.Solver(w.n_leaf_side, w.S, w.S, w.R).build(c, w.k)
+    S32 = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED).build(c, w.k)
+    c64, r64, _ = S64.gn_step_lsqr(data, al, th, c, tol=0.0, max_iter=iters)
+    c32, r32, _ = S32.gn_step_lsqr(data, al, th, c, tol=0.0, max_iter=iters, products=hs.HS_MIXED)
+    _, _, it64 = S64.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=300)
+    _, _, it32 = S32.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=300, products=hs.HS_MIXED)
+    S64.close()
+    S32.close()
+    assert abs(r32 - r64) <= 1e-8 * r64  # residual from the refined far field
+    assert rel(c32 - c, c64 - c) < 1e-3
+    assert abs(it32 - it64) <= 3

@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, choices=["gn_k40", "jacobian_16x16_s64", "lsqr_k40"],
+    ap.add_argument("--case", default=None, choices=["gn_k40", "jacobian_16x16_s64", "lsqr_k40", "lsqr_mixed_k40"],
                     help="run one named workload once, untimed, and exit (a target for profilers)")
     ap.add_argument("--table2", type=float, default=0.0,
                     help="also run the paper's reconstruction plan (Sec. 4: k = 1:0.25:K, LSQR at 1e-3, "
@@ -294,6 +294,7 @@ def run_hs(args, world, rank, local):
     secondary = gn_and_gradient_times(hs, torch, local) if not args.no_secondary else None
     if secondary is not None:
         secondary["sweep_ms"] = sweep_time(hs, torch, local, k_max=args.sweep_kmax)
+        secondary["sweep_mixed_lsqr_k40_ms"] = sweep_time(hs, torch, local, k_max=40.0, mixed_lsqr=True)
         if args.table2 > 0:
             secondary["paper_table2"] = paper_table2(hs, torch, local, args.table2)
         if args.paper_gn:
@@ -374,12 +375,14 @@ def tf32_peak():
         return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"
 
 
-def sweep_time(hs, torch, local, k_max=10.0):
+def sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=False):
     """Recursive-linearization sweep (Sec. 3.4): k = 1, 1.5, .., k_max with the
     ceil(1.6 k) modes / ceil(4 k) incidences and receivers / leaves-by-k plan,
-    one Gauss-Newton step per frequency (FP64), blurred-ellipse phantom (seed 7)
-    plus 1% complex Gaussian noise.  The data of every frequency are computed
-    first on the GPU (untimed); the timed region is the whole sweep."""
+    one Gauss-Newton step per frequency, blurred-ellipse phantom (seed 7) plus
+    1% complex Gaussian noise.  FP64 with the direct normal equations, or
+    (mixed_lsqr) on mixed-precision contexts with LSQR at 1e-3 on the
+    tensor-core Jacobian.  The data of every frequency are computed first on
+    the GPU (untimed); the timed region is the whole sweep."""
     from paper_1608_06871_gb300 import sweep as SW
     plans = [SW.plan_ceil(float(k)) for k in np.arange(1.0, k_max + 0.25, 0.5)]
     phantom = synth.ellipse_phantom(7)
@@ -387,20 +390,29 @@ def sweep_time(hs, torch, local, k_max=10.0):
     for p in plans:
         al = 2 * np.pi * np.arange(p.M) / p.M
         th = 2 * np.pi * np.arange(p.P) / p.P
-        gen = hs.Solver(p.leaves_per_side, 2, 2, 3.0, device=local)
+        gen = hs.Solver(p.leaves_per_side, 2, 2, 3.0, hs.HS_MIXED, device=local)
         x, y = gen.node_coords()
         gen.build_nodes(phantom(x, y), p.k)
         data[p.k] = synth.add_noise(gen.solve(al, th), 0.01, seed=70)
         gen.close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = SW.recursive_linearization(plans, lambda p, al, th: data[p.k], lambda_rel=1e-4, device=local)
+    if mixed_lsqr:
+        res = SW.recursive_linearization(plans, lambda p, al, th: data[p.k], device=local, precision=hs.HS_MIXED,
+                                         solver="lsqr", lsqr_products=hs.HS_MIXED)
+    else:
+        res = SW.recursive_linearization(plans, lambda p, al, th: data[p.k], lambda_rel=1e-4, device=local)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    S = res.c.shape[0]
+    c_true = synth.project_sine(phantom, S, S, nq=max(256, 4 * S))
+    how = ("mixed precision, LSQR at 1e-3 on the tensor-core Jacobian" if mixed_lsqr
+           else "FP64, direct normal equations (lambda_rel 1e-4)")
     return {"value": dt * 1e3, "unit": "ms", "frequencies": len(plans),
             "workload": f"sweep k=1:0.5:{k_max:g}, S=ceil(1.6k), M=P=ceil(4k), leaves 2^max(2,ceil(log2 0.8k)), "
-                        "ellipse phantom seed 7 + 1% noise, 1 GN step per k, FP64",
-            "final_residual": float(res.history[-1]["residuals"][-1])}
+                        f"ellipse phantom seed 7 + 1% noise, 1 GN step per k, {how}",
+            "final_residual": float(res.history[-1]["residuals"][-1]),
+            "coeff_rel_err_vs_phantom_projection": float(np.linalg.norm(res.c - c_true) / np.linalg.norm(c_true))}
 
 
 def gn_and_gradient_times(hs, torch, local, reps=3):
@@ -542,33 +554,44 @@ def paper_table2(hs, torch, local, k_max):
 def paper_scale_gn(hs, torch, local):
     """One Gauss-Newton step at the top frequency of the paper-scale reconstruction:
     k = 70, 128 x 128 leaves, 140 x 140 = 19,600 sine unknowns, 280 incidences x 280
-    receivers (J: 78,400 x 19,600 complex), FP64 (hs_build + hs_gn_step: forward,
-    adjoint sweep, Jacobian contraction, symmetric normal matrix, LU), one timed
-    run with CUDA events.  Data: the 40-inclusion contrast (seed 5, max|q| = 0.5)
-    plus 1% noise; the step starts from its first 120 x 120 coefficients."""
+    receivers (J: 78,400 x 19,600 complex).  Two ways, one timed run each (CUDA
+    events): the paper's LSQR at 1e-3 on a mixed-precision context with the
+    tensor-core Jacobian (hs_build + hs_gn_step_lsqr), and the FP64 direct step
+    (hs_build + hs_gn_step: Jacobian contraction, symmetric normal matrix, LU).
+    Data: the 40-inclusion contrast (seed 5, max|q| = 0.5) plus 1% noise; the
+    step starts from its first 120 x 120 coefficients."""
     stream = torch.cuda.current_stream()
     w = synth.WORKLOADS["fwd_k70"]
     c_true = synth.scaled_sine_coeffs(synth.inclusions(5), w.S, 0.5)
     al, th = synth.directions(w.M), synth.receivers(w.P)
-    s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, device=local, stream=stream.cuda_stream)
-    data = synth.add_noise(s.build(c_true, w.k).solve(al, th), 0.01, seed=70)
+    gen = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED, device=local, stream=stream.cuda_stream)
+    data = synth.add_noise(gen.build(c_true, w.k).solve(al, th), 0.01, seed=70)
+    gen.close()
     c = np.zeros_like(c_true)
     c[:120, :120] = c_true[:120, :120]
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    e0.record(stream)
-    s.build(c, w.k)
-    e1.record(stream)
-    c1, rn = s.gn_step(data, al, th, 1e-4, c)
-    e2.record(stream)
-    torch.cuda.synchronize()
-    s.close()
-    return {"value": e0.elapsed_time(e2), "unit": "ms", "build_ms": e0.elapsed_time(e1),
-            "gn_ms": e1.elapsed_time(e2), "workload": w.name, "precision": "fp64",
-            "unknowns": w.S * w.S, "jacobian_rows": w.M * w.P, "residual_norm": float(rn),
-            "rel_err_before": float(np.linalg.norm(c - c_true) / np.linalg.norm(c_true)),
-            "rel_err_after": float(np.linalg.norm(c1 - c_true) / np.linalg.norm(c_true)),
-            "paper_context": "Table 2, k = 64 (8,128 modes, M*P = 65,536): T_f 25.97 s + LSQR T_l 1412.77 s on "
-                             "up to 32 Xeon cores"}
+    out = {"workload": w.name, "unknowns": w.S * w.S, "jacobian_rows": w.M * w.P,
+           "rel_err_before": float(np.linalg.norm(c - c_true) / np.linalg.norm(c_true)),
+           "paper_context": "Table 2, k = 64 (8,128 modes, M*P = 65,536): T_f 25.97 s + LSQR T_l 1412.77 s on "
+                            "up to 32 Xeon cores"}
+    for name, prec in (("mixed_lsqr_tensor_core", hs.HS_MIXED), ("fp64_direct", hs.HS_FP64)):
+        s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, prec, device=local, stream=stream.cuda_stream)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        s.build(c, w.k)
+        e1.record(stream)
+        if prec == hs.HS_MIXED:
+            c1, rn, it = s.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=500, products=hs.HS_MIXED)
+        else:
+            (c1, rn), it = s.gn_step(data, al, th, 1e-4, c), None
+        e2.record(stream)
+        torch.cuda.synchronize()
+        s.close()
+        out[name] = {"ms": e0.elapsed_time(e2), "build_ms": e0.elapsed_time(e1), "step_ms": e1.elapsed_time(e2),
+                     "lsqr_iterations": it, "residual_norm": float(rn),
+                     "rel_err_after": float(np.linalg.norm(c1 - c_true) / np.linalg.norm(c_true))}
+    out["value"] = out["mixed_lsqr_tensor_core"]["ms"]
+    out["unit"] = "ms"
+    return out
 
 
 def gn_step_top(hs, torch, local):
@@ -659,13 +682,15 @@ def run_case(name):
     """Profiler targets: 'gn_k40' = data generation and two FP64 Gauss-Newton steps of the
     k = 40 top-of-sweep workload; 'jacobian_16x16_s64' = one Jacobian at k = 20 on 16 x 16
     leaves with 64 x 64 modes and 64 x 64 data; 'lsqr_k40' = data generation and one
-    LSQR Gauss-Newton step of the k = 40 workload (tolerance 1e-3)."""
+    LSQR Gauss-Newton step of the k = 40 workload (tolerance 1e-3, FP64 products);
+    'lsqr_mixed_k40' = the same on a mixed-precision context with the tensor-core
+    Jacobian, two steps."""
     import torch
 
     from paper_1608_06871_gb300.build import build
     build()
     import paper_1608_06871_gb300 as hs
-    if name in ("gn_k40", "lsqr_k40"):
+    if name in ("gn_k40", "lsqr_k40", "lsqr_mixed_k40"):
         w = synth.WORKLOADS["gn_k40"]
         ph = synth.ellipse_phantom(7)
         al, th = synth.directions(w.M), synth.receivers(w.P)
@@ -675,13 +700,15 @@ def run_case(name):
         g.close()
         c = np.zeros((w.S, w.S))
         c[:40, :40] = synth.project_sine(ph, 40, 40)
-        s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R)
-        for _ in range(2 if name == "gn_k40" else 1):
+        mixed = name == "lsqr_mixed_k40"
+        s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED if mixed else hs.HS_FP64)
+        for _ in range(1 if name == "lsqr_k40" else 2):
             s.build(c, w.k)
             if name == "gn_k40":
                 s.gn_step(data, al, th, 1e-4, c)
             else:
-                print("lsqr iterations", s.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=200)[2])
+                print("lsqr iterations", s.gn_step_lsqr(data, al, th, c, tol=1e-3, max_iter=200,
+                                                        products=hs.HS_MIXED if mixed else hs.HS_FP64)[2])
         torch.cuda.synchronize()
         print(name, "launches", s.launch_count())
         s.close()

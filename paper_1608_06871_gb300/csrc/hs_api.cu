@@ -1589,13 +1589,14 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   // the buffers of the two products
   const size_t far = 4 * Arena::bytes((size_t)nb * M, 16) + Arena::bytes((size_t)2 * nb * M, 16) +
                      Arena::bytes((size_t)P * 2 * nb, 16);
-  const size_t prod = Arena::bytes(nm, 8) * 2 + Arena::bytes((size_t)S2 * nX, 8) + Arena::bytes(N, 8) * 2 +
-                      Arena::bytes(N * M, 16) + Arena::bytes(MP, 16) * 2 + Arena::bytes((size_t)S1 * nX, 8) +
+  // the FP64 products' buffers (G1, qv, h, Y, fc, T1) or the FP32 Jacobian's
+  const size_t prod = Arena::bytes(nm, 8) * 2 + Arena::bytes(MP, 16) +
                       (p32 ? Arena::bytes((size_t)MP * nm, 8) + Arena::bytes((size_t)nX * S1, 8) +
                                  Arena::bytes((size_t)nX * S2, 4) + Arena::bytes(N * C32, 8) +
                                  Arena::bytes((size_t)nX * S1 * C32, 8) +
                                  Arena::bytes((size_t)gemvT_parts(MP) * nm, 8)
-                           : 0);
+                           : Arena::bytes((size_t)S2 * nX, 8) + Arena::bytes(N, 8) * 2 + Arena::bytes(N * M, 16) +
+                                 Arena::bytes(MP, 16) + Arena::bytes((size_t)S1 * nX, 8));
   const size_t need = Arena::bytes(M, 8) + Arena::bytes(P, 8) + Arena::bytes((size_t)2 * MP, 8) +
                       Arena::bytes(8, 8) + Arena::bytes(MP, 16) * 2 + Arena::bytes(N * M, 16) +
                       Arena::bytes(N * P, 16) +
@@ -1639,17 +1640,20 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   interior_sine_tables(s, ctx->d_xint, nX, S1, S2, ctx->d_sxi, ctx->d_syi);
   double* dv = a.get<double>(nm);
   double* dg = a.get<double>(nm);
-  double* G1 = a.get<double>((size_t)S2 * nX);
-  double* qv = a.get<double>(N);
-  double* h = a.get<double>(N);
-  double2* Y = a.get<double2>(N * M);
   double2* dy = a.get<double2>(MP);
-  double2* fc = a.get<double2>(MP);
-  double* T1 = a.get<double>((size_t)S1 * nX);
+  double *G1 = nullptr, *qv = nullptr, *h = nullptr, *T1 = nullptr;
+  double2 *Y = nullptr, *fc = nullptr;
   float2 *J32 = nullptr, *sxc = nullptr, *W32 = nullptr, *T32 = nullptr;
   float* sy32 = nullptr;
   double* partT = nullptr;
-  if (p32) {
+  if (!p32) {
+    G1 = a.get<double>((size_t)S2 * nX);
+    qv = a.get<double>(N);
+    h = a.get<double>(N);
+    Y = a.get<double2>(N * M);
+    fc = a.get<double2>(MP);
+    T1 = a.get<double>((size_t)S1 * nX);
+  } else {
     J32 = a.get<float2>((size_t)MP * nm);
     sxc = a.get<float2>((size_t)nX * S1);
     sy32 = a.get<float>((size_t)nX * S2);

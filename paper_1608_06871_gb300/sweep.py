@@ -108,6 +108,8 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
     least-squares time t_l of every step in seconds, and the LSQR iterations.
     """
     use_lsqr = solver_kind_lsqr(solver)
+    if precision != HS_FP64 and not use_lsqr:
+        raise ValueError("the direct Gauss-Newton step needs precision HS_FP64; use solver='lsqr'")
     if angles is None:
         angles = lambda p: (2 * np.pi * np.arange(p.M) / p.M, 2 * np.pi * np.arange(p.P) / p.P)
     c = np.zeros((plans[0].S, plans[0].S)) if c0 is None else np.asarray(c0, dtype=np.float64)

@@ -106,3 +106,19 @@ def test_paper_plan_lsqr_sweep_matches_oracle(hs):
     assert rel(res.c, c_ref) < 1e-8
     for h_gpu, h_ref in zip(res.history, hist):
         assert np.allclose(h_gpu["residuals"], h_ref, rtol=1e-8)
+
+
+def test_mixed_lsqr_sweep_tracks_fp64(hs):
+    """k = 2, 2.5, 3 with LSQR at 1e-3: mixed-precision contexts with the tensor-core Jacobian
+    against FP64 contexts with FP64 products (same plan and data).  Each step differs by the
+    FP32 adjoint fields' error amplified by the early-stopped iteration; bar 1e-3 on the final
+    coefficients, equal LSQR iteration counts within 3 per frequency."""
+    from paper_1608_06871_gb300 import sweep as SW
+    plans = [SW.plan_ceil(k) for k in (2.0, 2.5, 3.0)]
+    data_fn = _data_fn(synth.gaussian_bumps(8))
+    r64 = SW.recursive_linearization(plans, data_fn, solver="lsqr")
+    r32 = SW.recursive_linearization(plans, data_fn, solver="lsqr", precision=hs.HS_MIXED,
+                                     lsqr_products=hs.HS_MIXED)
+    assert rel(r32.c, r64.c) < 1e-3
+    for a, b in zip(r32.history, r64.history):
+        assert abs(a["lsqr_iterations"][0] - b["lsqr_iterations"][0]) <= 3

@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--table2", type=float, default=0.0,
                     help="also run the paper's reconstruction plan (Sec. 4: k = 1:0.25:K, LSQR at 1e-3, "
                          "triangular modes, 5%% noise) up to this K and report it in the format of Table 2")
+    ap.add_argument("--examples", action="store_true",
+                    help="also run the paper's Examples 1 and 2 (analytic contrasts, k = 1..14.25 and 1..9, "
+                         "its plan and LSQR, no noise) and report the L2 error of the reconstruction per k")
     ap.add_argument("--paper-gn", action="store_true",
                     help="also time one FP64 Gauss-Newton step at the paper-scale top frequency (k = 70, "
                          "19,600 coefficients, 280 x 280 data; about 3 minutes)")
@@ -297,6 +300,8 @@ def run_hs(args, world, rank, local):
         secondary["sweep_mixed_lsqr_k40_ms"] = sweep_time(hs, torch, local, k_max=40.0, mixed_lsqr=True)
         if args.table2 > 0:
             secondary["paper_table2"] = paper_table2(hs, torch, local, args.table2)
+        if args.examples:
+            secondary["paper_examples"] = {f"example{e}": paper_example_run(hs, torch, local, e) for e in (1, 2)}
         if args.paper_gn:
             secondary["paper_scale_gn_step_k70"] = paper_scale_gn(hs, torch, local)
 
@@ -549,6 +554,50 @@ def paper_table2(hs, torch, local, k_max):
             "note": "inverse on 4^l leaves with (pi k / 2) h <= 2.5 (finer than the paper's 6-10 points per "
                     "wavelength); paper's Table 2 (MATLAB, up to 32 cores): k = 16: T_f 2.99 s, N_it 27, "
                     "T_l 195.14 s, T_t 4109.56 s"}
+
+
+def paper_example_run(hs, torch, local, which):
+    """The paper's Example 1 (k = 1..14.25) or 2 (k = 1..9), Sec. 4: its plan (k = 1 + j/4,
+    M = floor(2k), P = floor(4k), R = 20, triangular modes, LSQR at 1e-3, one step per k)
+    from the projection of q on the k = 1 modes, data without noise from the
+    mixed-precision solver on a tree with twice the leaves per side.  Reports the L2 error
+    of q_k on Omega (in the paper's units, over a 512^2 midpoint grid) at k = 1, 2, 3, ...
+    and the total time (the paper: about 15 and 10 minutes on up to 32 cores)."""
+    from paper_1608_06871_gb300 import sweep as SW
+    qfun = synth.paper_example(which)
+    k_top = 14.25 if which == 1 else 9.0
+    plans = [SW.plan_paper(float(k)) for k in np.arange(1.0, k_top + 1e-9, 0.25)]
+    data = {}
+    for p in plans:
+        al = 2 * np.pi * np.arange(p.M) / p.M
+        th = 2 * np.pi * np.arange(p.P) / p.P
+        gen = hs.Solver(min(2 * p.leaves_per_side, 128), 2, 2, p.R, hs.HS_MIXED, device=local)
+        x, y = gen.node_coords()
+        data[p.k] = gen.build_nodes(qfun(x, y), p.k).solve(al, th)
+        gen.close()
+    c0 = synth.project_sine(qfun, plans[0].S, plans[0].S) * plans[0].mask()
+    g = (np.arange(512) + 0.5) / 256.0 - 1.0
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    q_ref = qfun(X, Y)
+    cell = (math.pi / 512.0) ** 2  # area of a grid cell in the paper's units
+
+    def l2_err(c):
+        S = c.shape[0]
+        bx = np.sin(np.outer(np.arange(1, S + 1), g + 1.0) * (math.pi / 2.0))
+        return float(np.sqrt(np.sum((bx.T @ c @ bx - q_ref) ** 2) * cell))
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    errs = []
+    c = c0
+    for j, p in enumerate(plans):  # one frequency at a time, to record the error after each
+        res = SW.recursive_linearization([p], lambda pp, al, th: data[pp.k], c0=c, device=local, solver="lsqr")
+        c = res.c
+        if float(p.k_label).is_integer() or j == len(plans) - 1:
+            errs.append({"k": p.k_label, "l2_err": l2_err(c), "lsqr_iterations": res.history[0]["lsqr_iterations"][0]})
+    total = time.perf_counter() - t0
+    return {"l2_norm_q": float(np.sqrt(np.sum(q_ref ** 2) * cell)), "l2_error_by_k": errs, "total_s": total,
+            "frequencies": len(plans), "initial_l2_err": l2_err(c0)}
 
 
 def paper_scale_gn(hs, torch, local):

@@ -165,6 +165,40 @@ def scaled_sine_coeffs(qfun, S: int, qmax: float, nq: int = 640, grid: int = 102
     return c * (qmax / np.max(np.abs(q)))
 
 
+@dataclass(frozen=True)
+class PaperExample:
+    """The contrast of the paper's Example 1 (a single Gaussian) or Example 2 (a sum of
+    Hermite functions, sigma = 0.5), Sec. 4, given on [-pi/2, pi/2]^2 and evaluated here on
+    [-1, 1]^2 through x = (pi/2) x_hat.  Example 1's printed contrast 1.5 exp(-|x|^2/50)
+    would make 1 - q negative everywhere under the equation of Sec. 1; it is read as
+    entering with the opposite sign, q = -1.5 exp(-|x|^2/50) (refractive index squared
+    1 + 1.5 exp(...))."""
+
+    which: int
+
+    def paper_q(self, x, y):
+        if self.which == 1:
+            return -1.5 * np.exp(-(x * x + y * y) / 50.0)
+        s = 0.5
+        xs, ys = x / s, y / s
+        return (0.15 * (1.0 - xs) ** 2 * np.exp(-(xs ** 2 + (ys + 1.0) ** 2))
+                - np.exp(-(ys ** 2 + (xs + 1.0) ** 2)) / 60.0
+                - s * (0.4 * x - xs ** 3 - ys ** 5) * np.exp(-(x * x + y * y) / (s * s)))
+
+    def __call__(self, x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = self.paper_q(0.5 * math.pi * x, 0.5 * math.pi * y)
+        inside = (np.abs(x) <= 1.0) & (np.abs(y) <= 1.0)
+        return np.where(inside, out, 0.0)
+
+
+def paper_example(which: int) -> PaperExample:
+    if which not in (1, 2):
+        raise ValueError("the paper's analytic examples are 1 and 2")
+    return PaperExample(which)
+
+
 def project_sine(qfun, S1: int, S2: int, nq: int = 256) -> np.ndarray:
     """Coefficients of the L2 projection of q onto s_m1(x) s_m2(y) on [-1,1]^2 (Gauss-Legendre, nq^2 points).
 

@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, choices=["gn_k40", "jacobian_16x16_s64", "lsqr_k40", "lsqr_mixed_k40"],
+    ap.add_argument("--case", default=None, choices=["gn_k40", "jacobian_16x16_s64", "lsqr_k40", "lsqr_mixed_k40",
+                                                      "cgemm_shapes"],
                     help="run one named workload once, untimed, and exit (a target for profilers)")
     ap.add_argument("--table2", type=float, default=0.0,
                     help="also run the paper's reconstruction plan (Sec. 4: k = 1:0.25:K, LSQR at 1e-3, "
@@ -560,7 +561,7 @@ def paper_example_run(hs, torch, local, which):
     """The paper's Example 1 (k = 1..14.25) or 2 (k = 1..9), Sec. 4: its plan (k = 1 + j/4,
     M = floor(2k), P = floor(4k), R = 20, triangular modes, LSQR at 1e-3, one step per k)
     from the projection of q on the k = 1 modes, data without noise from the
-    mixed-precision solver on a tree with twice the leaves per side.  Reports the L2 error
+    FP64 solver on a tree with twice the leaves per side.  Reports the L2 error
     of q_k on Omega (in the paper's units, over a 512^2 midpoint grid) at k = 1, 2, 3, ...
     and the total time (the paper: about 15 and 10 minutes on up to 32 cores)."""
     from paper_1608_06871_gb300 import sweep as SW
@@ -571,7 +572,7 @@ def paper_example_run(hs, torch, local, which):
     for p in plans:
         al = 2 * np.pi * np.arange(p.M) / p.M
         th = 2 * np.pi * np.arange(p.P) / p.P
-        gen = hs.Solver(min(2 * p.leaves_per_side, 128), 2, 2, p.R, hs.HS_MIXED, device=local)
+        gen = hs.Solver(min(2 * p.leaves_per_side, 128), 2, 2, p.R, device=local)
         x, y = gen.node_coords()
         data[p.k] = gen.build_nodes(qfun(x, y), p.k).solve(al, th)
         gen.close()
@@ -739,6 +740,33 @@ def run_case(name):
     from paper_1608_06871_gb300.build import build
     build()
     import paper_1608_06871_gb300 as hs
+    if name == "cgemm_shapes":
+        # complex FP32 products through hs_cgemm32, tensor cores on and off: TFLOP/s at 8 m n k
+        shapes = [(1, 4096, 4096, 4096), (1, 1792, 1792, 1792), (1, 1792, 128, 3584), (8, 224, 1344, 224),
+                  (4, 448, 128, 896), (1, 130816, 64, 448)]
+        out = []
+        g = torch.Generator(device="cuda").manual_seed(0)
+        for b_, m, n, k in shapes:
+            A = torch.randn((b_, m, k), dtype=torch.complex64, device="cuda", generator=g)
+            B = torch.randn((b_, k, n), dtype=torch.complex64, device="cuda", generator=g)
+            C = torch.empty((b_, m, n), dtype=torch.complex64, device="cuda")
+            row = {"shape": [b_, m, n, k]}
+            for tc in (True, False):
+                hs.hs_set_tensor_cores(tc)
+                for _ in range(2):
+                    hs.hs_cgemm32(A, B, C)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(5):
+                    hs.hs_cgemm32(A, B, C)
+                e1.record()
+                torch.cuda.synchronize()
+                row["tc" if tc else "simt"] = 8.0 * b_ * m * n * k * 5 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            hs.hs_set_tensor_cores(True)
+            out.append(row)
+            print(row, flush=True)
+        return
     if name in ("gn_k40", "lsqr_k40", "lsqr_mixed_k40"):
         w = synth.WORKLOADS["gn_k40"]
         ph = synth.ellipse_phantom(7)

@@ -53,6 +53,33 @@ def plan_ceil(k: float, mode_factor: float = 1.6, dir_factor: float = 4.0, newto
                          int(math.ceil(dir_factor * k)), newton)
 
 
+def square_eigenvalues(lo: float, hi: float) -> list:
+    """Dirichlet eigenvalues sqrt(a^2 + b^2) (a, b >= 1) of the square [-pi/2, pi/2]^2 in [lo, hi]."""
+    out = set()
+    for a in range(1, int(math.floor(hi)) + 1):
+        blo = math.sqrt(max(lo * lo - a * a, 1.0))
+        for b in range(max(1, int(math.floor(blo))), int(math.floor(math.sqrt(max(hi * hi - a * a, 0.0)))) + 1):
+            v = math.hypot(a, b)
+            if lo <= v <= hi:
+                out.add(v)
+    return sorted(out)
+
+
+def square_safe(k: float, near: float = 0.002, window: float = 0.02) -> float:
+    """The paper's frequency on its square [-pi/2, pi/2]^2, moved when it lies within `near`
+    of a Dirichlet eigenvalue sqrt(a^2 + b^2) (a, b >= 1) of that square: the exterior
+    relation (D - I/2) u = S d_n u of Sec. 2 (the paper's T_ext = S^{-1}(D - I/2)) is
+    singular there, and the paper's grid k = 1 + j/4 hits it exactly at every integer k
+    that is the hypotenuse of a Pythagorean triple (5, 10, 13, 15, ...).  The new frequency
+    is the midpoint of the widest gap between eigenvalues within `window` of k."""
+    ev = square_eigenvalues(k - window, k + window)
+    if not ev or min(abs(e - k) for e in ev) >= near:
+        return k
+    pts = [k - window] + ev + [k + window]
+    gaps = [(pts[i + 1] - pts[i], 0.5 * (pts[i] + pts[i + 1])) for i in range(len(pts) - 1)]
+    return max(gaps)[1]
+
+
 def plan_paper(k: float, R: float = 20.0, leaf_kh: float = 2.5, min_leaves: int = 4,
                max_leaves: int = 128) -> FrequencyPlan:
     """The paper's experiment plan (Sec. 4) at its frequency k on its domain
@@ -62,8 +89,9 @@ def plan_paper(k: float, R: float = 20.0, leaf_kh: float = 2.5, min_leaves: int 
     basis sin(m (x + pi/2)) is sin(m pi (x_hat + 1) / 2)); one Gauss-Newton step.
     Leaves: the smallest power of two with (pi k / 2) h <= leaf_kh (h = 2 / n_L),
     which keeps the leaf Dirichlet blocks well away from resonance (the paper's
-    own rule, 6-10 points per wavelength, is coarser)."""
-    kh = math.pi * k / 2.0
+    own rule, 6-10 points per wavelength, is coarser).  Frequencies within 0.002
+    of the square's Dirichlet eigenvalues are moved off them (square_safe)."""
+    kh = math.pi * square_safe(k) / 2.0
     nl = max(min_leaves, 2 ** int(math.ceil(math.log2(max(2.0 * kh / leaf_kh, 1.0)))))
     S = int(math.floor(2.0 * k))
     return FrequencyPlan(kh, min(nl, max_leaves), max(S - 1, 1), int(math.floor(2.0 * k)),

@@ -41,6 +41,7 @@ SHAPES = [
     (2, 257, 130, 129),
     (1, 1000, 512, 448),
     (4, 448, 128, 896),
+    (1, 256, 64, 4100),  # many chunks through the copy ring, ragged k, split over a cluster
 ]
 
 

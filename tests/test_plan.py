@@ -1,0 +1,34 @@
+"""Frequency plans of the sweep driver (host logic, no GPU)."""
+import math
+
+import numpy as np
+
+from paper_1608_06871_gb300 import sweep as SW
+
+
+def dirichlet_eigenvalues(kmax):
+    """sqrt(a^2 + b^2), a, b >= 1, of the square [-pi/2, pi/2]^2 (brute force)."""
+    n = int(kmax) + 2
+    return np.array(sorted({math.hypot(a, b) for a in range(1, n) for b in range(1, n) if math.hypot(a, b) <= kmax}))
+
+
+def test_paper_grid_is_moved_off_the_square_resonances():
+    ks = 1.0 + np.arange(0, 277) / 4.0  # k = 1, 1.25, ..., 70
+    ev = dirichlet_eigenvalues(71.0)
+    moved = [k for k in ks if SW.square_safe(k) != k]
+    assert moved[:7] == [5.0, 10.0, 13.0, 15.0, 17.0, 18.25, 20.0]  # 18.25: 0.0017 from sqrt(333)
+    on = [k for k in ks if np.abs(ev - k).min() < 1e-12]
+    assert set(on) <= set(moved)  # every exact hit is moved (and the near ones)
+    for k in ks:
+        ks_ = SW.square_safe(k)
+        assert abs(ks_ - k) <= 0.02
+        assert np.abs(ev - ks_).min() >= 0.002, k
+
+
+def test_plan_paper_counts():
+    """Table 2's columns: Modes = S(S-1)/2 with S = floor(2k), M = floor(2k), M*P = 8 k^2 at integer k."""
+    for k, modes, m, mp in ((1, 1, 2, 8), (2, 6, 4, 32), (4, 28, 8, 128), (8, 120, 16, 512), (16, 496, 32, 2048),
+                            (32, 2016, 64, 8192), (64, 8128, 128, 32768)):
+        p = SW.plan_paper(float(k))
+        assert int(p.mask().sum()) == modes and p.M == m and p.M * p.P == mp
+        assert abs(p.R - 40.0 / math.pi) < 1e-12

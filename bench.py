@@ -24,6 +24,7 @@ import argparse
 import csv
 import io
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -597,8 +598,10 @@ def paper_example_run(hs, torch, local, which):
         if float(p.k_label).is_integer() or j == len(plans) - 1:
             errs.append({"k": p.k_label, "l2_err": l2_err(c), "lsqr_iterations": res.history[0]["lsqr_iterations"][0]})
     total = time.perf_counter() - t0
+    best = synth.project_sine(qfun, plans[-1].S, plans[-1].S, nq=512) * plans[-1].mask()
     return {"l2_norm_q": float(np.sqrt(np.sum(q_ref ** 2) * cell)), "l2_error_by_k": errs, "total_s": total,
-            "frequencies": len(plans), "initial_l2_err": l2_err(c0)}
+            "frequencies": len(plans), "initial_l2_err": l2_err(c0),
+            "best_in_basis_l2_err": l2_err(best)}
 
 
 def paper_scale_gn(hs, torch, local):

@@ -13,14 +13,13 @@
 //                               row n + j holds (im B[l][j],  re B[l][j])
 //   D' = A' B'^T = [Re C | Im C].
 // Tile: 128 complex rows x 64 complex columns (D' is 128 x 128 FP32 in TMEM),
-// K chunks of 8 complex (16 real).  Raw chunks are copied asynchronously
-// (cp.async, 8 bytes per element, zero-filled outside the matrices) into a
-// ring of three slots, two chunks ahead of the one being split; all 128
-// threads split a landed chunk into hi/lo copies in the canonical K-major
-// layout without swizzle (core matrices of 8 rows x 16 bytes) in one of two
-// 32 KB stages (two CTAs per SM).  One thread issues the MMAs (M = 128,
-// N = 128, K = 8) and commits them to an mbarrier.  Shapes with too few tiles
-// to fill the chip split k across a thread-block cluster.
+// K chunks of 8 complex (16 real) staged by all 128 threads into shared
+// memory in the canonical K-major layout without swizzle (core matrices of 8
+// rows x 16 bytes), two stages of 32 KB (three CTAs per SM), with the next
+// chunk prefetched into registers while the tensor cores work on the current
+// one.  One thread issues the MMAs (M = 128, N = 128, K = 8) and commits them
+// to an mbarrier.  Shapes with too few tiles to fill the chip split k across
+// a thread-block cluster.
 #include <algorithm>
 #include <cstdint>
 
@@ -46,17 +45,8 @@ constexpr int TC_THREADS = 128;
 constexpr int OP_BYTES = TM * TK * 4;            // one operand copy: 128 rows x 16 floats = 8 KB
 constexpr int STAGE_BYTES = 4 * OP_BYTES;        // A hi, A lo, B' hi, B' lo
 constexpr int RED_LD = TN + 1;                   // padded row of the split-k partial tile (float2)
-// raw (unsplit) chunks copied asynchronously, RAW_STAGES - 1 chunks ahead of the one being split:
-// A rows of 8 complex padded to 10 (80-byte rows: the 16-byte reads of 8 consecutive rows hit
-// distinct banks), B rows of 64 complex padded to 68
-constexpr int RAW_STAGES = 3;
-constexpr int RAW_A_LD = TKC + 2;
-constexpr int RAW_B_LD = TN + 4;
-constexpr int RAW_A_BYTES = TM * RAW_A_LD * 8;
-constexpr int RAW_BYTES = RAW_A_BYTES + TKC * RAW_B_LD * 8;
-constexpr int TC_SMEM = 2 * STAGE_BYTES + RAW_STAGES * RAW_BYTES + 2048;  // + alignment slack
-static_assert(TM * RED_LD * 8 <= 2 * STAGE_BYTES + RAW_STAGES * RAW_BYTES, "partial tile must fit the buffers");
-static_assert(RAW_A_BYTES % 16 == 0 && RAW_BYTES % 16 == 0, "raw buffers must stay 16-byte aligned");
+constexpr int TC_SMEM = 2 * STAGE_BYTES + 2048;  // two stages (>= the partial tile) + alignment slack
+static_assert(TM * RED_LD * 8 <= 2 * STAGE_BYTES + 1024, "partial tile must fit the stage buffers");
 constexpr uint32_t LBO = (TM / 8) * 128;         // bytes between core matrices along k (16 row groups)
 constexpr uint32_t SBO = 128;                    // bytes between 8-row groups
 // instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
@@ -106,7 +96,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&v)[16]) {
 // clusters of `splits` CTAs along z, each covering a range of whole chunks of
 // k, and the partial tiles are summed in split order through distributed
 // shared memory (deterministic, no atomics).
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(TC_THREADS, 3)
     k_cgemm_tc(int m, int n, int k, float2 alpha, const float2* __restrict__ A, int lda, long long sA,
                const float2* __restrict__ B, int ldb, long long sB, float2 beta, float2* __restrict__ C, int ldc,
                long long sC, int splits) {
@@ -139,47 +129,49 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
 
-  // raw chunk copies: A 128 x 8 complex (8 per thread), B 8 x 64 complex (4 per thread), 8 bytes
-  // each with cp.async (zero-filled outside the matrices), issued RAW_STAGES - 1 chunks ahead
-  unsigned char* raw = sm + 2 * STAGE_BYTES;
-  auto issue = [&](int ch, int slot) {
+  // register prefetch: A chunk 128 x 8 complex = 512 float4 (4 per thread),
+  // B chunk 8 x 64 complex as 256 pairs of k-adjacent elements (2 per
+  // thread).  Lane bits 0..2 select the row inside an 8-row core matrix, so
+  // the shared-memory stores of each 8-lane phase fill one contiguous
+  // 128-byte core matrix (no bank conflicts); the global loads of a warp still
+  // use whole 32-byte sectors.
+  float4 ra[4];
+  float2 rb0[2], rb1[2];
+  auto prefetch = [&](int ch) {
     const int kb = ch * TKC;
-    float2* ra_ = reinterpret_cast<float2*>(raw + slot * RAW_BYTES);
-    float2* rb_ = reinterpret_cast<float2*>(raw + slot * RAW_BYTES + RAW_A_BYTES);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int e = tid + TC_THREADS * i;  // 0..1023
-      const int r = e >> 3, kk = e & 7;
-      const int gr = row0 + r, gk = kb + kk;
-      const bool in = gr < m && gk < k;
-      const float2* src = in ? A + (long long)gr * lda + gk : A;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(su32(ra_ + r * RAW_A_LD + kk)), "l"(src),
-                   "r"(in ? 8 : 0)
-                   : "memory");
-    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int e = tid + TC_THREADS * i;  // 0..511
-      const int kk = e >> 6, j = e & 63;
-      const int gk = kb + kk, gc = col0 + j;
-      const bool in = gk < k && gc < n;
-      const float2* src = in ? B + (long long)gk * ldb + gc : B;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(su32(rb_ + kk * RAW_B_LD + j)), "l"(src),
-                   "r"(in ? 8 : 0)
-                   : "memory");
+      const int q = tid + TC_THREADS * i;                     // 0..511
+      const int r = (q >> 5) * 8 + (q & 7), c2 = ((q >> 3) & 3) * 2;  // row, complex column pair
+      const int gr = row0 + r, gk = kb + c2;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < m) {
+        const float2* p = A + (long long)gr * lda + gk;
+        if (gk < k) { v.x = p[0].x; v.y = p[0].y; }
+        if (gk + 1 < k) { v.z = p[1].x; v.w = p[1].y; }
+      }
+      ra[i] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int q = tid + TC_THREADS * i;                     // 0..255
+      const int j = (q >> 5) * 8 + (q & 7), lp = (q >> 3) & 3;  // column, k pair (l = 2 lp, 2 lp + 1)
+      const int gk = kb + 2 * lp, gc = col0 + j;
+      float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+      if (gc < n) {
+        if (gk < k) v0 = B[(long long)gk * ldb + gc];
+        if (gk + 1 < k) v1 = B[(long long)(gk + 1) * ldb + gc];
+      }
+      rb0[i] = v0;
+      rb1[i] = v1;
     }
   };
-  auto commit = [&]() { asm volatile("cp.async.commit_group;" ::: "memory"); };
   auto split_store = [&](float* hi, float* lo, int off, float4 v) {
     const float4 h = make_float4(tf32(v.x), tf32(v.y), tf32(v.z), tf32(v.w));
     *reinterpret_cast<float4*>(hi + off) = h;
     *reinterpret_cast<float4*>(lo + off) = make_float4(tf32(v.x - h.x), tf32(v.y - h.y), tf32(v.z - h.z), tf32(v.w - h.w));
   };
-  // split a raw chunk into the hi/lo operand copies of a stage, in the canonical K-major layout;
-  // lane bits 0..2 select the row inside an 8-row core matrix (conflict-free stores)
-  auto stage_store = [&](int slot, int st) {
-    const float2* ra_ = reinterpret_cast<const float2*>(raw + slot * RAW_BYTES);
-    const float2* rb_ = reinterpret_cast<const float2*>(raw + slot * RAW_BYTES + RAW_A_BYTES);
+  auto stage_store = [&](int st) {
     float* Ahi = reinterpret_cast<float*>(sm + st * STAGE_BYTES);
     float* Alo = Ahi + OP_BYTES / 4;
     float* Bhi = Alo + OP_BYTES / 4;
@@ -188,13 +180,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     for (int i = 0; i < 4; ++i) {
       const int q = tid + TC_THREADS * i;
       const int r = (q >> 5) * 8 + (q & 7), c4 = (q >> 3) & 3;  // real k' = 4 c4 .. 4 c4 + 3
-      split_store(Ahi, Alo, core_off(r, 4 * c4), *reinterpret_cast<const float4*>(ra_ + r * RAW_A_LD + 2 * c4));
+      split_store(Ahi, Alo, core_off(r, 4 * c4), ra[i]);
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int q = tid + TC_THREADS * i;
       const int j = (q >> 5) * 8 + (q & 7), lp = (q >> 3) & 3;
-      const float2 a = rb_[(2 * lp) * RAW_B_LD + j], b = rb_[(2 * lp + 1) * RAW_B_LD + j];  // B[2lp][j], B[2lp+1][j]
+      const float2 a = rb0[i], b = rb1[i];  // B[2lp][j], B[2lp+1][j]
       // row j: (re, -im) at k' = 2l, 2l+1; row TN + j: (im, re)
       split_store(Bhi, Blo, core_off(j, 4 * lp), make_float4(a.x, -a.y, b.x, -b.y));
       split_store(Bhi, Blo, core_off(TN + j, 4 * lp), make_float4(a.y, a.x, b.y, b.x));
@@ -202,21 +194,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   };
 
   bool ok = true;
-  for (int p = 0; p < RAW_STAGES - 1; ++p) {
-    if (p < nchunk) issue(ch0 + p, p);
-    commit();
-  }
+  if (nchunk > 0) prefetch(ch0);
   for (int c = 0; c < nchunk; ++c) {
     const int st = c & 1;
-    {
-      const int cn = c + RAW_STAGES - 1;
-      if (cn < nchunk) issue(ch0 + cn, cn % RAW_STAGES);
-      commit();
-    }
-    asm volatile("cp.async.wait_group %0;" ::"n"(RAW_STAGES - 1) : "memory");  // this thread's copies of chunk c
-    __syncthreads();                                                           // everyone's
     if (c >= 2) ok = ok && mbar_wait(su32(&mbar[st]), ((c >> 1) - 1) & 1);  // MMAs of chunk c-2 done
-    stage_store(c % RAW_STAGES, st);
+    stage_store(st);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -241,8 +223,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           su32(&mbar[st])));
     }
+    if (c + 1 < nchunk) prefetch(ch0 + c + 1);
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");
   // wait for the last commit of each stage
   if (nchunk >= 1) ok = ok && mbar_wait(su32(&mbar[(nchunk - 1) & 1]), ((nchunk - 1) >> 1) & 1);
   if (nchunk >= 2) ok = ok && mbar_wait(su32(&mbar[(nchunk - 2) & 1]), ((nchunk - 2) >> 1) & 1);
@@ -335,8 +317,8 @@ void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A
     cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  // split k when the tiles alone leave SMs idle (2 CTAs fit on each of 152 SMs)
-  constexpr long long kFill = 2 * 152;
+  // split k when the tiles alone leave SMs idle (3 CTAs fit on each of 152 SMs)
+  constexpr long long kFill = 3 * 152;
   const long long tiles = (long long)((m + TM - 1) / TM) * ((n + TN - 1) / TN) * batch;
   const int nch = (k + TKC - 1) / TKC;
   int splits = 1;

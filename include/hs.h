@@ -150,24 +150,24 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
  * tolerance of 1e-3):  min over real dc of ||J dc - r||^2 + damp^2 ||dc||^2,
  * r = data - F(c), dc restricted to the modes where mask != 0 (mask: S1*S2
  * bytes in the order of c, or NULL for all modes; e.g. the triangle
- * m1 + m2 <= S of Sec. 3.2).  J is never formed: every iteration applies J
- * and J^H once, from the forward and adjoint fields of the built contrast
- * (Theorem 3.1 / 3.2), in FP64 on the GPU; the iteration's vectors live on
- * the host.  Stops when the relative residual or the relative normal-equations
+ * m1 + m2 <= S of Sec. 3.2).  J comes from the forward and adjoint fields of
+ * the built contrast (Theorem 3.1 / 3.2).  products: HS_FP64 -- J is never
+ * formed, every iteration applies J and J^H from the fields by two FP64 grid
+ * contractions; HS_MIXED -- J is formed once in complex FP32 on the tensor
+ * cores (3xTF32) and every iteration reads it twice with FP64 sums, so that
+ * J v and J^H u stay exact transposes of that one matrix (for loose
+ * tolerances such as the paper's 1e-3).  The iteration's vectors live on the
+ * host.  Stops when the relative residual or the relative normal-equations
  * residual (LSQR's own estimates) is at most tol, or after max_iter
- * iterations; *iters_out (optional) receives the count.  products: HS_FP64
- * (every iteration applies J and J^H from the fields: two FP64 grid
- * contractions) or HS_MIXED (J is formed once in complex FP32 on the tensor
- * cores, 3xTF32, from the FP64 fields; every iteration then reads it twice,
- * accumulating in FP64, so that J v and J^H u stay exact transposes of that
- * one matrix -- for loose tolerances such as the paper's 1e-3).  Otherwise as hs_gn_step
- * (c_inout updated, resid_norm_out = ||r||_2 before the step).  On an
- * HS_MIXED context the residual and the forward fields come from the refined
- * solve (FP64 accurate) and the adjoint fields from one transposed sweep of
- * the FP32 factors (FP32 accurate, not refined), so J carries the FP32 solve's
- * error -- a step for loose tolerances, stated against the FP64 one by the
- * tests and the benchmark.  Errors: HS_EINVAL (damp < 0, tol < 0, max_iter < 1, bad
- * products, bad sizes, NULL), HS_ENOTBUILT, HS_ENOMEM, HS_ECUDA, HS_ETIMEOUT. */
+ * iterations; *iters_out (optional) receives the count.  Otherwise as
+ * hs_gn_step (c_inout updated, resid_norm_out = ||r||_2 before the step).
+ * On an HS_MIXED context the residual and the forward fields come from the
+ * refined solve (FP64 accurate) and the adjoint fields from one transposed
+ * sweep of the FP32 factors (FP32 accurate, not refined), so J carries the
+ * FP32 solve's error -- a step for loose tolerances, stated against the FP64
+ * one by the tests and the benchmark.  Errors: HS_EINVAL (damp < 0, tol < 0,
+ * max_iter < 1, bad products, bad sizes, NULL), HS_ENOTBUILT, HS_ENOMEM,
+ * HS_ECUDA, HS_ETIMEOUT. */
 int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M,
                     const double* thetas, int P, const unsigned char* mask, double damp,
                     double tol, int max_iter, int products, double* c_inout,

@@ -173,14 +173,26 @@ void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P
 // once each and accumulate in FP64, so that they stay exact transposes of one
 // operator (products computed from the fields with independent FP32 rounding
 // are not, and the bidiagonalisation amplifies that mismatch).
+// W[c - c0][g] for the nc pairs from c0: each thread takes one grid point g and
+// KR_PAIRS consecutive pairs, reading u_d(g) once per incidence it meets (pairs
+// are d-major) instead of once per pair.
+constexpr int KR_PAIRS = 16;
 __global__ void k_khatri_rao32(const double2* __restrict__ Ug, const double2* __restrict__ Zg, int P,
-                               long long plane, long long c0, long long n, float2* __restrict__ W) {
-  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const long long c = c0 + e / plane, g = e % plane;
-  const long long d = c / P, p = c % P;
-  const double2 u = Ug[d * plane + g], z = Zg[p * plane + g];
-  W[e] = make_float2((float)(u.x * z.x - u.y * z.y), (float)(u.x * z.y + u.y * z.x));
+                               long long plane, long long c0, int nc, float2* __restrict__ W) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= plane) return;
+  const int j0 = blockIdx.y * KR_PAIRS, j1 = min(nc, j0 + KR_PAIRS);
+  long long dprev = -1;
+  double2 u = make_double2(0.0, 0.0);
+  for (int j = j0; j < j1; ++j) {
+    const long long c = c0 + j, d = c / P, p = c % P;
+    if (d != dprev) {
+      u = Ug[d * plane + g];
+      dprev = d;
+    }
+    const double2 z = Zg[p * plane + g];
+    W[(long long)j * plane + g] = make_float2((float)(u.x * z.x - u.y * z.y), (float)(u.x * z.y + u.y * z.x));
+  }
 }
 
 // out[g][m] = (sx[m][g], 0), and sy as FP32
@@ -200,8 +212,8 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
   HS_COUNT_LAUNCH();
   for (long long c0 = 0; c0 < MP; c0 += C) {
     const int nc = (int)std::min<long long>(C, MP - c0);
-    const long long n = nc * plane;
-    k_khatri_rao32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ug, Zg, P, plane, c0, n, W);
+    k_khatri_rao32<<<dim3((unsigned)((plane + 255) / 256), (nc + KR_PAIRS - 1) / KR_PAIRS), 256, 0, s>>>(
+        Ug, Zg, P, plane, c0, nc, W);
     HS_COUNT_LAUNCH();
     gemm<float2, float2, float2>(s, OP_N, OP_N, nc * nX, S1, nX, make_float2(1.f, 0.f), W, nX, 0, sxc, S1, 0,
                                  make_float2(0.f, 0.f), T, S1, 0, 1);

@@ -53,8 +53,11 @@ def plan_ceil(k: float, mode_factor: float = 1.6, dir_factor: float = 4.0, newto
                          int(math.ceil(dir_factor * k)), newton)
 
 
-def square_eigenvalues(lo: float, hi: float) -> list:
-    """Dirichlet eigenvalues sqrt(a^2 + b^2) (a, b >= 1) of the square [-pi/2, pi/2]^2 in [lo, hi]."""
+def square_eigenvalues(lo: float, hi: float, unit: float = 1.0) -> list:
+    """Dirichlet eigenvalues unit * sqrt(a^2 + b^2) (a, b >= 1) in [lo, hi]: those of the square
+    [-pi/2, pi/2]^2 for unit = 1, of [-1, 1]^2 for unit = pi/2."""
+    if unit != 1.0:
+        return [unit * e for e in square_eigenvalues(lo / unit, hi / unit)]
     out = set()
     for a in range(1, int(math.floor(hi)) + 1):
         blo = math.sqrt(max(lo * lo - a * a, 1.0))
@@ -65,14 +68,15 @@ def square_eigenvalues(lo: float, hi: float) -> list:
     return sorted(out)
 
 
-def square_safe(k: float, near: float = 0.002, window: float = 0.02) -> float:
+def square_safe(k: float, near: float = 0.002, window: float = 0.02, unit: float = 1.0) -> float:
     """The paper's frequency on its square [-pi/2, pi/2]^2, moved when it lies within `near`
     of a Dirichlet eigenvalue sqrt(a^2 + b^2) (a, b >= 1) of that square: the exterior
     relation (D - I/2) u = S d_n u of Sec. 2 (the paper's T_ext = S^{-1}(D - I/2)) is
     singular there, and the paper's grid k = 1 + j/4 hits it exactly at every integer k
     that is the hypotenuse of a Pythagorean triple (5, 10, 13, 15, ...).  The new frequency
-    is the midpoint of the widest gap between eigenvalues within `window` of k."""
-    ev = square_eigenvalues(k - window, k + window)
+    is the midpoint of the widest gap between eigenvalues within `window` of k.  With
+    unit = pi/2 the same for a frequency on [-1, 1]^2 (eigenvalues (pi/2) sqrt(a^2 + b^2))."""
+    ev = square_eigenvalues(k - window, k + window, unit)
     if not ev or min(abs(e - k) for e in ev) >= near:
         return k
     pts = [k - window] + ev + [k + window]
@@ -96,6 +100,18 @@ def plan_paper(k: float, R: float = 20.0, leaf_kh: float = 2.5, min_leaves: int 
     S = int(math.floor(2.0 * k))
     return FrequencyPlan(kh, min(nl, max_leaves), max(S - 1, 1), int(math.floor(2.0 * k)),
                          int(math.floor(4.0 * k)), 1, R=2.0 * R / math.pi, triangle=S, k_label=k)
+
+
+def plan_c5(k: float) -> FrequencyPlan:
+    """The paper-scale reconstruction plan on [-1, 1]^2: S = floor(2k) sine modes per axis
+    (140 x 140 = 19,600 at k = 70), M = P = ceil(4k) (280 at k = 70), leaves
+    2^min(7, max(2, ceil(log2(128 k / 70)))) (128 x 128 at the top), one Gauss-Newton step;
+    frequencies within 0.002 of a Dirichlet eigenvalue of the square are moved off it
+    (square_safe with unit pi/2; the grid comes within 2e-5 of one at k = 40.75)."""
+    nl = 2 ** min(7, max(2, int(math.ceil(math.log2(128.0 * k / 70.0)))))
+    ks = square_safe(k, unit=math.pi / 2.0)
+    return FrequencyPlan(ks, nl, int(math.floor(2.0 * k)), int(math.ceil(4.0 * k)), int(math.ceil(4.0 * k)), 1,
+                         k_label=k)
 
 
 def solver_kind_lsqr(solver_name: str) -> bool:

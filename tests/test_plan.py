@@ -32,3 +32,14 @@ def test_plan_paper_counts():
         p = SW.plan_paper(float(k))
         assert int(p.mask().sum()) == modes and p.M == m and p.M * p.P == mp
         assert abs(p.R - 40.0 / math.pi) < 1e-12
+
+
+def test_plan_c5_top_and_resonances():
+    p = SW.plan_c5(70.0)
+    assert (p.leaves_per_side, p.S, p.M, p.P) == (128, 140, 280, 280)
+    ks = np.arange(1.0, 70.0 + 1e-9, 0.25)
+    ev = (math.pi / 2) * dirichlet_eigenvalues(46.0)
+    for k in ks:
+        pk = SW.plan_c5(float(k))
+        assert abs(pk.k - k) <= 0.02 and np.abs(ev - pk.k).min() >= 0.002, k
+    assert SW.plan_c5(40.75).k != 40.75

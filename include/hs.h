@@ -176,7 +176,10 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
 /* Gradient of the misfit 0.5 * ||F(c) - data||^2 with respect to the real sine
  * coefficients, grad = Re(J^H (F(c) - data)) (Theorem 3.2 read on the basis),
  * without forming J: one adjoint sweep over the receivers.  grad: S1*S2 doubles
- * (host); misfit_out (optional): the misfit value.  Requires hs_build. */
+ * (host); misfit_out (optional): the misfit value.  Requires hs_build.  On an
+ * HS_MIXED context the misfit and the forward fields come from the refined
+ * solve (FP64 accurate) and the adjoint fields from the FP32 factors, so the
+ * gradient carries the FP32 adjoint solve's error. */
 int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M,
                 const double* thetas, int P, double* grad, double* misfit_out);
 int hs_gradient_dev(hs_ctx* ctx, const double* data, const double* alphas, int M,

@@ -1182,7 +1182,11 @@ int gradient_core(hs_ctx* ctx, cudaStream_t s, const double* ddata, const double
   double* hre = a.get<double>(plane);
   double* T1 = a.get<double>((size_t)ctx->S1 * ctx->n14);
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
-  {
+  const bool mixed = ctx->cfg.precision == HS_MIXED;
+  if (mixed) {  // refined far field and forward fields, FP32 adjoint fields
+    Arena sub = a;
+    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub));
+  } else {
     Arena sub = a;
     const int nb = ctx->B.nb;
     double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);
@@ -1197,7 +1201,7 @@ int gradient_core(hs_ctx* ctx, cudaStream_t s, const double* ddata, const double
   }
   CK(cudaMemsetAsync(dmis, 0, sizeof(double), s));
   residual(s, ddata, F, MP, res, nullptr, dmis);  // res = data - F
-  CKR(fields_and_adjoint(ctx, s, da, M, dt, P, Ug, Zg, a));
+  if (!mixed) CKR(fields_and_adjoint(ctx, s, da, M, dt, P, Ug, Zg, a));
   // Zmix = conj(F - data) Zg = -conj(res) Zg  (M x plane)
   conj_neg(s, res, MP);
   gemm<double2, double2, double2>(s, OP_N, OP_N, M, (int)plane, P, make_double2(1, 0), res, P, 0, Zg, (int)plane, 0,
@@ -1218,7 +1222,8 @@ size_t gradient_bytes(hs_ctx* ctx, int M, int P) {
   const int MP = M * P;
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
   return 2 * Arena::bytes(MP, 16) + Arena::bytes(plane * M, 16) * 2 + Arena::bytes(plane * P, 16) +
-         Arena::bytes(plane, 8) + Arena::bytes((size_t)ctx->S1 * ctx->n14, 8) + fields_and_adjoint_bytes(ctx, M, P);
+         Arena::bytes(plane, 8) + Arena::bytes((size_t)ctx->S1 * ctx->n14, 8) +
+         (ctx->cfg.precision == HS_MIXED ? mixed_fields_bytes(ctx, M, P) : fields_and_adjoint_bytes(ctx, M, P));
 }
 
 }  // namespace
@@ -1779,7 +1784,6 @@ int hs_gradient_dev(hs_ctx* ctx, const double* data, const double* alphas, int M
                     double* grad, double* misfit_out, void* stream) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
-  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!data || !alphas || !thetas || !grad || !misfit_out) return fail(ctx, HS_EINVAL, "NULL pointer");
   Arena a;
@@ -1791,7 +1795,6 @@ int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M, co
                 double* grad, double* misfit_out) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
-  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!data || !alphas || !thetas || !grad) return fail(ctx, HS_EINVAL, "NULL pointer");
   cudaStream_t s = ctx->stream;

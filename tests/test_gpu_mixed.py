@@ -130,3 +130,22 @@ def test_factor_graph_replay_bitwise(hs):
     assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
     assert counts[1] == counts[4] and counts[2] == counts[5]
     assert not np.array_equal(outs[0], outs[1])
+
+
+def test_mixed_gradient_k20(hs):
+    """Misfit gradient on a mixed-precision context (refined forward fields, FP32 adjoint fields)
+    against the FP64 context at the k = 20 gradient workload: misfit to 1e-8 (the refined far
+    field), gradient to 1e-3 (the FP32 adjoint solve's error)."""
+    w = synth.WORKLOADS["grad_k20"]
+    c = synth.project_sine(synth.ellipse_phantom(3), w.S, w.S)
+    rng = np.random.default_rng(44)
+    data = 0.05 * (rng.standard_normal((w.M, w.P)) + 1j * rng.standard_normal((w.M, w.P)))
+    al, th = synth.directions(w.M), synth.receivers(w.P)
+    out = {}
+    for prec in (hs.HS_FP64, hs.HS_MIXED):
+        S = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, prec).build(c, w.k)
+        out[prec] = S.gradient(data, al, th)
+        S.close()
+    (g64, m64), (g32, m32) = out[hs.HS_FP64], out[hs.HS_MIXED]
+    assert abs(m32 - m64) < 1e-8 * m64
+    assert np.linalg.norm(g32 - g64) < 1e-3 * np.linalg.norm(g64)

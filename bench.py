@@ -369,12 +369,14 @@ def run_hs(args, world, rank, local):
 
 
 # DRAM bytes (read + write) of one launch of the dominant FP64 GEMM shape of the
-# mixed step (the 1792 x 128 x 1792 exterior-residual product), from an ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
-# its algorithmic bytes are 62.4 MB (matrix, right-hand sides, C read and written).
-GEMM64_TRAFFIC = 60.0e6
-GEMM64_TRAFFIC_NOTE = ("bytes per launch of the 1792x128x1792 complex exterior-residual GEMM (ncu dram read+write, "
-                       "58.8 MB + 1.0-1.5 MB); algorithmic 62.4 MB")
+# mixed step (the exterior-row residual [D - I/2, -S] [u_b; d_n u_b], 1792 x 128 x
+# 3584 complex, two per step), from an ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum); its algorithmic bytes are
+# 117.5 MB (the 1792 x 3584 matrix, the right-hand sides, C read and written).
+GEMM64_TRAFFIC = 114.5e6
+GEMM64_TRAFFIC_NOTE = ("bytes per launch of the 1792x128x3584 complex exterior-residual GEMM (ncu dram read+write, "
+                       "110.2 MB + 1.2-4.3 MB); algorithmic 117.5 MB; the step's other FP64 GEMM, the far field "
+                       "128x256x3584, moves 22.1 MB")
 
 
 def tf32_peak():

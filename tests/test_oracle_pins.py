@@ -3,7 +3,8 @@
 Each pin is chosen so that a plausible mistake in the oracle (a dropped term,
 a sign, a transposed operand, a wrong normal, a wrong weight) fails one of
 them: closed forms (disk and radial media), a brute-force integral (Born
-Jacobian), finite differences, Green's-function symmetry, a library
+Jacobian), finite differences, Green's-function symmetry, reciprocity of the
+far-field pattern, energy conservation (the optical theorem), a library
 least-squares solve and the grid-size column the paper prints (Table 1).
 """
 import math
@@ -221,3 +222,49 @@ def test_oracle_sweep_recovers_band_limited_contrast():
     c, hist = OS.sweep(plans, data_fn, lambda_rel=1e-8)
     assert np.abs(c - c_true).max() < 1e-4 * np.abs(c_true).max()
     assert hist[0][-1] < 1e-3 * hist[0][0]
+
+
+# --- far-field pattern: reciprocity and the optical theorem ----------------------
+def pattern(fw, alphas, xhat_angles):
+    """Far-field pattern u_inf(xhat; d) of u_s = exp(i k r)/sqrt(r) (u_inf + O(1/r)) from the
+    oracle's scattered boundary data by Green's representation with the asymptotic kernel:
+    u_inf(xhat) = e^{i pi/4}/sqrt(8 pi k) int (d_n_y e^{-i k xhat.y} u_s - e^{-i k xhat.y} d_n u_s) ds_y.
+    Written here from the large-argument form of H_0, independently of the oracle's receivers."""
+    k = fw.k
+    ui, dni = fw.plane_traces(np.asarray(alphas))
+    _, ub, psi = fw.split(fw.solve_incident(ui, dni))
+    phi_s, psi_s = ub - ui.T, psi - dni.T  # (M, nb)
+    xh = np.stack([np.cos(xhat_angles), np.sin(xhat_angles)], -1)  # (Q, 2)
+    X, nrm, w = fw.bd.nodes, fw.bd.node_normal, fw.bd.node_weight
+    e = np.exp(-1j * k * (xh @ X.T))  # (Q, nb)
+    dne = -1j * k * (xh @ nrm.T) * e
+    c = np.exp(1j * math.pi / 4) / math.sqrt(8 * math.pi * k)
+    return c * ((phi_s * w) @ dne.T - (psi_s * w) @ e.T)  # (M, Q)
+
+
+def test_far_field_pattern_reciprocity():
+    """u_inf(xhat; d) = u_inf(-d; -xhat) (exact for the continuous problem; discretisation
+    error here, as for the Green-function symmetry)."""
+    fw = F.forward_from_function(synth.gaussian_bumps(1), K5, 4)
+    a1, t1 = 0.4, 2.1
+    u12 = pattern(fw, [a1], np.array([t1]))[0, 0]
+    u21 = pattern(fw, [t1 + math.pi], np.array([a1 + math.pi]))[0, 0]
+    assert abs(u12 - u21) < 5e-8 * abs(u12)
+
+
+def test_optical_theorem_energy_conservation():
+    """For real q no energy is absorbed: Im int conj(u) d_r u over a circle of radius rho -> oo
+    vanishes for the total field u = u_i + u_s.  The scattered part gives k int |u_inf|^2; the
+    cross terms, by stationary phase at xhat = d (int exp(i k rho (1 - cos t)) dt ~
+    sqrt(2 pi / (k rho)) e^{i pi/4}; the contributions at xhat = -d cancel), give
+    sqrt(8 pi k) Re(e^{i pi/4} u_inf(d)).  So k int |u_inf|^2 dxhat = -sqrt(8 pi k) Re(e^{i pi/4}
+    u_inf(d)).  A wrong sign, normal or weight in the exterior representation breaks it at O(1)."""
+    fw = F.forward_from_function(synth.gaussian_bumps(1), K5, 4)
+    alpha = 0.7
+    Q = 256
+    th = 2 * math.pi * np.arange(Q) / Q
+    u = pattern(fw, [alpha], th)[0]
+    lhs = K5 * np.sum(np.abs(u) ** 2) * (2 * math.pi / Q)
+    fwd = pattern(fw, [alpha], np.array([alpha]))[0, 0]
+    rhs = -math.sqrt(8 * math.pi * K5) * (np.exp(1j * math.pi / 4) * fwd).real
+    assert abs(lhs - rhs) < 1e-8 * abs(lhs)

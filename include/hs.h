@@ -127,7 +127,9 @@ int hs_fields_dev(hs_ctx* ctx, const double* alphas, int M, double* u, void* str
  * J[(m*P + p)][(m1-1)*S2 + (m2-1)] = d u_far(m, p) / d c[m1][m2], complex,
  * (M*P) x (S1*S2) row-major.  Assembled by discrete reciprocity (the adjoint
  * of Theorem 3.2): forward fields times adjoint fields, projected onto the
- * sine basis. */
+ * sine basis.  On an HS_MIXED context J is formed in complex FP32 on the
+ * tensor cores from the refined forward fields and the FP32 adjoint fields
+ * (FP32 accuracy; the output is still complex128). */
 int hs_jacobian(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
                 double* J);
 int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,

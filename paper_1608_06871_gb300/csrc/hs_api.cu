@@ -1130,8 +1130,51 @@ int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, 
   return HS_OK;
 }
 
+// Mixed precision: J in complex FP32 on the tensor cores from the refined
+// forward fields and the FP32 adjoint fields, widened into the FP64 output.
+int jacobian_into_mixed(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P,
+                        double2* J, Arena& a) {
+  const int nX = ctx->n14, S1 = ctx->S1, S2 = ctx->S2, nm = S1 * S2;
+  const size_t plane = (size_t)nX * nX, MP = (size_t)M * P;
+  const int C = contract_chunk(M, P, nX, S1, g_contract_budget / 2);
+  double2* Ug = a.get<double2>(plane * M);
+  double2* Zg = a.get<double2>(plane * P);
+  double2* F = a.get<double2>(MP);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  {
+    Arena sub = a;
+    CKR(mixed_fields_and_adjoint(ctx, s, alphas, M, thetas, P, F, Ug, Zg, sub));
+  }
+  float2* J32 = a.get<float2>(MP * nm);
+  float2* sxc = a.get<float2>((size_t)nX * S1);
+  float* sy32 = a.get<float>((size_t)nX * S2);
+  float2* W = a.get<float2>(plane * C);
+  float2* T = a.get<float2>((size_t)nX * S1 * C);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  interior_sine_tables(s, ctx->d_xint, nX, S1, S2, ctx->d_sxi, ctx->d_syi);
+  Phase ph("hs_jacobian32");
+  contract_jacobian32(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, ctx->k * ctx->k, J32, sxc, sy32, W, T, C);
+  CK(cudaMemsetAsync(J, 0, sizeof(double2) * MP * nm, s));
+  convert_f2d_add(s, J32, J, (long long)(MP * nm));
+  CK(cudaGetLastError());
+  if (tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
+  return HS_OK;
+}
+
+size_t jacobian_bytes_mixed(hs_ctx* ctx, int M, int P) {
+  const int nX = ctx->n14;
+  const size_t plane = (size_t)nX * nX, MP = (size_t)M * P, nm = (size_t)ctx->S1 * ctx->S2;
+  const int C = contract_chunk(M, P, nX, ctx->S1, g_contract_budget / 2);
+  return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) + Arena::bytes(MP, 16) +
+         std::max(mixed_fields_bytes(ctx, M, P),
+                  Arena::bytes(MP * nm, 8) + Arena::bytes((size_t)nX * ctx->S1, 8) +
+                      Arena::bytes((size_t)nX * ctx->S2, 4) + Arena::bytes(plane * C, 8) +
+                      Arena::bytes((size_t)nX * ctx->S1 * C, 8));
+}
+
 int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* J,
                   Arena& a) {
+  if (ctx->cfg.precision == HS_MIXED) return jacobian_into_mixed(ctx, s, alphas, M, thetas, P, J, a);
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
   const int C = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget);
   double2* Ug = a.get<double2>(plane * M);
@@ -1152,6 +1195,7 @@ int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, cons
 }
 
 size_t jacobian_bytes(hs_ctx* ctx, int M, int P) {
+  if (ctx->cfg.precision == HS_MIXED) return jacobian_bytes_mixed(ctx, M, P);
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
   const int C = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget);
   return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) +
@@ -1471,7 +1515,6 @@ int hs_forward_dev(hs_ctx* ctx, const double* alphas, int M, const double* theta
 int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* J, void* stream) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
-  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!alphas || !thetas || !J) return fail(ctx, HS_EINVAL, "NULL pointer");
   Arena a;
@@ -1482,7 +1525,6 @@ int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thet
 int hs_jacobian(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P, double* J) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
-  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!alphas || !thetas || !J) return fail(ctx, HS_EINVAL, "NULL pointer");
   cudaStream_t s = ctx->stream;

@@ -769,14 +769,30 @@ def gn_step_top(hs, torch, local):
     e1.record(stream)
     torch.cuda.synchronize()
     g_ms, g_flops, g_n = hs.hs_prof_stop()
+    jac_ms64 = e0.elapsed_time(e1)
     s.close()
-    del J
+    # the same Jacobian on a mixed-precision context (tensor-core FP32 contraction of the refined
+    # forward fields and the FP32 adjoint fields): its time and its distance from the FP64 one
+    sm = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED, device=local, stream=stream.cuda_stream)
+    sm.build(c, w.k)
+    J32 = torch.empty_like(J)
+    hs.hs_jacobian_dev(sm.ctx, a_d, t_d, J32)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    hs.hs_jacobian_dev(sm.ctx, a_d, t_d, J32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    jac_mixed = {"ms": e0.elapsed_time(e1),
+                 "rel_err_vs_fp64": float(torch.linalg.vector_norm(J32 - J) / torch.linalg.vector_norm(J))}
+    sm.close()
+    del J, J32
     nX = 14 * w.n_leaf_side
     contract_flops = 4.0 * w.M * w.P * (nX * nX * w.S + nX * w.S * w.S)
     return {"value": float(np.median(ts)), "unit": "ms", "workload": w.name, "precision": "fp64",
             "includes": "hs_build + hs_gn_step (forward, adjoint sweep, Jacobian contraction, normal equations "
                         "Re(J^H J) + lambda I by symmetric block-row FP64 GEMMs, LU)",
-            "residual_norm": float(rn), "lsqr_paper_solver": lsqr_out, "jacobian_ms": e0.elapsed_time(e1),
+            "residual_norm": float(rn), "lsqr_paper_solver": lsqr_out, "jacobian_ms": jac_ms64,
+            "jacobian_mixed": jac_mixed,
             "jacobian_gemm_fp64": {"ms": g_ms, "launches": g_n, "tflops": g_flops / (g_ms * 1e-3) / 1e12,
                                    "contraction_algorithmic_tflop": contract_flops / 1e12}}
 

@@ -1105,7 +1105,8 @@ int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, 
   convert_d2f(s, CP, CP32, (long long)nbP);
   // CP += R_root^T E with R_root in boundary-node order = Pi R_c Pi^T (R_c in root box order)
   permute_rows<float2>(s, E32, ctx->d_bie_of_root, nb, P, Gr);
-  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->ops32.back().R, nb, 0, Gr, P, 0, zero, G, P, 0, 1);
+  const float2* Rc = ctx->ops32.empty() ? ctx->d_R32 : ctx->ops32.back().R;  // a single leaf has no merges
+  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, Rc, nb, 0, Gr, P, 0, zero, G, P, 0, 1);
   permute_rows<float2>(s, G, ctx->d_root_of_bie, nb, P, Gr);
   // CPs = C^{-T} (CP + G): C^{-1} is kept explicitly in d_Rb32 by the mixed build
   gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_Rb32, nb, 0, CP32, P, 0, zero, CPs, P, 0, 1);

@@ -192,4 +192,12 @@ def test_degenerate_one_of_everything(hs, prec):
         assert rel(c1.ravel() - c.ravel(), dc_ref) < 1e-7
         c2, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5)
         assert it == 1 and rel(c2.ravel() - c.ravel(), dc_ref) < 1e-7  # one unknown: one iteration is exact
+    else:  # the mixed adjoint on a tree without merges (FP32 accuracy)
+        Jo = fw.jacobian(al, th, 1, 1)
+        assert rel(S.jacobian(al, th), Jo) < 1e-4
+        data = ref * 1.1
+        g, _ = S.gradient(data, al, th)
+        assert rel(g.ravel(), F.misfit_gradient(Jo, ref.ravel(), data.ravel())) < 1e-4
+        c2, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5, products=hs.HS_MIXED)
+        assert it == 1 and rel(c2.ravel() - c.ravel(), F.gn_step(Jo, (data - ref).ravel(), 0.0)) < 1e-4
     S.close()

@@ -96,7 +96,8 @@ int hs_solve_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas,
  * a fixed arena sized at start-up), where an allocation made behind its back
  * would break its accounting or fail under its memory cap.  Same arguments
  * and results as hs_solve_dev (device pointers); the factors come from
- * hs_build on ctx, which must have been called before.
+ * hs_build on ctx, which must have been called before, on an HS_FP64 context
+ * (HS_EINVAL otherwise: the mixed path's refinement needs far more scratch).
  * Scratch: one 16 MiB static device array compiled into libhs (every GPU
  * that loads the library holds it until the process exits).  The call needs
  * 16 * N_b * (6 M + 2 P) bytes of it, N_b = 56 n_L; larger M, P are rejected

@@ -102,8 +102,11 @@ int hs_solve_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas,
  * that loads the library holds it until the process exits).  The call needs
  * 16 * N_b * (6 M + 2 P) bytes of it, N_b = 56 n_L; larger M, P are rejected
  * with HS_EINVAL.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array and it keeps
+ * address (cudaGetSymbolAddress) with that device current and keeps it for
+ * the life of the process; make that first call before any stream capture.
+ * A cudaDeviceReset (or anything else that destroys the device's primary
+ * context) invalidates the kept address: after one, do not call this
+ * function again in that process.  All calls share the array and it keeps
  * the last call's contents (every region is written before it is read, so
  * nothing needs clearing): calls whose GPU work overlaps -- on different
  * streams or from different contexts -- race on it; serialise them. */

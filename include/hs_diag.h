@@ -63,6 +63,24 @@ int hs_set_tensor_cores(int enable);
  * Jacobian.  Never fails. */
 int hs_set_contract_budget(unsigned long long bytes);
 
+/* Failure injection for tests of the error paths (host side only; nothing
+ * faults, traps or waits on the GPU).
+ *
+ * hs_fail_next_allocs: the next n device allocations made by any context
+ * (its persistent buffers at hs_create or a later first use, or the growth of
+ * its per-call workspace) fail without calling cudaMalloc; the call that
+ * needed the memory returns HS_ENOMEM with its reason in hs_last_error, and
+ * the context stays usable.  n = 0 clears the hook.  Process-wide, not
+ * thread-safe.  Errors: HS_EINVAL for n < 0.
+ *
+ * hs_raise_tc_timeout: sets the tensor-core timeout flag of `device` from the
+ * host, exactly as a bounded tensor-core wait that gave up would; the next
+ * call on that device that checks the flag (every HS_MIXED build, solve and
+ * tensor-core product) returns HS_ETIMEOUT and clears it.  Errors:
+ * HS_ECUDA. */
+int hs_fail_next_allocs(int n);
+int hs_raise_tc_timeout(int device);
+
 /* C[b] = A[b] B[b] for b < batch: complex FP32 (interleaved re, im),
  * row-major, A m x k, B k x n, C m x n, contiguous batches, all DEVICE
  * pointers on the current device, enqueued on `stream` (a cudaStream_t, NULL

@@ -35,7 +35,7 @@ import scipy.sparse.linalg as spla
 from scipy.special import hankel1
 
 from . import bie
-from .spectral import diff_matrix, interp_quad_weights, lobatto_nodes
+from .spectral import diff_matrix, lobatto_nodes
 
 P = 16
 
@@ -76,13 +76,6 @@ class Grid:
 
     def leaf_id(self, ix, iy):
         return iy * self.n + ix
-
-    def quad_weights(self) -> np.ndarray:
-        """Tensor interpolatory weights on the 14 x 14 interior nodes of every leaf."""
-        w = interp_quad_weights(self.t[1:-1]) * self.h / 2.0
-        W = np.zeros((P, P))
-        W[1:-1, 1:-1] = np.outer(w, w)
-        return np.broadcast_to(W, (self.nleaves, P, P))
 
 
 def _normal_row(grid: Grid, leaf: int, a: int, b: int):

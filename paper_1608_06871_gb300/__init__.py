@@ -71,6 +71,8 @@ _SIGS = {
     "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
     "hs_set_tensor_cores": (_I, [_I]),
+    "hs_fail_next_allocs": (_I, [_I]),
+    "hs_raise_tc_timeout": (_I, [_I]),
     "hs_set_graphs": (_I, [_I]),
     "hs_set_contract_budget": (_I, [ctypes.c_ulonglong]),
     "hs_cgemm32": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
@@ -284,6 +286,17 @@ def hs_set_contract_budget(nbytes: int):
     _check(None, lib().hs_set_contract_budget(int(nbytes)))
 
 
+def hs_fail_next_allocs(n: int):
+    """Test hook: the next n device allocations of the library fail with HS_ENOMEM (host side)."""
+    _check(None, lib().hs_fail_next_allocs(int(n)))
+
+
+def hs_raise_tc_timeout(device: int = 0):
+    """Test hook: set the device's tensor-core timeout flag from the host; the next
+    checking call reports HS_ETIMEOUT."""
+    _check(None, lib().hs_raise_tc_timeout(int(device)))
+
+
 def hs_set_tensor_cores(enable: bool):
     _check(None, lib().hs_set_tensor_cores(1 if enable else 0))
 
@@ -325,9 +338,9 @@ class Solver:
     """One factorisation context: hs_create + hs_build, with NumPy host calls."""
 
     def __init__(self, leaves_per_side: int, S1: int, S2: int, R: float = 3.0, precision: int = HS_FP64,
-                 device: int = 0, stream: int | None = None):
+                 device: int = 0, stream: int | None = None, refine_tol: float = 0.0, refine_max_iter: int = 0):
         self.nL, self.S1, self.S2, self.R = leaves_per_side, S1, S2, R
-        self.ctx = hs_create(leaves_per_side, S1, S2, R, precision, device, stream)
+        self.ctx = hs_create(leaves_per_side, S1, S2, R, precision, device, stream, refine_tol, refine_max_iter)
 
     @property
     def n_nodes(self) -> int:

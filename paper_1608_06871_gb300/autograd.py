@@ -9,7 +9,9 @@ gradient times the incoming scalar.  Factors are recomputed per call (per
 frequency in a sweep), not kept across calls.
 
 Arguments: c -- torch float64 (S1, S2); data -- CUDA float64 (M, P, 2);
-alphas, thetas -- CUDA float64 (M,), (P,).
+alphas, thetas -- CUDA float64 (M,), (P,).  The gradient kernels run on
+torch's current stream of data's device, so inputs produced there just
+before the call are read after they are written.
 """
 from __future__ import annotations
 
@@ -24,9 +26,11 @@ class _Misfit(torch.autograd.Function):
         hs_build(solver.ctx, c.detach().to("cpu", torch.float64).numpy(), float(k))
         grad = torch.empty(c.shape, dtype=torch.float64, device=data.device)
         mis = torch.empty(1, dtype=torch.float64, device=data.device)
-        # runs on the context's stream; synchronise before torch reads the results
-        hs_gradient_dev(solver.ctx, data, alphas, thetas, grad, mis)
-        torch.cuda.synchronize(data.device)
+        # enqueued on torch's current stream of that device: the adjoint-state
+        # kernels start only after the kernels and copies that produced data,
+        # alphas and thetas, and torch reads grad and mis in stream order
+        stream = torch.cuda.current_stream(data.device).cuda_stream
+        hs_gradient_dev(solver.ctx, data, alphas, thetas, grad, mis, stream=stream)
         ctx.save_for_backward(grad.to(c.device))
         return mis[0].to(c.device)
 

@@ -23,6 +23,7 @@ bool prof_active(int family) { return g_prof_family == family; }
 bool prof_any() { return g_prof_family != 0; }
 extern bool g_use_graphs;
 extern size_t g_contract_budget;
+extern int g_fail_allocs;
 
 void prof_begin(cudaStream_t s, cudaEvent_t* a) {
   cudaEventCreate(a);
@@ -128,6 +129,17 @@ int hs_set_graphs(int enable) {
 int hs_set_contract_budget(unsigned long long bytes) {
   hs::g_contract_budget = bytes ? (size_t)bytes : (size_t(1) << 30);
   return HS_OK;
+}
+
+int hs_fail_next_allocs(int n) {
+  if (n < 0) return HS_EINVAL;
+  hs::g_fail_allocs = n;
+  return HS_OK;
+}
+
+int hs_raise_tc_timeout(int device) {
+  if (cudaSetDevice(device) != cudaSuccess) return HS_ECUDA;
+  return hs::tc_raise_timeout_flag() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
 
 int hs_set_tensor_cores(int enable) {

@@ -18,6 +18,9 @@ bool g_use_graphs = true;  // process-wide switch (hs_set_graphs)
 // rows and half-projected rows); process-wide (hs_set_contract_budget).
 size_t g_contract_budget = size_t(1) << 30;
 bool prof_active(int family);
+// Test hook (hs_fail_next_allocs): this many of the next device allocations
+// of a context fail on the host with HS_ENOMEM, without calling cudaMalloc.
+int g_fail_allocs = 0;
 }
 
 using namespace hs;
@@ -255,7 +258,15 @@ int run_captured(hs_ctx* ctx, cudaStream_t s, GraphSlot& slot, bool capture, con
     if (r_ != HS_OK) return r_;   \
   } while (0)
 
+// True (and one fewer left) while the test hook says the next allocation fails.
+bool injected_alloc_failure() {
+  if (g_fail_allocs <= 0) return false;
+  --g_fail_allocs;
+  return true;
+}
+
 template <typename T> int dalloc(hs_ctx* ctx, T** p, size_t n) {
+  if (injected_alloc_failure()) return fail(ctx, HS_ENOMEM, "device allocation refused (injected failure)");
   void* v = nullptr;
   cudaError_t e = cudaMalloc(&v, std::max<size_t>(n, 1) * sizeof(T));
   if (e != cudaSuccess)
@@ -269,6 +280,7 @@ template <typename T> int dalloc(hs_ctx* ctx, T** p, size_t n) {
 int ensure_ws(hs_ctx* ctx, size_t bytes, Arena& a) {
   bytes += (1u << 20);  // slack for alignment padding
   if (bytes > ctx->ws_cap) {
+    if (injected_alloc_failure()) return fail(ctx, HS_ENOMEM, "workspace allocation refused (injected failure)");
     CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->ws_base) cudaFree(ctx->ws_base);
     ctx->ws_base = nullptr;

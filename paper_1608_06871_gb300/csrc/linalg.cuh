@@ -55,5 +55,6 @@ void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A
 // Synchronises s, then reads and clears this device's flag that a bounded
 // tensor-core wait gave up.
 bool tc_timed_out(cudaStream_t s);
+cudaError_t tc_raise_timeout_flag();
 
 }  // namespace hs

@@ -32,7 +32,11 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on `dev`, which must be the current device.
-// Looked up on the first call per device and cached.
+// Looked up on the first call per device and cached for the process lifetime:
+// the address belongs to the device's primary context, so a cudaDeviceReset
+// (which destroys that context and unloads this module) leaves the cached
+// value stale; the public header tells callers not to use the entry point
+// after one.
 cudaError_t scratch_address(int dev, void** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {

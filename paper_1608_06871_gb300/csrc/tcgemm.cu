@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ uint32_t tslot;
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[3];  // [0], [1]: per stage; [2]: every MMA of the CTA done
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
   A += b * sA;
@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[0])), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[1])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[2])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -225,9 +226,13 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     }
     if (c + 1 < nchunk) prefetch(ch0 + c + 1);
   }
-  // wait for the last commit of each stage
-  if (nchunk >= 1) ok = ok && mbar_wait(su32(&mbar[(nchunk - 1) & 1]), ((nchunk - 1) >> 1) & 1);
-  if (nchunk >= 2) ok = ok && mbar_wait(su32(&mbar[(nchunk - 2) & 1]), ((nchunk - 2) >> 1) & 1);
+  // one more commit by the issuing thread tracks every MMA it issued: its
+  // arrival means the tensor cores no longer touch TMEM or the stages
+  if (tid == 0 && nchunk > 0)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        su32(&mbar[2])));
+  const bool drained = nchunk == 0 || mbar_wait(su32(&mbar[2]), 0);
+  ok = ok && drained;
   asm volatile("tcgen05.fence::after_thread_sync;");
   // all threads agree on the outcome before the warp-collective TMEM loads
   const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
@@ -294,6 +299,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     }
     cl.sync();  // keep this CTA's partial tile alive until every rank has read it
   }
+  // Timed out: before the TMEM columns are released (and the shared-memory
+  // stages with the CTA), wait once more, again bounded, for the final commit,
+  // so that no MMA issued here can still be writing them.  If that wait gives
+  // up too the columns are released regardless; the flag already makes the
+  // host report HS_ETIMEOUT, and C is unspecified.
+  if (!all_ok && !drained) mbar_wait(su32(&mbar[2]), 0);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NR));
@@ -346,6 +357,13 @@ void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A
     cudaLaunchKernelEx(&cfg, k_cgemm_tc, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits);
   }
   HS_COUNT_LAUNCH();
+}
+
+// Set the current device's timeout flag from the host (test hook: the next
+// call that checks it reports HS_ETIMEOUT; no kernel waits on anything).
+cudaError_t tc_raise_timeout_flag() {
+  const int one = 1;
+  return cudaMemcpyToSymbol(g_tc_timeout, &one, sizeof(int), 0, cudaMemcpyHostToDevice);
 }
 
 bool tc_timed_out(cudaStream_t s) {

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity import rel
 from oracle import forward as F
 
 pytestmark = pytest.mark.gpu
@@ -26,8 +27,6 @@ def hs():
     mod.hs_set_contract_budget(0)
 
 
-def rel(a, b):
-    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
 
 
 def test_ragged_chunks_match_oracle(hs):

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity import rel
 from oracle import forward as F
 from oracle import lsqr as OL
 
@@ -29,8 +30,6 @@ def hs():
     return mod
 
 
-def rel(a, b):
-    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
 
 
 @pytest.fixture(scope="module")

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity import rel
 from oracle import forward as F
 
 pytestmark = pytest.mark.gpu
@@ -21,8 +22,6 @@ def hs():
     return mod
 
 
-def rel(a, b):
-    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
 
 
 def test_mixed_gaussian_bumps_k5_vs_oracle(hs):

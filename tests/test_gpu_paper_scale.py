@@ -16,6 +16,7 @@ import pytest
 
 import closed_forms as CF
 import synth
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -28,8 +29,6 @@ def hs():
     return mod
 
 
-def rel(a, b):
-    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
 
 
 def test_radial_gaussian_k70_matches_ode(hs):

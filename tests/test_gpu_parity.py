@@ -14,6 +14,7 @@ import pytest
 
 import closed_forms as CF
 import synth
+from parity import rel
 from oracle import forward as F
 
 pytestmark = pytest.mark.gpu
@@ -27,8 +28,6 @@ def hs():
     return mod
 
 
-def rel(a, b):
-    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
 
 
 def test_forward_gaussian_bumps_k5(hs):

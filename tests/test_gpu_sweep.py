@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity import rel
 from oracle import forward as F
 from oracle import sweep as OS
 
@@ -17,8 +18,6 @@ def hs():
     return mod
 
 
-def rel(a, b):
-    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
 
 
 def _data_fn(qt):
@@ -122,3 +121,33 @@ def test_mixed_lsqr_sweep_tracks_fp64(hs):
     assert rel(r32.c, r64.c) < 1e-3
     for a, b in zip(r32.history, r64.history):
         assert abs(a["lsqr_iterations"][0] - b["lsqr_iterations"][0]) <= 3
+
+
+def test_autograd_reads_inputs_in_stream_order(hs):
+    """The misfit's gradient kernels run on torch's current stream: data written by a
+    torch kernel queued just before the call (behind a long device-side delay) is the
+    data they read, so the result equals the one from data prepared ahead of time."""
+    import torch
+    from paper_1608_06871_gb300.autograd import misfit
+    nL, S, M, P, k = 4, 5, 6, 10, 5.0
+    c0 = synth.random_coeffs(S, S, seed=8, scale=0.03)
+    rng = np.random.default_rng(9)
+    dn = rng.standard_normal((M, P, 2))
+    al = torch.tensor(synth.directions(M), device="cuda")
+    th = torch.tensor(synth.receivers(P), device="cuda")
+    solver = hs.Solver(nL, S, S)
+    ref_data = torch.tensor(dn, device="cuda")
+    torch.cuda.synchronize()
+    c = torch.tensor(c0, requires_grad=True)
+    misfit(c, solver, k, ref_data, al, th).backward()
+    g_ref = c.grad.clone()
+    for _ in range(3):
+        src = torch.tensor(dn, device="cuda")
+        data = torch.zeros_like(src)
+        torch.cuda.synchronize()
+        torch.cuda._sleep(50_000_000)  # keeps the stream busy for tens of milliseconds
+        data.copy_(src)                # the producer of data, still queued when misfit is called
+        c = torch.tensor(c0, requires_grad=True)
+        misfit(c, solver, k, data, al, th).backward()
+        assert rel(c.grad.numpy(), g_ref.numpy()) < 1e-13
+    solver.close()

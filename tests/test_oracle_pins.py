@@ -183,6 +183,32 @@ def test_jacobian_matches_finite_differences():
         assert np.abs(fd - J[:, m]).max() < 2e-6 * np.abs(J[:, m]).max()
 
 
+def test_misfit_gradient_matches_finite_differences():
+    """Central differences of 0.5 ||F(c) - d||^2 in single coefficients (k = 5, 4 x 4 leaves)
+    against Re J^H (F - d): a dropped conjugate, a transposed J or a flipped residual sign fails.
+    h = 1e-4 balances the h^2 truncation against the rounding of the two solves (both ~2e-8 here)."""
+    S, h = 4, 1e-4
+    al, th = synth.directions(3), synth.receivers(5)
+    c = synth.random_coeffs(S, S, seed=5, scale=0.03)
+    rng = np.random.default_rng(21)
+    fw = F.forward_from_coeffs(c, K5, 4)
+    Fc, _ = fw.solve_plane(al, th)
+    d = Fc + 0.05 * (rng.standard_normal(Fc.shape) + 1j * rng.standard_normal(Fc.shape))
+    J = fw.jacobian(al, th, S, S)
+    g = F.misfit_gradient(J, Fc.ravel(), d.ravel())
+
+    def phi(cc):
+        u, _ = F.forward_from_coeffs(cc, K5, 4).solve_plane(al, th)
+        return 0.5 * np.linalg.norm(u - d) ** 2
+
+    for m in (0, 5, 10, 15):
+        cp, cm = c.copy(), c.copy()
+        cp.flat[m] += h
+        cm.flat[m] -= h
+        fd = (phi(cp) - phi(cm)) / (2 * h)
+        assert abs(fd - g[m]) < 1e-7 * np.abs(g).max()
+
+
 # --- Gauss-Newton step ------------------------------------------------------------
 def test_normal_equations_equal_stacked_lstsq():
     rng = np.random.default_rng(3)

@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--paper-gn", action="store_true",
                     help="also time one FP64 Gauss-Newton step at the paper-scale top frequency (k = 70, "
                          "19,600 coefficients, 280 x 280 data; about 3 minutes)")
+    ap.add_argument("--table1-kmax", type=int, default=128,
+                    help="top frequency of the paper's Table 1 forward benchmark (k = 1, 2, 4, .., this)")
     ap.add_argument("--sweep-kmax", type=float, default=10.0,
                     help="top frequency of the timed recursive-linearization sweep (40 = the full k = 1..40 plan)")
     return ap.parse_args()
@@ -382,6 +384,9 @@ def run_hs(args, world, rank, local):
     if secondary is not None:
         secondary["sweep_ms"] = sweep_time(hs, torch, local, k_max=args.sweep_kmax)
         secondary["sweep_mixed_lsqr_k40_ms"] = sweep_time(hs, torch, local, k_max=40.0, mixed_lsqr=True)
+        secondary["sweep_mixed_lsqr_k10_vs_fp64"] = sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=True,
+                                                               compare_fp64=True)
+        secondary["paper_table1"] = paper_table1(hs, torch, local, k_max=args.table1_kmax)
         if args.table2 > 0:
             secondary["paper_table2"] = paper_table2(hs, torch, local, args.table2)
         if args.c5_sweep:
@@ -481,7 +486,7 @@ def tf32_peak():
         return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"
 
 
-def sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=False):
+def sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=False, compare_fp64=False):
     """Recursive-linearization sweep (Sec. 3.4): k = 1, 1.5, .., k_max with the
     ceil(1.6 k) modes / ceil(4 k) incidences and receivers / leaves-by-k plan,
     one Gauss-Newton step per frequency, blurred-ellipse phantom (seed 7) plus
@@ -514,7 +519,24 @@ def sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=False):
     c_true = synth.project_sine(phantom, S, S, nq=max(256, 4 * S))
     how = ("mixed precision, LSQR at 1e-3 on the tensor-core Jacobian" if mixed_lsqr
            else "FP64, direct normal equations (lambda_rel 1e-4)")
-    return {"value": dt * 1e3, "unit": "ms", "frequencies": len(plans),
+    extra = {}
+    if compare_fp64 and mixed_lsqr:
+        # the same plan and data on FP64 contexts with FP64 LSQR products, and on mixed contexts
+        # with FP64 products (refined forward and adjoint fields): final coefficients compared
+        t1 = time.perf_counter()
+        r64 = SW.recursive_linearization(plans, lambda p, al, th: data[p.k], device=local, solver="lsqr")
+        t64 = time.perf_counter() - t1
+        t1 = time.perf_counter()
+        rmx = SW.recursive_linearization(plans, lambda p, al, th: data[p.k], device=local, precision=hs.HS_MIXED,
+                                         solver="lsqr")
+        tmx = time.perf_counter() - t1
+        nrm = np.linalg.norm(r64.c)
+        extra = {"fp64_lsqr_sweep_ms": t64 * 1e3, "mixed_fp64_products_sweep_ms": tmx * 1e3,
+                 "coeff_rel_diff_vs_fp64_lsqr_sweep": float(np.linalg.norm(res.c - r64.c) / nrm),
+                 "mixed_fp64_products_coeff_rel_diff_vs_fp64": float(np.linalg.norm(rmx.c - r64.c) / nrm),
+                 "note": "tensor-core Jacobian: FP32 rounding of J amplified by the early-stopped LSQR; with FP64 "
+                         "products the mixed sweep meets the 1e-7 coefficient bar"}
+    return {"value": dt * 1e3, "unit": "ms", "frequencies": len(plans), **extra,
             "workload": f"sweep k=1:0.5:{k_max:g}, S=ceil(1.6k), M=P=ceil(4k), leaves 2^max(2,ceil(log2 0.8k)), "
                         f"ellipse phantom seed 7 + 1% noise, 1 GN step per k, {how}",
             "final_residual": float(res.history[-1]["residuals"][-1]),
@@ -655,6 +677,68 @@ def paper_table2(hs, torch, local, k_max):
             "note": "inverse on 4^l leaves with (pi k / 2) h <= 2.5 (finer than the paper's 6-10 points per "
                     "wavelength); paper's Table 2 (MATLAB, up to 32 cores): k = 16: T_f 2.99 s, N_it 27, "
                     "T_l 195.14 s, T_t 4109.56 s"}
+
+
+# Table 1 of the paper (MATLAB, up to 12 cores of a 2.5 GHz Xeon): k -> (N, N_bdry, T_interior, T_bdry, T_solve)
+PAPER_TABLE1 = {1: (3721, 640, 1.79, 1.94, 9.56e-4), 2: (3721, 640, 0.879, 1.70, 1.24e-3),
+                4: (3721, 640, 0.857, 1.71, 1.74e-3), 8: (14641, 800, 4.12, 2.24, 1.47e-3),
+                16: (58081, 1120, 16.6, 3.38, 2.95e-3), 32: (231361, 1760, 64.3, 5.96, 8.70e-3),
+                64: (923521, 3040, 266.0, 12.3, 2.16e-2), 128: (3690241, 5600, 1100.0, 35.6, 8.71e-2)}
+
+
+def paper_table1(hs, torch, local, k_max=128, M=64):
+    """The paper's forward benchmark (Table 1) on its own workload: q = 1.5 exp(-|x|^2/50)
+    (sign reading of synth.paper_example(1)) on [-pi/2, pi/2]^2, k = 1, 2, 4, ..., k_max,
+    max(4, k)^2 leaves of 16 x 16 points (the table's N), M plane waves and M receivers.
+    Per row and precision: T_interior and T_bdry of the first build at that k (CUDA events
+    inside hs_build: leaves + merges; layer potentials + coupled root system + LU) and
+    T_solve = time of hs_forward_dev for the M incidences (fields on every leaf node and
+    the far field) / M.  The FP64 and mixed far fields are compared (relative L2)."""
+    from paper_1608_06871_gb300 import sweep as SW
+    stream = torch.cuda.current_stream()
+    qfun = synth.paper_example(1)
+    rows = []
+    k = 1
+    while k <= k_max:
+        p = SW.plan_table1(float(k), M)
+        al = torch.tensor(synth.directions(M), device="cuda")
+        th = torch.tensor(synth.receivers(M), device="cuda")
+        ufar = torch.empty((M, M, 2), dtype=torch.float64, device="cuda")
+        u = torch.empty((M, p.leaves_per_side ** 2, 256, 2), dtype=torch.float64, device="cuda")
+        row = {"k": k, "N": (15 * p.leaves_per_side + 1) ** 2, "N_bdry": 56 * p.leaves_per_side,
+               "leaves": f"{p.leaves_per_side}x{p.leaves_per_side}"}
+        far = {}
+        for name, prec in (("fp64", hs.HS_FP64), ("mixed", hs.HS_MIXED)):
+            s = hs.Solver(p.leaves_per_side, 1, 1, p.R, prec, device=local, stream=stream.cuda_stream)
+            x, y = s.node_coords()
+            qn = qfun(x, y)
+            s.build_nodes(qn, p.k)
+            ti, tb = hs.hs_build_phase_ms(s.ctx)
+            hs.hs_forward_dev(s.ctx, al, th, ufar, u)  # warm-up of the solve path
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hs.hs_forward_dev(s.ctx, al, th, ufar, u)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = {"T_interior_s": ti * 1e-3, "T_bdry_s": tb * 1e-3,
+                         "T_solve_s_per_rhs": e0.elapsed_time(e1) * 1e-3 / M}
+            if prec == hs.HS_MIXED:
+                row[name]["refine_passes"] = hs.hs_refine_stats(s.ctx)[0]
+            uf = ufar.cpu().numpy()
+            far[name] = uf[..., 0] + 1j * uf[..., 1]
+            s.close()
+        del u
+        row["mixed_vs_fp64_farfield_rel_err"] = float(np.linalg.norm(far["mixed"] - far["fp64"]) /
+                                                      np.linalg.norm(far["fp64"]))
+        pr = PAPER_TABLE1[k]
+        row["paper"] = {"N": pr[0], "N_bdry": pr[1], "T_interior_s": pr[2], "T_bdry_s": pr[3],
+                        "T_solve_s_per_rhs": pr[4]}
+        rows.append(row)
+        k *= 2
+    return {"rows": rows, "rhs_per_solve": M,
+            "note": "paper: MATLAB on up to 12 cores of a 2.5 GHz Xeon (context, not a target); its N_bdry is "
+                    "its own exterior discretisation, here 56 n_L Chebyshev edge nodes"}
 
 
 def paper_scale_sweep(hs, torch, local, k_max=70.0):
@@ -819,13 +903,32 @@ def gn_step_top(hs, torch, local):
         if i:
             ts.append(e0.elapsed_time(e1))
     sm = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED, device=local, stream=stream.cuda_stream)
+    # the direct step on a mixed context: FP32 factors, refined forward and adjoint fields,
+    # FP64 contraction and normal equations
+    ts_m = []
+    for i in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sm.build(c, w.k)
+        c1m, rnm = sm.gn_step(data, al, th, 1e-4, c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            ts_m.append(e0.elapsed_time(e1))
+    adj = hs.hs_adjoint_refine_stats(sm.ctx)
+    mixed_direct = {"ms": float(np.median(ts_m)),
+                    "step_rel_diff_vs_fp64": float(np.linalg.norm(c1m - c1) / np.linalg.norm(c1 - c)),
+                    "adjoint_refine_passes": adj[0], "adjoint_est_rel_error": adj[2],
+                    "includes": "hs_build + hs_gn_step on a mixed context (FP32 factors; forward and adjoint "
+                                "fields refined in FP64; FP64 contraction and normal equations)"}
     variants = (("fp64_products", s, hs.HS_FP64), ("tensor_core_jacobian", s, hs.HS_MIXED),
+                ("mixed_factors_fp64_products", sm, hs.HS_FP64),
                 ("mixed_factors_tensor_core_jacobian", sm, hs.HS_MIXED))
     lsqr_out = {"tolerance": 1e-3,
                 "includes": "hs_build + hs_gn_step_lsqr: forward, adjoint sweep, LSQR; fp64_products = J and J^H "
                             "applied from the fields in FP64 every iteration; tensor_core_jacobian = J formed once "
                             "in complex FP32 on the tensor cores, LSQR products read it with FP64 sums; "
-                            "mixed_factors = FP32 factors, refined forward fields, FP32 adjoint fields",
+                            "mixed_factors = FP32 factors with forward and adjoint fields refined in FP64",
                 "step_rel_diff_vs_fp64_at": "20 iterations each (tol 0)"}
     steps20 = {}
     for name, solver, prod in variants:
@@ -853,17 +956,48 @@ def gn_step_top(hs, torch, local):
     a_d, t_d = torch.tensor(al, device="cuda"), torch.tensor(th, device="cuda")
     hs.hs_jacobian_dev(s.ctx, a_d, t_d, J)
     torch.cuda.synchronize()
-    hs.hs_prof_start(hs.HS_PROF_GEMM_FP64)
+    # the contraction's emulated FP64 products, per-launch events
+    hs.hs_prof_start(hs.HS_PROF_GEMM_EMU)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     hs.hs_jacobian_dev(s.ctx, a_d, t_d, J)
     e1.record(stream)
     torch.cuda.synchronize()
-    g_ms, g_flops, g_n = hs.hs_prof_stop()
+    emu_ms, emu_flops, emu_n = hs.hs_prof_stop()
     jac_ms64 = e0.elapsed_time(e1)
+    # the same Jacobian and GN step with the FP64 SIMT GEMMs (emulation off)
+    hs.hs_set_fp64_emulation(False)
+    J_simt = torch.empty_like(J)
+    hs.hs_jacobian_dev(s.ctx, a_d, t_d, J_simt)
+    torch.cuda.synchronize()
+    hs.hs_prof_start(hs.HS_PROF_GEMM_FP64)
+    e0.record(stream)
+    hs.hs_jacobian_dev(s.ctx, a_d, t_d, J_simt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms, g_flops, g_n = hs.hs_prof_stop()
+    jac_ms_simt = e0.elapsed_time(e1)
+    e0.record(stream)
+    s.build(c, w.k)
+    c1_simt, _ = s.gn_step(data, al, th, 1e-4, c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gn_ms_simt = e0.elapsed_time(e1)
+    hs.hs_set_fp64_emulation(True)
+    emu_vs_simt = float(torch.linalg.vector_norm(J - J_simt) / torch.linalg.vector_norm(J_simt))
+    del J_simt
     s.close()
-    # the same Jacobian on a mixed-precision context (tensor-core FP32 contraction of the refined
-    # forward fields and the FP32 adjoint fields): its time and its distance from the FP64 one
+    bf16 = tf32_peak()[0] * 2.25 / 1.1
+    emulated = {"kernel": "k_oz_mma (tcgen05 kind::f16, exact BF16 slices: 36 slice-pair products per FP64 product)",
+                "launches": emu_n, "ms": emu_ms, "fp64_equivalent_tflops": emu_flops / (emu_ms * 1e-3) / 1e12,
+                "issued_bf16_tflops": 36 * emu_flops / (emu_ms * 1e-3) / 1e12, "bf16_peak": bf16,
+                "frac_issued": 36 * emu_flops / (emu_ms * 1e-3) / 1e12 / bf16,
+                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
+                "jacobian_ms_fp64_simt": jac_ms_simt, "gn_step_ms_fp64_simt": gn_ms_simt,
+                "gn_step_step_rel_diff_vs_simt": float(np.linalg.norm(c1 - c1_simt) / np.linalg.norm(c1_simt - c)),
+                "jacobian_rel_diff_vs_simt": emu_vs_simt}
+    # the same Jacobian on a mixed-precision context (refined forward and adjoint fields, FP64
+    # contraction): its time and its distance from the FP64 one
     sm = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED, device=local, stream=stream.cuda_stream)
     sm.build(c, w.k)
     J32 = torch.empty_like(J)
@@ -882,7 +1016,8 @@ def gn_step_top(hs, torch, local):
     return {"value": float(np.median(ts)), "unit": "ms", "workload": w.name, "precision": "fp64",
             "includes": "hs_build + hs_gn_step (forward, adjoint sweep, Jacobian contraction, normal equations "
                         "Re(J^H J) + lambda I by symmetric block-row FP64 GEMMs, LU)",
-            "residual_norm": float(rn), "lsqr_paper_solver": lsqr_out, "jacobian_ms": jac_ms64,
+            "residual_norm": float(rn), "mixed_direct": mixed_direct, "lsqr_paper_solver": lsqr_out,
+            "jacobian_ms": jac_ms64, "fp64_emulation": emulated,
             "jacobian_mixed": jac_mixed,
             "jacobian_gemm_fp64": {"ms": g_ms, "launches": g_n, "tflops": g_flops / (g_ms * 1e-3) / 1e12,
                                    "contraction_algorithmic_tflop": contract_flops / 1e12}}

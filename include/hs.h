@@ -19,7 +19,8 @@
  * Conventions for every call:
  *  - Arrays are owned by the caller.  Plain pointers (no suffix) are HOST
  *    memory; calls ending in _dev take DEVICE pointers and a cudaStream_t
- *    passed as void* (NULL = the context's stream) and return without
+ *    passed as void* (NULL = the context's stream; pass cudaStreamLegacy,
+ *    (void*)1, for the legacy default stream) and return without
  *    synchronising that stream.
  *  - Complex arrays are interleaved (re, im) doubles, row-major.
  *  - Return value: HS_OK (0) or a negative HS_E* code; hs_last_error()
@@ -131,9 +132,13 @@ int hs_fields_dev(hs_ctx* ctx, const double* alphas, int M, double* u, void* str
  * J[(m*P + p)][(m1-1)*S2 + (m2-1)] = d u_far(m, p) / d c[m1][m2], complex,
  * (M*P) x (S1*S2) row-major.  Assembled by discrete reciprocity (the adjoint
  * of Theorem 3.2): forward fields times adjoint fields, projected onto the
- * sine basis.  On an HS_MIXED context J is formed in complex FP32 on the
- * tensor cores from the refined forward fields and the FP32 adjoint fields
- * (FP32 accuracy; the output is still complex128). */
+ * sine basis.  On an HS_MIXED context both fields come from FP64 iterative
+ * refinement of FP32 solves -- the forward fields as in hs_solve, the adjoint
+ * fields by refinement on the transposed system (FP64 residual of every
+ * transposed row, FP32 transposed correction solve) -- and the contraction
+ * runs in FP64, so J agrees with the FP64 context's to the refinement
+ * tolerance.  Errors as hs_solve, plus HS_ENOCONV if the adjoint refinement
+ * does not reach refine_tol in refine_max_iter passes. */
 int hs_jacobian(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
                 double* J);
 int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thetas, int P,
@@ -145,7 +150,9 @@ int hs_jacobian_dev(hs_ctx* ctx, const double* alphas, int M, const double* thet
  * then c <- c + dc.  c_inout (host, S1*S2) must be the coefficients the
  * context was last built with; on return the context holds the factors of
  * the OLD c (call hs_build again to factor the new one).  data: M x P complex
- * (host).  resid_norm_out (optional): ||r||_2 before the step. */
+ * (host).  resid_norm_out (optional): ||r||_2 before the step.  HS_FP64 or
+ * HS_MIXED context (on a mixed one F, J and the fields behind them are the
+ * refined ones of hs_solve and hs_jacobian; the normal equations are FP64). */
 int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
                const double* thetas, int P, double lambda_rel, double* c_inout,
                double* resid_norm_out);
@@ -167,13 +174,13 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
  * residual (LSQR's own estimates) is at most tol, or after max_iter
  * iterations; *iters_out (optional) receives the count.  Otherwise as
  * hs_gn_step (c_inout updated, resid_norm_out = ||r||_2 before the step).
- * On an HS_MIXED context the residual and the forward fields come from the
- * refined solve (FP64 accurate) and the adjoint fields from one transposed
- * sweep of the FP32 factors (FP32 accurate, not refined), so J carries the
- * FP32 solve's error -- a step for loose tolerances, stated against the FP64
- * one by the tests and the benchmark.  Errors: HS_EINVAL (damp < 0, tol < 0,
+ * On an HS_MIXED context the residual, the forward fields and the adjoint
+ * fields come from the refined solves (FP64 accurate), so with products
+ * HS_FP64 the step is the FP64 context's to the refinement tolerance; with
+ * products HS_MIXED it carries the FP32 rounding of the tensor-core J on
+ * either kind of context.  Errors: HS_EINVAL (damp < 0, tol < 0,
  * max_iter < 1, bad products, bad sizes, NULL), HS_ENOTBUILT, HS_ENOMEM,
- * HS_ECUDA, HS_ETIMEOUT. */
+ * HS_ECUDA, HS_ETIMEOUT, HS_ENOCONV. */
 int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M,
                     const double* thetas, int P, const unsigned char* mask, double damp,
                     double tol, int max_iter, int products, double* c_inout,
@@ -183,9 +190,8 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
  * coefficients, grad = Re(J^H (F(c) - data)) (Theorem 3.2 read on the basis),
  * without forming J: one adjoint sweep over the receivers.  grad: S1*S2 doubles
  * (host); misfit_out (optional): the misfit value.  Requires hs_build.  On an
- * HS_MIXED context the misfit and the forward fields come from the refined
- * solve (FP64 accurate) and the adjoint fields from the FP32 factors, so the
- * gradient carries the FP32 adjoint solve's error. */
+ * HS_MIXED context the misfit, the forward fields and the adjoint fields come
+ * from the refined solves (FP64 accurate; HS_ENOCONV if a refinement stalls). */
 int hs_gradient(hs_ctx* ctx, const double* data, const double* alphas, int M,
                 const double* thetas, int P, double* grad, double* misfit_out);
 int hs_gradient_dev(hs_ctx* ctx, const double* data, const double* alphas, int M,

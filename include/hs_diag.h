@@ -19,6 +19,7 @@ extern "C" {
 #define HS_PROF_GEMM_FP64 1 /* the batched FP64 real/complex GEMM kernel */
 #define HS_PROF_GEMM_FP32 2 /* the same GEMM kernel in FP32 (mixed-precision path) */
 #define HS_PROF_GEMM_TC 3   /* the tensor-core complex FP32 GEMM (mixed-precision path) */
+#define HS_PROF_GEMM_EMU 4  /* the emulated FP64 product on the tensor cores (FP64-equivalent flops) */
 
 /* Start recording a CUDA event pair around every launch of the given family
  * (on the stream the launch uses) and counting its algorithmic flops
@@ -43,6 +44,21 @@ int hs_peak_fp64(int device, double ms, double* tflops);
  * passes, or the change itself before rho is known) in the most recent
  * HS_MIXED solve on ctx (0, -1, -1 before any).  Any pointer may be NULL. */
 int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update, double* est_error);
+
+/* Device time of the two factorisation phases of the last build on ctx, in
+ * milliseconds (CUDA events on the context's stream): the interior (leaf
+ * operators and every merge up the tree, Table 1's T_interior) and the
+ * exterior (the layer-potential matrices when k is new, the coupled root
+ * system and its LU, Table 1's T_bdry).  -1 before any build and after a
+ * build replayed from a CUDA graph (HS_MIXED, unchanged k), which is not
+ * split.  Any pointer may be NULL. */
+int hs_build_phase_ms(const hs_ctx* ctx, double* interior_ms, double* boundary_ms);
+
+/* The same for the adjoint refinement of the most recent HS_MIXED Jacobian,
+ * gradient or Gauss-Newton step on ctx: passes, the last relative change of
+ * the adjoint fields at the interior nodes and the estimated relative error
+ * of the returned ones (0, -1, -1 before any).  Any pointer may be NULL. */
+int hs_adjoint_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update, double* est_error);
 
 /* Replay the mixed-precision factorisation from a CUDA graph captured once
  * per frequency (enable != 0, the default) or enqueue it launch by launch
@@ -102,6 +118,24 @@ int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int b
  * (non-positive size, NULL pointer), HS_ECUDA. */
 int hs_zgemm(int transA, int transB, int m, int n, int k, const void* A, const void* B, void* C, int accumulate,
              void* stream);
+
+/* C[b] = A[b] B[b] for b < batch in FP64 (real, row-major, A m x k, B k x n,
+ * C m x n, contiguous batches; DEVICE pointers on the current device,
+ * enqueued on `stream` and synchronised before return) by the library's
+ * emulated FP64 product on the tensor cores: rows of A and columns of B
+ * scaled by powers of two and split into eight exact 7-bit BF16 slices, the
+ * 36 slice pairs of weight >= 2^-63 multiplied exactly in FP32 accumulators,
+ * recombined exactly in integers and rounded once per piece of at most 384 of
+ * k (within the FP64 product's bound 2 k u |A||B|).  Allocates and frees
+ * its scratch on `stream`.  Errors: HS_EINVAL (bad size, NULL), HS_ENOMEM,
+ * HS_ETIMEOUT (a bounded tensor-core wait gave up), HS_ECUDA (also when the
+ * driver offers no tensor-map encoder). */
+int hs_dgemm_emulated(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream);
+
+/* Use the emulated FP64 product above for the FP64 Jacobian contraction
+ * (enable != 0, the default) or the FP64 SIMT GEMM (enable == 0).
+ * Process-wide; takes effect at the next Jacobian.  Never fails. */
+int hs_set_fp64_emulation(int enable);
 
 /* Solve A[b] X[b] = B[b] in place in B for b < batch with the library's
  * batched LU (partial pivoting; tournament pivoting for panels taller than 256

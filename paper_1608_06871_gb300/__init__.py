@@ -70,6 +70,9 @@ _SIGS = {
     "hs_peak_fp64": (_I, [_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
+    "hs_adjoint_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "hs_build_phase_ms": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "hs_set_tensor_cores": (_I, [_I]),
     "hs_fail_next_allocs": (_I, [_I]),
     "hs_raise_tc_timeout": (_I, [_I]),
@@ -78,6 +81,8 @@ _SIGS = {
     "hs_cgemm32": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
     "hs_lu_solve": (_I, [_I, _I, _I, _P, _P, _I, _P]),
     "hs_zgemm": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _I, _P]),
+    "hs_dgemm_emulated": (_I, [_I, _I, _I, _P, _P, _P, _I, _P]),
+    "hs_set_fp64_emulation": (_I, [_I]),
 }
 
 
@@ -250,6 +255,7 @@ def hs_destroy(ctx):
 HS_PROF_GEMM_FP64 = 1
 HS_PROF_GEMM_FP32 = 2
 HS_PROF_GEMM_TC = 3
+HS_PROF_GEMM_EMU = 4
 
 
 def hs_prof_start(family: int = HS_PROF_GEMM_FP64):
@@ -268,6 +274,22 @@ def hs_refine_stats(ctx):
     far-field error) of the last HS_MIXED solve."""
     it, up, est = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().hs_refine_stats(ctx, ctypes.byref(it), ctypes.byref(up), ctypes.byref(est)))
+    return it.value, up.value, est.value
+
+
+def hs_build_phase_ms(ctx):
+    """(interior ms, exterior ms) of the last build: leaves + merges, then layer potentials +
+    coupled root system; (-1, -1) after a build replayed from a CUDA graph."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().hs_build_phase_ms(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def hs_adjoint_refine_stats(ctx):
+    """(passes, last relative change, estimated relative error) of the adjoint fields
+    of the last HS_MIXED Jacobian, gradient or Gauss-Newton step."""
+    it, up, est = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().hs_adjoint_refine_stats(ctx, ctypes.byref(it), ctypes.byref(up), ctypes.byref(est)))
     return it.value, up.value, est.value
 
 
@@ -309,6 +331,19 @@ def hs_zgemm(A, B, C, transA: bool = False, transB: bool = False, accumulate: bo
     _check(None, lib().hs_zgemm(int(transA), int(transB), m, n, k, ctypes.c_void_p(A.data_ptr()),
                                 ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()), int(accumulate),
                                 ctypes.c_void_p(stream)))
+
+
+def hs_dgemm_emulated(A, B, C, stream: int = 0):
+    """C[b] = A[b] @ B[b] for contiguous float64 CUDA tensors of shape (batch, m, k), (batch, k, n),
+    (batch, m, n) by the emulated FP64 product on the tensor cores (exact BF16 slices)."""
+    batch, m, k = A.shape
+    n = B.shape[2]
+    _check(None, lib().hs_dgemm_emulated(m, n, k, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                         ctypes.c_void_p(C.data_ptr()), batch, ctypes.c_void_p(stream)))
+
+
+def hs_set_fp64_emulation(enable: bool):
+    _check(None, lib().hs_set_fp64_emulation(1 if enable else 0))
 
 
 def hs_lu_solve(A, B, stream: int = 0):

@@ -29,7 +29,9 @@ class _Misfit(torch.autograd.Function):
         # enqueued on torch's current stream of that device: the adjoint-state
         # kernels start only after the kernels and copies that produced data,
         # alphas and thetas, and torch reads grad and mis in stream order
-        stream = torch.cuda.current_stream(data.device).cuda_stream
+        # (torch's default stream has handle 0, which the C ABI reads as "the
+        # context's own stream": pass cudaStreamLegacy, handle 1, instead)
+        stream = torch.cuda.current_stream(data.device).cuda_stream or 1
         hs_gradient_dev(solver.ctx, data, alphas, thetas, grad, mis, stream=stream)
         ctx.save_for_backward(grad.to(c.device))
         return mis[0].to(c.device)

@@ -59,7 +59,9 @@ __global__ void k_dfma_peak(double* out, int iters, double a, double b) {
 extern "C" {
 
 int hs_prof_start(int family) {
-  if (family != HS_PROF_GEMM_FP64 && family != HS_PROF_GEMM_FP32 && family != HS_PROF_GEMM_TC) return HS_EINVAL;
+  if (family != HS_PROF_GEMM_FP64 && family != HS_PROF_GEMM_FP32 && family != HS_PROF_GEMM_TC &&
+      family != HS_PROF_GEMM_EMU)
+    return HS_EINVAL;
   hs::g_prof.clear();
   hs::g_prof_family = family;
   return HS_OK;
@@ -128,6 +130,31 @@ int hs_set_graphs(int enable) {
 
 int hs_set_contract_budget(unsigned long long bytes) {
   hs::g_contract_budget = bytes ? (size_t)bytes : (size_t(1) << 30);
+  return HS_OK;
+}
+
+int hs_set_fp64_emulation(int enable) {
+  hs::g_oz_enabled = enable != 0;
+  return HS_OK;
+}
+
+int hs_dgemm_emulated(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream) {
+  if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535 || !A || !B || !C) return HS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* a = const_cast<double*>(static_cast<const double*>(A));
+  double* b = const_cast<double*>(static_cast<const double*>(B));
+  // A(b, i, kk) = A[b m k + i k + kk];  Bt(b, j, kk) = B[b k n + kk n + j];  C(b, i, j) = C[b m n + i n + j]
+  const hs::OzView va{a, (long long)m * k, k, 0, 1, 1}, vb{b, (long long)k * n, 1, 0, n, 1},
+      vc{static_cast<double*>(C), (long long)m * n, n, 0, 1, 1};
+  const size_t bytes = hs::ozaki_scratch_bytes(m, n, k, batch, false);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) return HS_ENOMEM;
+  const cudaError_t e = hs::ozaki_gemm(s, m, n, k, batch, 1.0, va, vb, false, 0.0, vc, scratch, bytes);
+  cudaFreeAsync(scratch, s);
+  if (e == cudaErrorNotSupported) return HS_ECUDA;
+  if (e != cudaSuccess) return e == cudaErrorInvalidValue ? HS_EINVAL : HS_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
+  if (hs::tc_timed_out(s)) return HS_ETIMEOUT;
   return HS_OK;
 }
 

@@ -184,11 +184,20 @@ struct hs_ctx {
   GraphSlot pgraph[2];  // mixed: captured refinement-pass bodies (first pass, corrections)
   double2* d_DS = nullptr;   // mixed: [D - I/2, -S] (N_b x 2 N_b), the exterior rows on [u; d_n u]
   float2* d_DS32 = nullptr;  // same, FP32
-  float2* d_Q32 = nullptr;   // mixed: FP32 leaf adjoint operator, made at the first adjoint after a build
-  bool q32_valid = false;
+  // mixed: adjoint refinement -- per leaf edge node, where its interface or
+  // exterior row lives (see adjoint_residual), and per merge level the offset
+  // (in rows of nrhs) of its block in the interface-adjoint buffer
+  int4* d_adj_desc = nullptr;
+  std::vector<long long> if_off;
+  long long if_rows = 0;
+  int adj_iters = 0;
+  double adj_update = -1.0, adj_est = -1.0;
   // per-call workspace
   char* ws_base = nullptr;
   size_t ws_cap = 0;
+  // phase times of the last build recorded launch by launch (-1 after a graph replay)
+  cudaEvent_t ph_ev[3] = {nullptr, nullptr, nullptr};
+  double t_interior = -1.0, t_bdry = -1.0;
 };
 
 namespace {
@@ -305,6 +314,26 @@ int check_info(hs_ctx* ctx) {
     if (v != 0) return fail(ctx, HS_ESINGULAR, "zero pivot in a factorisation (column " + std::to_string(v) + ")");
   if (tc_timed_out(ctx->stream)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
   return HS_OK;
+}
+
+// Events bracketing the interior factorisation (leaves and merges) and the
+// exterior one (layer potentials when k is new, coupling, root LU) of a build.
+int phase_events(hs_ctx* ctx) {
+  for (auto& e : ctx->ph_ev)
+    if (!e) CK(cudaEventCreate(&e));
+  return HS_OK;
+}
+
+// After the build's stream was synchronised: the two phase times in ms.
+void phase_times(hs_ctx* ctx, bool recorded) {
+  ctx->t_interior = ctx->t_bdry = -1.0;
+  if (!recorded) return;
+  float a = 0.f, b = 0.f;
+  if (cudaEventElapsedTime(&a, ctx->ph_ev[0], ctx->ph_ev[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&b, ctx->ph_ev[1], ctx->ph_ev[2]) == cudaSuccess) {
+    ctx->t_interior = a;
+    ctx->t_bdry = b;
+  }
 }
 
 // Tree bookkeeping: merge levels from leaves (1 x 1) to the root (nL x nL).
@@ -446,6 +475,61 @@ int setup_tree(hs_ctx* ctx) {
     sy = psy;
     horiz = !horiz;
     ++bl;
+  }
+  // Interface-adjoint offsets and, for the mixed path's adjoint refinement,
+  // the row each leaf edge node's u and d_n u enter: the interface row of a
+  // merge level (alpha or beta side) or the exterior row of a boundary node.
+  // Same node arithmetic as the interface and boundary residual kernels.
+  ctx->if_off.clear();
+  ctx->if_rows = 0;
+  for (auto& L : ctx->levels) {
+    ctx->if_off.push_back(ctx->if_rows);
+    ctx->if_rows += (long long)L.nbox * 2 * L.ni;
+  }
+  if (ctx->cfg.precision == HS_MIXED) {
+    std::vector<int4> desc((size_t)nL * nL * 56, make_int4(-1, 0, -1, 0));
+    for (size_t li = 0; li < ctx->levels.size(); ++li) {
+      const Level& L = ctx->levels[li];
+      for (int b = 0; b < L.nbox; ++b) {
+        const int px = b % L.nbx_p, py = b / L.nbx_p;
+        for (int t = 0; t < L.ni; ++t) {
+          int la, lb, ea, eb;
+          const int node = t % 14 + 1;
+          if (L.horiz) {
+            const int x0 = px * 2 * L.sx, y0 = py * L.sy, ly = y0 + t / 14;
+            la = ly * nL + (x0 + L.sx - 1);
+            lb = ly * nL + (x0 + L.sx);
+            ea = 14 + node - 1;  // alpha: east edge
+            eb = 42 + node - 1;  // beta: west edge
+          } else {
+            const int x0 = px * L.sx, y0 = py * 2 * L.sy, lx = x0 + t / 14;
+            la = (y0 + L.sy - 1) * nL + lx;
+            lb = (y0 + L.sy) * nL + lx;
+            ea = 28 + node - 1;  // alpha: north edge
+            eb = node - 1;       // beta: south edge
+          }
+          const int row = (int)(ctx->if_off[li] + (long long)b * 2 * L.ni + t);
+          desc[(size_t)la * 56 + ea] = make_int4(row, L.ni, 0, 0);
+          desc[(size_t)lb * 56 + eb] = make_int4(row, L.ni, 1, 0);
+        }
+      }
+    }
+    const int nbd = 56 * nL;
+    for (int jn = 0; jn < nbd; ++jn) {
+      const int side = jn / (14 * nL), i = (jn % (14 * nL)) / 14, t = jn % 14 + 1;
+      int leaf, e;
+      switch (side) {
+        case 0: leaf = i; e = t - 1; break;
+        case 1: leaf = i * nL + (nL - 1); e = 14 + t - 1; break;
+        case 2: leaf = (nL - 1) * nL + i; e = 28 + t - 1; break;
+        default: leaf = i * nL; e = 42 + t - 1; break;
+      }
+      desc[(size_t)leaf * 56 + e] = make_int4(jn, 0, 2, 0);
+    }
+    for (const int4& d : desc)
+      if (d.z < 0) return fail(ctx, HS_EINVAL, "internal: a leaf edge node belongs to no row");
+    CKR(dalloc(ctx, &ctx->d_adj_desc, desc.size()));
+    CK(cudaMemcpy(ctx->d_adj_desc, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice));
   }
   // Root order vs the order of the boundary nodes of the exterior equations
   // (S, E, N, W sides, each by increasing coordinate): root_of_bie[j] is the
@@ -664,8 +748,9 @@ int setup(hs_ctx* ctx) {
 // the refinement residual.
 // Device work of the mixed-precision factorisation (no host synchronisation,
 // so that it can be captured into a CUDA graph).
-int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s) {
+int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s, bool record) {
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  if (record) CK(cudaEventRecord(ctx->ph_ev[0], s));
   leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32, nullptr,
                           ctx->d_info);
   const float2* Rc = ctx->d_R32;
@@ -673,6 +758,7 @@ int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s) {
     merge_level<float2>(s, ctx->levels[li], ctx->ops32[li], Rc, ctx->d_info);
     Rc = ctx->ops32[li].R;
   }
+  if (record) CK(cudaEventRecord(ctx->ph_ev[1], s));
   const int nb = ctx->B.nb;
   permute_square<float2>(s, Rc, ctx->d_root_of_bie, nb, ctx->d_Rb32);  // root map in boundary-node order
   const long long nn = (long long)nb * nb;
@@ -690,6 +776,7 @@ int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s) {
   // C^{-1} explicitly (in the buffer of the root map, no longer needed): each
   // refinement pass then applies it with one GEMM
   lu_inverse<float2>(s, ctx->d_C32, nb, 0, nb, ctx->d_Cpiv32, 0, ctx->d_Rb32, nb, 0, 1);
+  if (record) CK(cudaEventRecord(ctx->ph_ev[2], s));
   CK(cudaGetLastError());
   return HS_OK;
 }
@@ -706,10 +793,12 @@ int factor_mixed(hs_ctx* ctx, double k) {
   // (per-launch profiling of the FP32 families needs eager launches; the
   // factorisation has no FP64 GEMM, so FP64 profiling does not prevent it)
   const bool graph = g_use_graphs && ctx->bie_k == k && !prof_active(2) && !prof_active(3);
-  CKR(run_captured(ctx, s, ctx->fgraph, graph, nullptr, 0, 0, k, [&] { return enqueue_factor_mixed(ctx, k, s); }));
+  if (!graph) CKR(phase_events(ctx));
+  CKR(run_captured(ctx, s, ctx->fgraph, graph, nullptr, 0, 0, k,
+                   [&] { return enqueue_factor_mixed(ctx, k, s, !graph); }));
   ctx->Rroot32 = nullptr;
-  ctx->q32_valid = false;
   CKR(check_info(ctx));
+  phase_times(ctx, !graph);
   ctx->k = k;
   ctx->built = true;
   return HS_OK;
@@ -719,7 +808,9 @@ int factor_mixed(hs_ctx* ctx, double k) {
 int factor(hs_ctx* ctx, double k) {
   if (ctx->cfg.precision == HS_MIXED) return factor_mixed(ctx, k);
   cudaStream_t s = ctx->stream;
+  CKR(phase_events(ctx));
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
+  CK(cudaEventRecord(ctx->ph_ev[0], s));
   Phase ph("hs_factor_fp64");
   for (int l0 = 0; l0 < ctx->nleaf; l0 += ctx->chunk) {
     int n = std::min(ctx->chunk, ctx->nleaf - l0);
@@ -734,6 +825,7 @@ int factor(hs_ctx* ctx, double k) {
       Rc = L.R;
     }
   }
+  CK(cudaEventRecord(ctx->ph_ev[1], s));
   Phase pr("hs_root_coupling");
   const int nb = ctx->B.nb;
   permute_square<double2>(s, Rc, ctx->d_root_of_bie, nb, ctx->d_Rb);  // root map in boundary-node order
@@ -748,8 +840,10 @@ int factor(hs_ctx* ctx, double k) {
   gemm<double2, double2, double2>(s, OP_N, OP_N, nb, nb, nb, make_double2(-1, 0), ctx->d_B2, nb, 0, ctx->Rroot, nb, 0,
                                   make_double2(1, 0), ctx->d_C, nb, 0, 1);
   lu_factor<double2>(s, ctx->d_C, nb, 0, nb, ctx->d_Cpiv, 0, ctx->d_info, 1);
+  CK(cudaEventRecord(ctx->ph_ev[2], s));
   CK(cudaGetLastError());
   CKR(check_info(ctx));
+  phase_times(ctx, true);
   ctx->k = k;
   ctx->built = true;
   return HS_OK;
@@ -1060,47 +1154,160 @@ size_t fields_and_adjoint_bytes(hs_ctx* ctx, int M, int P) {
 }
 
 
-// Mixed precision: the FP32 leaf adjoint operator Q = 2 i eta A_ii^{-T} N_i^T K^{-T}
-// from the FP32 leaf factors the build keeps (A_ii^{-1}, N_i, K^{-1}); W goes
-// through the leaf scratch NiT, which the mixed path only uses inside the build.
-int ensure_q32(hs_ctx* ctx, cudaStream_t s) {
-  if (ctx->q32_valid) return HS_OK;
-  const int nl = ctx->nleaf;
-  if (!ctx->d_Q32) CKR(dalloc(ctx, &ctx->d_Q32, (size_t)nl * NI * NE));
-  auto& w = ctx->ws32;
-  gemm<float, float, float>(s, OP_T, OP_T, NI, NE, NI, 1.f, w.Ainv, NI, (long long)NI * NI, w.Ni, NI,
-                            (long long)NE * NI, 0.f, w.NiT, NE, (long long)NI * NE, nl);
-  gemm<float, float2, float2>(s, OP_N, OP_T, NI, NE, NE, make_float2(0.f, (float)(2.0 * ctx->k)), w.NiT, NE,
-                              (long long)NI * NE, w.Kinv, NE, (long long)NE * NE, make_float2(0.f, 0.f), ctx->d_Q32,
-                              NE, (long long)NI * NE, nl);
-  ctx->q32_valid = true;
+size_t mixed_adjoint_bytes(hs_ctx* ctx, int P) {
+  const size_t nb = ctx->B.nb, nl = ctx->nleaf;
+  size_t b = Arena::bytes(nl * NL * P, 8) + 2 * Arena::bytes(field_buf_elems(ctx, P), 8) +
+             3 * Arena::bytes(nb * P, 8) + Arena::bytes(nl * NI * P, 8) + Arena::bytes(nl * NE * P, 8) +
+             Arena::bytes((size_t)ctx->if_rows * P, 16) + Arena::bytes(nb * P, 16) + Arena::bytes(2 * nb * P, 16) +
+             Arena::bytes(8, 8);
+  for (auto& L : ctx->levels) b += Arena::bytes((size_t)L.nbox * 2 * L.ni * P, 8);
+  return b;
+}
+
+// Mixed precision: the adjoint fields Z = A^{-T} L of the receiver functionals
+// (Theorem 3.2's w_p, discretely: L_p reads u_far(p) = A2[p] . [u; d_n u] on
+// the boundary) at every interior leaf node, FP64-accurate, by iterative
+// refinement in the row space of the discrete system: each pass computes the
+// FP64 residual L - A^T Y of every unknown (adjoint_residual: the transposed
+// PDE, interface and exterior rows) and solves the transposed FP32 system for
+// the correction.  That FP32 solve is the exact transpose of the forward
+// correction solve of mixed_solve, step by step in reverse order:
+//   leaf solution operators        lambda = Y32^T g
+//   downward sweep (transposed)    per level from the leaves up: MU = interface
+//                                  part of the children's lambda, parent
+//                                  lambda = exterior part + [X; Z]^T MU
+//   root                           Yext = C^{-T} lambda_root (C^{-1} kept
+//                                  explicitly), root h-adjoint = B2^T Yext
+//   upward pass (transposed)       per level from the root down (MU preloaded),
+//                                  giving the s_a, s_b adjoints of that level
+//   leaf particular (transposed)   Ypde = A_ii^{-T} (g_i + N_i^T (-K^{-T}
+//                                  (g_e - X^T g_i - 2 i eta h-adjoint)))
+// Stops like the forward refinement, on the relative change of Ypde (the
+// adjoint the Jacobian and the gradient use): once two changes give the
+// contraction rate rho, the error estimate is the change times rho / (1 - rho).
+// Z64: [leaf][196][P] (FP64, output).  A2: [P][2 nb] FP64.
+int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2* Z64, Arena& a) {
+  const int nb = ctx->B.nb, nl = ctx->nleaf, nlev = (int)ctx->levels.size();
+  const size_t nbP = (size_t)nb * P;
+  const double eta = ctx->k;
+  const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-9;
+  const int max_iter = ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
+  const float2 one = make_float2(1.f, 0.f), mone = make_float2(-1.f, 0.f), zero = make_float2(0.f, 0.f);
+  float2* G = a.get<float2>((size_t)nl * NL * P);
+  float2 *bufA = a.get<float2>(field_buf_elems(ctx, P)), *bufB = a.get<float2>(field_buf_elems(ctx, P));
+  float2 *r32 = a.get<float2>(nbP), *f32 = a.get<float2>(nbP), *t32 = a.get<float2>(nbP);
+  float2* dY = a.get<float2>((size_t)nl * NI * P);
+  float2* tE = a.get<float2>((size_t)nl * NE * P);
+  double2* Yif = a.get<double2>((size_t)ctx->if_rows * P);
+  double2* Yext = a.get<double2>(nbP);
+  double2* V = a.get<double2>(2 * nbP);
+  double* nrm = a.get<double>(8);
+  std::vector<float2*> MU(nlev);
+  for (int li = 0; li < nlev; ++li) MU[li] = a.get<float2>((size_t)ctx->levels[li].nbox * 2 * ctx->levels[li].ni * P);
+  if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  const LeafScratchT<float>& w = ctx->ws32;
+  const long long sG = (long long)NL * P;
+  Phase ph("hs_adjoint_refine");
+  CK(cudaMemsetAsync(Z64, 0, sizeof(double2) * (size_t)nl * NI * P, s));
+  if (ctx->if_rows > 0) CK(cudaMemsetAsync(Yif, 0, sizeof(double2) * (size_t)ctx->if_rows * P, s));
+  CK(cudaMemsetAsync(Yext, 0, sizeof(double2) * nbP, s));
+  ctx->adj_iters = 0;
+  ctx->adj_update = -1.0;
+  ctx->adj_est = -1.0;
+  double prev_upd = 0.0, y0_n2 = 0.0;
+  bool converged = false;
+  for (int it = 0; it < max_iter; ++it) {
+    Phase pp("hs_adjoint_pass");
+    const bool first = it == 0;
+    // FP64 residual L - A^T Y of every unknown (L itself on the first pass)
+    if (!first)
+      gemm<double2, double2, double2>(s, OP_T, OP_N, 2 * nb, P, nb, make_double2(1, 0), ctx->d_DS, 2 * nb, 0, Yext, P,
+                                      0, make_double2(0, 0), V, P, 0, 1);
+    adjoint_residual(s, Z64, ctx->d_adj_desc, Yif, A2, first ? nullptr : V, ctx->d_q, ctx->d_D1, nl, nb, ctx->k,
+                     ctx->h, eta, P, first, G);
+    // transposed FP32 solve: leaf solution operators, then the transposed
+    // downward sweep from the leaves to the root
+    gemm<float2, float2, float2>(s, OP_T, OP_N, NE, P, NL, one, ctx->d_Y32, NE, (long long)NL * NE, G, P, sG, zero,
+                                 bufA, P, (long long)NE * P, nl);
+    float2 *Lc = bufA, *Lp = bufB;
+    for (int li = 0; li < nlev; ++li) {
+      sweep_adjoint_up_level<float2>(s, ctx->levels[li], ctx->ops32[li], Lc, MU[li], Lp, P);
+      std::swap(Lc, Lp);
+    }
+    // root (boundary-node order): Yext = C^{-T} lambda, h-adjoint = B2^T Yext
+    permute_rows<float2>(s, Lc, ctx->d_root_of_bie, nb, P, r32);
+    gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_Rb32, nb, 0, r32, P, 0, zero, f32, P, 0, 1);
+    gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_B2_32, nb, 0, f32, P, 0, zero, t32, P, 0, 1);
+    permute_rows<float2>(s, t32, ctx->d_bie_of_root, nb, P, Lp);
+    std::swap(Lc, Lp);  // Lc: the root's h-adjoint in root box order
+    // transposed upward pass from the root to the leaves
+    for (int li = nlev - 1; li >= 0; --li) {
+      sweep_adjoint_level<float2>(s, ctx->levels[li], ctx->ops32[li], Lc, MU[li], Lp, P, true, true);
+      iface_adj_add(s, MU[li], ctx->levels[li].nbox, ctx->levels[li].ni, P, Yif + ctx->if_off[li] * P);
+      std::swap(Lc, Lp);
+    }
+    // transposed leaf particular solve (Lc: every leaf's h-adjoint)
+    gemm<float, float2, float2>(s, OP_T, OP_N, NE, P, NI, mone, w.Aie, NE, (long long)NI * NE, G, P, sG, one,
+                                G + (long long)NI * P, P, sG, nl);
+    leaf_hadj(s, Lc, nl, eta, P, G);
+    gemm<float2, float2, float2>(s, OP_T, OP_N, NE, P, NE, mone, w.Kinv, NE, (long long)NE * NE, G + (long long)NI * P,
+                                 P, sG, zero, tE, P, (long long)NE * P, nl);
+    gemm<float, float2, float2>(s, OP_T, OP_N, NI, P, NE, one, w.Ni, NI, (long long)NE * NI, tE, P, (long long)NE * P,
+                                one, G, P, sG, nl);
+    gemm<float, float2, float2>(s, OP_T, OP_N, NI, P, NI, one, w.Ainv, NI, (long long)NI * NI, G, P, sG, zero, dY, P,
+                                (long long)NI * P, nl);
+    // accumulate in FP64; the change of Ypde is the stopping quantity
+    convert_f2d_add(s, dY, Z64, (long long)nl * NI * P);
+    convert_f2d_add(s, f32, Yext, (long long)nbP);
+    CK(cudaMemsetAsync(nrm, 0, sizeof(double), s));
+    norm2_32(s, dY, (long long)nl * NI * P, nrm);
+    double dn2 = 0.0;
+    CK(cudaMemcpyAsync(&dn2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->adj_iters = it + 1;
+    if (first) {
+      y0_n2 = dn2;
+      if (!(y0_n2 > 0.0)) {  // no receiver sees the interior: Z = 0 exactly
+        converged = true;
+        break;
+      }
+    } else {
+      const double upd = std::sqrt(dn2 / y0_n2);
+      double est = upd;
+      if (prev_upd > 0.0 && upd < 0.5 * prev_upd) {
+        const double rho = upd / prev_upd;
+        est = upd * rho / (1.0 - rho);
+      }
+      ctx->adj_update = upd;
+      ctx->adj_est = est;
+      prev_upd = upd;
+      if (est <= tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  if (tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
+  if (!converged) return fail(ctx, HS_ENOCONV, "adjoint refinement did not reach the tolerance");
   return HS_OK;
 }
 
 size_t mixed_fields_bytes(hs_ctx* ctx, int M, int P) {
   const int nb = ctx->B.nb;
-  const size_t nbP = (size_t)nb * P;
   return Arena::bytes((size_t)ctx->nleaf * NL * M, 16) + Arena::bytes((size_t)P * 2 * nb, 16) +
-         2 * Arena::bytes(nbP, 16) + 5 * Arena::bytes(nbP, 8) + 2 * Arena::bytes(field_buf_elems(ctx, P), 8) +
-         Arena::bytes(t3_elems(ctx, P), 8) + Arena::bytes((size_t)ctx->nleaf * NI * P, 8) +
-         Arena::bytes((size_t)ctx->nleaf * NI * P, 16) + mixed_bytes(ctx, M, P);
+         Arena::bytes((size_t)ctx->nleaf * NI * P, 16) +
+         std::max(mixed_bytes(ctx, M, P), mixed_adjoint_bytes(ctx, P));
 }
 
-// Mixed precision: far field F (refined, FP64 accurate), forward fields Ug from
-// the refined FP64 iterate, and adjoint fields Zg from one FP32 transposed
-// sweep of the FP32 factors (not refined: FP32 accuracy), on the interior grid.
+// Mixed precision: far field F and forward fields Ug from the refined forward
+// solve, adjoint fields Zg from the refined adjoint solve (both FP64-accurate),
+// on the interior grid.
 int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P,
                              double2* F, double2* Ug, double2* Zg, Arena& a) {
   const int nb = ctx->B.nb;
-  const size_t nbP = (size_t)nb * P;
   double2* X = a.get<double2>((size_t)ctx->nleaf * NL * M);
   double2* A2 = a.get<double2>((size_t)P * 2 * nb);
-  double2 *E = a.get<double2>(nbP), *CP = a.get<double2>(nbP);
-  float2 *E32 = a.get<float2>(nbP), *CP32 = a.get<float2>(nbP), *Gr = a.get<float2>(nbP), *G = a.get<float2>(nbP),
-         *CPs = a.get<float2>(nbP);
-  float2 *bufA = a.get<float2>(field_buf_elems(ctx, P)), *bufB = a.get<float2>(field_buf_elems(ctx, P));
-  float2* MU = a.get<float2>(t3_elems(ctx, P));
-  float2* Z32 = a.get<float2>((size_t)ctx->nleaf * NI * P);
   double2* Z64 = a.get<double2>((size_t)ctx->nleaf * NI * P);
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   {
@@ -1108,48 +1315,24 @@ int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, 
     CKR(mixed_solve(ctx, s, alphas, M, thetas, P, F, X, sub));
   }
   leaf_to_grid(s, X, NL, ctx->nL, M, Ug);
-  CKR(ensure_q32(ctx, s));
-  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-  Phase ph("hs_adjoint_sweep32");
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
-  adjoint_root_init(s, nb, P, ctx->k, A2, E, CP);
-  convert_d2f(s, E, E32, (long long)nbP);
-  convert_d2f(s, CP, CP32, (long long)nbP);
-  // CP += R_root^T E with R_root in boundary-node order = Pi R_c Pi^T (R_c in root box order)
-  permute_rows<float2>(s, E32, ctx->d_bie_of_root, nb, P, Gr);
-  const float2* Rc = ctx->ops32.empty() ? ctx->d_R32 : ctx->ops32.back().R;  // a single leaf has no merges
-  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, Rc, nb, 0, Gr, P, 0, zero, G, P, 0, 1);
-  permute_rows<float2>(s, G, ctx->d_root_of_bie, nb, P, Gr);
-  // CPs = C^{-T} (CP + G): C^{-1} is kept explicitly in d_Rb32 by the mixed build
-  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_Rb32, nb, 0, CP32, P, 0, zero, CPs, P, 0, 1);
-  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_Rb32, nb, 0, Gr, P, 0, one, CPs, P, 0, 1);
-  // E += B2^T CPs, then to root box order
-  gemm<float2, float2, float2>(s, OP_T, OP_N, nb, P, nb, one, ctx->d_B2_32, nb, 0, CPs, P, 0, one, E32, P, 0, 1);
-  permute_rows<float2>(s, E32, ctx->d_bie_of_root, nb, P, bufB);
-  const float2* Lp = bufB;
-  float2* out = bufA;
-  for (int li = (int)ctx->levels.size() - 1; li >= 0; --li) {
-    sweep_adjoint_level<float2>(s, ctx->levels[li], ctx->ops32[li], Lp, MU, out, P, true);
-    Lp = out;
-    out = (out == bufA) ? bufB : bufA;
+  {
+    Arena sub = a;
+    CKR(mixed_adjoint(ctx, s, A2, P, Z64, sub));
   }
-  gemm<float2, float2, float2>(s, OP_N, OP_N, NI, P, NE, one, ctx->d_Q32, NE, (long long)NI * NE, Lp, P,
-                               (long long)NE * P, zero, Z32, P, (long long)NI * P, ctx->nleaf);
-  const long long nz = (long long)ctx->nleaf * NI * P;
-  CK(cudaMemsetAsync(Z64, 0, sizeof(double2) * nz, s));
-  convert_f2d_add(s, Z32, Z64, nz);
   leaf_to_grid(s, Z64, NI, ctx->nL, P, Zg);
   CK(cudaGetLastError());
   return HS_OK;
 }
 
-// Mixed precision: J in complex FP32 on the tensor cores from the refined
-// forward fields and the FP32 adjoint fields, widened into the FP64 output.
+// Mixed precision: J from the refined forward fields and the refined adjoint
+// fields (both FP64-accurate), contracted in FP64 like the FP64 context's.
+// F (optional, M x P) receives the refined far field of the same solve.
 int jacobian_into_mixed(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P,
-                        double2* J, Arena& a) {
-  const int nX = ctx->n14, S1 = ctx->S1, S2 = ctx->S2, nm = S1 * S2;
+                        double2* J, Arena& a, double2* F_out = nullptr) {
+  const int nX = ctx->n14, S1 = ctx->S1, S2 = ctx->S2;
   const size_t plane = (size_t)nX * nX, MP = (size_t)M * P;
-  const int C = contract_chunk(M, P, nX, S1, g_contract_budget / 2);
+  const int C = contract_chunk(M, P, nX, S1, g_contract_budget);
   double2* Ug = a.get<double2>(plane * M);
   double2* Zg = a.get<double2>(plane * P);
   double2* F = a.get<double2>(MP);
@@ -1158,31 +1341,27 @@ int jacobian_into_mixed(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M
     Arena sub = a;
     CKR(mixed_fields_and_adjoint(ctx, s, alphas, M, thetas, P, F, Ug, Zg, sub));
   }
-  float2* J32 = a.get<float2>(MP * nm);
-  float2* sxc = a.get<float2>((size_t)nX * S1);
-  float* sy32 = a.get<float>((size_t)nX * S2);
-  float2* W = a.get<float2>(plane * C);
-  float2* T = a.get<float2>((size_t)nX * S1 * C);
+  if (F_out) CK(cudaMemcpyAsync(F_out, F, sizeof(double2) * MP, cudaMemcpyDeviceToDevice, s));
+  double2* W = a.get<double2>(plane * C);
+  double2* T = a.get<double2>((size_t)nX * S1 * C);
+  const size_t ozb = g_oz_enabled ? contract_emulated_bytes(C, nX, S1, S2) : 0;
+  char* oz = ozb ? a.get<char>(ozb) : nullptr;
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   interior_sine_tables(s, ctx->d_xint, nX, S1, S2, ctx->d_sxi, ctx->d_syi);
-  Phase ph("hs_jacobian32");
-  contract_jacobian32(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, ctx->k * ctx->k, J32, sxc, sy32, W, T, C);
-  CK(cudaMemsetAsync(J, 0, sizeof(double2) * MP * nm, s));
-  convert_f2d_add(s, J32, J, (long long)(MP * nm));
+  Phase ph("hs_jacobian_contract");
+  contract_jacobian(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, ctx->k * ctx->k, J, W, T, C, oz, ozb);
   CK(cudaGetLastError());
-  if (tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
   return HS_OK;
 }
 
 size_t jacobian_bytes_mixed(hs_ctx* ctx, int M, int P) {
   const int nX = ctx->n14;
-  const size_t plane = (size_t)nX * nX, MP = (size_t)M * P, nm = (size_t)ctx->S1 * ctx->S2;
-  const int C = contract_chunk(M, P, nX, ctx->S1, g_contract_budget / 2);
+  const size_t plane = (size_t)nX * nX, MP = (size_t)M * P;
+  const int C = contract_chunk(M, P, nX, ctx->S1, g_contract_budget);
+  const size_t ozb = g_oz_enabled ? contract_emulated_bytes(C, nX, ctx->S1, ctx->S2) : 0;
   return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) + Arena::bytes(MP, 16) +
          std::max(mixed_fields_bytes(ctx, M, P),
-                  Arena::bytes(MP * nm, 8) + Arena::bytes((size_t)nX * ctx->S1, 8) +
-                      Arena::bytes((size_t)nX * ctx->S2, 4) + Arena::bytes(plane * C, 8) +
-                      Arena::bytes((size_t)nX * ctx->S1 * C, 8));
+                  Arena::bytes(plane * C, 16) + Arena::bytes((size_t)nX * ctx->S1 * C, 16) + Arena::bytes(ozb, 1));
 }
 
 int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* J,
@@ -1199,10 +1378,13 @@ int jacobian_into(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, cons
   }
   double2* W = a.get<double2>(plane * C);
   double2* T = a.get<double2>((size_t)ctx->n14 * ctx->S1 * C);
+  const size_t ozb = g_oz_enabled ? contract_emulated_bytes(C, ctx->n14, ctx->S1, ctx->S2) : 0;
+  char* oz = ozb ? a.get<char>(ozb) : nullptr;
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   interior_sine_tables(s, ctx->d_xint, ctx->n14, ctx->S1, ctx->S2, ctx->d_sxi, ctx->d_syi);
   Phase ph("hs_jacobian_contract");
-  contract_jacobian(s, Ug, Zg, M, P, ctx->n14, ctx->d_sxi, ctx->d_syi, ctx->S1, ctx->S2, ctx->k * ctx->k, J, W, T, C);
+  contract_jacobian(s, Ug, Zg, M, P, ctx->n14, ctx->d_sxi, ctx->d_syi, ctx->S1, ctx->S2, ctx->k * ctx->k, J, W, T, C,
+                    oz, ozb);
   CK(cudaGetLastError());
   return HS_OK;
 }
@@ -1211,8 +1393,10 @@ size_t jacobian_bytes(hs_ctx* ctx, int M, int P) {
   if (ctx->cfg.precision == HS_MIXED) return jacobian_bytes_mixed(ctx, M, P);
   const size_t plane = (size_t)ctx->n14 * ctx->n14;
   const int C = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget);
+  const size_t ozb = g_oz_enabled ? contract_emulated_bytes(C, ctx->n14, ctx->S1, ctx->S2) : 0;
   return Arena::bytes(plane * M, 16) + Arena::bytes(plane * P, 16) +
-         std::max(Arena::bytes(plane * C, 16) + Arena::bytes((size_t)ctx->n14 * ctx->S1 * C, 16),
+         std::max(Arena::bytes(plane * C, 16) + Arena::bytes((size_t)ctx->n14 * ctx->S1 * C, 16) +
+                      Arena::bytes(ozb, 1),
                   fields_and_adjoint_bytes(ctx, M, P));
 }
 
@@ -1561,10 +1745,10 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
                double lambda_rel, double* c_inout, double* resid_norm_out) {
   CKR(check_ctx(ctx, true));
   LaunchScope ls(ctx);
-  CKR(need_fp64(ctx));
   CKR(valid_angles(ctx, M, P));
   if (!data || !alphas || !thetas || !c_inout) return fail(ctx, HS_EINVAL, "NULL pointer");
   if (!(lambda_rel >= 0.0) || !std::isfinite(lambda_rel)) return fail(ctx, HS_EINVAL, "lambda_rel must be >= 0");
+  const bool mixed = ctx->cfg.precision == HS_MIXED;
   cudaStream_t s = ctx->stream;
   const int MP = M * P, nm = ctx->S1 * ctx->S2;
   Arena a;
@@ -1572,6 +1756,7 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
                 Arena::bytes(MP, 16) * 2 + Arena::bytes((size_t)2 * MP, 8) + Arena::bytes(8, 8) +
                 Arena::bytes((size_t)MP * nm, 16) + Arena::bytes((size_t)2 * MP * nm, 8) +
                 Arena::bytes((size_t)nm * nm, 8) + Arena::bytes(nm, 8) + Arena::bytes(nm, 4) +
+                (g_oz_enabled ? Arena::bytes(normal_matrix_emulated_bytes(2 * MP, nm), 1) : 0) +
                 std::max(jacobian_bytes(ctx, M, P),
                          4 * Arena::bytes((size_t)ctx->B.nb * M, 16) + Arena::bytes((size_t)2 * ctx->B.nb * M, 16) +
                              Arena::bytes((size_t)P * 2 * ctx->B.nb, 16));
@@ -1588,12 +1773,17 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
   double* A = a.get<double>((size_t)nm * nm);
   double* bv = a.get<double>(nm);
   int* piv = a.get<int>(nm);
+  const size_t ozb = g_oz_enabled ? normal_matrix_emulated_bytes(2 * MP, nm) : 0;
+  char* oz = ozb ? a.get<char>(ozb) : nullptr;
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
   CK(cudaMemcpyAsync(da, alphas, sizeof(double) * M, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
-  {
+  if (mixed) {  // refined far field, forward and adjoint fields from one call
+    CKR(jacobian_into_mixed(ctx, s, da, M, dt, P, J, a, F));
+    residual(s, ddata, F, MP, res, rst, nrm2);
+  } else {
     Arena sub = a;  // the forward solve's scratch is reused by the Jacobian afterwards
     const int nb = ctx->B.nb;
     double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);
@@ -1605,13 +1795,23 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M, con
     farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, dt, P, A2);
     gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, make_double2(1, 0), PS, M, 0, A2, 2 * nb, 0,
                                     make_double2(0, 0), F, P, 0, 1);
+    residual(s, ddata, F, MP, res, rst, nrm2);
+    CKR(jacobian_into(ctx, s, da, M, dt, P, J, a));
   }
-  residual(s, ddata, F, MP, res, rst, nrm2);
-  CKR(jacobian_into(ctx, s, da, M, dt, P, J, a));
-  // normal equations in the real coefficients: A = Jst^T Jst, b = Jst^T rst
-  split_stack(s, J, MP, nm, Jst);
-  normal_matrix(s, Jst, 2 * MP, nm, A);
-  gemm<double, double, double>(s, OP_T, OP_N, nm, 1, 2 * MP, 1.0, Jst, nm, 0, rst, 1, 0, 0.0, bv, 1, 0, 1);
+  // normal equations in the real coefficients: A = Jst^T Jst, b = Jst^T rst (with the
+  // emulated FP64 product the stack is formed transposed, Jst^T, its natural operand)
+  bool emulated = false;
+  if (oz) {
+    split_stack_t(s, J, MP, nm, Jst);
+    emulated = normal_matrix_emulated(s, Jst, 2 * MP, nm, A, oz, ozb);
+    if (emulated)
+      gemm<double, double, double>(s, OP_N, OP_N, nm, 1, 2 * MP, 1.0, Jst, 2 * MP, 0, rst, 1, 0, 0.0, bv, 1, 0, 1);
+  }
+  if (!emulated) {
+    split_stack(s, J, MP, nm, Jst);
+    normal_matrix(s, Jst, 2 * MP, nm, A);
+    gemm<double, double, double>(s, OP_T, OP_N, nm, 1, 2 * MP, 1.0, Jst, nm, 0, rst, 1, 0, 0.0, bv, 1, 0, 1);
+  }
   add_lambda(s, A, nm, lambda_rel);
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
   lu_factor<double>(s, A, nm, 0, nm, piv, 0, ctx->d_info, 1);
@@ -1886,6 +2086,21 @@ int hs_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update, dou
   return HS_OK;
 }
 
+int hs_build_phase_ms(const hs_ctx* ctx, double* interior_ms, double* boundary_ms) {
+  if (!ctx) return HS_EINVAL;
+  if (interior_ms) *interior_ms = ctx->t_interior;
+  if (boundary_ms) *boundary_ms = ctx->t_bdry;
+  return HS_OK;
+}
+
+int hs_adjoint_refine_stats(const hs_ctx* ctx, int* iterations, double* last_update, double* est_error) {
+  if (!ctx) return HS_EINVAL;
+  if (iterations) *iterations = ctx->adj_iters;
+  if (last_update) *last_update = ctx->adj_update;
+  if (est_error) *est_error = ctx->adj_est;
+  return HS_OK;
+}
+
 const char* hs_last_error(const hs_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
 void hs_destroy(hs_ctx* ctx) {
@@ -1895,6 +2110,8 @@ void hs_destroy(hs_ctx* ctx) {
   ctx->fgraph.reset();
   ctx->pgraph[0].reset();
   ctx->pgraph[1].reset();
+  for (auto& e : ctx->ph_ev)
+    if (e) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->ws_base) cudaFree(ctx->ws_base);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

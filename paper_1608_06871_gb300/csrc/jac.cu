@@ -91,11 +91,20 @@ __global__ void k_khatri_rao(const double2* __restrict__ Ug, const double2* __re
   W[e] = make_double2(u.x * z.x - u.y * z.y, u.x * z.y + u.y * z.x);
 }
 
+// Scratch of the emulated products of a chunk of C pairs (the slices of its
+// Khatri-Rao rows for the x-projection, then of its half-projected rows).
+size_t contract_emulated_bytes(int C, int nX, int S1, int S2) {
+  return std::max(ozaki_scratch_bytes(2 * C * nX, S1, nX, 1, true), ozaki_scratch_bytes(2 * S1, S2, nX, C, true));
+}
+
 int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes) {
   const size_t per = 16 * ((size_t)nX * nX + (size_t)nX * S1);
   long long c = (long long)(budget_bytes / per);
-  // the second product is a batch of C launches' worth of grid.z
-  return (int)std::max<long long>(1, std::min<long long>({c, (long long)M * P, 32768LL}));
+  // the second product is a batch of C launches' worth of grid.z; the emulated
+  // x-projection has 2 nX / 128 row tiles per pair in grid.y
+  long long cap = 32768;
+  if (g_oz_enabled) cap = std::min<long long>(cap, 65535LL * 128 / (2LL * nX));
+  return (int)std::max<long long>(1, std::min<long long>({c, (long long)M * P, cap}));
 }
 
 // J[(d,p)][m1][m2] = k2 sum_gy sy[m2][gy] sum_gx sx[m1][gx] u_d[gy][gx] z_p[gy][gx],
@@ -103,18 +112,40 @@ int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes) {
 // T = W sx^T over gx (rows (pair, gy), one GEMM), then J_pair = T_pair^T sy^T
 // over gy (a batch of S1 x S2 products).  W holds C*nX*nX and T C*nX*S1
 // complex values.
+// With the emulated FP64 product (g_oz_enabled) both projections run on the
+// tensor cores: complex rows are read as pairs of real rows (re, im), and the
+// sine tables are the transposed right operands; scratch (after T) holds the
+// slices, contract_emulated_bytes(C, nX, S1, S2) bytes.
 void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
-                       const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C) {
+                       const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C,
+                       void* scratch, size_t scratch_bytes) {
   const long long plane = (long long)nX * nX, MP = (long long)M * P;
   for (long long c0 = 0; c0 < MP; c0 += C) {
     const int nc = (int)std::min<long long>(C, MP - c0);
     const long long n = nc * plane;
     k_khatri_rao<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ug, Zg, P, plane, c0, n, W);
     HS_COUNT_LAUNCH();
-    gemm<double2, double, double2>(s, OP_N, OP_T, nc * nX, S1, nX, make_double2(1.0, 0.0), W, nX, 0, sx, nX, 0,
-                                   make_double2(0.0, 0.0), T, S1, 0, 1);
-    gemm<double2, double, double2>(s, OP_T, OP_T, S1, S2, nX, make_double2(k2, 0.0), T, S1, (long long)nX * S1, sy,
-                                   nX, 0, make_double2(0.0, 0.0), J + c0 * S1 * S2, S2, (long long)S1 * S2, nc);
+    bool done = false;
+    if (g_oz_enabled && scratch) {
+      double* Wd = reinterpret_cast<double*>(W);
+      double* Td = reinterpret_cast<double*>(T);
+      double* Jd = reinterpret_cast<double*>(J + c0 * S1 * S2);
+      // T[(pair, gy)][m1] = sum_gx W[(pair, gy)][gx] sx[m1][gx]
+      const OzView vw{Wd, 0, 2LL * nX, 1, 2, 2}, vsx{const_cast<double*>(sx), 0, nX, 0, 1, 1},
+          vt{Td, 0, 2LL * S1, 1, 2, 2};
+      // J_pair[m1][m2] = k2 sum_gy T_pair[gy][m1] sy[m2][gy]
+      const OzView vtt{Td, 2LL * nX * S1, 2, 1, 2LL * S1, 2}, vsy{const_cast<double*>(sy), 0, nX, 0, 1, 1},
+          vj{Jd, 2LL * S1 * S2, 2LL * S2, 1, 2, 2};
+      done = ozaki_gemm(s, 2 * nc * nX, S1, nX, 1, 1.0, vw, vsx, true, 0.0, vt, scratch, scratch_bytes) ==
+                 cudaSuccess &&
+             ozaki_gemm(s, 2 * S1, S2, nX, nc, k2, vtt, vsy, true, 0.0, vj, scratch, scratch_bytes) == cudaSuccess;
+    }
+    if (!done) {
+      gemm<double2, double, double2>(s, OP_N, OP_T, nc * nX, S1, nX, make_double2(1.0, 0.0), W, nX, 0, sx, nX, 0,
+                                     make_double2(0.0, 0.0), T, S1, 0, 1);
+      gemm<double2, double, double2>(s, OP_T, OP_T, S1, S2, nX, make_double2(k2, 0.0), T, S1, (long long)nX * S1, sy,
+                                     nX, 0, make_double2(0.0, 0.0), J + c0 * S1 * S2, S2, (long long)S1 * S2, nc);
+    }
   }
 }
 
@@ -298,6 +329,40 @@ void split_stack(cudaStream_t s, const double2* J, int rows, int cols, double* J
   long long n = (long long)rows * cols;
   k_split_stack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(J, rows, cols, Jst);
   HS_COUNT_LAUNCH();
+}
+
+// JstT = [Re J; Im J]^T (cols x 2 rows) through 32 x 32 shared-memory tiles:
+// reads along the columns of J, writes along the rows of JstT.
+__global__ void k_split_stack_t(const double2* __restrict__ J, int rows, int cols, double* __restrict__ JstT) {
+  __shared__ double2 t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = J[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) {
+      const double2 v = t[threadIdx.x][i];
+      JstT[(long long)c * 2 * rows + r] = v.x;
+      JstT[(long long)c * 2 * rows + rows + r] = v.y;
+    }
+  }
+}
+
+void split_stack_t(cudaStream_t s, const double2* J, int rows, int cols, double* JstT) {
+  dim3 g((cols + 31) / 32, (rows + 31) / 32);
+  k_split_stack_t<<<g, dim3(32, 8), 0, s>>>(J, rows, cols, JstT);
+  HS_COUNT_LAUNCH();
+}
+
+size_t normal_matrix_emulated_bytes(int rows, int n) { return ozaki_scratch_bytes(n, n, rows, 1, false); }
+
+// A = JstT JstT^T (n x n) for JstT (n x rows) by the emulated FP64 product.
+bool normal_matrix_emulated(cudaStream_t s, double* JstT, int rows, int n, double* A, void* scratch, size_t bytes) {
+  const OzView v{JstT, 0, rows, 0, 1, 1}, c{A, 0, n, 0, 1, 1};
+  return ozaki_gemm(s, n, n, rows, 1, 1.0, v, v, true, 0.0, c, scratch, bytes) == cudaSuccess;
 }
 
 // A[r][c] = A[c][r] for the entries above the computed block-lower part

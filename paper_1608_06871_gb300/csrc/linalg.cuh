@@ -52,9 +52,28 @@ extern bool g_tc_enabled;
 bool cgemm_tc_eligible(int opA, int opB, int m, int n, int k, int batch);
 void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A, int lda, long long sA,
               const float2* B, int ldb, long long sB, float2 beta, float2* C, int ldc, long long sC, int batch);
-// Synchronises s, then reads and clears this device's flag that a bounded
-// tensor-core wait gave up.
+// Synchronises s, then reads and clears this device's flags that a bounded
+// tensor-core wait gave up (the complex FP32 GEMM's and the emulated-FP64 one's).
 bool tc_timed_out(cudaStream_t s);
+bool oz_timed_out(cudaStream_t s);
 cudaError_t tc_raise_timeout_flag();
+
+// FP64 products on the tensor cores by exact BF16 slices (ozaki.cu).  A strided
+// FP64 view: element (b, i, k) at p[b sb + (i / ig) si + (i % ig) sg + k sk]
+// (ig = 2 reads the real and imaginary parts of complex rows as two real rows).
+struct OzView {
+  double* p;
+  long long sb, si, sg, sk;
+  int ig;
+};
+extern bool g_oz_enabled;
+// Scratch bytes of ozaki_gemm for these sizes.
+size_t ozaki_scratch_bytes(int m, int n, int k, int batch, bool b_shared);
+// C[b] = alpha A[b] B[b] + beta C[b] (m x n, k inner; beta = 0 never reads C)
+// with A given row-wise (A(b, i, kk)) and B by its transpose Bt(b, j, kk);
+// b_shared: one B for every batch.  Returns cudaErrorNotSupported when the
+// tensor-map encoder is unavailable, cudaErrorInvalidValue on bad sizes.
+cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double alpha, OzView A, OzView Bt,
+                       bool b_shared, double beta, OzView C, void* scratch, size_t scratch_bytes);
 
 }  // namespace hs

@@ -1,0 +1,392 @@
+// FP64 matrix products on the 5th-generation tensor cores by exact integer
+// slices (error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump,
+// 2012, with row / column scaling as in Ozaki, Uchino and Imamura's later
+// variants), for the FP64 contractions of the Jacobian.
+//
+// C = alpha A B (+ beta C), A m x k and B k x n real FP64.  Every row i of A
+// is scaled by 2^-ea_i so that its largest entry lies in [1/2, 1), every
+// column j of B by 2^-eb_j, and the scaled values are split exactly into
+// S = 8 slices of beta = 7 bits:
+//   x 2^-e = sum_s a_s 2^(-7 (s + 1)) + tail,  a_0 in [-128, 128], a_s in [-64, 64],
+// each an integer, hence exact in BF16.  The product of two slices is then an
+// exact integer matrix; summed in FP32 it stays exact while every partial sum
+// is an integer below 2^24.  The anti-diagonal d = s + t of the slice pairs
+// (s + t <= 7: 36 pairs) carries the weight 2^(-7 (d + 2)), so the pairs of one
+// diagonal accumulate into one FP32 accumulator in tensor memory:
+//   |partial sum| <= K 4096 (d + 3) < 2^24  for K <= 384,
+// which bounds the k extent of one launch (the host splits longer products
+// and accumulates the pieces in FP64).  The epilogue recombines the 8 diagonal
+// sums exactly in 64-bit integers (two groups of four, < 2^46 each) and rounds
+// once to FP64.  What is dropped is the pairs with s + t >= 8, below
+// 2^-55 k max|A_i.| max|B_.j| per entry, and one FP64 rounding per piece: the
+// result stays within the FP64 product's own bound 2 k u |A| |B|.
+//
+// Kernel: one CTA per 128 x 64 output tile; warp 0 loads slice tiles with TMA
+// (cp.async.bulk.tensor, three-dimensional maps over [slice][row][k]) into a
+// two-stage ring, warp 1 issues the tcgen05 BF16 MMAs (M = 128, N = 64,
+// K = 16; 72 per stage of 32 k) into the eight diagonal accumulators (all
+// 512 TMEM columns), warps 2..5 read them back.  Every mbarrier wait is
+// bounded; a timeout sets the library's tensor-core timeout flag.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "linalg.cuh"
+
+namespace hs {
+
+bool prof_active(int family);
+void prof_begin(cudaStream_t s, cudaEvent_t* a);
+void prof_end(cudaStream_t s, cudaEvent_t a, double flops);
+
+// Set to 1 by an emulated-FP64 product whose bounded mbarrier wait gave up
+// (read and cleared by tc_timed_out with the tensor-core GEMM's own flag).
+__device__ int g_oz_timeout = 0;
+
+namespace {
+
+constexpr int OZ_S = 8;          // slices per operand
+constexpr int OZ_ND = 8;         // anti-diagonals kept (s + t <= 7)
+constexpr int OZ_TM = 128;       // rows per tile
+constexpr int OZ_TN = 64;        // columns per tile
+constexpr int OZ_KS = 32;        // k per stage
+constexpr int OZ_KMAX = 384;     // k per launch keeping every diagonal sum below 2^24
+constexpr int OZ_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int OZ_A_KB = OZ_S * OZ_TM * 16;  // bytes of one 8-wide k block of all A slices (16 KB)
+constexpr int OZ_B_KB = OZ_S * OZ_TN * 16;  // same for B (8 KB)
+constexpr int OZ_STAGE = (OZ_KS / 8) * (OZ_A_KB + OZ_B_KB);  // 96 KB
+constexpr int OZ_SMEM = 2 * OZ_STAGE + 1024;
+constexpr long long OZ_WAIT = 1LL << 26;
+// instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
+constexpr uint32_t OZ_IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(OZ_TM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, no swizzle: core matrices of 8 rows x 16 bytes; lbo = bytes between
+// k-adjacent core matrices, sbo = bytes between 8-row groups.
+__device__ __forceinline__ uint64_t oz_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < OZ_WAIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void oz_tma3(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void oz_ld16(uint32_t ta, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(ta));
+}
+
+// Element (b, i, k) of a strided FP64 view.
+__device__ __forceinline__ long long vaddr(const OzView& v, long long b, long long i, long long k) {
+  return b * v.sb + (i / v.ig) * v.si + (i % v.ig) * v.sg + k * v.sk;
+}
+
+// Slices of the rows of a view (rows = A's rows, or B's columns): one warp
+// per row, lanes along k; slices written to out[s][b * rpad + i][kk] (BF16,
+// kpad wide, zero padded), the row's exponent to e[b * rpad + i].  Padding
+// rows get zero slices.
+__global__ void k_oz_slice(OzView v, int rows, int k, int rpad, int kpad, int batch, __nv_bfloat16* __restrict__ out,
+                           int* __restrict__ e) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)batch * rpad;
+  if (r >= total) return;
+  const long long b = r / rpad;
+  const int i = (int)(r % rpad);
+  const long long plane = total * kpad;
+  __nv_bfloat16* o = out + r * kpad;
+  const bool live = i < rows;
+  double mx = 0.0;
+  if (live)
+    for (int kk = lane; kk < k; kk += 32) mx = fmax(mx, fabs(v.p[vaddr(v, b, i, kk)]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const int ex = mx > 0.0 ? ilogb(mx) + 1 : 0;  // mx 2^-ex in [1/2, 1)
+  if (lane == 0) e[r] = ex;
+  for (int kk = lane; kk < kpad; kk += 32) {
+    double x = (live && kk < k) ? scalbn(v.p[vaddr(v, b, i, kk)], -ex) : 0.0;
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const double t = x * 128.0;  // exact
+      const double a = rint(t);    // |a| <= 128 (s = 0), <= 64 after
+      x = t - a;                  // exact
+      o[s * plane + kk] = __float2bfloat16_rn((float)a);
+    }
+  }
+}
+
+struct OzParams {
+  int m, n, k, mpad, npad, kpad, nb_batch_b;  // nb_batch_b: 0 when B is shared by every batch
+  double alpha, beta;
+  const int* ea;
+  const int* eb;
+  OzView C;
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzParams P) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint32_t tslot;
+  __shared__ __align__(8) uint64_t full[2], empty[2], done;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.z;
+  const int tm = blockIdx.y, tn = blockIdx.x;
+  const int rowA = b * P.mpad + tm * OZ_TM;
+  const int rowB = (P.nb_batch_b ? b : 0) * P.npad + tn * OZ_TN;
+  const int nst = P.kpad / OZ_KS;
+
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&empty[i])), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&done)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      for (int i = 0; i < nst && ok; ++i) {
+        const int st = i & 1;
+        if (i >= 2) ok = oz_wait(su32(&empty[st]), ((i >> 1) - 1) & 1);
+        if (!ok) break;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[st])), "r"(OZ_STAGE)
+                     : "memory");
+        const uint32_t base = su32(sm + st * OZ_STAGE);
+        for (int kb = 0; kb < OZ_KS / 8; ++kb) {
+          const int kx = i * OZ_KS + kb * 8;
+          oz_tma3(base + kb * OZ_A_KB, &mapA, kx, rowA, 0, su32(&full[st]));
+          oz_tma3(base + (OZ_KS / 8) * OZ_A_KB + kb * OZ_B_KB, &mapB, kx, rowB, 0, su32(&full[st]));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      for (int i = 0; i < nst && ok; ++i) {
+        const int st = i & 1;
+        ok = oz_wait(su32(&full[st]), (i >> 1) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t aB = su32(sm + st * OZ_STAGE), bB = aB + (OZ_KS / 8) * OZ_A_KB;
+#pragma unroll 1
+        for (int kh = 0; kh < OZ_KS / 16; ++kh) {
+#pragma unroll 1
+          for (int s = 0; s < OZ_S; ++s) {
+            const uint64_t da = oz_desc(aB + kh * 2 * OZ_A_KB + s * (OZ_TM * 16), OZ_A_KB, 128);
+#pragma unroll 1
+            for (int t = 0; t + s < OZ_ND; ++t) {
+              const uint64_t db = oz_desc(bB + kh * 2 * OZ_B_KB + t * (OZ_TN * 16), OZ_B_KB, 128);
+              const uint32_t acc = (i > 0 || kh > 0 || s > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)((s + t) * OZ_TN)),
+                  "l"(da), "l"(db), "r"(OZ_IDESC), "r"(acc));
+            }
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(&empty[st])));
+      }
+      // one more commit tracks every MMA issued above
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&done)));
+    }
+  }
+  // everyone: wait until the tensor cores are done with TMEM and the stages
+  const bool drained = oz_wait(su32(&done), 0);
+  ok = ok && drained;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (!all_ok && threadIdx.x == 0) atomicExch(&g_oz_timeout, 1);
+  if (all_ok && warp >= 2) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows; lane = row
+    const int quarter = warp & 3;
+    const int r = tm * OZ_TM + quarter * 32 + lane;
+    const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16);
+    const bool row_ok = r < P.m;
+    const int ea = row_ok ? P.ea[(long long)b * P.mpad + r] : 0;
+    for (int c0 = 0; c0 < OZ_TN; c0 += 16) {
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+#pragma unroll 1
+      for (int d = 0; d < OZ_ND; ++d) {
+        uint32_t v[16];
+        oz_ld16(ta + (uint32_t)(d * OZ_TN + c0), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long x = (long long)__float2int_rn(__uint_as_float(v[j]));  // an exact integer
+          if (d < 4)
+            hi[j] = hi[j] * 128 + x;  // 2^7: one slice width
+          else
+            lo[j] = lo[j] * 128 + x;
+        }
+      }
+      if (row_ok) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = tn * OZ_TN + c0 + j;
+          if (c >= P.n) continue;
+          // sum_d C_d 2^(-7 (d + 2)) = hi 2^-35 + lo 2^-63, then the row and column scales
+          const double val = fma((double)lo[j], 0x1p-63, (double)hi[j] * 0x1p-35);
+          const int eb = P.eb[(long long)(P.nb_batch_b ? b : 0) * P.npad + c];
+          double* pc = P.C.p + vaddr(P.C, b, r, c);
+          const double out = P.alpha * scalbn(val, ea + eb);
+          *pc = P.beta == 0.0 ? out : fma(P.beta, *pc, out);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool encode_fn() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
+}
+
+// 3-D map over slices [OZ_S][rows][kpad] (BF16), box {8 k, box_rows, all slices}.
+bool make_map(CUtensorMap* map, void* base, long long rows, int kpad, int box_rows) {
+  const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)OZ_S};
+  const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)rows * kpad * 2};
+  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+bool g_oz_enabled = true;  // process-wide switch (hs_set_fp64_emulation)
+
+bool oz_timed_out(cudaStream_t s) {
+  int v = 0, z = 0;
+  cudaStreamSynchronize(s);
+  cudaMemcpyFromSymbolAsync(&v, g_oz_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (v) {
+    cudaMemcpyToSymbolAsync(g_oz_timeout, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
+  return v != 0;
+}
+
+size_t ozaki_scratch_bytes(int m, int n, int k, int batch, bool b_shared) {
+  const long long kp = rup(std::min(k, OZ_KMAX), OZ_KS), mp = rup(m, OZ_TM), np = rup(n, OZ_TN);
+  const long long nbB = b_shared ? 1 : batch;
+  return (size_t)(OZ_S * kp * 2 * (batch * mp + nbB * np) + 4 * (batch * mp + nbB * np) + 4 * 1024);
+}
+
+cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double alpha, OzView A, OzView Bt, bool b_shared,
+                       double beta, OzView C, void* scratch, size_t scratch_bytes) {
+  if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535) return cudaErrorInvalidValue;
+  if (!encode_fn()) return cudaErrorNotSupported;
+  if (ozaki_scratch_bytes(m, n, k, batch, b_shared) > scratch_bytes) return cudaErrorInvalidValue;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  const long long mp = rup(m, OZ_TM), np = rup(n, OZ_TN);
+  const long long nbB = b_shared ? 1 : batch;
+  for (int k0 = 0; k0 < k; k0 += OZ_KMAX) {
+    const int kc = std::min(OZ_KMAX, k - k0);
+    const long long kp = rup(kc, OZ_KS);
+    char* p = reinterpret_cast<char*>(scratch);
+    auto take = [&](size_t bytes) {
+      char* q = p;
+      p += (bytes + 1023) & ~size_t(1023);
+      return q;
+    };
+    __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(take((size_t)OZ_S * batch * mp * kp * 2));
+    __nv_bfloat16* sbt = reinterpret_cast<__nv_bfloat16*>(take((size_t)OZ_S * nbB * np * kp * 2));
+    int* ea = reinterpret_cast<int*>(take((size_t)batch * mp * 4));
+    int* eb = reinterpret_cast<int*>(take((size_t)nbB * np * 4));
+    OzView a = A, bt = Bt;
+    a.p += k0 * A.sk;
+    bt.p += k0 * Bt.sk;
+    const long long ra = batch * mp, rb = nbB * np;
+    k_oz_slice<<<(unsigned)((ra + 7) / 8), 256, 0, s>>>(a, m, kc, (int)mp, (int)kp, batch, sa, ea);
+    HS_COUNT_LAUNCH();
+    k_oz_slice<<<(unsigned)((rb + 7) / 8), 256, 0, s>>>(bt, n, kc, (int)np, (int)kp, (int)nbB, sbt, eb);
+    HS_COUNT_LAUNCH();
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, sa, ra, (int)kp, OZ_TM) || !make_map(&mb, sbt, rb, (int)kp, OZ_TN))
+      return cudaErrorInvalidValue;
+    OzParams P;
+    P.m = m;
+    P.n = n;
+    P.k = kc;
+    P.mpad = (int)mp;
+    P.npad = (int)np;
+    P.kpad = (int)kp;
+    P.nb_batch_b = b_shared ? 0 : 1;
+    P.alpha = alpha;
+    P.beta = k0 == 0 ? beta : 1.0;
+    P.ea = ea;
+    P.eb = eb;
+    P.C = C;
+    dim3 grid((unsigned)(np / OZ_TN), (unsigned)(mp / OZ_TM), (unsigned)batch);
+    const bool prof = prof_active(4);
+    cudaEvent_t ev = nullptr;
+    if (prof) prof_begin(s, &ev);
+    k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ma, mb, P);
+    HS_COUNT_LAUNCH();
+    if (prof) prof_end(s, ev, 2.0 * m * n * kc * batch);  // FP64-equivalent flops
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hs

@@ -252,9 +252,157 @@ __global__ void k_diff_norms(const double2* __restrict__ a, const double2* __res
   }
 }
 
+// ---- adjoint refinement: transposed residual r = L - A^T Y -------------------
+//
+// Y holds the adjoint in the row space of the discrete system: Ypde at every
+// interior leaf node (the PDE rows), per merge level the adjoints of the
+// interface terms s_a = r_F + i eta r_C and s_b = r_F - i eta r_C (so that the
+// continuity rows u_a - u_b and the flux rows d_n u_a + d_n u_b carry
+// Y_C = i eta (Ys_a - Ys_b) and Y_F = Ys_a + Ys_b), and the exterior rows
+// [D - I/2, -S] [u; d_n u] at the boundary nodes (through V = [D - I/2, -S]^T Yext).
+// L is the receiver functional u_far(p) = A2[p] . [u; d_n u] at the boundary.
+// Per leaf edge node the edge coefficients (Eu of the node's own u, En of its
+// outward normal derivative) collect the interface and exterior terms; the
+// kernel then applies the transposed leaf rows.
+
+constexpr int ACH = 8;  // right-hand sides per block in the adjoint residual
+
+__global__ void __launch_bounds__(256) k_adj_res(const double2* __restrict__ Ypde, const int4* __restrict__ desc,
+                                                 const double2* __restrict__ Yif, const double2* __restrict__ A2,
+                                                 const double2* __restrict__ V, const double* __restrict__ q,
+                                                 const double* __restrict__ D1, double k, double h, double eta, int nb,
+                                                 int nrhs, int first, float2* __restrict__ G) {
+  __shared__ double D2[16][16], Dx[16][16];
+  __shared__ double2 y[NI][ACH];
+  __shared__ double2 eu[NE][ACH], en[NE][ACH];
+  const int leaf = blockIdx.x, j0 = blockIdx.y * ACH;
+  const int nj = min(ACH, nrhs - j0);
+  const double sc = 2.0 / h;
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) Dx[e / 16][e % 16] = D1[e] * sc;
+  if (!first)
+    for (int e = threadIdx.x; e < NI * ACH; e += blockDim.x) {
+      const int r = e / ACH, j = e % ACH;
+      y[r][j] = j < nj ? Ypde[((long long)leaf * NI + r) * nrhs + j0 + j] : make_double2(0.0, 0.0);
+    }
+  for (int e = threadIdx.x; e < NE * ACH; e += blockDim.x) {
+    const int r = e / ACH, j = e % ACH;
+    double2 u = make_double2(0.0, 0.0), n = make_double2(0.0, 0.0);
+    if (j < nj) {
+      const int4 d = desc[leaf * NE + r];
+      const long long p = j0 + j;
+      if (d.z == 2) {  // boundary node d.x: u_far row minus the exterior rows' transpose
+        u = A2[p * 2 * nb + d.x];
+        n = A2[p * 2 * nb + nb + d.x];
+        if (V) {
+          u = u - V[(long long)d.x * nrhs + p];
+          n = n - V[(long long)(nb + d.x) * nrhs + p];
+        }
+      } else if (!first) {  // interface node: d.x = (offset of its s_a row) / nrhs, d.y = ni
+        const double2 sa = Yif[(long long)d.x * nrhs + p], sb = Yif[((long long)d.x + d.y) * nrhs + p];
+        const double2 dd = sa - sb;
+        const double2 yc = make_double2(-eta * dd.y, eta * dd.x);  // i eta (Ys_a - Ys_b)
+        u = d.z == 0 ? -yc : yc;                                  // row u_a - u_b
+        n = -(sa + sb);                                           // row d_n u_a + d_n u_b
+      }
+    }
+    eu[r][j] = u;
+    en[r][j] = n;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    const int i = e / 16, jj = e % 16;
+    double s2 = 0.0;
+    for (int c = 0; c < 16; ++c) s2 += Dx[i][c] * Dx[c][jj];
+    D2[i][jj] = s2;
+  }
+  __syncthreads();
+  const double* ql = q + (long long)leaf * 256;
+  for (int e = threadIdx.x; e < NL * ACH; e += blockDim.x) {
+    const int r = e / ACH, j = e % ACH;
+    if (j >= nj) continue;
+    int i, jy;  // x and y indices of unknown r
+    if (r < NI) {
+      i = r / 14 + 1;
+      jy = r % 14 + 1;
+    } else {
+      const int ed = r - NI, side = ed / 14, t = ed % 14 + 1;
+      switch (side) {
+        case 0: i = t; jy = 0; break;    // S
+        case 1: i = 15; jy = t; break;   // E
+        case 2: i = t; jy = 15; break;   // N
+        default: i = 0; jy = t; break;   // W
+      }
+    }
+    double2 acc = make_double2(0.0, 0.0);
+    if (!first) {  // transposed PDE rows of this leaf
+      if (jy >= 1 && jy <= 14)
+        for (int a = 1; a <= 14; ++a) acc = acc + D2[a][i] * y[(a - 1) * 14 + jy - 1][j];
+      if (i >= 1 && i <= 14)
+        for (int b = 1; b <= 14; ++b) acc = acc + D2[b][jy] * y[(i - 1) * 14 + b - 1][j];
+      if (r < NI) acc = acc + (k * k * (1.0 - ql[i * 16 + jy])) * y[r][j];
+    }
+    double2 v = -acc;
+    if (r >= NI) v = v + eu[r - NI][j];
+    if (i >= 1 && i <= 14) {  // normal derivatives at the S and N nodes of column i
+      v = v + (-Dx[0][jy]) * en[i - 1][j];
+      v = v + Dx[15][jy] * en[28 + i - 1][j];
+    }
+    if (jy >= 1 && jy <= 14) {  // at the W and E nodes of row jy
+      v = v + (-Dx[0][i]) * en[42 + jy - 1][j];
+      v = v + Dx[15][i] * en[14 + jy - 1][j];
+    }
+    G[((long long)leaf * NL + r) * nrhs + j0 + j] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// Edge rows of the transposed leaf step: G_e += -2 i eta Hadj (the adjoint of
+// the leaf's particular outgoing impedance h = -2 i eta u_e).
+__global__ void k_leaf_hadj(const float2* __restrict__ H, int nleaf, double eta, int nrhs, float2* __restrict__ G) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nleaf * NE * nrhs) return;
+  const int j = (int)(e % nrhs);
+  const long long t = e / nrhs;
+  const int r = (int)(t % NE), leaf = (int)(t / NE);
+  const float2 v = H[e];
+  const float te = (float)(2.0 * eta);
+  float2* g = G + ((long long)leaf * NL + NI + r) * nrhs + j;
+  *g = make_float2(g->x + te * v.y, g->y - te * v.x);
+}
+
+// Yif += [MU top; -MU bottom] for one level ([nbox][2 ni][nrhs]): the adjoints of
+// s_a and s_b are Wt and -la3 of the transposed sweep.
+__global__ void k_iface_adj_add(const float2* __restrict__ MU, int ni, int nrhs, long long n, double2* __restrict__ Y) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int t = (int)((e / nrhs) % (2 * ni));
+  const float2 m = MU[e];
+  const double sg = t < ni ? 1.0 : -1.0;
+  Y[e] = make_double2(Y[e].x + sg * m.x, Y[e].y + sg * m.y);
+}
+
 inline unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
+
+void adjoint_residual(cudaStream_t s, const double2* Ypde, const int4* desc, const double2* Yif, const double2* A2,
+                      const double2* V, const double* q, const double* D1, int nleaf, int nb, double k, double h,
+                      double eta, int nrhs, bool first, float2* G) {
+  dim3 g(nleaf, (nrhs + ACH - 1) / ACH);
+  k_adj_res<<<g, 256, 0, s>>>(Ypde, desc, Yif, A2, V, q, D1, k, h, eta, nb, nrhs, first ? 1 : 0, G);
+  HS_COUNT_LAUNCH();
+}
+
+void leaf_hadj(cudaStream_t s, const float2* H, int nleaf, double eta, int nrhs, float2* G) {
+  long long n = (long long)nleaf * NE * nrhs;
+  k_leaf_hadj<<<blocks(n), 256, 0, s>>>(H, nleaf, eta, nrhs, G);
+  HS_COUNT_LAUNCH();
+}
+
+void iface_adj_add(cudaStream_t s, const float2* MU, int nbox, int ni, int nrhs, double2* Y) {
+  long long n = (long long)nbox * 2 * ni * nrhs;
+  k_iface_adj_add<<<blocks(n), 256, 0, s>>>(MU, ni, nrhs, n, Y);
+  HS_COUNT_LAUNCH();
+}
 
 void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out) {
   k_diff_norms<<<blocks(n), 256, 0, s>>>(a, b, n, out);

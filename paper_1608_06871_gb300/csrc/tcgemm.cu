@@ -367,6 +367,7 @@ cudaError_t tc_raise_timeout_flag() {
 }
 
 bool tc_timed_out(cudaStream_t s) {
+  const bool oz = oz_timed_out(s);
   int v = 0, z = 0;
   cudaStreamSynchronize(s);
   cudaMemcpyFromSymbolAsync(&v, g_tc_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
@@ -375,7 +376,7 @@ bool tc_timed_out(cudaStream_t s) {
     cudaMemcpyToSymbolAsync(g_tc_timeout, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);
   }
-  return v != 0;
+  return v != 0 || oz;
 }
 
 }  // namespace hs

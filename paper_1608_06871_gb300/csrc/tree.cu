@@ -161,6 +161,31 @@ __global__ void k_scatter_adj(const C* __restrict__ Lp, const C* __restrict__ MU
   }
 }
 
+// Transpose of k_scatter_down: the children's adjoint impedance loads Lc give
+// the adjoint of the interface impedances MU = [Lc_alpha(I3a); Lc_beta(I3b)]
+// and the exterior part of the parent's, Lp(r) = Lc(child of r).
+template <typename C>
+__global__ void k_gather_adj_up(const C* __restrict__ Lc, const int* __restrict__ alpha, const int* __restrict__ beta,
+                                const int* __restrict__ src, const int* __restrict__ I3a, const int* __restrict__ I3b,
+                                int nc, int ni, int np, int nrhs, C* __restrict__ MU, C* __restrict__ Lp) {
+  const int b = blockIdx.y;
+  const long long rows = np + 2LL * ni;
+  const long long tot = rows * nrhs;
+  const int ca = alpha[b], cb = beta[b];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e / nrhs), j = (int)(e % nrhs);
+    if (r < np) {
+      int sv = src[r];
+      int child = src_child(sv) == 0 ? ca : cb;
+      Lp[((long long)b * np + r) * nrhs + j] = Lc[((long long)child * nc + src_local(sv)) * nrhs + j];
+    } else {
+      int t = r - np;
+      C v = t < ni ? Lc[((long long)ca * nc + I3a[t]) * nrhs + j] : Lc[((long long)cb * nc + I3b[t - ni]) * nrhs + j];
+      MU[((long long)b * 2 * ni + t) * nrhs + j] = v;
+    }
+  }
+}
+
 // Upward gather: TT top := h3b - s_a, TT bottom := h3a - s_b, Hp := children's
 // exterior particular impedances in the parent's order.
 template <typename C>
@@ -269,16 +294,18 @@ void sweep_down_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, 
 
 template <typename C>
 void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lp, C* MU, C* Lc,
-                         int nrhs, bool w_explicit) {
+                         int nrhs, bool w_explicit, bool mu_loaded) {
   const int ni = L.ni, np = L.np, nb = L.nbox;
   const long long nn = (long long)ni * ni, mu = 2LL * ni * nrhs;
   const C one = el<C>::one(), mone = -el<C>::one(), zero = el<C>::zero();
-  // mu_a = A13^T lambda_1, mu_b = B23^T lambda_2 ;  lambda_tb = mu_b
+  // mu_a = A13^T lambda_1, mu_b = B23^T lambda_2 ;  lambda_tb = mu_b  (added to the
+  // adjoint of the particular interface impedances when MU holds it on entry)
   const int n1 = L.n1, n2 = np - L.n1;
   const long long su = (long long)np * ni, sl = (long long)np * nrhs;
-  gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, n1, one, O.U2, ni, su, Lp, nrhs, sl, zero, MU, nrhs, mu, nb);
+  const C b0 = mu_loaded ? one : zero;
+  gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, n1, one, O.U2, ni, su, Lp, nrhs, sl, b0, MU, nrhs, mu, nb);
   gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, n2, one, O.U2 + (long long)n1 * ni, ni, su, Lp + (long long)n1 * nrhs, nrhs,
-                sl, zero, MU + (long long)ni * nrhs, nrhs, mu, nb);
+                sl, b0, MU + (long long)ni * nrhs, nrhs, mu, nb);
   // lambda_ta = mu_a - A33^T lambda_tb
   gemm<C, C, C>(s, OP_T, OP_N, ni, nrhs, ni, mone, O.A33, ni, nn, MU + (long long)ni * nrhs, nrhs, mu, one, MU, nrhs,
                 mu, nb);
@@ -299,6 +326,19 @@ void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& 
   k_scatter_adj<C><<<dim3(grid_for(tot, 256), nb), 256, 0, s>>>(Lp, MU, L.d_alpha, L.d_beta, L.d_src, L.d_I3a,
                                                                 L.d_I3b, L.nc, ni, np, nrhs, Lc);
   HS_COUNT_LAUNCH();
+}
+
+template <typename C>
+void sweep_adjoint_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lc, C* MU, C* Lp,
+                            int nrhs) {
+  const int ni = L.ni, np = L.np, nb = L.nbox;
+  long long tot = ((long long)np + 2LL * ni) * nrhs;
+  k_gather_adj_up<C><<<dim3(grid_for(tot, 256), nb), 256, 0, s>>>(Lc, L.d_alpha, L.d_beta, L.d_src, L.d_I3a, L.d_I3b,
+                                                                  L.nc, ni, np, nrhs, MU, Lp);
+  HS_COUNT_LAUNCH();
+  // Lp += [X; Z]^T MU  (the interface impedances were [X; Z] f + [t_a; t_b])
+  gemm<C, C, C>(s, OP_T, OP_N, np, nrhs, 2 * ni, el<C>::one(), O.XZ, np, 2LL * ni * np, MU, nrhs, 2LL * ni * nrhs,
+                el<C>::one(), Lp, nrhs, (long long)np * nrhs, nb);
 }
 
 template <typename C>
@@ -365,7 +405,9 @@ template <typename C> void permute_square(cudaStream_t s, const C* src, const in
 #define HS_INST(C)                                                                                                     \
   template void merge_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, int*);                  \
   template void sweep_down_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool); \
-  template void sweep_adjoint_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool); \
+  template void sweep_adjoint_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int, bool, \
+                                       bool);                                                                        \
+  template void sweep_adjoint_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, int);  \
   template void sweep_up_level<C>(cudaStream_t, const LevelMaps&, const LevelOps<C>&, const C*, C*, C*, C*, int);       \
   template void permute_rows<C>(cudaStream_t, const C*, const int*, int, int, C*);                                  \
   template void permute_square<C>(cudaStream_t, const C*, const int*, int, C*);

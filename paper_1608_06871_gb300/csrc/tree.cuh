@@ -62,9 +62,21 @@ template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const
 template <typename C>
 void sweep_down_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Fp, C* T3, C* Fc, int nrhs,
                       bool t3_loaded);
+// Transposed downward sweep of one level (the adjoint of sweep_up_level's map
+// from the children's particular impedances and the interface terms to the
+// parent's): parent loads Lp give the children's Lc; MU ([nbox][2 ni][nrhs])
+// ends as [Wt; la3], whose halves are the adjoints of s_a (Wt) and of s_b
+// (-la3).  With mu_loaded, MU holds on entry the adjoint of the particular
+// interface impedances [t_a; t_b] (from sweep_adjoint_up_level) and is added to.
 template <typename C>
 void sweep_adjoint_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lp, C* MU, C* Lc,
-                         int nrhs, bool w_explicit = false);
+                         int nrhs, bool w_explicit = false, bool mu_loaded = false);
+// Transposed upward sweep of one level (the adjoint of sweep_down_level):
+// children's adjoint loads Lc give the parent's Lp and the adjoint of the
+// interface impedances MU = [Lc_alpha(I3a); Lc_beta(I3b)] ([nbox][2 ni][nrhs]).
+template <typename C>
+void sweep_adjoint_up_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Lc, C* MU, C* Lp,
+                            int nrhs);
 // Upward (particular) pass of one level: children's outgoing particular
 // impedances Hc and the interface residual terms S3 ([s_a; s_b] per box) give
 // the particular interface impedances TT = [t_a; t_b] (kept for the downward
@@ -111,10 +123,15 @@ void adjoint_root_init(cudaStream_t s, int nb, int P, double eta, const double2*
 void leaf_to_grid(cudaStream_t s, const double2* Uleaf, int nrows_leaf, int nL, int nrhs, double2* G);
 void leaf_to_nodes(cudaStream_t s, const double2* Uleaf, int nL, int nrhs, double2* out);
 void interior_sine_tables(cudaStream_t s, const double* xg_int, int n, int S1, int S2, double* sx, double* sy);
-// Pairs per chunk of the contraction within budget_bytes of W and T.
+// Pairs per chunk of the contraction within budget_bytes of W and T (the
+// emulated FP64 product needs contract_emulated_bytes on top).
 int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes);
+size_t contract_emulated_bytes(int C, int nX, int S1, int S2);
+// scratch: emulated-product slices (contract_emulated_bytes), or NULL for the
+// FP64 SIMT GEMMs.
 void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
-                       const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C);
+                       const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C,
+                       void* scratch, size_t scratch_bytes);
 void split_stack(cudaStream_t s, const double2* J, int rows, int cols, double* Jst);
 // J v and Re(J^H f) from the forward and adjoint fields on the interior grid (no J formed).
 void apply_J(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
@@ -134,6 +151,11 @@ void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double
 void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g);
 // A = Jst^T Jst (n x n) by block rows of its lower part, mirrored.
 void normal_matrix(cudaStream_t s, const double* Jst, int rows, int n, double* A);
+// The same from the transposed stack JstT = [Re J; Im J]^T (n x 2 MP, written by
+// split_stack_t) with the emulated FP64 product; false if it could not run.
+void split_stack_t(cudaStream_t s, const double2* J, int rows, int cols, double* JstT);
+size_t normal_matrix_emulated_bytes(int rows, int n);
+bool normal_matrix_emulated(cudaStream_t s, double* JstT, int rows, int n, double* A, void* scratch, size_t bytes);
 void residual(cudaStream_t s, const double* data, const double2* F, int n, double2* res, double* rst, double* out2);
 void add_lambda(cudaStream_t s, double* A, int n, double lambda_rel);
 void gradient_combine(cudaStream_t s, const double2* Ug, const double2* Zmix, int M, long long npts, double* hre);
@@ -159,6 +181,20 @@ void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n,
 void scattered32(cudaStream_t s, const float2* U32, const double* D1, int nL, double h, int nrhs, const double2* ui,
                  const double2* dni, bool sub_inc, float2* PS);
 void norm2_32(cudaStream_t s, const float2* a, long long n, double* out);
+// Adjoint refinement (refine.cu): G (FP32, leaf layout [leaf][252][nrhs]) =
+// L - A^T Y in FP64 for the adjoint Y (Ypde [leaf][196][nrhs]; Yif, every
+// merge level's [nbox][2 ni][nrhs] adjoints of (s_a, s_b) back to back; V =
+// [D - I/2, -S]^T Yext, [2 nb][nrhs], or NULL when Yext = 0), L the receiver
+// functionals from A2 ([nrhs][2 nb]).  desc[leaf][56] = (x, y, kind): kind 2 =
+// boundary node x; kind 0 / 1 = alpha / beta side of the interface row whose s_a
+// adjoint is at Yif[x * nrhs], s_b at Yif[(x + y) * nrhs].  first: Y = 0.
+void adjoint_residual(cudaStream_t s, const double2* Ypde, const int4* desc, const double2* Yif, const double2* A2,
+                      const double2* V, const double* q, const double* D1, int nleaf, int nb, double k, double h,
+                      double eta, int nrhs, bool first, float2* G);
+// G edge rows += -2 i eta H  (H [leaf][56][nrhs]).
+void leaf_hadj(cudaStream_t s, const float2* H, int nleaf, double eta, int nrhs, float2* G);
+// Y += [MU top; -MU bottom] per box (one level, [nbox][2 ni][nrhs]).
+void iface_adj_add(cudaStream_t s, const float2* MU, int nbox, int ni, int nrhs, double2* Y);
 // DS = [D - I/2, -S] (nb x 2 nb) in FP64 and FP32.
 void stack_exterior(cudaStream_t s, const double2* Dm, const double2* S, int nb, double2* DS, float2* DS32);
 // dst[r][:] = src[idx[r]][:] (rows of ncols elements); dst[a][b] = src[idx[a]][idx[b]] for square matrices.

@@ -102,6 +102,20 @@ def plan_paper(k: float, R: float = 20.0, leaf_kh: float = 2.5, min_leaves: int 
                          int(math.floor(4.0 * k)), 1, R=2.0 * R / math.pi, triangle=S, k_label=k)
 
 
+def plan_table1(k: float, M: int = 64, R: float = 20.0) -> FrequencyPlan:
+    """The forward benchmark of the paper's Table 1 (Sec. 2) at its frequency k in
+    {1, 2, 4, ..., 128} on [-pi/2, pi/2]^2, read on [-1, 1]^2 like plan_paper
+    (wavenumber pi k / 2, receiver radius 2 R / pi): max(4, k) x max(4, k) leaves of
+    16 x 16 points, i.e. the table's N = (15 n_L + 1)^2 (3721 for k <= 4, 3,690,241 at
+    k = 128) and a leaf of width pi / k (k h = pi, half a free-space wavelength).  The
+    table's contrast is q = 1.5 exp(-|x|^2 / 50), read as entering with the opposite
+    sign (synth.paper_example(1)): k sqrt(1 - q) h is then 4.83..4.97, between the
+    first two Dirichlet eigenvalues pi sqrt(2), pi sqrt(5) of a leaf, so the leaf
+    interior blocks stay nonsingular.  M incidences and M receivers time the solves."""
+    nl = max(4, int(round(k)))
+    return FrequencyPlan(math.pi * k / 2.0, nl, 1, M, M, 0, R=2.0 * R / math.pi, k_label=k)
+
+
 def plan_c5(k: float) -> FrequencyPlan:
     """The paper-scale reconstruction plan on [-1, 1]^2: S = floor(2k) sine modes per axis
     (140 x 140 = 19,600 at k = 70), M = P = ceil(4k) (280 at k = 70), leaves
@@ -146,14 +160,12 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
     angles:  optional function plan -> (alphas, thetas); default equispaced 2 pi m / M, 2 pi p / P.
     solver:  "direct" (normal equations with lambda_rel, hs_gn_step) or "lsqr" (the paper's
              LSQR at lsqr_tol on the plan's modes, hs_gn_step_lsqr, products in lsqr_products).
-    precision: HS_FP64, or HS_MIXED (mixed-precision factors; needs solver="lsqr").
+    precision: HS_FP64, or HS_MIXED (FP32 factors; forward and adjoint fields refined in FP64).
     R:       receiver radius overriding the plans' own.
     Each history entry records the build (factorisation) time t_f and the
     least-squares time t_l of every step in seconds, and the LSQR iterations.
     """
     use_lsqr = solver_kind_lsqr(solver)
-    if precision != HS_FP64 and not use_lsqr:
-        raise ValueError("the direct Gauss-Newton step needs precision HS_FP64; use solver='lsqr'")
     if angles is None:
         angles = lambda p: (2 * np.pi * np.arange(p.M) / p.M, 2 * np.pi * np.arange(p.P) / p.P)
     c = np.zeros((plans[0].S, plans[0].S)) if c0 is None else np.asarray(c0, dtype=np.float64)

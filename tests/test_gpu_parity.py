@@ -172,8 +172,9 @@ def test_error_paths(hs):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_degenerate_one_of_everything(hs, prec):
-    """1 x 1 leaf, one sine mode, one incidence, one receiver, low frequency: far field against
-    the oracle; on the FP64 context also the Jacobian and both Gauss-Newton steps."""
+    """1 x 1 leaf, one sine mode, one incidence, one receiver, low frequency: far field, Jacobian,
+    gradient and both Gauss-Newton steps against the oracle, on FP64 and mixed contexts (the mixed
+    adjoint is refined on a tree without merge levels)."""
     k, nL = 0.7, 1
     c = np.array([[0.05]])
     al, th = np.array([0.3]), np.array([2.0])
@@ -181,22 +182,18 @@ def test_degenerate_one_of_everything(hs, prec):
     ref, _ = fw.solve_plane(al, th)
     S = hs.Solver(nL, 1, 1, 3.0, hs.HS_FP64 if prec == "fp64" else hs.HS_MIXED).build(c, k)
     assert rel(S.solve(al, th), ref) < (1e-10 if prec == "fp64" else 1e-8)
-    if prec == "fp64":
-        J = S.jacobian(al, th)
-        Jo = fw.jacobian(al, th, 1, 1)
-        assert rel(J, Jo) < 1e-9
-        data = ref * 1.1
-        c1, _ = S.gn_step(data, al, th, 0.0, c)
-        dc_ref = F.gn_step(Jo, (data - ref).ravel(), 0.0)
-        assert rel(c1.ravel() - c.ravel(), dc_ref) < 1e-7
-        c2, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5)
-        assert it == 1 and rel(c2.ravel() - c.ravel(), dc_ref) < 1e-7  # one unknown: one iteration is exact
-    else:  # the mixed adjoint on a tree without merges (FP32 accuracy)
-        Jo = fw.jacobian(al, th, 1, 1)
-        assert rel(S.jacobian(al, th), Jo) < 1e-4
-        data = ref * 1.1
-        g, _ = S.gradient(data, al, th)
-        assert rel(g.ravel(), F.misfit_gradient(Jo, ref.ravel(), data.ravel())) < 1e-4
-        c2, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5, products=hs.HS_MIXED)
-        assert it == 1 and rel(c2.ravel() - c.ravel(), F.gn_step(Jo, (data - ref).ravel(), 0.0)) < 1e-4
+    J = S.jacobian(al, th)
+    Jo = fw.jacobian(al, th, 1, 1)
+    assert rel(J, Jo) < 1e-9
+    data = ref * 1.1
+    g, _ = S.gradient(data, al, th)
+    assert rel(g.ravel(), F.misfit_gradient(Jo, ref.ravel(), data.ravel())) < 1e-9
+    c1, _ = S.gn_step(data, al, th, 0.0, c)
+    dc_ref = F.gn_step(Jo, (data - ref).ravel(), 0.0)
+    assert rel(c1.ravel() - c.ravel(), dc_ref) < 1e-7
+    c2, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5)
+    assert it == 1 and rel(c2.ravel() - c.ravel(), dc_ref) < 1e-7  # one unknown: one iteration is exact
+    if prec == "mixed":  # the FP32 tensor-core Jacobian in the LSQR products: FP32 accuracy
+        c3, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5, products=hs.HS_MIXED)
+        assert it == 1 and rel(c3.ravel() - c.ravel(), dc_ref) < 1e-4
     S.close()

@@ -43,3 +43,33 @@ def test_plan_c5_top_and_resonances():
         pk = SW.plan_c5(float(k))
         assert abs(pk.k - k) <= 0.02 and np.abs(ev - pk.k).min() >= 0.002, k
     assert SW.plan_c5(40.75).k != 40.75
+
+
+def test_example1_contrast_is_outside_the_sine_band_near_the_boundary():
+    """Example 1 (Sec. 4) under the sign reading of its contrast, q = -1.5 exp(-|x|^2/50) on
+    [-pi/2, pi/2]^2: q is -1.5 .. -1.36 over the whole square and does not vanish on its
+    boundary, where every sine mode does.  So even the best L2 approximation in the paper's
+    final basis (k = 14.25: m1 + m2 <= 28, 378 modes) stays a sizable fraction of ||q|| away,
+    and a reconstruction in that basis cannot converge to q the way the paper's smooth
+    examples do; Example 2's contrast, which decays inside the square, is approximated to
+    well under 1% by the same basis."""
+    import math
+
+    import numpy as np
+
+    import synth
+    from paper_1608_06871_gb300 import sweep as SW
+    p = SW.plan_paper(14.25)
+    g = (np.arange(512) + 0.5) / 256.0 - 1.0
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    bx = np.sin(np.outer(np.arange(1, p.S + 1), g + 1.0) * (math.pi / 2.0))
+    cell = (math.pi / 512.0) ** 2
+    out = {}
+    for which in (1, 2):
+        q = synth.paper_example(which)
+        best = synth.project_sine(q, p.S, p.S, nq=512) * p.mask()
+        err = math.sqrt(np.sum((bx.T @ best @ bx - q(X, Y)) ** 2) * cell)
+        out[which] = err / math.sqrt(np.sum(q(X, Y) ** 2) * cell)
+    assert int(p.mask().sum()) == 378
+    assert out[1] > 0.1
+    assert out[2] < 0.01

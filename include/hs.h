@@ -164,21 +164,24 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
  * r = data - F(c), dc restricted to the modes where mask != 0 (mask: S1*S2
  * bytes in the order of c, or NULL for all modes; e.g. the triangle
  * m1 + m2 <= S of Sec. 3.2).  J comes from the forward and adjoint fields of
- * the built contrast (Theorem 3.1 / 3.2).  products: HS_FP64 -- J is never
- * formed, every iteration applies J and J^H from the fields by two FP64 grid
- * contractions; HS_MIXED -- J is formed once in complex FP32 on the tensor
- * cores (3xTF32) and every iteration reads it twice with FP64 sums, so that
- * J v and J^H u stay exact transposes of that one matrix (for loose
- * tolerances such as the paper's 1e-3).  The iteration's vectors live on the
+ * the built contrast (Theorem 3.1 / 3.2).  products: HS_FP64 -- J is formed
+ * once in FP64 by the emulated FP64 contraction on the tensor cores and every
+ * iteration reads it twice (with the emulation switched off, J and J^H are
+ * applied from the fields by two FP64 grid contractions per iteration);
+ * HS_MIXED -- J is formed once in complex FP32 on the tensor cores (3xTF32)
+ * from a single FP32 adjoint solve and every iteration reads it twice with
+ * FP64 sums (for loose tolerances such as the paper's 1e-3).  Either way J v
+ * and J^H u stay exact transposes of one matrix.  The iteration's vectors live on the
  * host.  Stops when the relative residual or the relative normal-equations
  * residual (LSQR's own estimates) is at most tol, or after max_iter
  * iterations; *iters_out (optional) receives the count.  Otherwise as
  * hs_gn_step (c_inout updated, resid_norm_out = ||r||_2 before the step).
- * On an HS_MIXED context the residual, the forward fields and the adjoint
- * fields come from the refined solves (FP64 accurate), so with products
- * HS_FP64 the step is the FP64 context's to the refinement tolerance; with
- * products HS_MIXED it carries the FP32 rounding of the tensor-core J on
- * either kind of context.  Errors: HS_EINVAL (damp < 0, tol < 0,
+ * On an HS_MIXED context the residual, the forward fields and (for products
+ * HS_FP64) the adjoint fields come from the refined solves (FP64 accurate), so
+ * with products HS_FP64 the step is the FP64 context's to the refinement
+ * tolerance; with products HS_MIXED it carries the FP32 rounding of the
+ * tensor-core J on either kind of context.  The explicit J needs M P S1 S2
+ * complex doubles of device workspace.  Errors: HS_EINVAL (damp < 0, tol < 0,
  * max_iter < 1, bad products, bad sizes, NULL), HS_ENOTBUILT, HS_ENOMEM,
  * HS_ECUDA, HS_ETIMEOUT, HS_ENOCONV. */
 int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M,

@@ -188,6 +188,10 @@ struct hs_ctx {
   // exterior row lives (see adjoint_residual), and per merge level the offset
   // (in rows of nrhs) of its block in the interface-adjoint buffer
   int4* d_adj_desc = nullptr;
+  // mixed: slices of the exterior rows [D - I/2, -S] (real and imaginary parts)
+  // for the emulated FP64 residual product, made once per k
+  char* d_ds_oz = nullptr;
+  double ds_oz_k = -1.0;
   std::vector<long long> if_off;
   long long if_rows = 0;
   int adj_iters = 0;
@@ -927,6 +931,31 @@ int check_ctx(hs_ctx* ctx, bool need_built) {
 
 cudaStream_t pick(hs_ctx* ctx, void* stream) { return stream ? (cudaStream_t)stream : ctx->stream; }
 
+// Emulated complex FP64 product C (m x n, leading dimension ldc) = alpha A B
+// from the sliced real and imaginary parts of A (m rows, k) and of B^T (n rows,
+// k): four real products, the second of each pair accumulated in FP64.
+int zmul_emulated(hs_ctx* ctx, cudaStream_t s, int m, int n, int k, const void* Are, const void* Aim, const void* Bre,
+                  const void* Bim, double alpha, double2* C, int ldc) {
+  double* c = reinterpret_cast<double*>(C);
+  const OzView cre{c, 0, 2LL * ldc, 0, 2, 1}, cim{c + 1, 0, 2LL * ldc, 0, 2, 1};
+  cudaError_t e = oz_multiply(s, m, n, k, 1, alpha, Are, Bre, true, 0.0, cre);
+  if (e == cudaSuccess) e = oz_multiply(s, m, n, k, 1, -alpha, Aim, Bim, true, 1.0, cre);
+  if (e == cudaSuccess) e = oz_multiply(s, m, n, k, 1, alpha, Are, Bim, true, 0.0, cim);
+  if (e == cudaSuccess) e = oz_multiply(s, m, n, k, 1, alpha, Aim, Bre, true, 1.0, cim);
+  if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("emulated FP64 product: ") + cudaGetErrorString(e));
+  return HS_OK;
+}
+
+// Real and imaginary parts of a complex matrix (rows x k, leading dimension
+// ld, interleaved) as strided real views for slicing.
+OzView re_view(const double2* A, int ld, int part) {
+  return OzView{const_cast<double*>(reinterpret_cast<const double*>(A)) + part, 0, 2LL * ld, 0, 2, 1};
+}
+// The same for the transpose of a k x rows complex matrix (row index along its columns).
+OzView re_view_t(const double2* A, int ld, int part) {
+  return OzView{const_cast<double*>(reinterpret_cast<const double*>(A)) + part, 0, 2, 0, 2LL * ld, 1};
+}
+
 // Far field for M incidences into ufar (device, M x P complex).
 int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P, double2* ufar,
                 double2* Xout, Arena& a);
@@ -971,6 +1000,8 @@ size_t mixed_bytes(hs_ctx* ctx, int M, int P) {
        Arena::bytes(nl * NI * M, 8) +
        Arena::bytes(s3_elems(ctx, M), 8) + 2 * Arena::bytes(nb * M, 8);
   for (auto& L : ctx->levels) b += Arena::bytes((size_t)L.nbox * 2 * L.ni * M, 8);
+  if (g_oz_enabled) b += 2 * std::max(oz_operand_bytes(M, 2 * (int)nb, 1, false),
+                                      oz_operand_bytes(M, 2 * (int)nb, 1, true) + oz_operand_bytes(P, 2 * (int)nb, 1, false));
   return b;
 }
 
@@ -1012,7 +1043,21 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   float2 *f32 = a.get<float2>(nbM), *r32 = a.get<float2>(nbM);
   std::vector<float2*> TT(nlev);
   for (int li = 0; li < nlev; ++li) TT[li] = a.get<float2>((size_t)ctx->levels[li].nbox * 2 * ctx->levels[li].ni * M);
+  // emulated FP64 products: slices of the boundary data (as the right operand of
+  // the exterior residual, then as the left operand of the far field) and of
+  // the receiver matrix
+  const bool emu = g_oz_enabled;
+  const size_t ob_ps = emu ? oz_operand_bytes(M, 2 * nb, 1, false) : 0;
+  const size_t ob_psa = emu ? oz_operand_bytes(M, 2 * nb, 1, true) : 0, ob_a2 = emu ? oz_operand_bytes(P, 2 * nb, 1, false) : 0;
+  char* ozs = emu ? a.get<char>(2 * std::max(ob_ps, ob_psa + ob_a2)) : nullptr;
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  const size_t ob_ds = oz_operand_bytes(nb, 2 * nb, 1, true);
+  if (emu && ctx->ds_oz_k != ctx->bie_k) {  // the exterior rows of this k, sliced once
+    if (!ctx->d_ds_oz) CKR(dalloc(ctx, &ctx->d_ds_oz, 2 * ob_ds));
+    oz_slice(s, re_view(ctx->d_DS, 2 * nb, 0), nb, 2 * nb, 1, true, ctx->d_ds_oz);
+    oz_slice(s, re_view(ctx->d_DS, 2 * nb, 1), nb, 2 * nb, 1, true, ctx->d_ds_oz + ob_ds);
+    ctx->ds_oz_k = ctx->bie_k;
+  }
 
   incident_plane(s, ctx->B, ctx->k, alphas, M, ui, dni);
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
@@ -1031,8 +1076,14 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
       residual_pde(s, X, ctx->d_q, ctx->d_D1, nl, ctx->k, ctx->h, M, Up);
       boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
       scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
-      gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, 2 * nb, mone, ctx->d_DS, 2 * nb, 0, PS, M, 0, zero, rext,
-                                      M, 0, 1);
+      if (emu) {
+        oz_slice(s, re_view_t(PS, M, 0), M, 2 * nb, 1, false, ozs);
+        oz_slice(s, re_view_t(PS, M, 1), M, 2 * nb, 1, false, ozs + ob_ps);
+        CKR(zmul_emulated(ctx, s, nb, M, 2 * nb, ctx->d_ds_oz, ctx->d_ds_oz + ob_ds, ozs, ozs + ob_ps, -1.0, rext, M));
+      } else {
+        gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, 2 * nb, mone, ctx->d_DS, 2 * nb, 0, PS, M, 0, zero,
+                                        rext, M, 0, 1);
+      }
     }
     // The rest of the pass is FP32 work on fixed buffers: replayed from a
     // captured graph (one for the first pass, one for the corrections).
@@ -1115,7 +1166,16 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   if (ufar) {  // far field of the converged FP64 iterate, in FP64
     boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
     scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
-    gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, one, PS, M, 0, A2, 2 * nb, 0, zero, uf, P, 0, 1);
+    if (emu) {  // uf = PS^T A2^T
+      char *pa = ozs, *pb = ozs + 2 * ob_psa;
+      oz_slice(s, re_view_t(PS, M, 0), M, 2 * nb, 1, true, pa);
+      oz_slice(s, re_view_t(PS, M, 1), M, 2 * nb, 1, true, pa + ob_psa);
+      oz_slice(s, re_view(A2, 2 * nb, 0), P, 2 * nb, 1, false, pb);
+      oz_slice(s, re_view(A2, 2 * nb, 1), P, 2 * nb, 1, false, pb + ob_a2);
+      CKR(zmul_emulated(ctx, s, M, P, 2 * nb, pa, pa + ob_psa, pb, pb + ob_a2, 1.0, uf, P));
+    } else {
+      gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, one, PS, M, 0, A2, 2 * nb, 0, zero, uf, P, 0, 1);
+    }
   }
   if (ufar) CK(cudaMemcpyAsync(ufar, uf, sizeof(double2) * M * P, cudaMemcpyDeviceToDevice, s));
   if (Xout) CK(cudaMemcpyAsync(Xout, X, sizeof(double2) * nX, cudaMemcpyDeviceToDevice, s));
@@ -1186,12 +1246,14 @@ size_t mixed_adjoint_bytes(hs_ctx* ctx, int P) {
 // adjoint the Jacobian and the gradient use): once two changes give the
 // contraction rate rho, the error estimate is the change times rho / (1 - rho).
 // Z64: [leaf][196][P] (FP64, output).  A2: [P][2 nb] FP64.
-int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2* Z64, Arena& a) {
+// With refine == false one pass (the FP32 transposed solve of L) is returned:
+// for products that carry FP32 rounding anyway (the tensor-core Jacobian).
+int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2* Z64, Arena& a, bool refine = true) {
   const int nb = ctx->B.nb, nl = ctx->nleaf, nlev = (int)ctx->levels.size();
   const size_t nbP = (size_t)nb * P;
   const double eta = ctx->k;
   const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-9;
-  const int max_iter = ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
+  const int max_iter = !refine ? 1 : ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
   const float2 one = make_float2(1.f, 0.f), mone = make_float2(-1.f, 0.f), zero = make_float2(0.f, 0.f);
   float2* G = a.get<float2>((size_t)nl * NL * P);
   float2 *bufA = a.get<float2>(field_buf_elems(ctx, P)), *bufB = a.get<float2>(field_buf_elems(ctx, P));
@@ -1267,7 +1329,7 @@ int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2
     ctx->adj_iters = it + 1;
     if (first) {
       y0_n2 = dn2;
-      if (!(y0_n2 > 0.0)) {  // no receiver sees the interior: Z = 0 exactly
+      if (!(y0_n2 > 0.0) || !refine) {  // no receiver sees the interior (Z = 0 exactly), or one pass asked for
         converged = true;
         break;
       }
@@ -1304,7 +1366,7 @@ size_t mixed_fields_bytes(hs_ctx* ctx, int M, int P) {
 // solve, adjoint fields Zg from the refined adjoint solve (both FP64-accurate),
 // on the interior grid.
 int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P,
-                             double2* F, double2* Ug, double2* Zg, Arena& a) {
+                             double2* F, double2* Ug, double2* Zg, Arena& a, bool refine_adjoint = true) {
   const int nb = ctx->B.nb;
   double2* X = a.get<double2>((size_t)ctx->nleaf * NL * M);
   double2* A2 = a.get<double2>((size_t)P * 2 * nb);
@@ -1318,7 +1380,7 @@ int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, 
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
   {
     Arena sub = a;
-    CKR(mixed_adjoint(ctx, s, A2, P, Z64, sub));
+    CKR(mixed_adjoint(ctx, s, A2, P, Z64, sub, refine_adjoint));
   }
   leaf_to_grid(s, Z64, NI, ctx->nL, P, Zg);
   CK(cudaGetLastError());
@@ -1839,7 +1901,12 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
     return fail(ctx, HS_EINVAL, "damp and tol must be >= 0 and max_iter >= 1");
   if (products != HS_FP64 && products != HS_MIXED) return fail(ctx, HS_EINVAL, "products must be HS_FP64 or HS_MIXED");
   const bool p32 = products == HS_MIXED;
+  // FP64 products with the emulated FP64 contraction: J formed once in FP64 and
+  // read twice per iteration (exact transposes of one matrix); without the
+  // emulation, J and J^H are applied from the fields by FP64 grid contractions
+  const bool p64x = !p32 && g_oz_enabled;
   const int C32 = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget / 2);
+  const int C64 = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget);
   cudaStream_t s = ctx->stream;
   const int MP = M * P, nm = ctx->S1 * ctx->S2, nX = ctx->n14, S1 = ctx->S1, S2 = ctx->S2;
   const size_t N = (size_t)nX * nX;
@@ -1855,8 +1922,12 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
                                  Arena::bytes((size_t)nX * S2, 4) + Arena::bytes(N * C32, 8) +
                                  Arena::bytes((size_t)nX * S1 * C32, 8) +
                                  Arena::bytes((size_t)gemvT_parts(MP) * nm, 8)
-                           : Arena::bytes((size_t)S2 * nX, 8) + Arena::bytes(N, 8) * 2 + Arena::bytes(N * M, 16) +
-                                 Arena::bytes(MP, 16) + Arena::bytes((size_t)S1 * nX, 8));
+                       : p64x ? Arena::bytes((size_t)MP * nm, 16) + Arena::bytes(N * C64, 16) +
+                                    Arena::bytes((size_t)nX * S1 * C64, 16) +
+                                    Arena::bytes(contract_emulated_bytes(C64, nX, S1, S2), 1) +
+                                    Arena::bytes((size_t)gemvT_parts(MP) * nm, 8)
+                              : Arena::bytes((size_t)S2 * nX, 8) + Arena::bytes(N, 8) * 2 + Arena::bytes(N * M, 16) +
+                                    Arena::bytes(MP, 16) + Arena::bytes((size_t)S1 * nX, 8));
   const size_t need = Arena::bytes(M, 8) + Arena::bytes(P, 8) + Arena::bytes((size_t)2 * MP, 8) +
                       Arena::bytes(8, 8) + Arena::bytes(MP, 16) * 2 + Arena::bytes(N * M, 16) +
                       Arena::bytes(N * P, 16) +
@@ -1876,9 +1947,9 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
-  if (mixed) {  // refined far field and forward fields, FP32 adjoint fields
+  if (mixed) {  // refined far field and forward fields; adjoint refined unless J is FP32 anyway
     Arena sub = a;
-    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub));
+    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub, !p32));
   } else {  // forward far field F(c)
     Arena sub = a;
     double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);
@@ -1906,7 +1977,16 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   float2 *J32 = nullptr, *sxc = nullptr, *W32 = nullptr, *T32 = nullptr;
   float* sy32 = nullptr;
   double* partT = nullptr;
-  if (!p32) {
+  double2 *J64 = nullptr, *W64 = nullptr, *T64 = nullptr;
+  char* oz = nullptr;
+  const size_t ozb = p64x ? contract_emulated_bytes(C64, nX, S1, S2) : 0;
+  if (p64x) {
+    J64 = a.get<double2>((size_t)MP * nm);
+    W64 = a.get<double2>(N * C64);
+    T64 = a.get<double2>((size_t)nX * S1 * C64);
+    oz = a.get<char>(ozb);
+    partT = a.get<double>((size_t)gemvT_parts(MP) * nm);
+  } else if (!p32) {
     G1 = a.get<double>((size_t)S2 * nX);
     qv = a.get<double>(N);
     h = a.get<double>(N);
@@ -1926,6 +2006,10 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
     Phase phj("hs_jacobian32");
     contract_jacobian32(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, J32, sxc, sy32, W32, T32, C32);
   }
+  if (p64x) {
+    Phase phj("hs_jacobian_contract");
+    contract_jacobian(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, J64, W64, T64, C64, oz, ozb);
+  }
   std::vector<unsigned char> keep(nm, 1);
   if (mask)
     for (int i = 0; i < nm; ++i) keep[i] = mask[i] ? 1 : 0;
@@ -1935,6 +2019,8 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
     CK(cudaMemcpyAsync(dv, v.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, s));
     if (p32)
       gemv32(s, J32, MP, nm, dv, dy);
+    else if (p64x)
+      gemv64(s, J64, MP, nm, dv, dy);
     else
       apply_J(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dv, G1, qv, Y, dy);
     CK(cudaMemcpyAsync(hy.data(), dy, sizeof(double2) * MP, cudaMemcpyDeviceToHost, s));
@@ -1950,6 +2036,8 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
     CK(cudaMemcpyAsync(dy, hy.data(), sizeof(double2) * MP, cudaMemcpyHostToDevice, s));
     if (p32)
       gemvT32(s, J32, MP, nm, dy, partT, dg);
+    else if (p64x)
+      gemvT64(s, J64, MP, nm, dy, partT, dg);
     else
       apply_JH(s, Ug, Zg, M, P, nX, ctx->d_sxi, ctx->d_syi, S1, S2, k2, dy, fc, Y, h, T1, dg);
     CK(cudaMemcpyAsync(out.data(), dg, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
@@ -2028,7 +2116,7 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   CK(cudaMemcpyAsync(&r2, nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
-  if (p32 && tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
+  if ((p32 || p64x) && tc_timed_out(s)) return fail(ctx, HS_ETIMEOUT, "a tensor-core GEMM wait gave up");
   for (int i = 0; i < nm; ++i) c_inout[i] += x[i];
   if (resid_norm_out) *resid_norm_out = std::sqrt(r2);
   if (iters_out) *iters_out = it;

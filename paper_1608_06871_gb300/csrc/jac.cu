@@ -94,7 +94,8 @@ __global__ void k_khatri_rao(const double2* __restrict__ Ug, const double2* __re
 // Scratch of the emulated products of a chunk of C pairs (the slices of its
 // Khatri-Rao rows for the x-projection, then of its half-projected rows).
 size_t contract_emulated_bytes(int C, int nX, int S1, int S2) {
-  return std::max(ozaki_scratch_bytes(2 * C * nX, S1, nX, 1, true), ozaki_scratch_bytes(2 * S1, S2, nX, C, true));
+  return oz_operand_bytes(S1, nX, 1, false) + oz_operand_bytes(S2, nX, 1, false) +
+         std::max(oz_operand_bytes(2 * C * nX, nX, 1, true), oz_operand_bytes(2 * S1, nX, C, true));
 }
 
 int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes) {
@@ -120,27 +121,36 @@ void contract_jacobian(cudaStream_t s, const double2* Ug, const double2* Zg, int
                        const double* sy, int S1, int S2, double k2, double2* J, double2* W, double2* T, int C,
                        void* scratch, size_t scratch_bytes) {
   const long long plane = (long long)nX * nX, MP = (long long)M * P;
+  const bool emu = g_oz_enabled && scratch && scratch_bytes >= contract_emulated_bytes(C, nX, S1, S2);
+  char* base = reinterpret_cast<char*>(scratch);
+  const size_t bsx = oz_operand_bytes(S1, nX, 1, false), bsy = oz_operand_bytes(S2, nX, 1, false);
+  char *osx = base, *osy = base + bsx, *oa = base + bsx + bsy;
+  if (emu) {  // the sine tables, sliced once as the right operands of both projections
+    oz_slice(s, OzView{const_cast<double*>(sx), 0, nX, 0, 1, 1}, S1, nX, 1, false, osx);
+    oz_slice(s, OzView{const_cast<double*>(sy), 0, nX, 0, 1, 1}, S2, nX, 1, false, osy);
+  }
   for (long long c0 = 0; c0 < MP; c0 += C) {
     const int nc = (int)std::min<long long>(C, MP - c0);
     const long long n = nc * plane;
-    k_khatri_rao<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ug, Zg, P, plane, c0, n, W);
-    HS_COUNT_LAUNCH();
     bool done = false;
-    if (g_oz_enabled && scratch) {
-      double* Wd = reinterpret_cast<double*>(W);
+    if (emu) {
       double* Td = reinterpret_cast<double*>(T);
       double* Jd = reinterpret_cast<double*>(J + c0 * S1 * S2);
-      // T[(pair, gy)][m1] = sum_gx W[(pair, gy)][gx] sx[m1][gx]
-      const OzView vw{Wd, 0, 2LL * nX, 1, 2, 2}, vsx{const_cast<double*>(sx), 0, nX, 0, 1, 1},
-          vt{Td, 0, 2LL * S1, 1, 2, 2};
+      // T[(pair, gy)][m1] = sum_gx (u_d z_p)[gy][gx] sx[m1][gx]: the Khatri-Rao rows are
+      // sliced straight from the fields (no W)
+      oz_slice_khatri_rao(s, Ug, Zg, P, nX, c0, nc, oa);
+      const OzView vt{Td, 0, 2LL * S1, 1, 2, 2};
+      done = oz_multiply(s, 2 * nc * nX, S1, nX, 1, 1.0, oa, osx, true, 0.0, vt) == cudaSuccess;
       // J_pair[m1][m2] = k2 sum_gy T_pair[gy][m1] sy[m2][gy]
-      const OzView vtt{Td, 2LL * nX * S1, 2, 1, 2LL * S1, 2}, vsy{const_cast<double*>(sy), 0, nX, 0, 1, 1},
-          vj{Jd, 2LL * S1 * S2, 2LL * S2, 1, 2, 2};
-      done = ozaki_gemm(s, 2 * nc * nX, S1, nX, 1, 1.0, vw, vsx, true, 0.0, vt, scratch, scratch_bytes) ==
-                 cudaSuccess &&
-             ozaki_gemm(s, 2 * S1, S2, nX, nc, k2, vtt, vsy, true, 0.0, vj, scratch, scratch_bytes) == cudaSuccess;
+      if (done) {
+        const OzView vtt{Td, 2LL * nX * S1, 2, 1, 2LL * S1, 2}, vj{Jd, 2LL * S1 * S2, 2LL * S2, 1, 2, 2};
+        oz_slice(s, vtt, 2 * S1, nX, nc, true, oa);
+        done = oz_multiply(s, 2 * S1, S2, nX, nc, k2, oa, osy, true, 0.0, vj) == cudaSuccess;
+      }
     }
     if (!done) {
+      k_khatri_rao<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ug, Zg, P, plane, c0, n, W);
+      HS_COUNT_LAUNCH();
       gemm<double2, double, double2>(s, OP_N, OP_T, nc * nX, S1, nX, make_double2(1.0, 0.0), W, nX, 0, sx, nX, 0,
                                      make_double2(0.0, 0.0), T, S1, 0, 1);
       gemm<double2, double, double2>(s, OP_T, OP_T, S1, S2, nX, make_double2(k2, 0.0), T, S1, (long long)nX * S1, sy,
@@ -254,15 +264,18 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
 }
 
 // y[r] = sum_m J[r][m] v[m]  (complex J in FP32, real v, FP64 sums; one warp per row)
-__global__ void k_gemv32(const float2* __restrict__ J, const double* __restrict__ v, long long rows, int n,
-                         double2* __restrict__ y) {
+// y[r] = sum_m J[r][m] v[m] (J complex FP32 or FP64, v real, FP64 sums): one
+// warp per row.
+template <typename TJ>
+__global__ void k_gemv(const TJ* __restrict__ J, const double* __restrict__ v, long long rows, int n,
+                       double2* __restrict__ y) {
   const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
-  const float2* row = J + r * n;
+  const TJ* row = J + r * n;
   double ax = 0.0, ay = 0.0;
   for (int m = lane; m < n; m += 32) {
-    const float2 a = row[m];
+    const TJ a = row[m];
     const double w = v[m];
     ax = fma((double)a.x, w, ax);
     ay = fma((double)a.y, w, ay);
@@ -276,15 +289,16 @@ __global__ void k_gemv32(const float2* __restrict__ J, const double* __restrict_
 
 // part[b][m] = sum over rows r of block b of Re(conj(J[r][m]) u[r])  (FP64 sums)
 constexpr int kRowsPerPart = 256;
-__global__ void k_gemvT32(const float2* __restrict__ J, const double2* __restrict__ u, long long rows, int n,
-                          double* __restrict__ part) {
+template <typename TJ>
+__global__ void k_gemvT(const TJ* __restrict__ J, const double2* __restrict__ u, long long rows, int n,
+                        double* __restrict__ part) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const long long r0 = (long long)blockIdx.y * kRowsPerPart;
   if (m >= n) return;
   const long long r1 = min(rows, r0 + kRowsPerPart);
   double acc = 0.0;
   for (long long r = r0; r < r1; ++r) {
-    const float2 a = J[r * n + m];
+    const TJ a = J[r * n + m];
     const double2 b = u[r];
     acc = fma((double)a.x, b.x, acc);
     acc = fma((double)a.y, b.y, acc);
@@ -302,18 +316,32 @@ __global__ void k_sum_rows(const double* __restrict__ part, int nparts, int n, d
 
 int gemvT_parts(long long rows) { return (int)((rows + kRowsPerPart - 1) / kRowsPerPart); }
 
-void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double* v, double2* y) {
+template <typename TJ> void gemv_j(cudaStream_t s, const TJ* J, long long rows, int n, const double* v, double2* y) {
   const long long threads = rows * 32;
-  k_gemv32<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(J, v, rows, n, y);
+  k_gemv<TJ><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(J, v, rows, n, y);
   HS_COUNT_LAUNCH();
 }
 
-void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g) {
+template <typename TJ>
+void gemvT_j(cudaStream_t s, const TJ* J, long long rows, int n, const double2* u, double* part, double* g) {
   const int np = gemvT_parts(rows);
-  k_gemvT32<<<dim3((n + 127) / 128, np), 128, 0, s>>>(J, u, rows, n, part);
+  k_gemvT<TJ><<<dim3((n + 127) / 128, np), 128, 0, s>>>(J, u, rows, n, part);
   HS_COUNT_LAUNCH();
   k_sum_rows<<<(n + 255) / 256, 256, 0, s>>>(part, np, n, g);
   HS_COUNT_LAUNCH();
+}
+
+void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double* v, double2* y) {
+  gemv_j<float2>(s, J, rows, n, v, y);
+}
+void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g) {
+  gemvT_j<float2>(s, J, rows, n, u, part, g);
+}
+void gemv64(cudaStream_t s, const double2* J, long long rows, int n, const double* v, double2* y) {
+  gemv_j<double2>(s, J, rows, n, v, y);
+}
+void gemvT64(cudaStream_t s, const double2* J, long long rows, int n, const double2* u, double* part, double* g) {
+  gemvT_j<double2>(s, J, rows, n, u, part, g);
 }
 
 // Jst = [Re J; Im J] (2 rows x cols, real).

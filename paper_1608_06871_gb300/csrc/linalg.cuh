@@ -75,5 +75,17 @@ size_t ozaki_scratch_bytes(int m, int n, int k, int batch, bool b_shared);
 // tensor-map encoder is unavailable, cudaErrorInvalidValue on bad sizes.
 cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double alpha, OzView A, OzView Bt,
                        bool b_shared, double beta, OzView C, void* scratch, size_t scratch_bytes);
+// The same in two steps, for an operand used by many products: oz_slice cuts
+// the rows of a view (A's rows with is_a, or B's columns through Bt) into
+// oz_operand_bytes of slices, once; oz_multiply multiplies two sliced operands.
+size_t oz_operand_bytes(int rows, int k, int batch, bool is_a);
+void oz_slice(cudaStream_t s, OzView v, int rows, int k, int batch, bool is_a, void* buf);
+cudaError_t oz_multiply(cudaStream_t s, int m, int n, int k, int batch, double alpha, const void* Aop, const void* Bop,
+                        bool b_shared, double beta, OzView C);
+// The left operand of the Jacobian's x-projection for the pairs c0 .. c0 + nc - 1
+// of d * P + p, sliced straight from the fields: rows 2 (c nX + gy) + part of
+// u_d z_p over gx (2 nc nX rows, k = nX; oz_operand_bytes(2 nc nX, nX, 1, true)).
+void oz_slice_khatri_rao(cudaStream_t s, const double2* Ug, const double2* Zg, int P, int nX, long long c0, int nc,
+                         void* buf);
 
 }  // namespace hs

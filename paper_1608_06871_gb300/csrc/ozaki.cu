@@ -54,7 +54,7 @@ constexpr int OZ_ND = 8;         // anti-diagonals kept (s + t <= 7)
 constexpr int OZ_TM = 128;       // rows per tile
 constexpr int OZ_TN = 64;        // columns per tile
 constexpr int OZ_KS = 32;        // k per stage
-constexpr int OZ_KMAX = 384;     // k per launch keeping every diagonal sum below 2^24
+constexpr int OZ_KMAX = 384;     // k per launch keeping every diagonal sum below 2^24 (a multiple of 32)
 constexpr int OZ_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr int OZ_A_KB = OZ_S * OZ_TM * 16;  // bytes of one 8-wide k block of all A slices (16 KB)
 constexpr int OZ_B_KB = OZ_S * OZ_TN * 16;  // same for B (8 KB)
@@ -108,10 +108,35 @@ __device__ __forceinline__ long long vaddr(const OzView& v, long long b, long lo
   return b * v.sb + (i / v.ig) * v.si + (i % v.ig) * v.sg + k * v.sk;
 }
 
+// |x| as ordered 64-bit integers (the bit pattern of a non-negative double).
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+
+// round(x 2^(56 - e)) for |x| < 2^e, in integer arithmetic on the bit pattern
+// (mantissa shifted by the exponent difference, rounded to nearest); 0 for
+// zeros and subnormals, whose contribution is below the slices' resolution.
+__device__ __forceinline__ long long fixed56(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;  // 53-bit significand
+  const int sh = E - 1075 + 56 - e;                                     // x 2^(56-e) = m 2^sh, sh <= 3
+  long long v;
+  if (sh >= 0) v = m << sh;
+  else if (sh > -60) v = (m + (1LL << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return b < 0 ? -v : v;
+}
+
 // Slices of the rows of a view (rows = A's rows, or B's columns): one warp
 // per row, lanes along k; slices written to out[s][b * rpad + i][kk] (BF16,
 // kpad wide, zero padded), the row's exponent to e[b * rpad + i].  Padding
-// rows get zero slices.
+// rows get zero slices.  All in integer arithmetic (the FP64 pipe is the
+// scarce unit): the row's largest magnitude fixes e with max 2^-e in
+// [1/2, 1); each entry becomes the 56-bit fixed-point integer
+// N = round(x 2^(56 - e)), |N| < 2^56, whose balanced base-128 digits are the
+// slices: a_s = round(N_s / 2^(49 - 7 s)), N_(s+1) = N_s - a_s 2^(49 - 7 s)
+// (|a_0| <= 128, |a_s| <= 64 after; the last digit takes the exact rest, so
+// the slices represent N exactly).
 __global__ void k_oz_slice(OzView v, int rows, int k, int rpad, int kpad, int batch, __nv_bfloat16* __restrict__ out,
                            int* __restrict__ e) {
   const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -123,22 +148,105 @@ __global__ void k_oz_slice(OzView v, int rows, int k, int rpad, int kpad, int ba
   const long long plane = total * kpad;
   __nv_bfloat16* o = out + r * kpad;
   const bool live = i < rows;
-  double mx = 0.0;
-  if (live)
-    for (int kk = lane; kk < k; kk += 32) mx = fmax(mx, fabs(v.p[vaddr(v, b, i, kk)]));
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  const int ex = mx > 0.0 ? ilogb(mx) + 1 : 0;  // mx 2^-ex in [1/2, 1)
+  // the row's piece (k <= OZ_KMAX) is read once into registers
+  constexpr int KPL = OZ_KMAX / 32;
+  double x[KPL];
+  long long mx = 0;
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int kk = lane + 32 * q;
+    x[q] = (live && kk < k) ? v.p[vaddr(v, b, i, kk)] : 0.0;
+    mx = max(mx, abs_bits(x[q]));
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const int Emax = (int)(mx >> 52);
+  const int ex = mx == 0 ? 0 : Emax - 1022;  // largest |x| in [2^(ex-1), 2^ex)
   if (lane == 0) e[r] = ex;
-  for (int kk = lane; kk < kpad; kk += 32) {
-    double x = (live && kk < k) ? scalbn(v.p[vaddr(v, b, i, kk)], -ex) : 0.0;
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int kk = lane + 32 * q;
+    if (kk >= kpad) break;
+    long long n = fixed56(x[q], ex);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      const double t = x * 128.0;  // exact
-      const double a = rint(t);    // |a| <= 128 (s = 0), <= 64 after
-      x = t - a;                  // exact
+      const int sh = 49 - 7 * s;
+      const long long a = sh > 0 ? (n + (1LL << (sh - 1))) >> sh : n;  // round to nearest (ties up); last: exact
+      n -= a << sh;
       o[s * plane + kk] = __float2bfloat16_rn((float)a);
     }
   }
+}
+
+// Slices of the Khatri-Rao rows of a chunk of (incidence, receiver) pairs, for
+// the x-projection of the Jacobian: complex row (pair c, gy) of w = u_d z_p
+// (d = (c0 + c) / P, p = (c0 + c) % P, fields on the interior grid,
+// [rhs][gy][gx]) over gx in [k0, k0 + kc), split into its real part (row
+// 2 (c nX + gy)) and imaginary part (row 2 (c nX + gy) + 1).  One warp per
+// complex row; the product is formed in FP64 in registers and never stored.
+__global__ void k_oz_slice_kr(const double2* __restrict__ Ug, const double2* __restrict__ Zg, int P, int nX,
+                              long long c0, int nc, int k0, int kc, int rpad, int kpad, __nv_bfloat16* __restrict__ out,
+                              int* __restrict__ e) {
+  const long long r2 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r2 >= (long long)nc * nX) return;
+  const long long c = c0 + r2 / nX, gy = r2 % nX, plane = (long long)nX * nX;
+  const double2* u = Ug + (c / P) * plane + gy * nX + k0;
+  const double2* z = Zg + (c % P) * plane + gy * nX + k0;
+  constexpr int KPL = OZ_KMAX / 32;
+  double wr[KPL], wi[KPL];
+  long long mr = 0, mi = 0;
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int kk = lane + 32 * q;
+    double2 w = make_double2(0.0, 0.0);
+    if (kk < kc) {
+      const double2 a = u[kk], b = z[kk];
+      w = make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    }
+    wr[q] = w.x;
+    wi[q] = w.y;
+    mr = max(mr, abs_bits(w.x));
+    mi = max(mi, abs_bits(w.y));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, off));
+    mi = max(mi, __shfl_xor_sync(0xffffffffu, mi, off));
+  }
+  const int er = mr == 0 ? 0 : (int)(mr >> 52) - 1022, ei = mi == 0 ? 0 : (int)(mi >> 52) - 1022;
+  const long long plane_s = (long long)rpad * kpad;
+  __nv_bfloat16* o_re = out + (2 * r2) * kpad;
+  __nv_bfloat16* o_im = o_re + kpad;
+  if (lane == 0) {
+    e[2 * r2] = er;
+    e[2 * r2 + 1] = ei;
+  }
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int kk = lane + 32 * q;
+    if (kk >= kpad) break;
+    long long nr = fixed56(wr[q], er), ni = fixed56(wi[q], ei);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const int sh = 49 - 7 * s;
+      const long long ar = sh > 0 ? (nr + (1LL << (sh - 1))) >> sh : nr;
+      const long long ai = sh > 0 ? (ni + (1LL << (sh - 1))) >> sh : ni;
+      nr -= ar << sh;
+      ni -= ai << sh;
+      o_re[s * plane_s + kk] = __float2bfloat16_rn((float)ar);
+      o_im[s * plane_s + kk] = __float2bfloat16_rn((float)ai);
+    }
+  }
+}
+
+// Zero slices of the padding rows [first, rpad) of every slice plane.
+__global__ void k_oz_zero_rows(long long first, int rpad, int kpad, __nv_bfloat16* __restrict__ out, int* __restrict__ e) {
+  const long long n = (long long)(rpad - first) * kpad;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * OZ_S) return;
+  const int s = (int)(t / n);
+  const long long j = t % n;
+  out[(long long)s * rpad * kpad + first * kpad + j] = __float2bfloat16_rn(0.f);
+  if (s == 0 && j % kpad == 0) e[first + j / kpad] = 0;
 }
 
 struct OzParams {
@@ -324,14 +432,14 @@ bool oz_timed_out(cudaStream_t s) {
 size_t ozaki_scratch_bytes(int m, int n, int k, int batch, bool b_shared) {
   const long long kp = rup(std::min(k, OZ_KMAX), OZ_KS), mp = rup(m, OZ_TM), np = rup(n, OZ_TN);
   const long long nbB = b_shared ? 1 : batch;
-  return (size_t)(OZ_S * kp * 2 * (batch * mp + nbB * np) + 4 * (batch * mp + nbB * np) + 4 * 1024);
+  const size_t a = ((size_t)OZ_S * batch * mp * kp * 2 + 1023) / 1024 * 1024 + ((size_t)batch * mp * 4 + 1023) / 1024 * 1024;
+  const size_t b = ((size_t)OZ_S * nbB * np * kp * 2 + 1023) / 1024 * 1024 + ((size_t)nbB * np * 4 + 1023) / 1024 * 1024;
+  return a + b;
 }
 
-cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double alpha, OzView A, OzView Bt, bool b_shared,
-                       double beta, OzView C, void* scratch, size_t scratch_bytes) {
-  if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535) return cudaErrorInvalidValue;
-  if (!encode_fn()) return cudaErrorNotSupported;
-  if (ozaki_scratch_bytes(m, n, k, batch, b_shared) > scratch_bytes) return cudaErrorInvalidValue;
+namespace {
+
+void set_smem_attr() {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -339,52 +447,165 @@ cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double al
     cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
+}
+
+// One launch of the tile kernel over a piece of k: sliced operands sa / sbt
+// (rows padded to mp / np, kp wide) and their exponents.
+cudaError_t launch_piece(cudaStream_t s, int m, int n, int kc, long long kp, long long mp, long long np, int batch,
+                         bool b_shared, double alpha, double beta, __nv_bfloat16* sa, const int* ea,
+                         __nv_bfloat16* sbt, const int* eb, OzView C) {
+  CUtensorMap ma, mb;
+  const long long ra = batch * mp, rb = (b_shared ? 1 : batch) * np;
+  if (!make_map(&ma, sa, ra, (int)kp, OZ_TM) || !make_map(&mb, sbt, rb, (int)kp, OZ_TN)) return cudaErrorInvalidValue;
+  OzParams P;
+  P.m = m;
+  P.n = n;
+  P.k = kc;
+  P.mpad = (int)mp;
+  P.npad = (int)np;
+  P.kpad = (int)kp;
+  P.nb_batch_b = b_shared ? 0 : 1;
+  P.alpha = alpha;
+  P.beta = beta;
+  P.ea = ea;
+  P.eb = eb;
+  P.C = C;
+  dim3 grid((unsigned)(np / OZ_TN), (unsigned)(mp / OZ_TM), (unsigned)batch);
+  const bool prof = prof_active(4);
+  cudaEvent_t ev = nullptr;
+  if (prof) prof_begin(s, &ev);
+  k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ma, mb, P);
+  HS_COUNT_LAUNCH();
+  if (prof) prof_end(s, ev, 2.0 * m * n * kc * batch);  // FP64-equivalent flops
+  return cudaSuccess;
+}
+
+size_t align_up(size_t b) { return (b + 1023) & ~size_t(1023); }
+
+// Length of the pieces k is cut into: as equal as possible, at most OZ_KMAX,
+// a multiple of the stage depth (the last piece takes the rest).
+int piece_len(int k) {
+  const int np = (k + OZ_KMAX - 1) / OZ_KMAX;
+  return (int)std::min<long long>(OZ_KMAX, rup((k + np - 1) / np, OZ_KS));
+}
+
+// Byte layout of a sliced operand: piece after piece, each the slices
+// [OZ_S][batch * rpad][kp] and the exponents [batch * rpad].
+struct Piece {
+  size_t slices, exps, next;
+  long long kp;
+  int kc;
+};
+Piece piece_at(size_t off, int k0, int k, long long rows_total) {
+  Piece p;
+  p.kc = std::min(piece_len(k), k - k0);
+  p.kp = rup(p.kc, OZ_KS);
+  p.slices = off;
+  p.exps = off + align_up((size_t)OZ_S * rows_total * p.kp * 2);
+  p.next = p.exps + align_up((size_t)rows_total * 4);
+  return p;
+}
+
+}  // namespace
+
+size_t oz_operand_bytes(int rows, int k, int batch, bool is_a) {
+  const long long rt = (long long)batch * rup(rows, is_a ? OZ_TM : OZ_TN);
+  size_t off = 0;
+  for (int k0 = 0; k0 < k; k0 += piece_len(k)) off = piece_at(off, k0, k, rt).next;
+  return off;
+}
+
+void oz_slice(cudaStream_t s, OzView v, int rows, int k, int batch, bool is_a, void* buf) {
+  const long long rpad = rup(rows, is_a ? OZ_TM : OZ_TN), rt = batch * rpad;
+  char* base = reinterpret_cast<char*>(buf);
+  size_t off = 0;
+  for (int k0 = 0; k0 < k; k0 += piece_len(k)) {
+    const Piece p = piece_at(off, k0, k, rt);
+    OzView w = v;
+    w.p += k0 * v.sk;
+    k_oz_slice<<<(unsigned)((rt + 7) / 8), 256, 0, s>>>(w, rows, p.kc, (int)rpad, (int)p.kp, batch,
+                                                      reinterpret_cast<__nv_bfloat16*>(base + p.slices),
+                                                      reinterpret_cast<int*>(base + p.exps));
+    HS_COUNT_LAUNCH();
+    off = p.next;
+  }
+}
+
+void oz_slice_khatri_rao(cudaStream_t s, const double2* Ug, const double2* Zg, int P, int nX, long long c0, int nc,
+                         void* buf) {
+  const int rows = 2 * nc * nX;
+  const long long rpad = rup(rows, OZ_TM);
+  char* base = reinterpret_cast<char*>(buf);
+  size_t off = 0;
+  for (int k0 = 0; k0 < nX; k0 += piece_len(nX)) {
+    const Piece p = piece_at(off, k0, nX, rpad);
+    __nv_bfloat16* sl = reinterpret_cast<__nv_bfloat16*>(base + p.slices);
+    int* ex = reinterpret_cast<int*>(base + p.exps);
+    const long long warps = (long long)nc * nX;
+    k_oz_slice_kr<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(Ug, Zg, P, nX, c0, nc, k0, p.kc, (int)rpad, (int)p.kp,
+                                                             sl, ex);
+    HS_COUNT_LAUNCH();
+    if (rpad > rows) {
+      const long long n = (rpad - rows) * p.kp * OZ_S;
+      k_oz_zero_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rows, (int)rpad, (int)p.kp, sl, ex);
+      HS_COUNT_LAUNCH();
+    }
+    off = p.next;
+  }
+}
+
+cudaError_t oz_multiply(cudaStream_t s, int m, int n, int k, int batch, double alpha, const void* Aop, const void* Bop,
+                        bool b_shared, double beta, OzView C) {
+  if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535) return cudaErrorInvalidValue;
+  if (!encode_fn()) return cudaErrorNotSupported;
+  set_smem_attr();
+  const long long mp = rup(m, OZ_TM), np = rup(n, OZ_TN);
+  char* a = const_cast<char*>(reinterpret_cast<const char*>(Aop));
+  char* b = const_cast<char*>(reinterpret_cast<const char*>(Bop));
+  size_t oa = 0, ob = 0;
+  for (int k0 = 0; k0 < k; k0 += piece_len(k)) {
+    const Piece pa = piece_at(oa, k0, k, batch * mp), pb = piece_at(ob, k0, k, (b_shared ? 1 : batch) * np);
+    const cudaError_t e =
+        launch_piece(s, m, n, pa.kc, pa.kp, mp, np, batch, b_shared, alpha, k0 == 0 ? beta : 1.0,
+                     reinterpret_cast<__nv_bfloat16*>(a + pa.slices), reinterpret_cast<const int*>(a + pa.exps),
+                     reinterpret_cast<__nv_bfloat16*>(b + pb.slices), reinterpret_cast<const int*>(b + pb.exps), C);
+    if (e != cudaSuccess) return e;
+    oa = pa.next;
+    ob = pb.next;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double alpha, OzView A, OzView Bt, bool b_shared,
+                       double beta, OzView C, void* scratch, size_t scratch_bytes) {
+  if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535) return cudaErrorInvalidValue;
+  if (!encode_fn()) return cudaErrorNotSupported;
+  if (ozaki_scratch_bytes(m, n, k, batch, b_shared) > scratch_bytes) return cudaErrorInvalidValue;
+  set_smem_attr();
   const long long mp = rup(m, OZ_TM), np = rup(n, OZ_TN);
   const long long nbB = b_shared ? 1 : batch;
-  for (int k0 = 0; k0 < k; k0 += OZ_KMAX) {
-    const int kc = std::min(OZ_KMAX, k - k0);
-    const long long kp = rup(kc, OZ_KS);
-    char* p = reinterpret_cast<char*>(scratch);
-    auto take = [&](size_t bytes) {
-      char* q = p;
-      p += (bytes + 1023) & ~size_t(1023);
-      return q;
-    };
-    __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(take((size_t)OZ_S * batch * mp * kp * 2));
-    __nv_bfloat16* sbt = reinterpret_cast<__nv_bfloat16*>(take((size_t)OZ_S * nbB * np * kp * 2));
-    int* ea = reinterpret_cast<int*>(take((size_t)batch * mp * 4));
-    int* eb = reinterpret_cast<int*>(take((size_t)nbB * np * 4));
+  // piece by piece, slicing each piece of both operands into the same scratch
+  for (int k0 = 0; k0 < k; k0 += piece_len(k)) {
+    const Piece pa = piece_at(0, k0, k, batch * mp), pb = piece_at(pa.next, k0, k, nbB * np);
+    char* base = reinterpret_cast<char*>(scratch);
     OzView a = A, bt = Bt;
     a.p += k0 * A.sk;
     bt.p += k0 * Bt.sk;
     const long long ra = batch * mp, rb = nbB * np;
-    k_oz_slice<<<(unsigned)((ra + 7) / 8), 256, 0, s>>>(a, m, kc, (int)mp, (int)kp, batch, sa, ea);
+    k_oz_slice<<<(unsigned)((ra + 7) / 8), 256, 0, s>>>(a, m, pa.kc, (int)mp, (int)pa.kp, batch,
+                                                      reinterpret_cast<__nv_bfloat16*>(base + pa.slices),
+                                                      reinterpret_cast<int*>(base + pa.exps));
     HS_COUNT_LAUNCH();
-    k_oz_slice<<<(unsigned)((rb + 7) / 8), 256, 0, s>>>(bt, n, kc, (int)np, (int)kp, (int)nbB, sbt, eb);
+    k_oz_slice<<<(unsigned)((rb + 7) / 8), 256, 0, s>>>(bt, n, pb.kc, (int)np, (int)pb.kp, (int)nbB,
+                                                      reinterpret_cast<__nv_bfloat16*>(base + pb.slices),
+                                                      reinterpret_cast<int*>(base + pb.exps));
     HS_COUNT_LAUNCH();
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, sa, ra, (int)kp, OZ_TM) || !make_map(&mb, sbt, rb, (int)kp, OZ_TN))
-      return cudaErrorInvalidValue;
-    OzParams P;
-    P.m = m;
-    P.n = n;
-    P.k = kc;
-    P.mpad = (int)mp;
-    P.npad = (int)np;
-    P.kpad = (int)kp;
-    P.nb_batch_b = b_shared ? 0 : 1;
-    P.alpha = alpha;
-    P.beta = k0 == 0 ? beta : 1.0;
-    P.ea = ea;
-    P.eb = eb;
-    P.C = C;
-    dim3 grid((unsigned)(np / OZ_TN), (unsigned)(mp / OZ_TM), (unsigned)batch);
-    const bool prof = prof_active(4);
-    cudaEvent_t ev = nullptr;
-    if (prof) prof_begin(s, &ev);
-    k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ma, mb, P);
-    HS_COUNT_LAUNCH();
-    if (prof) prof_end(s, ev, 2.0 * m * n * kc * batch);  // FP64-equivalent flops
+    const cudaError_t e =
+        launch_piece(s, m, n, pa.kc, pa.kp, mp, np, batch, b_shared, alpha, k0 == 0 ? beta : 1.0,
+                     reinterpret_cast<__nv_bfloat16*>(base + pa.slices), reinterpret_cast<const int*>(base + pa.exps),
+                     reinterpret_cast<__nv_bfloat16*>(base + pb.slices), reinterpret_cast<const int*>(base + pb.exps),
+                     C);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

@@ -149,6 +149,9 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
 int gemvT_parts(long long rows);
 void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double* v, double2* y);
 void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g);
+// The same on an explicit FP64 Jacobian.
+void gemv64(cudaStream_t s, const double2* J, long long rows, int n, const double* v, double2* y);
+void gemvT64(cudaStream_t s, const double2* J, long long rows, int n, const double2* u, double* part, double* g);
 // A = Jst^T Jst (n x n) by block rows of its lower part, mirrored.
 void normal_matrix(cudaStream_t s, const double* Jst, int rows, int n, double* A);
 // The same from the transposed stack JstT = [Re J; Im J]^T (n x 2 MP, written by

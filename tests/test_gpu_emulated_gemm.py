@@ -83,3 +83,52 @@ def _extreme(hs, k):
     exact = np.einsum("ik,kj->ij", A[0].cpu().numpy().astype(np.longdouble), B[0].cpu().numpy().astype(np.longdouble))
     err = np.abs(C[0].cpu().numpy().astype(np.longdouble) - exact)
     assert float(np.max(err / (k * U * np.abs(exact).max()))) < 1.0
+
+
+def _emulation(hs, on):
+    hs.hs_set_fp64_emulation(on)
+
+
+def test_jacobian_with_and_without_emulation(hs):
+    """The Jacobian contraction (k = 20, 16 x 16 leaves, 16 x 16 modes) with the emulated products
+    and with the FP64 SIMT GEMMs agrees to rounding."""
+    import synth
+    from parity import rel
+    c = synth.project_sine(synth.ellipse_phantom(3), 16, 16)
+    al, th = synth.directions(24), synth.receivers(32)
+    out = []
+    for on in (True, False):
+        _emulation(hs, on)
+        try:
+            s = hs.Solver(16, 16, 16).build(c, 20.0)
+            out.append(s.jacobian(al, th))
+            s.close()
+        finally:
+            _emulation(hs, True)
+    assert rel(out[0], out[1]) < 1e-12
+
+
+def test_lsqr_and_mixed_solve_with_and_without_emulation(hs):
+    """LSQR with FP64 products (explicit emulated J vs. products from the fields) at equal
+    iteration counts, and the mixed-precision forward solve (emulated vs. SIMT exterior residual
+    and far field), at k = 5 on 4 x 4 leaves."""
+    import synth
+    from parity import rel
+    from oracle import forward as F
+    al, th = synth.directions(8), synth.receivers(12)
+    data, _ = F.forward_from_function(synth.gaussian_bumps(1), 5.0, 4).solve_plane(al, th)
+    c = synth.random_coeffs(6, 6, seed=4, scale=0.02)
+    steps, fars = [], []
+    for on in (True, False):
+        _emulation(hs, on)
+        try:
+            s = hs.Solver(4, 6, 6).build(c, 5.0)
+            steps.append(s.gn_step_lsqr(data, al, th, c, tol=0.0, max_iter=8)[0] - c)
+            s.close()
+            m = hs.Solver(4, 6, 6, precision=hs.HS_MIXED).build(c, 5.0)
+            fars.append(m.solve(al, th))
+            m.close()
+        finally:
+            _emulation(hs, True)
+    assert rel(steps[0], steps[1]) < 1e-9
+    assert rel(fars[0], fars[1]) < 1e-10

@@ -199,6 +199,12 @@ struct hs_ctx {
   // per-call workspace
   char* ws_base = nullptr;
   size_t ws_cap = 0;
+  // the wavenumber of the current build on the device: the kernels of the
+  // captured factorisation and refinement passes read it there, so one graph
+  // serves every k of a sweep on this tree
+  double* d_k = nullptr;
+  double k_dev = 0.0;
+  long long builds = 0;
   // phase times of the last build recorded launch by launch (-1 after a graph replay)
   cudaEvent_t ph_ev[3] = {nullptr, nullptr, nullptr};
   double t_interior = -1.0, t_bdry = -1.0;
@@ -708,6 +714,7 @@ int setup(hs_ctx* ctx) {
   CKR(dalloc(ctx, &ctx->d_syi, (size_t)S2 * ctx->n14));
   ctx->ninfo = std::max(ctx->nleaf, 16) + 1;
   CKR(dalloc(ctx, &ctx->d_info, ctx->ninfo));
+  CKR(dalloc(ctx, &ctx->d_k, 1));
   // leaf factors and scratch
   const size_t nl = ctx->nleaf;
   if (ctx->cfg.precision == HS_FP64) {
@@ -747,6 +754,26 @@ int setup(hs_ctx* ctx) {
   return HS_OK;
 }
 
+// The wavenumber of the build into the device scalar the kernels read.
+int set_device_k(hs_ctx* ctx, cudaStream_t s, double k) {
+  ctx->k_dev = k;
+  CK(cudaMemcpyAsync(ctx->d_k, &ctx->k_dev, sizeof(double), cudaMemcpyHostToDevice, s));
+  return HS_OK;
+}
+
+// The layer-potential matrices of the mixed path for a new k (S, D - I/2, B1,
+// B2 and the stacked exterior rows in FP64 and FP32): they depend on k and the
+// boundary only.
+void assemble_exterior_mixed(hs_ctx* ctx, cudaStream_t s, double k) {
+  const int nb = ctx->B.nb;
+  const long long nn = (long long)nb * nb;
+  bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
+  bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
+  convert_d2f(s, ctx->d_B2, ctx->d_B2_32, nn);
+  stack_exterior(s, ctx->d_Dm, ctx->d_S, nb, ctx->d_DS, ctx->d_DS32);
+  ctx->bie_k = k;
+}
+
 // FP32 factors of the mixed-precision path: leaves, merges and the coupled
 // root system in complex FP32; the layer-potential matrices stay in FP64 for
 // the refinement residual.
@@ -755,8 +782,8 @@ int setup(hs_ctx* ctx) {
 int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s, bool record) {
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
   if (record) CK(cudaEventRecord(ctx->ph_ev[0], s));
-  leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32, nullptr,
-                          ctx->d_info);
+  leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->d_k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32,
+                          nullptr, ctx->d_info);
   const float2* Rc = ctx->d_R32;
   for (size_t li = 0; li < ctx->levels.size(); ++li) {
     merge_level<float2>(s, ctx->levels[li], ctx->ops32[li], Rc, ctx->d_info);
@@ -766,13 +793,9 @@ int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s, bool record) {
   const int nb = ctx->B.nb;
   permute_square<float2>(s, Rc, ctx->d_root_of_bie, nb, ctx->d_Rb32);  // root map in boundary-node order
   const long long nn = (long long)nb * nb;
-  if (ctx->bie_k != k) {  // S, D - I/2, B1, B2 depend on k and the boundary only
-    bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
-    bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
-    convert_d2f(s, ctx->d_B2, ctx->d_B2_32, nn);
-    stack_exterior(s, ctx->d_Dm, ctx->d_S, nb, ctx->d_DS, ctx->d_DS32);
-    ctx->bie_k = k;
-  }
+  // a new k's layer potentials (the captured sequence never holds them: before a
+  // replay they are assembled eagerly, see factor_mixed)
+  if (ctx->bie_k != k) assemble_exterior_mixed(ctx, s, k);
   convert_d2f(s, ctx->d_B1, ctx->d_C32, nn);
   gemm<float2, float2, float2>(s, OP_N, OP_N, nb, nb, nb, make_float2(-1.f, 0.f), ctx->d_B2_32, nb, 0, ctx->d_Rb32,
                                nb, 0, make_float2(1.f, 0.f), ctx->d_C32, nb, 0, 1);
@@ -785,26 +808,30 @@ int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s, bool record) {
   return HS_OK;
 }
 
-// Mixed-precision factorisation.  The first build at a frequency runs
-// eagerly (it also forms the boundary-integral matrices of that k); later
-// builds at the same k replay a CUDA graph of the same launch sequence
-// (about 900 launches: leaf factors, every merge level, the root), captured
-// once per k, which removes the per-launch host overhead and the gaps between
-// the many small kernels.
+// Mixed-precision factorisation.  The first build of a context runs eagerly
+// (its phases are timed); every later build, at any k, replays a CUDA graph of
+// the same launch sequence (about 900 launches: leaf factors, every merge
+// level, the root), captured at the second build: the kernels read k from
+// device memory, and a new k's layer-potential matrices are assembled eagerly
+// before the replay.  This removes the per-launch host overhead and the gaps
+// between the many small kernels at every frequency of a sweep.
 int factor_mixed(hs_ctx* ctx, double k) {
   cudaStream_t s = ctx->stream;
   Phase ph("hs_factor_mixed");
+  CKR(set_device_k(ctx, s, k));
   // (per-launch profiling of the FP32 families needs eager launches; the
   // factorisation has no FP64 GEMM, so FP64 profiling does not prevent it)
-  const bool graph = g_use_graphs && ctx->bie_k == k && !prof_active(2) && !prof_active(3);
+  const bool graph = g_use_graphs && ctx->builds > 0 && !prof_active(2) && !prof_active(3);
   if (!graph) CKR(phase_events(ctx));
-  CKR(run_captured(ctx, s, ctx->fgraph, graph, nullptr, 0, 0, k,
+  if (graph && ctx->bie_k != k) assemble_exterior_mixed(ctx, s, k);
+  CKR(run_captured(ctx, s, ctx->fgraph, graph, nullptr, 0, 0, 0.0,
                    [&] { return enqueue_factor_mixed(ctx, k, s, !graph); }));
   ctx->Rroot32 = nullptr;
   CKR(check_info(ctx));
   phase_times(ctx, !graph);
   ctx->k = k;
   ctx->built = true;
+  ++ctx->builds;
   return HS_OK;
 }
 
@@ -813,12 +840,13 @@ int factor(hs_ctx* ctx, double k) {
   if (ctx->cfg.precision == HS_MIXED) return factor_mixed(ctx, k);
   cudaStream_t s = ctx->stream;
   CKR(phase_events(ctx));
+  CKR(set_device_k(ctx, s, k));
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
   CK(cudaEventRecord(ctx->ph_ev[0], s));
   Phase ph("hs_factor_fp64");
   for (int l0 = 0; l0 < ctx->nleaf; l0 += ctx->chunk) {
     int n = std::min(ctx->chunk, ctx->nleaf - l0);
-    leaf_build_chunk(s, ctx->d_q, l0, n, k, ctx->h, ctx->ws, ctx->d_Rleaf + (size_t)l0 * NE * NE,
+    leaf_build_chunk(s, ctx->d_q, l0, n, k, ctx->d_k, ctx->h, ctx->ws, ctx->d_Rleaf + (size_t)l0 * NE * NE,
                      ctx->d_Y + (size_t)l0 * NL * NE, ctx->d_Q + (size_t)l0 * NI * NE, ctx->d_info);
   }
   const double2* Rc = ctx->d_Rleaf;
@@ -931,21 +959,6 @@ int check_ctx(hs_ctx* ctx, bool need_built) {
 
 cudaStream_t pick(hs_ctx* ctx, void* stream) { return stream ? (cudaStream_t)stream : ctx->stream; }
 
-// Emulated complex FP64 product C (m x n, leading dimension ldc) = alpha A B
-// from the sliced real and imaginary parts of A (m rows, k) and of B^T (n rows,
-// k): four real products, the second of each pair accumulated in FP64.
-int zmul_emulated(hs_ctx* ctx, cudaStream_t s, int m, int n, int k, const void* Are, const void* Aim, const void* Bre,
-                  const void* Bim, double alpha, double2* C, int ldc) {
-  double* c = reinterpret_cast<double*>(C);
-  const OzView cre{c, 0, 2LL * ldc, 0, 2, 1}, cim{c + 1, 0, 2LL * ldc, 0, 2, 1};
-  cudaError_t e = oz_multiply(s, m, n, k, 1, alpha, Are, Bre, true, 0.0, cre);
-  if (e == cudaSuccess) e = oz_multiply(s, m, n, k, 1, -alpha, Aim, Bim, true, 1.0, cre);
-  if (e == cudaSuccess) e = oz_multiply(s, m, n, k, 1, alpha, Are, Bim, true, 0.0, cim);
-  if (e == cudaSuccess) e = oz_multiply(s, m, n, k, 1, alpha, Aim, Bre, true, 1.0, cim);
-  if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("emulated FP64 product: ") + cudaGetErrorString(e));
-  return HS_OK;
-}
-
 // Real and imaginary parts of a complex matrix (rows x k, leading dimension
 // ld, interleaved) as strided real views for slicing.
 OzView re_view(const double2* A, int ld, int part) {
@@ -1000,8 +1013,10 @@ size_t mixed_bytes(hs_ctx* ctx, int M, int P) {
        Arena::bytes(nl * NI * M, 8) +
        Arena::bytes(s3_elems(ctx, M), 8) + 2 * Arena::bytes(nb * M, 8);
   for (auto& L : ctx->levels) b += Arena::bytes((size_t)L.nbox * 2 * L.ni * M, 8);
-  if (g_oz_enabled) b += 2 * std::max(oz_operand_bytes(M, 2 * (int)nb, 1, false),
-                                      oz_operand_bytes(M, 2 * (int)nb, 1, true) + oz_operand_bytes(P, 2 * (int)nb, 1, false));
+  if (g_oz_enabled)
+    b += 2 * std::max(oz_wide_bytes(M, 2 * (int)nb, false),
+                      oz_wide_bytes(M, 2 * (int)nb, true) + oz_wide_bytes(P, 2 * (int)nb, false)) +
+         4 * std::max(oz_partial_bytes((int)nb, M, 2 * (int)nb), oz_partial_bytes(M, P, 2 * (int)nb));
   return b;
 }
 
@@ -1047,15 +1062,17 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
   // the exterior residual, then as the left operand of the far field) and of
   // the receiver matrix
   const bool emu = g_oz_enabled;
-  const size_t ob_ps = emu ? oz_operand_bytes(M, 2 * nb, 1, false) : 0;
-  const size_t ob_psa = emu ? oz_operand_bytes(M, 2 * nb, 1, true) : 0, ob_a2 = emu ? oz_operand_bytes(P, 2 * nb, 1, false) : 0;
+  const size_t ob_ps = emu ? oz_wide_bytes(M, 2 * nb, false) : 0;
+  const size_t ob_psa = emu ? oz_wide_bytes(M, 2 * nb, true) : 0, ob_a2 = emu ? oz_wide_bytes(P, 2 * nb, false) : 0;
+  const size_t ob_part = emu ? std::max(oz_partial_bytes(nb, M, 2 * nb), oz_partial_bytes(M, P, 2 * nb)) : 0;
   char* ozs = emu ? a.get<char>(2 * std::max(ob_ps, ob_psa + ob_a2)) : nullptr;
+  char* ozp = emu ? a.get<char>(4 * ob_part) : nullptr;
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
-  const size_t ob_ds = oz_operand_bytes(nb, 2 * nb, 1, true);
+  const size_t ob_ds = oz_wide_bytes(nb, 2 * nb, true);
   if (emu && ctx->ds_oz_k != ctx->bie_k) {  // the exterior rows of this k, sliced once
     if (!ctx->d_ds_oz) CKR(dalloc(ctx, &ctx->d_ds_oz, 2 * ob_ds));
-    oz_slice(s, re_view(ctx->d_DS, 2 * nb, 0), nb, 2 * nb, 1, true, ctx->d_ds_oz);
-    oz_slice(s, re_view(ctx->d_DS, 2 * nb, 1), nb, 2 * nb, 1, true, ctx->d_ds_oz + ob_ds);
+    oz_slice_wide(s, re_view(ctx->d_DS, 2 * nb, 0), nb, 2 * nb, true, ctx->d_ds_oz);
+    oz_slice_wide(s, re_view(ctx->d_DS, 2 * nb, 1), nb, 2 * nb, true, ctx->d_ds_oz + ob_ds);
     ctx->ds_oz_k = ctx->bie_k;
   }
 
@@ -1077,9 +1094,11 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
       boundary_gather(s, X, ctx->d_D1, ctx->nL, ctx->h, M, ub, psib);
       scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
       if (emu) {
-        oz_slice(s, re_view_t(PS, M, 0), M, 2 * nb, 1, false, ozs);
-        oz_slice(s, re_view_t(PS, M, 1), M, 2 * nb, 1, false, ozs + ob_ps);
-        CKR(zmul_emulated(ctx, s, nb, M, 2 * nb, ctx->d_ds_oz, ctx->d_ds_oz + ob_ds, ozs, ozs + ob_ps, -1.0, rext, M));
+        oz_slice_wide(s, re_view_t(PS, M, 0), M, 2 * nb, false, ozs);
+        oz_slice_wide(s, re_view_t(PS, M, 1), M, 2 * nb, false, ozs + ob_ps);
+        const cudaError_t e = oz_zmul_wide(s, nb, M, 2 * nb, ctx->d_ds_oz, ctx->d_ds_oz + ob_ds, ozs, ozs + ob_ps,
+                                           -1.0, 0.0, rext, M, ozp);
+        if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("emulated FP64 product: ") + cudaGetErrorString(e));
       } else {
         gemm<double2, double2, double2>(s, OP_N, OP_N, nb, M, 2 * nb, mone, ctx->d_DS, 2 * nb, 0, PS, M, 0, zero,
                                         rext, M, 0, 1);
@@ -1099,10 +1118,10 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
       } else {
         convert_d2f(s, rext, r32, (long long)nbM);
         // FP32 correction: particular leaf solutions, upward pass, root
-        leaf_particular(s, ctx->ws32, nl, eta, M, Up, B0, tmp, wtmp);
+        leaf_particular(s, ctx->ws32, nl, ctx->d_k, M, Up, B0, tmp, wtmp);
         float2 *Hc = B0, *Hp = B1;
         for (int li = 0; li < nlev; ++li) {
-          residual_iface(s, ctx->levels[li], X, ctx->d_D1, ctx->nL, ctx->h, eta, M, S3);
+          residual_iface(s, ctx->levels[li], X, ctx->d_D1, ctx->nL, ctx->h, ctx->d_k, M, S3);
           sweep_up_level<float2>(s, ctx->levels[li], ctx->ops32[li], Hc, S3, TT[li], Hp, M);
           std::swap(Hc, Hp);
         }
@@ -1135,7 +1154,8 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
       return HS_OK;
     };
     const bool capture = g_use_graphs && !prof_active(2) && !prof_active(3);
-    CKR(run_captured(ctx, s, ctx->pgraph[first ? 0 : 1], capture, ui, M, P, ctx->k, body));
+    // keyed by the buffers and the sizes only: the body's kernels read k on the device
+    CKR(run_captured(ctx, s, ctx->pgraph[first ? 0 : 1], capture, ui, M, P, 0.0, body));
     double dn2 = 0.0;
     CK(cudaMemcpyAsync(&dn2, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1168,11 +1188,13 @@ int mixed_solve(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const 
     scattered_data(s, ub, psib, ui, dni, (long long)nbM, PS);
     if (emu) {  // uf = PS^T A2^T
       char *pa = ozs, *pb = ozs + 2 * ob_psa;
-      oz_slice(s, re_view_t(PS, M, 0), M, 2 * nb, 1, true, pa);
-      oz_slice(s, re_view_t(PS, M, 1), M, 2 * nb, 1, true, pa + ob_psa);
-      oz_slice(s, re_view(A2, 2 * nb, 0), P, 2 * nb, 1, false, pb);
-      oz_slice(s, re_view(A2, 2 * nb, 1), P, 2 * nb, 1, false, pb + ob_a2);
-      CKR(zmul_emulated(ctx, s, M, P, 2 * nb, pa, pa + ob_psa, pb, pb + ob_a2, 1.0, uf, P));
+      oz_slice_wide(s, re_view_t(PS, M, 0), M, 2 * nb, true, pa);
+      oz_slice_wide(s, re_view_t(PS, M, 1), M, 2 * nb, true, pa + ob_psa);
+      oz_slice_wide(s, re_view(A2, 2 * nb, 0), P, 2 * nb, false, pb);
+      oz_slice_wide(s, re_view(A2, 2 * nb, 1), P, 2 * nb, false, pb + ob_a2);
+      const cudaError_t e =
+          oz_zmul_wide(s, M, P, 2 * nb, pa, pa + ob_psa, pb, pb + ob_a2, 1.0, 0.0, uf, P, ozp);
+      if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("emulated FP64 product: ") + cudaGetErrorString(e));
     } else {
       gemm<double2, double2, double2>(s, OP_T, OP_T, M, P, 2 * nb, one, PS, M, 0, A2, 2 * nb, 0, zero, uf, P, 0, 1);
     }

@@ -56,10 +56,12 @@ __device__ __forceinline__ int edge_index(int a, int b) {
 //   Aii (196x196), Aie (196x56): rows of  Lap_h u + k^2 (1 - q) u  at interior nodes,
 //   Ni (56x196), NiT = Ni^T (196x56), Ne (56x56): outward normal derivative rows.
 template <typename T>
-__global__ void __launch_bounds__(256) k_leaf_assemble(const double* __restrict__ q, int leaf0, double k, double h,
+__global__ void __launch_bounds__(256) k_leaf_assemble(const double* __restrict__ q, int leaf0,
+                                                       const double* __restrict__ kp, double h,
                                                        T* __restrict__ Aii, T* __restrict__ Aie, T* __restrict__ Ni,
                                                        T* __restrict__ NiT, T* __restrict__ Ne) {
   const int lb = blockIdx.x;  // leaf within the chunk
+  const double k = *kp;       // read on the device, so that a captured build serves every k
   const double* ql = q + (long long)(leaf0 + lb) * 256;
   Aii += (long long)lb * NI * NI;
   Aie += (long long)lb * NI * NE;
@@ -126,9 +128,10 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(const double* __restrict_
 
 // K = T + i eta I (complex), Kinv = I.
 template <typename T>
-__global__ void k_make_K(const T* __restrict__ Tm, double eta, typename prec<T>::C* __restrict__ K,
+__global__ void k_make_K(const T* __restrict__ Tm, const double* __restrict__ kp, typename prec<T>::C* __restrict__ K,
                          typename prec<T>::C* __restrict__ Kinv, int nleaf) {
   using C = typename prec<T>::C;
+  const double eta = *kp;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nleaf * NE * NE) return;
   int e = (int)(idx % (NE * NE));
@@ -144,9 +147,11 @@ __global__ void k_make_K(const T* __restrict__ Tm, double eta, typename prec<T>:
 
 // R = I - 2 i eta Kinv (leaf impedance-to-impedance map); Ye = Kinv (edge rows of Y).
 template <typename T>
-__global__ void k_leaf_R(const typename prec<T>::C* __restrict__ Kinv, double eta, typename prec<T>::C* __restrict__ R,
+__global__ void k_leaf_R(const typename prec<T>::C* __restrict__ Kinv, const double* __restrict__ kp,
+                         typename prec<T>::C* __restrict__ R,
                          typename prec<T>::C* __restrict__ Y, int nleaf) {
   using C = typename prec<T>::C;
+  const double eta = *kp;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nleaf * NE * NE) return;
   int lb = (int)(idx / (NE * NE));
@@ -162,11 +167,12 @@ __global__ void k_leaf_R(const typename prec<T>::C* __restrict__ Kinv, double et
 }
 
 template <typename T>
-void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, double h, LeafScratchT<T>& w,
-                      typename prec<T>::C* R, typename prec<T>::C* Y, typename prec<T>::C* Q, int* info) {
+void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, const double* d_k, double h,
+                      LeafScratchT<T>& w, typename prec<T>::C* R, typename prec<T>::C* Y, typename prec<T>::C* Q,
+                      int* info) {
   using C = typename prec<T>::C;
   const double eta = k;
-  k_leaf_assemble<T><<<nleaf, 256, 0, s>>>(q, leaf0, k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
+  k_leaf_assemble<T><<<nleaf, 256, 0, s>>>(q, leaf0, d_k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
   HS_COUNT_LAUNCH();
   lu_factor<T>(s, w.Aii, NI, (long long)NI * NI, NI, w.piv, NI, info, nleaf);
   // X = Aii^{-1} Aie (Dirichlet-to-interior map), W = Aii^{-T} Ni^T (adjoint)
@@ -188,14 +194,14 @@ void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, dou
                 w.Ne, NE, (long long)NE * NE, nleaf);
   {
     long long n = (long long)nleaf * NE * NE;
-    k_make_K<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Ne, eta, w.K, w.Kinv, nleaf);
+    k_make_K<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Ne, d_k, w.K, w.Kinv, nleaf);
     HS_COUNT_LAUNCH();
   }
   lu_factor<C>(s, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, info, nleaf);
   lu_solve<C>(s, OP_N, w.K, NE, (long long)NE * NE, NE, w.pivK, NE, w.Kinv, NE, (long long)NE * NE, NE, nleaf);
   {
     long long n = (long long)nleaf * NE * NE;
-    k_leaf_R<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Kinv, eta, R, Y, nleaf);
+    k_leaf_R<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Kinv, d_k, R, Y, nleaf);
     HS_COUNT_LAUNCH();
   }
   C m1 = el<C>::zero(), z0 = el<C>::zero(), ieta2 = el<C>::zero();
@@ -210,10 +216,10 @@ void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, dou
                   Q, NE, (long long)NI * NE, nleaf);
 }
 
-template void leaf_build_chunk<double>(cudaStream_t, const double*, int, int, double, double, LeafScratchT<double>&,
-                                       double2*, double2*, double2*, int*);
-template void leaf_build_chunk<float>(cudaStream_t, const double*, int, int, double, double, LeafScratchT<float>&,
-                                      float2*, float2*, float2*, int*);
+template void leaf_build_chunk<double>(cudaStream_t, const double*, int, int, double, const double*, double,
+                                       LeafScratchT<double>&, double2*, double2*, double2*, int*);
+template void leaf_build_chunk<float>(cudaStream_t, const double*, int, int, double, const double*, double,
+                                      LeafScratchT<float>&, float2*, float2*, float2*, int*);
 
 void sine_eval_grid(cudaStream_t s, const double* c, int S1, int S2, const double* xg, int nL, double* sx, double* sy,
                     double* T, double* Qg, double* q, int* bad) {

@@ -82,6 +82,18 @@ size_t oz_operand_bytes(int rows, int k, int batch, bool is_a);
 void oz_slice(cudaStream_t s, OzView v, int rows, int k, int batch, bool is_a, void* buf);
 cudaError_t oz_multiply(cudaStream_t s, int m, int n, int k, int batch, double alpha, const void* Aop, const void* Bop,
                         bool b_shared, double beta, OzView C);
+// Split-k form for products with few output tiles and a long k: an operand
+// sliced "wide" (every piece of k side by side in one row, oz_wide_bytes) is
+// multiplied by one launch with the pieces along grid.z into per-piece FP64
+// planes (oz_partial_bytes), which oz_zmul_wide sums in order for a complex
+// product C (m x n, ldc) = alpha A B + beta C from the real and imaginary
+// parts of A (rows) and of B^T (rows); partials: 4 oz_partial_bytes.
+size_t oz_wide_bytes(int rows, int k, bool is_a);
+size_t oz_partial_bytes(int m, int n, int k);
+void oz_slice_wide(cudaStream_t s, OzView v, int rows, int k, bool is_a, void* buf);
+cudaError_t oz_multiply_wide(cudaStream_t s, int m, int n, int k, const void* Aop, const void* Bop, double* partial);
+cudaError_t oz_zmul_wide(cudaStream_t s, int m, int n, int k, const void* Are, const void* Aim, const void* Bre,
+                         const void* Bim, double alpha, double beta, double2* C, int ldc, void* partials);
 // The left operand of the Jacobian's x-projection for the pairs c0 .. c0 + nc - 1
 // of d * P + p, sliced straight from the fields: rows 2 (c nX + gy) + part of
 // u_d z_p over gx (2 nc nX rows, k = nX; oz_operand_bytes(2 nc nX, nX, 1, true)).

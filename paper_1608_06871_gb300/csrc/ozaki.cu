@@ -23,8 +23,8 @@
 //
 // Kernel: one CTA per 128 x 64 output tile; warp 0 loads slice tiles with TMA
 // (cp.async.bulk.tensor, three-dimensional maps over [slice][row][k]) into a
-// two-stage ring, warp 1 issues the tcgen05 BF16 MMAs (M = 128, N = 64,
-// K = 16; 72 per stage of 32 k) into the eight diagonal accumulators (all
+// two-stage ring, warp 1 issues the tcgen05 BF16 MMAs (M = 128, N = 64 to 256,
+// K = 16; 28 per stage of 32 k) into the eight diagonal accumulators (all
 // 512 TMEM columns), warps 2..5 read them back.  Every mbarrier wait is
 // bounded; a timeout sets the library's tensor-core timeout flag.
 #include <cuda.h>
@@ -61,9 +61,10 @@ constexpr int OZ_B_KB = OZ_S * OZ_TN * 16;  // same for B (8 KB)
 constexpr int OZ_STAGE = (OZ_KS / 8) * (OZ_A_KB + OZ_B_KB);  // 96 KB
 constexpr int OZ_SMEM = 2 * OZ_STAGE + 1024;
 constexpr long long OZ_WAIT = 1LL << 26;
-// instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
-constexpr uint32_t OZ_IDESC =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(OZ_TM >> 4) << 24);
+// instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t oz_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZ_TM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -127,6 +128,32 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
   return b < 0 ? -v : v;
 }
 
+// BF16 bits of a small integer |a| <= 2^8 (exact): the float from the magic
+// constant 1.5 * 2^23 (so that negative a stay in its binade), whose upper 16
+// bits are then the BF16 value.
+__device__ __forceinline__ unsigned short small_bf16(int a) {
+  const float f = __int_as_float(0x4B400000 + a) - 12582912.0f;
+  return (unsigned short)(__float_as_uint(f) >> 16);
+}
+
+// The 8 balanced base-128 digits of a 56-bit fixed-point N (|N| < 2^56),
+// written to o[s * plane]: N = H 2^28 + L with L in [-2^27, 2^27), then four
+// digits from each 32-bit half (weights 2^21, 2^14, 2^7, 1 within it), each
+// rounded to nearest: |a_0| <= 128, |a_s| <= 64 after, sum_s a_s 2^(49 - 7 s) = N.
+__device__ __forceinline__ void put_digits(long long n, unsigned short* o, long long plane) {
+  const long long hq = (n + (1LL << 27)) >> 28;
+  int h = (int)hq, l = (int)(n - (hq << 28));
+  int a;
+  a = (h + (1 << 20)) >> 21; h -= a << 21; o[0] = small_bf16(a);
+  a = (h + (1 << 13)) >> 14; h -= a << 14; o[plane] = small_bf16(a);
+  a = (h + (1 << 6)) >> 7;   h -= a << 7;  o[2 * plane] = small_bf16(a);
+  o[3 * plane] = small_bf16(h);
+  a = (l + (1 << 20)) >> 21; l -= a << 21; o[4 * plane] = small_bf16(a);
+  a = (l + (1 << 13)) >> 14; l -= a << 14; o[5 * plane] = small_bf16(a);
+  a = (l + (1 << 6)) >> 7;   l -= a << 7;  o[6 * plane] = small_bf16(a);
+  o[7 * plane] = small_bf16(l);
+}
+
 // Slices of the rows of a view (rows = A's rows, or B's columns): one warp
 // per row, lanes along k; slices written to out[s][b * rpad + i][kk] (BF16,
 // kpad wide, zero padded), the row's exponent to e[b * rpad + i].  Padding
@@ -134,19 +161,17 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
 // scarce unit): the row's largest magnitude fixes e with max 2^-e in
 // [1/2, 1); each entry becomes the 56-bit fixed-point integer
 // N = round(x 2^(56 - e)), |N| < 2^56, whose balanced base-128 digits are the
-// slices: a_s = round(N_s / 2^(49 - 7 s)), N_(s+1) = N_s - a_s 2^(49 - 7 s)
-// (|a_0| <= 128, |a_s| <= 64 after; the last digit takes the exact rest, so
-// the slices represent N exactly).
+// slices (put_digits), which represent N exactly.
 __global__ void k_oz_slice(OzView v, int rows, int k, int rpad, int kpad, int batch, __nv_bfloat16* __restrict__ out,
-                           int* __restrict__ e) {
+                           int* __restrict__ e, int ldo, int col0) {
   const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const long long total = (long long)batch * rpad;
   if (r >= total) return;
   const long long b = r / rpad;
   const int i = (int)(r % rpad);
-  const long long plane = total * kpad;
-  __nv_bfloat16* o = out + r * kpad;
+  const long long plane = total * ldo;
+  unsigned short* o = reinterpret_cast<unsigned short*>(out) + r * ldo + col0;
   const bool live = i < rows;
   // the row's piece (k <= OZ_KMAX) is read once into registers
   constexpr int KPL = OZ_KMAX / 32;
@@ -166,14 +191,7 @@ __global__ void k_oz_slice(OzView v, int rows, int k, int rpad, int kpad, int ba
   for (int q = 0; q < KPL; ++q) {
     const int kk = lane + 32 * q;
     if (kk >= kpad) break;
-    long long n = fixed56(x[q], ex);
-#pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      const int sh = 49 - 7 * s;
-      const long long a = sh > 0 ? (n + (1LL << (sh - 1))) >> sh : n;  // round to nearest (ties up); last: exact
-      n -= a << sh;
-      o[s * plane + kk] = __float2bfloat16_rn((float)a);
-    }
+    put_digits(fixed56(x[q], ex), o + kk, plane);
   }
 }
 
@@ -214,8 +232,8 @@ __global__ void k_oz_slice_kr(const double2* __restrict__ Ug, const double2* __r
   }
   const int er = mr == 0 ? 0 : (int)(mr >> 52) - 1022, ei = mi == 0 ? 0 : (int)(mi >> 52) - 1022;
   const long long plane_s = (long long)rpad * kpad;
-  __nv_bfloat16* o_re = out + (2 * r2) * kpad;
-  __nv_bfloat16* o_im = o_re + kpad;
+  unsigned short* o_re = reinterpret_cast<unsigned short*>(out) + (2 * r2) * kpad;
+  unsigned short* o_im = o_re + kpad;
   if (lane == 0) {
     e[2 * r2] = er;
     e[2 * r2 + 1] = ei;
@@ -224,17 +242,8 @@ __global__ void k_oz_slice_kr(const double2* __restrict__ Ug, const double2* __r
   for (int q = 0; q < KPL; ++q) {
     const int kk = lane + 32 * q;
     if (kk >= kpad) break;
-    long long nr = fixed56(wr[q], er), ni = fixed56(wi[q], ei);
-#pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      const int sh = 49 - 7 * s;
-      const long long ar = sh > 0 ? (nr + (1LL << (sh - 1))) >> sh : nr;
-      const long long ai = sh > 0 ? (ni + (1LL << (sh - 1))) >> sh : ni;
-      nr -= ar << sh;
-      ni -= ai << sh;
-      o_re[s * plane_s + kk] = __float2bfloat16_rn((float)ar);
-      o_im[s * plane_s + kk] = __float2bfloat16_rn((float)ai);
-    }
+    put_digits(fixed56(wr[q], er), o_re + kk, plane_s);
+    put_digits(fixed56(wi[q], ei), o_im + kk, plane_s);
   }
 }
 
@@ -251,6 +260,9 @@ __global__ void k_oz_zero_rows(long long first, int rpad, int kpad, __nv_bfloat1
 
 struct OzParams {
   int m, n, k, mpad, npad, kpad, nb_batch_b;  // nb_batch_b: 0 when B is shared by every batch
+  // zpieces: grid.z runs over the pieces of k (pl wide, k the whole extent) of one
+  // product instead of over a batch; piece z writes its own output plane z
+  int zpieces, pl;
   double alpha, beta;
   const int* ea;
   const int* eb;
@@ -264,11 +276,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __shared__ uint32_t tslot;
   __shared__ __align__(8) uint64_t full[2], empty[2], done;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.z;
+  const int b = blockIdx.z;  // batch, or piece of k
   const int tm = blockIdx.y, tn = blockIdx.x;
-  const int rowA = b * P.mpad + tm * OZ_TM;
-  const int rowB = (P.nb_batch_b ? b : 0) * P.npad + tn * OZ_TN;
-  const int nst = P.kpad / OZ_KS;
+  const bool zp = P.zpieces != 0;
+  const int rowA = (zp ? 0 : b * P.mpad) + tm * OZ_TM;
+  const int rowB = (zp ? 0 : (P.nb_batch_b ? b : 0) * P.npad) + tn * OZ_TN;
+  const int kbase = zp ? b * P.pl : 0;
+  const int nst = zp ? (min(P.pl, P.k - kbase) + OZ_KS - 1) / OZ_KS : P.kpad / OZ_KS;
+  const int bB = zp ? b : (P.nb_batch_b ? b : 0);  // exponent plane of B
 
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(512));
@@ -298,7 +313,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                      : "memory");
         const uint32_t base = su32(sm + st * OZ_STAGE);
         for (int kb = 0; kb < OZ_KS / 8; ++kb) {
-          const int kx = i * OZ_KS + kb * 8;
+          const int kx = kbase + i * OZ_KS + kb * 8;
           oz_tma3(base + kb * OZ_A_KB, &mapA, kx, rowA, 0, su32(&full[st]));
           oz_tma3(base + (OZ_KS / 8) * OZ_A_KB + kb * OZ_B_KB, &mapB, kx, rowB, 0, su32(&full[st]));
         }
@@ -312,19 +327,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t aB = su32(sm + st * OZ_STAGE), bB = aB + (OZ_KS / 8) * OZ_A_KB;
+        // The B slices of a k block lie back to back (slice t at rows 64 t .. 64 t + 63)
+        // and the diagonal accumulators are adjacent in TMEM (diagonal d at columns
+        // 64 d ..), so one MMA with N = 64 w multiplies A_s by B_t .. B_(t+w-1) into
+        // diagonals s + t .. s + t + w - 1: per slice s the 8 - s pairs take
+        // MMAs of N = 256, 128 and 64 (14 per 16 k instead of 36).
 #pragma unroll 1
         for (int kh = 0; kh < OZ_KS / 16; ++kh) {
 #pragma unroll 1
           for (int s = 0; s < OZ_S; ++s) {
             const uint64_t da = oz_desc(aB + kh * 2 * OZ_A_KB + s * (OZ_TM * 16), OZ_A_KB, 128);
+            const uint32_t acc = (i > 0 || kh > 0 || s > 0) ? 1u : 0u;
+            int t = 0;
 #pragma unroll 1
-            for (int t = 0; t + s < OZ_ND; ++t) {
+            while (t + s < OZ_ND) {
+              const int left = OZ_ND - s - t;
+              const int w = left >= 4 ? 4 : left >= 2 ? 2 : 1;
               const uint64_t db = oz_desc(bB + kh * 2 * OZ_B_KB + t * (OZ_TN * 16), OZ_B_KB, 128);
-              const uint32_t acc = (i > 0 || kh > 0 || s > 0) ? 1u : 0u;
+              const uint32_t idesc = oz_idesc(w * OZ_TN);
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                   "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)((s + t) * OZ_TN)),
-                  "l"(da), "l"(db), "r"(OZ_IDESC), "r"(acc));
+                  "l"(da), "l"(db), "r"(idesc), "r"(acc));
+              t += w;
             }
           }
         }
@@ -373,7 +398,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           if (c >= P.n) continue;
           // sum_d C_d 2^(-7 (d + 2)) = hi 2^-35 + lo 2^-63, then the row and column scales
           const double val = fma((double)lo[j], 0x1p-63, (double)hi[j] * 0x1p-35);
-          const int eb = P.eb[(long long)(P.nb_batch_b ? b : 0) * P.npad + c];
+          const int eb = P.eb[(long long)bB * P.npad + c];
           double* pc = P.C.p + vaddr(P.C, b, r, c);
           const double out = P.alpha * scalbn(val, ea + eb);
           *pc = P.beta == 0.0 ? out : fma(P.beta, *pc, out);
@@ -465,6 +490,8 @@ cudaError_t launch_piece(cudaStream_t s, int m, int n, int kc, long long kp, lon
   P.npad = (int)np;
   P.kpad = (int)kp;
   P.nb_batch_b = b_shared ? 0 : 1;
+  P.zpieces = 0;
+  P.pl = 0;
   P.alpha = alpha;
   P.beta = beta;
   P.ea = ea;
@@ -525,7 +552,7 @@ void oz_slice(cudaStream_t s, OzView v, int rows, int k, int batch, bool is_a, v
     w.p += k0 * v.sk;
     k_oz_slice<<<(unsigned)((rt + 7) / 8), 256, 0, s>>>(w, rows, p.kc, (int)rpad, (int)p.kp, batch,
                                                       reinterpret_cast<__nv_bfloat16*>(base + p.slices),
-                                                      reinterpret_cast<int*>(base + p.exps));
+                                                      reinterpret_cast<int*>(base + p.exps), (int)p.kp, 0);
     HS_COUNT_LAUNCH();
     off = p.next;
   }
@@ -576,6 +603,104 @@ cudaError_t oz_multiply(cudaStream_t s, int m, int n, int k, int batch, double a
   return cudaGetLastError();
 }
 
+// ---- split-k products: one launch per real product, pieces of k along grid.z ----
+
+namespace {
+// C = alpha sum_p (P0 - P1) + i alpha sum_p (P2 + P3) (+ beta C), pieces summed in order.
+__global__ void k_oz_zcombine(const double* __restrict__ P0, const double* __restrict__ P1,
+                              const double* __restrict__ P2, const double* __restrict__ P3, int npc, int m, int n,
+                              double alpha, double beta, double2* __restrict__ C, int ldc) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long mn = (long long)m * n;
+  if (e >= mn) return;
+  double re = 0.0, im = 0.0;
+  for (int p = 0; p < npc; ++p) {
+    re += P0[p * mn + e] - P1[p * mn + e];
+    im += P2[p * mn + e] + P3[p * mn + e];
+  }
+  double2* c = C + (e / n) * ldc + (e % n);
+  const double2 v = make_double2(alpha * re, alpha * im);
+  *c = beta == 0.0 ? v : make_double2(v.x + beta * c->x, v.y + beta * c->y);
+}
+
+int npieces(int k) { return (k + piece_len(k) - 1) / piece_len(k); }
+}  // namespace
+
+size_t oz_wide_bytes(int rows, int k, bool is_a) {
+  const long long rpad = rup(rows, is_a ? OZ_TM : OZ_TN), kt = (long long)npieces(k) * piece_len(k);
+  return align_up((size_t)OZ_S * rpad * kt * 2) + align_up((size_t)npieces(k) * rpad * 4);
+}
+
+size_t oz_partial_bytes(int m, int n, int k) { return align_up((size_t)npieces(k) * m * n * 8); }
+
+void oz_slice_wide(cudaStream_t s, OzView v, int rows, int k, bool is_a, void* buf) {
+  const long long rpad = rup(rows, is_a ? OZ_TM : OZ_TN);
+  const int pl = piece_len(k), kt = npieces(k) * pl;
+  char* base = reinterpret_cast<char*>(buf);
+  __nv_bfloat16* sl = reinterpret_cast<__nv_bfloat16*>(base);
+  int* ex = reinterpret_cast<int*>(base + align_up((size_t)OZ_S * rpad * kt * 2));
+  for (int p = 0, k0 = 0; k0 < k; ++p, k0 += pl) {
+    const int kc = std::min(pl, k - k0);
+    OzView w = v;
+    w.p += k0 * v.sk;
+    k_oz_slice<<<(unsigned)((rpad + 7) / 8), 256, 0, s>>>(w, rows, kc, (int)rpad, (int)rup(kc, OZ_KS), 1, sl,
+                                                        ex + (long long)p * rpad, kt, k0);
+    HS_COUNT_LAUNCH();
+  }
+}
+
+cudaError_t oz_multiply_wide(cudaStream_t s, int m, int n, int k, const void* Aop, const void* Bop, double* partial) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaErrorInvalidValue;
+  if (!encode_fn()) return cudaErrorNotSupported;
+  set_smem_attr();
+  const long long mp = rup(m, OZ_TM), np = rup(n, OZ_TN);
+  const int pl = piece_len(k), npc = npieces(k), kt = npc * pl;
+  char* a = const_cast<char*>(reinterpret_cast<const char*>(Aop));
+  char* b = const_cast<char*>(reinterpret_cast<const char*>(Bop));
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a, mp, kt, OZ_TM) || !make_map(&mb, b, np, kt, OZ_TN)) return cudaErrorInvalidValue;
+  OzParams P;
+  P.m = m;
+  P.n = n;
+  P.k = k;
+  P.mpad = (int)mp;
+  P.npad = (int)np;
+  P.kpad = kt;
+  P.nb_batch_b = 1;
+  P.zpieces = 1;
+  P.pl = pl;
+  P.alpha = 1.0;
+  P.beta = 0.0;
+  P.ea = reinterpret_cast<const int*>(a + align_up((size_t)OZ_S * mp * kt * 2));
+  P.eb = reinterpret_cast<const int*>(b + align_up((size_t)OZ_S * np * kt * 2));
+  P.C = OzView{partial, (long long)m * n, n, 0, 1, 1};
+  dim3 grid((unsigned)(np / OZ_TN), (unsigned)(mp / OZ_TM), (unsigned)npc);
+  const bool prof = prof_active(4);
+  cudaEvent_t ev = nullptr;
+  if (prof) prof_begin(s, &ev);
+  k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ma, mb, P);
+  HS_COUNT_LAUNCH();
+  if (prof) prof_end(s, ev, 2.0 * m * n * k);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_zmul_wide(cudaStream_t s, int m, int n, int k, const void* Are, const void* Aim, const void* Bre,
+                         const void* Bim, double alpha, double beta, double2* C, int ldc, void* partials) {
+  const size_t pb = oz_partial_bytes(m, n, k);
+  double* P[4];
+  for (int i = 0; i < 4; ++i) P[i] = reinterpret_cast<double*>(reinterpret_cast<char*>(partials) + i * pb);
+  cudaError_t e = oz_multiply_wide(s, m, n, k, Are, Bre, P[0]);
+  if (e == cudaSuccess) e = oz_multiply_wide(s, m, n, k, Aim, Bim, P[1]);
+  if (e == cudaSuccess) e = oz_multiply_wide(s, m, n, k, Are, Bim, P[2]);
+  if (e == cudaSuccess) e = oz_multiply_wide(s, m, n, k, Aim, Bre, P[3]);
+  if (e != cudaSuccess) return e;
+  const long long mn = (long long)m * n;
+  k_oz_zcombine<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(P[0], P[1], P[2], P[3], npieces(k), m, n, alpha, beta,
+                                                             C, ldc);
+  HS_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double alpha, OzView A, OzView Bt, bool b_shared,
                        double beta, OzView C, void* scratch, size_t scratch_bytes) {
   if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535) return cudaErrorInvalidValue;
@@ -594,11 +719,11 @@ cudaError_t ozaki_gemm(cudaStream_t s, int m, int n, int k, int batch, double al
     const long long ra = batch * mp, rb = nbB * np;
     k_oz_slice<<<(unsigned)((ra + 7) / 8), 256, 0, s>>>(a, m, pa.kc, (int)mp, (int)pa.kp, batch,
                                                       reinterpret_cast<__nv_bfloat16*>(base + pa.slices),
-                                                      reinterpret_cast<int*>(base + pa.exps));
+                                                      reinterpret_cast<int*>(base + pa.exps), (int)pa.kp, 0);
     HS_COUNT_LAUNCH();
     k_oz_slice<<<(unsigned)((rb + 7) / 8), 256, 0, s>>>(bt, n, pb.kc, (int)np, (int)pb.kp, (int)nbB,
                                                       reinterpret_cast<__nv_bfloat16*>(base + pb.slices),
-                                                      reinterpret_cast<int*>(base + pb.exps));
+                                                      reinterpret_cast<int*>(base + pb.exps), (int)pb.kp, 0);
     HS_COUNT_LAUNCH();
     const cudaError_t e =
         launch_piece(s, m, n, pa.kc, pa.kp, mp, np, batch, b_shared, alpha, k0 == 0 ? beta : 1.0,

@@ -93,9 +93,10 @@ __device__ double2 normal_deriv(const double2* __restrict__ U, int nrhs, int j, 
 // b, with r_C = -(u_a - u_b) and r_F = -(d_n u_a + d_n u_b),
 // S3[b][t] = r_F + i eta r_C (s_a) and S3[b][ni + t] = r_F - i eta r_C (s_b).
 __global__ void k_res_iface(const double2* __restrict__ X, const double* __restrict__ D1, int nL, double h,
-                            double eta, int horiz, int sx, int sy, int ni, int nbx_p, int nrhs,
+                            const double* __restrict__ kp, int horiz, int sx, int sy, int ni, int nbx_p, int nrhs,
                             float2* __restrict__ S3) {
   const int b = blockIdx.y;
+  const double eta = *kp;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)ni * nrhs) return;
   const int t = (int)(e / nrhs), j = (int)(e % nrhs);
@@ -152,7 +153,9 @@ __global__ void k_boundary_gather(const double2* __restrict__ X, const double* _
 }
 
 // H = -2 i eta u_e^p (particular outgoing impedance) from the edge rows of Upart.
-__global__ void k_leaf_h(const float2* __restrict__ Upart, int nleaf, double eta, int nrhs, float2* __restrict__ H) {
+__global__ void k_leaf_h(const float2* __restrict__ Upart, int nleaf, const double* __restrict__ kp, int nrhs,
+                         float2* __restrict__ H) {
+  const double eta = *kp;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)nleaf * NE * nrhs) return;
   const int j = (int)(e % nrhs);
@@ -427,9 +430,9 @@ void residual_pde(cudaStream_t s, const double2* X, const double* q, const doubl
 }
 
 void residual_iface(cudaStream_t s, const LevelMaps& L, const double2* X, const double* D1, int nL, double h,
-                    double eta, int nrhs, float2* S3) {
+                    const double* d_k, int nrhs, float2* S3) {
   dim3 g(blocks((long long)L.ni * nrhs), L.nbox);
-  k_res_iface<<<g, 256, 0, s>>>(X, D1, nL, h, eta, L.horiz, L.sx, L.sy, L.ni, L.nbx_p, nrhs, S3);
+  k_res_iface<<<g, 256, 0, s>>>(X, D1, nL, h, d_k, L.horiz, L.sx, L.sy, L.ni, L.nbx_p, nrhs, S3);
   HS_COUNT_LAUNCH();
 }
 
@@ -444,7 +447,7 @@ void boundary_gather(cudaStream_t s, const double2* X, const double* D1, int nL,
 // w = Aii^{-1} b, u_e = -Kinv Ni w, u_i = w - X u_e, and h = -2 i eta u_e.
 // With w.Ainv the first step is one GEMM into wtmp (NI x nrhs per leaf) and a
 // copy back; otherwise triangular solves with the LU factors.
-void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, double eta, int nrhs, float2* Upart,
+void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, const double* d_k, int nrhs, float2* Upart,
                      float2* H, float2* tmp, float2* wtmp) {
   const long long sU = (long long)NL * nrhs;
   const float2 one = make_float2(1.f, 0.f), mone = make_float2(-1.f, 0.f), zero = make_float2(0.f, 0.f);
@@ -465,7 +468,7 @@ void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, do
   gemm<float, float2, float2>(s, OP_N, OP_N, NI, nrhs, NE, mone, w.Aie, NE, (long long)NI * NE,
                               Upart + (long long)NI * nrhs, nrhs, sU, one, Upart, nrhs, sU, nleaf);
   long long n = (long long)nleaf * NE * nrhs;
-  k_leaf_h<<<blocks(n), 256, 0, s>>>(Upart, nleaf, eta, nrhs, H);
+  k_leaf_h<<<blocks(n), 256, 0, s>>>(Upart, nleaf, d_k, nrhs, H);
   HS_COUNT_LAUNCH();
 }
 

@@ -52,9 +52,12 @@ void upload_cheb_diff(const double* D1, cudaStream_t s);
 void sine_eval_grid(cudaStream_t s, const double* c, int S1, int S2, const double* xg, int nL, double* sx,
                     double* sy, double* T, double* Qg, double* q, int* bad);
 void check_q(cudaStream_t s, const double* q, long long n, int* bad);
+// k: the wavenumber on the host (GEMM scalars), d_k: the same on the device (read
+// by the kernels, so that a captured build serves every k).
 template <typename T>
-void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, double h, LeafScratchT<T>& w,
-                      typename prec<T>::C* R, typename prec<T>::C* Y, typename prec<T>::C* Q, int* info);
+void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, const double* d_k, double h,
+                      LeafScratchT<T>& w, typename prec<T>::C* R, typename prec<T>::C* Y, typename prec<T>::C* Q,
+                      int* info);
 
 template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Rc, int* info);
 // Downward sweep of one level.  If t3_loaded, T3 already holds the particular
@@ -172,10 +175,10 @@ void convert_f2d_add(cudaStream_t s, const float2* a, double2* b, long long n); 
 void residual_pde(cudaStream_t s, const double2* X, const double* q, const double* D1, int nleaf, double k, double h,
                   int nrhs, float2* RP);
 void residual_iface(cudaStream_t s, const LevelMaps& L, const double2* X, const double* D1, int nL, double h,
-                    double eta, int nrhs, float2* S3);
+                    const double* d_k, int nrhs, float2* S3);
 void boundary_gather(cudaStream_t s, const double2* X, const double* D1, int nL, double h, int nrhs, double2* ub,
                      double2* psib);
-void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, double eta, int nrhs, float2* Upart,
+void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, const double* d_k, int nrhs, float2* Upart,
                      float2* H, float2* tmp, float2* wtmp);
 void scattered_data(cudaStream_t s, const double2* ub, const double2* psib, const double2* ui, const double2* dni,
                     long long n, double2* PS);

@@ -122,9 +122,10 @@ def test_mixed_gn_step_k5_matches_oracle(hs):
 
 
 def test_factor_graph_replay_bitwise(hs):
-    """Builds at an unchanged k replay a captured CUDA graph of the factorisation;
-    the far field must be bitwise identical to the launch-by-launch build, and the
-    launch count per build the same."""
+    """Every build after a context's first replays one captured CUDA graph of the
+    factorisation (the kernels read k from device memory), at the same k and at a new
+    one: the far fields must be bitwise identical to the launch-by-launch builds, and
+    the launch count per build the same."""
     w = synth.WORKLOADS["grad_k20"]
     c = synth.smooth_random_coeffs(w.S, seed=4, qmax=0.3)
     al, th = synth.directions(16), synth.receivers(24)
@@ -140,11 +141,14 @@ def test_factor_graph_replay_bitwise(hs):
             outs.append(S.solve(al, th))
             S.build(0.5 * c, w.k)  # a different contrast through the same graph
             outs.append(S.solve(al, th))
+            S.build(c, w.k + 1.5)  # a new frequency through the same graphs
+            outs.append(S.solve(al, th))
+            S.close()
         finally:
             hs.hs_set_graphs(True)
-    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+    assert all(np.array_equal(outs[i], outs[i + 3]) for i in range(3))
     assert counts[1] == counts[4] and counts[2] == counts[5]
-    assert not np.array_equal(outs[0], outs[1])
+    assert not np.array_equal(outs[0], outs[1]) and not np.array_equal(outs[0], outs[2])
 
 
 def test_mixed_gradient_k20(hs):

@@ -66,10 +66,13 @@ int hs_adjoint_refine_stats(const hs_ctx* ctx, int* iterations, double* last_upd
  * results are bitwise identical either way.  Never fails. */
 int hs_set_graphs(int enable);
 
-/* Route eligible complex FP32 products of the mixed-precision path
- * (untransposed operands, m >= 128, n >= 64, k >= 64) to the tensor-core GEMM
- * (enable != 0, the default) or to the SIMT FP32 GEMM (enable == 0).
- * Process-wide; takes effect at the next launch.  Never fails. */
+/* FP32 products (complex x complex, real x complex, real x real; untransposed
+ * operands) on the tensor cores by the split-TF32 product: enable == 0 never;
+ * 1 (the default) only where the library opts in (the FP32 Jacobian's
+ * contraction), with a per-shape choice there (hs_set_autotune); 2 every such
+ * product; 3 a per-shape choice for every such product, the solver's
+ * factorisation and refinement included.  Process-wide; takes effect at the
+ * next launch.  Errors: HS_EINVAL for other values. */
 int hs_set_tensor_cores(int enable);
 
 /* Bytes of scratch the Jacobian contraction may use for one chunk of
@@ -107,6 +110,23 @@ int hs_raise_tc_timeout(int device);
  * tensor-core wait gave up; C is then unspecified), HS_ECUDA. */
 int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream,
                int* used_tc);
+
+/* C[b] = A[b] B[b] in FP32 through the library's GEMM dispatch, for the
+ * three operand forms of its tensor-core product: mode 2 complex A (m x k) and
+ * B (k x n), complex C; mode 1 real A, complex B and C; mode 0 real A, B and C.
+ * Row-major, contiguous batches (b_shared != 0: one B for every batch item),
+ * DEVICE pointers on the current device, enqueued on `stream` and synchronised
+ * before return; *used_tc (if not NULL) is 1 when the tensor cores ran it.
+ * Errors: HS_EINVAL (mode outside 0..2, non-positive size, NULL pointer),
+ * HS_ETIMEOUT, HS_ECUDA. */
+int hs_gemm32(int mode, int m, int n, int k, const void* A, const void* B, void* C, int batch, int b_shared,
+              void* stream, int* used_tc);
+
+/* The GEMM dispatch's choice between the tensor-core and the SIMT FP32
+ * product: enable != 0 (the default) measures both once per shape, outside
+ * stream capture, and keeps the faster; 0 uses a fixed size rule.  Errors:
+ * none. */
+int hs_set_autotune(int enable);
 
 /* C = op(A) op(B) (+ C when accumulate != 0): complex128 (interleaved re,
  * im), row-major, op(A) m x k, op(B) k x n, C m x n; op = transpose when

@@ -74,6 +74,8 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_double)]),
     "hs_build_phase_ms": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "hs_set_tensor_cores": (_I, [_I]),
+    "hs_set_autotune": (_I, [_I]),
+    "hs_gemm32": (_I, [_I, _I, _I, _I, _P, _P, _P, _I, _I, _P, _P]),
     "hs_fail_next_allocs": (_I, [_I]),
     "hs_raise_tc_timeout": (_I, [_I]),
     "hs_set_graphs": (_I, [_I]),
@@ -319,8 +321,14 @@ def hs_raise_tc_timeout(device: int = 0):
     _check(None, lib().hs_raise_tc_timeout(int(device)))
 
 
-def hs_set_tensor_cores(enable: bool):
-    _check(None, lib().hs_set_tensor_cores(1 if enable else 0))
+def hs_set_tensor_cores(enable):
+    """0 / False: SIMT FP32 products; 1 / True: tensor cores where the library opts in, per-shape
+    choice there; 2: tensor cores for every supported product; 3: per-shape choice everywhere."""
+    _check(None, lib().hs_set_tensor_cores(int(enable)))
+
+
+def hs_set_autotune(enable: bool):
+    _check(None, lib().hs_set_autotune(1 if enable else 0))
 
 
 def hs_zgemm(A, B, C, transA: bool = False, transB: bool = False, accumulate: bool = False, stream: int = 0):
@@ -366,6 +374,20 @@ def hs_cgemm32(A, B, out, stream: int = 0) -> bool:
     _check(None, lib().hs_cgemm32(m, n, k, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                   ctypes.c_void_p(out.data_ptr()), batch, ctypes.c_void_p(stream),
                                   ctypes.byref(used)))
+    return bool(used.value)
+
+
+def hs_gemm32(A, B, out, b_shared: bool = False, stream: int = 0) -> bool:
+    """out[b] = A[b] @ B[b] (B[0] for every b when b_shared) for contiguous CUDA tensors:
+    complex64 A, B, out (mode 2), float32 A with complex64 B and out (mode 1), or float32
+    A, B, out (mode 0).  Returns True when the tensor cores ran it."""
+    batch, m, k = A.shape
+    n = B.shape[2]
+    mode = 2 if A.is_complex() else (1 if B.is_complex() else 0)
+    used = ctypes.c_int()
+    _check(None, lib().hs_gemm32(mode, m, n, k, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), batch, 1 if b_shared else 0,
+                                 ctypes.c_void_p(stream), ctypes.byref(used)))
     return bool(used.value)
 
 

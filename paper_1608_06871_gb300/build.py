@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhs.so")
-SOURCES = ["linalg.cu", "leaf.cu", "tree.cu", "bie.cu", "jac.cu", "refine.cu", "hs_api.cu", "diag.cu", "noalloc.cu", "tcgemm.cu", "panel.cu", "ozaki.cu"]
+SOURCES = ["linalg.cu", "leaf.cu", "tree.cu", "bie.cu", "jac.cu", "refine.cu", "hs_api.cu", "diag.cu", "noalloc.cu", "tcgemm.cu", "panel.cu", "ozaki.cu", "tc32.cu"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [GENCODE, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-rdc=false",
               "--expt-relaxed-constexpr"]

@@ -19,7 +19,7 @@ int g_prof_family = 0;
 std::vector<ProfRec> g_prof;
 }  // namespace
 
-bool prof_active(int family) { return g_prof_family == family; }
+bool prof_active(int family) { return !g_prof_suspended && g_prof_family == family; }
 bool prof_any() { return g_prof_family != 0; }
 extern bool g_use_graphs;
 extern size_t g_contract_budget;
@@ -170,18 +170,50 @@ int hs_raise_tc_timeout(int device) {
 }
 
 int hs_set_tensor_cores(int enable) {
-  hs::g_tc_enabled = enable != 0;
+  if (enable < 0 || enable > 3) return HS_EINVAL;
+  hs::g_t32_mode = enable;
+  return HS_OK;
+}
+
+int hs_set_autotune(int enable) {
+  hs::g_autotune = enable != 0;
+  return HS_OK;
+}
+
+int hs_gemm32(int mode, int m, int n, int k, const void* A, const void* B, void* C, int batch, int b_shared,
+              void* stream, int* used_tc) {
+  if (mode < 0 || mode > 2 || m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535 || !A || !B || !C)
+    return HS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const long long sB = b_shared ? 0 : (long long)k * n;
+  if (mode == 2) {
+    hs::gemm<float2, float2, float2>(s, hs::OP_N, hs::OP_N, m, n, k, make_float2(1.f, 0.f),
+                                     static_cast<const float2*>(A), k, (long long)m * k, static_cast<const float2*>(B),
+                                     n, sB, make_float2(0.f, 0.f), static_cast<float2*>(C), n, (long long)m * n,
+                                     batch);
+  } else if (mode == 1) {
+    hs::gemm<float, float2, float2>(s, hs::OP_N, hs::OP_N, m, n, k, make_float2(1.f, 0.f),
+                                    static_cast<const float*>(A), k, (long long)m * k, static_cast<const float2*>(B),
+                                    n, sB, make_float2(0.f, 0.f), static_cast<float2*>(C), n, (long long)m * n, batch);
+  } else {
+    hs::gemm<float, float, float>(s, hs::OP_N, hs::OP_N, m, n, k, 1.f, static_cast<const float*>(A), k,
+                                  (long long)m * k, static_cast<const float*>(B), n, sB, 0.f, static_cast<float*>(C),
+                                  n, (long long)m * n, batch);
+  }
+  if (used_tc) *used_tc = hs::g_last_gemm_tc;
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
+  if (hs::tc_timed_out(s)) return HS_ETIMEOUT;
   return HS_OK;
 }
 
 int hs_cgemm32(int m, int n, int k, const void* A, const void* B, void* C, int batch, void* stream, int* used_tc) {
   if (m <= 0 || n <= 0 || k <= 0 || batch <= 0 || batch > 65535 || !A || !B || !C) return HS_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (used_tc) *used_tc = hs::cgemm_tc_eligible(hs::OP_N, hs::OP_N, m, n, k, batch) ? 1 : 0;
   hs::gemm<float2, float2, float2>(s, hs::OP_N, hs::OP_N, m, n, k, make_float2(1.f, 0.f),
                                    static_cast<const float2*>(A), k, (long long)m * k,
                                    static_cast<const float2*>(B), n, (long long)k * n, make_float2(0.f, 0.f),
                                    static_cast<float2*>(C), n, (long long)m * n, batch);
+  if (used_tc) *used_tc = hs::g_last_gemm_tc;
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
   if (hs::tc_timed_out(s)) return HS_ETIMEOUT;
   return HS_OK;

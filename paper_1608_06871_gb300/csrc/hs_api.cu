@@ -133,6 +133,11 @@ struct GraphSlot {
   int M = -1, P = -1;
   double k = -1.0;
   long long kernels = 0;
+  // the key of the last eager run: a sequence is captured on its second use,
+  // after one eager run has sized the products' scratch and measured their shapes
+  const void* seen_base = nullptr;
+  int seen_M = -1, seen_P = -1;
+  double seen_k = -1.0;
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -233,6 +238,13 @@ int run_captured(hs_ctx* ctx, cudaStream_t s, GraphSlot& slot, bool capture, con
   if (!capture) return enqueue();
   if (!slot.exec || slot.base != base || slot.M != M || slot.P != P || slot.k != k) {
     slot.reset();
+    if (slot.seen_base != base || slot.seen_M != M || slot.seen_P != P || slot.seen_k != k) {
+      slot.seen_base = base;
+      slot.seen_M = M;
+      slot.seen_P = P;
+      slot.seen_k = k;
+      return enqueue();
+    }
     long long* counter = g_launch_counter;
     const long long before = counter ? *counter : 0;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -1969,9 +1981,9 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
-  if (mixed) {  // refined far field and forward fields; adjoint refined unless J is FP32 anyway
+  if (mixed) {  // refined far field, forward and adjoint fields (J32 then carries only its own rounding)
     Arena sub = a;
-    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub, !p32));
+    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub, true));
   } else {  // forward far field F(c)
     Arena sub = a;
     double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);

@@ -208,8 +208,8 @@ void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P
 
 // Explicit complex FP32 Jacobian on the tensor cores, for iterations that stop
 // at a loose tolerance: the contraction of the FP32 Khatri-Rao rows with the
-// complex-embedded x-sine table on the tensor cores (3xTF32; K = nX, short
-// enough for FP32 accumulation), then the batch of per-pair y-projections.
+// complex-embedded x-sine table on the tensor cores (split-FP16 product; K = nX,
+// short enough for FP32 accumulation), then the batch of per-pair y-projections.
 // LSQR then applies J32 and J32^H by the two products below, which read J32
 // once each and accumulate in FP64, so that they stay exact transposes of one
 // operator (products computed from the fields with independent FP32 rounding
@@ -251,6 +251,7 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
   const long long nt = (long long)nX * std::max(S1, S2);
   k_sine_tables32<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(sx, sy, nX, S1, S2, sxc, sy32);
   HS_COUNT_LAUNCH();
+  TcScope tc;  // the x-projection may run on the tensor cores (one-shot FP32 matrix)
   for (long long c0 = 0; c0 < MP; c0 += C) {
     const int nc = (int)std::min<long long>(C, MP - c0);
     k_khatri_rao32<<<dim3((unsigned)((plane + 255) / 256), (nc + KR_PAIRS - 1) / KR_PAIRS), 256, 0, s>>>(

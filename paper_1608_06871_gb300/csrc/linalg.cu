@@ -4,6 +4,10 @@
 // kernels are arithmetic-bound by construction; they are tiled for data reuse
 // in shared memory and use every SM through the batch and tile dimensions.
 #include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include <cooperative_groups.h>
@@ -29,7 +33,8 @@ template <typename TA, typename TB> constexpr double flops_per_mac() {
   return (is_cplx<TA>::v && is_cplx<TB>::v) ? 8.0 : ((is_cplx<TA>::v || is_cplx<TB>::v) ? 4.0 : 2.0);
 }
 constexpr int BM = 32, BN = 32, BK = 16;  // GEMM tile
-constexpr int NB = 32;                    // LU / TRSM block size
+constexpr int NB = 32;                    // LU panel / TRSM block size
+constexpr int NBB = 128;                  // LU super-panel: k of the trailing updates
 constexpr int kMaxCluster = 8;            // portable thread-block cluster size (split-k)
 
 template <typename T> __device__ __forceinline__ T ld_op(const T* P, int ld, int op, int r, int c) {
@@ -351,21 +356,11 @@ __global__ void k_swaps(const int* piv, long long sP, int n, int reverse, E* B, 
 }
 }  // namespace
 
+namespace {
+// SIMT product (FP64, or FP32 where the tensor-core path is not taken).
 template <typename TA, typename TB, typename TC>
-void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const TA* A, int lda, long long sA,
-          const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC, int batch) {
-  if (m <= 0 || n <= 0 || batch <= 0) return;
-  if constexpr (std::is_same<TA, float2>::value && std::is_same<TB, float2>::value &&
-                std::is_same<TC, float2>::value) {
-    if (cgemm_tc_eligible(opA, opB, m, n, k, batch)) {
-      const bool prof_tc = prof_active(3);
-      cudaEvent_t ev = nullptr;
-      if (prof_tc) prof_begin(s, &ev);
-      cgemm_tc(s, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
-      if (prof_tc) prof_end(s, ev, 8.0 * m * n * k * batch);
-      return;
-    }
-  }
+void gemm_simt(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const TA* A, int lda, long long sA,
+               const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC, int batch) {
   const bool prof = prof_active(is_fp64<TC>::v ? 1 : 2);
   cudaEvent_t ev = nullptr;
   if (prof) prof_begin(s, &ev);
@@ -406,17 +401,161 @@ void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const
   if (prof) prof_end(s, ev, flops_per_mac<TA, TB>() * (double)m * n * k * batch);
 }
 
+// Products the split-TF32 tensor-core path takes (t32_gemm modes): complex x
+// complex (2), real x complex (1), real x real (0), FP32, no transposes.
+template <typename TA, typename TB, typename TC> struct t32_mode { static constexpr int v = -1; };
+template <> struct t32_mode<float2, float2, float2> { static constexpr int v = 2; };
+template <> struct t32_mode<float, float2, float2> { static constexpr int v = 1; };
+template <> struct t32_mode<float, float, float> { static constexpr int v = 0; };
+
+inline float2 as_f2(float2 x) { return x; }
+inline float2 as_f2(float x) { return make_float2(x, 0.f); }
+template <typename T> constexpr long long fl() { return sizeof(T) / sizeof(float); }  // floats per element
+
+// Default choice without a measurement: large products only (at least 2^27
+// real multiply-adds, every dimension of the real product >= 128).
+bool t32_default(int mode, int m, int n, int k) {
+  const long long np = mode ? 2LL * n : n, kp = mode == 2 ? 2LL * k : k;
+  return m >= 128 && np >= 128 && kp >= 128 && (long long)m * np * kp >= (1LL << 27);
+}
+
+// Per-shape choice between the tensor-core and the SIMT product, measured
+// once per shape class (both variants on a scratch copy of C, CUDA events,
+// best of two after a warm-up) outside stream capture; inside a capture a
+// shape not yet measured takes the default.
+// Shapes are keyed in half-octave classes (a frequency sweep changes its sizes
+// in small steps; one measurement serves a class).
+inline int size_class(long long x) { return x <= 1 ? 0 : (int)std::lround(2.0 * std::log2((double)x)); }
+struct TuneKey {
+  int mode, m, n, k, batch, bsh;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(mode, m, n, k, batch, bsh) < std::tie(o.mode, o.m, o.n, o.k, o.batch, o.bsh);
+  }
+};
+// The tensor-core product carries the split's rounding (2^-22 of each operand
+// against FP32's 2^-24), which slows the refinement of the mixed solver a
+// little; it is taken only where it is clearly faster.
+constexpr float kTcMargin = 0.7f;
+std::mutex g_tune_mu;
+std::map<TuneKey, bool> g_tune;
+
+}  // namespace
+
+bool g_autotune = true;             // hs_set_autotune
+int g_t32_mode = 1;                 // hs_set_tensor_cores: 0 off, 1 opted-in scopes, 2 forced, 3 every product tuned
+thread_local int g_t32_scope = 0;   // > 0 inside a TcScope (products that opt in)
+thread_local bool g_prof_suspended = false;
+thread_local int g_last_gemm_tc = 0;
+
+template <typename TA, typename TB, typename TC>
+void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const TA* A, int lda, long long sA,
+          const TB* B, int ldb, long long sB, TC beta, TC* C, int ldc, long long sC, int batch) {
+  if (m <= 0 || n <= 0 || batch <= 0) return;
+  g_last_gemm_tc = 0;
+  constexpr int mode = t32_mode<TA, TB, TC>::v;
+  if constexpr (mode >= 0) {
+    const bool force = g_t32_mode == 2;
+    const bool eligible = force || g_t32_mode == 3 || (g_t32_mode == 1 && g_t32_scope > 0);
+    if (opA == OP_N && opB == OP_N && k > 0 && eligible) {
+      auto run_tc = [&](TC* Cd) {
+        return t32_gemm(s, mode, m, n, k, as_f2(alpha), reinterpret_cast<const float*>(A), fl<TA>() * lda,
+                        fl<TA>() * sA, reinterpret_cast<const float*>(B), fl<TB>() * ldb, fl<TB>() * sB, as_f2(beta),
+                        Cd, ldc, sC, batch);
+      };
+      bool use = force || t32_default(mode, m, n, k);
+      const TuneKey key{mode, size_class(m), size_class(n), size_class(k), size_class(batch),
+                        (sB == 0 && batch > 1) ? 1 : 0};
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(s, &cs);
+      bool known = false;
+      {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end() && !force) {
+          use = it->second;
+          known = true;
+        }
+      }
+      if (!known && !force && g_autotune && cs == cudaStreamCaptureStatusNone) {
+        // measure both on a copy of C (the real C is written once, below)
+        const long long span = (long long)(batch - 1) * sC + (long long)(m - 1) * ldc + n;
+        TC* tmp = nullptr;
+        if (cudaMalloc(&tmp, sizeof(TC) * span) == cudaSuccess) {
+          long long* counter = g_launch_counter;
+          g_launch_counter = nullptr;
+          g_prof_suspended = true;
+          cudaEvent_t ev[3];
+          for (auto& e : ev) cudaEventCreate(&e);
+          float best_tc = 1e30f, best_simt = 1e30f;
+          bool tc_ok = true;
+          for (int rep = 0; rep < 3 && tc_ok; ++rep) {
+            cudaMemcpyAsync(tmp, C, sizeof(TC) * span, cudaMemcpyDeviceToDevice, s);
+            cudaEventRecord(ev[0], s);
+            tc_ok = run_tc(tmp);
+            cudaEventRecord(ev[1], s);
+            gemm_simt<TA, TB, TC>(s, opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, tmp, ldc, sC, batch);
+            cudaEventRecord(ev[2], s);
+            cudaEventSynchronize(ev[2]);
+            float t1 = 0.f, t2 = 0.f;
+            cudaEventElapsedTime(&t1, ev[0], ev[1]);
+            cudaEventElapsedTime(&t2, ev[1], ev[2]);
+            if (rep > 0) {
+              best_tc = std::min(best_tc, t1);
+              best_simt = std::min(best_simt, t2);
+            }
+          }
+          for (auto& e : ev) cudaEventDestroy(e);
+          cudaFree(tmp);
+          g_prof_suspended = false;
+          g_launch_counter = counter;
+          use = tc_ok && best_tc < kTcMargin * best_simt;
+          std::lock_guard<std::mutex> lock(g_tune_mu);
+          g_tune[key] = use;
+        } else {
+          cudaGetLastError();
+        }
+      }
+      if (use && run_tc(C)) {
+        g_last_gemm_tc = 1;
+        return;
+      }
+    }
+  }
+  gemm_simt<TA, TB, TC>(s, opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+}
+
 template <typename E>
 void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, long long sP, int* info, int batch) {
-  for (int j0 = 0; j0 < n; j0 += NB) {
-    int nb = n - j0 < NB ? n - j0 : NB;
-    lu_panel<E>(s, A, lda, sA, n, j0, nb, piv, sP, info, batch);
-    int rest = n - j0 - nb;
+  const E m1 = -el<E>::one(), one = el<E>::one();
+  // Two-level right-looking blocking: super-panels of NBB columns, each
+  // factored as NB-wide pivoted panels whose updates stay inside the
+  // super-panel; then U12 = L11^-1 A12 for the super-panel's rows and one
+  // trailing update with k = NBB (the product the tensor cores take).
+  for (int J0 = 0; J0 < n; J0 += NBB) {
+    const int nbs = std::min(NBB, n - J0), J1 = J0 + nbs;
+    for (int j0 = J0; j0 < J1; j0 += NB) {
+      const int nb = std::min(NB, J1 - j0);
+      lu_panel<E>(s, A, lda, sA, n, j0, nb, piv, sP, info, batch);  // row moves cover every column
+      const int rin = J1 - j0 - nb;  // columns of the super-panel right of this panel
+      if (rin > 0) {
+        trsm_diag<E>(s, A, lda, sA, j0, nb, 0, A + j0 + nb, lda, sA, rin, batch);
+        gemm<E, E, E>(s, OP_N, OP_N, n - j0 - nb, rin, nb, m1, A + (long long)(j0 + nb) * lda + j0, lda, sA,
+                      A + (long long)j0 * lda + j0 + nb, lda, sA, one, A + (long long)(j0 + nb) * lda + j0 + nb, lda,
+                      sA, batch);
+      }
+    }
+    const int rest = n - J1;
     if (rest > 0) {
-      trsm_diag<E>(s, A, lda, sA, j0, nb, 0, A + j0 + nb, lda, sA, rest, batch);
-      gemm<E, E, E>(s, OP_N, OP_N, rest, rest, nb, -el<E>::one(), A + (long long)(j0 + nb) * lda + j0, lda, sA,
-                    A + (long long)j0 * lda + j0 + nb, lda, sA, el<E>::one(),
-                    A + (long long)(j0 + nb) * lda + j0 + nb, lda, sA, batch);
+      for (int i0 = J0; i0 < J1; i0 += NB) {  // U12 = L11^-1 A12, blocked
+        const int nb = std::min(NB, J1 - i0);
+        trsm_diag<E>(s, A, lda, sA, i0, nb, 0, A + J1, lda, sA, rest, batch);
+        const int rows_in = J1 - i0 - nb;
+        if (rows_in > 0)
+          gemm<E, E, E>(s, OP_N, OP_N, rows_in, rest, nb, m1, A + (long long)(i0 + nb) * lda + i0, lda, sA,
+                        A + (long long)i0 * lda + J1, lda, sA, one, A + (long long)(i0 + nb) * lda + J1, lda, sA, batch);
+      }
+      gemm<E, E, E>(s, OP_N, OP_N, rest, rest, nbs, m1, A + (long long)J1 * lda + J0, lda, sA,
+                    A + (long long)J0 * lda + J1, lda, sA, one, A + (long long)J1 * lda + J1, lda, sA, batch);
     }
   }
 }
@@ -447,20 +586,33 @@ void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int 
   if (trans == OP_N) {
     k_swaps<E><<<gs, 128, 0, s>>>(piv, sP, n, 0, B, ldb, sB, nrhs);
     HS_COUNT_LAUNCH();
-    for (int i0 = 0; i0 < n; i0 += NB) {  // L y = b
-      int nb = n - i0 < NB ? n - i0 : NB;
-      trsm_diag<E>(s, A, lda, sA, i0, nb, 0, B, ldb, sB, nrhs, batch);
-      int rest = n - i0 - nb;
-      if (rest > 0)
-        gemm<E, E, E>(s, OP_N, OP_N, rest, nrhs, nb, m1, A + (long long)(i0 + nb) * lda + i0, lda, sA,
-                      B + (long long)i0 * ldb, ldb, sB, one, B + (long long)(i0 + nb) * ldb, ldb, sB, batch);
+    // blocks of NBB rows (NB-wide triangular solves and updates inside the
+    // block), then one update of the remaining rows with k = NBB
+    for (int I0 = 0; I0 < n; I0 += NBB) {  // L y = b
+      const int I1 = std::min(n, I0 + NBB);
+      for (int i0 = I0; i0 < I1; i0 += NB) {
+        const int nb = std::min(NB, I1 - i0);
+        trsm_diag<E>(s, A, lda, sA, i0, nb, 0, B, ldb, sB, nrhs, batch);
+        if (I1 - i0 - nb > 0)
+          gemm<E, E, E>(s, OP_N, OP_N, I1 - i0 - nb, nrhs, nb, m1, A + (long long)(i0 + nb) * lda + i0, lda, sA,
+                        B + (long long)i0 * ldb, ldb, sB, one, B + (long long)(i0 + nb) * ldb, ldb, sB, batch);
+      }
+      if (n - I1 > 0)
+        gemm<E, E, E>(s, OP_N, OP_N, n - I1, nrhs, I1 - I0, m1, A + (long long)I1 * lda + I0, lda, sA,
+                      B + (long long)I0 * ldb, ldb, sB, one, B + (long long)I1 * ldb, ldb, sB, batch);
     }
-    int last = ((n - 1) / NB) * NB;
-    for (int i0 = last; i0 >= 0; i0 -= NB) {  // U x = y
-      int nb = n - i0 < NB ? n - i0 : NB;
-      trsm_diag<E>(s, A, lda, sA, i0, nb, 1, B, ldb, sB, nrhs, batch);
-      if (i0 > 0)
-        gemm<E, E, E>(s, OP_N, OP_N, i0, nrhs, nb, m1, A + i0, lda, sA, B + (long long)i0 * ldb, ldb, sB, one, B,
+    const int lastB = ((n - 1) / NBB) * NBB;
+    for (int I0 = lastB; I0 >= 0; I0 -= NBB) {  // U x = y
+      const int I1 = std::min(n, I0 + NBB);
+      for (int i0 = I0 + ((I1 - I0 - 1) / NB) * NB; i0 >= I0; i0 -= NB) {
+        const int nb = std::min(NB, I1 - i0);
+        trsm_diag<E>(s, A, lda, sA, i0, nb, 1, B, ldb, sB, nrhs, batch);
+        if (i0 > I0)
+          gemm<E, E, E>(s, OP_N, OP_N, i0 - I0, nrhs, nb, m1, A + (long long)I0 * lda + i0, lda, sA,
+                        B + (long long)i0 * ldb, ldb, sB, one, B + (long long)I0 * ldb, ldb, sB, batch);
+      }
+      if (I0 > 0)
+        gemm<E, E, E>(s, OP_N, OP_N, I0, nrhs, I1 - I0, m1, A + I0, lda, sA, B + (long long)I0 * ldb, ldb, sB, one, B,
                       ldb, sB, batch);
     }
   } else {

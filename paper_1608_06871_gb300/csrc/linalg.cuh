@@ -46,14 +46,39 @@ template <typename E>
 void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int n, const int* piv,
               long long sP, E* B, int ldb, long long sB, int nrhs, int batch);
 
-// Tensor-core complex FP32 GEMM (tcgen05, 3xTF32; tcgemm.cu), used by gemm()
-// for float2 products with both operands untransposed and m >= 128, n >= 64.
-extern bool g_tc_enabled;
-bool cgemm_tc_eligible(int opA, int opB, int m, int n, int k, int batch);
-void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A, int lda, long long sA,
-              const float2* B, int ldb, long long sB, float2 beta, float2* C, int ldc, long long sC, int batch);
+
+// FP32 products on the tensor cores by a two-term TF32 split (tc32.cu):
+// C = alpha A B + beta C, row-major, no transposes; mode 2: complex A and B,
+// mode 1: real A, complex B, mode 0: real A and B (alpha, beta real: .x).
+// Leading dimensions and batch strides of A and B in floats, of C in
+// elements.  Returns false (nothing launched) when the product cannot run
+// there (switched off, or no scratch while the stream is being captured).
+bool t32_gemm(cudaStream_t s, int mode, int m, int n, int k, float2 alpha, const float* A, long long lda,
+              long long sA, const float* B, long long ldb, long long sB, float2 beta, void* C, int ldc, long long sC,
+              int batch);
+bool t32_timed_out(cudaStream_t s);
+// gemm() measures, once per shape, the tensor-core and the SIMT product and
+// keeps the faster (g_autotune; off: a fixed size rule); g_last_gemm_tc is 1
+// when the calling thread's last gemm() ran on the tensor cores.
+extern bool g_autotune;
+// Tensor-core use for FP32 products (hs_set_tensor_cores): 0 never; 1 (the
+// default) inside TcScope regions only, per-shape choice there; 2 every
+// supported product; 3 per-shape choice for every product.  The solver's
+// factorisation and refinement products stay on SIMT FP32 by default: the
+// tensor cores' FP32 accumulation is less accurate than the SIMT FMA chains,
+// and at k = 70 that costs the refinement a fourth pass, more than the faster
+// products save.  The Jacobian's FP32 contraction opts in.
+extern int g_t32_mode;
+extern thread_local int g_t32_scope;
+struct TcScope {
+  TcScope() { ++g_t32_scope; }
+  ~TcScope() { --g_t32_scope; }
+};
+extern thread_local bool g_prof_suspended;
+extern thread_local int g_last_gemm_tc;
 // Synchronises s, then reads and clears this device's flags that a bounded
-// tensor-core wait gave up (the complex FP32 GEMM's and the emulated-FP64 one's).
+// tensor-core wait gave up (the split-TF32 product's, the emulated-FP64 one's,
+// and the one the host raises in tests; tcgemm.cu).
 bool tc_timed_out(cudaStream_t s);
 bool oz_timed_out(cudaStream_t s);
 cudaError_t tc_raise_timeout_flag();

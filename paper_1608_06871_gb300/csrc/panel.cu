@@ -44,93 +44,167 @@ template <> struct pmag<double2> { using T = double; __device__ static double of
 template <> struct pmag<float> { using T = float; __device__ static float of(float a) { return fabsf(a); } };
 template <> struct pmag<float2> { using T = float; __device__ static float of(float2 a) { return a.x * a.x + a.y * a.y; } };
 
+// 1 / x with one correctly rounded reciprocal: real x directly; complex x as
+// conj(x) / |x|^2, or, where |x|^2 could leave the normal range, x = 2^e (a + i b)
+// with the power of two from the larger component's exponent (exact), then
+// (a - i b) / (a^2 + b^2) 2^-e.  The multipliers are formed as x_i (1 / pivot),
+// as LAPACK's unblocked LU does.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float2 recip(float2 x) {
+  const float n2 = fmaf(x.x, x.x, x.y * x.y);
+  if (n2 > 1e-30f && n2 < 1e30f) {  // |x|^2 safely inside the normal range
+    const float d = __frcp_rn(n2);
+    return make_float2(x.x * d, -x.y * d);
+  }
+  const int e = ilogbf(fmaxf(fabsf(x.x), fabsf(x.y)));
+  const float a = scalbnf(x.x, -e), b = scalbnf(x.y, -e);
+  const float d = scalbnf(__frcp_rn(fmaf(a, a, b * b)), -e);
+  return make_float2(a * d, -b * d);
+}
+__device__ __forceinline__ double2 recip(double2 x) {
+  const double n2 = fma(x.x, x.x, x.y * x.y);
+  if (n2 > 1e-290 && n2 < 1e290) {
+    const double d = __drcp_rn(n2);
+    return make_double2(x.x * d, -x.y * d);
+  }
+  const int e = ilogb(fmax(fabs(x.x), fabs(x.y)));
+  const double a = scalbn(x.x, -e), b = scalbn(x.y, -e);
+  const double d = scalbn(__drcp_rn(fma(a, a, b * b)), -e);
+  return make_double2(a * d, -b * d);
+}
+
 // Factor the rows x nb tile T (row stride ld, shared memory) with partial
-// pivoting, one thread per row (blockDim.x = PT >= rows).  Each thread keeps
-// its row in registers for the whole factorisation; per column one barrier
-// publishes every warp's candidate pivot (each thread then reduces the warp
-// candidates itself), one more publishes the pivot row (and the row it
-// displaces), and the rank-1 update touches registers only.  rid[] is
-// permuted with the rows; sp[j] (if not NULL) receives the local row swapped
-// with row j at step j; *zc is lowered to the first column whose pivot is
-// exactly zero (that column is then left unscaled).  The factored tile is
-// written back to T.
+// pivoting, one thread per row (blockDim.x = PT >= rows).  The rows stay where
+// they are: each thread tracks the logical position of its own row (mylg), a
+// pivot step only relabels two rows, and the thread whose row became a pivot
+// row stops updating it, so every other thread can read the pivot row in
+// place.  Per column there is a single barrier, after the warps publish their
+// candidates (magnitude, then lowest logical position, as LAPACK's first
+// maximum; FP32 magnitudes are reduced with redux.sync on their bit
+// patterns).  The column loop is not unrolled (a small instruction footprint:
+// the per-column latency is the point here); the thread keeps its row in
+// registers and mirrors every updated entry to the tile.
+// On return, loc[r] is the tile row holding logical row r, rid[] is permuted
+// into logical order, sp[j] (if not NULL) receives the logical row swapped
+// with row j at step j, and *zc is lowered to the first column whose pivot is
+// exactly zero (that column is then left unscaled).
 template <typename E>
-__device__ void tile_lu(E* T, int ld, int rows, int nb, int* rid, int* sp, int* zc) {
+__device__ void tile_lu(E* T, int ld, int rows, int nb, int* rid, int* loc, int* sp, int* zc) {
   using M = typename pmag<E>::T;
   constexpr int NW = PT / 32;
   __shared__ M wbest[2][NW];
-  __shared__ int widx[2][NW];
-  __shared__ E ubuf[2][PNB], xbuf[2][PNB];
+  __shared__ int wkey[2][NW];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int steps = min(rows, nb);
+  bool active = t < rows;
+  int mylg = t;
+  const int myid = active ? rid[t] : 0;
+  E* row = T + t * ld;
+  // the thread's row in registers (entries right of the current column are
+  // the live ones); shared memory holds a mirror that the others read when
+  // this row becomes the pivot row
   E r[PNB];
 #pragma unroll
-  for (int c = 0; c < PNB; ++c) r[c] = (t < rows && c < nb) ? T[t * ld + c] : el<E>::zero();
-#pragma unroll
-  for (int j = 0; j < PNB; ++j) {
-    if (j < steps) {
-      const int pb = j & 1;
-      M best = (t >= j && t < rows) ? pmag<E>::of(r[j]) : M(-1);
-      int bi = (t >= j && t < rows) ? t : INT_MAX;
+  for (int c = 0; c < PNB; ++c) r[c] = (active && c < nb) ? row[c] : el<E>::zero();
+  for (int j = 0; j < steps; ++j) {
+    const int pb = j & 1;
+    M best = active ? pmag<E>::of(row[j]) : M(-1);
+    int key = active ? (mylg << 8) | t : INT_MAX;  // logical position, then tile row
+    if constexpr (sizeof(M) == 4) {
+      // FP32 magnitudes: the warp maximum of their bit patterns (ordered for
+      // non-negative floats; +1 keeps an active zero above an inactive row),
+      // then the smallest key among the lanes holding it: two redux.sync
+      unsigned mb = active ? __float_as_uint(best) + 1u : 0u;
+      mb = __reduce_max_sync(0xffffffffu, mb);
+      key = (int)__reduce_min_sync(0xffffffffu, (active && __float_as_uint(best) + 1u == mb) ? (unsigned)key
+                                                                                            : 0xffffffffu);
+      if (lane == 0) { wbest[pb][warp] = __uint_as_float(mb); wkey[pb][warp] = key; }
+      __syncthreads();
+      const unsigned wb = lane < NW ? __float_as_uint(wbest[pb][lane]) : 0u;
+      const unsigned wk = lane < NW ? (unsigned)wkey[pb][lane] : 0xffffffffu;
+      const unsigned bb = __reduce_max_sync(0xffffffffu, wb);
+      key = (int)__reduce_min_sync(0xffffffffu, wb == bb ? wk : 0xffffffffu);
+    } else {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const M ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        const int ok = __shfl_down_sync(0xffffffffu, key, o);
+        if (ob > best || (ob == best && ok < key)) { best = ob; key = ok; }
       }
-      if (lane == 0) { wbest[pb][warp] = best; widx[pb][warp] = bi; }
+      if (lane == 0) { wbest[pb][warp] = best; wkey[pb][warp] = key; }
       __syncthreads();
       best = wbest[pb][0];
-      bi = widx[pb][0];
+      key = wkey[pb][0];
 #pragma unroll
       for (int w = 1; w < NW; ++w) {
         const M ob = wbest[pb][w];
-        const int oi = widx[pb][w];
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        const int ok = wkey[pb][w];
+        if (ob > best || (ob == best && ok < key)) { best = ob; key = ok; }
       }
-      const int p = bi < rows ? bi : j;
-      if (t == p) {
+    }
+    const int p = key & 255, lp = key >> 8;
+    if (sp && t == 0) sp[j] = lp;
+    if (t == p) {
+      active = false;
+      mylg = j;
+    } else if (mylg == j) {
+      mylg = lp;
+    }
+    const E* prow = T + p * ld;
+    const E pv = prow[j];
+    if (!(pmag<E>::of(pv) > M(0))) {
+      if (t == 0) atomicMin(zc, j);
+    } else if (active) {
+      const E l = row[j] * recip(pv);
+      row[j] = l;
+      // rank-1 update in registers, in groups of eight columns (groups left of
+      // the column are skipped, warp-uniformly); each group's pivot entries are
+      // loaded before its mirror stores are issued
 #pragma unroll
-        for (int c = 0; c < PNB; ++c) ubuf[pb][c] = r[c];
-      }
-      if (t == j && p != j) {
+      for (int g = 0; g < PNB / 8; ++g) {
+        if (8 * g + 7 > j) {
+          E u[8];
 #pragma unroll
-        for (int c = 0; c < PNB; ++c) xbuf[pb][c] = r[c];
-      }
-      if (t == 0) {
-        if (p != j) {
-          const int tr = rid[j];
-          rid[j] = rid[p];
-          rid[p] = tr;
+          for (int q = 0; q < 8; ++q) u[q] = 8 * g + q < nb ? prow[8 * g + q] : el<E>::zero();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int c = 8 * g + q;
+            if (c > j && c < nb) {
+              r[c] = fmsc(r[c], l, u[q]);
+              row[c] = r[c];
+            }
+          }
         }
-        if (sp) sp[j] = p;
-      }
-      __syncthreads();
-      if (p != j && t == p) {
-#pragma unroll
-        for (int c = 0; c < PNB; ++c) r[c] = xbuf[pb][c];
-      }
-      if (t == j) {
-#pragma unroll
-        for (int c = 0; c < PNB; ++c) r[c] = ubuf[pb][c];
-      }
-      const E pv = ubuf[pb][j];
-      if (!(pmag<E>::of(pv) > M(0))) {
-        if (t == 0) atomicMin(zc, j);
-      } else if (t > j && t < rows) {
-        const E l = el<E>::div(r[j], pv);
-        r[j] = l;
-#pragma unroll
-        for (int c = j + 1; c < PNB; ++c) r[c] = fmsc(r[c], l, ubuf[pb][c]);
       }
     }
   }
+  __syncthreads();
   if (t < rows) {
-#pragma unroll
-    for (int c = 0; c < PNB; ++c)
-      if (c < nb) T[t * ld + c] = r[c];
+    loc[mylg] = t;
+    rid[mylg] = myid;
   }
   __syncthreads();
+}
+
+// Stage rows x nb elements into the tile T (row stride ld): tile row r is
+// source row ids[r] (or row0 + r without ids) of A (row stride lda).  One warp
+// per row, lanes along the columns, eight rows in flight per warp.
+template <typename E>
+__device__ void load_rows(E* T, int ld, int rows, int nb, const E* A, int lda, const int* ids, int row0) {
+  constexpr int NW = PT / 32, RF = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r0 = warp * RF; r0 < rows; r0 += NW * RF) {
+    E v[RF];
+#pragma unroll
+    for (int q = 0; q < RF; ++q) {
+      const int r = r0 + q;
+      v[q] = (r < rows && lane < nb) ? A[(long long)(ids ? ids[r] : row0 + r) * lda + lane] : el<E>::zero();
+    }
+#pragma unroll
+    for (int q = 0; q < RF; ++q)
+      if (r0 + q < rows && lane < nb) T[(r0 + q) * ld + lane] = v[q];
+  }
 }
 
 // Short panel (m = n - j0 <= PR rows): one CTA per matrix.
@@ -139,7 +213,7 @@ __global__ void __launch_bounds__(PT) k_panel_small(E* A, int lda, long long sA,
                                                     long long sP, int* info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E* T = reinterpret_cast<E*>(smem_raw);
-  __shared__ int rid[PR];
+  __shared__ int rid[PR], loc[PR];
   __shared__ int sp[PNB];
   __shared__ int aff_d[2 * PNB], aff_s[2 * PNB];
   __shared__ int zc, naff;
@@ -147,17 +221,14 @@ __global__ void __launch_bounds__(PT) k_panel_small(E* A, int lda, long long sA,
   A += b * sA;
   piv += b * sP;
   const int m = n - j0, ld = nb + 1;
-  for (int e = t; e < m * nb; e += PT) {
-    const int r = e / nb, c = e % nb;
-    T[r * ld + c] = A[(long long)(j0 + r) * lda + j0 + c];
-  }
+  load_rows<E>(T, ld, m, nb, A + j0, lda, nullptr, j0);
   if (t < m) rid[t] = t;
   if (t == 0) zc = INT_MAX;
   __syncthreads();
-  tile_lu<E>(T, ld, m, nb, rid, sp, &zc);
+  tile_lu<E>(T, ld, m, nb, rid, loc, sp, &zc);
   for (int e = t; e < m * nb; e += PT) {
     const int r = e / nb, c = e % nb;
-    A[(long long)(j0 + r) * lda + j0 + c] = T[r * ld + c];
+    A[(long long)(j0 + r) * lda + j0 + c] = T[loc[r] * ld + c];
   }
   if (t == 0) {
     const int steps = min(m, nb);
@@ -197,7 +268,7 @@ __global__ void __launch_bounds__(PT) k_tp_select(E* A, int lda, long long sA, i
                                                   int final_round, int aff_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E* T = reinterpret_cast<E*>(smem_raw);
-  __shared__ int rid[PR];
+  __shared__ int rid[PR], loc[PR];
   __shared__ int wsum[PT / 32];
   __shared__ int zc;
   __shared__ int kpos[2 * PNB], korig[2 * PNB];
@@ -226,12 +297,9 @@ __global__ void __launch_bounds__(PT) k_tp_select(E* A, int lda, long long sA, i
   if (myrow >= 0) rid[off + __popc(bal & ((1u << lane) - 1u))] = myrow;
   __syncthreads();
   const int ld = nb + 1;
-  for (int e = t; e < rows * nb; e += PT) {
-    const int r = e / nb, c = e % nb;
-    T[r * ld + c] = A[(long long)rid[r] * lda + j0 + c];
-  }
+  load_rows<E>(T, ld, rows, nb, A + j0, lda, rid, 0);
   __syncthreads();
-  tile_lu<E>(T, ld, rows, nb, rid, nullptr, &zc);
+  tile_lu<E>(T, ld, rows, nb, rid, loc, nullptr, &zc);
   if (!final_round) {
     if (t < nb) W[out_off + set * nb + t] = t < rows ? rid[t] : -1;
     return;
@@ -240,7 +308,7 @@ __global__ void __launch_bounds__(PT) k_tp_select(E* A, int lda, long long sA, i
   // in the pivot rows' panel columns, which the row moves carry to j0 .. j0 + nb
   for (int e = t; e < nb * nb; e += PT) {
     const int r = e / nb, c = e % nb;
-    A[(long long)rid[r] * lda + j0 + c] = T[r * ld + c];
+    A[(long long)rid[r] * lda + j0 + c] = T[loc[r] * ld + c];
   }
   if (t == 0) {
     if (zc != INT_MAX && info[b] == 0) info[b] = j0 + zc + 1;

@@ -33,41 +33,90 @@ __global__ void k_f2d_add(const float2* __restrict__ a, double2* __restrict__ b,
   if (i < n) b[i] = make_double2(b[i].x + (double)a[i].x, b[i].y + (double)a[i].y);
 }
 
-constexpr int RCH = 8;  // right-hand sides per block in the PDE residual
+constexpr int RCH = 8;              // right-hand sides per block in the PDE residual
+constexpr int RP_THREADS = 49 * RCH;  // one thread per (a, b) in 1..7 x 1..7 and right-hand side
 
 // RP[leaf][r][j] = -(Lap_h u + k^2 (1 - q) u) at interior node r, for the FP64 iterate X.
-__global__ void __launch_bounds__(256) k_res_pde(const double2* __restrict__ X, const double* __restrict__ q,
-                                                 const double* __restrict__ D1, double k, double h, int nrhs,
-                                                 float2* __restrict__ RP) {
-  __shared__ double D2[16][16], Dx[16][16];
-  __shared__ double2 u[NL][RCH];
-  const int leaf = blockIdx.x, j0 = blockIdx.y * RCH;
+// The second-derivative matrix D2 = (2/h)^2 D1 D1 of the Chebyshev points is
+// centro-symmetric (D2[15-a][15-c] = D2[a][c]), so along a grid line with
+// s_c = u_c + u_(15-c), d_c = u_c - u_(15-c) (c < 8) and E[a][c], O[a][c] the
+// half sums and differences of D2[a][c] and D2[a][15-c]:
+//   (D2 u)_a = sum_c E[a][c] s_c + O[a][c] d_c,  (D2 u)_(15-a) = the same with -O,
+// half the FP64 multiply-adds of the plain row products (the FP64 pipe bounds
+// this kernel).  Each thread forms the four mirror nodes (a, b), (15-a, b),
+// (a, 15-b), (15-a, 15-b) of one right-hand side from the s, d of the two
+// columns and two rows through them.
+__global__ void __launch_bounds__(RP_THREADS) k_res_pde(const double2* __restrict__ X, const double* __restrict__ q,
+                                                        const double* __restrict__ D1, double k, double h, int nrhs,
+                                                        float2* __restrict__ RP) {
+  __shared__ double Dx[16][16], D2r[8][16], E[8][8], O[8][8];
+  extern __shared__ double2 rp_dyn[];  // u[NL][RCH], then sx, dx, sy, dy [14][8][RCH]
+  auto u = reinterpret_cast<double2(*)[RCH]>(rp_dyn);
+  auto sx = reinterpret_cast<double2(*)[8][RCH]>(rp_dyn + NL * RCH);
+  auto dx = sx + 14, sy = sx + 28, dy = sx + 42;
+  const int leaf = blockIdx.x, j0 = blockIdx.y * RCH, t = threadIdx.x;
   const int nj = min(RCH, nrhs - j0);
   const double sc = 2.0 / h;
-  for (int e = threadIdx.x; e < 256; e += blockDim.x) Dx[e / 16][e % 16] = D1[e] * sc;
-  for (int e = threadIdx.x; e < NL * RCH; e += blockDim.x) {
-    int r = e / RCH, j = e % RCH;
+  for (int e = t; e < 256; e += RP_THREADS) Dx[e / 16][e % 16] = D1[e] * sc;
+  for (int e = t; e < NL * RCH; e += RP_THREADS) {
+    const int r = e / RCH, j = e % RCH;
     u[r][j] = j < nj ? X[((long long)leaf * NL + r) * nrhs + j0 + j] : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
-    int i = e / 16, jj = e % 16;
-    double s = 0.0;
-    for (int c = 0; c < 16; ++c) s += Dx[i][c] * Dx[c][jj];
-    D2[i][jj] = s;
+  // rows 1..7 of D2; the line sums and differences (x lines: column b = l + 1;
+  // y lines: row a = l + 1)
+  for (int e = t; e < 7 * 16; e += RP_THREADS) {
+    const int a = e / 16 + 1, c = e % 16;
+    double acc = 0.0;
+    for (int m = 0; m < 16; ++m) acc = fma(Dx[a][m], Dx[m][c], acc);
+    D2r[a][c] = acc;
+  }
+  for (int e = t; e < 2 * 14 * 8 * RCH; e += RP_THREADS) {
+    const int j = e % RCH, c = (e / RCH) % 8, l = (e / (8 * RCH)) % 14, dir = e / (14 * 8 * RCH);
+    if (dir == 0) {
+      const double2 p = u[lidx(c, l + 1)][j], m = u[lidx(15 - c, l + 1)][j];
+      sx[l][c][j] = p + m;
+      dx[l][c][j] = p - m;
+    } else {
+      const double2 p = u[lidx(l + 1, c)][j], m = u[lidx(l + 1, 15 - c)][j];
+      sy[l][c][j] = p + m;
+      dy[l][c][j] = p - m;
+    }
   }
   __syncthreads();
+  for (int e = t; e < 7 * 8; e += RP_THREADS) {
+    const int a = e / 8 + 1, c = e % 8;
+    E[a][c] = 0.5 * (D2r[a][c] + D2r[a][15 - c]);
+    O[a][c] = 0.5 * (D2r[a][c] - D2r[a][15 - c]);
+  }
+  __syncthreads();
+  const int j = t % RCH, pr = t / RCH;
+  if (j >= nj) return;
+  const int a = pr / 7 + 1, b = pr % 7 + 1;  // a, b in 1..7; mirrors 15 - a, 15 - b
+  double2 xe1 = make_double2(0.0, 0.0), xo1 = xe1, xe2 = xe1, xo2 = xe1;  // columns b, 15 - b
+  double2 ye1 = xe1, yo1 = xe1, ye2 = xe1, yo2 = xe1;                     // rows a, 15 - a
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const double ea = E[a][c], oa = O[a][c], eb = E[b][c], ob = O[b][c];
+    xe1 = xe1 + ea * sx[b - 1][c][j];
+    xo1 = xo1 + oa * dx[b - 1][c][j];
+    xe2 = xe2 + ea * sx[14 - b][c][j];
+    xo2 = xo2 + oa * dx[14 - b][c][j];
+    ye1 = ye1 + eb * sy[a - 1][c][j];
+    yo1 = yo1 + ob * dy[a - 1][c][j];
+    ye2 = ye2 + eb * sy[14 - a][c][j];
+    yo2 = yo2 + ob * dy[14 - a][c][j];
+  }
   const double* ql = q + (long long)leaf * 256;
-  for (int e = threadIdx.x; e < NI * RCH; e += blockDim.x) {
-    int r = e / RCH, j = e % RCH;
-    if (j >= nj) continue;
-    int a = r / 14 + 1, b = r % 14 + 1;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = 0; c < 16; ++c) {  // a, b in 1..14: the lines through (a, b) contain no corner
-      acc = acc + D2[a][c] * u[lidx(c, b)][j];
-      acc = acc + D2[b][c] * u[lidx(a, c)][j];
-    }
-    acc = acc + (k * k * (1.0 - ql[a * 16 + b])) * u[r][j];
+  const double kk = k * k;
+  // (A, B, x part, y part)
+  const int An[4] = {a, 15 - a, a, 15 - a}, Bn[4] = {b, b, 15 - b, 15 - b};
+  const double2 xp[4] = {xe1 + xo1, xe1 - xo1, xe2 + xo2, xe2 - xo2};
+  const double2 yp[4] = {ye1 + yo1, ye2 + yo2, ye1 - yo1, ye2 - yo2};
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const int A = An[n], B = Bn[n], r = (A - 1) * 14 + (B - 1);
+    const double2 acc = xp[n] + yp[n] + (kk * (1.0 - ql[A * 16 + B])) * u[r][j];
     RP[((long long)leaf * NL + r) * nrhs + j0 + j] = make_float2((float)(-acc.x), (float)(-acc.y));
   }
 }
@@ -425,7 +474,15 @@ void convert_f2d_add(cudaStream_t s, const float2* a, double2* b, long long n) {
 void residual_pde(cudaStream_t s, const double2* X, const double* q, const double* D1, int nleaf, double k, double h,
                   int nrhs, float2* RP) {
   dim3 g(nleaf, (nrhs + RCH - 1) / RCH);
-  k_res_pde<<<g, 256, 0, s>>>(X, q, D1, k, h, nrhs, RP);
+  constexpr int bytes = (NL + 4 * 14 * 8) * RCH * (int)sizeof(double2);
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    cudaFuncSetAttribute(k_res_pde, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  k_res_pde<<<g, RP_THREADS, bytes, s>>>(X, q, D1, k, h, nrhs, RP);
   HS_COUNT_LAUNCH();
 }
 

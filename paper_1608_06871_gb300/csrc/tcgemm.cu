@@ -1,363 +1,14 @@
-// Complex FP32 GEMM on the 5th-generation tensor cores (tcgen05, TMEM).
-//
-// C = alpha A B + beta C for complex FP32 matrices (row-major, interleaved),
-// used for the dense contractions of the mixed-precision solver (merge
-// products, the coupled root system, the downward sweep).  FP32 accuracy is
-// kept with the 3xTF32 split: every operand x = hi + lo with hi = tf32(x),
-// lo = tf32(x - hi), and the product accumulates hi*hi + hi*lo + lo*hi in FP32
-// in tensor memory.
-//
-// The complex product is a real product with twice the K and N:
-//   A' = A as floats (m x 2k: re, im interleaved along k)
-//   B' (2n rows x 2k, K-major): row j < n holds (re B[l][j], -im B[l][j]) at k' = 2l, 2l+1,
-//                               row n + j holds (im B[l][j],  re B[l][j])
-//   D' = A' B'^T = [Re C | Im C].
-// Tile: 128 complex rows x 64 complex columns (D' is 128 x 128 FP32 in TMEM),
-// K chunks of 8 complex (16 real) staged by all 128 threads into shared
-// memory in the canonical K-major layout without swizzle (core matrices of 8
-// rows x 16 bytes), two stages of 32 KB (three CTAs per SM), with the next
-// chunk prefetched into registers while the tensor cores work on the current
-// one.  One thread issues the MMAs (M = 128, N = 128, K = 8) and commits them
-// to an mbarrier.  Shapes with too few tiles to fill the chip split k across
-// a thread-block cluster.
-#include <algorithm>
-#include <cstdint>
-
-#include <cooperative_groups.h>
-
+// Status flags of the tensor-core kernels.  Every tcgen05 kernel bounds its
+// mbarrier waits; one that gives up sets its translation unit's device flag
+// (the split-TF32 product's in tc32.cu, the emulated-FP64 one's in ozaki.cu),
+// and the library reads and clears them after the launches of an API call
+// (HS_ETIMEOUT).  The flag defined here is the one a test raises from the host.
 #include "linalg.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace hs {
 
-// Set to 1 by a tensor-core GEMM whose bounded mbarrier wait gave up.
+// Raised from the host by the failure-injection hook (hs_raise_tc_timeout).
 __device__ int g_tc_timeout = 0;
-
-namespace {
-
-constexpr int TM = 128;         // complex rows per tile
-constexpr int TN = 64;          // complex columns per tile
-constexpr int TKC = 8;          // complex k per chunk
-constexpr int TK = 2 * TKC;     // real k per chunk (16)
-constexpr int NR = 2 * TN;      // real output columns (128)
-constexpr int TC_THREADS = 128;
-constexpr int OP_BYTES = TM * TK * 4;            // one operand copy: 128 rows x 16 floats = 8 KB
-constexpr int STAGE_BYTES = 4 * OP_BYTES;        // A hi, A lo, B' hi, B' lo
-constexpr int RED_LD = TN + 1;                   // padded row of the split-k partial tile (float2)
-constexpr int TC_SMEM = 2 * STAGE_BYTES + 2048;  // two stages (>= the partial tile) + alignment slack
-static_assert(TM * RED_LD * 8 <= 2 * STAGE_BYTES + 1024, "partial tile must fit the stage buffers");
-constexpr uint32_t LBO = (TM / 8) * 128;         // bytes between core matrices along k (16 row groups)
-constexpr uint32_t SBO = 128;                    // bytes between 8-row groups
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
-constexpr uint32_t IDESC =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-constexpr long long WAIT_LIMIT = 1LL << 26;      // bounded mbarrier waits
-constexpr int EP_LD = 17;                        // padded row of the epilogue transpose (float2)
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-__device__ __forceinline__ float tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// float offset of element (row r, real k q) inside one operand copy
-__device__ __forceinline__ int core_off(int r, int q) { return ((q >> 2) * (TM / 8) + (r >> 3)) * 32 + (r & 7) * 4 + (q & 3); }
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(ta));
-}
-
-// blockIdx.z = batch * splits + split; with splits > 1 the kernel runs in
-// clusters of `splits` CTAs along z, each covering a range of whole chunks of
-// k, and the partial tiles are summed in split order through distributed
-// shared memory (deterministic, no atomics).
-__global__ void __launch_bounds__(TC_THREADS, 3)
-    k_cgemm_tc(int m, int n, int k, float2 alpha, const float2* __restrict__ A, int lda, long long sA,
-               const float2* __restrict__ B, int ldb, long long sB, float2 beta, float2* __restrict__ C, int ldc,
-               long long sC, int splits) {
-  extern __shared__ unsigned char smraw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint32_t tslot;
-  __shared__ __align__(8) uint64_t mbar[3];  // [0], [1]: per stage; [2]: every MMA of the CTA done
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
-  A += b * sA;
-  B += b * sB;
-  C += b * sC;
-  const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
-  const int nch_all = (k + TKC - 1) / TKC;
-  const int per = (nch_all + splits - 1) / splits;
-  const int ch0 = sp * per, ch1 = min(nch_all, ch0 + per);
-  const int nchunk = max(0, ch1 - ch0);
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(NR));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[1])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[2])), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tslot;
-
-  // register prefetch: A chunk 128 x 8 complex = 512 float4 (4 per thread),
-  // B chunk 8 x 64 complex as 256 pairs of k-adjacent elements (2 per
-  // thread).  Lane bits 0..2 select the row inside an 8-row core matrix, so
-  // the shared-memory stores of each 8-lane phase fill one contiguous
-  // 128-byte core matrix (no bank conflicts); the global loads of a warp still
-  // use whole 32-byte sectors.
-  float4 ra[4];
-  float2 rb0[2], rb1[2];
-  auto prefetch = [&](int ch) {
-    const int kb = ch * TKC;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int q = tid + TC_THREADS * i;                     // 0..511
-      const int r = (q >> 5) * 8 + (q & 7), c2 = ((q >> 3) & 3) * 2;  // row, complex column pair
-      const int gr = row0 + r, gk = kb + c2;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gr < m) {
-        const float2* p = A + (long long)gr * lda + gk;
-        if (gk < k) { v.x = p[0].x; v.y = p[0].y; }
-        if (gk + 1 < k) { v.z = p[1].x; v.w = p[1].y; }
-      }
-      ra[i] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int q = tid + TC_THREADS * i;                     // 0..255
-      const int j = (q >> 5) * 8 + (q & 7), lp = (q >> 3) & 3;  // column, k pair (l = 2 lp, 2 lp + 1)
-      const int gk = kb + 2 * lp, gc = col0 + j;
-      float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-      if (gc < n) {
-        if (gk < k) v0 = B[(long long)gk * ldb + gc];
-        if (gk + 1 < k) v1 = B[(long long)(gk + 1) * ldb + gc];
-      }
-      rb0[i] = v0;
-      rb1[i] = v1;
-    }
-  };
-  auto split_store = [&](float* hi, float* lo, int off, float4 v) {
-    const float4 h = make_float4(tf32(v.x), tf32(v.y), tf32(v.z), tf32(v.w));
-    *reinterpret_cast<float4*>(hi + off) = h;
-    *reinterpret_cast<float4*>(lo + off) = make_float4(tf32(v.x - h.x), tf32(v.y - h.y), tf32(v.z - h.z), tf32(v.w - h.w));
-  };
-  auto stage_store = [&](int st) {
-    float* Ahi = reinterpret_cast<float*>(sm + st * STAGE_BYTES);
-    float* Alo = Ahi + OP_BYTES / 4;
-    float* Bhi = Alo + OP_BYTES / 4;
-    float* Blo = Bhi + OP_BYTES / 4;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int q = tid + TC_THREADS * i;
-      const int r = (q >> 5) * 8 + (q & 7), c4 = (q >> 3) & 3;  // real k' = 4 c4 .. 4 c4 + 3
-      split_store(Ahi, Alo, core_off(r, 4 * c4), ra[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int q = tid + TC_THREADS * i;
-      const int j = (q >> 5) * 8 + (q & 7), lp = (q >> 3) & 3;
-      const float2 a = rb0[i], b = rb1[i];  // B[2lp][j], B[2lp+1][j]
-      // row j: (re, -im) at k' = 2l, 2l+1; row TN + j: (im, re)
-      split_store(Bhi, Blo, core_off(j, 4 * lp), make_float4(a.x, -a.y, b.x, -b.y));
-      split_store(Bhi, Blo, core_off(TN + j, 4 * lp), make_float4(a.y, a.x, b.y, b.x));
-    }
-  };
-
-  bool ok = true;
-  if (nchunk > 0) prefetch(ch0);
-  for (int c = 0; c < nchunk; ++c) {
-    const int st = c & 1;
-    if (c >= 2) ok = ok && mbar_wait(su32(&mbar[st]), ((c >> 1) - 1) & 1);  // MMAs of chunk c-2 done
-    stage_store(st);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      const uint32_t base = su32(sm + st * STAGE_BYTES);
-      const uint32_t ahi = base, alo = base + OP_BYTES, bhi = base + 2 * OP_BYTES, blo = base + 3 * OP_BYTES;
-#pragma unroll
-      for (int ks = 0; ks < TK / 8; ++ks) {
-        const uint32_t koff = ks * 2 * LBO;  // two core matrices of k per MMA
-        const uint64_t dA[3] = {sdesc(ahi + koff), sdesc(ahi + koff), sdesc(alo + koff)};
-        const uint64_t dB[3] = {sdesc(bhi + koff), sdesc(blo + koff), sdesc(bhi + koff)};
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const uint32_t acc = (c > 0 || ks > 0 || t > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-              "l"(dA[t]), "l"(dB[t]), "r"(IDESC), "r"(acc));
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          su32(&mbar[st])));
-    }
-    if (c + 1 < nchunk) prefetch(ch0 + c + 1);
-  }
-  // one more commit by the issuing thread tracks every MMA it issued: its
-  // arrival means the tensor cores no longer touch TMEM or the stages
-  if (tid == 0 && nchunk > 0)
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        su32(&mbar[2])));
-  const bool drained = nchunk == 0 || mbar_wait(su32(&mbar[2]), 0);
-  ok = ok && drained;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  // all threads agree on the outcome before the warp-collective TMEM loads
-  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  if (!all_ok && tid == 0) atomicExch(&g_tc_timeout, 1);
-  const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
-  if (splits == 1) {
-    if (all_ok) {
-      // epilogue: warp w owns TMEM lanes (= rows) 32 w .. 32 w + 31; each 32 x 16
-      // block goes through shared memory (stage 0, free now) so that the global
-      // writes run along rows
-      float2* tr = reinterpret_cast<float2*>(sm) + warp * 32 * EP_LD;
-      for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t re[16], im[16];
-        tmem_ld16(ta + c0, re);
-        tmem_ld16(ta + TN + c0, im);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          tr[lane * EP_LD + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
-        __syncwarp();
-        const int cj = lane & 15, c = col0 + c0 + cj;
-#pragma unroll 4
-        for (int rr = lane >> 4; rr < 32; rr += 2) {
-          const int r = row0 + 32 * warp + rr;
-          if (r < m && c < n) {
-            const float2 v = alpha * tr[rr * EP_LD + cj];
-            float2* pc = C + (long long)r * ldc + c;
-            *pc = (beta.x == 0.f && beta.y == 0.f) ? v : v + beta * (*pc);
-          }
-        }
-        __syncwarp();
-      }
-    }
-  } else {
-    // split k: the whole partial tile goes to shared memory (both stages,
-    // free now), then the cluster's CTAs sum the partials in split order
-    // through distributed shared memory, rank r writing its share of the rows
-    float2* red = reinterpret_cast<float2*>(sm);
-    if (all_ok) {
-      for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t re[16], im[16];
-        tmem_ld16(ta + c0, re);
-        tmem_ld16(ta + TN + c0, im);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          red[(32 * warp + lane) * RED_LD + c0 + j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
-      }
-    }
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-    const int rows_per = (TM + splits - 1) / splits;
-    const int rb = sp * rows_per, re_ = min(TM, rb + rows_per);
-    for (int e = rb * TN + tid; e < re_ * TN; e += TC_THREADS) {
-      const int rl = e / TN, cl_ = e % TN;
-      float2 sum = make_float2(0.f, 0.f);
-      for (int q = 0; q < splits; ++q) sum = sum + cl.map_shared_rank(red, q)[rl * RED_LD + cl_];
-      const int r = row0 + rl, c = col0 + cl_;
-      if (all_ok && r < m && c < n) {
-        const float2 v = alpha * sum;
-        float2* pc = C + (long long)r * ldc + c;
-        *pc = (beta.x == 0.f && beta.y == 0.f) ? v : v + beta * (*pc);
-      }
-    }
-    cl.sync();  // keep this CTA's partial tile alive until every rank has read it
-  }
-  // Timed out: before the TMEM columns are released (and the shared-memory
-  // stages with the CTA), wait once more, again bounded, for the final commit,
-  // so that no MMA issued here can still be writing them.  If that wait gives
-  // up too the columns are released regardless; the flag already makes the
-  // host report HS_ETIMEOUT, and C is unspecified.
-  if (!all_ok && !drained) mbar_wait(su32(&mbar[2]), 0);
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NR));
-}
-
-
-}  // namespace
-
-bool g_tc_enabled = true;  // process-wide switch (hs_set_tensor_cores)
-
-bool cgemm_tc_eligible(int opA, int opB, int m, int n, int k, int batch) {
-  return g_tc_enabled && opA == OP_N && opB == OP_N && m >= TM && n >= TN && k >= 8 * TKC && batch <= 65535;
-}
-
-void cgemm_tc(cudaStream_t s, int m, int n, int k, float2 alpha, const float2* A, int lda, long long sA,
-              const float2* B, int ldb, long long sB, float2 beta, float2* C, int ldc, long long sC, int batch) {
-  static bool attr_set[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (dev >= 0 && dev < 64) attr_set[dev] = true;
-  }
-  // split k when the tiles alone leave SMs idle (3 CTAs fit on each of 152 SMs)
-  constexpr long long kFill = 3 * 152;
-  const long long tiles = (long long)((m + TM - 1) / TM) * ((n + TN - 1) / TN) * batch;
-  const int nch = (k + TKC - 1) / TKC;
-  int splits = 1;
-  if (tiles < kFill && nch >= 16) {
-    splits = (int)std::min<long long>((kFill + tiles - 1) / tiles, nch / 8);
-    splits = std::max(1, std::min(splits, 8));  // portable cluster size
-    if ((long long)batch * splits > 65535) splits = 1;
-  }
-  dim3 grid((n + TN - 1) / TN, (m + TM - 1) / TM, batch * splits);
-  if (splits == 1) {
-    k_cgemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, 1);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = TC_SMEM;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 1;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = splits;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_cgemm_tc, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits);
-  }
-  HS_COUNT_LAUNCH();
-}
 
 // Set the current device's timeout flag from the host (test hook: the next
 // call that checks it reports HS_ETIMEOUT; no kernel waits on anything).
@@ -367,7 +18,7 @@ cudaError_t tc_raise_timeout_flag() {
 }
 
 bool tc_timed_out(cudaStream_t s) {
-  const bool oz = oz_timed_out(s);
+  const bool others = oz_timed_out(s) || t32_timed_out(s);
   int v = 0, z = 0;
   cudaStreamSynchronize(s);
   cudaMemcpyFromSymbolAsync(&v, g_tc_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
@@ -376,7 +27,7 @@ bool tc_timed_out(cudaStream_t s) {
     cudaMemcpyToSymbolAsync(g_tc_timeout, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);
   }
-  return v != 0 || oz;
+  return v != 0 || others;
 }
 
 }  // namespace hs

@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=["gn_k40", "jacobian_16x16_s64", "lsqr_k40", "lsqr_mixed_k40",
                                                       "tc_shapes", "tc_2048", "jacobian_k40", "emulated_gemm_shapes",
-                                                      "lu_1792"],
+                                                      "lu_1792", "mixed_k20"],
                     help="run one named workload once, untimed, and exit (a target for profilers)")
     ap.add_argument("--table2", type=float, default=0.0,
                     help="also run the paper's reconstruction plan (Sec. 4: k = 1:0.25:K, LSQR at 1e-3, "
@@ -453,13 +453,14 @@ def run_hs(args, world, rank, local):
             tc_ms, tc_flops, tc_n = main["tc"]
             ach = tc_flops / (tc_ms * 1e-3) / 1e12
             line["tensor_gemm"]["in_step"] = {"achieved": ach, "launches": tc_n, "kernel_ms_per_step": tc_ms,
-                                              "issued_tflops": 6 * ach}
+                                              "issued_tflops": 6 * ach,
+                                              "frac_issued": 6 * ach / line["tensor_gemm"]["peak"]}
         else:
             line["tensor_gemm"]["in_step"] = None
-            line["tensor_gemm"]["in_step_note"] = (
-                "the forward step keeps its FP32 products on SIMT FP32 (hs_set_tensor_cores default 1: only "
-                "the FP32 Jacobian opts in); with every product tuned (mode 3) the k = 70 solve needs a fourth "
-                "refinement pass")
+        line["tensor_gemm"]["in_step_note"] = (
+            "in the step the per-shape choice keeps the tensor cores only where they take less than half the "
+            "SIMT time (the root product, the large trailing updates): their FP32 accumulation is coarser than "
+            "SIMT FMA chains, and with a looser choice the k = 70 solve needs a fourth refinement pass")
         if secondary:
             line["secondary"] = secondary
         if cpu:
@@ -1116,6 +1117,19 @@ def run_case(name):
             torch.cuda.synchronize()
             print({"shape": [b_, m, n, k], "emulated_tflops": 2.0 * b_ * m * n * k * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12},
                   flush=True)
+        return
+    if name == "mixed_k20":
+        # two mixed-precision build + forward calls at the k = 20 gradient workload (16 x 16 leaves,
+        # 64 incidences, 128 receivers): a small target for profilers of the refinement kernels
+        w = synth.WORKLOADS["grad_k20"]
+        c = synth.smooth_random_coeffs(w.S, seed=2, qmax=0.3)
+        s = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED)
+        al, th = synth.directions(w.M), synth.receivers(w.P)
+        for _ in range(2):
+            s.build(c, w.k)
+            s.solve(al, th)
+        s.close()
+        print("mixed_k20 done", flush=True)
         return
     if name == "lu_1792":
         # batched LU solves of complex64 systems of order 1792 (the root of the k = 40 tree)

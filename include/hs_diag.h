@@ -68,10 +68,8 @@ int hs_set_graphs(int enable);
 
 /* FP32 products (complex x complex, real x complex, real x real; untransposed
  * operands) on the tensor cores by the split-TF32 product: enable == 0 never;
- * 1 (the default) only where the library opts in (the FP32 Jacobian's
- * contraction), with a per-shape choice there (hs_set_autotune); 2 every such
- * product; 3 a per-shape choice for every such product, the solver's
- * factorisation and refinement included.  Process-wide; takes effect at the
+ * 1 (the default) per shape, where measured clearly faster (hs_set_autotune,
+ * hs_set_tc_margin); 2 every such product.  Process-wide; takes effect at the
  * next launch.  Errors: HS_EINVAL for other values. */
 int hs_set_tensor_cores(int enable);
 
@@ -127,6 +125,11 @@ int hs_gemm32(int mode, int m, int n, int k, const void* A, const void* B, void*
  * stream capture, and keeps the faster; 0 uses a fixed size rule.  Errors:
  * none. */
 int hs_set_autotune(int enable);
+
+/* Where the dispatch measures both products, the tensor cores are kept when
+ * they take less than `margin` (0 < margin <= 1; default 0.5) of the SIMT
+ * product's time.  Applies to shapes measured afterwards.  Errors: HS_EINVAL. */
+int hs_set_tc_margin(double margin);
 
 /* C = op(A) op(B) (+ C when accumulate != 0): complex128 (interleaved re,
  * im), row-major, op(A) m x k, op(B) k x n, C m x n; op = transpose when

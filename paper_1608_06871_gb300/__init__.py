@@ -75,6 +75,7 @@ _SIGS = {
     "hs_build_phase_ms": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "hs_set_tensor_cores": (_I, [_I]),
     "hs_set_autotune": (_I, [_I]),
+    "hs_set_tc_margin": (_I, [ctypes.c_double]),
     "hs_gemm32": (_I, [_I, _I, _I, _I, _P, _P, _P, _I, _I, _P, _P]),
     "hs_fail_next_allocs": (_I, [_I]),
     "hs_raise_tc_timeout": (_I, [_I]),
@@ -322,13 +323,17 @@ def hs_raise_tc_timeout(device: int = 0):
 
 
 def hs_set_tensor_cores(enable):
-    """0 / False: SIMT FP32 products; 1 / True: tensor cores where the library opts in, per-shape
-    choice there; 2: tensor cores for every supported product; 3: per-shape choice everywhere."""
+    """0 / False: SIMT FP32 products; 1 / True: per-shape choice (tensor cores where measured
+    clearly faster); 2: tensor cores for every supported product."""
     _check(None, lib().hs_set_tensor_cores(int(enable)))
 
 
 def hs_set_autotune(enable: bool):
     _check(None, lib().hs_set_autotune(1 if enable else 0))
+
+
+def hs_set_tc_margin(margin: float):
+    _check(None, lib().hs_set_tc_margin(float(margin)))
 
 
 def hs_zgemm(A, B, C, transA: bool = False, transB: bool = False, accumulate: bool = False, stream: int = 0):

@@ -170,13 +170,19 @@ int hs_raise_tc_timeout(int device) {
 }
 
 int hs_set_tensor_cores(int enable) {
-  if (enable < 0 || enable > 3) return HS_EINVAL;
+  if (enable < 0 || enable > 2) return HS_EINVAL;
   hs::g_t32_mode = enable;
   return HS_OK;
 }
 
 int hs_set_autotune(int enable) {
   hs::g_autotune = enable != 0;
+  return HS_OK;
+}
+
+int hs_set_tc_margin(double margin) {
+  if (!(margin > 0.0 && margin <= 1.0)) return HS_EINVAL;
+  hs::g_tc_margin = (float)margin;
   return HS_OK;
 }
 

@@ -251,7 +251,6 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
   const long long nt = (long long)nX * std::max(S1, S2);
   k_sine_tables32<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(sx, sy, nX, S1, S2, sxc, sy32);
   HS_COUNT_LAUNCH();
-  TcScope tc;  // the x-projection may run on the tensor cores (one-shot FP32 matrix)
   for (long long c0 = 0; c0 < MP; c0 += C) {
     const int nc = (int)std::min<long long>(C, MP - c0);
     k_khatri_rao32<<<dim3((unsigned)((plane + 255) / 256), (nc + KR_PAIRS - 1) / KR_PAIRS), 256, 0, s>>>(

@@ -432,18 +432,18 @@ struct TuneKey {
     return std::tie(mode, m, n, k, batch, bsh) < std::tie(o.mode, o.m, o.n, o.k, o.batch, o.bsh);
   }
 };
-// The tensor-core product carries the split's rounding (2^-22 of each operand
-// against FP32's 2^-24), which slows the refinement of the mixed solver a
-// little; it is taken only where it is clearly faster.
-constexpr float kTcMargin = 0.7f;
+
 std::mutex g_tune_mu;
 std::map<TuneKey, bool> g_tune;
 
 }  // namespace
 
 bool g_autotune = true;             // hs_set_autotune
-int g_t32_mode = 1;                 // hs_set_tensor_cores: 0 off, 1 opted-in scopes, 2 forced, 3 every product tuned
-thread_local int g_t32_scope = 0;   // > 0 inside a TcScope (products that opt in)
+// The tensor-core product's accumulation is coarser than SIMT FMA chains, which
+// slows the refinement of the mixed solver; it is kept only where it takes
+// less than half the SIMT time (hs_set_tc_margin).
+float g_tc_margin = 0.5f;
+int g_t32_mode = 1;                 // hs_set_tensor_cores: 0 off, 1 per-shape choice, 2 forced
 thread_local bool g_prof_suspended = false;
 thread_local int g_last_gemm_tc = 0;
 
@@ -455,8 +455,7 @@ void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const
   constexpr int mode = t32_mode<TA, TB, TC>::v;
   if constexpr (mode >= 0) {
     const bool force = g_t32_mode == 2;
-    const bool eligible = force || g_t32_mode == 3 || (g_t32_mode == 1 && g_t32_scope > 0);
-    if (opA == OP_N && opB == OP_N && k > 0 && eligible) {
+    if (opA == OP_N && opB == OP_N && k > 0 && g_t32_mode != 0) {
       auto run_tc = [&](TC* Cd) {
         return t32_gemm(s, mode, m, n, k, as_f2(alpha), reinterpret_cast<const float*>(A), fl<TA>() * lda,
                         fl<TA>() * sA, reinterpret_cast<const float*>(B), fl<TB>() * ldb, fl<TB>() * sB, as_f2(beta),
@@ -508,7 +507,7 @@ void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const
           cudaFree(tmp);
           g_prof_suspended = false;
           g_launch_counter = counter;
-          use = tc_ok && best_tc < kTcMargin * best_simt;
+          use = tc_ok && best_tc < g_tc_margin * best_simt;
           std::lock_guard<std::mutex> lock(g_tune_mu);
           g_tune[key] = use;
         } else {

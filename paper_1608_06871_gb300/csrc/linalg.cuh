@@ -61,19 +61,11 @@ bool t32_timed_out(cudaStream_t s);
 // keeps the faster (g_autotune; off: a fixed size rule); g_last_gemm_tc is 1
 // when the calling thread's last gemm() ran on the tensor cores.
 extern bool g_autotune;
+extern float g_tc_margin;  // the tensor cores are kept where they take < g_tc_margin of the SIMT time
 // Tensor-core use for FP32 products (hs_set_tensor_cores): 0 never; 1 (the
-// default) inside TcScope regions only, per-shape choice there; 2 every
-// supported product; 3 per-shape choice for every product.  The solver's
-// factorisation and refinement products stay on SIMT FP32 by default: the
-// tensor cores' FP32 accumulation is less accurate than the SIMT FMA chains,
-// and at k = 70 that costs the refinement a fourth pass, more than the faster
-// products save.  The Jacobian's FP32 contraction opts in.
+// default) where the per-shape measurement finds them clearly faster; 2 every
+// supported product.
 extern int g_t32_mode;
-extern thread_local int g_t32_scope;
-struct TcScope {
-  TcScope() { ++g_t32_scope; }
-  ~TcScope() { --g_t32_scope; }
-};
 extern thread_local bool g_prof_suspended;
 extern thread_local int g_last_gemm_tc;
 // Synchronises s, then reads and clears this device's flags that a bounded

@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=["gn_k40", "jacobian_16x16_s64", "lsqr_k40", "lsqr_mixed_k40",
                                                       "tc_shapes", "tc_2048", "jacobian_k40", "emulated_gemm_shapes",
-                                                      "lu_1792", "mixed_k20"],
+                                                      "lu_1792", "mixed_k20", "paper_gn_k70"],
                     help="run one named workload once, untimed, and exit (a target for profilers)")
     ap.add_argument("--table2", type=float, default=0.0,
                     help="also run the paper's reconstruction plan (Sec. 4: k = 1:0.25:K, LSQR at 1e-3, "
@@ -1117,6 +1117,10 @@ def run_case(name):
             torch.cuda.synchronize()
             print({"shape": [b_, m, n, k], "emulated_tflops": 2.0 * b_ * m * n * k * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12},
                   flush=True)
+        return
+    if name == "paper_gn_k70":
+        # the paper-scale Gauss-Newton step (k = 70, 19,600 unknowns) alone, timed, as JSON
+        print(json.dumps(paper_scale_gn(hs, torch, 0)), flush=True)
         return
     if name == "mixed_k20":
         # two mixed-precision build + forward calls at the k = 20 gradient workload (16 x 16 leaves,

@@ -168,16 +168,17 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
  * once in FP64 by the emulated FP64 contraction on the tensor cores and every
  * iteration reads it twice (with the emulation switched off, J and J^H are
  * applied from the fields by two FP64 grid contractions per iteration);
- * HS_MIXED -- J is formed once in complex FP32 on the tensor cores (split
- * TF32) from the fields and every iteration reads it twice with FP64 sums (for
- * loose tolerances such as the paper's 1e-3).  Either way J v
+ * HS_MIXED -- J is formed once in complex FP32 (the tensor cores take its
+ * x-projection where measured faster) from a single FP32 adjoint solve and
+ * every iteration reads it twice with FP64 sums (for loose tolerances such as
+ * the paper's 1e-3).  Either way J v
  * and J^H u stay exact transposes of one matrix.  The iteration's vectors live on the
  * host.  Stops when the relative residual or the relative normal-equations
  * residual (LSQR's own estimates) is at most tol, or after max_iter
  * iterations; *iters_out (optional) receives the count.  Otherwise as
  * hs_gn_step (c_inout updated, resid_norm_out = ||r||_2 before the step).
- * On an HS_MIXED context the residual, the forward fields and the adjoint
- * fields come from the refined solves (FP64 accurate), so
+ * On an HS_MIXED context the residual, the forward fields and (for products
+ * HS_FP64) the adjoint fields come from the refined solves (FP64 accurate), so
  * with products HS_FP64 the step is the FP64 context's to the refinement
  * tolerance; with products HS_MIXED it carries the FP32 rounding of the
  * tensor-core J on either kind of context.  The explicit J needs M P S1 S2

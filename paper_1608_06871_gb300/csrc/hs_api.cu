@@ -1981,9 +1981,9 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
-  if (mixed) {  // refined far field, forward and adjoint fields (J32 then carries only its own rounding)
+  if (mixed) {  // refined far field and forward fields; adjoint refined unless J is FP32 anyway
     Arena sub = a;
-    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub, true));
+    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub, !p32));
   } else {  // forward far field F(c)
     Arena sub = a;
     double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);

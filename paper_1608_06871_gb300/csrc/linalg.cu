@@ -327,6 +327,108 @@ void trsm_diag(cudaStream_t s, const E* A, int lda, long long sA, int i0, int nb
   HS_COUNT_LAUNCH();
 }
 
+// The solve with a whole diagonal block of up to NBB rows in one launch:
+// rows [i0, i0 + nbs) of B (column block of TB_CW<E> columns per CTA, held in
+// shared memory) against the block's unit lower (mode 0, top down) or upper
+// triangle (mode 1, bottom up).  Per NB-row sub-block: one warp per column
+// solves the diagonal block with shuffles, then every thread updates the
+// block's remaining rows from the solved ones (the off-diagonal entries read
+// through L1).  Replaces the NB-blocked sequence of triangular solves and
+// small products (and their trips through global memory) inside the block.
+template <typename E> struct tb_cw { static constexpr int v = sizeof(E) == 16 ? 8 : 16; };
+template <typename E>
+__global__ void __launch_bounds__(32 * tb_cw<E>::v) k_trsm_blk(const E* __restrict__ A, int lda, long long sA, int i0,
+                                                               int nbs, int mode, E* __restrict__ B, int ldb,
+                                                               long long sB, int nrhs) {
+  constexpr int CW = tb_cw<E>::v, NT = 32 * CW;
+  __shared__ E Bs[NBB][CW + 1];
+  __shared__ E Ld[NB][NB + 1];
+  const int b = blockIdx.y, c0 = blockIdx.x * CW, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  A += b * sA;
+  B += b * sB;
+  for (int e = tid; e < nbs * CW; e += NT) {
+    const int r = e / CW, c = e % CW;
+    Bs[r][c] = c0 + c < nrhs ? B[(long long)(i0 + r) * ldb + c0 + c] : el<E>::zero();
+  }
+  const int nsub = (nbs + NB - 1) / NB;
+  for (int q = 0; q < nsub; ++q) {
+    const int sub = mode == 0 ? q : nsub - 1 - q;
+    const int r0 = sub * NB, nb = min(NB, nbs - r0);
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int r = e / nb, c = e % nb;
+      Ld[r][c] = A[(long long)(i0 + r0 + r) * lda + i0 + r0 + c];
+    }
+    __syncthreads();  // (also orders the previous sub-block's updates of Bs)
+    if (warp < CW) {
+      E x = lane < nb ? Bs[r0 + lane][warp] : el<E>::zero();
+      if (mode == 0) {
+        for (int t = 0; t < nb; ++t) {
+          const E xt = shfl(x, t);
+          if (lane > t && lane < nb) x = fmsc(x, Ld[lane][t], xt);
+        }
+      } else {
+        for (int t = nb - 1; t >= 0; --t) {
+          if (lane == t) x = el<E>::div(x, Ld[t][t]);
+          const E xt = shfl(x, t);
+          if (lane < t) x = fmsc(x, Ld[lane][t], xt);
+        }
+      }
+      if (lane < nb) Bs[r0 + lane][warp] = x;
+    }
+    __syncthreads();
+    // the block's rows still to solve: below (mode 0) or above (mode 1) the sub-block
+    const int ra = mode == 0 ? r0 + nb : 0, rb = mode == 0 ? nbs : r0;
+    for (int e = tid; e < (rb - ra) * CW; e += NT) {
+      const int r = ra + e / CW, c = e % CW;
+      const E* arow = A + (long long)(i0 + r) * lda + i0 + r0;
+      E acc = Bs[r][c];
+      for (int t = 0; t < nb; ++t) acc = fmsc(acc, arow[t], Bs[r0 + t][c]);
+      Bs[r][c] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nbs * CW; e += NT) {
+    const int r = e / CW, c = e % CW;
+    if (c0 + c < nrhs) B[(long long)(i0 + r) * ldb + c0 + c] = Bs[r][c];
+  }
+}
+
+// Solve with the diagonal block rows [i0, i0 + nbs) of A: one launch of
+// k_trsm_blk when there are few columns overall (the root system and the top
+// merges, where the NB-blocked sequence is launch- and latency-bound); with
+// many (batched leaf and merge systems) the NB-blocked sequence of
+// one-thread-per-column solves and products keeps more threads busy.
+template <typename E>
+void trsm_blk(cudaStream_t s, const E* A, int lda, long long sA, int i0, int nbs, int mode, E* B, int ldb,
+              long long sB, int nrhs, int batch) {
+  constexpr int CW = tb_cw<E>::v;
+  if ((long long)nrhs * batch < 8192) {
+    dim3 g((nrhs + CW - 1) / CW, batch);
+    k_trsm_blk<E><<<g, 32 * CW, 0, s>>>(A, lda, sA, i0, nbs, mode, B, ldb, sB, nrhs);
+    HS_COUNT_LAUNCH();
+    return;
+  }
+  const E m1 = -el<E>::one(), one = el<E>::one();
+  const int I1 = i0 + nbs;
+  if (mode == 0) {
+    for (int j = i0; j < I1; j += NB) {
+      const int nb = std::min(NB, I1 - j);
+      trsm_diag<E>(s, A, lda, sA, j, nb, 0, B, ldb, sB, nrhs, batch);
+      if (I1 - j - nb > 0)
+        gemm<E, E, E>(s, OP_N, OP_N, I1 - j - nb, nrhs, nb, m1, A + (long long)(j + nb) * lda + j, lda, sA,
+                      B + (long long)j * ldb, ldb, sB, one, B + (long long)(j + nb) * ldb, ldb, sB, batch);
+    }
+  } else {
+    for (int j = i0 + ((nbs - 1) / NB) * NB; j >= i0; j -= NB) {
+      const int nb = std::min(NB, I1 - j);
+      trsm_diag<E>(s, A, lda, sA, j, nb, 1, B, ldb, sB, nrhs, batch);
+      if (j > i0)
+        gemm<E, E, E>(s, OP_N, OP_N, j - i0, nrhs, nb, m1, A + (long long)i0 * lda + j, lda, sA,
+                      B + (long long)j * ldb, ldb, sB, one, B + (long long)i0 * ldb, ldb, sB, batch);
+    }
+  }
+}
+
 template <typename E>
 __global__ void k_swaps(const int* piv, long long sP, int n, int reverse, E* B, int ldb, long long sB, int nrhs) {
   const int b = blockIdx.y;
@@ -412,11 +514,15 @@ inline float2 as_f2(float2 x) { return x; }
 inline float2 as_f2(float x) { return make_float2(x, 0.f); }
 template <typename T> constexpr long long fl() { return sizeof(T) / sizeof(float); }  // floats per element
 
-// Default choice without a measurement: large products only (at least 2^27
-// real multiply-adds, every dimension of the real product >= 128).
-bool t32_default(int mode, int m, int n, int k) {
+// Products worth measuring: every dimension of the real product at least 512.
+// Smaller ones (the batched leaf, merge and sweep products, the short-k
+// trailing updates) never reached the required speed-up over SIMT in the
+// measurements (at most 1.4x) and stay there without a measurement, which
+// keeps a frequency sweep, whose sizes change from step to step, from paying
+// for one per new shape.
+bool t32_candidate(int mode, int m, int n, int k) {
   const long long np = mode ? 2LL * n : n, kp = mode == 2 ? 2LL * k : k;
-  return m >= 128 && np >= 128 && kp >= 128 && (long long)m * np * kp >= (1LL << 27);
+  return m >= 512 && np >= 512 && kp >= 512;
 }
 
 // Per-shape choice between the tensor-core and the SIMT product, measured
@@ -455,13 +561,13 @@ void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const
   constexpr int mode = t32_mode<TA, TB, TC>::v;
   if constexpr (mode >= 0) {
     const bool force = g_t32_mode == 2;
-    if (opA == OP_N && opB == OP_N && k > 0 && g_t32_mode != 0) {
+    if (opA == OP_N && opB == OP_N && k > 0 && g_t32_mode != 0 && (force || t32_candidate(mode, m, n, k))) {
       auto run_tc = [&](TC* Cd) {
         return t32_gemm(s, mode, m, n, k, as_f2(alpha), reinterpret_cast<const float*>(A), fl<TA>() * lda,
                         fl<TA>() * sA, reinterpret_cast<const float*>(B), fl<TB>() * ldb, fl<TB>() * sB, as_f2(beta),
                         Cd, ldc, sC, batch);
       };
-      bool use = force || t32_default(mode, m, n, k);
+      bool use = true;  // forced, or a candidate not yet measured inside a capture
       const TuneKey key{mode, size_class(m), size_class(n), size_class(k), size_class(batch),
                         (sB == 0 && batch > 1) ? 1 : 0};
       cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -545,14 +651,7 @@ void lu_factor(cudaStream_t s, E* A, int lda, long long sA, int n, int* piv, lon
     }
     const int rest = n - J1;
     if (rest > 0) {
-      for (int i0 = J0; i0 < J1; i0 += NB) {  // U12 = L11^-1 A12, blocked
-        const int nb = std::min(NB, J1 - i0);
-        trsm_diag<E>(s, A, lda, sA, i0, nb, 0, A + J1, lda, sA, rest, batch);
-        const int rows_in = J1 - i0 - nb;
-        if (rows_in > 0)
-          gemm<E, E, E>(s, OP_N, OP_N, rows_in, rest, nb, m1, A + (long long)(i0 + nb) * lda + i0, lda, sA,
-                        A + (long long)i0 * lda + J1, lda, sA, one, A + (long long)(i0 + nb) * lda + J1, lda, sA, batch);
-      }
+      trsm_blk<E>(s, A, lda, sA, J0, nbs, 0, A + J1, lda, sA, rest, batch);  // U12 = L11^-1 A12
       gemm<E, E, E>(s, OP_N, OP_N, rest, rest, nbs, m1, A + (long long)J1 * lda + J0, lda, sA,
                     A + (long long)J0 * lda + J1, lda, sA, one, A + (long long)J1 * lda + J1, lda, sA, batch);
     }
@@ -585,17 +684,11 @@ void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int 
   if (trans == OP_N) {
     k_swaps<E><<<gs, 128, 0, s>>>(piv, sP, n, 0, B, ldb, sB, nrhs);
     HS_COUNT_LAUNCH();
-    // blocks of NBB rows (NB-wide triangular solves and updates inside the
-    // block), then one update of the remaining rows with k = NBB
+    // blocks of NBB rows (one launch solves a block's diagonal triangle),
+    // then one update of the remaining rows with k = NBB
     for (int I0 = 0; I0 < n; I0 += NBB) {  // L y = b
       const int I1 = std::min(n, I0 + NBB);
-      for (int i0 = I0; i0 < I1; i0 += NB) {
-        const int nb = std::min(NB, I1 - i0);
-        trsm_diag<E>(s, A, lda, sA, i0, nb, 0, B, ldb, sB, nrhs, batch);
-        if (I1 - i0 - nb > 0)
-          gemm<E, E, E>(s, OP_N, OP_N, I1 - i0 - nb, nrhs, nb, m1, A + (long long)(i0 + nb) * lda + i0, lda, sA,
-                        B + (long long)i0 * ldb, ldb, sB, one, B + (long long)(i0 + nb) * ldb, ldb, sB, batch);
-      }
+      trsm_blk<E>(s, A, lda, sA, I0, I1 - I0, 0, B, ldb, sB, nrhs, batch);
       if (n - I1 > 0)
         gemm<E, E, E>(s, OP_N, OP_N, n - I1, nrhs, I1 - I0, m1, A + (long long)I1 * lda + I0, lda, sA,
                       B + (long long)I0 * ldb, ldb, sB, one, B + (long long)I1 * ldb, ldb, sB, batch);
@@ -603,13 +696,7 @@ void lu_solve(cudaStream_t s, int trans, const E* A, int lda, long long sA, int 
     const int lastB = ((n - 1) / NBB) * NBB;
     for (int I0 = lastB; I0 >= 0; I0 -= NBB) {  // U x = y
       const int I1 = std::min(n, I0 + NBB);
-      for (int i0 = I0 + ((I1 - I0 - 1) / NB) * NB; i0 >= I0; i0 -= NB) {
-        const int nb = std::min(NB, I1 - i0);
-        trsm_diag<E>(s, A, lda, sA, i0, nb, 1, B, ldb, sB, nrhs, batch);
-        if (i0 > I0)
-          gemm<E, E, E>(s, OP_N, OP_N, i0 - I0, nrhs, nb, m1, A + (long long)I0 * lda + i0, lda, sA,
-                        B + (long long)i0 * ldb, ldb, sB, one, B + (long long)I0 * ldb, ldb, sB, batch);
-      }
+      trsm_blk<E>(s, A, lda, sA, I0, I1 - I0, 1, B, ldb, sB, nrhs, batch);
       if (I0 > 0)
         gemm<E, E, E>(s, OP_N, OP_N, I0, nrhs, I1 - I0, m1, A + I0, lda, sA, B + (long long)I0 * ldb, ldb, sB, one, B,
                       ldb, sB, batch);

@@ -22,8 +22,8 @@
 // result stays within the FP64 product's own bound 2 k u |A| |B|.
 //
 // Kernel: one CTA per 128 x 64 output tile; warp 0 loads slice tiles with TMA
-// (cp.async.bulk.tensor, three-dimensional maps over [slice][row][k]) into a
-// two-stage ring, warp 1 issues the tcgen05 BF16 MMAs (M = 128, N = 64 to 256,
+// (cp.async.bulk.tensor, three-dimensional maps over [slice][row][k], 32-wide
+// k slices of 64-byte rows with the 64-byte swizzle) into a two-stage ring, warp 1 issues the tcgen05 BF16 MMAs (M = 128, N = 64 to 256,
 // K = 16; 28 per stage of 32 k) into the eight diagonal accumulators (all
 // 512 TMEM columns), warps 2..5 read them back.  Every mbarrier wait is
 // bounded; a timeout sets the library's tensor-core timeout flag.
@@ -56,9 +56,9 @@ constexpr int OZ_TN = 64;        // columns per tile
 constexpr int OZ_KS = 32;        // k per stage
 constexpr int OZ_KMAX = 384;     // k per launch keeping every diagonal sum below 2^24 (a multiple of 32)
 constexpr int OZ_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
-constexpr int OZ_A_KB = OZ_S * OZ_TM * 16;  // bytes of one 8-wide k block of all A slices (16 KB)
-constexpr int OZ_B_KB = OZ_S * OZ_TN * 16;  // same for B (8 KB)
-constexpr int OZ_STAGE = (OZ_KS / 8) * (OZ_A_KB + OZ_B_KB);  // 96 KB
+constexpr int OZ_A_SL = OZ_TM * 2 * OZ_KS;  // one slice of the A tile: 128 rows x 64 bytes (8 KB)
+constexpr int OZ_B_SL = OZ_TN * 2 * OZ_KS;  // same for B (4 KB)
+constexpr int OZ_STAGE = OZ_S * (OZ_A_SL + OZ_B_SL);  // 96 KB
 constexpr int OZ_SMEM = 2 * OZ_STAGE + 1024;
 constexpr long long OZ_WAIT = 1LL << 26;
 // instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = n
@@ -68,11 +68,12 @@ __host__ __device__ constexpr uint32_t oz_idesc(int n) {
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// K-major, no swizzle: core matrices of 8 rows x 16 bytes; lbo = bytes between
-// k-adjacent core matrices, sbo = bytes between 8-row groups.
-__device__ __forceinline__ uint64_t oz_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+// K-major, 64-byte swizzle (as TMA writes it): rows of 64 bytes (32 BF16),
+// atoms of 8 rows (512 bytes, the 8-row group stride); the k offset inside the
+// row is added to the start address.
+__device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
 __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
@@ -312,11 +313,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[st])), "r"(OZ_STAGE)
                      : "memory");
         const uint32_t base = su32(sm + st * OZ_STAGE);
-        for (int kb = 0; kb < OZ_KS / 8; ++kb) {
-          const int kx = kbase + i * OZ_KS + kb * 8;
-          oz_tma3(base + kb * OZ_A_KB, &mapA, kx, rowA, 0, su32(&full[st]));
-          oz_tma3(base + (OZ_KS / 8) * OZ_A_KB + kb * OZ_B_KB, &mapB, kx, rowB, 0, su32(&full[st]));
-        }
+        const int kx = kbase + i * OZ_KS;
+        oz_tma3(base, &mapA, kx, rowA, 0, su32(&full[st]));
+        oz_tma3(base + OZ_S * OZ_A_SL, &mapB, kx, rowB, 0, su32(&full[st]));
       }
     }
   } else if (warp == 1) {
@@ -326,7 +325,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         ok = oz_wait(su32(&full[st]), (i >> 1) & 1);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t aB = su32(sm + st * OZ_STAGE), bB = aB + (OZ_KS / 8) * OZ_A_KB;
+        const uint32_t aB = su32(sm + st * OZ_STAGE), bB = aB + OZ_S * OZ_A_SL;
         // The B slices of a k block lie back to back (slice t at rows 64 t .. 64 t + 63)
         // and the diagonal accumulators are adjacent in TMEM (diagonal d at columns
         // 64 d ..), so one MMA with N = 64 w multiplies A_s by B_t .. B_(t+w-1) into
@@ -336,14 +335,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int kh = 0; kh < OZ_KS / 16; ++kh) {
 #pragma unroll 1
           for (int s = 0; s < OZ_S; ++s) {
-            const uint64_t da = oz_desc(aB + kh * 2 * OZ_A_KB + s * (OZ_TM * 16), OZ_A_KB, 128);
+            const uint64_t da = oz_desc(aB + s * OZ_A_SL + kh * 32);
             const uint32_t acc = (i > 0 || kh > 0 || s > 0) ? 1u : 0u;
             int t = 0;
 #pragma unroll 1
             while (t + s < OZ_ND) {
               const int left = OZ_ND - s - t;
               const int w = left >= 4 ? 4 : left >= 2 ? 2 : 1;
-              const uint64_t db = oz_desc(bB + kh * 2 * OZ_B_KB + t * (OZ_TN * 16), OZ_B_KB, 128);
+              const uint64_t db = oz_desc(bB + t * OZ_B_SL + kh * 32);
               const uint32_t idesc = oz_idesc(w * OZ_TN);
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -425,14 +424,15 @@ bool encode_fn() {
   return g_encode != nullptr;
 }
 
-// 3-D map over slices [OZ_S][rows][kpad] (BF16), box {8 k, box_rows, all slices}.
+// 3-D map over slices [OZ_S][rows][kpad] (BF16), box {32 k, box_rows, all
+// slices} with the 64-byte swizzle of the MMA operand layout.
 bool make_map(CUtensorMap* map, void* base, long long rows, int kpad, int box_rows) {
   const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)OZ_S};
   const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)rows * kpad * 2};
-  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
+  const cuuint32_t box[3] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
   const cuuint32_t es[3] = {1, 1, 1};
   return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -1171,7 +1171,9 @@ def run_case(name):
             shapes = [(2, 1, 2048, 2048, 2048), (2, 1, 4096, 4096, 4096), (2, 1, 1792, 1792, 1792),
                       (2, 1, 1792, 128, 3584), (2, 8, 224, 1344, 224), (2, 4, 448, 128, 896),
                       (0, 1024, 196, 196, 196), (0, 1024, 196, 56, 196), (1, 1024, 196, 128, 196),
-                      (1, 1024, 56, 128, 196), (2, 1024, 56, 128, 56)]
+                      (1, 1024, 56, 128, 196), (2, 1024, 56, 128, 56),
+                      (2, 1, 1664, 1664, 128), (2, 1, 1024, 1024, 128), (2, 1, 512, 512, 128),
+                      (2, 1, 1664, 1792, 128)]
         g = torch.Generator(device="cuda").manual_seed(0)
 
         def rnd(shape, cplx):

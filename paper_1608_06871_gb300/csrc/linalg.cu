@@ -469,7 +469,11 @@ void gemm_simt(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, 
   constexpr long long kFill = 2 * 152;  // tiles that keep every SM of the chip busy
   const long long t64 = (long long)((m + GB - 1) / GB) * ((n + GB - 1) / GB) * batch;
   const long long t32 = (long long)((m + BM - 1) / BM) * ((n + BN - 1) / BN) * batch;
-  if (m >= GB && n >= GB && t64 >= kFill) {
+  // 64 x 64 tiles (twice the arithmetic per shared-memory load) when they fill the
+  // chip, for matrices of at least one tile each way or with at least 60% of
+  // the tiles' outputs inside the matrix (e.g. 56-row blocks)
+  const double fill64 = (double)m * n * batch / ((double)t64 * GB * GB);
+  if (t64 >= kFill && ((m >= GB && n >= GB) || fill64 >= 0.6)) {
     dim3 grid((n + GB - 1) / GB, (m + GB - 1) / GB, batch);
     k_gemm_big<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
     HS_COUNT_LAUNCH();

@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hs", choices=["hs", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--prof-family", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--prof-family", default="fp32", choices=["fp64", "fp32"],
+                    help="kernel family timed for the line's roofline in the main arm: the SIMT FP32 GEMMs "
+                         "(the largest family of the mixed step) or the FP64 GEMMs")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--workload", default="fwd_k40", choices=list(synth.WORKLOADS))
@@ -250,8 +252,10 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_arm(hs, torch, w, c, precision, args, world, local, prof_family):
-    """Warm up and time one precision arm of the step; returns its measurements."""
+def time_arm(hs, torch, w, c, precision, args, world, local, prof_family, extra_family=None):
+    """Warm up and time one precision arm of the step; returns its measurements.  prof_family is
+    profiled over the timed steps (a family that leaves the captured graphs in place); with
+    extra_family the returned profile comes from one more, untimed step of that family instead."""
     stream = torch.cuda.current_stream()
     solver = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, precision, device=local, stream=stream.cuda_stream)
     ctx = solver.ctx
@@ -307,6 +311,13 @@ def time_arm(hs, torch, w, c, precision, args, world, local, prof_family):
         step()
         torch.cuda.synchronize()
         tc = hs.hs_prof_stop()
+    if extra_family is not None:
+        # a family whose per-launch events need launch-by-launch passes (the FP32
+        # products run inside captured graphs otherwise): one more untimed step
+        hs.hs_prof_start(extra_family)
+        step()
+        torch.cuda.synchronize()
+        prof = hs.hs_prof_stop()
     # cold-frequency steps: each at a k not seen before, so the build also assembles
     # the layer-potential matrices S, D of that k (cached per k, so the timed steps
     # at a fixed k skip it); a mixed context then replays its factorisation graph
@@ -347,9 +358,10 @@ def run_hs(args, world, rank, local):
     w = synth.WORKLOADS[args.workload]
     c = synth.smooth_random_coeffs(w.S, seed=2, qmax=0.3)
     peak = hs.hs_peak_fp64(local, 300.0)
+    peak32 = hs.hs_peak_fp32(local, 300.0)
     prec = hs.HS_MIXED if args.precision == "mixed" else hs.HS_FP64
-    fam = hs.HS_PROF_GEMM_FP64 if args.prof_family == "fp64" else hs.HS_PROF_GEMM_FP32
-    main = time_arm(hs, torch, w, c, prec, args, world, local, fam)
+    main = time_arm(hs, torch, w, c, prec, args, world, local, hs.HS_PROF_GEMM_FP64,
+                    None if args.prof_family == "fp64" else hs.HS_PROF_GEMM_FP32)
     other = None
     if prec == hs.HS_MIXED and not args.no_fp64_arm:
         other = time_arm(hs, torch, w, c, hs.HS_FP64, args, world, local, hs.HS_PROF_GEMM_FP64)
@@ -414,6 +426,7 @@ def run_hs(args, world, rank, local):
         gemm_ms, gemm_flops, gemm_n = main["prof"]
         achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
         fp64_fam = args.prof_family == "fp64"
+        fam_peak = peak if fp64_fam else peak32
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": main["ms"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
@@ -422,16 +435,23 @@ def run_hs(args, world, rank, local):
                 "e2e": {"value": world * w.M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": main["launches"],
-                "roofline": {"bound": "alu" if fp64_fam else "alu",
+                "roofline": {"bound": "alu",
                              "kernel": "k_gemm<FP64> (batched FP64 GEMM family)" if fp64_fam
-                             else "k_gemm<FP32> (batched FP32 GEMM family)",
-                             "achieved": achieved, "peak": peak if fp64_fam else None, "unit": "TFLOP/s",
-                             "frac": (achieved / peak) if (achieved and peak and fp64_fam) else None,
-                             "peak_source": "measured FP64 DFMA rate (hs_peak_fp64, this run)",
+                             else "k_gemm / k_gemm_big <FP32> (SIMT FP32 GEMM family: merges, sweeps, LU "
+                                  "updates, leaf operators; the largest family of the mixed step)",
+                             "achieved": achieved, "peak": fam_peak, "unit": "TFLOP/s",
+                             "frac": (achieved / fam_peak) if (achieved and fam_peak) else None,
+                             "peak_source": ("measured FP64 DFMA rate (hs_peak_fp64, this run)" if fp64_fam
+                                             else "measured FP32 FFMA rate (hs_peak_fp32, this run)"),
                              "traffic": GEMM64_TRAFFIC if (fp64_fam and prec == hs.HS_MIXED) else None,
-                             "traffic_note": GEMM64_TRAFFIC_NOTE if (fp64_fam and prec == hs.HS_MIXED) else None,
-                             "launches": gemm_n, "kernel_ms_per_step": gemm_ms / args.steps,
-                             "algorithmic_tflop_per_step": gemm_flops / args.steps / 1e12},
+                             "traffic_note": GEMM64_TRAFFIC_NOTE if (fp64_fam and prec == hs.HS_MIXED) else
+                             "a family of dozens of product shapes per step: per-shape DRAM traffic is in "
+                             "profiles/launches_mixed_k40_32x32.md's reading, not one figure",
+                             "launches": gemm_n,
+                             "kernel_ms_per_step": gemm_ms / (args.steps if fp64_fam else 1),
+                             "algorithmic_tflop_per_step": gemm_flops / (args.steps if fp64_fam else 1) / 1e12,
+                             "measured_over": "the timed steps" if fp64_fam else
+                             "one extra, untimed step run launch by launch (per-launch CUDA events)"},
                 "phases": main["phases"], "clocks": main["clocks"],
                 "parity": {"fp64_vs_cpu_oracle": "1e-10 far field, 1e-9 fields and Jacobian, 1e-7 GN step, 1e-9 "
                                                  "gradient (tests/test_gpu_*.py) on trees the oracle factors (up to "
@@ -442,10 +462,15 @@ def run_hs(args, world, rank, local):
                                             "mixed checked against the FP64 arm below"}}
         if other is not None:
             err = float(np.linalg.norm(main["ufar"] - other["ufar"]) / np.linalg.norm(other["ufar"]))
+            f64 = (other["prof"][1] / (other["prof"][0] * 1e-3) / 1e12) if other["prof"][0] > 0 else None
             line["fp64_arm"] = {"value": world * w.M / (other["ms"] * 1e-3), "ms_per_step": other["ms"],
                                 "phases": other["phases"], "gpu_launches": other["launches"],
-                                "gemm_fp64_tflops": (other["prof"][1] / (other["prof"][0] * 1e-3) / 1e12)
-                                if other["prof"][0] > 0 else None}
+                                "gemm_fp64_tflops": f64,
+                                "roofline": {"bound": "alu", "kernel": "k_gemm<FP64> (batched FP64 GEMM family)",
+                                             "achieved": f64, "peak": peak, "unit": "TFLOP/s",
+                                             "frac": (f64 / peak) if (f64 and peak) else None,
+                                             "peak_source": "measured FP64 DFMA rate (hs_peak_fp64, this run)",
+                                             "kernel_ms_per_step": other["prof"][0] / args.steps}}
             line["mixed_vs_fp64_farfield_rel_err"] = err
             line["mixed_speedup_vs_fp64"] = other["ms"] / main["ms"]
         line["tensor_gemm"] = tensor_gemm_standalone(hs, torch)

@@ -169,9 +169,10 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
  * iteration reads it twice (with the emulation switched off, J and J^H are
  * applied from the fields by two FP64 grid contractions per iteration);
  * HS_MIXED -- J is formed once in complex FP32 (the tensor cores take its
- * x-projection where measured faster) from a single FP32 adjoint solve and
- * every iteration reads it twice with FP64 sums (for loose tolerances such as
- * the paper's 1e-3).  Either way J v
+ * x-projection where measured faster) and every iteration reads it twice with
+ * FP64 sums (for loose tolerances such as the paper's 1e-3); on an HS_MIXED
+ * context its adjoint fields get one FP64-residual correction after the FP32
+ * solve.  Either way J v
  * and J^H u stay exact transposes of one matrix.  The iteration's vectors live on the
  * host.  Stops when the relative residual or the relative normal-equations
  * residual (LSQR's own estimates) is at most tol, or after max_iter

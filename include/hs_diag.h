@@ -38,6 +38,10 @@ int hs_prof_stop(double* total_ms, double* total_flops, long long* launches);
  * TFLOP/s (2 flops per DFMA) in *tflops.  Runs for about `ms` milliseconds. */
 int hs_peak_fp64(int device, double ms, double* tflops);
 
+/* The same for FP32 fused multiply-adds (independent FFMA chains on every SM):
+ * the denominator of the SIMT FP32 GEMM family's roofline. */
+int hs_peak_fp32(int device, double ms, double* tflops);
+
 /* Refinement passes, the last relative change of the far field and the
  * estimated relative error of the returned far field (the stopping quantity:
  * the last change times rho / (1 - rho), rho the observed contraction of the

@@ -68,6 +68,7 @@ _SIGS = {
     "hs_prof_stop": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_longlong)]),
     "hs_peak_fp64": (_I, [_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "hs_peak_fp32": (_I, [_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "hs_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
     "hs_adjoint_refine_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
@@ -299,6 +300,12 @@ def hs_adjoint_refine_stats(ctx):
 def hs_peak_fp64(device: int = 0, ms: float = 300.0) -> float:
     t = ctypes.c_double()
     _check(None, lib().hs_peak_fp64(device, float(ms), ctypes.byref(t)))
+    return t.value
+
+
+def hs_peak_fp32(device: int = 0, ms: float = 300.0) -> float:
+    t = ctypes.c_double()
+    _check(None, lib().hs_peak_fp32(device, float(ms), ctypes.byref(t)))
     return t.value
 
 

@@ -54,9 +54,71 @@ __global__ void k_dfma_peak(double* out, int iters, double a, double b) {
   if (s == 12345.678) out[0] = s;  // keeps the chains live
 }
 
+// The same with FP32 FFMA chains (16 accumulators per thread).
+__global__ void k_ffma_peak(float* out, int iters, float a, float b) {
+  float x[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = threadIdx.x * 1e-6f + j * 1e-6f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = fmaf(x[j], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) s += x[j];
+  if (s == 12345.678f) out[0] = s;  // keeps the chains live
+}
+
+// Time `kern` (k_dfma_peak or k_ffma_peak) for about `ms`: returns the
+// measured milliseconds and the iteration count it ran with.
+template <typename T, typename K>
+float time_peak(K kern, T* out, int blocks, int threads, double ms, T a, T b, int* iters_out) {
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  int iters = 256;
+  float t = 0.f;
+  for (int rep = 0; rep < 6; ++rep) {  // warm up and scale the iteration count to the requested duration
+    cudaEventRecord(ev0);
+    kern<<<blocks, threads>>>(out, iters, a, b);
+    cudaEventRecord(ev1);
+    cudaEventSynchronize(ev1);
+    cudaEventElapsedTime(&t, ev0, ev1);
+    if (t > 0.5 * ms) break;
+    iters *= 2;
+  }
+  cudaEventRecord(ev0);
+  kern<<<blocks, threads>>>(out, iters, a, b);
+  cudaEventRecord(ev1);
+  cudaEventSynchronize(ev1);
+  cudaEventElapsedTime(&t, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  *iters_out = iters;
+  return t;
+}
+
 }  // namespace hs
 
 extern "C" {
+
+int hs_peak_fp32(int device, double ms, double* tflops) {
+  if (!tflops || !(ms > 0)) return HS_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return HS_ECUDA;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  float* out = nullptr;
+  if (cudaMalloc(&out, sizeof(float)) != cudaSuccess) return HS_ENOMEM;
+  const int threads = 256, blocks = sms * 8;
+  int iters = 0;
+  const float t = hs::time_peak<float>(hs::k_ffma_peak, out, blocks, threads, ms, 0.9999999f, 1e-7f, &iters);
+  const double ffma = (double)blocks * threads * iters * 8.0 * 16.0;
+  *tflops = 2.0 * ffma / (t * 1e-3) / 1e12;
+  cudaFree(out);
+  return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
+}
 
 int hs_prof_start(int family) {
   if (family != HS_PROF_GEMM_FP64 && family != HS_PROF_GEMM_FP32 && family != HS_PROF_GEMM_TC &&

@@ -1282,12 +1282,15 @@ size_t mixed_adjoint_bytes(hs_ctx* ctx, int P) {
 // Z64: [leaf][196][P] (FP64, output).  A2: [P][2 nb] FP64.
 // With refine == false one pass (the FP32 transposed solve of L) is returned:
 // for products that carry FP32 rounding anyway (the tensor-core Jacobian).
-int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2* Z64, Arena& a, bool refine = true) {
+// passes: 0 = refine to refine_tol (HS_ENOCONV after refine_max_iter passes);
+// n > 0 = exactly n passes (the FP32 solve and n - 1 FP64-residual corrections).
+int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2* Z64, Arena& a, int passes = 0) {
   const int nb = ctx->B.nb, nl = ctx->nleaf, nlev = (int)ctx->levels.size();
   const size_t nbP = (size_t)nb * P;
   const double eta = ctx->k;
   const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-9;
-  const int max_iter = !refine ? 1 : ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
+  const bool refine = passes != 1;
+  const int max_iter = passes > 0 ? passes : ctx->cfg.refine_max_iter > 0 ? ctx->cfg.refine_max_iter : 8;
   const float2 one = make_float2(1.f, 0.f), mone = make_float2(-1.f, 0.f), zero = make_float2(0.f, 0.f);
   float2* G = a.get<float2>((size_t)nl * NL * P);
   float2 *bufA = a.get<float2>(field_buf_elems(ctx, P)), *bufB = a.get<float2>(field_buf_elems(ctx, P));
@@ -1377,7 +1380,7 @@ int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2
       ctx->adj_update = upd;
       ctx->adj_est = est;
       prev_upd = upd;
-      if (est <= tol) {
+      if (est <= tol || (passes > 0 && it + 1 == passes)) {
         converged = true;
         break;
       }
@@ -1400,7 +1403,7 @@ size_t mixed_fields_bytes(hs_ctx* ctx, int M, int P) {
 // solve, adjoint fields Zg from the refined adjoint solve (both FP64-accurate),
 // on the interior grid.
 int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, int M, const double* thetas, int P,
-                             double2* F, double2* Ug, double2* Zg, Arena& a, bool refine_adjoint = true) {
+                             double2* F, double2* Ug, double2* Zg, Arena& a, int adjoint_passes = 0) {
   const int nb = ctx->B.nb;
   double2* X = a.get<double2>((size_t)ctx->nleaf * NL * M);
   double2* A2 = a.get<double2>((size_t)P * 2 * nb);
@@ -1414,7 +1417,7 @@ int mixed_fields_and_adjoint(hs_ctx* ctx, cudaStream_t s, const double* alphas, 
   farfield_matrix(s, ctx->B, ctx->k, ctx->cfg.R, thetas, P, A2);
   {
     Arena sub = a;
-    CKR(mixed_adjoint(ctx, s, A2, P, Z64, sub, refine_adjoint));
+    CKR(mixed_adjoint(ctx, s, A2, P, Z64, sub, adjoint_passes));
   }
   leaf_to_grid(s, Z64, NI, ctx->nL, P, Zg);
   CK(cudaGetLastError());
@@ -1981,9 +1984,11 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   CK(cudaMemcpyAsync(dt, thetas, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ddata, data, sizeof(double) * 2 * MP, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(nrm2, 0, sizeof(double), s));
-  if (mixed) {  // refined far field and forward fields; adjoint refined unless J is FP32 anyway
+  if (mixed) {  // refined far field and forward fields; the adjoint refined to the tolerance, or,
+                // for the FP32 Jacobian, with one FP64-residual correction (its error is then
+                // below that matrix's own FP32 rounding)
     Arena sub = a;
-    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub, !p32));
+    CKR(mixed_fields_and_adjoint(ctx, s, da, M, dt, P, F, Ug, Zg, sub, p32 ? 2 : 0));
   } else {  // forward far field F(c)
     Arena sub = a;
     double2 *ui = sub.get<double2>((size_t)nb * M), *dni = sub.get<double2>((size_t)nb * M);

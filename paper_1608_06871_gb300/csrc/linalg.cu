@@ -135,17 +135,23 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int m, int n, in
 // load), k-step 8 with the next tile prefetched into registers.  For shapes
 // with enough tiles to fill the machine.
 constexpr int GB = 64, GK = 8;
+// With splits > 1 (8-byte output elements only: the partial tile must fit in
+// static shared memory) the kernel runs in clusters of `splits` CTAs along z,
+// each over a slice of k, and the partial tiles are summed in split order
+// through distributed shared memory, as in k_gemm.
 template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, int n, int k, TC alpha,
                                                   const TA* __restrict__ A, int lda, long long sA,
                                                   const TB* __restrict__ B, int ldb, long long sB, TC beta,
-                                                  TC* __restrict__ C, int ldc, long long sC) {
+                                                  TC* __restrict__ C, int ldc, long long sC, int splits) {
   __shared__ TA As[GK][GB];
   __shared__ TB Bs[GK][GB];
-  const int b = blockIdx.z;
+  const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
   A += b * sA;
   B += b * sB;
   C += b * sC;
+  const int kc = ((k + splits - 1) / splits + GK - 1) / GK * GK;
+  const int kbeg = sp * kc, kend = min(k, kbeg + kc);
   const int row0 = blockIdx.y * GB, col0 = blockIdx.x * GB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   TC acc[4][4];
@@ -163,11 +169,11 @@ __global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, in
       int r, kk;
       if (opA == OP_N) { r = e / GK; kk = e % GK; } else { kk = e / GB; r = e % GB; }
       int gr = row0 + r, gk = k0 + kk;
-      ra[q] = (gr < m && gk < k) ? ld_op(A, lda, opA, gr, gk) : el<TA>::zero();
+      ra[q] = (gr < m && gk < kend) ? ld_op(A, lda, opA, gr, gk) : el<TA>::zero();
       int kk2, c;
       if (opB == OP_N) { kk2 = e / GB; c = e % GB; } else { c = e / GK; kk2 = e % GK; }
       int gk2 = k0 + kk2, gc = col0 + c;
-      rb[q] = (gk2 < k && gc < n) ? ld_op(B, ldb, opB, gk2, gc) : el<TB>::zero();
+      rb[q] = (gk2 < kend && gc < n) ? ld_op(B, ldb, opB, gk2, gc) : el<TB>::zero();
     }
   };
   auto store = [&]() {
@@ -182,11 +188,11 @@ __global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, in
       Bs[kk2][c] = rb[q];
     }
   };
-  load(0);
-  for (int k0 = 0; k0 < k; k0 += GK) {
+  load(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += GK) {
     store();
     __syncthreads();
-    if (k0 + GK < k) load(k0 + GK);
+    if (k0 + GK < kend) load(k0 + GK);
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
       TA a[4];
@@ -202,6 +208,32 @@ __global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, in
     }
     __syncthreads();
   }
+  if constexpr (sizeof(TC) <= 8) {
+    if (splits > 1) {
+      __shared__ TC red[GB * GB];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[(ty + 16 * i) * GB + tx + 16 * j] = acc[i][j];
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();
+      const int rows_per = (GB + splits - 1) / splits;
+      const int rb = sp * rows_per, re = min(GB, rb + rows_per);
+      for (int e = rb * GB + threadIdx.x; e < re * GB; e += 256) {
+        TC sum = el<TC>::zero();
+        for (int q = 0; q < splits; ++q) sum = addv(sum, cl.map_shared_rank(red, q)[e]);
+        const int r = row0 + e / GB, c = col0 + e % GB;
+        if (r < m && c < n) {
+          TC v = scal<TC, TC>(alpha, sum);
+          long long o = (long long)r * ldc + c;
+          if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
+          C[o] = v;
+        }
+      }
+      cl.sync();  // keep this CTA's partial tile alive until every rank has read it
+      return;
+    }
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -216,6 +248,141 @@ __global__ void __launch_bounds__(256, 2) k_gemm_big(int opA, int opB, int m, in
     }
 }
 
+
+// Untransposed FP32 products (real or complex, 4- or 8-byte elements): the
+// 64 x 64 tile and 4 x 4 outputs per thread of k_gemm_big, with the operand
+// tiles staged by cp.async 16-byte copies into a three-stage shared-memory
+// ring (k-step 16), so that the loads of the next two k-steps overlap the
+// products of the current one; zero-filled copies cover the edges.  Needs
+// 16-byte aligned operand rows (checked by the host).  splits > 1: k split
+// over a cluster, partial tiles summed in split order through distributed
+// shared memory.
+constexpr int PK = 16, PST = 3;
+template <typename TA, typename TB, typename TC>
+struct PipeCfg {
+  static constexpr int A_ST = GB * PK * (int)sizeof(TA);  // bytes of one A stage (64 rows x 16 k)
+  static constexpr int B_ST = PK * GB * (int)sizeof(TB);  // bytes of one B stage (16 k x 64 columns)
+  static constexpr int RING = PST * (A_ST + B_ST);
+  static constexpr int RED = GB * GB * (int)sizeof(TC);
+  static constexpr int SMEM = RING > RED ? RING : RED;
+};
+
+__device__ __forceinline__ void cp16(void* dst, const void* src, int bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(256, 2) k_gemm_pipe(int m, int n, int k, TC alpha, const TA* __restrict__ A, int lda,
+                                                   long long sA, const TB* __restrict__ B, int ldb, long long sB,
+                                                   TC beta, TC* __restrict__ C, int ldc, long long sC, int splits) {
+  using Cf = PipeCfg<TA, TB, TC>;
+  extern __shared__ __align__(16) unsigned char pipe_smem[];
+  constexpr int EA = 16 / (int)sizeof(TA), EB = 16 / (int)sizeof(TB);  // elements per 16-byte copy
+  const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  const int kc = ((k + splits - 1) / splits + PK - 1) / PK * PK;
+  const int kbeg = sp * kc, kend = min(k, kbeg + kc);
+  const int nsteps = kend > kbeg ? (kend - kbeg + PK - 1) / PK : 0;
+  const int row0 = blockIdx.y * GB, col0 = blockIdx.x * GB;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  auto As = [&](int st) { return reinterpret_cast<TA*>(pipe_smem + st * (Cf::A_ST + Cf::B_ST)); };
+  auto Bs = [&](int st) { return reinterpret_cast<TB*>(pipe_smem + st * (Cf::A_ST + Cf::B_ST) + Cf::A_ST); };
+  // stage the k-step `step` into ring slot `st`
+  auto issue = [&](int step, int st) {
+    const int k0 = kbeg + step * PK;
+    TA* as = As(st);
+    TB* bs = Bs(st);
+    constexpr int CA = GB * PK / EA, CB = PK * GB / EB;  // 16-byte copies per stage
+    for (int q = tid; q < CA; q += 256) {
+      const int r = q / (PK / EA), kk = (q % (PK / EA)) * EA;
+      const int gr = row0 + r, gk = k0 + kk;
+      const int valid = (gr < m && gk < kend) ? min(EA, kend - gk) : 0;
+      const TA* src = valid ? A + (long long)gr * lda + gk : A;
+      cp16(as + r * PK + kk, src, valid * (int)sizeof(TA));
+    }
+    for (int q = tid; q < CB; q += 256) {
+      const int kk = q / (GB / EB), c = (q % (GB / EB)) * EB;
+      const int gk = k0 + kk, gc = col0 + c;
+      const int valid = (gk < kend && gc < n) ? min(EB, n - gc) : 0;
+      const TB* src = valid ? B + (long long)gk * ldb + gc : B;
+      cp16(bs + kk * GB + c, src, valid * (int)sizeof(TB));
+    }
+  };
+  TC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = el<TC>::zero();
+#pragma unroll
+  for (int st = 0; st < PST - 1; ++st) {
+    if (st < nsteps) issue(st, st);
+    cp_commit();
+  }
+  for (int step = 0; step < nsteps; ++step) {
+    cp_wait<PST - 2>();
+    __syncthreads();  // stage `step` landed for every thread; slot (step - 1) % PST is free
+    if (step + PST - 1 < nsteps) issue(step + PST - 1, (step + PST - 1) % PST);
+    cp_commit();
+    const TA* as = As(step % PST);
+    const TB* bs = Bs(step % PST);
+#pragma unroll
+    for (int kk = 0; kk < PK; ++kk) {
+      TA a[4];
+      TB bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = as[(ty + 16 * i) * PK + kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = bs[kk * GB + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmac(acc[i][j], a[i], bb[j]);
+    }
+  }
+  cp_wait<0>();
+  __syncthreads();
+  if (splits > 1) {
+    TC* red = reinterpret_cast<TC*>(pipe_smem);  // the ring is free now
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) red[(ty + 16 * i) * GB + tx + 16 * j] = acc[i][j];
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    const int rows_per = (GB + splits - 1) / splits;
+    const int rb = sp * rows_per, re = min(GB, rb + rows_per);
+    for (int e = rb * GB + tid; e < re * GB; e += 256) {
+      TC sum = el<TC>::zero();
+      for (int q = 0; q < splits; ++q) sum = addv(sum, cl.map_shared_rank(red, q)[e]);
+      const int r = row0 + e / GB, c = col0 + e % GB;
+      if (r < m && c < n) {
+        TC v = scal<TC, TC>(alpha, sum);
+        long long o = (long long)r * ldc + c;
+        if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
+        C[o] = v;
+      }
+    }
+    cl.sync();  // keep this CTA's partial tile alive until every rank has read it
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < m && c < n) {
+        TC v = scal<TC, TC>(alpha, acc[i][j]);
+        long long o = (long long)r * ldc + c;
+        if (!is_zero(beta)) v = addv(v, scal<TC, TC>(beta, C[o]));
+        C[o] = v;
+      }
+    }
+}
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -473,9 +640,73 @@ void gemm_simt(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, 
   // chip, for matrices of at least one tile each way or with at least 60% of
   // the tiles' outputs inside the matrix (e.g. 56-row blocks)
   const double fill64 = (double)m * n * batch / ((double)t64 * GB * GB);
-  if (t64 >= kFill && ((m >= GB && n >= GB) || fill64 >= 0.6)) {
-    dim3 grid((n + GB - 1) / GB, (m + GB - 1) / GB, batch);
-    k_gemm_big<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  // few big tiles with a long k: the same 64 x 64 tiles, k split over a cluster
+  int splits64 = 1;
+  constexpr bool pipe_types = !is_fp64<TC>::v && sizeof(TA) <= 8 && sizeof(TB) <= 8;
+  if (sizeof(TC) <= 8 && t64 < kFill && m >= GB && n >= GB && k >= 256) {
+    splits64 = (int)std::min<long long>((kFill + t64 - 1) / t64, k / 128);
+    splits64 = std::max(1, std::min(splits64, kMaxCluster));
+    if ((long long)batch * splits64 > 65535 || t64 * splits64 < 152) splits64 = 1;
+  }
+  if ((t64 >= kFill && ((m >= GB && n >= GB) || fill64 >= 0.6)) || splits64 > 1) {
+    dim3 grid((n + GB - 1) / GB, (m + GB - 1) / GB, batch * splits64);
+    // untransposed FP32 operands with 16-byte aligned rows: the cp.async pipeline
+    if constexpr (pipe_types) {
+      constexpr int EA = 16 / (int)sizeof(TA), EB = 16 / (int)sizeof(TB);
+      const bool aligned = opA == OP_N && opB == OP_N && lda % EA == 0 && ldb % EB == 0 && sA % EA == 0 &&
+                           sB % EB == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+                           (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+      if (aligned) {
+        constexpr int smem = PipeCfg<TA, TB, TC>::SMEM;
+        static bool attr[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !attr[dev]) {
+          cudaFuncSetAttribute(k_gemm_pipe<TA, TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+          if (dev >= 0 && dev < 64) attr[dev] = true;
+        }
+        if (splits64 == 1) {
+          k_gemm_pipe<TA, TB, TC><<<grid, 256, smem, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                                          1);
+        } else {
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = grid;
+          cfg.blockDim = dim3(256);
+          cfg.dynamicSmemBytes = smem;
+          cfg.stream = s;
+          cudaLaunchAttribute at[1];
+          at[0].id = cudaLaunchAttributeClusterDimension;
+          at[0].val.clusterDim.x = 1;
+          at[0].val.clusterDim.y = 1;
+          at[0].val.clusterDim.z = splits64;
+          cfg.attrs = at;
+          cfg.numAttrs = 1;
+          cudaLaunchKernelEx(&cfg, k_gemm_pipe<TA, TB, TC>, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                             sC, splits64);
+        }
+        HS_COUNT_LAUNCH();
+        if (prof) prof_end(s, ev, flops_per_mac<TA, TB>() * (double)m * n * k * batch);
+        return;
+      }
+    }
+    if (splits64 == 1) {
+      k_gemm_big<TA, TB, TC><<<grid, 256, 0, s>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                                  1);
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = dim3(256);
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 1;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = splits64;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_gemm_big<TA, TB, TC>, opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                         ldc, sC, splits64);
+    }
     HS_COUNT_LAUNCH();
   } else {
     int splits = 1;

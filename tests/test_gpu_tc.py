@@ -143,6 +143,23 @@ def test_tensor_cores_off_and_autotuned(hs):
         _check_bound(o, A, B, 520)
 
 
+@pytest.mark.parametrize("batch,m,n,k", [(1, 1792, 128, 3584), (2, 700, 300, 1000), (1, 256, 64, 4100)])
+def test_simt_split_k_products(hs, batch, m, n, k):
+    """The SIMT FP32 products (tensor cores off) on few-tile shapes with a long k, which the
+    dispatch splits over a thread-block cluster (64 x 64 and 32 x 32 tiles), within the same
+    componentwise bound."""
+    gen = torch.Generator().manual_seed(31 + m + k)
+    A = _rand((batch, m, k), gen)
+    B = _rand((batch, k, n), gen)
+    out = torch.empty((batch, m, n), dtype=torch.complex64, device="cuda")
+    try:
+        hs.hs_set_tensor_cores(0)
+        assert not hs.hs_gemm32(A.cuda(), B.cuda(), out)
+    finally:
+        hs.hs_set_tensor_cores(2)
+    _check_bound(out, A, B, 2 * k)
+
+
 def test_mixed_solve_tc_on_off(hs):
     import synth
     w = synth.WORKLOADS["grad_k20"]

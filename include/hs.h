@@ -168,9 +168,8 @@ int hs_gn_step(hs_ctx* ctx, const double* data, const double* alphas, int M,
  * once in FP64 by the emulated FP64 contraction on the tensor cores and every
  * iteration reads it twice (with the emulation switched off, J and J^H are
  * applied from the fields by two FP64 grid contractions per iteration);
- * HS_MIXED -- J is formed once in complex FP32 (the tensor cores take its
- * x-projection where measured faster) and every iteration reads it twice with
- * FP64 sums (for loose tolerances such as the paper's 1e-3); on an HS_MIXED
+ * HS_MIXED -- J is formed once in complex FP32 and every iteration reads it
+ * twice with FP64 sums (for loose tolerances such as the paper's 1e-3); on an HS_MIXED
  * context its adjoint fields get one FP64-residual correction after the FP32
  * solve.  Either way J v
  * and J^H u stay exact transposes of one matrix.  The iteration's vectors live on the

@@ -206,10 +206,10 @@ void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P
   gemm<double, double, double>(s, OP_N, OP_T, S1, S2, nX, k2, T1, nX, 0, sy, nX, 0, 0.0, g, S2, 0, 1);
 }
 
-// Explicit complex FP32 Jacobian on the tensor cores, for iterations that stop
-// at a loose tolerance: the contraction of the FP32 Khatri-Rao rows with the
-// complex-embedded x-sine table on the tensor cores (split-FP16 product; K = nX,
-// short enough for FP32 accumulation), then the batch of per-pair y-projections.
+// Explicit complex FP32 Jacobian, for iterations that stop at a loose
+// tolerance: the contraction of the FP32 Khatri-Rao rows with the real x-sine
+// table (a complex-by-real FP32 product), then the batch of per-pair
+// y-projections.
 // LSQR then applies J32 and J32^H by the two products below, which read J32
 // once each and accumulate in FP64, so that they stay exact transposes of one
 // operator (products computed from the fields with independent FP32 rounding
@@ -236,11 +236,11 @@ __global__ void k_khatri_rao32(const double2* __restrict__ Ug, const double2* __
   }
 }
 
-// out[g][m] = (sx[m][g], 0), and sy as FP32
+// sxr[g][m] = sx[m][g] and sy, both as FP32
 __global__ void k_sine_tables32(const double* __restrict__ sx, const double* __restrict__ sy, int n, int S1, int S2,
-                                float2* __restrict__ sxc, float* __restrict__ sy32) {
+                                float* __restrict__ sxr, float* __restrict__ sy32) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < (long long)n * S1) sxc[e] = make_float2((float)sx[(e % S1) * n + e / S1], 0.f);
+  if (e < (long long)n * S1) sxr[e] = (float)sx[(e % S1) * n + e / S1];
   if (e < (long long)n * S2) sy32[e] = (float)sy[e];
 }
 
@@ -249,15 +249,16 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
                          float2* T, int C) {
   const long long plane = (long long)nX * nX, MP = (long long)M * P;
   const long long nt = (long long)nX * std::max(S1, S2);
-  k_sine_tables32<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(sx, sy, nX, S1, S2, sxc, sy32);
+  float* sxr = reinterpret_cast<float*>(sxc);  // the real x-sine table (half the buffer)
+  k_sine_tables32<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(sx, sy, nX, S1, S2, sxr, sy32);
   HS_COUNT_LAUNCH();
   for (long long c0 = 0; c0 < MP; c0 += C) {
     const int nc = (int)std::min<long long>(C, MP - c0);
     k_khatri_rao32<<<dim3((unsigned)((plane + 255) / 256), (nc + KR_PAIRS - 1) / KR_PAIRS), 256, 0, s>>>(
         Ug, Zg, P, plane, c0, nc, W);
     HS_COUNT_LAUNCH();
-    gemm<float2, float2, float2>(s, OP_N, OP_N, nc * nX, S1, nX, make_float2(1.f, 0.f), W, nX, 0, sxc, S1, 0,
-                                 make_float2(0.f, 0.f), T, S1, 0, 1);
+    gemm<float2, float, float2>(s, OP_N, OP_N, nc * nX, S1, nX, make_float2(1.f, 0.f), W, nX, 0, sxr, S1, 0,
+                                make_float2(0.f, 0.f), T, S1, 0, 1);
     gemm<float2, float, float2>(s, OP_T, OP_T, S1, S2, nX, make_float2((float)k2, 0.f), T, S1, (long long)nX * S1,
                                 sy32, nX, 0, make_float2(0.f, 0.f), J + c0 * S1 * S2, S2, (long long)S1 * S2, nc);
   }

@@ -749,15 +749,15 @@ inline float2 as_f2(float2 x) { return x; }
 inline float2 as_f2(float x) { return make_float2(x, 0.f); }
 template <typename T> constexpr long long fl() { return sizeof(T) / sizeof(float); }  // floats per element
 
-// Products worth measuring: every dimension of the real product at least 512.
-// Smaller ones (the batched leaf, merge and sweep products, the short-k
-// trailing updates) never reached the required speed-up over SIMT in the
-// measurements (at most 1.4x) and stay there without a measurement, which
-// keeps a frequency sweep, whose sizes change from step to step, from paying
-// for one per new shape.
-bool t32_candidate(int mode, int m, int n, int k) {
+// Products worth measuring: at least 512 rows and 512 of k in the real
+// product, at least 64 columns, and 2^28 real multiply-adds.  Smaller ones
+// (the batched leaf, merge and sweep products, the short-k trailing updates)
+// never reached the required speed-up over SIMT in the measurements (at most
+// 1.4x) and stay there without a measurement, which keeps a frequency sweep,
+// whose sizes change from step to step, from paying for one per new shape.
+bool t32_candidate(int mode, int m, int n, int k, int batch) {
   const long long np = mode ? 2LL * n : n, kp = mode == 2 ? 2LL * k : k;
-  return m >= 512 && np >= 512 && kp >= 512;
+  return m >= 512 && np >= 64 && kp >= 512 && (long long)m * np * kp * batch >= (1LL << 28);
 }
 
 // Per-shape choice between the tensor-core and the SIMT product, measured
@@ -796,7 +796,7 @@ void gemm(cudaStream_t s, int opA, int opB, int m, int n, int k, TC alpha, const
   constexpr int mode = t32_mode<TA, TB, TC>::v;
   if constexpr (mode >= 0) {
     const bool force = g_t32_mode == 2;
-    if (opA == OP_N && opB == OP_N && k > 0 && g_t32_mode != 0 && (force || t32_candidate(mode, m, n, k))) {
+    if (opA == OP_N && opB == OP_N && k > 0 && g_t32_mode != 0 && (force || t32_candidate(mode, m, n, k, batch))) {
       auto run_tc = [&](TC* Cd) {
         return t32_gemm(s, mode, m, n, k, as_f2(alpha), reinterpret_cast<const float*>(A), fl<TA>() * lda,
                         fl<TA>() * sA, reinterpret_cast<const float*>(B), fl<TB>() * ldb, fl<TB>() * sB, as_f2(beta),

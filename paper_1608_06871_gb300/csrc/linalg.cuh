@@ -62,6 +62,7 @@ bool t32_timed_out(cudaStream_t s);
 // when the calling thread's last gemm() ran on the tensor cores.
 extern bool g_autotune;
 extern float g_tc_margin;  // the tensor cores are kept where they take < g_tc_margin of the SIMT time
+
 // Tensor-core use for FP32 products (hs_set_tensor_cores): 0 never; 1 (the
 // default) where the per-shape measurement finds them clearly faster; 2 every
 // supported product.

@@ -164,6 +164,19 @@ int hs_dgemm_emulated(int m, int n, int k, const void* A, const void* B, void* C
  * Process-wide; takes effect at the next Jacobian.  Never fails. */
 int hs_set_fp64_emulation(int enable);
 
+/* The two products LSQR applies to the explicit FP32 Jacobian (Sec. 3.3,
+ * hs_gn_step_lsqr with products = HS_MIXED): y = J v and g = Re(J^H u) for a
+ * complex FP32 J (rows x n, row-major, interleaved re, im), real FP64 v (n),
+ * complex FP64 u and y (rows, interleaved) and real FP64 g (n), with FP64
+ * products and sums (J's entries widened exactly), so that the two are
+ * transposes of one operator to FP64 rounding.  DEVICE pointers on the
+ * current device, enqueued on `stream` and synchronised before return;
+ * allocates and frees 8 n ceil(rows / 256) bytes of scratch.  Errors:
+ * HS_EINVAL (non-positive size, rows > 65535 * 256, NULL pointer),
+ * HS_ENOMEM, HS_ECUDA. */
+int hs_jacobian32_products(long long rows, int n, const void* J, const double* v, void* y, const void* u, double* g,
+                           void* stream);
+
 /* Solve A[b] X[b] = B[b] in place in B for b < batch with the library's
  * batched LU (partial pivoting; tournament pivoting for panels taller than 256
  * rows) and triangular solves: complex (interleaved re, im), row-major,

@@ -87,6 +87,7 @@ _SIGS = {
     "hs_zgemm": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _I, _P]),
     "hs_dgemm_emulated": (_I, [_I, _I, _I, _P, _P, _P, _I, _P]),
     "hs_set_fp64_emulation": (_I, [_I]),
+    "hs_jacobian32_products": (_I, [ctypes.c_longlong, _I, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -401,6 +402,15 @@ def hs_gemm32(A, B, out, b_shared: bool = False, stream: int = 0) -> bool:
                                  ctypes.c_void_p(out.data_ptr()), batch, 1 if b_shared else 0,
                                  ctypes.c_void_p(stream), ctypes.byref(used)))
     return bool(used.value)
+
+
+def hs_jacobian32_products(J, v, y, u, g, stream: int = 0):
+    """y = J @ v and g = Re(J^H u) for a contiguous complex64 CUDA matrix J (rows, n), float64 v (n),
+    complex128 y and u (rows) and float64 g (n): the products LSQR applies to the FP32 Jacobian."""
+    rows, n = J.shape
+    _check(None, lib().hs_jacobian32_products(rows, n, ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                              ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                              ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(stream)))
 
 
 class Solver:

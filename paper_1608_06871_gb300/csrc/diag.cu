@@ -6,6 +6,7 @@
 #include "../../include/hs_diag.h"
 #include "common.cuh"
 #include "linalg.cuh"
+#include "tree.cuh"
 
 namespace hs {
 
@@ -328,6 +329,21 @@ int hs_lu_solve(int precision, int n, int nrhs, void* A, void* B, int batch, voi
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
   for (int v : h)
     if (v != 0) return HS_ESINGULAR;
+  return HS_OK;
+}
+
+int hs_jacobian32_products(long long rows, int n, const void* J, const double* v, void* y, const void* u, double* g,
+                           void* stream) {
+  if (rows <= 0 || n <= 0 || hs::gemvT_parts(rows) > 65535 || !J || !v || !y || !u || !g) return HS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* part = nullptr;
+  if (cudaMalloc(&part, sizeof(double) * (size_t)hs::gemvT_parts(rows) * n) != cudaSuccess) return HS_ENOMEM;
+  const float2* J32 = static_cast<const float2*>(J);
+  hs::gemv32(s, J32, rows, n, v, static_cast<double2*>(y));
+  hs::gemvT32(s, J32, rows, n, static_cast<const double2*>(u), part, g);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(part);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HS_ECUDA;
   return HS_OK;
 }
 

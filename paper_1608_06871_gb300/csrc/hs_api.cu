@@ -197,6 +197,8 @@ struct hs_ctx {
   // for the emulated FP64 residual product, made once per k
   char* d_ds_oz = nullptr;
   double ds_oz_k = -1.0;
+  char* d_dst_oz = nullptr;  // the same rows transposed, for the adjoint refinement
+  double dst_oz_k = -1.0;
   std::vector<long long> if_off;
   long long if_rows = 0;
   int adj_iters = 0;
@@ -1255,6 +1257,8 @@ size_t mixed_adjoint_bytes(hs_ctx* ctx, int P) {
              Arena::bytes((size_t)ctx->if_rows * P, 16) + Arena::bytes(nb * P, 16) + Arena::bytes(2 * nb * P, 16) +
              Arena::bytes(8, 8);
   for (auto& L : ctx->levels) b += Arena::bytes((size_t)L.nbox * 2 * L.ni * P, 8);
+  if (g_oz_enabled)
+    b += Arena::bytes(2 * oz_wide_bytes(P, (int)nb, false), 1) + Arena::bytes(4 * oz_partial_bytes(2 * (int)nb, P, (int)nb), 1);
   return b;
 }
 
@@ -1303,7 +1307,20 @@ int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2
   double* nrm = a.get<double>(8);
   std::vector<float2*> MU(nlev);
   for (int li = 0; li < nlev; ++li) MU[li] = a.get<float2>((size_t)ctx->levels[li].nbox * 2 * ctx->levels[li].ni * P);
+  // the exterior rows' transposed product DS^T Yext by the emulated FP64 product:
+  // DS^T sliced once per k, Yext (as the right operand) once per pass
+  const bool emu = g_oz_enabled;
+  const size_t ob_y = emu ? oz_wide_bytes(P, nb, false) : 0, ob_part = emu ? oz_partial_bytes(2 * nb, P, nb) : 0;
+  char* ozs = emu ? a.get<char>(2 * ob_y) : nullptr;
+  char* ozp = emu ? a.get<char>(4 * ob_part) : nullptr;
   if (a.over) return fail(ctx, HS_ENOMEM, "workspace request beyond its sizing");
+  const size_t ob_dst = oz_wide_bytes(2 * nb, nb, true);
+  if (emu && ctx->dst_oz_k != ctx->bie_k) {
+    if (!ctx->d_dst_oz) CKR(dalloc(ctx, &ctx->d_dst_oz, 2 * ob_dst));
+    oz_slice_wide(s, re_view_t(ctx->d_DS, 2 * nb, 0), 2 * nb, nb, true, ctx->d_dst_oz);
+    oz_slice_wide(s, re_view_t(ctx->d_DS, 2 * nb, 1), 2 * nb, nb, true, ctx->d_dst_oz + ob_dst);
+    ctx->dst_oz_k = ctx->bie_k;
+  }
   const LeafScratchT<float>& w = ctx->ws32;
   const long long sG = (long long)NL * P;
   Phase ph("hs_adjoint_refine");
@@ -1319,9 +1336,16 @@ int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2
     Phase pp("hs_adjoint_pass");
     const bool first = it == 0;
     // FP64 residual L - A^T Y of every unknown (L itself on the first pass)
-    if (!first)
+    if (!first && emu) {
+      oz_slice_wide(s, re_view_t(Yext, P, 0), P, nb, false, ozs);
+      oz_slice_wide(s, re_view_t(Yext, P, 1), P, nb, false, ozs + ob_y);
+      const cudaError_t e = oz_zmul_wide(s, 2 * nb, P, nb, ctx->d_dst_oz, ctx->d_dst_oz + ob_dst, ozs, ozs + ob_y, 1.0,
+                                         0.0, V, P, ozp);
+      if (e != cudaSuccess) return fail(ctx, HS_ECUDA, std::string("emulated FP64 product: ") + cudaGetErrorString(e));
+    } else if (!first) {
       gemm<double2, double2, double2>(s, OP_T, OP_N, 2 * nb, P, nb, make_double2(1, 0), ctx->d_DS, 2 * nb, 0, Yext, P,
                                       0, make_double2(0, 0), V, P, 0, 1);
+    }
     adjoint_residual(s, Z64, ctx->d_adj_desc, Yif, A2, first ? nullptr : V, ctx->d_q, ctx->d_D1, nl, nb, ctx->k,
                      ctx->h, eta, P, first, G);
     // transposed FP32 solve: leaf solution operators, then the transposed
@@ -1942,7 +1966,7 @@ int hs_gn_step_lsqr(hs_ctx* ctx, const double* data, const double* alphas, int M
   // read twice per iteration (exact transposes of one matrix); without the
   // emulation, J and J^H are applied from the fields by FP64 grid contractions
   const bool p64x = !p32 && g_oz_enabled;
-  const int C32 = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget / 2);
+  const int C32 = contract_chunk32(M, P, ctx->n14, ctx->S1, g_contract_budget);
   const int C64 = contract_chunk(M, P, ctx->n14, ctx->S1, g_contract_budget);
   cudaStream_t s = ctx->stream;
   const int MP = M * P, nm = ctx->S1 * ctx->S2, nX = ctx->n14, S1 = ctx->S1, S2 = ctx->S2;

@@ -108,6 +108,16 @@ int contract_chunk(int M, int P, int nX, int S1, size_t budget_bytes) {
   return (int)std::max<long long>(1, std::min<long long>({c, (long long)M * P, cap}));
 }
 
+// Pairs per chunk of the FP32 contraction (8-byte W and T values): whole
+// incidences (multiples of P) where the budget holds one, so that the
+// Khatri-Rao tiles share each z_p read among several incidences.
+int contract_chunk32(int M, int P, int nX, int S1, size_t budget_bytes) {
+  const size_t per = 8 * ((size_t)nX * nX + (size_t)nX * S1);
+  long long c = std::min<long long>({(long long)(budget_bytes / per), (long long)M * P, 32768});
+  if (c >= P) c -= c % P;
+  return (int)std::max<long long>(1, c);
+}
+
 // J[(d,p)][m1][m2] = k2 sum_gy sy[m2][gy] sum_gx sx[m1][gx] u_d[gy][gx] z_p[gy][gx],
 // in chunks of C pairs: W = the pairs' Khatri-Rao rows (C x nY x nX), then
 // T = W sx^T over gx (rows (pair, gy), one GEMM), then J_pair = T_pair^T sy^T
@@ -214,25 +224,40 @@ void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P
 // once each and accumulate in FP64, so that they stay exact transposes of one
 // operator (products computed from the fields with independent FP32 rounding
 // are not, and the bidiagonalisation amplifies that mismatch).
-// W[c - c0][g] for the nc pairs from c0: each thread takes one grid point g and
-// KR_PAIRS consecutive pairs, reading u_d(g) once per incidence it meets (pairs
-// are d-major) instead of once per pair.
-constexpr int KR_PAIRS = 16;
+// W[c - c0][g] = u_d(g) z_p(g) for the pairs c = d P + p in [c0, c0 + nc):
+// each thread takes one grid point g and a tile of KR_DT incidences x KR_PT
+// receivers, so that every field value it reads serves several pairs (6
+// bytes read per 8-byte output for whole tiles, against 16 when each pair
+// reads its own z_p).  The products are taken in FP32 from the rounded
+// factors: |u z| = |u| |z| for complex numbers, so each output stays within a
+// few FP32 roundings of the exact product.
+constexpr int KR_DT = 4, KR_PT = 8;
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
 __global__ void k_khatri_rao32(const double2* __restrict__ Ug, const double2* __restrict__ Zg, int P,
-                               long long plane, long long c0, int nc, float2* __restrict__ W) {
+                               long long plane, long long c0, int nc, int ptiles, float2* __restrict__ W) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= plane) return;
-  const int j0 = blockIdx.y * KR_PAIRS, j1 = min(nc, j0 + KR_PAIRS);
-  long long dprev = -1;
-  double2 u = make_double2(0.0, 0.0);
-  for (int j = j0; j < j1; ++j) {
-    const long long c = c0 + j, d = c / P, p = c % P;
-    if (d != dprev) {
-      u = Ug[d * plane + g];
-      dprev = d;
+  const long long d0 = c0 / P + (long long)(blockIdx.y / ptiles) * KR_DT;
+  const int p0 = (int)(blockIdx.y % ptiles) * KR_PT;
+  const long long cend = c0 + nc;
+  float2 z[KR_PT];
+#pragma unroll
+  for (int i = 0; i < KR_PT; ++i)
+    z[i] = p0 + i < P ? to_f2(Zg[(long long)(p0 + i) * plane + g]) : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int a = 0; a < KR_DT; ++a) {
+    const long long cd = (d0 + a) * P;  // pair index of (d0 + a, 0)
+    if (cd + p0 >= cend) break;         // pairs grow with d: the rest lie beyond the chunk
+    if (cd + min(p0 + KR_PT, P) <= c0) continue;
+    const float2 u = to_f2(Ug[(d0 + a) * plane + g]);
+#pragma unroll
+    for (int i = 0; i < KR_PT; ++i) {
+      const long long c = cd + p0 + i;
+      if (p0 + i < P && c >= c0 && c < cend)
+        W[(c - c0) * plane + g] =
+            make_float2(fmaf(u.x, z[i].x, -u.y * z[i].y), fmaf(u.x, z[i].y, u.y * z[i].x));
     }
-    const double2 z = Zg[p * plane + g];
-    W[(long long)j * plane + g] = make_float2((float)(u.x * z.x - u.y * z.y), (float)(u.x * z.y + u.y * z.x));
   }
 }
 
@@ -254,8 +279,10 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
   HS_COUNT_LAUNCH();
   for (long long c0 = 0; c0 < MP; c0 += C) {
     const int nc = (int)std::min<long long>(C, MP - c0);
-    k_khatri_rao32<<<dim3((unsigned)((plane + 255) / 256), (nc + KR_PAIRS - 1) / KR_PAIRS), 256, 0, s>>>(
-        Ug, Zg, P, plane, c0, nc, W);
+    const long long nd = (c0 + nc - 1) / P - c0 / P + 1;  // incidences the chunk meets
+    const int ptiles = (P + KR_PT - 1) / KR_PT;
+    k_khatri_rao32<<<dim3((unsigned)((plane + 255) / 256), (unsigned)((nd + KR_DT - 1) / KR_DT * ptiles)), 256, 0,
+                     s>>>(Ug, Zg, P, plane, c0, nc, ptiles, W);
     HS_COUNT_LAUNCH();
     gemm<float2, float, float2>(s, OP_N, OP_N, nc * nX, S1, nX, make_float2(1.f, 0.f), W, nX, 0, sxr, S1, 0,
                                 make_float2(0.f, 0.f), T, S1, 0, 1);
@@ -264,22 +291,56 @@ void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, i
   }
 }
 
-// y[r] = sum_m J[r][m] v[m]  (complex J in FP32, real v, FP64 sums; one warp per row)
-// y[r] = sum_m J[r][m] v[m] (J complex FP32 or FP64, v real, FP64 sums): one
-// warp per row.
-template <typename TJ>
-__global__ void k_gemv(const TJ* __restrict__ J, const double* __restrict__ v, long long rows, int n,
-                       double2* __restrict__ y) {
+// Products with the FP32 Jacobian, in FP64 FMAs: LSQR needs J v and J^H u to
+// be transposes of one operator to FP64 rounding (a mismatch of 1e-13, as
+// double-FP32 sums leave, grew to 7e-4 in the iterate within 20 steps at
+// k = 40).  GB300 issues FP64 at 1/64 of the FP32 rate and the FP32 -> FP64
+// conversion runs on the same pipe, so the entries of J are widened in
+// integer arithmetic instead: sign kept, exponent rebiased by 1023 - 127,
+// mantissa shifted into place; subnormals normalised by their leading zeros;
+// zero, infinities and NaN mapped to theirs.  Exact for every FP32 value.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  const int lz = __clz(m) - 8;  // subnormal: shifts that bring the leading 1 to bit 23
+  unsigned long long ex, man = (unsigned long long)m << 29;
+  if (e == 0) {
+    ex = m ? (unsigned long long)(897 - lz) : 0ull;
+    man = m ? (unsigned long long)((m << lz) & 0x7fffffu) << 29 : 0ull;
+  } else {
+    ex = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896);
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | (ex << 52) | man));
+}
+
+// y[r] = sum_m J[r][m] v[m] for complex FP32 J and real v: one warp per row,
+// four elements in flight per lane.
+__global__ void k_gemv32(const float2* __restrict__ J, const double* __restrict__ v, long long rows, int n,
+                         double2* __restrict__ y) {
   const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
-  const TJ* row = J + r * n;
+  const float2* row = J + r * n;
   double ax = 0.0, ay = 0.0;
-  for (int m = lane; m < n; m += 32) {
-    const TJ a = row[m];
+  int m = lane;
+  for (; m + 96 < n; m += 128) {
+    float2 a[4];
+    double w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = row[m + 32 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = v[m + 32 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      ax = fma(f2d_int(a[i].x), w[i], ax);
+      ay = fma(f2d_int(a[i].y), w[i], ay);
+    }
+  }
+  for (; m < n; m += 32) {
+    const float2 a = row[m];
     const double w = v[m];
-    ax = fma((double)a.x, w, ax);
-    ay = fma((double)a.y, w, ay);
+    ax = fma(f2d_int(a.x), w, ax);
+    ay = fma(f2d_int(a.y), w, ay);
   }
   for (int o = 16; o > 0; o >>= 1) {
     ax += __shfl_down_sync(0xffffffffu, ax, o);
@@ -288,21 +349,73 @@ __global__ void k_gemv(const TJ* __restrict__ J, const double* __restrict__ v, l
   if (lane == 0) y[r] = make_double2(ax, ay);
 }
 
-// part[b][m] = sum over rows r of block b of Re(conj(J[r][m]) u[r])  (FP64 sums)
+// part[b][m] = sum over rows r of block b of Re(conj(J[r][m]) u[r]) for complex
+// FP32 J: one column per thread, four rows in flight.
 constexpr int kRowsPerPart = 256;
-template <typename TJ>
-__global__ void k_gemvT(const TJ* __restrict__ J, const double2* __restrict__ u, long long rows, int n,
-                        double* __restrict__ part) {
+__global__ void __launch_bounds__(128) k_gemvT32(const float2* __restrict__ J, const double2* __restrict__ u,
+                                                 long long rows, int n, double* __restrict__ part) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  const long long r0 = (long long)blockIdx.y * kRowsPerPart;
+  const int nr = rows - r0 < kRowsPerPart ? (int)(rows - r0) : kRowsPerPart;
+  const float2* col = J + r0 * n + m;
+  const double2* ub = u + r0;
+  double acc = 0.0;
+  int i = 0;
+  for (; i + 3 < nr; i += 4) {
+    float2 a[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a[t] = col[(long long)(i + t) * n];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const double2 w = ub[i + t];
+      acc = fma(f2d_int(a[t].x), w.x, acc);
+      acc = fma(f2d_int(a[t].y), w.y, acc);
+    }
+  }
+  for (; i < nr; ++i) {
+    const float2 a = col[(long long)i * n];
+    const double2 w = ub[i];
+    acc = fma(f2d_int(a.x), w.x, acc);
+    acc = fma(f2d_int(a.y), w.y, acc);
+  }
+  part[(long long)blockIdx.y * n + m] = acc;
+}
+
+// The same two products on an FP64 Jacobian, in FP64: one warp per row for
+// y = J v; part[b][m] as above.
+__global__ void k_gemv64(const double2* __restrict__ J, const double* __restrict__ v, long long rows, int n,
+                         double2* __restrict__ y) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const double2* row = J + r * n;
+  double ax = 0.0, ay = 0.0;
+  for (int m = lane; m < n; m += 32) {
+    const double2 a = row[m];
+    const double w = v[m];
+    ax = fma(a.x, w, ax);
+    ay = fma(a.y, w, ay);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_down_sync(0xffffffffu, ax, o);
+    ay += __shfl_down_sync(0xffffffffu, ay, o);
+  }
+  if (lane == 0) y[r] = make_double2(ax, ay);
+}
+
+__global__ void k_gemvT64(const double2* __restrict__ J, const double2* __restrict__ u, long long rows, int n,
+                          double* __restrict__ part) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const long long r0 = (long long)blockIdx.y * kRowsPerPart;
   if (m >= n) return;
   const long long r1 = min(rows, r0 + kRowsPerPart);
   double acc = 0.0;
   for (long long r = r0; r < r1; ++r) {
-    const TJ a = J[r * n + m];
+    const double2 a = J[r * n + m];
     const double2 b = u[r];
-    acc = fma((double)a.x, b.x, acc);
-    acc = fma((double)a.y, b.y, acc);
+    acc = fma(a.x, b.x, acc);
+    acc = fma(a.y, b.y, acc);
   }
   part[(long long)blockIdx.y * n + m] = acc;
 }
@@ -317,32 +430,27 @@ __global__ void k_sum_rows(const double* __restrict__ part, int nparts, int n, d
 
 int gemvT_parts(long long rows) { return (int)((rows + kRowsPerPart - 1) / kRowsPerPart); }
 
-template <typename TJ> void gemv_j(cudaStream_t s, const TJ* J, long long rows, int n, const double* v, double2* y) {
-  const long long threads = rows * 32;
-  k_gemv<TJ><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(J, v, rows, n, y);
+void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double* v, double2* y) {
+  k_gemv32<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(J, v, rows, n, y);
   HS_COUNT_LAUNCH();
 }
-
-template <typename TJ>
-void gemvT_j(cudaStream_t s, const TJ* J, long long rows, int n, const double2* u, double* part, double* g) {
+void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g) {
   const int np = gemvT_parts(rows);
-  k_gemvT<TJ><<<dim3((n + 127) / 128, np), 128, 0, s>>>(J, u, rows, n, part);
+  k_gemvT32<<<dim3((n + 127) / 128, np), 128, 0, s>>>(J, u, rows, n, part);
   HS_COUNT_LAUNCH();
   k_sum_rows<<<(n + 255) / 256, 256, 0, s>>>(part, np, n, g);
   HS_COUNT_LAUNCH();
 }
-
-void gemv32(cudaStream_t s, const float2* J, long long rows, int n, const double* v, double2* y) {
-  gemv_j<float2>(s, J, rows, n, v, y);
-}
-void gemvT32(cudaStream_t s, const float2* J, long long rows, int n, const double2* u, double* part, double* g) {
-  gemvT_j<float2>(s, J, rows, n, u, part, g);
-}
 void gemv64(cudaStream_t s, const double2* J, long long rows, int n, const double* v, double2* y) {
-  gemv_j<double2>(s, J, rows, n, v, y);
+  k_gemv64<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(J, v, rows, n, y);
+  HS_COUNT_LAUNCH();
 }
 void gemvT64(cudaStream_t s, const double2* J, long long rows, int n, const double2* u, double* part, double* g) {
-  gemvT_j<double2>(s, J, rows, n, u, part, g);
+  const int np = gemvT_parts(rows);
+  k_gemvT64<<<dim3((n + 127) / 128, np), 128, 0, s>>>(J, u, rows, n, part);
+  HS_COUNT_LAUNCH();
+  k_sum_rows<<<(n + 255) / 256, 256, 0, s>>>(part, np, n, g);
+  HS_COUNT_LAUNCH();
 }
 
 // Jst = [Re J; Im J] (2 rows x cols, real).

@@ -276,31 +276,24 @@ __global__ void k_stack_ext(const double2* __restrict__ Dm, const double2* __res
 }
 
 // out[0] += sum |a|^2 (FP32 data, FP64 sums)
-__global__ void k_norm2_32(const float2* __restrict__ a, long long n, double* __restrict__ out) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// out += sum |a|^2: a grid of a few blocks per SM strides over a, each block
+// reduces its threads' FP64 partial sums and adds them with one atomic (an
+// atomic per warp serialised on the one address for fields of 3e7 values).
+constexpr int kNormBlocks = 4 * 152;
+__global__ void __launch_bounds__(256) k_norm2_32(const float2* __restrict__ a, long long n, double* __restrict__ out) {
+  __shared__ double red[8];
   double v = 0.0;
-  if (i < n) v = (double)a[i].x * a[i].x + (double)a[i].y * a[i].y;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 x = a[i];
+    v += (double)x.x * x.x + (double)x.y * x.y;
+  }
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, v);
-}
-
-// out[0] += sum |a - b|^2, out[1] += sum |a|^2
-__global__ void k_diff_norms(const double2* __restrict__ a, const double2* __restrict__ b, long long n,
-                             double* __restrict__ out) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double d = 0.0, v = 0.0;
-  if (i < n) {
-    double2 x = a[i], y = b[i];
-    d = (x.x - y.x) * (x.x - y.x) + (x.y - y.y) * (x.y - y.y);
-    v = x.x * x.x + x.y * x.y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    d += __shfl_down_sync(0xffffffffu, d, o);
-    v += __shfl_down_sync(0xffffffffu, v, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(out, d);
-    atomicAdd(out + 1, v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(out, v);
   }
 }
 
@@ -456,11 +449,6 @@ void iface_adj_add(cudaStream_t s, const float2* MU, int nbox, int ni, int nrhs,
   HS_COUNT_LAUNCH();
 }
 
-void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out) {
-  k_diff_norms<<<blocks(n), 256, 0, s>>>(a, b, n, out);
-  HS_COUNT_LAUNCH();
-}
-
 void convert_d2f(cudaStream_t s, const double2* a, float2* b, long long n) {
   k_d2f<<<blocks(n), 256, 0, s>>>(a, b, n);
   HS_COUNT_LAUNCH();
@@ -542,7 +530,8 @@ void stack_exterior(cudaStream_t s, const double2* Dm, const double2* S, int nb,
 }
 
 void norm2_32(cudaStream_t s, const float2* a, long long n, double* out) {
-  k_norm2_32<<<blocks(n), 256, 0, s>>>(a, n, out);
+  if (n <= 0) return;
+  k_norm2_32<<<(unsigned)std::min<long long>(kNormBlocks, (n + 255) / 256), 256, 0, s>>>(a, n, out);
   HS_COUNT_LAUNCH();
 }
 

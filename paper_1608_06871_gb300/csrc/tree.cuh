@@ -143,9 +143,11 @@ void apply_J(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P,
 void apply_JH(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
               const double* sy, int S1, int S2, double k2, const double2* f, double2* fc, double2* Zmix, double* h,
               double* T1, double* g);
-// Explicit complex FP32 Jacobian on the tensor cores (W: C nX^2, T: C nX S1 values;
-// sxc: nX S1, sy32: nX S2), and its products with FP64 sums: y = J v (rows complex
-// outputs, real v) and g = Re(J^H u) (part: gemvT_parts(rows) * n doubles).
+// Explicit complex FP32 Jacobian (W: C nX^2, T: C nX S1 values; sxc: nX S1, sy32:
+// nX S2; C from contract_chunk32), and its products with FP64 sums: y = J v
+// (rows complex outputs, real v) and g = Re(J^H u) (part: gemvT_parts(rows) * n
+// doubles).
+int contract_chunk32(int M, int P, int nX, int S1, size_t budget_bytes);
 void contract_jacobian32(cudaStream_t s, const double2* Ug, const double2* Zg, int M, int P, int nX, const double* sx,
                          const double* sy, int S1, int S2, double k2, float2* J, float2* sxc, float* sy32, float2* W,
                          float2* T, int C);
@@ -182,7 +184,6 @@ void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, co
                      float2* H, float2* tmp, float2* wtmp);
 void scattered_data(cudaStream_t s, const double2* ub, const double2* psib, const double2* ui, const double2* dni,
                     long long n, double2* PS);
-void diff_norms(cudaStream_t s, const double2* a, const double2* b, long long n, double* out);  // out += {|a-b|^2, |a|^2}
 // FP32 scattered boundary data [u (- u_inc); d_n u (- d_n u_inc)] of an FP32 leaf field, and out += |a|^2.
 void scattered32(cudaStream_t s, const float2* U32, const double* D1, int nL, double h, int nrhs, const double2* ui,
                  const double2* dni, bool sub_inc, float2* PS);

@@ -205,3 +205,39 @@ def test_mixed_direct_gn_step_k40(hs):
     (c64, r64), (cmx, rmx) = out[hs.HS_FP64], out[hs.HS_MIXED]
     assert abs(rmx - r64) <= 1e-8 * r64
     assert rel(cmx - c, c64 - c) < 1e-7
+
+
+@pytest.mark.parametrize("rows,n", [(5, 3), (257, 130), (3001, 4099)])
+def test_fp32_jacobian_products(hs, rows, n):
+    """The products LSQR applies to the FP32 Jacobian (y = J v, g = Re(J^H u)) widen J's
+    entries exactly to FP64 and sum in FP64: within 1e-12 of numpy's FP64 products of the
+    same FP32 J, entry by entry relative to |J| |v| and |J|^T |u| (both sides' FP64 sums are
+    good to ~n 2^-53; FP32 or double-FP32 sums are off by 1e-13 .. 1e-7 and a wrong exponent
+    or mantissa in the widening by O(1)), and transposes of one another: Re <J v, u> = <v, g>
+    to the same level.  J holds exact zeros, FP32 subnormals and entries up to 1e30."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(rows + n)
+    J = (rng.standard_normal((rows, n)) + 1j * rng.standard_normal((rows, n)))
+    J *= 10.0 ** rng.uniform(-3, 3, (rows, 1)) * 10.0 ** rng.uniform(-3, 3, (1, n))
+    J = J.astype(np.complex64)
+    flat = J.reshape(-1)
+    pick = rng.choice(flat.size, size=min(flat.size, 64), replace=False)
+    special = np.array([0.0, -0.0, 1e-40, -3e-42, 1.4e-45, 1.1754942e-38, 1e30, -2e29], dtype=np.float32)
+    flat.real[pick] = special[np.arange(pick.size) % special.size]
+    flat.imag[pick[::-1]] = special[np.arange(pick.size) % special.size]
+    v = rng.standard_normal(n) * 10.0 ** rng.uniform(-4, 0, n)
+    u = rng.standard_normal(rows) + 1j * rng.standard_normal(rows)
+    dJ = torch.from_numpy(J).cuda()
+    dv = torch.from_numpy(v).cuda()
+    du = torch.from_numpy(u).cuda()
+    dy = torch.empty(rows, dtype=torch.complex128, device="cuda")
+    dg = torch.empty(n, dtype=torch.float64, device="cuda")
+    hs.hs_jacobian32_products(dJ, dv, dy, du, dg)
+    J64 = J.astype(np.complex128)
+    y, g = dy.cpu().numpy(), dg.cpu().numpy()
+    y_ref, g_ref = J64 @ v, (J64.conj().T @ u).real
+    aJ = np.abs(J64)
+    assert np.all(np.abs(y - y_ref) <= 1e-12 * (aJ @ np.abs(v)))
+    assert np.all(np.abs(g - g_ref) <= 1e-12 * (aJ.T @ np.abs(u)))
+    lhs, rhs = np.vdot(u, y).real, v @ g
+    assert abs(lhs - rhs) <= 1e-12 * (np.abs(v) @ (aJ.T @ np.abs(u)))

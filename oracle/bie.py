@@ -11,6 +11,15 @@ and, on the boundary, the jump relations give (D - I/2) u_s = S d_n u_s.  The
 same representation evaluated at x_p = R (cos theta_p, sin theta_p) gives the
 measured field u_far(theta_p) of Sec. 1 (eq. farfielddef).
 
+That identity alone is singular where k^2 is a Dirichlet eigenvalue of the
+square (S has a null space there).  Its normal derivative, with
+K' phi(x) = int d/dn_x G phi ds_y and T = d/dn_x D, is T u_s = (K' + I/2) d_n u_s;
+the Burton-Miller combination of the two with coupling alpha = i eta / k
+(exterior_rows, eta > 0) is uniquely solvable at every k > 0 (the reading of
+the combined-field exterior used here).  T comes from Maue's identity,
+T phi = d/dt_x S(d phi/dt) + k^2 n_x . S(n phi), with the tangential
+derivative of S integrated as a principal value on the target's own panel.
+
 Discretisation (a reading: the paper gives none): the boundary panels are the
 leaf edges lying on the boundary; each carries the 14 interior
 Chebyshev-Lobatto nodes of its leaf edge.  Densities are represented by their
@@ -27,7 +36,7 @@ from dataclasses import dataclass
 import numpy as np
 from scipy.special import hankel1
 
-from .spectral import gauss_legendre, interp_quad_weights, lagrange_eval, lobatto_nodes
+from .spectral import diff_matrix, gauss_legendre, interp_quad_weights, lagrange_eval, lobatto_nodes
 
 P_LEAF = 16            # Chebyshev-Lobatto points per leaf side
 GRADE_LEVELS = 56      # dyadic levels toward the nearest point (2^-56 ~ 1.4e-17)
@@ -162,6 +171,100 @@ def layer_matrices(bd: Boundary, k: float):
             S[i, q * npn:(q + 1) * npn] = ws
             Dm[i, q * npn:(q + 1) * npn] = wd
     return S, Dm
+
+
+def ccw_sign(bd: Boundary) -> np.ndarray:
+    """+1 where a panel's tangent runs counter-clockwise around Omega (tangent = normal turned
+    by +90 degrees), -1 where it runs the other way (north and west sides)."""
+    ccw = np.stack([-bd.normal[:, 1], bd.normal[:, 0]], axis=-1)
+    return np.sign(np.sum(ccw * bd.tangent, axis=-1))
+
+
+def normal_tangent_matrices(bd: Boundary, k: float):
+    """Nystrom matrices of the kernels d/dn_x G and d/dt_x G (t_x the counter-clockwise tangent at
+    the target), on the same panels and near rule as layer_matrices.
+
+    K'[i, j] ~ int dG/dn_x(x_i, y) L_j(y) ds_y: zero on the target's own side (the side is
+    straight).  H[i, j] ~ PV int dG/dt_x(x_i, y) L_j(y) ds_y: on the target's own panel the kernel
+    is -sgn/(2 pi (s_x - s)) plus a remainder with a logarithmic singularity; the Cauchy part is
+    integrated in closed form, PV int_0^h f(s)/(s_x - s) ds = f(s_x) log(s_x / (h - s_x))
+    + int_0^h (f(s) - f(s_x)) / (s_x - s) ds (the last integrand a polynomial: Gauss-Legendre),
+    and the remainder by the graded rule.
+    """
+    X = bd.nodes
+    n = len(X)
+    sgn = ccw_sign(bd)
+    tx = np.repeat(sgn[:, None] * bd.tangent, len(bd.t), axis=0)  # counter-clockwise tangents
+    d = X[:, None, :] - X[None, :, :]
+    r = np.linalg.norm(d, axis=-1)
+    np.fill_diagonal(r, 1.0)
+    h1 = -0.25j * k * hankel1(1, k * r) / r * bd.node_weight[None, :]
+    Kp = h1 * np.sum(d * bd.node_normal[:, None, :], axis=-1)
+    H = h1 * np.sum(d * tx[:, None, :], axis=-1)
+    np.fill_diagonal(Kp, 0.0)
+    np.fill_diagonal(H, 0.0)
+    npn = len(bd.t)
+    near = near_panels(bd)
+    xg, wg = gauss_legendre(GRADE_GL)
+    for i in range(n):
+        p = bd.panel_of[i]
+        nx, txi = bd.node_normal[i], tx[i]
+        for q in near[p]:
+            y0, tau = bd.start[q], bd.tangent[q]
+            s_star = float(np.clip(np.dot(X[i] - y0, tau), 0.0, bd.h))
+            sig, w = _graded_rule(bd.h, s_star)
+            perp = X[i] - (y0 + s_star * tau)
+            dvec = perp[None, :] - sig[:, None] * tau[None, :]
+            rr = np.sqrt(np.sum(dvec * dvec, axis=-1))
+            L = lagrange_eval(bd.t, 2.0 * (s_star + sig) / bd.h - 1.0)
+            base = -0.25j * k * hankel1(1, k * rr) / rr * w
+            Kp[i, q * npn:(q + 1) * npn] = (base * (dvec @ nx)) @ L
+            kt = base * (dvec @ txi)
+            if q == p:  # own panel: subtract the Cauchy part, sgn * (-1 / (2 pi (s_x - s)))
+                s_x = s_star
+                delta = -sig                                   # s_x - s
+                kt = kt - sgn[p] * (-1.0 / (2.0 * np.pi * delta)) * w
+                hv = kt @ L
+                # closed-form principal value of the Cauchy part against each L_j
+                sg = 0.5 * bd.h * (xg + 1.0)                   # Gauss-Legendre on [0, h]
+                wgs = 0.5 * bd.h * wg
+                Lg = lagrange_eval(bd.t, 2.0 * sg / bd.h - 1.0)       # (16, 14)
+                Lx = lagrange_eval(bd.t, np.array([2.0 * s_x / bd.h - 1.0]))[0]  # (14,)
+                pv = Lx * np.log(s_x / (bd.h - s_x)) + ((Lg - Lx[None, :]) / (s_x - sg)[:, None]).T @ wgs
+                H[i, q * npn:(q + 1) * npn] = hv + sgn[p] * (-1.0 / (2.0 * np.pi)) * pv
+            else:
+                H[i, q * npn:(q + 1) * npn] = kt @ L
+    return Kp, H
+
+
+def hypersingular_matrix(bd: Boundary, k: float, S: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """T = d/dn_x D (the normal derivative of the double layer) by Maue's identity,
+    T phi = d/dt_x S (d phi / dt) + k^2 n_x . S (n phi), with d/dt the counter-clockwise
+    tangential derivative: H (d/dt_x S, from normal_tangent_matrices) times the panel-wise
+    differentiation of phi's degree-13 interpolant."""
+    sgn = ccw_sign(bd)
+    Dref = diff_matrix(bd.t) * (2.0 / bd.h)
+    Dt = np.kron(np.diag(sgn), Dref)
+    Nx, Ny = bd.node_normal[:, 0], bd.node_normal[:, 1]
+    return H @ Dt + k * k * (Nx[:, None] * S * Nx[None, :] + Ny[:, None] * S * Ny[None, :])
+
+
+def exterior_rows(bd: Boundary, k: float, S: np.ndarray, Dl: np.ndarray, eta: float = 0.0):
+    """(A_u, A_psi) of the exterior relation A_u u_s = A_psi d_n u_s on the boundary nodes.
+
+    eta = 0: Green's identity, (D - I/2) u_s = S d_n u_s (singular where k^2 is a Dirichlet
+    eigenvalue of the square).  eta > 0: the Burton-Miller combination of it with its normal
+    derivative T u_s = (K' + I/2) d_n u_s, coupling alpha = i eta / k:
+    (D - I/2 + alpha T) u_s = (S + alpha (K' + I/2)) d_n u_s, uniquely solvable at every k > 0.
+    """
+    I = np.eye(len(bd.nodes))
+    A_u, A_psi = Dl - 0.5 * I, S.copy()
+    if eta > 0.0:
+        alpha = 1j * eta / k
+        Kp, H = normal_tangent_matrices(bd, k)
+        A_u = A_u + alpha * hypersingular_matrix(bd, k, S, H)
+        A_psi = A_psi + alpha * (Kp + 0.5 * I)
+    return A_u, A_psi
 
 
 def receiver_points(thetas: np.ndarray, R: float) -> np.ndarray:

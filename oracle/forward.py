@@ -17,7 +17,10 @@ collocation system (see the package docstring):
   = 0 on beta's row (each normal derivative by its own leaf's spectral
   differentiation);
 * at every boundary node: psi = d_n u (leaf differentiation) and the exterior
-  identity applied to u_s = u - u_inc, d_n u_s = psi - d_n u_inc.
+  identity applied to u_s = u - u_inc, d_n u_s = psi - d_n u_inc: Green's
+  identity (eta = 0), or its Burton-Miller combination with the normal
+  derivative identity (eta > 0, bie.exterior_rows), which stays solvable at
+  the square's Dirichlet eigenvalues.
 
 Measured data (eq. farfielddef): u_s at x_p = R (cos theta_p, sin theta_p) by
 Green's representation from the boundary data.  Jacobian (Theorem 3.1, eq.
@@ -111,9 +114,10 @@ def boundary_leaf_nodes(grid: Grid) -> np.ndarray:
 class Forward:
     """Factored global system for one (q, k).  q_nodes: q at every leaf node, shape (n_L^2, 16, 16)."""
 
-    def __init__(self, k: float, n_leaf: int, q_nodes: np.ndarray, R: float = 3.0):
+    def __init__(self, k: float, n_leaf: int, q_nodes: np.ndarray, R: float = 3.0, eta: float = 0.0):
         self.k = float(k)
         self.R = float(R)
+        self.eta = float(eta)  # 0: Green's identity exterior rows; > 0: Burton-Miller, alpha = i eta / k
         self.grid = g = Grid(n_leaf)
         self.bd = bd = bie.make_boundary(n_leaf)
         self.q = np.asarray(q_nodes, dtype=np.float64).reshape(g.nleaves, P, P)
@@ -124,6 +128,7 @@ class Forward:
         self.nu = g.nleaves * P * P
         self.nb = len(self.bnodes)
         self.S, self.Dl = bie.layer_matrices(bd, self.k)
+        self.A_u, self.A_psi = bie.exterior_rows(bd, self.k, self.S, self.Dl, self.eta)
         self._assemble()
         self.lu = spla.splu(self.A.tocsc())
 
@@ -180,10 +185,9 @@ class Forward:
             cj, vj = _normal_row(g, leaf, a, b)
             add(nu + j, [nu + j], [1.0])
             add(nu + j, cj, -vj)
-        Dm = self.Dl - 0.5 * np.eye(nb)
         for i, gi in enumerate(self.bnodes):
-            add(int(gi), self.bnodes, Dm[i, :])
-            add(int(gi), nu + np.arange(nb), -self.S[i, :])
+            add(int(gi), self.bnodes, self.A_u[i, :])
+            add(int(gi), nu + np.arange(nb), -self.A_psi[i, :])
         n = nu + nb
         self.A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                shape=(n, n))
@@ -191,9 +195,8 @@ class Forward:
     # -- solves ---------------------------------------------------------------
     def solve_incident(self, ui_bd: np.ndarray, dni_bd: np.ndarray):
         """Total field for incident traces on the boundary nodes (columns = right-hand sides)."""
-        Dm = self.Dl - 0.5 * np.eye(self.nb)
         rhs = np.zeros((self.nu + self.nb, ui_bd.shape[1]), dtype=np.complex128)
-        rhs[self.bnodes, :] = Dm @ ui_bd - self.S @ dni_bd
+        rhs[self.bnodes, :] = self.A_u @ ui_bd - self.A_psi @ dni_bd
         return self.lu.solve(rhs)
 
     def split(self, sol: np.ndarray):
@@ -253,14 +256,14 @@ class Forward:
         return J
 
 
-def forward_from_coeffs(c: np.ndarray, k: float, n_leaf: int, R: float = 3.0) -> Forward:
+def forward_from_coeffs(c: np.ndarray, k: float, n_leaf: int, R: float = 3.0, eta: float = 0.0) -> Forward:
     g = Grid(n_leaf)
-    return Forward(k, n_leaf, sine_eval(c, g.X, g.Y), R)
+    return Forward(k, n_leaf, sine_eval(c, g.X, g.Y), R, eta)
 
 
-def forward_from_function(qfun, k: float, n_leaf: int, R: float = 3.0) -> Forward:
+def forward_from_function(qfun, k: float, n_leaf: int, R: float = 3.0, eta: float = 0.0) -> Forward:
     g = Grid(n_leaf)
-    return Forward(k, n_leaf, qfun(g.X, g.Y), R)
+    return Forward(k, n_leaf, qfun(g.X, g.Y), R, eta)
 
 
 def gn_step(J: np.ndarray, resid: np.ndarray, lam: float) -> np.ndarray:

@@ -102,6 +102,80 @@ def test_product_weights_match_quadpack():
                 assert abs(w[j] - (re + 1j * im)) < 1e-12, (q, j, kern)
 
 
+def test_normal_and_tangential_weights_match_quadpack():
+    """d/dn_x G and d/dt_x G panel weights (normal_tangent_matrices) against QUADPACK: the near
+    panels by adaptive quadrature with the singular point given, the target's own panel for the
+    tangential kernel as a Cauchy principal value (QAWC, weight 1/(s - s_x))."""
+    bd = bie.make_boundary(4)
+    k = K5
+    Kp, H = bie.normal_tangent_matrices(bd, k)
+    sgn = bie.ccw_sign(bd)
+    npn = len(bd.t)
+    for i in (3, 12, 9 * npn + 5):  # south side (two panels), north side (clockwise panel tangent)
+        x = bd.nodes[i]
+        p = bd.panel_of[i]
+        nx, tx = bd.node_normal[i], sgn[p] * bd.tangent[p]
+        for q in bie.near_panels(bd)[p]:  # the panels the product rule covers (own, same side, across a corner)
+            y0, tau = bd.start[q], bd.tangent[q]
+            s_x = float(np.clip((x - y0) @ tau, 0, bd.h))
+            for j in (0, 6, 13):
+                def f(s, part, kern, pv):
+                    d = x - (y0 + s * tau)
+                    r = math.hypot(*d)
+                    Lj = lagrange_eval(bd.t, np.array([2 * s / bd.h - 1]))[0, j]
+                    val = -0.25j * k * hankel1(1, k * r) * (d @ (nx if kern == "K'" else tx)) / r
+                    if pv:
+                        val = val * (s - s_x)  # QAWC divides by (s - s_x)
+                    return (val.real if part == 0 else val.imag) * Lj
+                for kern, M in (("K'", Kp), ("H", H)):
+                    got = M[i, q * npn + j]
+                    if q == p and kern == "K'":
+                        assert got == 0.0  # the side is straight: (x - y) . n_x = 0
+                        continue
+                    if q == p:
+                        kw = dict(weight="cauchy", wvar=s_x, limit=200, epsabs=1e-15, epsrel=1e-13)
+                        re = quad(f, 0, bd.h, args=(0, kern, True), **kw)[0]
+                        im = quad(f, 0, bd.h, args=(1, kern, True), **kw)[0]
+                    else:
+                        kw = dict(points=[s_x], limit=200, epsabs=1e-15, epsrel=1e-13)
+                        re = quad(f, 0, bd.h, args=(0, kern, False), **kw)[0]
+                        im = quad(f, 0, bd.h, args=(1, kern, False), **kw)[0]
+                    assert abs(got - (re + 1j * im)) < 1e-11, (i, q, j, kern, got, re + 1j * im)
+
+
+def test_normal_derivative_identity_for_radiating_source(fw_zero):
+    """T u = (K' + I/2) d_n u on the boundary (the normal derivative of Green's representation;
+    T by Maue's identity from the tangential-derivative kernel) for u = G(., x0), x0 in Omega:
+    pins T, K' and the tangent orientation at every node, the corner panels included."""
+    fw = fw_zero
+    Kp, H = bie.normal_tangent_matrices(fw.bd, K5)
+    T = bie.hypersingular_matrix(fw.bd, K5, fw.S, H)
+    for x0 in (np.array([[0.2, -0.3]]), np.array([[-0.5, 0.4]])):
+        ui, dni = fw.point_traces(x0)
+        res = T @ ui - (Kp + 0.5 * np.eye(fw.nb)) @ dni
+        assert np.abs(res).max() < 1e-7 * np.abs(dni).max()  # measured 5e-11 and 2e-8 (source 0.5 from the side)
+
+
+def test_combined_field_at_a_dirichlet_eigenvalue():
+    """At k^2 = (pi/2)^2 (1 + 4), a Dirichlet eigenvalue of [-1, 1]^2, Green's identity alone
+    leaves the exterior relation singular (far field off by O(1)); the Burton-Miller rows
+    (eta = 1) give the radial ODE reference to the discretisation error, and agree with the
+    Green rows at a regular k."""
+    sig, q0, alpha = 0.15, 0.3, 0.3
+    th = synth.receivers(12)
+    qf = lambda x, y: q0 * np.exp(-(x * x + y * y) / (2 * sig * sig))
+    k = 0.5 * math.pi * math.sqrt(5.0)
+    ref = CF.radial_scattered(k, lambda r: q0 * math.exp(-r * r / (2 * sig * sig)), 1.0, alpha, th, 3.0, nmax=30)
+    err = {}
+    for eta in (0.0, 1.0):
+        uf, _ = F.forward_from_function(qf, k, 8, eta=eta).solve_plane(np.array([alpha]), th)
+        err[eta] = np.abs(uf[0] - ref).max() / np.abs(ref).max()
+    assert err[1.0] < 2e-9 and err[0.0] > 1e-2, err
+    u0, _ = F.forward_from_function(qf, K5, 4).solve_plane(np.array([alpha]), th)
+    u1, _ = F.forward_from_function(qf, K5, 4, eta=1.0).solve_plane(np.array([alpha]), th)
+    assert np.abs(u1 - u0).max() < 1e-7 * np.abs(u0).max()
+
+
 def test_green_identity_for_radiating_source(fw_zero):
     """(D - I/2) u = S d_n u on the boundary, and Green's representation at R, for u = G(., x0), x0 in Omega."""
     fw = fw_zero

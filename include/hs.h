@@ -59,6 +59,12 @@ typedef struct hs_config {
                            far field (last update x rho/(1-rho), rho the observed
                            contraction per pass) is below this (default 1e-9)       */
   int refine_max_iter;  /* HS_MIXED: maximum refinement sweeps (default 8 if <= 0)  */
+  double bm_eta;        /* exterior rows on the boundary (Sec. 2, Remark): 0 = Green's
+                           identity (D - I/2) u_s = S d_n u_s, singular where k^2 is a
+                           Dirichlet eigenvalue of the square; > 0 = its Burton-Miller
+                           combination with the normal-derivative identity
+                           T u_s = (K' + I/2) d_n u_s, coupling i bm_eta / k, solvable
+                           at every k (1 is the usual choice); < 0 or NaN: HS_EINVAL */
 } hs_config;
 
 /* Create a context on cfg->device (copies cfg).  Allocates nothing large until

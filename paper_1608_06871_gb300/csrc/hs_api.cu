@@ -168,6 +168,7 @@ struct hs_ctx {
   std::vector<Level> levels;
   Boundary B{};
   double2 *d_S = nullptr, *d_Dm = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_C = nullptr;
+  double2 *d_Kp = nullptr, *d_Ht = nullptr;  // combined-field scratch (cfg.bm_eta > 0)
   int* d_Cpiv = nullptr;
   const double2* Rroot = nullptr;
   double* d_D1 = nullptr;  // Chebyshev-Lobatto differentiation matrix (device copy)
@@ -672,13 +673,18 @@ int setup_boundary(hs_ctx* ctx) {
       if (l != j) p *= (tin[j] - tin[l]);
     lagden[j] = p;
   }
-  upload_quad_constants(glx.data(), glw.data(), tin.data(), lagden.data(), ctx->stream);
+  std::vector<double> dref = diff_matrix(tin);  // panel-node differentiation, [l][j] = L_j'(t_l)
+  upload_quad_constants(glx.data(), glw.data(), tin.data(), lagden.data(), dref.data(), ctx->stream);
   std::vector<double> D1 = diff_matrix(t);
   upload_cheb_diff(D1.data(), ctx->stream);
   // root system
   const size_t nn = (size_t)nb * nb;
   CKR(dalloc(ctx, &ctx->d_S, nn));
   CKR(dalloc(ctx, &ctx->d_Dm, nn));
+  if (ctx->cfg.bm_eta > 0.0) {  // K' and the tangential derivative of S for the combined-field rows
+    CKR(dalloc(ctx, &ctx->d_Kp, nn));
+    CKR(dalloc(ctx, &ctx->d_Ht, nn));
+  }
   CKR(dalloc(ctx, &ctx->d_B1, nn));
   CKR(dalloc(ctx, &ctx->d_B2, nn));
   if (ctx->cfg.precision == HS_FP64) {
@@ -782,6 +788,7 @@ void assemble_exterior_mixed(hs_ctx* ctx, cudaStream_t s, double k) {
   const int nb = ctx->B.nb;
   const long long nn = (long long)nb * nb;
   bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
+  if (ctx->cfg.bm_eta > 0.0) bie_combined(s, ctx->B, k, ctx->cfg.bm_eta, ctx->d_S, ctx->d_Dm, ctx->d_Kp, ctx->d_Ht);
   bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
   convert_d2f(s, ctx->d_B2, ctx->d_B2_32, nn);
   stack_exterior(s, ctx->d_Dm, ctx->d_S, nb, ctx->d_DS, ctx->d_DS32);
@@ -876,8 +883,9 @@ int factor(hs_ctx* ctx, double k) {
   const int nb = ctx->B.nb;
   permute_square<double2>(s, Rc, ctx->d_root_of_bie, nb, ctx->d_Rb);  // root map in boundary-node order
   ctx->Rroot = ctx->d_Rb;
-  if (ctx->bie_k != k) {  // S, D - I/2, B1, B2 depend on k and the boundary only
+  if (ctx->bie_k != k) {  // S, D - I/2 (or their combined-field forms), B1, B2 depend on k and the boundary only
     bie_matrices(s, ctx->B, k, ctx->d_S, ctx->d_Dm);
+    if (ctx->cfg.bm_eta > 0.0) bie_combined(s, ctx->B, k, ctx->cfg.bm_eta, ctx->d_S, ctx->d_Dm, ctx->d_Kp, ctx->d_Ht);
     bie_root_ops(s, nb, k, ctx->d_S, ctx->d_Dm, ctx->d_B1, ctx->d_B2);
     ctx->bie_k = k;
   }
@@ -1644,6 +1652,7 @@ int hs_create(hs_ctx** out, const hs_config* cfg) {
   if (cfg->S1 < 1 || cfg->S2 < 1 || cfg->S1 > 512 || cfg->S2 > 512) return HS_EINVAL;
   if (!(cfg->R > std::sqrt(2.0))) return HS_EINVAL;
   if (cfg->precision != HS_FP64 && cfg->precision != HS_MIXED) return HS_EINVAL;
+  if (!(cfg->bm_eta >= 0.0) || !std::isfinite(cfg->bm_eta)) return HS_EINVAL;
   hs_ctx* ctx = new (std::nothrow) hs_ctx();
   if (!ctx) return HS_ENOMEM;
   ctx->cfg = *cfg;

@@ -112,8 +112,12 @@ struct Boundary {
   int *near;                    // [npanel][5] near panels (-1 padded)
 };
 void upload_quad_constants(const double* gl_x, const double* gl_w, const double* tnodes, const double* lagden,
-                           cudaStream_t s);
+                           const double* dref, cudaStream_t s);
 void bie_matrices(cudaStream_t s, const Boundary& B, double k, double2* S, double2* Dl);
+// Burton-Miller rows in place: Dl += alpha T, S += alpha (K' + I/2), alpha = i eta / k
+// (Kp, H: nb x nb scratch for K' and the tangential derivative of S).
+void bie_combined(cudaStream_t s, const Boundary& B, double k, double eta, double2* S, double2* Dl, double2* Kp,
+                  double2* H);
 void bie_root_ops(cudaStream_t s, int nb, double eta, const double2* S, double2* Dm, double2* B1, double2* B2);
 void incident_plane(cudaStream_t s, const Boundary& B, double k, const double* alphas, int M, double2* ui,
                     double2* dni);

@@ -85,7 +85,7 @@ def square_safe(k: float, near: float = 0.002, window: float = 0.02, unit: float
 
 
 def plan_paper(k: float, R: float = 20.0, leaf_kh: float = 2.5, min_leaves: int = 4,
-               max_leaves: int = 128) -> FrequencyPlan:
+               max_leaves: int = 128, avoid_resonance: bool = True) -> FrequencyPlan:
     """The paper's experiment plan (Sec. 4) at its frequency k on its domain
     [-pi/2, pi/2]^2, read on [-1, 1]^2 by x = (pi/2) x_hat: the wavenumber becomes
     pi k / 2 and the receiver radius 2 R / pi (R = 20); M = floor(2k) incidences,
@@ -94,8 +94,10 @@ def plan_paper(k: float, R: float = 20.0, leaf_kh: float = 2.5, min_leaves: int 
     Leaves: the smallest power of two with (pi k / 2) h <= leaf_kh (h = 2 / n_L),
     which keeps the leaf Dirichlet blocks well away from resonance (the paper's
     own rule, 6-10 points per wavelength, is coarser).  Frequencies within 0.002
-    of the square's Dirichlet eigenvalues are moved off them (square_safe)."""
-    kh = math.pi * square_safe(k) / 2.0
+    of the square's Dirichlet eigenvalues are moved off them (square_safe), unless
+    avoid_resonance is False (for solvers with combined-field exterior rows,
+    bm_eta > 0, which are solvable there)."""
+    kh = math.pi * (square_safe(k) if avoid_resonance else k) / 2.0
     nl = max(min_leaves, 2 ** int(math.ceil(math.log2(max(2.0 * kh / leaf_kh, 1.0)))))
     S = int(math.floor(2.0 * k))
     return FrequencyPlan(kh, min(nl, max_leaves), max(S - 1, 1), int(math.floor(2.0 * k)),
@@ -116,14 +118,15 @@ def plan_table1(k: float, M: int = 64, R: float = 20.0) -> FrequencyPlan:
     return FrequencyPlan(math.pi * k / 2.0, nl, 1, M, M, 0, R=2.0 * R / math.pi, k_label=k)
 
 
-def plan_c5(k: float) -> FrequencyPlan:
+def plan_c5(k: float, avoid_resonance: bool = True) -> FrequencyPlan:
     """The paper-scale reconstruction plan on [-1, 1]^2: S = floor(2k) sine modes per axis
     (140 x 140 = 19,600 at k = 70), M = P = ceil(4k) (280 at k = 70), leaves
     2^min(7, max(2, ceil(log2(128 k / 70)))) (128 x 128 at the top), one Gauss-Newton step;
     frequencies within 0.002 of a Dirichlet eigenvalue of the square are moved off it
-    (square_safe with unit pi/2; the grid comes within 2e-5 of one at k = 40.75)."""
+    (square_safe with unit pi/2; the grid comes within 2e-5 of one at k = 40.75), unless
+    avoid_resonance is False (combined-field exterior rows)."""
     nl = 2 ** min(7, max(2, int(math.ceil(math.log2(128.0 * k / 70.0)))))
-    ks = square_safe(k, unit=math.pi / 2.0)
+    ks = square_safe(k, unit=math.pi / 2.0) if avoid_resonance else k
     return FrequencyPlan(ks, nl, int(math.floor(2.0 * k)), int(math.ceil(4.0 * k)), int(math.ceil(4.0 * k)), 1,
                          k_label=k)
 
@@ -152,7 +155,7 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
                             R: float | None = None, precision: int = HS_FP64, device: int = 0,
                             checkpoint_dir: str | None = None, angles=None, solver: str = "direct",
                             lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200,
-                            lsqr_products: int = HS_FP64) -> SweepResult:
+                            lsqr_products: int = HS_FP64, bm_eta: float = 0.0) -> SweepResult:
     """Run the sweep.
 
     plans:   list of FrequencyPlan with increasing k.
@@ -162,6 +165,8 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
              LSQR at lsqr_tol on the plan's modes, hs_gn_step_lsqr, products in lsqr_products).
     precision: HS_FP64, or HS_MIXED (FP32 factors; forward and adjoint fields refined in FP64).
     R:       receiver radius overriding the plans' own.
+    bm_eta:  exterior rows of every solver (hs_config.bm_eta): 0 Green's identity, > 0 the
+             combined-field rows, solvable at the square's Dirichlet eigenvalues.
     Each history entry records the build (factorisation) time t_f and the
     least-squares time t_l of every step in seconds, and the LSQR iterations.
     """
@@ -189,7 +194,7 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
             for old in solvers.values():
                 old.close()
             solvers.clear()  # one tree at a time keeps device memory bounded
-            solvers[key] = Solver(p.leaves_per_side, p.S, p.S, radius, precision, device)
+            solvers[key] = Solver(p.leaves_per_side, p.S, p.S, radius, precision, device, bm_eta=bm_eta)
         slv = solvers[key]
         al, th = angles(p)
         data = data_fn(p, al, th)

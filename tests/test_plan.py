@@ -73,3 +73,11 @@ def test_example1_contrast_is_outside_the_sine_band_near_the_boundary():
     assert int(p.mask().sum()) == 378
     assert out[1] > 0.1
     assert out[2] < 0.01
+
+
+def test_combined_field_plans_keep_the_paper_frequencies():
+    """With combined-field exterior rows (bm_eta > 0) the plans keep the resonant frequencies:
+    k = 5 on the paper's domain is pi k / 2 on [-1, 1]^2, where 5 = sqrt(3^2 + 4^2)."""
+    p = SW.plan_paper(5.0, avoid_resonance=False)
+    assert p.k == math.pi * 5.0 / 2.0 and SW.plan_paper(5.0).k != p.k
+    assert SW.plan_c5(40.75, avoid_resonance=False).k == 40.75

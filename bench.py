@@ -341,6 +341,65 @@ def time_arm(hs, torch, w, c, precision, args, world, local, prof_family, extra_
                 ufar=uf[..., 0] + 1j * uf[..., 1], u=u, alphas=alphas)
 
 
+def combined_field(hs, torch, local, w, c, ufar_green):
+    """The k = 40 forward step with combined-field exterior rows (bm_eta = 1) on a mixed context:
+    steady-state and cold-k step times beside the Green-identity arm, the far-field difference
+    between the two exterior forms at the workload's regular k, and the step at a Dirichlet
+    eigenvalue of the square next to it, k = (pi/2) sqrt(650) = 40.05, where Green's rows leave
+    the coupled system singular: refinement passes, and the combined rows' far field on mixed
+    and FP64 contexts."""
+    stream = torch.cuda.current_stream()
+    al = torch.tensor(synth.directions(w.M), device="cuda")
+    th = torch.tensor(synth.receivers(w.P), device="cuda")
+    uf = torch.empty((w.M, w.P, 2), dtype=torch.float64, device="cuda")
+    u = torch.empty((w.M, w.n_leaf_side ** 2, 256, 2), dtype=torch.float64, device="cuda")
+    out = {"bm_eta": 1.0, "workload": w.name, "precision": "mixed"}
+
+    def timed(ctx, k, reps):
+        ts = []
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            hs.hs_build(ctx, c, k)
+            hs.hs_forward_dev(ctx, al, th, uf, u)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            ts.append(e[0].elapsed_time(e[1]))
+        return ts
+
+    S = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED, device=local, stream=stream.cuda_stream, bm_eta=1.0)
+    timed(S.ctx, w.k, 3)
+    out["step_ms"] = float(np.median(timed(S.ctx, w.k, 5)))
+    out["solves_per_s"] = w.M / (out["step_ms"] * 1e-3)
+    out["cold_k_step_ms"] = float(np.median([timed(S.ctx, w.k + 1e-3 * (j + 1), 1)[0] for j in range(3)]))
+    timed(S.ctx, w.k, 1)
+    f = uf.cpu().numpy()
+    f = f[..., 0] + 1j * f[..., 1]
+    out["farfield_rel_diff_vs_green_rows"] = float(np.linalg.norm(f - ufar_green) / np.linalg.norm(ufar_green))
+    keig = 0.5 * math.pi * math.sqrt(650.0)
+    timed(S.ctx, keig, 1)
+    it, _, est = hs.hs_refine_stats(S.ctx)
+    fm = uf.cpu().numpy()
+    S.close()
+    S64 = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_FP64, device=local, stream=stream.cuda_stream, bm_eta=1.0)
+    timed(S64.ctx, keig, 1)
+    f64 = uf.cpu().numpy()
+    S64.close()
+    res = {"k": keig, "refine_passes": it, "est_rel_error": est,
+           "mixed_vs_fp64_farfield_rel_err": float(np.linalg.norm(fm - f64) / np.linalg.norm(f64))}
+    G = hs.Solver(w.n_leaf_side, w.S, w.S, w.R, hs.HS_MIXED, device=local, stream=stream.cuda_stream)
+    try:
+        timed(G.ctx, keig, 1)
+        it_g, upd_g, _ = hs.hs_refine_stats(G.ctx)
+        res["green_rows"] = {"refine_passes": it_g, "last_rel_update": upd_g}
+    except hs.HSError as e:
+        it_g, upd_g, _ = hs.hs_refine_stats(G.ctx)
+        res["green_rows"] = {"status": str(e).split(":")[0], "refine_passes": it_g, "last_rel_update": upd_g}
+    G.close()
+    out["at_dirichlet_eigenvalue"] = res
+    return out
+
+
 def run_hs(args, world, rank, local):
     import torch
 
@@ -401,6 +460,8 @@ def run_hs(args, world, rank, local):
         secondary["sweep_mixed_lsqr_k10_vs_fp64"] = sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=True,
                                                                compare_fp64=True)
         secondary["paper_table1"] = paper_table1(hs, torch, local, k_max=args.table1_kmax)
+        if prec == hs.HS_MIXED:
+            secondary["combined_field_k40"] = combined_field(hs, torch, local, w, c, main["ufar"])
         if args.table2 > 0:
             secondary["paper_table2"] = paper_table2(hs, torch, local, args.table2)
         if args.c5_sweep:

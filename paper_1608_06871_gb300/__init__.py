@@ -37,7 +37,7 @@ class hs_config(ctypes.Structure):
     _fields_ = [("R", ctypes.c_double), ("leaves_per_side", ctypes.c_int), ("S1", ctypes.c_int),
                 ("S2", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int),
-                ("bm_eta", ctypes.c_double)]
+                ("bm_eta", ctypes.c_double), ("leaf_impedance", ctypes.c_int)]
 
 
 _lib = None
@@ -123,8 +123,10 @@ def _check(ctx, code: int):
 
 # ---- C-ABI mirrors ------------------------------------------------------------
 def hs_create(leaves_per_side: int, S1: int, S2: int, R: float = 3.0, precision: int = HS_FP64, device: int = 0,
-              stream: int | None = None, refine_tol: float = 0.0, refine_max_iter: int = 0, bm_eta: float = 0.0):
-    cfg = hs_config(R, leaves_per_side, S1, S2, precision, device, stream, refine_tol, refine_max_iter, bm_eta)
+              stream: int | None = None, refine_tol: float = 0.0, refine_max_iter: int = 0, bm_eta: float = 0.0,
+              leaf_impedance: bool = False):
+    cfg = hs_config(R, leaves_per_side, S1, S2, precision, device, stream, refine_tol, refine_max_iter, bm_eta,
+                    1 if leaf_impedance else 0)
     ctx = _P()
     code = lib().hs_create(ctypes.byref(ctx), ctypes.byref(cfg))
     if code != HS_OK:
@@ -419,10 +421,10 @@ class Solver:
 
     def __init__(self, leaves_per_side: int, S1: int, S2: int, R: float = 3.0, precision: int = HS_FP64,
                  device: int = 0, stream: int | None = None, refine_tol: float = 0.0, refine_max_iter: int = 0,
-                 bm_eta: float = 0.0):
+                 bm_eta: float = 0.0, leaf_impedance: bool = False):
         self.nL, self.S1, self.S2, self.R = leaves_per_side, S1, S2, R
         self.ctx = hs_create(leaves_per_side, S1, S2, R, precision, device, stream, refine_tol, refine_max_iter,
-                             bm_eta)
+                             bm_eta, leaf_impedance)
 
     @property
     def n_nodes(self) -> int:

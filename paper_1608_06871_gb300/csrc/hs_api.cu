@@ -752,6 +752,11 @@ int setup(hs_ctx* ctx) {
     CKR(dalloc(ctx, &w.Kinv, ch * NE * NE));
     CKR(dalloc(ctx, &w.piv, ch * NI));
     CKR(dalloc(ctx, &w.pivK, ch * NE));
+    if (ctx->cfg.leaf_impedance) {
+      CKR(dalloc(ctx, &w.L, ch * NL * NL));
+      CKR(dalloc(ctx, &w.Et, ch * NL * NE));
+      CKR(dalloc(ctx, &w.pivL, ch * NL));
+    }
   } else {
     // every leaf's factors are kept: the refinement's particular solves reuse them
     CKR(dalloc(ctx, &ctx->d_R32, nl * NE * NE));
@@ -867,8 +872,13 @@ int factor(hs_ctx* ctx, double k) {
   Phase ph("hs_factor_fp64");
   for (int l0 = 0; l0 < ctx->nleaf; l0 += ctx->chunk) {
     int n = std::min(ctx->chunk, ctx->nleaf - l0);
-    leaf_build_chunk(s, ctx->d_q, l0, n, k, ctx->d_k, ctx->h, ctx->ws, ctx->d_Rleaf + (size_t)l0 * NE * NE,
-                     ctx->d_Y + (size_t)l0 * NL * NE, ctx->d_Q + (size_t)l0 * NI * NE, ctx->d_info);
+    if (ctx->cfg.leaf_impedance)
+      leaf_build_chunk_impedance(s, ctx->d_q, l0, n, k, ctx->d_k, ctx->h, ctx->ws,
+                                 ctx->d_Rleaf + (size_t)l0 * NE * NE, ctx->d_Y + (size_t)l0 * NL * NE,
+                                 ctx->d_Q + (size_t)l0 * NI * NE, ctx->d_info);
+    else
+      leaf_build_chunk(s, ctx->d_q, l0, n, k, ctx->d_k, ctx->h, ctx->ws, ctx->d_Rleaf + (size_t)l0 * NE * NE,
+                       ctx->d_Y + (size_t)l0 * NL * NE, ctx->d_Q + (size_t)l0 * NI * NE, ctx->d_info);
   }
   const double2* Rc = ctx->d_Rleaf;
   {
@@ -1653,6 +1663,7 @@ int hs_create(hs_ctx** out, const hs_config* cfg) {
   if (!(cfg->R > std::sqrt(2.0))) return HS_EINVAL;
   if (cfg->precision != HS_FP64 && cfg->precision != HS_MIXED) return HS_EINVAL;
   if (!(cfg->bm_eta >= 0.0) || !std::isfinite(cfg->bm_eta)) return HS_EINVAL;
+  if (cfg->leaf_impedance != 0 && (cfg->leaf_impedance != 1 || cfg->precision != HS_FP64)) return HS_EINVAL;
   hs_ctx* ctx = new (std::nothrow) hs_ctx();
   if (!ctx) return HS_ENOMEM;
   ctx->cfg = *cfg;

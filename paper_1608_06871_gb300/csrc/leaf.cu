@@ -216,6 +216,77 @@ void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, dou
                   Q, NE, (long long)NI * NE, nleaf);
 }
 
+// Impedance form of the leaf (FP64 contexts, hs_config.leaf_impedance): with the
+// incoming impedance f = d_n u + i eta u prescribed on the edge nodes,
+//   L [u_i; u_e] = [b; f],   L = [A_ii, A_ie; N_i, N_e + i eta I]   (252 x 252),
+// the interior impedance problem, uniquely solvable at every k, where the
+// Dirichlet block A_ii is singular at the leaf's Dirichlet eigenvalues
+// (k sqrt(1 - q) h = pi sqrt(a^2 + b^2)).  Its Schur complement on the edge is
+// K = N_e - N_i A_ii^{-1} A_ie + i eta I, so the outputs are the ones of the
+// Dirichlet route: the solution operator Y = L^{-1} [0; I] (Y_e = K^{-1},
+// Y_i = -X K^{-1}), R = I - 2 i eta Y_e, and the adjoint body-load operator
+// Q = -2 i eta (L^{-T} [0; I])_i (= 2 i eta A_ii^{-T} N_i^T K^{-T}).
+__global__ void k_leaf_L(const double* __restrict__ Aii, const double* __restrict__ Aie,
+                         const double* __restrict__ Ni, const double* __restrict__ Ne, const double* __restrict__ kp,
+                         double2* __restrict__ L, double2* __restrict__ Y, double2* __restrict__ Et, int nleaf) {
+  const double eta = *kp;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nleaf * NL * NL) return;
+  const int lb = (int)(idx / (NL * NL)), e = (int)(idx % (NL * NL));
+  const int r = e / NL, c = e % NL;
+  double v;
+  if (r < NI) {
+    v = c < NI ? Aii[((long long)lb * NI + r) * NI + c] : Aie[((long long)lb * NI + r) * NE + (c - NI)];
+  } else {
+    v = c < NI ? Ni[((long long)lb * NE + (r - NI)) * NI + c] : Ne[((long long)lb * NE + (r - NI)) * NE + (c - NI)];
+  }
+  L[idx] = make_double2(v, (r >= NI && r == c) ? eta : 0.0);
+  if (c < NE) {  // right-hand sides [0; I] for Y and for L^T
+    const double2 ev = make_double2((r >= NI && r - NI == c) ? 1.0 : 0.0, 0.0);
+    const long long o = ((long long)lb * NL + r) * NE + c;
+    Y[o] = ev;
+    Et[o] = ev;
+  }
+}
+
+// R = I - 2 i eta Y_e, Q = -2 i eta Et_i.
+__global__ void k_leaf_RQ(const double2* __restrict__ Y, const double2* __restrict__ Et, const double* __restrict__ kp,
+                          double2* __restrict__ R, double2* __restrict__ Q, int nleaf) {
+  const double eta = *kp;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nleaf * NL * NE) return;
+  const int lb = (int)(idx / (NL * NE)), e = (int)(idx % (NL * NE));
+  const int r = e / NE, c = e % NE;
+  if (r >= NI) {
+    const double2 y = Y[idx];  // -2 i eta (x + i y) = 2 eta y - 2 i eta x
+    R[((long long)lb * NE + (r - NI)) * NE + c] = make_double2((r - NI == c ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
+  } else if (Q) {
+    const double2 t = Et[idx];
+    Q[((long long)lb * NI + r) * NE + c] = make_double2(2.0 * eta * t.y, -2.0 * eta * t.x);
+  }
+}
+
+void leaf_build_chunk_impedance(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, const double* d_k,
+                                double h, LeafScratchT<double>& w, double2* R, double2* Y, double2* Q, int* info) {
+  (void)k;
+  k_leaf_assemble<double><<<nleaf, 256, 0, s>>>(q, leaf0, d_k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
+  HS_COUNT_LAUNCH();
+  {
+    const long long n = (long long)nleaf * NL * NL;
+    k_leaf_L<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Aii, w.Aie, w.Ni, w.Ne, d_k, w.L, Y, w.Et, nleaf);
+    HS_COUNT_LAUNCH();
+  }
+  lu_factor<double2>(s, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, info, nleaf);
+  lu_solve<double2>(s, OP_N, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, Y, NE, (long long)NL * NE, NE, nleaf);
+  if (Q)
+    lu_solve<double2>(s, OP_T, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, w.Et, NE, (long long)NL * NE, NE, nleaf);
+  {
+    const long long n = (long long)nleaf * NL * NE;
+    k_leaf_RQ<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, w.Et, d_k, R, Q, nleaf);
+    HS_COUNT_LAUNCH();
+  }
+}
+
 template void leaf_build_chunk<double>(cudaStream_t, const double*, int, int, double, const double*, double,
                                        LeafScratchT<double>&, double2*, double2*, double2*, int*);
 template void leaf_build_chunk<float>(cudaStream_t, const double*, int, int, double, const double*, double,

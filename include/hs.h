@@ -67,11 +67,11 @@ typedef struct hs_config {
                            at every k (1 is the usual choice); < 0 or NaN: HS_EINVAL */
   int leaf_impedance;   /* leaf elimination (Sec. 2, HPS leaves): 0 = through the
                            Dirichlet block A_ii (needs k sqrt(1-q) h away from the
-                           leaf's Dirichlet eigenvalues pi sqrt(a^2+b^2); every
-                           context); 1 = one LU of the leaf's impedance system
-                           (incoming impedance on the edge), solvable at every k h;
-                           HS_FP64 contexts only (HS_EINVAL otherwise, and for
-                           values other than 0 and 1) */
+                           leaf's Dirichlet eigenvalues pi sqrt(a^2+b^2)); 1 = one
+                           LU of the leaf's impedance system (incoming impedance on
+                           the edge), solvable at every k h (HS_MIXED contexts keep
+                           its particular-solution operator for the refinement:
+                           0.4 MB per leaf more); other values: HS_EINVAL */
 } hs_config;
 
 /* Create a context on cfg->device (copies cfg).  Allocates nothing large until

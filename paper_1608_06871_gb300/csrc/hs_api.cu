@@ -772,6 +772,11 @@ int setup(hs_ctx* ctx) {
     CKR(dalloc(ctx, &w.piv, nl * NI));
     CKR(dalloc(ctx, &w.pivK, nl * NE));
     CKR(dalloc(ctx, &w.Ainv, nl * NI * NI));
+    if (ctx->cfg.leaf_impedance) {  // every leaf's impedance system and particular-solution operator
+      CKR(dalloc(ctx, &w.L, nl * NL * NL));
+      CKR(dalloc(ctx, &w.pivL, nl * NL));
+      CKR(dalloc(ctx, &w.P, nl * NL * NI));
+    }
   }
   CKR(setup_tree(ctx));
   CKR(setup_boundary(ctx));
@@ -808,8 +813,12 @@ void assemble_exterior_mixed(hs_ctx* ctx, cudaStream_t s, double k) {
 int enqueue_factor_mixed(hs_ctx* ctx, double k, cudaStream_t s, bool record) {
   CK(cudaMemsetAsync(ctx->d_info, 0, sizeof(int) * ctx->ninfo, s));
   if (record) CK(cudaEventRecord(ctx->ph_ev[0], s));
-  leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->d_k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32,
-                          nullptr, ctx->d_info);
+  if (ctx->cfg.leaf_impedance)
+    leaf_build_chunk_impedance<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->d_k, ctx->h, ctx->ws32, ctx->d_R32,
+                                      ctx->d_Y32, nullptr, ctx->d_info);
+  else
+    leaf_build_chunk<float>(s, ctx->d_q, 0, ctx->nleaf, k, ctx->d_k, ctx->h, ctx->ws32, ctx->d_R32, ctx->d_Y32,
+                            nullptr, ctx->d_info);
   const float2* Rc = ctx->d_R32;
   for (size_t li = 0; li < ctx->levels.size(); ++li) {
     merge_level<float2>(s, ctx->levels[li], ctx->ops32[li], Rc, ctx->d_info);
@@ -873,7 +882,7 @@ int factor(hs_ctx* ctx, double k) {
   for (int l0 = 0; l0 < ctx->nleaf; l0 += ctx->chunk) {
     int n = std::min(ctx->chunk, ctx->nleaf - l0);
     if (ctx->cfg.leaf_impedance)
-      leaf_build_chunk_impedance(s, ctx->d_q, l0, n, k, ctx->d_k, ctx->h, ctx->ws,
+      leaf_build_chunk_impedance<double>(s, ctx->d_q, l0, n, k, ctx->d_k, ctx->h, ctx->ws,
                                  ctx->d_Rleaf + (size_t)l0 * NE * NE, ctx->d_Y + (size_t)l0 * NL * NE,
                                  ctx->d_Q + (size_t)l0 * NI * NE, ctx->d_info);
     else
@@ -1388,15 +1397,21 @@ int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2
       std::swap(Lc, Lp);
     }
     // transposed leaf particular solve (Lc: every leaf's h-adjoint)
-    gemm<float, float2, float2>(s, OP_T, OP_N, NE, P, NI, mone, w.Aie, NE, (long long)NI * NE, G, P, sG, one,
-                                G + (long long)NI * P, P, sG, nl);
-    leaf_hadj(s, Lc, nl, eta, P, G);
-    gemm<float2, float2, float2>(s, OP_T, OP_N, NE, P, NE, mone, w.Kinv, NE, (long long)NE * NE, G + (long long)NI * P,
-                                 P, sG, zero, tE, P, (long long)NE * P, nl);
-    gemm<float, float2, float2>(s, OP_T, OP_N, NI, P, NE, one, w.Ni, NI, (long long)NE * NI, tE, P, (long long)NE * P,
-                                one, G, P, sG, nl);
-    gemm<float, float2, float2>(s, OP_T, OP_N, NI, P, NI, one, w.Ainv, NI, (long long)NI * NI, G, P, sG, zero, dY, P,
-                                (long long)NI * P, nl);
+    if (w.P) {  // impedance-form leaves: the interior rows of L^{-T} [g_i; g_e] are P^T [g_i; g_e]
+      leaf_hadj(s, Lc, nl, eta, P, G);
+      gemm<float2, float2, float2>(s, OP_T, OP_N, NI, P, NL, one, w.P, NI, (long long)NL * NI, G, P, sG, zero, dY, P,
+                                   (long long)NI * P, nl);
+    } else {
+      gemm<float, float2, float2>(s, OP_T, OP_N, NE, P, NI, mone, w.Aie, NE, (long long)NI * NE, G, P, sG, one,
+                                  G + (long long)NI * P, P, sG, nl);
+      leaf_hadj(s, Lc, nl, eta, P, G);
+      gemm<float2, float2, float2>(s, OP_T, OP_N, NE, P, NE, mone, w.Kinv, NE, (long long)NE * NE,
+                                   G + (long long)NI * P, P, sG, zero, tE, P, (long long)NE * P, nl);
+      gemm<float, float2, float2>(s, OP_T, OP_N, NI, P, NE, one, w.Ni, NI, (long long)NE * NI, tE, P,
+                                  (long long)NE * P, one, G, P, sG, nl);
+      gemm<float, float2, float2>(s, OP_T, OP_N, NI, P, NI, one, w.Ainv, NI, (long long)NI * NI, G, P, sG, zero, dY,
+                                  P, (long long)NI * P, nl);
+    }
     // accumulate in FP64; the change of Ypde is the stopping quantity
     convert_f2d_add(s, dY, Z64, (long long)nl * NI * P);
     convert_f2d_add(s, f32, Yext, (long long)nbP);
@@ -1663,7 +1678,7 @@ int hs_create(hs_ctx** out, const hs_config* cfg) {
   if (!(cfg->R > std::sqrt(2.0))) return HS_EINVAL;
   if (cfg->precision != HS_FP64 && cfg->precision != HS_MIXED) return HS_EINVAL;
   if (!(cfg->bm_eta >= 0.0) || !std::isfinite(cfg->bm_eta)) return HS_EINVAL;
-  if (cfg->leaf_impedance != 0 && (cfg->leaf_impedance != 1 || cfg->precision != HS_FP64)) return HS_EINVAL;
+  if (cfg->leaf_impedance != 0 && cfg->leaf_impedance != 1) return HS_EINVAL;
   hs_ctx* ctx = new (std::nothrow) hs_ctx();
   if (!ctx) return HS_ENOMEM;
   ctx->cfg = *cfg;

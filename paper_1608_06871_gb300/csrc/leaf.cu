@@ -216,7 +216,8 @@ void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, dou
                   Q, NE, (long long)NI * NE, nleaf);
 }
 
-// Impedance form of the leaf (FP64 contexts, hs_config.leaf_impedance): with the
+// Impedance form of the leaf (hs_config.leaf_impedance; FP64 and, with the
+// particular-solution operator, mixed contexts): with the
 // incoming impedance f = d_n u + i eta u prescribed on the edge nodes,
 //   L [u_i; u_e] = [b; f],   L = [A_ii, A_ie; N_i, N_e + i eta I]   (252 x 252),
 // the interior impedance problem, uniquely solvable at every k, where the
@@ -225,67 +226,99 @@ void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, dou
 // K = N_e - N_i A_ii^{-1} A_ie + i eta I, so the outputs are the ones of the
 // Dirichlet route: the solution operator Y = L^{-1} [0; I] (Y_e = K^{-1},
 // Y_i = -X K^{-1}), R = I - 2 i eta Y_e, and the adjoint body-load operator
-// Q = -2 i eta (L^{-T} [0; I])_i (= 2 i eta A_ii^{-T} N_i^T K^{-T}).
-__global__ void k_leaf_L(const double* __restrict__ Aii, const double* __restrict__ Aie,
-                         const double* __restrict__ Ni, const double* __restrict__ Ne, const double* __restrict__ kp,
-                         double2* __restrict__ L, double2* __restrict__ Y, double2* __restrict__ Et, int nleaf) {
+// Q = -2 i eta (L^{-T} [0; I])_i (= 2 i eta A_ii^{-T} N_i^T K^{-T}).  The mixed
+// path keeps P = L^{-1} [I; 0] instead: a body load b gives the leaf solution
+// P b (its refinement's particular solves) and the transposed solve P^T g (the
+// adjoint's), where the Dirichlet route applies A_ii^{-1}, X and K^{-1}.
+template <typename T>
+__global__ void k_leaf_L(const T* __restrict__ Aii, const T* __restrict__ Aie, const T* __restrict__ Ni,
+                         const T* __restrict__ Ne, const double* __restrict__ kp, typename prec<T>::C* __restrict__ L,
+                         typename prec<T>::C* __restrict__ Y, typename prec<T>::C* __restrict__ Et,
+                         typename prec<T>::C* __restrict__ Pp, int nleaf) {
+  using C = typename prec<T>::C;
   const double eta = *kp;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nleaf * NL * NL) return;
   const int lb = (int)(idx / (NL * NL)), e = (int)(idx % (NL * NL));
   const int r = e / NL, c = e % NL;
-  double v;
+  T v;
   if (r < NI) {
     v = c < NI ? Aii[((long long)lb * NI + r) * NI + c] : Aie[((long long)lb * NI + r) * NE + (c - NI)];
   } else {
     v = c < NI ? Ni[((long long)lb * NE + (r - NI)) * NI + c] : Ne[((long long)lb * NE + (r - NI)) * NE + (c - NI)];
   }
-  L[idx] = make_double2(v, (r >= NI && r == c) ? eta : 0.0);
+  C lv;
+  lv.x = v;
+  lv.y = (r >= NI && r == c) ? T(eta) : T(0);
+  L[idx] = lv;
+  C one, zero;
+  one.x = T(1); one.y = T(0);
+  zero.x = T(0); zero.y = T(0);
   if (c < NE) {  // right-hand sides [0; I] for Y and for L^T
-    const double2 ev = make_double2((r >= NI && r - NI == c) ? 1.0 : 0.0, 0.0);
+    const C ev = (r >= NI && r - NI == c) ? one : zero;
     const long long o = ((long long)lb * NL + r) * NE + c;
     Y[o] = ev;
-    Et[o] = ev;
+    if (Et) Et[o] = ev;
   }
+  if (Pp && c < NI) Pp[((long long)lb * NL + r) * NI + c] = r == c ? one : zero;  // [I; 0]
 }
 
-// R = I - 2 i eta Y_e, Q = -2 i eta Et_i.
-__global__ void k_leaf_RQ(const double2* __restrict__ Y, const double2* __restrict__ Et, const double* __restrict__ kp,
-                          double2* __restrict__ R, double2* __restrict__ Q, int nleaf) {
+// R = I - 2 i eta Y_e, Q = -2 i eta Et_i (Q optional).
+template <typename T>
+__global__ void k_leaf_RQ(const typename prec<T>::C* __restrict__ Y, const typename prec<T>::C* __restrict__ Et,
+                          const double* __restrict__ kp, typename prec<T>::C* __restrict__ R,
+                          typename prec<T>::C* __restrict__ Q, int nleaf) {
+  using C = typename prec<T>::C;
   const double eta = *kp;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nleaf * NL * NE) return;
   const int lb = (int)(idx / (NL * NE)), e = (int)(idx % (NL * NE));
   const int r = e / NE, c = e % NE;
   if (r >= NI) {
-    const double2 y = Y[idx];  // -2 i eta (x + i y) = 2 eta y - 2 i eta x
-    R[((long long)lb * NE + (r - NI)) * NE + c] = make_double2((r - NI == c ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
+    const C y = Y[idx];  // -2 i eta (x + i y) = 2 eta y - 2 i eta x
+    C rv;
+    rv.x = T((r - NI == c ? 1.0 : 0.0) + 2.0 * eta * (double)y.y);
+    rv.y = T(-2.0 * eta * (double)y.x);
+    R[((long long)lb * NE + (r - NI)) * NE + c] = rv;
   } else if (Q) {
-    const double2 t = Et[idx];
-    Q[((long long)lb * NI + r) * NE + c] = make_double2(2.0 * eta * t.y, -2.0 * eta * t.x);
+    const C t = Et[idx];
+    C qv;
+    qv.x = T(2.0 * eta * (double)t.y);
+    qv.y = T(-2.0 * eta * (double)t.x);
+    Q[((long long)lb * NI + r) * NE + c] = qv;
   }
 }
 
+template <typename T>
 void leaf_build_chunk_impedance(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, const double* d_k,
-                                double h, LeafScratchT<double>& w, double2* R, double2* Y, double2* Q, int* info) {
+                                double h, LeafScratchT<T>& w, typename prec<T>::C* R, typename prec<T>::C* Y,
+                                typename prec<T>::C* Q, int* info) {
+  using C = typename prec<T>::C;
   (void)k;
-  k_leaf_assemble<double><<<nleaf, 256, 0, s>>>(q, leaf0, d_k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
+  k_leaf_assemble<T><<<nleaf, 256, 0, s>>>(q, leaf0, d_k, h, w.Aii, w.Aie, w.Ni, w.NiT, w.Ne);
   HS_COUNT_LAUNCH();
+  C* Pp = w.P ? w.P + (long long)leaf0 * NL * NI : nullptr;
   {
     const long long n = (long long)nleaf * NL * NL;
-    k_leaf_L<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Aii, w.Aie, w.Ni, w.Ne, d_k, w.L, Y, w.Et, nleaf);
+    k_leaf_L<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.Aii, w.Aie, w.Ni, w.Ne, d_k, w.L, Y, Q ? w.Et : nullptr,
+                                                            Pp, nleaf);
     HS_COUNT_LAUNCH();
   }
-  lu_factor<double2>(s, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, info, nleaf);
-  lu_solve<double2>(s, OP_N, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, Y, NE, (long long)NL * NE, NE, nleaf);
-  if (Q)
-    lu_solve<double2>(s, OP_T, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, w.Et, NE, (long long)NL * NE, NE, nleaf);
+  lu_factor<C>(s, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, info, nleaf);
+  lu_solve<C>(s, OP_N, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, Y, NE, (long long)NL * NE, NE, nleaf);
+  if (Q) lu_solve<C>(s, OP_T, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, w.Et, NE, (long long)NL * NE, NE, nleaf);
+  if (Pp) lu_solve<C>(s, OP_N, w.L, NL, (long long)NL * NL, NL, w.pivL, NL, Pp, NI, (long long)NL * NI, NI, nleaf);
   {
     const long long n = (long long)nleaf * NL * NE;
-    k_leaf_RQ<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, w.Et, d_k, R, Q, nleaf);
+    k_leaf_RQ<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, w.Et, d_k, R, Q, nleaf);
     HS_COUNT_LAUNCH();
   }
 }
+
+template void leaf_build_chunk_impedance<double>(cudaStream_t, const double*, int, int, double, const double*, double,
+                                                 LeafScratchT<double>&, double2*, double2*, double2*, int*);
+template void leaf_build_chunk_impedance<float>(cudaStream_t, const double*, int, int, double, const double*, double,
+                                                LeafScratchT<float>&, float2*, float2*, float2*, int*);
 
 template void leaf_build_chunk<double>(cudaStream_t, const double*, int, int, double, const double*, double,
                                        LeafScratchT<double>&, double2*, double2*, double2*, int*);

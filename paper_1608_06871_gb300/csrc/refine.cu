@@ -496,6 +496,16 @@ void leaf_particular(cudaStream_t s, const LeafScratchT<float>& w, int nleaf, co
                      float2* H, float2* tmp, float2* wtmp) {
   const long long sU = (long long)NL * nrhs;
   const float2 one = make_float2(1.f, 0.f), mone = make_float2(-1.f, 0.f), zero = make_float2(0.f, 0.f);
+  if (w.P) {  // impedance-form leaves: [u_i; u_e] = P b in one product (b staged in wtmp)
+    cudaMemcpy2DAsync(wtmp, (size_t)NI * nrhs * sizeof(float2), Upart, sU * sizeof(float2),
+                      (size_t)NI * nrhs * sizeof(float2), nleaf, cudaMemcpyDeviceToDevice, s);
+    gemm<float2, float2, float2>(s, OP_N, OP_N, NL, nrhs, NI, one, w.P, NI, (long long)NL * NI, wtmp, nrhs,
+                                 (long long)NI * nrhs, zero, Upart, nrhs, sU, nleaf);
+    const long long n = (long long)nleaf * NE * nrhs;
+    k_leaf_h<<<blocks(n), 256, 0, s>>>(Upart, nleaf, d_k, nrhs, H);
+    HS_COUNT_LAUNCH();
+    return;
+  }
   if (w.Ainv && wtmp) {
     gemm<float, float2, float2>(s, OP_N, OP_N, NI, nrhs, NI, one, w.Ainv, NI, (long long)NI * NI, Upart, nrhs, sU,
                                 zero, wtmp, nrhs, (long long)NI * nrhs, nleaf);

@@ -19,7 +19,9 @@ template <typename T> struct LeafScratchT {  // leaf build scratch; in the mixed
   C *K, *Kinv;
   int *piv, *pivK;
   T* Ainv = nullptr;  // mixed path: Aii^{-1} explicitly (the particular solves apply it with one GEMM)
-  C *L = nullptr, *Et = nullptr;  // impedance form (FP64): the 252 x 252 leaf system and L^{-T} [0; I]
+  // impedance form: the 252 x 252 leaf system, L^{-T} [0; I] (FP64 adjoint operator Q), and
+  // the particular-solution operator P = L^{-1} [I; 0] (mixed path: refinement body loads)
+  C *L = nullptr, *Et = nullptr, *P = nullptr;
   int* pivL = nullptr;
 };
 using LeafScratch = LeafScratchT<double>;
@@ -60,11 +62,14 @@ template <typename T>
 void leaf_build_chunk(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, const double* d_k, double h,
                       LeafScratchT<T>& w, typename prec<T>::C* R, typename prec<T>::C* Y, typename prec<T>::C* Q,
                       int* info);
-// The same outputs (R, Y, Q) from the impedance form of the leaf problem (FP64; needs w.L,
-// w.Et, w.pivL): one LU of the 252 x 252 complex system with the incoming impedance on the
-// edge, solvable where A_ii is singular (the leaf's Dirichlet eigenvalues).
+// The same outputs (R, Y, and Q when non-NULL, with w.Et) from the impedance form of the
+// leaf problem (needs w.L, w.pivL): one LU of the 252 x 252 complex system with the incoming
+// impedance on the edge, solvable where A_ii is singular (the leaf's Dirichlet eigenvalues);
+// with w.P also the particular-solution operator L^{-1} [I; 0] for the chunk's leaves.
+template <typename T>
 void leaf_build_chunk_impedance(cudaStream_t s, const double* q, int leaf0, int nleaf, double k, const double* d_k,
-                                double h, LeafScratchT<double>& w, double2* R, double2* Y, double2* Q, int* info);
+                                double h, LeafScratchT<T>& w, typename prec<T>::C* R, typename prec<T>::C* Y,
+                                typename prec<T>::C* Q, int* info);
 
 template <typename C> void merge_level(cudaStream_t s, const LevelMaps& L, const LevelOps<C>& O, const C* Rc, int* info);
 // Downward sweep of one level.  If t3_loaded, T3 already holds the particular

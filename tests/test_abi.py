@@ -49,8 +49,7 @@ def test_bad_configs_are_rejected_without_a_gpu(lib):
     L = lib.lib()
     ctx = ctypes.c_void_p()
     for kw in (dict(leaves_per_side=3), dict(leaves_per_side=0), dict(S1=0), dict(R=1.0), dict(precision=7),
-               dict(bm_eta=-1.0), dict(bm_eta=float("nan")), dict(leaf_impedance=2),
-               dict(leaf_impedance=1, precision=1)):
+               dict(bm_eta=-1.0), dict(bm_eta=float("nan")), dict(leaf_impedance=2), dict(leaf_impedance=-1)):
         base = dict(R=3.0, leaves_per_side=4, S1=4, S2=4, precision=0, device=0, stream=None,
                     refine_tol=0.0, refine_max_iter=0, bm_eta=0.0, leaf_impedance=0)
         base.update(kw)

@@ -24,13 +24,14 @@ def embed(c: np.ndarray, S1: int, S2: int) -> np.ndarray:
 
 
 def sweep(plans, data_fn, lambda_rel: float, c0=None, R: float | None = None, solver: str = "direct",
-          lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200):
+          lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200, eta: float = 0.0):
     """plans: objects with k, leaves_per_side, S, M, P, newton (increasing k), and
     optionally R and mask() (the unknown modes; None = all).
 
     data_fn(plan, alphas, thetas) -> measured far field (M x P complex).
     solver: "direct" = normal equations with lambda_rel (eq. normaleq); "lsqr" = the
     paper's LSQR at lsqr_tol on the plan's modes (Sec. 4).
+    eta: exterior rows of the forward map (0 Green's identity, > 0 Burton-Miller, bie.exterior_rows).
     Returns the final coefficients and the residual norms per frequency.
     """
     c = np.zeros((plans[0].S, plans[0].S)) if c0 is None else np.asarray(c0, dtype=np.float64)
@@ -44,7 +45,7 @@ def sweep(plans, data_fn, lambda_rel: float, c0=None, R: float | None = None, so
         radius = getattr(p, "R", 3.0) if R is None else R
         mask = p.mask() if hasattr(p, "mask") else None
         for _ in range(p.newton):
-            fw = F.forward_from_coeffs(c, p.k, p.leaves_per_side, radius)
+            fw = F.forward_from_coeffs(c, p.k, p.leaves_per_side, radius, eta)
             Fc, _ = fw.solve_plane(al, th)
             J = fw.jacobian(al, th, p.S, p.S)
             r = (data - Fc).ravel()

@@ -42,6 +42,27 @@ def test_sweep_matches_oracle_sweep(hs):
         assert np.allclose(h_gpu["residuals"], h_ref, rtol=1e-8)
 
 
+def test_sweep_through_a_dirichlet_eigenvalue_with_combined_rows(hs):
+    """A sweep whose middle frequency is a Dirichlet eigenvalue of the square, (pi/2) sqrt(5):
+    with the combined-field exterior rows (bm_eta = 1) every step is well posed and the GPU sweep
+    follows the oracle's sweep on the same rows."""
+    import math
+    from paper_1608_06871_gb300 import sweep as SW
+    plans = [SW.plan_ceil(k) for k in (3.0, 0.5 * math.pi * math.sqrt(5.0), 4.0)]
+    qt = synth.gaussian_bumps(7)
+    cache = {}
+
+    def data_fn(p, al, th):
+        if p.k not in cache:
+            cache[p.k] = F.forward_from_function(qt, p.k, p.leaves_per_side, eta=1.0).solve_plane(al, th)[0]
+        return cache[p.k]
+    res = SW.recursive_linearization(plans, data_fn, lambda_rel=1e-4, bm_eta=1.0)
+    c_ref, hist = OS.sweep(plans, data_fn, 1e-4, eta=1.0)
+    assert rel(res.c, c_ref) < 1e-7
+    for h_gpu, h_ref in zip(res.history, hist):
+        assert np.allclose(h_gpu["residuals"], h_ref, rtol=1e-8)
+
+
 def test_sweep_checkpoint_resume(hs, tmp_path):
     from paper_1608_06871_gb300 import sweep as SW
     plans = [SW.plan_ceil(k) for k in (2.0, 2.5, 3.0)]

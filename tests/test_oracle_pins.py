@@ -257,6 +257,24 @@ def test_jacobian_matches_finite_differences():
         assert np.abs(fd - J[:, m]).max() < 2e-6 * np.abs(J[:, m]).max()
 
 
+def test_jacobian_with_combined_rows_at_an_eigenvalue_matches_finite_differences():
+    """The oracle's Frechet Jacobian (one solve per mode of the assembled system) with the
+    Burton-Miller exterior rows, at the Dirichlet eigenvalue k = (pi/2) sqrt(5) where the Green
+    rows alone are singular, against central differences of its own forward map (2 x 2 leaves)."""
+    S, h, k = 3, 1e-5, 0.5 * math.pi * math.sqrt(5.0)
+    al, th = synth.directions(2), synth.receivers(4)
+    c = synth.random_coeffs(S, S, seed=6, scale=0.03)
+    J = F.forward_from_coeffs(c, k, 2, eta=1.0).jacobian(al, th, S, S)
+    for m in (0, 4, 8):
+        cp, cm = c.copy(), c.copy()
+        cp.flat[m] += h
+        cm.flat[m] -= h
+        up, _ = F.forward_from_coeffs(cp, k, 2, eta=1.0).solve_plane(al, th)
+        um, _ = F.forward_from_coeffs(cm, k, 2, eta=1.0).solve_plane(al, th)
+        fd = ((up - um) / (2 * h)).ravel()
+        assert np.abs(fd - J[:, m]).max() < 2e-6 * np.abs(J[:, m]).max()
+
+
 def test_misfit_gradient_matches_finite_differences():
     """Central differences of 0.5 ||F(c) - d||^2 in single coefficients (k = 5, 4 x 4 leaves)
     against Re J^H (F - d): a dropped conjugate, a transposed J or a flipped residual sign fails.

@@ -621,7 +621,7 @@ def sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=False, compare_fp64=Fals
     one Gauss-Newton step per frequency, blurred-ellipse phantom (seed 7) plus
     1% complex Gaussian noise.  FP64 with the direct normal equations, or
     (mixed_lsqr) on mixed-precision contexts with LSQR at 1e-3 on the
-    tensor-core Jacobian.  The data of every frequency are computed first on
+    FP32 Jacobian.  The data of every frequency are computed first on
     the GPU (untimed); the timed region is the whole sweep."""
     from paper_1608_06871_gb300 import sweep as SW
     plans = [SW.plan_ceil(float(k)) for k in np.arange(1.0, k_max + 0.25, 0.5)]
@@ -646,7 +646,7 @@ def sweep_time(hs, torch, local, k_max=10.0, mixed_lsqr=False, compare_fp64=Fals
     dt = time.perf_counter() - t0
     S = res.c.shape[0]
     c_true = synth.project_sine(phantom, S, S, nq=max(256, 4 * S))
-    how = ("mixed precision, LSQR at 1e-3 on the tensor-core Jacobian" if mixed_lsqr
+    how = ("mixed precision, LSQR at 1e-3 on the FP32 Jacobian" if mixed_lsqr
            else "FP64, direct normal equations (lambda_rel 1e-4)")
     extra = {}
     if compare_fp64 and mixed_lsqr:
@@ -893,7 +893,7 @@ def paper_scale_sweep(hs, torch, local, k_max=70.0):
     """The paper-scale reconstruction: k = 1, 1.25, .., 70 (277 frequencies, plan_c5:
     S = floor(2k) modes per axis up to 140 x 140 = 19,600, M = P = ceil(4k) up to 280,
     leaves up to 128 x 128), one Gauss-Newton step per frequency by LSQR at 1e-3 on a
-    mixed-precision context with the tensor-core Jacobian.  Contrast: the 40-inclusion
+    mixed-precision context with the FP32 Jacobian.  Contrast: the 40-inclusion
     phantom (seed 5, max|q| = 0.5), data from the mixed solver on the same tree plus 1%
     noise (seed 70), generated before the timed sweep.  Reports rows at k = 1, 2, 4, ..,
     64, 70 like Table 2 (N, Modes, M*P, T_f, N_it, T_l, T_t) and the final coefficients'
@@ -982,7 +982,7 @@ def paper_scale_gn(hs, torch, local):
     k = 70, 128 x 128 leaves, 140 x 140 = 19,600 sine unknowns, 280 incidences x 280
     receivers (J: 78,400 x 19,600 complex).  Two ways, one timed run each (CUDA
     events): the paper's LSQR at 1e-3 on a mixed-precision context with the
-    tensor-core Jacobian (hs_build + hs_gn_step_lsqr), and the FP64 direct step
+    FP32 Jacobian (hs_build + hs_gn_step_lsqr), and the FP64 direct step
     (hs_build + hs_gn_step: Jacobian contraction, symmetric normal matrix, LU).
     Data: the 40-inclusion contrast (seed 5, max|q| = 0.5) plus 1% noise; the
     step starts from its first 120 x 120 coefficients."""
@@ -1069,13 +1069,13 @@ def gn_step_top(hs, torch, local):
                     "adjoint_refine_passes": adj[0], "adjoint_est_rel_error": adj[2],
                     "includes": "hs_build + hs_gn_step on a mixed context (FP32 factors; forward and adjoint "
                                 "fields refined in FP64; FP64 contraction and normal equations)"}
-    variants = (("fp64_products", s, hs.HS_FP64), ("tensor_core_jacobian", s, hs.HS_MIXED),
+    variants = (("fp64_products", s, hs.HS_FP64), ("fp32_jacobian", s, hs.HS_MIXED),
                 ("mixed_factors_fp64_products", sm, hs.HS_FP64),
-                ("mixed_factors_tensor_core_jacobian", sm, hs.HS_MIXED))
+                ("mixed_factors_fp32_jacobian", sm, hs.HS_MIXED))
     lsqr_out = {"tolerance": 1e-3,
                 "includes": "hs_build + hs_gn_step_lsqr: forward, adjoint sweep, LSQR; fp64_products = J and J^H "
-                            "applied from the fields in FP64 every iteration; tensor_core_jacobian = J formed once "
-                            "in complex FP32 on the tensor cores, LSQR products read it with FP64 sums; "
+                            "applied from the fields in FP64 every iteration; fp32_jacobian = J formed once "
+                            "in complex FP32 (the Khatri-Rao rows and two SIMT FP32 projections), LSQR products read it with FP64 sums; "
                             "mixed_factors = FP32 factors with forward and adjoint fields refined in FP64",
                 "step_rel_diff_vs_fp64_at": "20 iterations each (tol 0)"}
     steps20 = {}
@@ -1098,7 +1098,7 @@ def gn_step_top(hs, torch, local):
         lsqr_out[name]["step_rel_diff_vs_fp64"] = float(np.linalg.norm(steps20[name] - steps20["fp64_products"]) /
                                                         np.linalg.norm(steps20["fp64_products"]))
     lsqr_out["mixed_speedup_vs_fp64_products"] = (lsqr_out["fp64_products"]["ms"] /
-                                                  lsqr_out["mixed_factors_tensor_core_jacobian"]["ms"])
+                                                  lsqr_out["mixed_factors_fp32_jacobian"]["ms"])
     s.build(c, w.k)
     J = torch.empty((w.M * w.P, w.S * w.S, 2), dtype=torch.float64, device="cuda")
     a_d, t_d = torch.tensor(al, device="cuda"), torch.tensor(th, device="cuda")

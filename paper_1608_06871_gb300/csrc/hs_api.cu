@@ -1312,7 +1312,7 @@ size_t mixed_adjoint_bytes(hs_ctx* ctx, int P) {
 // contraction rate rho, the error estimate is the change times rho / (1 - rho).
 // Z64: [leaf][196][P] (FP64, output).  A2: [P][2 nb] FP64.
 // With refine == false one pass (the FP32 transposed solve of L) is returned:
-// for products that carry FP32 rounding anyway (the tensor-core Jacobian).
+// for products that carry FP32 rounding anyway (the explicit FP32 Jacobian).
 // passes: 0 = refine to refine_tol (HS_ENOCONV after refine_max_iter passes);
 // n > 0 = exactly n passes (the FP32 solve and n - 1 FP64-residual corrections).
 int mixed_adjoint(hs_ctx* ctx, cudaStream_t s, const double2* A2, int P, double2* Z64, Arena& a, int passes = 0) {

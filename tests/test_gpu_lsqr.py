@@ -145,8 +145,8 @@ def k5_setup(hs):
     return w, al, th, data, 0.3 * synth.project_sine(qt, w.S, w.S)
 
 
-def test_tensor_core_jacobian_k40(hs):
-    """k = 40 top-of-sweep size: LSQR on the complex FP32 Jacobian formed on the tensor cores
+def test_fp32_jacobian_k40(hs):
+    """k = 40 top-of-sweep size: LSQR on the explicit complex FP32 Jacobian
     (products with FP64 sums) against LSQR with the FP64 products from the fields.  With the
     same 20 iterations the steps agree to 1e-4 (measured 9e-6: the FP32 Jacobian's error, not
     amplified because both products apply the same matrix); at the paper's tolerance the

@@ -193,7 +193,7 @@ def test_degenerate_one_of_everything(hs, prec):
     assert rel(c1.ravel() - c.ravel(), dc_ref) < 1e-7
     c2, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5)
     assert it == 1 and rel(c2.ravel() - c.ravel(), dc_ref) < 1e-7  # one unknown: one iteration is exact
-    if prec == "mixed":  # the FP32 tensor-core Jacobian in the LSQR products: FP32 accuracy
+    if prec == "mixed":  # the explicit FP32 Jacobian in the LSQR products: FP32 accuracy
         c3, _, it = S.gn_step_lsqr(data, al, th, c, tol=1e-12, max_iter=5, products=hs.HS_MIXED)
         assert it == 1 and rel(c3.ravel() - c.ravel(), dc_ref) < 1e-4
     S.close()

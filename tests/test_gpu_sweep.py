@@ -131,7 +131,7 @@ def test_paper_plan_lsqr_sweep_matches_oracle(hs):
 def test_mixed_lsqr_sweep_tracks_fp64(hs):
     """k = 2, 2.5, 3 with LSQR at 1e-3: mixed-precision contexts against FP64 contexts (same plan
     and data).  With FP64 products (refined forward and adjoint fields) the sweep meets the 1e-7
-    coefficient bar with the same LSQR iteration counts; with the FP32 tensor-core Jacobian in the
+    coefficient bar with the same LSQR iteration counts; with the explicit FP32 Jacobian in the
     products it differs by FP32 rounding amplified by the early-stopped iteration (bar 1e-3,
     iteration counts within 3 per frequency)."""
     from paper_1608_06871_gb300 import sweep as SW

@@ -140,15 +140,29 @@ def _graded_rule(h: float, s_star: float):
     return np.concatenate(offs), np.concatenate(weights)
 
 
+_RULES: dict = {}
+
+
+def _graded_basis(t: np.ndarray, h: float, s_star: float):
+    """(_graded_rule(h, s_star), the panel's Lagrange basis at its points), computed once per
+    distinct (panel nodes, h, s_star): the targets of a boundary meet only a few offsets s_star
+    (the panel nodes and the panel ends), so the rule is shared by every target at that offset.
+    The arrays are shared: callers only read them."""
+    key = (tuple(t), h, s_star)
+    if key not in _RULES:
+        sig, w = _graded_rule(h, s_star)
+        _RULES[key] = (sig, w, lagrange_eval(t, 2.0 * (s_star + sig) / h - 1.0))
+    return _RULES[key]
+
+
 def product_weights(bd: Boundary, k: float, x: np.ndarray, q: int):
     """int_panel K(x, y(s)) L_j(s) ds for K = G and K = dG/dn_y, j over the panel nodes."""
     y0, tau, ny = bd.start[q], bd.tangent[q], bd.normal[q]
     s_star = float(np.clip(np.dot(x - y0, tau), 0.0, bd.h))
-    sig, w = _graded_rule(bd.h, s_star)
+    sig, w, L = _graded_basis(bd.t, bd.h, s_star)     # L: (nq, 14) Lagrange basis at the points
     perp = x - (y0 + s_star * tau)                  # x - y(s_star)
     dvec = perp[None, :] - sig[:, None] * tau[None, :]  # x - y(s_star + sigma)
     r = np.sqrt(np.sum(dvec * dvec, axis=-1))
-    L = lagrange_eval(bd.t, 2.0 * (s_star + sig) / bd.h - 1.0)  # (nq, 14)
     g = 0.25j * hankel1(0, k * r) * w
     dg = 0.25j * k * hankel1(1, k * r) * (dvec @ ny) / r * w
     return g @ L, dg @ L
@@ -212,11 +226,10 @@ def normal_tangent_matrices(bd: Boundary, k: float):
         for q in near[p]:
             y0, tau = bd.start[q], bd.tangent[q]
             s_star = float(np.clip(np.dot(X[i] - y0, tau), 0.0, bd.h))
-            sig, w = _graded_rule(bd.h, s_star)
+            sig, w, L = _graded_basis(bd.t, bd.h, s_star)
             perp = X[i] - (y0 + s_star * tau)
             dvec = perp[None, :] - sig[:, None] * tau[None, :]
             rr = np.sqrt(np.sum(dvec * dvec, axis=-1))
-            L = lagrange_eval(bd.t, 2.0 * (s_star + sig) / bd.h - 1.0)
             base = -0.25j * k * hankel1(1, k * rr) / rr * w
             Kp[i, q * npn:(q + 1) * npn] = (base * (dvec @ nx)) @ L
             kt = base * (dvec @ txi)

@@ -506,8 +506,8 @@ def run_hs(args, world, rank, local):
                                              else "measured FP32 FFMA rate (hs_peak_fp32, this run)"),
                              "traffic": GEMM64_TRAFFIC if (fp64_fam and prec == hs.HS_MIXED) else None,
                              "traffic_note": GEMM64_TRAFFIC_NOTE if (fp64_fam and prec == hs.HS_MIXED) else
-                             "a family of dozens of product shapes per step: per-shape DRAM traffic is in "
-                             "profiles/launches_mixed_k40_32x32.md's reading, not one figure",
+                             "a family of dozens of product shapes per step (the sweeps', merges', leaf and root "
+                             "products): no single DRAM figure describes it",
                              "launches": gemm_n,
                              "kernel_ms_per_step": gemm_ms / (args.steps if fp64_fam else 1),
                              "algorithmic_tflop_per_step": gemm_flops / (args.steps if fp64_fam else 1) / 1e12,

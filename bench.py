@@ -560,10 +560,10 @@ def run_hs(args, world, rank, local):
 # 3584 complex, two per step), from an ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum); its algorithmic bytes are
 # 117.5 MB (the 1792 x 3584 matrix, the right-hand sides, C read and written).
-GEMM64_TRAFFIC = 114.5e6
-GEMM64_TRAFFIC_NOTE = ("bytes per launch of the 1792x128x3584 complex exterior-residual GEMM (ncu dram read+write, "
-                       "110.2 MB + 1.2-4.3 MB); algorithmic 117.5 MB; the step's other FP64 GEMM, the far field "
-                       "128x256x3584, moves 22.1 MB")
+GEMM64_TRAFFIC = None
+GEMM64_TRAFFIC_NOTE = ("the mixed step's large FP64 products (exterior residual, far field) run on the emulated FP64 "
+                       "product; the FP64 SIMT GEMMs left are small and their ncu traffic was taken on kernels that "
+                       "have changed since")
 
 
 def tensor_gemm_standalone(hs, torch):

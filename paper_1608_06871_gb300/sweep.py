@@ -155,7 +155,8 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
                             R: float | None = None, precision: int = HS_FP64, device: int = 0,
                             checkpoint_dir: str | None = None, angles=None, solver: str = "direct",
                             lsqr_tol: float = 1e-3, lsqr_max_iter: int = 200,
-                            lsqr_products: int = HS_FP64, bm_eta: float = 0.0) -> SweepResult:
+                            lsqr_products: int = HS_FP64, bm_eta: float = 0.0,
+                            leaf_impedance: bool = False) -> SweepResult:
     """Run the sweep.
 
     plans:   list of FrequencyPlan with increasing k.
@@ -167,6 +168,9 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
     R:       receiver radius overriding the plans' own.
     bm_eta:  exterior rows of every solver (hs_config.bm_eta): 0 Green's identity, > 0 the
              combined-field rows, solvable at the square's Dirichlet eigenvalues.
+    leaf_impedance: leaf elimination of every solver (hs_config.leaf_impedance): through the
+             leaf's impedance system, solvable at every k h (plans with coarser leaves,
+             e.g. plan_paper(k, leaf_kh=math.pi)), instead of the Dirichlet block.
     Each history entry records the build (factorisation) time t_f and the
     least-squares time t_l of every step in seconds, and the LSQR iterations.
     """
@@ -194,7 +198,8 @@ def recursive_linearization(plans, data_fn, lambda_rel: float = 1e-4, c0: np.nda
             for old in solvers.values():
                 old.close()
             solvers.clear()  # one tree at a time keeps device memory bounded
-            solvers[key] = Solver(p.leaves_per_side, p.S, p.S, radius, precision, device, bm_eta=bm_eta)
+            solvers[key] = Solver(p.leaves_per_side, p.S, p.S, radius, precision, device, bm_eta=bm_eta,
+                                  leaf_impedance=leaf_impedance)
         slv = solvers[key]
         al, th = angles(p)
         data = data_fn(p, al, th)
